@@ -1,0 +1,291 @@
+"""Plain FP64 CPU oracle of the narrow-band first-order upwind level-set method.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` are the only callers.  The
+product path (the CUDA library and its binding) never imports this package,
+and this package imports nothing from the product.
+
+What it computes, and where the paper defines it (arXiv 1612.04040):
+
+* ``step``            -- Eq. 3-5 (section 1), one explicit upwind step on the
+                         points of active tiles; every other point is frozen.
+* ``classify``        -- Eq. 6 (section 1.1), tube T tested per tile.
+* ``dilate``          -- Eq. 11 (section 1.1), region N as a one-tile dilation.
+* ``compact``         -- the array of active points (section 2), as tile ids.
+* ``max_abs_speed``   -- CFL bound (the paper gives no rule for dt in Eq. 3).
+* ``Oracle``          -- the rebuild / step schedule of Steps 0-2 of the
+                         narrow-band algorithm (section 1.1), with the same
+                         call semantics as the C ABI of the library.
+
+The arithmetic lives in ``levelset_oracle.c`` (plain C, no FMA contraction);
+this module only marshals arrays and runs the schedule.  Parity pins are in
+``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "levelset_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BC = {"extrapolate": 0, "neumann": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle in place (gcc, -O2, no FMA contraction, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            dp = ctypes.POINTER(ctypes.c_double)
+            u8p = ctypes.POINTER(ctypes.c_uint8)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            ci, cd, c64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
+            lib.orc_point_update.restype = cd
+            lib.orc_point_update.argtypes = [ci, ci, ci, cd, ci, dp, cd, cd, ci, ci, ci]
+            lib.orc_step.restype = None
+            lib.orc_step.argtypes = [ci, ci, ci, cd, ci, dp, dp, cd, u8p, ci, cd, dp]
+            lib.orc_step_points.restype = None
+            lib.orc_step_points.argtypes = [ci, ci, ci, cd, ci, dp, dp, cd, i64p, c64, dp]
+            lib.orc_classify.restype = None
+            lib.orc_classify.argtypes = [ci, ci, ci, ci, dp, cd, u8p]
+            lib.orc_dilate.restype = None
+            lib.orc_dilate.argtypes = [ci, ci, ci, u8p, ci, u8p]
+            lib.orc_compact.restype = c64
+            lib.orc_compact.argtypes = [u8p, c64, i32p]
+            lib.orc_max_abs_speed.restype = cd
+            lib.orc_max_abs_speed.argtypes = [ci, ci, ci, ci, dp, cd, u8p]
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _ptr(a, ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def tiles_shape(shape, tile):
+    nz, ny, nx = shape
+    return (-(-nz // tile), -(-ny // tile), -(-nx // tile))
+
+
+def step(phi, h, dt, F=None, Fc=0.0, tile_active=None, tile=8, bc="extrapolate"):
+    """Eq. 3-5: one upwind step.  phi: (nz, ny, nx) array.  F: field or None
+    (then the constant Fc).  tile_active: (tnz, tny, tnx) flags or None for the
+    whole domain."""
+    lib = _load()
+    phi = _f64(phi)
+    nz, ny, nx = phi.shape
+    Fa = None if F is None else _f64(F)
+    if Fa is not None and Fa.shape != phi.shape:
+        raise ValueError("F shape")
+    ta = None
+    if tile_active is not None:
+        ta = np.ascontiguousarray(tile_active, dtype=np.uint8)
+        if ta.shape != tiles_shape(phi.shape, tile):
+            raise ValueError("tile_active shape")
+    out = np.empty_like(phi)
+    lib.orc_step(nx, ny, nz, float(h), BC[bc], _ptr(phi, ctypes.c_double),
+                 _ptr(Fa, ctypes.c_double), float(Fc), _ptr(ta, ctypes.c_uint8), int(tile),
+                 float(dt), _ptr(out, ctypes.c_double))
+    return out
+
+
+def step_points(phi, h, dt, flat_idx, F_at_pts, bc="extrapolate"):
+    """Eq. 3-5 evaluated at selected flat indices of phi (no other point is
+    touched).  F_at_pts: the speed at each selected point."""
+    lib = _load()
+    phi = _f64(phi)
+    nz, ny, nx = phi.shape
+    idx = np.ascontiguousarray(flat_idx, dtype=np.int64)
+    fp = _f64(np.broadcast_to(np.asarray(F_at_pts, dtype=np.float64), idx.shape))
+    out = np.empty(idx.shape, dtype=np.float64)
+    lib.orc_step_points(nx, ny, nz, float(h), BC[bc], _ptr(phi, ctypes.c_double),
+                        _ptr(fp, ctypes.c_double), float(dt), _ptr(idx, ctypes.c_int64),
+                        int(idx.size), _ptr(out, ctypes.c_double))
+    return out
+
+
+def classify(phi, gamma, tile=8):
+    """Eq. 6 per tile: 1 where some point of the tile has |phi| < gamma."""
+    lib = _load()
+    phi = _f64(phi)
+    nz, ny, nx = phi.shape
+    core = np.zeros(tiles_shape(phi.shape, tile), dtype=np.uint8)
+    lib.orc_classify(nx, ny, nz, int(tile), _ptr(phi, ctypes.c_double), float(gamma),
+                     _ptr(core, ctypes.c_uint8))
+    return core
+
+
+def dilate(core, conn=26):
+    """Eq. 11 as a one-tile dilation of the core set (6 or 26 neighbours)."""
+    lib = _load()
+    core = np.ascontiguousarray(core, dtype=np.uint8)
+    tnz, tny, tnx = core.shape
+    active = np.zeros_like(core)
+    lib.orc_dilate(tnx, tny, tnz, _ptr(core, ctypes.c_uint8), int(conn),
+                   _ptr(active, ctypes.c_uint8))
+    return active
+
+
+def compact(flags):
+    """Ascending ids of the set flags (the active array of section 2)."""
+    lib = _load()
+    f = np.ascontiguousarray(flags, dtype=np.uint8).reshape(-1)
+    ids = np.empty(f.size, dtype=np.int32)
+    n = lib.orc_compact(_ptr(f, ctypes.c_uint8), f.size, _ptr(ids, ctypes.c_int32))
+    return ids[:n].copy()
+
+
+def max_abs_speed(shape, F=None, Fc=0.0, tile_active=None, tile=8):
+    """max |F| over the points of active tiles (every point if tile_active is
+    None); 0 if there is none."""
+    lib = _load()
+    nz, ny, nx = shape
+    Fa = None if F is None else _f64(F)
+    ta = None if tile_active is None else np.ascontiguousarray(tile_active, dtype=np.uint8)
+    return float(lib.orc_max_abs_speed(nx, ny, nz, int(tile), _ptr(Fa, ctypes.c_double),
+                                       float(Fc), _ptr(ta, ctypes.c_uint8)))
+
+
+DT_FIXED, DT_CFL = 0, 1
+
+
+class Oracle:
+    """The narrow-band schedule (section 1.1, Steps 1-2) with the library's
+    call semantics:
+
+    * ``band_rebuild(halfwidth)``: gamma = halfwidth*h (FP64); core tiles by
+      Eq. 6 on the whole grid, active = dilation of core; M = max|F| over the
+      active points (CFL bound).
+    * ``step(nsteps, dt_or_cfl, mode, rebuild_every)``: before each step, the
+      band is rebuilt if it is stale (after ``set_phi`` / ``set_speed``) or if
+      ``rebuild_every`` steps have run since the last rebuild.  dt = CFL*h/M
+      (CFL*h when M = 0) in DT_CFL mode, else dt_or_cfl.
+    * full-domain mode: every tile active, no rebuilds, M over the whole grid.
+    """
+
+    def __init__(self, shape, h, tile=8, conn=26, bc="extrapolate"):
+        self.shape = tuple(int(s) for s in shape)
+        self.h = float(h)
+        self.tile = int(tile)
+        self.conn = int(conn)
+        self.bc = bc
+        self.tshape = tiles_shape(self.shape, self.tile)
+        self.phi = None
+        self.F = None
+        self.Fc = None
+        self.full_domain = False
+        self.halfwidth = None
+        self.active = None
+        self.band_valid = False
+        self.since_rebuild = 0
+        self.M = None
+        self.last_dt = None
+        self.rebuild_log = []  # active-tile id arrays, one per rebuild
+
+    # -- state -----------------------------------------------------------
+    def set_phi(self, phi):
+        phi = _f64(phi).reshape(self.shape)
+        if not np.all(np.isfinite(phi)):
+            raise ValueError("non-finite phi")
+        self.phi = phi.copy()
+        self.band_valid = False
+
+    def set_speed(self, F):
+        F = _f64(F).reshape(self.shape)
+        if not np.all(np.isfinite(F)):
+            raise ValueError("non-finite F")
+        self.F, self.Fc = F.copy(), None
+        self.band_valid = False
+
+    def set_speed_const(self, Fc):
+        self.F, self.Fc = None, float(Fc)
+        self.band_valid = False
+
+    def set_full_domain(self, on):
+        self.full_domain = bool(on)
+        self.band_valid = False
+
+    # -- band ------------------------------------------------------------
+    def _speed_bound(self, active):
+        if self.F is None and self.Fc is None:
+            return None
+        return max_abs_speed(self.shape, self.F, self.Fc or 0.0, active, self.tile)
+
+    def _rebuild(self):
+        gamma = self.halfwidth * self.h
+        # Eq. 6 over the whole grid every time (the plain definition; the
+        # library scans only the previous active set, and the tests check the
+        # two agree).
+        core = classify(self.phi, gamma, self.tile)
+        self.active = dilate(core, self.conn)
+        self.M = self._speed_bound(self.active)
+        self.band_valid = True
+        self.since_rebuild = 0
+        self.rebuild_log.append(compact(self.active))
+
+    def band_rebuild(self, halfwidth):
+        self.halfwidth = float(halfwidth)
+        self._rebuild()
+        return int(self.active.sum())
+
+    def active_tiles(self):
+        return compact(self.active)
+
+    # -- stepping ----------------------------------------------------------
+    def step(self, nsteps, dt_or_cfl, mode=DT_CFL, rebuild_every=0):
+        if self.phi is None:
+            raise RuntimeError("phi not set")
+        if mode == DT_CFL and self.F is None and self.Fc is None:
+            raise RuntimeError("speed not set")
+        if self.F is None and self.Fc is None:
+            raise RuntimeError("speed not set")
+        for _ in range(int(nsteps)):
+            if self.full_domain:
+                if not self.band_valid:
+                    self.M = self._speed_bound(None)
+                    self.band_valid = True
+                active = None
+            else:
+                if self.halfwidth is None:
+                    raise RuntimeError("no band")
+                if not self.band_valid:
+                    self._rebuild()
+                elif rebuild_every > 0 and self.since_rebuild >= rebuild_every:
+                    self._rebuild()
+                active = self.active
+            if mode == DT_CFL:
+                dt = float(dt_or_cfl) * self.h / self.M if self.M > 0 else float(dt_or_cfl) * self.h
+            else:
+                dt = float(dt_or_cfl)
+            self.phi = step(self.phi, self.h, dt, self.F, self.Fc or 0.0, active, self.tile, self.bc)
+            self.since_rebuild += 1
+            self.last_dt = dt
+        return self.last_dt

@@ -1,0 +1,225 @@
+/*
+ * levelset_oracle.c -- plain, slow, FP64 CPU oracle of the narrow-band
+ * first-order upwind level-set step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header or constant with the CUDA
+ * library.
+ *
+ * Paper: Z. Wang, "Parallel Level set algorithm with MPI and accelerated on
+ * GPU" (arXiv 1612.04040).  Equations are numbered in order of appearance:
+ *   Eq. 1  phi(x,0) = +-d                                  (section 1)
+ *   Eq. 2  phi_t + F|grad phi| = 0                         (section 1)
+ *   Eq. 3  phi^{n+1} = phi^n - dt[max(F,0) G+ + min(F,0) G-] (section 1)
+ *   Eq. 4  G+ = sqrt(sum over axes of max(D-,0)^2 + min(D+,0)^2)
+ *   Eq. 5  G- = sqrt(sum over axes of max(D+,0)^2 + min(D-,0)^2)
+ *   Eq. 6  tube T = {x : |phi(x)| < gamma}                (section 1.1)
+ *   Eq. 11 region N = points with a +-dx neighbour in T    (section 1.1)
+ *
+ * Readings where the paper is silent (each one is listed in the design notes):
+ *   - D-x = (phi_i - phi_{i-1})/h, D+x = (phi_{i+1} - phi_i)/h, and the same
+ *     for y and z (textbook one-sided differences of the scheme the paper
+ *     cites for Eq. 3-5).
+ *   - The six squared terms of Eq. 4/5 are summed per axis first,
+ *     s_a = max(..)^2 + min(..)^2, then ((s_x + s_y) + s_z).
+ *   - Domain faces: a missing one-sided difference equals the existing one on
+ *     the same axis ("extrapolate", the default), or is 0 ("neumann": ghost
+ *     value equal to the edge value).
+ *   - Band granularity: the tube test of Eq. 6 is applied per tile of
+ *     tile^3 points (a tile is "core" when one of its points is in T); the
+ *     active set is the core set dilated by one tile (26 or 6 neighbours).
+ *     tile = 1 with the 6-neighbour dilation gives exactly the pointwise T
+ *     and N of Eq. 6 and Eq. 11.  Points outside active tiles do not change.
+ *
+ * Layout: phi[z][y][x], x fastest: index = (z*ny + y)*nx + x.
+ * Build: -O2 -ffp-contract=off (no fused multiply-add anywhere), optional
+ * OpenMP over z planes; every result is independent of the thread count.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_BC_EXTRAPOLATE 0
+#define ORC_BC_NEUMANN 1
+
+static size_t idx3(int nx, int ny, int x, int y, int z)
+{
+    return ((size_t)z * (size_t)ny + (size_t)y) * (size_t)nx + (size_t)x;
+}
+
+static double max0(double a) { return a > 0.0 ? a : 0.0; }
+static double min0(double a) { return a < 0.0 ? a : 0.0; }
+
+/* One-sided differences D-, D+ of phi at position pos along one axis of
+ * length n, stride `stride` in the flat array (Eq. 4/5 symbols). */
+static void one_sided(const double *phi, size_t i, size_t stride, int pos, int n,
+                      double h, int bc, double *dm, double *dp)
+{
+    const double c = phi[i];
+    const int has_m = pos > 0;
+    const int has_p = pos < n - 1;
+    double m = 0.0, p = 0.0;
+    if (has_m) m = (c - phi[i - stride]) / h;
+    if (has_p) p = (phi[i + stride] - c) / h;
+    if (bc == ORC_BC_EXTRAPOLATE) {
+        if (!has_m && has_p) m = p;
+        if (!has_p && has_m) p = m;
+    }
+    /* neumann: the ghost value equals the edge value, so the missing
+     * difference stays 0 */
+    *dm = m;
+    *dp = p;
+}
+
+/* Eq. 3-5 at one grid point.  Returns phi^{n+1} at (x, y, z). */
+double orc_point_update(int nx, int ny, int nz, double h, int bc,
+                        const double *phi, double F, double dt,
+                        int x, int y, int z)
+{
+    const size_t i = idx3(nx, ny, x, y, z);
+    double dmx, dpx, dmy, dpy, dmz, dpz;
+    one_sided(phi, i, 1, x, nx, h, bc, &dmx, &dpx);
+    one_sided(phi, i, (size_t)nx, y, ny, h, bc, &dmy, &dpy);
+    one_sided(phi, i, (size_t)nx * (size_t)ny, z, nz, h, bc, &dmz, &dpz);
+
+    /* Eq. 4: max(D-,0)^2 + min(D+,0)^2 per axis */
+    const double ax = max0(dmx), bx = min0(dpx);
+    const double ay = max0(dmy), by = min0(dpy);
+    const double az = max0(dmz), bz = min0(dpz);
+    const double spx = ax * ax + bx * bx;
+    const double spy = ay * ay + by * by;
+    const double spz = az * az + bz * bz;
+    const double gplus = sqrt((spx + spy) + spz);
+
+    /* Eq. 5: max(D+,0)^2 + min(D-,0)^2 per axis */
+    const double cx = max0(dpx), ex = min0(dmx);
+    const double cy = max0(dpy), ey = min0(dmy);
+    const double cz = max0(dpz), ez = min0(dmz);
+    const double smx = cx * cx + ex * ex;
+    const double smy = cy * cy + ey * ey;
+    const double smz = cz * cz + ez * ez;
+    const double gminus = sqrt((smx + smy) + smz);
+
+    /* Eq. 3 */
+    return phi[i] - dt * (max0(F) * gplus + min0(F) * gminus);
+}
+
+static size_t tile_of(int tile, int tnx, int tny, int x, int y, int z)
+{
+    return ((size_t)(z / tile) * (size_t)tny + (size_t)(y / tile)) * (size_t)tnx
+           + (size_t)(x / tile);
+}
+
+/* One upwind step (Eq. 3) on every point of every active tile; points of
+ * inactive tiles are copied unchanged.  tile_active == NULL: whole domain.
+ * F == NULL: constant speed Fc. */
+void orc_step(int nx, int ny, int nz, double h, int bc, const double *phi,
+              const double *F, double Fc, const uint8_t *tile_active, int tile,
+              double dt, double *out)
+{
+    const int tnx = (nx + tile - 1) / tile;
+    const int tny = (ny + tile - 1) / tile;
+    int z;
+#pragma omp parallel for schedule(static)
+    for (z = 0; z < nz; ++z) {
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                const size_t i = idx3(nx, ny, x, y, z);
+                if (tile_active && !tile_active[tile_of(tile, tnx, tny, x, y, z)]) {
+                    out[i] = phi[i];
+                    continue;
+                }
+                const double f = F ? F[i] : Fc;
+                out[i] = orc_point_update(nx, ny, nz, h, bc, phi, f, dt, x, y, z);
+            }
+        }
+    }
+}
+
+/* Eq. 3 at a list of points (flat indices), reading phi only: for sampled
+ * checks of large grids. */
+void orc_step_points(int nx, int ny, int nz, double h, int bc, const double *phi,
+                     const double *Fpts, double dt, const int64_t *pts, int64_t npts,
+                     double *out)
+{
+    int64_t k;
+#pragma omp parallel for schedule(static)
+    for (k = 0; k < npts; ++k) {
+        const int64_t i = pts[k];
+        const int x = (int)(i % nx);
+        const int y = (int)((i / nx) % ny);
+        const int z = (int)(i / ((int64_t)nx * ny));
+        out[k] = orc_point_update(nx, ny, nz, h, bc, phi, Fpts[k], dt, x, y, z);
+    }
+}
+
+/* Eq. 6 per tile: core[t] = 1 when some point p of tile t has |phi_p| < gamma
+ * (strict). */
+void orc_classify(int nx, int ny, int nz, int tile, const double *phi,
+                  double gamma, uint8_t *core)
+{
+    const int tnx = (nx + tile - 1) / tile;
+    const int tny = (ny + tile - 1) / tile;
+    const int tnz = (nz + tile - 1) / tile;
+    const size_t ntiles = (size_t)tnx * tny * tnz;
+    memset(core, 0, ntiles);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                if (fabs(phi[idx3(nx, ny, x, y, z)]) < gamma)
+                    core[tile_of(tile, tnx, tny, x, y, z)] = 1;
+}
+
+/* Band dilation: active = core plus every tile sharing a face (conn = 6) or
+ * a face, edge or corner (conn = 26) with a core tile. */
+void orc_dilate(int tnx, int tny, int tnz, const uint8_t *core, int conn,
+                uint8_t *active)
+{
+    for (int z = 0; z < tnz; ++z)
+        for (int y = 0; y < tny; ++y)
+            for (int x = 0; x < tnx; ++x) {
+                int on = 0;
+                for (int dz = -1; dz <= 1 && !on; ++dz)
+                    for (int dy = -1; dy <= 1 && !on; ++dy)
+                        for (int dx = -1; dx <= 1 && !on; ++dx) {
+                            const int manhattan = abs(dx) + abs(dy) + abs(dz);
+                            if (conn == 6 && manhattan > 1) continue;
+                            const int X = x + dx, Y = y + dy, Z = z + dz;
+                            if (X < 0 || Y < 0 || Z < 0 || X >= tnx || Y >= tny || Z >= tnz)
+                                continue;
+                            if (core[((size_t)Z * tny + Y) * tnx + X]) on = 1;
+                        }
+                active[((size_t)z * tny + y) * tnx + x] = (uint8_t)on;
+            }
+}
+
+/* Active-point array (section 2): ascending ids of the set flags. */
+int64_t orc_compact(const uint8_t *flags, int64_t n, int32_t *ids)
+{
+    int64_t k = 0;
+    for (int64_t t = 0; t < n; ++t)
+        if (flags[t]) ids[k++] = (int32_t)t;
+    return k;
+}
+
+/* CFL speed bound: max |F| over the points of active tiles (all points when
+ * tile_active == NULL).  0 when there is no such point. */
+double orc_max_abs_speed(int nx, int ny, int nz, int tile, const double *F,
+                         double Fc, const uint8_t *tile_active)
+{
+    const int tnx = (nx + tile - 1) / tile;
+    const int tny = (ny + tile - 1) / tile;
+    double m = 0.0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                if (tile_active && !tile_active[tile_of(tile, tnx, tny, x, y, z)])
+                    continue;
+                const double a = fabs(F ? F[idx3(nx, ny, x, y, z)] : Fc);
+                if (a > m) m = a;
+            }
+    return m;
+}
