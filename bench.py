@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark: narrow-band first-order upwind level-set throughput on one B300.
+
+Workload (the standard sphere-union case): 512^3 FP32 grid, h = 1/512,
+phi^0 = signed distance to the union of 20 seeded spheres (centres
+U[0.15,0.85]^3, radii U[0.05,0.15]), F = 1 + 0.5 sin(2 pi x) sin(2 pi y)
+sin(2 pi z), band half-width 6h on 8^3 tiles, band rebuilt every 5 steps,
+500 steps at CFL 0.5.  One bench step = one whole run of that workload
+through the C ABI: ls_set_phi(phi^0 from device memory) -> ls_band_rebuild(6)
+-> ls_step(500, CFL 0.5, rebuild every 5).  The metric is grid-point updates
+per second over the band (GLUPS: sum over steps of the points of the active
+tiles, divided by the device time).
+
+Timing: W untimed warm-up steps, then K steps between CUDA events on the
+stream the library launches on, with a barrier and a synchronize on both
+sides; max over ranks.  The inputs (phi, F: 1.5 GB) and the active working
+set of a step (~0.2 GB) are larger than the 126 MB L2, so no L2 flush is
+needed between steps.
+
+Extra keys: roofline of the dominant kernel (the upwind step) from CUDA
+events around every step launch, e2e (the same run with host buffers and the
+host<->device copies inside the timed region), cpu_baseline (the FP64 CPU
+oracle on a bounded sample of the same workload), clocks sampled with
+nvidia-smi during the timed region.
+
+--impl reference times the FP64 CPU oracle on the same workload (each step a
+bounded sample: one rebuild period of 5 level-set steps), on rank 0 only.
+With --gpus N > 1 (torchrun) every rank runs an independent replica of the
+workload ("replicas only": the single-grid path has no sharded variant here);
+value = all ranks' updates / max time, scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "narrow-band upwind GLUPS"
+UNIT = "GLUPS"
+BYTES_PER_UPDATE = 12  # FP32: read phi (4) + read F (4) + write phi (4)
+WORKLOAD = "sphere-union 512^3 FP32, band 6h on 8^3 tiles, rebuild/5, 500 steps CFL 0.5"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    p.add_argument("--n", type=int, default=512, help="grid edge (512 = the standard workload)")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local, pg
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_1612_04040_b300", "csrc", "ls_step.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per grid-point update of the step kernel from the last ncu
+    capture, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "stencil_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("ls_step_cu_sha256_16") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_update"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"]
+        if device_uuid:
+            cmd += ["-i", device_uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) != 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(names[1:], r[3][1:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        loaded = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(phi0_f32, F_f32, w, steps=10):
+    """The FP64 CPU oracle, as it stands, on the first `steps` level-set steps
+    of the same workload (inputs: the same FP32 arrays, widened)."""
+    import numpy as np
+    import oracle
+    phi = phi0_f32.astype(np.float64)
+    F = F_f32.astype(np.float64)
+    o = oracle.Oracle(phi.shape, w.h)
+    o.set_phi(phi)
+    o.set_speed(F)
+    t0 = time.perf_counter()
+    o.band_rebuild(w.halfwidth)
+    updates = 0
+    for _ in range(steps):
+        o.step(1, w.cfl, oracle.DT_CFL, w.rebuild_every)
+        updates += int(o.active.sum()) * 512
+    t = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return {"value": updates / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d level-set steps (%d band rebuilds) of the %d^3 workload, FP64 C oracle "
+                      "with OpenMP on %d host threads, %.1f s" % (steps, (steps + w.rebuild_every - 1)
+                                                                    // w.rebuild_every, w.n, cores, t)}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the same workload and metric.
+    Each step = one rebuild period (5 level-set steps) of the 512^3 run."""
+    import numpy as np
+    import oracle
+    from paper_1612_04040_b300 import inputs
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = inputs.SphereUnion(n=args.n)
+    phi = w.phi(out_dtype=inputs.torch.float32).numpy().astype(np.float64)
+    F = w.speed(out_dtype=inputs.torch.float32).numpy().astype(np.float64)
+    o = oracle.Oracle(phi.shape, w.h)
+    o.set_phi(phi)
+    o.set_speed(F)
+    o.band_rebuild(w.halfwidth)
+
+    def one_step():
+        u = 0
+        for _ in range(w.rebuild_every):
+            o.step(1, w.cfl, oracle.DT_CFL, w.rebuild_every)
+            u += int(o.active.sum()) * 512
+        return u
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    updates = 0
+    for _ in range(args.steps):
+        updates += one_step()
+    t = time.perf_counter() - t0
+    value = updates / t / 1e9
+    cores = len(os.sched_getaffinity(0))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOAD, "grid": args.n, "reference_step": "5 level-set steps (one rebuild period)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d x 5 level-set steps of the %d^3 workload after %d warm-up periods"
+                                   % (args.steps, args.n, args.warmup)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    from paper_1612_04040_b300 import inputs
+    from paper_1612_04040_b300 import native as ls
+
+    world, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    w = inputs.SphereUnion(n=args.n)
+    phi0 = w.phi(device=dev).to(torch.float32).contiguous()
+    F = w.speed(device=dev).to(torch.float32).contiguous()
+    torch.cuda.synchronize()
+
+    g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32, stream=stream.cuda_stream)
+    g.set_speed(F)
+
+    def run_once():
+        g.set_phi(phi0)
+        g.band_rebuild(w.halfwidth, want_count=False)
+        g.step(w.steps, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+
+    for _ in range(max(args.warmup, 0)):
+        run_once()
+    torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+
+    u0 = g.updates()
+    g.reset_profile()
+    g.profile_enable(True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        run_once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    g.profile_enable(False)
+    prof = g.profile()
+    updates = g.updates() - u0
+
+    t_s = ms / 1e3
+    if pg:
+        tt = torch.tensor([t_s, float(updates)], dtype=torch.float64, device=dev)
+        tmax = tt[:1].clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        usum = tt[1:].clone()
+        pg.all_reduce(usum, op=pg.ReduceOp.SUM)
+        t_s, total_updates = float(tmax.item()), float(usum.item())
+    else:
+        total_updates = float(updates)
+    value = total_updates / t_s / 1e9
+
+    # dominant kernel: the upwind step, timed by events around every launch
+    peak, peak_kind = measured_peaks()
+    stencil_s = prof["stencil_ms"] / 1e3
+    n_launch = max(prof["stencil_timed"], 1)
+    achieved = (updates * BYTES_PER_UPDATE / 1e9) / stencil_s if stencil_s > 0 else None
+    tpu = recorded_traffic()
+    traffic = tpu * updates / n_launch if tpu is not None else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "peak_kind": peak_kind, "kernel": "k_step_f32 (upwind step over the active 8^3 tiles)",
+                "bytes_per_update": BYTES_PER_UPDATE,
+                "avg_launch_us": 1e6 * stencil_s / n_launch, "launches": prof["stencil_timed"],
+                "share_of_step_time": stencil_s / t_s if t_s > 0 else None}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        phi_h = phi0.cpu().pin_memory()
+        F_h = F.cpu().pin_memory()
+        out_h = torch.empty_like(phi_h).pin_memory()
+        u1 = g.updates()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            g.set_phi(phi_h)
+            g.set_speed(F_h)
+            g.band_rebuild(w.halfwidth, want_count=False)
+            g.step(w.steps, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+            g.get_phi(out_h)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        ue = g.updates() - u1
+        nb = phi_h.numel() * 4
+        e2e = {"value": ue / te / 1e9 * world, "unit": UNIT, "h2d_bytes_per_step": 2 * nb,
+               "d2h_bytes_per_step": nb,
+               "note": "ls_set_phi + ls_set_speed from pinned host memory, rebuild, 500 steps, "
+                       "ls_get_phi to pinned host memory; host wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(phi0.cpu().numpy(), F.cpu().numpy(), w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "grid": w.n, "halfwidth_h": w.halfwidth,
+                       "rebuild_every": w.rebuild_every, "level_set_steps_per_bench_step": w.steps,
+                       "cfl": w.cfl, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (phi + F 1.5 GB; active set per step ~0.2 GB)"},
+            "updates_per_step": updates / max(args.steps, 1),
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": prof["kernel_launches"],
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * ls.h -- C ABI of the B300 narrow-band level-set library (libls.so).
+ *
+ * The library advances a level-set function phi on a 3-D grid with the
+ * explicit first-order upwind scheme of arXiv 1612.04040, section 1:
+ *
+ *   Eq. 3  phi^{n+1}_{ijk} = phi^n_{ijk} - dt [max(F,0) G+ + min(F,0) G-]
+ *   Eq. 4  G+ = sqrt( sum over x,y,z of max(D-,0)^2 + min(D+,0)^2 )
+ *   Eq. 5  G- = sqrt( sum over x,y,z of max(D+,0)^2 + min(D-,0)^2 )
+ *
+ * restricted to a narrow band (section 1.1): the tube T = {|phi| < gamma}
+ * (Eq. 6), gamma = halfwidth * h, is tested per 8x8x8 tile, and the active
+ * tiles are the tube tiles dilated by one tile (covering the region N of
+ * Eq. 11).  Points of inactive tiles are frozen.  The band is rebuilt every
+ * `rebuild_every` steps; in CFL mode dt = CFL * h / max|F| over the active
+ * points (CFL * h if that max is 0).  D-x = (phi_i - phi_{i-1})/h and
+ * D+x = (phi_{i+1} - phi_i)/h; at a domain face the missing one-sided
+ * difference equals the existing one (LS_BC_EXTRAPOLATE, default) or is 0
+ * (LS_BC_NEUMANN).
+ *
+ * Conventions for every call:
+ *  - Return value: an ls_status code (0 = LS_OK, negative = error).  No call
+ *    aborts, throws or exits.
+ *  - Arrays crossing the ABI are dense row-major phi[z][y][x] (x fastest,
+ *    index = (z*ny + y)*nx + x, the indexing of the paper's GPU listing in
+ *    section 3), in the context's precision: float for LS_FP32, double for
+ *    LS_FP64.  `*_on_device` = 1 means a CUDA device pointer of the current
+ *    device, 0 a host pointer.  Inputs are copied; the caller keeps
+ *    ownership of every buffer it passes.  The library owns all device state
+ *    of a context and frees it in ls_destroy.
+ *  - Work is queued on the context's stream (ls_set_stream; default: the
+ *    legacy default stream).  Calls that return values to the host
+ *    (ls_get_*, ls_band_rebuild with a non-NULL count, ls_step with a
+ *    non-NULL last_dt, the non-finite checks of ls_set_phi / ls_set_speed)
+ *    synchronise that stream.
+ *  - Device-side failures are recorded in a sticky status word read by
+ *    ls_get_status; device waits are bounded and end in LS_ETIMEOUT, never
+ *    in a trap or a hang.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef LS_H
+#define LS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ls_ctx ls_ctx; /* opaque; created and freed by the library */
+
+typedef enum {
+    LS_OK = 0,
+    LS_EINVAL = -1,     /* bad argument (size, pointer, enum, alignment)   */
+    LS_ENOMEM = -2,     /* device or host allocation failed                */
+    LS_ECUDA = -3,      /* a CUDA call failed (see ls_last_cuda_error)     */
+    LS_ETIMEOUT = -4,   /* a bounded device wait ran out                   */
+    LS_ENONFINITE = -5, /* NaN or Inf in phi or F                          */
+    LS_ESTATE = -6      /* call not valid in the context's current state   */
+} ls_status;
+
+enum { LS_FP32 = 0, LS_FP64 = 1 };               /* storage + arithmetic precision */
+enum { LS_DT_FIXED = 0, LS_DT_CFL = 1 };         /* meaning of dt_or_cfl           */
+enum { LS_PLAIN = 0, LS_LEARNED = 1 };           /* step flavour                   */
+enum { LS_BC_EXTRAPOLATE = 0, LS_BC_NEUMANN = 1 };
+
+/* ---------------------------------------------------------------------
+ * Single grid
+ * ------------------------------------------------------------------- */
+
+/* Create a context for an nx*ny*nz grid with spacing h (section 1, Eq. 3).
+ * nx, ny, nz: multiples of 8, >= 8, nx*ny*nz <= 2^31; h > 0 and finite;
+ * precision LS_FP32 or LS_FP64.  Allocates two phi buffers (ping-pong), the
+ * speed field and the tile tables on the current CUDA device.
+ * Errors: LS_EINVAL (sizes, h, precision, out == NULL), LS_ENOMEM, LS_ECUDA. */
+int ls_create(int nx, int ny, int nz, double h, int precision, ls_ctx **out);
+
+/* Free every device and host resource of ctx (NULL is accepted). */
+int ls_destroy(ls_ctx *ctx);
+
+/* Queue all later work of ctx on cuda_stream (a cudaStream_t, e.g. PyTorch's
+ * current stream; NULL = legacy default stream). */
+int ls_set_stream(ls_ctx *ctx, void *cuda_stream);
+
+/* Initial level-set function phi^0 (Eq. 1; Step 0 of section 1.1).  Copies
+ * nx*ny*nz values from src (row-major, context precision).  Marks the band
+ * stale: the next ls_step rebuilds it from the whole grid.
+ * Errors: LS_EINVAL (NULL src), LS_ENONFINITE (NaN/Inf; phi unchanged is not
+ * guaranteed, the band stays stale), LS_ECUDA. */
+int ls_set_phi(ls_ctx *ctx, const void *src, int src_on_device);
+
+/* Speed field F (Eq. 2/3), same layout and precision as phi.  Also computes
+ * the per-tile max|F| used by the CFL rule.  Errors as ls_set_phi. */
+int ls_set_speed(ls_ctx *ctx, const void *src, int src_on_device);
+
+/* Constant speed F everywhere (replaces a speed field).  LS_ENONFINITE if F
+ * is not finite. */
+int ls_set_speed_const(ls_ctx *ctx, double F);
+
+/* Domain-face rule for the one-sided differences (LS_BC_*). */
+int ls_set_bc(ls_ctx *ctx, int bc);
+
+/* Build the band now (section 1.1, Step 1): gamma = halfwidth_in_h * h in
+ * FP64; a tile is in the tube when min |phi| over its points < gamma (Eq. 6,
+ * strict), the active set is the tube tiles plus their 26 neighbours, and the
+ * active tile ids are compacted in ascending order.  Scans the whole grid.
+ * Stores halfwidth for the rebuilds inside ls_step.  If n_active_tiles is not
+ * NULL the stream is synchronised and the active-tile count written there.
+ * Errors: LS_EINVAL (halfwidth <= 0 or not finite), LS_ESTATE (phi not set),
+ * LS_ECUDA. */
+int ls_band_rebuild(ls_ctx *ctx, double halfwidth_in_h, long long *n_active_tiles);
+
+/* Advance nsteps steps of Eq. 3 (section 1.1, Step 2) on the active tiles.
+ * dt_mode LS_DT_FIXED: dt = dt_or_cfl.  LS_DT_CFL: dt = dt_or_cfl * h / M,
+ * M = max|F| over the points of the active tiles at the latest rebuild (over
+ * the whole grid in full-domain mode), dt = dt_or_cfl * h when M = 0; dt is
+ * computed in FP64 on the device.  rebuild_every > 0: the band is rebuilt
+ * before a step whenever rebuild_every steps ran since the last rebuild
+ * (counted across calls); 0: never inside this call.  A stale band (after
+ * ls_set_phi / ls_set_speed*) is rebuilt from the whole grid before the first
+ * step.  If last_dt is not NULL the stream is synchronised and the dt of the
+ * last step written there.
+ * Errors: LS_EINVAL (nsteps < 0, rebuild_every < 0, dt_or_cfl <= 0 or not
+ * finite, bad dt_mode), LS_ESTATE (phi or speed not set; no halfwidth given
+ * yet and not in full-domain mode), LS_ECUDA. */
+int ls_step(ls_ctx *ctx, int nsteps, double dt_or_cfl, int dt_mode,
+            int rebuild_every, double *last_dt);
+
+/* Full-domain mode on/off: every tile is active and no rebuild happens
+ * (the O(n^3) variant the narrow band of section 1.1 replaces). */
+int ls_set_full_domain(ls_ctx *ctx, int on);
+
+/* Copy the current phi out (row-major, context precision) to dst.
+ * Synchronises the stream.  Errors: LS_EINVAL, LS_ESTATE (phi not set). */
+int ls_get_phi(ls_ctx *ctx, void *dst, int dst_on_device);
+
+/* Copy the ascending active tile ids (tile id = (tz*(ny/8) + ty)*(nx/8) + tx)
+ * to host array dst of capacity cap; *n receives the count (may exceed cap,
+ * then only cap ids are written).  Synchronises the stream.
+ * Errors: LS_EINVAL (n == NULL, cap < 0, dst == NULL with cap > 0),
+ * LS_ESTATE (no band). */
+int ls_get_active_tiles(ls_ctx *ctx, int *dst, long long cap, long long *n);
+
+/* Total grid-point updates done by ls_step since creation (sum over steps of
+ * 512 x active tiles).  Synchronises the stream. */
+int ls_get_updates(ls_ctx *ctx, unsigned long long *n);
+
+/* Profiling counters of a context. */
+typedef struct {
+    unsigned long long kernel_launches;  /* library kernels launched by this context */
+    unsigned long long stencil_launches; /* of which upwind-step (Eq. 3) launches    */
+    double stencil_ms;                   /* summed device time of the step launches
+                                            made while profiling was enabled         */
+    unsigned long long stencil_timed;    /* number of launches stencil_ms covers     */
+} ls_profile;
+
+/* Enable (1) or disable (0) CUDA-event timing of every upwind-step launch
+ * (one event pair per launch, recorded on the context's stream). */
+int ls_profile_enable(ls_ctx *ctx, int on);
+
+/* Read the counters (synchronises the stream).  Errors: LS_EINVAL. */
+int ls_get_profile(ls_ctx *ctx, ls_profile *out);
+
+/* Zero the counters. */
+int ls_reset_profile(ls_ctx *ctx);
+
+/* Sticky device status word: LS_OK, or the first device-side error. */
+int ls_get_status(ls_ctx *ctx);
+
+/* Static message for a status code. */
+const char *ls_strerror(int status);
+
+/* Last CUDA error code seen by any call (0 = none), for diagnostics. */
+int ls_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LS_H */

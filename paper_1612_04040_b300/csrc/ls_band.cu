@@ -1,0 +1,475 @@
+// ls_band.cu -- band rebuild kernels (section 1.1, Step 1 and Eq. 6 / 11),
+// the active-tile compaction (the "active points array" of section 2, here
+// at tile granularity), the max|F| reduction behind the CFL time step, and
+// the row-major <-> bricked layout conversion.
+//
+// All band decisions are exact: min |phi| over a tile is exact in any
+// precision, and the tube test min|phi| < gamma is done in FP64 against
+// gamma = halfwidth * h computed in FP64 on the host.
+#include "ls_internal.cuh"
+
+namespace lsk {
+
+namespace {
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+template <typename T>
+__device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
+
+// ---------------------------------------------------------------------------
+// layout conversion: one 128-thread block per tile; thread -> 4 x-consecutive
+// points (lz, ly, 4*xh .. 4*xh+3), i.e. element offset 4*threadIdx.x
+// ---------------------------------------------------------------------------
+template <typename T, bool PACK>
+__global__ void __launch_bounds__(128) k_convert(const T* __restrict__ src, T* __restrict__ dst,
+                                                 Inst in, unsigned* nonfinite)
+{
+    const int tid = threadIdx.x;
+    const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
+    const long long tpl = (long long)in.tnx * in.tny;
+    for (long long t = blockIdx.x; t < in.ntiles; t += gridDim.x) {
+        const int tz = (int)(t / tpl);
+        const int rem = (int)(t - (long long)tz * tpl);
+        const int ty = rem / in.tnx, tx = rem - ty * in.tnx;
+        const size_t rm = ((size_t)(tz * TILE + lz) * in.ny + (size_t)(ty * TILE + ly)) * in.nx
+                          + (size_t)(tx * TILE + 4 * xh);
+        const size_t bk = (size_t)t * TILE_PTS + 4 * tid;
+        const size_t from = PACK ? rm : bk;
+        const size_t to = PACK ? bk : rm;
+        T v0, v1, v2, v3;
+        if constexpr (sizeof(T) == 4) {
+            const float4 v = *reinterpret_cast<const float4*>(src + from);
+            v0 = v.x; v1 = v.y; v2 = v.z; v3 = v.w;
+            *reinterpret_cast<float4*>(dst + to) = v;
+        } else {
+            const double2 a = *reinterpret_cast<const double2*>(src + from);
+            const double2 b = *reinterpret_cast<const double2*>(src + from + 2);
+            v0 = a.x; v1 = a.y; v2 = b.x; v3 = b.y;
+            *reinterpret_cast<double2*>(dst + to) = a;
+            *reinterpret_cast<double2*>(dst + to + 2) = b;
+        }
+        if (PACK && nonfinite) {
+            const bool bad = !(finite_val(v0) && finite_val(v1) && finite_val(v2) && finite_val(v3));
+            if (bad) atomicAdd(nonfinite, 1u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-tile reductions: one warp per tile
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_min(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// max |v| over the 512 values of a tile, by one warp
+template <typename T>
+__device__ __forceinline__ T tile_absmax(const T* __restrict__ p)
+{
+    T m = T(0);
+    if constexpr (sizeof(T) == 4) {
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 v = __ldg(q + lane_id() + 32 * k);
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+    } else {
+        const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const double2 v = __ldg(q + lane_id() + 32 * k);
+            m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+        }
+    }
+    return warp_max(m);
+}
+
+// min |v| over the 512 values of a tile, by one warp
+template <typename T>
+__device__ __forceinline__ T tile_absmin(const T* __restrict__ p)
+{
+    T m;
+    if constexpr (sizeof(T) == 4) {
+        m = __int_as_float(0x7f800000);
+        const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float4 v = __ldg(q + lane_id() + 32 * k);
+            m = fminf(m, fminf(fminf(fabsf(v.x), fabsf(v.y)), fminf(fabsf(v.z), fabsf(v.w))));
+        }
+    } else {
+        m = __longlong_as_double(0x7ff0000000000000ll);
+        const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const double2 v = __ldg(q + lane_id() + 32 * k);
+            m = fmin(m, fmin(fabs(v.x), fabs(v.y)));
+        }
+    }
+    return warp_min(m);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tile_maxabs(const T* __restrict__ F, T* __restrict__ out,
+                                                     long long ntiles)
+{
+    const long long warps = (long long)gridDim.x * 8;
+    for (long long t = (long long)blockIdx.x * 8 + (threadIdx.x >> 5); t < ntiles; t += warps) {
+        const T m = tile_absmax(F + (size_t)t * TILE_PTS);
+        if (lane_id() == 0) out[t] = m;
+    }
+}
+
+__device__ __forceinline__ const Inst& inst_of(long long t, const Inst* d_inst,
+                                               const uint16_t* tile_inst, const Inst& single)
+{
+    return tile_inst ? d_inst[tile_inst[t]] : single;
+}
+
+// Eq. 6 per tile: core = (min |phi| over the tile) < gamma, compared in FP64
+template <typename T>
+__global__ void __launch_bounds__(256) k_classify_all(const T* __restrict__ phi, uint8_t* core,
+                                                      const Inst* d_inst,
+                                                      const uint16_t* tile_inst, Inst single,
+                                                      long long ntiles)
+{
+    const long long warps = (long long)gridDim.x * 8;
+    for (long long t = (long long)blockIdx.x * 8 + (threadIdx.x >> 5); t < ntiles; t += warps) {
+        const T m = tile_absmin(phi + (size_t)t * TILE_PTS);
+        if (lane_id() == 0) {
+            const double g = inst_of(t, d_inst, tile_inst, single).gamma;
+            core[t] = ((double)m < g) ? 1 : 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// dilation by one tile (26 neighbours, inside the instance), leaving-tile
+// buffer sync, per-block active counts.  One thread per tile, 256 per block.
+// ---------------------------------------------------------------------------
+template <int ESIZE>
+__global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core, uint8_t* act,
+                                                const uint4* __restrict__ cur, uint4* other,
+                                                int* block_counts, const Inst* d_inst,
+                                                const uint16_t* tile_inst, Inst single,
+                                                long long ntiles)
+{
+    const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+    int on = 0, old = 0;
+    if (t < ntiles) {
+        const Inst& in = inst_of(t, d_inst, tile_inst, single);
+        const long long loc = t - in.tile_base;
+        const long long tpl = (long long)in.tnx * in.tny;
+        const int tz = (int)(loc / tpl);
+        const int rem = (int)(loc - (long long)tz * tpl);
+        const int ty = rem / in.tnx, tx = rem - ty * in.tnx;
+        for (int dz = -1; dz <= 1 && !on; ++dz) {
+            const int z = tz + dz;
+            if (z < 0 || z >= in.tnz) continue;
+            for (int dy = -1; dy <= 1 && !on; ++dy) {
+                const int y = ty + dy;
+                if (y < 0 || y >= in.tny) continue;
+                const long long row = in.tile_base + ((long long)z * in.tny + y) * in.tnx;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x = tx + dx;
+                    if (x < 0 || x >= in.tnx) continue;
+                    if (core[row + x]) { on = 1; break; }
+                }
+            }
+        }
+        old = act[t];
+        act[t] = (uint8_t)on;
+    }
+    // tiles leaving the active set: copy their current values into the other
+    // ping-pong buffer so both buffers agree on every inactive tile
+    unsigned leaving = __ballot_sync(0xffffffffu, old && !on);
+    constexpr int VEC = TILE_PTS * ESIZE / 16;  // uint4 per tile
+    while (leaving) {
+        const int src_lane = __ffs(leaving) - 1;
+        leaving &= leaving - 1;
+        const long long lt = (long long)blockIdx.x * 256 + (threadIdx.x & ~31u) + src_lane;
+        const uint4* s = cur + (size_t)lt * VEC;
+        uint4* d = other + (size_t)lt * VEC;
+#pragma unroll
+        for (int k = 0; k < VEC / 32; ++k) d[lane_id() + 32 * k] = s[lane_id() + 32 * k];
+    }
+    const int cnt = __syncthreads_count(on);
+    if (threadIdx.x == 0) block_counts[blockIdx.x] = cnt;
+}
+
+// exclusive scan of up to 1024*32 block counts by one 1024-thread block
+__global__ void __launch_bounds__(1024) k_scan(int* counts, int n, int* total)
+{
+    __shared__ int warp_sums[32];
+    const int per = (n + 1023) / 1024;
+    const int b0 = threadIdx.x * per;
+    int local = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < n) local += counts[b0 + k];
+    // inclusive warp scan
+    int v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane_id() >= o) v += u;
+    }
+    if (lane_id() == 31) warp_sums[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int w = warp_sums[threadIdx.x];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, w, o);
+            if ((int)threadIdx.x >= o) w += u;
+        }
+        warp_sums[threadIdx.x] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int run = v - local + ((threadIdx.x >> 5) ? warp_sums[(threadIdx.x >> 5) - 1] : 0);
+    for (int k = 0; k < per; ++k) {
+        if (b0 + k < n) {
+            const int c = counts[b0 + k];
+            counts[b0 + k] = run;
+            run += c;
+        }
+    }
+    if (threadIdx.x == 1023) *total = run;
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned long long ordered_bits(T v)
+{
+    if constexpr (sizeof(T) == 4) return (unsigned long long)__float_as_uint(v);
+    else return (unsigned long long)__double_as_longlong(v);
+}
+
+// scatter active ids in ascending order; block max of tile max|F| over the
+// active tiles -> atomicMax on the ordered bits (values are >= 0)
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act,
+                                                 const int* __restrict__ offsets, int* list,
+                                                 long long ntiles, const T* __restrict__ tile_maxF,
+                                                 unsigned long long* Mbits)
+{
+    __shared__ int warp_cnt[8];
+    __shared__ unsigned long long warp_max_bits[8];
+    const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+    const int on = (t < ntiles) ? act[t] : 0;
+    const unsigned b = __ballot_sync(0xffffffffu, on);
+    const int w = threadIdx.x >> 5;
+    unsigned long long mb = 0;
+    if (on && tile_maxF) mb = ordered_bits(tile_maxF[t]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = u > mb ? u : mb;
+    }
+    if (lane_id() == 0) {
+        warp_cnt[w] = __popc(b);
+        warp_max_bits[w] = mb;
+    }
+    __syncthreads();
+    int before = 0;
+    for (int k = 0; k < w; ++k) before += warp_cnt[k];
+    if (on) {
+        const int rank = __popc(b & ((1u << lane_id()) - 1u));
+        list[offsets[blockIdx.x] + before + rank] = (int)t;
+    }
+    if (threadIdx.x == 0 && tile_maxF) {
+        unsigned long long m = 0;
+        for (int k = 0; k < 8; ++k) m = warp_max_bits[k] > m ? warp_max_bits[k] : m;
+        if (m) atomicMax(Mbits, m);
+    }
+}
+
+// max of tile max|F| over all tiles (full-domain CFL bound)
+template <typename T>
+__global__ void __launch_bounds__(256) k_max_all(const T* __restrict__ tile_maxF, long long ntiles,
+                                                 unsigned long long* Mbits)
+{
+    unsigned long long mb = 0;
+    for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < ntiles;
+         t += (long long)gridDim.x * 256) {
+        const unsigned long long u = ordered_bits(tile_maxF[t]);
+        mb = u > mb ? u : mb;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = u > mb ? u : mb;
+    }
+    if (lane_id() == 0 && mb) atomicMax(Mbits, mb);
+}
+
+// dt from M, FP64, single thread per instance.  finalize: M comes from the
+// reduction bits (then cleared); otherwise the stored M is reused.
+__global__ void k_set_dt(StepScalars* sc, int n_inst, const Inst* d_inst, Inst single, int mode,
+                         double value, int finalize, int prec, unsigned long long* Mbits,
+                         const int* count, long long fixed_count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    const Inst& in = d_inst ? d_inst[i] : single;
+    double M;
+    if (finalize) {
+        const long long n = count ? (long long)*count : fixed_count;
+        if (in.speed_mode == 1) {
+            M = (n > 0) ? fabs(in.Fc) : 0.0;
+        } else {
+            const unsigned long long b = Mbits[i];
+            M = prec == 0 ? (double)__uint_as_float((unsigned)b) : __longlong_as_double((long long)b);
+            if (n == 0) M = 0.0;
+        }
+        Mbits[i] = 0;
+        sc[i].M = M;
+    } else {
+        M = sc[i].M;
+    }
+    double dt;
+    if (mode == 1) {
+        const double ch = __dmul_rn(value, in.h);
+        dt = (M > 0.0) ? __ddiv_rn(ch, M) : ch;
+    } else {
+        dt = value;
+    }
+    sc[i].dt = dt;
+    sc[i].coef = __double2float_rn(__ddiv_rn(dt, in.h));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int conv_grid(long long ntiles)
+{
+    const long long g = ntiles < (1 << 20) ? ntiles : (1 << 20);
+    return (int)(g > 0 ? g : 1);
+}
+
+cudaError_t launch_pack(const void* src, void* dst, const Inst& in, int prec, unsigned* nonfinite,
+                        cudaStream_t s)
+{
+    if (prec == 0)
+        k_convert<float, true><<<conv_grid(in.ntiles), 128, 0, s>>>(
+            (const float*)src, (float*)dst, in, nonfinite);
+    else
+        k_convert<double, true><<<conv_grid(in.ntiles), 128, 0, s>>>(
+            (const double*)src, (double*)dst, in, nonfinite);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const void* src, void* dst, const Inst& in, int prec, cudaStream_t s)
+{
+    if (prec == 0)
+        k_convert<float, false><<<conv_grid(in.ntiles), 128, 0, s>>>(
+            (const float*)src, (float*)dst, in, nullptr);
+    else
+        k_convert<double, false><<<conv_grid(in.ntiles), 128, 0, s>>>(
+            (const double*)src, (double*)dst, in, nullptr);
+    return cudaGetLastError();
+}
+
+static int warp_grid(long long ntiles)
+{
+    long long g = (ntiles + 7) / 8;
+    if (g > 148 * 64) g = 148 * 64;
+    return (int)(g > 0 ? g : 1);
+}
+
+cudaError_t launch_tile_maxabs(const void* F, void* tile_maxF, long long ntiles, int prec,
+                               cudaStream_t s)
+{
+    if (prec == 0)
+        k_tile_maxabs<float><<<warp_grid(ntiles), 256, 0, s>>>((const float*)F, (float*)tile_maxF,
+                                                               ntiles);
+    else
+        k_tile_maxabs<double><<<warp_grid(ntiles), 256, 0, s>>>((const double*)F,
+                                                                (double*)tile_maxF, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_inst,
+                                const uint16_t* tile_inst, const Inst& single, long long ntiles,
+                                int prec, cudaStream_t s)
+{
+    if (prec == 0)
+        k_classify_all<float><<<warp_grid(ntiles), 256, 0, s>>>((const float*)phi, core, d_inst,
+                                                                tile_inst, single, ntiles);
+    else
+        k_classify_all<double><<<warp_grid(ntiles), 256, 0, s>>>((const double*)phi, core, d_inst,
+                                                                 tile_inst, single, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, const void* cur, void* other,
+                          int* block_counts, const Inst* d_inst, const uint16_t* tile_inst,
+                          const Inst& single, long long ntiles, int prec, cudaStream_t s)
+{
+    const int nb = (int)((ntiles + 255) / 256);
+    if (prec == 0)
+        k_dilate<4><<<nb, 256, 0, s>>>(core, act, (const uint4*)cur, (uint4*)other, block_counts,
+                                       d_inst, tile_inst, single, ntiles);
+    else
+        k_dilate<8><<<nb, 256, 0, s>>>(core, act, (const uint4*)cur, (uint4*)other, block_counts,
+                                       d_inst, tile_inst, single, ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(int* block_counts, int nblocks, int* count, cudaStream_t s)
+{
+    k_scan<<<1, 1024, 0, s>>>(block_counts, nblocks, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* list,
+                           long long ntiles, const void* tile_maxF, int prec,
+                           unsigned long long* Mbits, cudaStream_t s)
+{
+    const int nb = (int)((ntiles + 255) / 256);
+    if (prec == 0)
+        k_scatter<float><<<nb, 256, 0, s>>>(act, block_offsets, list, ntiles,
+                                            (const float*)tile_maxF, Mbits);
+    else
+        k_scatter<double><<<nb, 256, 0, s>>>(act, block_offsets, list, ntiles,
+                                             (const double*)tile_maxF, Mbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_all(const void* tile_maxF, long long ntiles, int prec,
+                           unsigned long long* Mbits, cudaStream_t s)
+{
+    long long g = (ntiles + 255) / 256;
+    if (g > 148 * 8) g = 148 * 8;
+    if (g < 1) g = 1;
+    if (prec == 0)
+        k_max_all<float><<<(int)g, 256, 0, s>>>((const float*)tile_maxF, ntiles, Mbits);
+    else
+        k_max_all<double><<<(int)g, 256, 0, s>>>((const double*)tile_maxF, ntiles, Mbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_dt(StepScalars* sc, int n_inst, const Inst* d_inst, const Inst& single,
+                          int mode, double value, int finalize, int prec,
+                          unsigned long long* Mbits, const int* count, long long fixed_count,
+                          cudaStream_t s)
+{
+    k_set_dt<<<(n_inst + 127) / 128, 128, 0, s>>>(sc, n_inst, d_inst, single, mode, value,
+                                                   finalize, prec, Mbits, count, fixed_count);
+    return cudaGetLastError();
+}
+
+}  // namespace lsk

@@ -1,0 +1,107 @@
+// ls_internal.cuh -- device-side data model shared by the library's kernels
+// and its host engine.
+//
+// Storage ("bricked") layout in HBM: every 8x8x8 tile is one contiguous
+// block of 512 values (2 KiB in FP32, 4 KiB in FP64); inside a tile the order
+// is (lz*8 + ly)*8 + lx, x fastest.  Tile t of instance i starts at element
+// (tile_base_i + t) * 512.  A tile is thus one DRAM-contiguous burst and the
+// stencil's face halos are 256-byte (z) or 32-byte (y) runs of the
+// neighbouring tiles.  Row-major arrays crossing the ABI are converted on
+// the device by the pack / unpack kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lsk {
+
+constexpr int TILE = 8;
+constexpr int TILE_PTS = TILE * TILE * TILE;
+
+// Per-instance parameters (one entry per independent grid).
+struct Inst {
+    int nx, ny, nz;        // grid points (multiples of 8)
+    int tnx, tny, tnz;     // tiles per axis
+    long long tile_base;   // global id of the instance's tile 0
+    long long ntiles;      // tnx * tny * tnz
+    double h;              // grid spacing
+    double inv_h;          // 1/h
+    double gamma;          // band threshold halfwidth * h (FP64)
+    double Fc;             // constant speed when speed_mode == 1
+    int speed_mode;        // 0: unset, 1: constant, 2: field
+    int pow2h;             // h is a power of two (1/h exact)
+    int bc;                // 0 extrapolate, 1 neumann
+    int pad;
+};
+
+// Device status word bits (sticky).
+enum : unsigned {
+    ST_TIMEOUT = 1u,
+    ST_BOUNDS = 2u,
+    ST_NONFINITE = 4u,
+};
+
+// Per-step scalars on the device, one per instance.
+struct StepScalars {
+    double M;      // max |F| over the active set at the last rebuild
+    double dt;     // current time step
+    float coef;    // (float)(dt / h), FP32 path
+    float pad;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (ls_band.cu)
+// ---------------------------------------------------------------------------
+// row-major <-> bricked conversion of one instance; counts non-finite values
+// into *nonfinite (may be NULL)
+cudaError_t launch_pack(const void* src, void* dst, const Inst& in, int prec, unsigned* nonfinite,
+                        cudaStream_t s);
+cudaError_t launch_unpack(const void* src, void* dst, const Inst& in, int prec, cudaStream_t s);
+// tile_maxF[t] = max |F| over tile t (field speed)
+cudaError_t launch_tile_maxabs(const void* F, void* tile_maxF, long long ntiles, int prec,
+                               cudaStream_t s);
+// core[t] = (min_{p in t} |phi_p| < gamma) over all tiles of all instances
+cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_inst,
+                                const uint16_t* tile_inst, const Inst& single, long long ntiles,
+                                int prec, cudaStream_t s);
+// band rebuild: dilation + leaving-tile sync + block counts
+cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, const void* cur, void* other,
+                          int* block_counts, const Inst* d_inst, const uint16_t* tile_inst,
+                          const Inst& single, long long ntiles, int prec, cudaStream_t s);
+// exclusive scan of block counts, writes total to *count
+cudaError_t launch_scan(int* block_counts, int nblocks, int* count, cudaStream_t s);
+// scatter active ids (ascending) and fold max |F| of the active tiles into
+// *Mbits (ordered bits of a non-negative float / double)
+cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* list,
+                           long long ntiles, const void* tile_maxF, int prec,
+                           unsigned long long* Mbits, cudaStream_t s);
+// max of tile max|F| over all tiles (full-domain mode)
+cudaError_t launch_max_all(const void* tile_maxF, long long ntiles, int prec,
+                           unsigned long long* Mbits, cudaStream_t s);
+// dt from M (FP64): mode 0 fixed (value = dt), 1 CFL (value = CFL number).
+// finalize = 1: M is taken from *Mbits (or |Fc| for a constant speed) and
+// *Mbits cleared; count (device) or fixed_count = number of active tiles.
+cudaError_t launch_set_dt(StepScalars* sc, int n_inst, const Inst* d_inst, const Inst& single,
+                          int mode, double value, int finalize, int prec,
+                          unsigned long long* Mbits, const int* count, long long fixed_count,
+                          cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// launchers (ls_step.cu)
+// ---------------------------------------------------------------------------
+struct StepArgs {
+    const void* src;
+    void* dst;
+    const void* F;            // field (bricked) or NULL for constant speed
+    const int* list;          // active tile ids, or NULL: tile id = index
+    const int* count;         // number of active tiles (device)
+    long long fixed_count;    // used when list == NULL
+    const StepScalars* sc;
+    uint8_t* core;            // fused tube test output, or NULL
+    unsigned long long* updates;
+    Inst in;                  // single instance parameters
+};
+cudaError_t launch_step(const StepArgs& a, int prec, int grid, cudaStream_t s);
+int step_grid_size(int prec, int classify);
+
+}  // namespace lsk

@@ -1,0 +1,227 @@
+"""ctypes binding of libls.so (the C ABI in include/ls.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Functions keep the C names (``ls_create``, ``ls_step`` ...) and
+raise ``LSError`` on a non-zero status.  Arrays may be torch tensors (CUDA or
+CPU) or numpy arrays; they must be C-contiguous, of the context's precision
+(float32 for LS_FP32, float64 for LS_FP64) and hold nx*ny*nz values in
+[z][y][x] order.  There is no fallback: if libls.so is missing or cannot be
+loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+try:
+    import torch
+except ImportError:  # pragma: no cover - torch is part of the image
+    torch = None
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libls.so")
+
+LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ETIMEOUT, LS_ENONFINITE, LS_ESTATE = 0, -1, -2, -3, -4, -5, -6
+LS_FP32, LS_FP64 = 0, 1
+LS_DT_FIXED, LS_DT_CFL = 0, 1
+LS_PLAIN, LS_LEARNED = 0, 1
+LS_BC_EXTRAPOLATE, LS_BC_NEUMANN = 0, 1
+
+_lib = None
+
+# name -> (restype, argtypes); every entry point declared in include/ls.h
+_c = ctypes
+_vp, _i, _d, _ll = _c.c_void_p, _c.c_int, _c.c_double, _c.c_longlong
+_pp = _c.POINTER(_c.c_void_p)
+SIGNATURES = {
+    "ls_create": (_i, [_i, _i, _i, _d, _i, _pp]),
+    "ls_destroy": (_i, [_vp]),
+    "ls_set_stream": (_i, [_vp, _vp]),
+    "ls_set_phi": (_i, [_vp, _vp, _i]),
+    "ls_set_speed": (_i, [_vp, _vp, _i]),
+    "ls_set_speed_const": (_i, [_vp, _d]),
+    "ls_set_bc": (_i, [_vp, _i]),
+    "ls_band_rebuild": (_i, [_vp, _d, _c.POINTER(_ll)]),
+    "ls_step": (_i, [_vp, _i, _d, _i, _i, _c.POINTER(_d)]),
+    "ls_set_full_domain": (_i, [_vp, _i]),
+    "ls_get_phi": (_i, [_vp, _vp, _i]),
+    "ls_get_active_tiles": (_i, [_vp, _c.POINTER(_c.c_int), _ll, _c.POINTER(_ll)]),
+    "ls_get_updates": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
+    "ls_profile_enable": (_i, [_vp, _i]),
+    "ls_get_profile": (_i, [_vp, _vp]),
+    "ls_reset_profile": (_i, [_vp]),
+    "ls_get_status": (_i, [_vp]),
+    "ls_strerror": (_c.c_char_p, [_i]),
+    "ls_last_cuda_error": (_i, []),
+}
+
+
+class Profile(ctypes.Structure):
+    """ls_profile of include/ls.h."""
+    _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("stencil_launches", ctypes.c_ulonglong),
+                ("stencil_ms", ctypes.c_double), ("stencil_timed", ctypes.c_ulonglong)]
+
+
+class LSError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = "%s: %s (%d)" % (what, strerror(status), status)
+        if status == LS_ECUDA and _lib is not None:
+            msg += " [cuda error %d]" % _lib.ls_last_cuda_error()
+        super().__init__(msg)
+
+
+def load():
+    """Load libls.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libls.so not found at %s; build it with "
+                               "`python -m paper_1612_04040_b300.build`" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def strerror(status):
+    if _lib is None:
+        return "status %d" % status
+    return _lib.ls_strerror(status).decode()
+
+
+def check(status, what=""):
+    if status != LS_OK:
+        raise LSError(status, what)
+    return status
+
+
+def array_ptr(a, dtype, count):
+    """(pointer, on_device) of a contiguous array of `count` values of dtype
+    (np.float32 / np.float64)."""
+    if torch is not None and isinstance(a, torch.Tensor):
+        want = torch.float32 if dtype == np.float32 else torch.float64
+        if a.dtype != want:
+            raise TypeError("expected %s, got %s" % (want, a.dtype))
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if a.numel() != count:
+            raise ValueError("expected %d values, got %d" % (count, a.numel()))
+        return ctypes.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0)
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype:
+            raise TypeError("expected %s, got %s" % (dtype, a.dtype))
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if a.size != count:
+            raise ValueError("expected %d values, got %d" % (count, a.size))
+        return ctypes.c_void_p(a.ctypes.data), 0
+    raise TypeError("expected a torch tensor or numpy array")
+
+
+class LevelSet:
+    """One grid behind an ls_ctx.  Thin wrapper: each method is one ABI call."""
+
+    def __init__(self, nx, ny, nz, h, precision=LS_FP32, stream=None):
+        self.lib = load()
+        self.shape = (int(nz), int(ny), int(nx))
+        self.count = int(nx) * int(ny) * int(nz)
+        self.precision = precision
+        self.dtype = np.float32 if precision == LS_FP32 else np.float64
+        self.h = float(h)
+        h_ = ctypes.c_void_p()
+        check(self.lib.ls_create(int(nx), int(ny), int(nz), float(h), int(precision), ctypes.byref(h_)),
+              "ls_create")
+        self.ctx = h_
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        if stream is not None:
+            check(self.lib.ls_set_stream(self.ctx, ctypes.c_void_p(stream)), "ls_set_stream")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.ls_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        check(self.lib.ls_set_stream(self.ctx, ctypes.c_void_p(stream)), "ls_set_stream")
+
+    def set_phi(self, a):
+        p, dev = array_ptr(a, self.dtype, self.count)
+        check(self.lib.ls_set_phi(self.ctx, p, dev), "ls_set_phi")
+
+    def set_speed(self, a):
+        p, dev = array_ptr(a, self.dtype, self.count)
+        check(self.lib.ls_set_speed(self.ctx, p, dev), "ls_set_speed")
+
+    def set_speed_const(self, F):
+        check(self.lib.ls_set_speed_const(self.ctx, float(F)), "ls_set_speed_const")
+
+    def set_bc(self, bc):
+        check(self.lib.ls_set_bc(self.ctx, int(bc)), "ls_set_bc")
+
+    def set_full_domain(self, on):
+        check(self.lib.ls_set_full_domain(self.ctx, int(bool(on))), "ls_set_full_domain")
+
+    def band_rebuild(self, halfwidth, want_count=True):
+        n = ctypes.c_longlong(-1)
+        check(self.lib.ls_band_rebuild(self.ctx, float(halfwidth), ctypes.byref(n) if want_count else None),
+              "ls_band_rebuild")
+        return n.value if want_count else None
+
+    def step(self, nsteps, dt_or_cfl, dt_mode=LS_DT_CFL, rebuild_every=0, want_dt=False):
+        d = ctypes.c_double(0.0)
+        check(self.lib.ls_step(self.ctx, int(nsteps), float(dt_or_cfl), int(dt_mode), int(rebuild_every),
+                               ctypes.byref(d) if want_dt else None), "ls_step")
+        return d.value if want_dt else None
+
+    def get_phi(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        p, dev = array_ptr(out, self.dtype, self.count)
+        check(self.lib.ls_get_phi(self.ctx, p, dev), "ls_get_phi")
+        return out
+
+    def active_tiles(self):
+        n = ctypes.c_longlong(0)
+        check(self.lib.ls_get_active_tiles(self.ctx, None, 0, ctypes.byref(n)), "ls_get_active_tiles")
+        buf = np.empty(max(n.value, 1), dtype=np.int32)
+        check(self.lib.ls_get_active_tiles(self.ctx, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                           n.value, ctypes.byref(n)), "ls_get_active_tiles")
+        return buf[:n.value].copy()
+
+    def updates(self):
+        n = ctypes.c_ulonglong(0)
+        check(self.lib.ls_get_updates(self.ctx, ctypes.byref(n)), "ls_get_updates")
+        return n.value
+
+    def status(self):
+        return self.lib.ls_get_status(self.ctx)
+
+    def profile_enable(self, on=True):
+        check(self.lib.ls_profile_enable(self.ctx, int(bool(on))), "ls_profile_enable")
+
+    def profile(self):
+        p = Profile()
+        check(self.lib.ls_get_profile(self.ctx, ctypes.byref(p)), "ls_get_profile")
+        return {k: getattr(p, k) for k, _ in Profile._fields_}
+
+    def reset_profile(self):
+        check(self.lib.ls_reset_profile(self.ctx), "ls_reset_profile")
