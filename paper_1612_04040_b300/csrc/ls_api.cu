@@ -43,6 +43,8 @@ struct ls_ctx {
     uint8_t* core = nullptr;
     uint8_t* act = nullptr;
     int* list = nullptr;
+    uint8_t* list_info = nullptr;
+    uint8_t* tile_sgn = nullptr;  // per-tile sign code of a speed field (lazy)
     int* d_count = nullptr;
     int* block_counts = nullptr;
     int nblocks = 0;
@@ -140,7 +142,7 @@ void free_all(ls_ctx* c)
     }
     for (auto e : c->ev_free) cudaEventDestroy(e);
     void* ptrs[] = {c->phi[0], c->phi[1], c->F, c->tile_maxF, c->staging, c->core, c->act,
-                    c->list, c->d_count, c->block_counts, c->d_sc, c->d_Mbits, c->d_updates,
+                    c->list, c->list_info, c->tile_sgn, c->d_count, c->block_counts, c->d_sc, c->d_Mbits, c->d_updates,
                     c->d_status, c->d_nonfinite};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -177,6 +179,16 @@ int pack_from(ls_ctx* c, const void* src, int on_device, void* dst)
     return bad ? LS_ENONFINITE : LS_OK;
 }
 
+unsigned const_sign_bits(const ls_ctx* c)
+{
+    return c->in.Fc >= 0.0 ? lsk::SG_POS : lsk::SG_NEG;
+}
+
+const uint8_t* sign_table(const ls_ctx* c)
+{
+    return c->in.speed_mode == 2 ? c->tile_sgn : nullptr;
+}
+
 int rebuild(ls_ctx* c, bool full_scan)
 {
     cudaStream_t s = c->stream;
@@ -184,12 +196,13 @@ int rebuild(ls_ctx* c, bool full_scan)
     void* other = c->phi[c->cur ^ 1];
     if (full_scan || !c->core_fresh)
         KL(c, lsk::launch_classify_all(cur, c->core, nullptr, nullptr, c->in, c->ntiles, c->prec, s));
-    KL(c, lsk::launch_dilate(c->core, c->act, cur, other, c->block_counts, nullptr, nullptr, c->in,
-                          c->ntiles, c->prec, s));
+    KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, nullptr, nullptr, c->in, c->ntiles,
+                             s));
     KL(c, lsk::launch_scan(c->block_counts, c->nblocks, c->d_count, s));
     const void* tmf = (c->in.speed_mode == 2) ? c->tile_maxF : nullptr;
-    KL(c, lsk::launch_scatter(c->act, c->block_counts, c->list, c->ntiles, tmf, c->prec, c->d_Mbits,
-                           s));
+    KL(c, lsk::launch_scatter(c->act, c->block_counts, c->list, c->list_info, sign_table(c),
+                              const_sign_bits(c), c->in, c->ntiles, tmf, c->prec, c->d_Mbits, cur,
+                              other, s));
     KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in, c->dt_mode, c->dt_value, 1, c->prec,
                           c->d_Mbits, c->d_count, 0, s));
     c->band_valid = true;
@@ -203,6 +216,8 @@ int full_domain_bound(ls_ctx* c)
     // every tile counts as active, so a later switch back to a band copies
     // every tile that leaves the active set into the other buffer
     CK(cudaMemsetAsync(c->act, 1, c->ntiles, c->stream));
+    KL(c, lsk::launch_full_list(c->list, c->list_info, sign_table(c), const_sign_bits(c), c->in,
+                                c->ntiles, c->d_count, c->stream));
     if (c->in.speed_mode == 2)
         KL(c, lsk::launch_max_all(c->tile_maxF, c->ntiles, c->prec, c->d_Mbits, c->stream));
     KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in, c->dt_mode, c->dt_value, 1, c->prec,
@@ -266,6 +281,7 @@ int ls_create(int nx, int ny, int nz, double h, int precision, ls_ctx** out)
     A(dalloc(&c->core, c->ntiles));
     A(dalloc(&c->act, c->ntiles));
     A(dalloc(&c->list, c->ntiles * sizeof(int)));
+    A(dalloc(&c->list_info, c->ntiles));
     A(dalloc(&c->d_count, sizeof(int)));
     A(dalloc(&c->block_counts, c->nblocks * sizeof(int)));
     A(dalloc(&c->d_sc, sizeof(lsk::StepScalars)));
@@ -334,11 +350,12 @@ int ls_set_speed(ls_ctx* c, const void* src, int on_device)
     if (!c || !src) return LS_EINVAL;
     if (!c->F) CK(dalloc(&c->F, grid_bytes(c)));
     if (!c->tile_maxF) CK(dalloc(&c->tile_maxF, c->ntiles * c->esize));
+    if (!c->tile_sgn) CK(dalloc(&c->tile_sgn, c->ntiles));
     c->band_valid = false;
     c->core_fresh = false;
     int r = pack_from(c, src, on_device, c->F);
     if (r) { c->in.speed_mode = 0; return r; }
-    KL(c, lsk::launch_tile_maxabs(c->F, c->tile_maxF, c->ntiles, c->prec, c->stream));
+    KL(c, lsk::launch_tile_speed(c->F, c->tile_maxF, c->tile_sgn, c->ntiles, c->prec, c->stream));
     c->in.speed_mode = 2;
     return LS_OK;
 }
@@ -421,9 +438,9 @@ int ls_step(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every,
         a.src = c->phi[c->cur];
         a.dst = c->phi[c->cur ^ 1];
         a.F = (c->in.speed_mode == 2) ? c->F : nullptr;
-        a.list = c->full_domain ? nullptr : c->list;
+        a.list = c->list;
+        a.info = c->list_info;
         a.count = c->d_count;
-        a.fixed_count = c->ntiles;
         a.sc = c->d_sc;
         a.core = classify ? c->core : nullptr;
         a.updates = c->d_updates;

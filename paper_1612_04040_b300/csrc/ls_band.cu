@@ -74,6 +74,12 @@ __device__ __forceinline__ T warp_min(T v)
     return v;
 }
 
+__device__ __forceinline__ const Inst& inst_of(long long t, const Inst* d_inst,
+                                               const uint16_t* tile_inst, const Inst& single)
+{
+    return tile_inst ? d_inst[tile_inst[t]] : single;
+}
+
 // max |v| over the 512 values of a tile, by one warp
 template <typename T>
 __device__ __forceinline__ T tile_absmax(const T* __restrict__ p)
@@ -122,22 +128,48 @@ __device__ __forceinline__ T tile_absmin(const T* __restrict__ p)
     return warp_min(m);
 }
 
+// per tile: max |F| (for the CFL bound) and the sign code of its speeds
 template <typename T>
-__global__ void __launch_bounds__(256) k_tile_maxabs(const T* __restrict__ F, T* __restrict__ out,
-                                                     long long ntiles)
+__global__ void __launch_bounds__(256) k_tile_speed(const T* __restrict__ F, T* __restrict__ out,
+                                                    uint8_t* sgn, long long ntiles)
 {
     const long long warps = (long long)gridDim.x * 8;
     for (long long t = (long long)blockIdx.x * 8 + (threadIdx.x >> 5); t < ntiles; t += warps) {
-        const T m = tile_absmax(F + (size_t)t * TILE_PTS);
-        if (lane_id() == 0) out[t] = m;
+        const T* p = F + (size_t)t * TILE_PTS;
+        const T m = tile_absmax(p);
+        bool pos = true, neg = true;
+        for (int k = lane_id(); k < TILE_PTS; k += 32) {
+            const T v = __ldg(p + k);
+            pos = pos && (v >= T(0));
+            neg = neg && (v < T(0));
+        }
+        pos = __all_sync(0xffffffffu, pos);
+        neg = __all_sync(0xffffffffu, neg);
+        if (lane_id() == 0) {
+            out[t] = m;
+            sgn[t] = (uint8_t)(pos ? SG_POS : (neg ? SG_NEG : 0u));
+        }
     }
 }
 
-__device__ __forceinline__ const Inst& inst_of(long long t, const Inst* d_inst,
-                                               const uint16_t* tile_inst, const Inst& single)
+// neighbour-existence bits of tile t (single instance or batched table)
+__device__ __forceinline__ unsigned nb_bits(long long t, const Inst& in)
 {
-    return tile_inst ? d_inst[tile_inst[t]] : single;
+    const long long loc = t - in.tile_base;
+    const long long tpl = (long long)in.tnx * in.tny;
+    const int tz = (int)(loc / tpl);
+    const int rem = (int)(loc - (long long)tz * tpl);
+    const int ty = rem / in.tnx, tx = rem - ty * in.tnx;
+    unsigned b = 0;
+    if (tx > 0) b |= NB_XM;
+    if (tx < in.tnx - 1) b |= NB_XP;
+    if (ty > 0) b |= NB_YM;
+    if (ty < in.tny - 1) b |= NB_YP;
+    if (tz > 0) b |= NB_ZM;
+    if (tz < in.tnz - 1) b |= NB_ZP;
+    return b;
 }
+
 
 // Eq. 6 per tile: core = (min |phi| over the tile) < gamma, compared in FP64
 template <typename T>
@@ -157,18 +189,18 @@ __global__ void __launch_bounds__(256) k_classify_all(const T* __restrict__ phi,
 }
 
 // ---------------------------------------------------------------------------
-// dilation by one tile (26 neighbours, inside the instance), leaving-tile
-// buffer sync, per-block active counts.  One thread per tile, 256 per block.
+// dilation by one tile (26 neighbours, inside the instance) and per-block
+// active counts.  One thread per tile, 256 per block.  act[t] keeps the new
+// flag in bit 0 and the previous one in bit 1 (the scatter pass uses both to
+// find the tiles that leave the active set).
 // ---------------------------------------------------------------------------
-template <int ESIZE>
 __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core, uint8_t* act,
-                                                const uint4* __restrict__ cur, uint4* other,
                                                 int* block_counts, const Inst* d_inst,
                                                 const uint16_t* tile_inst, Inst single,
                                                 long long ntiles)
 {
     const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
-    int on = 0, old = 0;
+    int on = 0;
     if (t < ntiles) {
         const Inst& in = inst_of(t, d_inst, tile_inst, single);
         const long long loc = t - in.tile_base;
@@ -190,21 +222,8 @@ __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core
                 }
             }
         }
-        old = act[t];
-        act[t] = (uint8_t)on;
-    }
-    // tiles leaving the active set: copy their current values into the other
-    // ping-pong buffer so both buffers agree on every inactive tile
-    unsigned leaving = __ballot_sync(0xffffffffu, old && !on);
-    constexpr int VEC = TILE_PTS * ESIZE / 16;  // uint4 per tile
-    while (leaving) {
-        const int src_lane = __ffs(leaving) - 1;
-        leaving &= leaving - 1;
-        const long long lt = (long long)blockIdx.x * 256 + (threadIdx.x & ~31u) + src_lane;
-        const uint4* s = cur + (size_t)lt * VEC;
-        uint4* d = other + (size_t)lt * VEC;
-#pragma unroll
-        for (int k = 0; k < VEC / 32; ++k) d[lane_id() + 32 * k] = s[lane_id() + 32 * k];
+        const int old = act[t] & 1;
+        act[t] = (uint8_t)(on | (old << 1));
     }
     const int cnt = __syncthreads_count(on);
     if (threadIdx.x == 0) block_counts[blockIdx.x] = cnt;
@@ -257,18 +276,30 @@ __device__ __forceinline__ unsigned long long ordered_bits(T v)
 }
 
 // scatter active ids in ascending order; block max of tile max|F| over the
-// active tiles -> atomicMax on the ordered bits (values are >= 0)
+// active tiles -> atomicMax on the ordered bits (values are >= 0).  Tiles
+// leaving the active set get their current values copied into the other
+// ping-pong buffer (the whole block copies them together), so both buffers
+// agree on every inactive tile.
 template <typename T>
 __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act,
                                                  const int* __restrict__ offsets, int* list,
+                                                 uint8_t* list_info,
+                                                 const uint8_t* __restrict__ tile_sgn,
+                                                 unsigned const_sgn, Inst single,
                                                  long long ntiles, const T* __restrict__ tile_maxF,
-                                                 unsigned long long* Mbits)
+                                                 unsigned long long* Mbits,
+                                                 const uint4* __restrict__ cur, uint4* other)
 {
     __shared__ int warp_cnt[8];
+    __shared__ int warp_leave[8];
     __shared__ unsigned long long warp_max_bits[8];
+    __shared__ int leave_ids[256];
     const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
-    const int on = (t < ntiles) ? act[t] : 0;
+    const int fl = (t < ntiles) ? act[t] : 0;
+    const int on = fl & 1;
+    const int leaving = (fl & 2) && !on;
     const unsigned b = __ballot_sync(0xffffffffu, on);
+    const unsigned bl = __ballot_sync(0xffffffffu, leaving);
     const int w = threadIdx.x >> 5;
     unsigned long long mb = 0;
     if (on && tile_maxF) mb = ordered_bits(tile_maxF[t]);
@@ -279,20 +310,52 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
     }
     if (lane_id() == 0) {
         warp_cnt[w] = __popc(b);
+        warp_leave[w] = __popc(bl);
         warp_max_bits[w] = mb;
     }
     __syncthreads();
-    int before = 0;
-    for (int k = 0; k < w; ++k) before += warp_cnt[k];
-    if (on) {
-        const int rank = __popc(b & ((1u << lane_id()) - 1u));
-        list[offsets[blockIdx.x] + before + rank] = (int)t;
+    int before = 0, lbefore = 0, ltotal = 0;
+    for (int k = 0; k < 8; ++k) {
+        if (k < w) {
+            before += warp_cnt[k];
+            lbefore += warp_leave[k];
+        }
+        ltotal += warp_leave[k];
     }
+    const unsigned below = (1u << lane_id()) - 1u;
+    if (on) {
+        const int pos = offsets[blockIdx.x] + before + __popc(b & below);
+        list[pos] = (int)t;
+        list_info[pos] = (uint8_t)(nb_bits(t, single) | (tile_sgn ? tile_sgn[t] : const_sgn));
+    }
+    if (leaving) leave_ids[lbefore + __popc(bl & below)] = (int)t;
     if (threadIdx.x == 0 && tile_maxF) {
         unsigned long long m = 0;
         for (int k = 0; k < 8; ++k) m = warp_max_bits[k] > m ? warp_max_bits[k] : m;
         if (m) atomicMax(Mbits, m);
     }
+    if (ltotal == 0) return;
+    __syncthreads();
+    constexpr int VEC = TILE_PTS * sizeof(T) / 16;  // uint4 per tile
+    const int total = ltotal * VEC;
+    for (int i = threadIdx.x; i < total; i += 256) {
+        const size_t off = (size_t)leave_ids[i / VEC] * VEC + (i % VEC);
+        other[off] = cur[off];
+    }
+}
+
+// full-domain list: every tile in ascending order
+__global__ void __launch_bounds__(256) k_full_list(int* list, uint8_t* list_info,
+                                                   const uint8_t* __restrict__ tile_sgn,
+                                                   unsigned const_sgn, Inst single,
+                                                   long long ntiles, int* count)
+{
+    for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < ntiles;
+         t += (long long)gridDim.x * 256) {
+        list[t] = (int)t;
+        list_info[t] = (uint8_t)(nb_bits(t, single) | (tile_sgn ? tile_sgn[t] : const_sgn));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = (int)ntiles;
 }
 
 // max of tile max|F| over all tiles (full-domain CFL bound)
@@ -390,15 +453,15 @@ static int warp_grid(long long ntiles)
     return (int)(g > 0 ? g : 1);
 }
 
-cudaError_t launch_tile_maxabs(const void* F, void* tile_maxF, long long ntiles, int prec,
-                               cudaStream_t s)
+cudaError_t launch_tile_speed(const void* F, void* tile_maxF, uint8_t* tile_sgn, long long ntiles,
+                              int prec, cudaStream_t s)
 {
     if (prec == 0)
-        k_tile_maxabs<float><<<warp_grid(ntiles), 256, 0, s>>>((const float*)F, (float*)tile_maxF,
-                                                               ntiles);
+        k_tile_speed<float><<<warp_grid(ntiles), 256, 0, s>>>((const float*)F, (float*)tile_maxF,
+                                                              tile_sgn, ntiles);
     else
-        k_tile_maxabs<double><<<warp_grid(ntiles), 256, 0, s>>>((const double*)F,
-                                                                (double*)tile_maxF, ntiles);
+        k_tile_speed<double><<<warp_grid(ntiles), 256, 0, s>>>((const double*)F,
+                                                               (double*)tile_maxF, tile_sgn, ntiles);
     return cudaGetLastError();
 }
 
@@ -415,17 +478,12 @@ cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_in
     return cudaGetLastError();
 }
 
-cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, const void* cur, void* other,
-                          int* block_counts, const Inst* d_inst, const uint16_t* tile_inst,
-                          const Inst& single, long long ntiles, int prec, cudaStream_t s)
+cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
+                          const Inst* d_inst, const uint16_t* tile_inst, const Inst& single,
+                          long long ntiles, cudaStream_t s)
 {
     const int nb = (int)((ntiles + 255) / 256);
-    if (prec == 0)
-        k_dilate<4><<<nb, 256, 0, s>>>(core, act, (const uint4*)cur, (uint4*)other, block_counts,
-                                       d_inst, tile_inst, single, ntiles);
-    else
-        k_dilate<8><<<nb, 256, 0, s>>>(core, act, (const uint4*)cur, (uint4*)other, block_counts,
-                                       d_inst, tile_inst, single, ntiles);
+    k_dilate<<<nb, 256, 0, s>>>(core, act, block_counts, d_inst, tile_inst, single, ntiles);
     return cudaGetLastError();
 }
 
@@ -436,16 +494,31 @@ cudaError_t launch_scan(int* block_counts, int nblocks, int* count, cudaStream_t
 }
 
 cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* list,
-                           long long ntiles, const void* tile_maxF, int prec,
-                           unsigned long long* Mbits, cudaStream_t s)
+                           uint8_t* list_info, const uint8_t* tile_sgn, unsigned const_sgn,
+                           const Inst& single, long long ntiles, const void* tile_maxF, int prec,
+                           unsigned long long* Mbits, const void* cur, void* other,
+                           cudaStream_t s)
 {
     const int nb = (int)((ntiles + 255) / 256);
     if (prec == 0)
-        k_scatter<float><<<nb, 256, 0, s>>>(act, block_offsets, list, ntiles,
-                                            (const float*)tile_maxF, Mbits);
+        k_scatter<float><<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, tile_sgn,
+                                            const_sgn, single, ntiles, (const float*)tile_maxF,
+                                            Mbits, (const uint4*)cur, (uint4*)other);
     else
-        k_scatter<double><<<nb, 256, 0, s>>>(act, block_offsets, list, ntiles,
-                                             (const double*)tile_maxF, Mbits);
+        k_scatter<double><<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, tile_sgn,
+                                             const_sgn, single, ntiles, (const double*)tile_maxF,
+                                             Mbits, (const uint4*)cur, (uint4*)other);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_full_list(int* list, uint8_t* list_info, const uint8_t* tile_sgn,
+                             unsigned const_sgn, const Inst& single, long long ntiles, int* count,
+                             cudaStream_t s)
+{
+    long long g = (ntiles + 255) / 256;
+    if (g > 148 * 16) g = 148 * 16;
+    k_full_list<<<(int)(g > 0 ? g : 1), 256, 0, s>>>(list, list_info, tile_sgn, const_sgn, single,
+                                                     ntiles, count);
     return cudaGetLastError();
 }
 

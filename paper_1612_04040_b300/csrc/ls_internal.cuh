@@ -41,6 +41,17 @@ enum : unsigned {
     ST_NONFINITE = 4u,
 };
 
+// Per-active-tile info byte written by the rebuild (read by the stencil, so
+// that it needs no tile-coordinate arithmetic): which of the six face
+// neighbours exist inside the instance, and whether every speed of the tile
+// has one sign.
+enum : unsigned {
+    NB_XM = 1u, NB_XP = 2u, NB_YM = 4u, NB_YP = 8u, NB_ZM = 16u, NB_ZP = 32u,
+    NB_ALL = 63u,
+    SG_POS = 64u,   // every F >= 0 in the tile (G+ of Eq. 4 everywhere)
+    SG_NEG = 128u,  // every F < 0 in the tile (G- of Eq. 5 everywhere)
+};
+
 // Per-step scalars on the device, one per instance.
 struct StepScalars {
     double M;      // max |F| over the active set at the last rebuild
@@ -57,24 +68,32 @@ struct StepScalars {
 cudaError_t launch_pack(const void* src, void* dst, const Inst& in, int prec, unsigned* nonfinite,
                         cudaStream_t s);
 cudaError_t launch_unpack(const void* src, void* dst, const Inst& in, int prec, cudaStream_t s);
-// tile_maxF[t] = max |F| over tile t (field speed)
-cudaError_t launch_tile_maxabs(const void* F, void* tile_maxF, long long ntiles, int prec,
-                               cudaStream_t s);
+// tile_maxF[t] = max |F| over tile t; tile_sgn[t] = SG_POS / SG_NEG / 0
+cudaError_t launch_tile_speed(const void* F, void* tile_maxF, uint8_t* tile_sgn, long long ntiles,
+                              int prec, cudaStream_t s);
 // core[t] = (min_{p in t} |phi_p| < gamma) over all tiles of all instances
 cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_inst,
                                 const uint16_t* tile_inst, const Inst& single, long long ntiles,
                                 int prec, cudaStream_t s);
-// band rebuild: dilation + leaving-tile sync + block counts
-cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, const void* cur, void* other,
-                          int* block_counts, const Inst* d_inst, const uint16_t* tile_inst,
-                          const Inst& single, long long ntiles, int prec, cudaStream_t s);
+// band rebuild: dilation (act bit 0 = new flag, bit 1 = previous) + block counts
+cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
+                          const Inst* d_inst, const uint16_t* tile_inst, const Inst& single,
+                          long long ntiles, cudaStream_t s);
 // exclusive scan of block counts, writes total to *count
 cudaError_t launch_scan(int* block_counts, int nblocks, int* count, cudaStream_t s);
-// scatter active ids (ascending) and fold max |F| of the active tiles into
-// *Mbits (ordered bits of a non-negative float / double)
+// scatter active ids (ascending) with their info bytes, fold max |F| of the
+// active tiles into *Mbits (ordered bits of a non-negative float / double),
+// and copy the tiles leaving the active set from cur into other.
+// tile_sgn == NULL: constant speed, sign bits const_sgn.
 cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* list,
-                           long long ntiles, const void* tile_maxF, int prec,
-                           unsigned long long* Mbits, cudaStream_t s);
+                           uint8_t* list_info, const uint8_t* tile_sgn, unsigned const_sgn,
+                           const Inst& single, long long ntiles, const void* tile_maxF, int prec,
+                           unsigned long long* Mbits, const void* cur, void* other,
+                           cudaStream_t s);
+// full-domain list: every tile, ascending, with info bytes; *count = ntiles
+cudaError_t launch_full_list(int* list, uint8_t* list_info, const uint8_t* tile_sgn,
+                             unsigned const_sgn, const Inst& single, long long ntiles, int* count,
+                             cudaStream_t s);
 // max of tile max|F| over all tiles (full-domain mode)
 cudaError_t launch_max_all(const void* tile_maxF, long long ntiles, int prec,
                            unsigned long long* Mbits, cudaStream_t s);
@@ -93,9 +112,9 @@ struct StepArgs {
     const void* src;
     void* dst;
     const void* F;            // field (bricked) or NULL for constant speed
-    const int* list;          // active tile ids, or NULL: tile id = index
+    const int* list;          // active tile ids (ascending)
+    const uint8_t* info;      // per-entry info byte (NB_* | SG_*)
     const int* count;         // number of active tiles (device)
-    long long fixed_count;    // used when list == NULL
     const StepScalars* sc;
     uint8_t* core;            // fused tube test output, or NULL
     unsigned long long* updates;

@@ -28,42 +28,114 @@ namespace lsk {
 
 namespace {
 
-__device__ __forceinline__ void tile_coords(int t, const Inst& in, int& tx, int& ty, int& tz)
-{
-    const int tpl = in.tnx * in.tny;
-    tz = t / tpl;
-    const int r = t - tz * tpl;
-    ty = r / in.tnx;
-    tx = r - ty * in.tnx;
-}
-
 // ------------------------------------------------------------------ FP32 ----
+// Pipelined variant: each thread stages, with cp.async, exactly the values it
+// needs for a tile S-1 iterations ahead (its 4 centre values and speeds, its
+// x-halo value, and the y/z-halo runs for threads on a tile face) into a
+// ring of S shared-memory stages, so the latency of the next tiles' loads
+// overlaps the arithmetic of the current one.
+constexpr int S32 = 3;  // pipeline stages
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+struct Stage32 {
+    float4 c[128];   // centre values, element offset 4*tid of the tile
+    float4 f[128];   // speeds (field speed only)
+    float xo[128];   // x-halo value of each thread
+    float4 yo[32];   // y-halo runs: [16*(ly==7) + 2*lz + xh]
+    float4 zo[32];   // z-halo runs: [16*(lz==7) + 2*ly + xh]
+    int4 meta;       // tile id, tx, ty, tz
+};
+
+// Eq. 3-5 at one point, FP32.  Differences are unscaled (1/h is folded into
+// coef = dt/h).  SGN = +1: every F >= 0 here, G+ of Eq. 4; SGN = -1: every
+// F < 0, G- of Eq. 5; SGN = 0: per point, through G-(phi) = G+(-phi).
+// |grad| = q * rsqrt(q) (q clamped away from 0, where the product is 0).
+template <int SGN>
 __device__ __forceinline__ float upd32(float c, float f, float dmx, float dpx, float dmy,
                                        float dpy, float dmz, float dpz, float coef)
 {
-    const float s = (f >= 0.f) ? 1.f : -1.f;  // G+ for F >= 0, G- = G+(-phi) for F < 0
-    const float ax = fmaxf(s * dmx, 0.f), bx = fminf(s * dpx, 0.f);
-    const float ay = fmaxf(s * dmy, 0.f), by = fminf(s * dpy, 0.f);
-    const float az = fmaxf(s * dmz, 0.f), bz = fminf(s * dpz, 0.f);
+    float ax, bx, ay, by, az, bz;
+    if (SGN > 0) {
+        ax = fmaxf(dmx, 0.f); bx = fminf(dpx, 0.f);
+        ay = fmaxf(dmy, 0.f); by = fminf(dpy, 0.f);
+        az = fmaxf(dmz, 0.f); bz = fminf(dpz, 0.f);
+    } else if (SGN < 0) {
+        ax = fminf(dmx, 0.f); bx = fmaxf(dpx, 0.f);
+        ay = fminf(dmy, 0.f); by = fmaxf(dpy, 0.f);
+        az = fminf(dmz, 0.f); bz = fmaxf(dpz, 0.f);
+    } else {
+        const float s = (f >= 0.f) ? 1.f : -1.f;
+        ax = fmaxf(s * dmx, 0.f); bx = fminf(s * dpx, 0.f);
+        ay = fmaxf(s * dmy, 0.f); by = fminf(s * dpy, 0.f);
+        az = fmaxf(s * dmz, 0.f); bz = fminf(s * dpz, 0.f);
+    }
     float q = ax * ax;
     q = fmaf(bx, bx, q);
     q = fmaf(ay, ay, q);
     q = fmaf(by, by, q);
     q = fmaf(az, az, q);
     q = fmaf(bz, bz, q);
-    const float g = sqrtf(q);
+    const float g = q * rsqrtf(fmaxf(q, 1e-30f));
     return fmaf(-(coef * f), g, c);
+}
+
+__device__ __forceinline__ float comp(const float4& v, int j)
+{
+    return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+
+// the four points of one thread.  FACES: apply the domain-face rule (only
+// for tiles that touch the domain boundary).
+template <int SGN, bool FACES>
+__device__ __forceinline__ float4 upd4(const float4& c, const float4& f, float xm0, float xp3,
+                                       const float4& ym, const float4& yp, const float4& zm,
+                                       const float4& zp, float coef, bool extrap, bool xlo,
+                                       bool xhi, bool ylo, bool yhi, bool zlo, bool zhi)
+{
+    const float xs[6] = {xm0, c.x, c.y, c.z, c.w, xp3};
+    float r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float cj = xs[j + 1];
+        float dmx = cj - xs[j], dpx = xs[j + 2] - cj;
+        float dmy = cj - comp(ym, j), dpy = comp(yp, j) - cj;
+        float dmz = cj - comp(zm, j), dpz = comp(zp, j) - cj;
+        if (FACES) {
+            if (j == 0 && xlo) dmx = extrap ? dpx : 0.f;
+            if (j == 3 && xhi) dpx = extrap ? dmx : 0.f;
+            if (ylo) dmy = extrap ? dpy : 0.f;
+            if (yhi) dpy = extrap ? dmy : 0.f;
+            if (zlo) dmz = extrap ? dpz : 0.f;
+            if (zhi) dpz = extrap ? dmz : 0.f;
+        }
+        r[j] = upd32<SGN>(cj, comp(f, j), dmx, dpx, dmy, dpy, dmz, dpz, coef);
+    }
+    return make_float4(r[0], r[1], r[2], r[3]);
 }
 
 template <bool FIELD, bool CLASSIFY>
 __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
 {
-    __shared__ float4 sm[2][8][8][2];
-    __shared__ unsigned smin[2];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Stage32* st = reinterpret_cast<Stage32*>(smem_raw);
+    __shared__ unsigned smin[S32];
     const int tid = threadIdx.x;
     const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
     const Inst in = a.in;
-    const long long n = a.list ? (long long)(*a.count) : a.fixed_count;
+    const int n = *a.count;
     if (blockIdx.x == 0 && tid == 0 && a.updates)
         atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
     const float coef = a.sc->coef;
@@ -72,97 +144,109 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     const float* __restrict__ Fp = (const float*)a.F;
     const float Fc = (float)in.Fc;
     const bool extrap = in.bc == 0;
-    const long long sy = (long long)in.tnx * TILE_PTS;
-    const long long sz = (long long)in.tnx * in.tny * TILE_PTS;
-    const int off = tid * 4;
-    int buf = 0;
-    int prev_t = -1;
-    for (long long k = blockIdx.x; k < n; k += gridDim.x) {
-        const int t = a.list ? __ldg(a.list + k) : (int)k;
-        int tx, ty, tz;
-        tile_coords(t, in, tx, ty, tz);
-        const float* tp = src + (size_t)t * TILE_PTS;
-        const float4 c = __ldg(reinterpret_cast<const float4*>(tp + off));
-        float4 f;
-        if (FIELD) f = __ldg(reinterpret_cast<const float4*>(Fp + (size_t)t * TILE_PTS + off));
-        else f = make_float4(Fc, Fc, Fc, Fc);
-        // x halo: left of point 0 (xh = 0) or right of point 3 (xh = 1)
-        const bool xlo_face = (xh == 0) && (tx == 0);
-        const bool xhi_face = (xh == 1) && (tx == in.tnx - 1);
-        float xo = 0.f;
-        if (xh == 0) {
-            if (!xlo_face) xo = __ldg(tp - TILE_PTS + lz * 64 + ly * 8 + 7);
-        } else {
-            if (!xhi_face) xo = __ldg(tp + TILE_PTS + lz * 64 + ly * 8);
+    const int sy = in.tnx * TILE_PTS;
+    const int sz = in.tnx * in.tny * TILE_PTS;
+    const int stride = gridDim.x;
+    // per-thread halo sources (offsets from the tile start) and the info bit
+    // that says the neighbour exists; 0 = this thread has no halo on that axis
+    const int x_off = xh ? (TILE_PTS + lz * 64 + ly * 8) : (-TILE_PTS + lz * 64 + ly * 8 + 7);
+    const unsigned x_bit = xh ? NB_XP : NB_XM;
+    const int y_off = (ly == 0) ? (-sy + lz * 64 + 56 + 4 * xh) : (sy + lz * 64 + 4 * xh);
+    const unsigned y_bit = (ly == 0) ? NB_YM : ((ly == 7) ? NB_YP : 0u);
+    const int y_slot = ((ly == 7) ? 16 : 0) + 2 * lz + xh;
+    const int z_off = (lz == 0) ? (-sz + 448 + ly * 8 + 4 * xh) : (sz + ly * 8 + 4 * xh);
+    const unsigned z_bit = (lz == 0) ? NB_ZM : ((lz == 7) ? NB_ZP : 0u);
+    const int z_slot = ((lz == 7) ? 16 : 0) + 2 * ly + xh;
+
+    // stage the data of list entry k into ring slot s
+    auto issue = [&](int k, int s) {
+        const unsigned t = (unsigned)__ldg(a.list + k);
+        const unsigned info = __ldg(a.info + k);
+        const unsigned base = t * TILE_PTS;
+        const float* tp = src + base;
+        Stage32& S = st[s];
+        if (tid == 0) {
+            S.meta = make_int4((int)t, (int)info, 0, 0);
+            if (CLASSIFY) smin[s] = 0x7f800000u;
         }
-        // y halo (rows ly = 0 / 7)
-        const bool ylo_face = (ly == 0) && (ty == 0);
-        const bool yhi_face = (ly == 7) && (ty == in.tny - 1);
-        float4 yo = c;
-        if (ly == 0 && !ylo_face)
-            yo = __ldg(reinterpret_cast<const float4*>(tp - sy + lz * 64 + 56 + 4 * xh));
-        if (ly == 7 && !yhi_face)
-            yo = __ldg(reinterpret_cast<const float4*>(tp + sy + lz * 64 + 4 * xh));
-        // z halo (planes lz = 0 / 7)
-        const bool zlo_face = (lz == 0) && (tz == 0);
-        const bool zhi_face = (lz == 7) && (tz == in.tnz - 1);
-        float4 zo = c;
-        if (lz == 0 && !zlo_face)
-            zo = __ldg(reinterpret_cast<const float4*>(tp - sz + 448 + ly * 8 + 4 * xh));
-        if (lz == 7 && !zhi_face)
-            zo = __ldg(reinterpret_cast<const float4*>(tp + sz + ly * 8 + 4 * xh));
+        cp_async16(&S.c[tid], tp + 4 * tid);
+        if (FIELD) cp_async16(&S.f[tid], Fp + base + 4 * tid);
+        if (info & x_bit) cp_async4(&S.xo[tid], tp + x_off);
+        if (info & y_bit) cp_async16(&S.yo[y_slot], tp + y_off);
+        if (info & z_bit) cp_async16(&S.zo[z_slot], tp + z_off);
+    };
 
-        sm[buf][lz][ly][xh] = c;
-        if (CLASSIFY && tid == 0) smin[buf] = 0x7f800000u;
+#pragma unroll
+    for (int s = 0; s < S32 - 1; ++s) {
+        const int k = blockIdx.x + s * stride;
+        if (k < n) issue(k, s);
+        cp_async_commit();
+    }
+    int cur = 0;
+    int prev = -1;
+    int prev_t = -1;
+    for (int k = blockIdx.x; k < n; k += stride) {
+        cp_async_wait<S32 - 2>();
         __syncthreads();
-        if (CLASSIFY && tid == 0 && prev_t >= 0)
-            a.core[prev_t] = ((double)__uint_as_float(smin[buf ^ 1]) < in.gamma) ? 1 : 0;
-
-        const float4 ym = (ly > 0) ? sm[buf][lz][ly - 1][xh] : yo;
-        const float4 yp = (ly < 7) ? sm[buf][lz][ly + 1][xh] : yo;
-        const float4 zm = (lz > 0) ? sm[buf][lz - 1][ly][xh] : zo;
-        const float4 zp = (lz < 7) ? sm[buf][lz + 1][ly][xh] : zo;
-        const float part = __shfl_xor_sync(0xffffffffu, xh ? c.x : c.w, 1);
-        const float xm0 = xh ? part : xo;
-        const float xp3 = xh ? xo : part;
-
-        // x differences (unscaled)
-        const float d0 = c.x - xm0, d1 = c.y - c.x, d2 = c.z - c.y, d3 = c.w - c.z, d4 = xp3 - c.w;
-        float dmx0 = d0;
-        float dpx3 = d4;
-        if (xlo_face) dmx0 = extrap ? d1 : 0.f;
-        if (xhi_face) dpx3 = extrap ? d3 : 0.f;
-        // y / z differences with the face rule
-        float4 dmy = make_float4(c.x - ym.x, c.y - ym.y, c.z - ym.z, c.w - ym.w);
-        float4 dpy = make_float4(yp.x - c.x, yp.y - c.y, yp.z - c.z, yp.w - c.w);
-        float4 dmz = make_float4(c.x - zm.x, c.y - zm.y, c.z - zm.z, c.w - zm.w);
-        float4 dpz = make_float4(zp.x - c.x, zp.y - c.y, zp.z - c.z, zp.w - c.w);
-        if (ylo_face) dmy = extrap ? dpy : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (yhi_face) dpy = extrap ? dmy : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (zlo_face) dmz = extrap ? dpz : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (zhi_face) dpz = extrap ? dmz : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (CLASSIFY && tid == 0 && prev >= 0)
+            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < in.gamma) ? 1 : 0;
+        {
+            const int kn = k + (S32 - 1) * stride;
+            const int sn = (cur + S32 - 1) % S32;
+            if (kn < n) issue(kn, sn);
+            cp_async_commit();
+        }
+        const Stage32& S = st[cur];
+        const int t = S.meta.x;
+        const unsigned info = (unsigned)S.meta.y;
+        const float4 c = S.c[tid];
+        const float4 f = FIELD ? S.f[tid] : make_float4(Fc, Fc, Fc, Fc);
+        const float4 ym = (ly > 0) ? S.c[tid - 2] : S.yo[y_slot];
+        const float4 yp = (ly < 7) ? S.c[tid + 2] : S.yo[y_slot];
+        const float4 zm = (lz > 0) ? S.c[tid - 16] : S.zo[z_slot];
+        const float4 zp = (lz < 7) ? S.c[tid + 16] : S.zo[z_slot];
+        const float4 pc = S.c[tid ^ 1];
+        const float xo = S.xo[tid];
+        const float xm0 = xh ? pc.w : xo;
+        const float xp3 = xh ? xo : pc.x;
 
         float4 o;
-        o.x = upd32(c.x, f.x, dmx0, d1, dmy.x, dpy.x, dmz.x, dpz.x, coef);
-        o.y = upd32(c.y, f.y, d1, d2, dmy.y, dpy.y, dmz.y, dpz.y, coef);
-        o.z = upd32(c.z, f.z, d2, d3, dmy.z, dpy.z, dmz.z, dpz.z, coef);
-        o.w = upd32(c.w, f.w, d3, dpx3, dmy.w, dpy.w, dmz.w, dpz.w, coef);
-        *reinterpret_cast<float4*>(dst + (size_t)t * TILE_PTS + off) = o;
+        if (info == (NB_ALL | SG_POS)) {
+            o = upd4<1, false>(c, f, xm0, xp3, ym, yp, zm, zp, coef, extrap, false, false, false,
+                               false, false, false);
+        } else if (info == (NB_ALL | SG_NEG)) {
+            o = upd4<-1, false>(c, f, xm0, xp3, ym, yp, zm, zp, coef, extrap, false, false, false,
+                                false, false, false);
+        } else {
+            const bool xlo = (xh == 0) && !(info & NB_XM);
+            const bool xhi = (xh == 1) && !(info & NB_XP);
+            const bool ylo = (ly == 0) && !(info & NB_YM);
+            const bool yhi = (ly == 7) && !(info & NB_YP);
+            const bool zlo = (lz == 0) && !(info & NB_ZM);
+            const bool zhi = (lz == 7) && !(info & NB_ZP);
+            o = upd4<0, true>(c, f, xm0, xp3, ym, yp, zm, zp, coef, extrap, xlo, xhi, ylo, yhi,
+                              zlo, zhi);
+        }
+        *reinterpret_cast<float4*>(dst + (unsigned)t * TILE_PTS + 4 * tid) = o;
 
         if (CLASSIFY) {
-            const float m = fminf(fminf(fabsf(o.x), fabsf(o.y)), fminf(fabsf(o.z), fabsf(o.w)));
-            const unsigned wm = __reduce_min_sync(0xffffffffu, __float_as_uint(m));
-            if ((tid & 31) == 0) atomicMin(&smin[buf], wm);
+            const float mn = fminf(fminf(fabsf(o.x), fabsf(o.y)), fminf(fabsf(o.z), fabsf(o.w)));
+            const unsigned wm = __reduce_min_sync(0xffffffffu, __float_as_uint(mn));
+            if ((tid & 31) == 0) atomicMin(&smin[cur], wm);
         }
-        buf ^= 1;
+        prev = cur;
         prev_t = t;
+        cur = (cur + 1) % S32;
     }
     if (CLASSIFY) {
         __syncthreads();
-        if (tid == 0 && prev_t >= 0)
-            a.core[prev_t] = ((double)__uint_as_float(smin[buf ^ 1]) < in.gamma) ? 1 : 0;
+        if (tid == 0 && prev >= 0)
+            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < in.gamma) ? 1 : 0;
     }
+    cp_async_wait<0>();
 }
+
+constexpr size_t SMEM32 = sizeof(Stage32) * S32;
 
 // ------------------------------------------------------------------ FP64 ----
 __device__ __forceinline__ double max0(double a) { return a > 0.0 ? a : 0.0; }
@@ -222,7 +306,7 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
     const int tid = threadIdx.x;
     const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
     const Inst in = a.in;
-    const long long n = a.list ? (long long)(*a.count) : a.fixed_count;
+    const long long n = *a.count;
     if (blockIdx.x == 0 && tid == 0 && a.updates)
         atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
     const double dt = a.sc->dt;
@@ -238,29 +322,28 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
     int buf = 0;
     int prev_t = -1;
     for (long long k = blockIdx.x; k < n; k += gridDim.x) {
-        const int t = a.list ? __ldg(a.list + k) : (int)k;
-        int tx, ty, tz;
-        tile_coords(t, in, tx, ty, tz);
+        const int t = __ldg(a.list + k);
+        const unsigned info = __ldg(a.info + k);
         const double* tp = src + (size_t)t * TILE_PTS;
         const D4 c = ld4(tp + off);
         D4 f;
         if (FIELD) f = ld4(Fp + (size_t)t * TILE_PTS + off);
         else { f.v[0] = f.v[1] = f.v[2] = f.v[3] = in.Fc; }
-        const bool xlo_face = (xh == 0) && (tx == 0);
-        const bool xhi_face = (xh == 1) && (tx == in.tnx - 1);
+        const bool xlo_face = (xh == 0) && !(info & NB_XM);
+        const bool xhi_face = (xh == 1) && !(info & NB_XP);
         double xo = 0.0;
         if (xh == 0) {
             if (!xlo_face) xo = __ldg(tp - TILE_PTS + lz * 64 + ly * 8 + 7);
         } else {
             if (!xhi_face) xo = __ldg(tp + TILE_PTS + lz * 64 + ly * 8);
         }
-        const bool ylo_face = (ly == 0) && (ty == 0);
-        const bool yhi_face = (ly == 7) && (ty == in.tny - 1);
+        const bool ylo_face = (ly == 0) && !(info & NB_YM);
+        const bool yhi_face = (ly == 7) && !(info & NB_YP);
         D4 yo = c;
         if (ly == 0 && !ylo_face) yo = ld4(tp - sy + lz * 64 + 56 + 4 * xh);
         if (ly == 7 && !yhi_face) yo = ld4(tp + sy + lz * 64 + 4 * xh);
-        const bool zlo_face = (lz == 0) && (tz == 0);
-        const bool zhi_face = (lz == 7) && (tz == in.tnz - 1);
+        const bool zlo_face = (lz == 0) && !(info & NB_ZM);
+        const bool zhi_face = (lz == 7) && !(info & NB_ZP);
         D4 zo = c;
         if (lz == 0 && !zlo_face) zo = ld4(tp - sz + 448 + ly * 8 + 4 * xh);
         if (lz == 7 && !zhi_face) zo = ld4(tp + sz + ly * 8 + 4 * xh);
@@ -321,12 +404,12 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
 }
 
 template <typename K>
-int occupancy_grid(K kernel)
+int occupancy_grid(K kernel, size_t smem)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 128, smem);
     if (per < 1) per = 1;
     return sms * per;
 }
@@ -339,9 +422,11 @@ int step_grid_size(int prec, int classify)
     int& g = cache[prec ? 1 : 0][classify ? 1 : 0];
     if (!g) {
         if (prec == 0)
-            g = classify ? occupancy_grid(k_step_f32<true, true>) : occupancy_grid(k_step_f32<true, false>);
+            g = classify ? occupancy_grid(k_step_f32<true, true>, SMEM32)
+                         : occupancy_grid(k_step_f32<true, false>, SMEM32);
         else
-            g = classify ? occupancy_grid(k_step_f64<true, true>) : occupancy_grid(k_step_f64<true, false>);
+            g = classify ? occupancy_grid(k_step_f64<true, true>, 0)
+                         : occupancy_grid(k_step_f64<true, false>, 0);
     }
     return g;
 }
@@ -351,10 +436,10 @@ cudaError_t launch_step(const StepArgs& a, int prec, int grid, cudaStream_t s)
     const bool field = a.F != nullptr;
     const bool cls = a.core != nullptr;
     if (prec == 0) {
-        if (field && cls) k_step_f32<true, true><<<grid, 128, 0, s>>>(a);
-        else if (field) k_step_f32<true, false><<<grid, 128, 0, s>>>(a);
-        else if (cls) k_step_f32<false, true><<<grid, 128, 0, s>>>(a);
-        else k_step_f32<false, false><<<grid, 128, 0, s>>>(a);
+        if (field && cls) k_step_f32<true, true><<<grid, 128, SMEM32, s>>>(a);
+        else if (field) k_step_f32<true, false><<<grid, 128, SMEM32, s>>>(a);
+        else if (cls) k_step_f32<false, true><<<grid, 128, SMEM32, s>>>(a);
+        else k_step_f32<false, false><<<grid, 128, SMEM32, s>>>(a);
     } else {
         if (field && cls) k_step_f64<true, true><<<grid, 128, 0, s>>>(a);
         else if (field) k_step_f64<true, false><<<grid, 128, 0, s>>>(a);
