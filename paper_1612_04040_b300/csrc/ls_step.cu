@@ -36,27 +36,43 @@ namespace {
 // overlaps the arithmetic of the current one.
 constexpr int S32 = 3;  // pipeline stages
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+// cp.async of 16 / 4 bytes into shared memory, predicated (no branch)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred = true)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %2, 0;\n"
+        "  @p cp.async.cg.shared.global [%0], [%1], 16; }\n" ::"r"(s), "l"(gmem), "r"((int)pred)
+        : "memory");
 }
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred = true)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %2, 0;\n"
+        "  @p cp.async.ca.shared.global [%0], [%1], 4; }\n" ::"r"(s), "l"(gmem), "r"((int)pred)
+        : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// hardware reciprocal square root (approximate, flush-to-zero): the inputs
+// here are clamped to >= 1e-30, so no denormal reaches it
+__device__ __forceinline__ float rsqrt_hw(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 struct Stage32 {
-    float4 c[128];   // centre values, element offset 4*tid of the tile
+    float4 v[192];   // [0,128): centre values (element offset 4*tid of the tile);
+                     // [128,160): y-halo runs [16*(ly==7) + 2*lz + xh];
+                     // [160,192): z-halo runs [16*(lz==7) + 2*ly + xh]
     float4 f[128];   // speeds (field speed only)
     float xo[128];   // x-halo value of each thread
-    float4 yo[32];   // y-halo runs: [16*(ly==7) + 2*lz + xh]
-    float4 zo[32];   // z-halo runs: [16*(lz==7) + 2*ly + xh]
-    int4 meta;       // tile id, tx, ty, tz
+    int4 meta;       // tile id, info byte
 };
 
 // Eq. 3-5 at one point, FP32.  Differences are unscaled (1/h is folded into
@@ -88,7 +104,7 @@ __device__ __forceinline__ float upd32(float c, float f, float dmx, float dpx, f
     q = fmaf(by, by, q);
     q = fmaf(az, az, q);
     q = fmaf(bz, bz, q);
-    const float g = q * rsqrtf(fmaxf(q, 1e-30f));
+    const float g = q * rsqrt_hw(fmaxf(q, 1e-30f));
     return fmaf(-(coef * f), g, c);
 }
 
@@ -134,7 +150,6 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     __shared__ unsigned smin[S32];
     const int tid = threadIdx.x;
     const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
-    const Inst in = a.in;
     const int n = *a.count;
     if (blockIdx.x == 0 && tid == 0 && a.updates)
         atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
@@ -142,26 +157,33 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     const float* __restrict__ src = (const float*)a.src;
     float* __restrict__ dst = (float*)a.dst;
     const float* __restrict__ Fp = (const float*)a.F;
-    const float Fc = (float)in.Fc;
-    const bool extrap = in.bc == 0;
-    const int sy = in.tnx * TILE_PTS;
-    const int sz = in.tnx * in.tny * TILE_PTS;
+    const int* __restrict__ list = a.list;
+    const uint8_t* __restrict__ linfo = a.info;
+    const float Fc = (float)a.in.Fc;
+    const double gamma = a.in.gamma;
+    const bool extrap = a.in.bc == 0;
+    const int sy = a.in.tnx * TILE_PTS;
+    const int sz = a.in.tnx * a.in.tny * TILE_PTS;
     const int stride = gridDim.x;
-    // per-thread halo sources (offsets from the tile start) and the info bit
-    // that says the neighbour exists; 0 = this thread has no halo on that axis
+    // per-thread halo sources (offsets from the tile start), the info bit that
+    // says the neighbour exists (0 = no halo on that axis) and the smem slots
     const int x_off = xh ? (TILE_PTS + lz * 64 + ly * 8) : (-TILE_PTS + lz * 64 + ly * 8 + 7);
     const unsigned x_bit = xh ? NB_XP : NB_XM;
     const int y_off = (ly == 0) ? (-sy + lz * 64 + 56 + 4 * xh) : (sy + lz * 64 + 4 * xh);
     const unsigned y_bit = (ly == 0) ? NB_YM : ((ly == 7) ? NB_YP : 0u);
-    const int y_slot = ((ly == 7) ? 16 : 0) + 2 * lz + xh;
+    const int y_slot = 128 + ((ly == 7) ? 16 : 0) + 2 * lz + xh;
     const int z_off = (lz == 0) ? (-sz + 448 + ly * 8 + 4 * xh) : (sz + ly * 8 + 4 * xh);
     const unsigned z_bit = (lz == 0) ? NB_ZM : ((lz == 7) ? NB_ZP : 0u);
-    const int z_slot = ((lz == 7) ? 16 : 0) + 2 * ly + xh;
+    const int z_slot = 160 + ((lz == 7) ? 16 : 0) + 2 * ly + xh;
+    // smem indices of the four y/z neighbour quads and of the partner value
+    const int i_ym = (ly > 0) ? tid - 2 : y_slot;
+    const int i_yp = (ly < 7) ? tid + 2 : y_slot;
+    const int i_zm = (lz > 0) ? tid - 16 : z_slot;
+    const int i_zp = (lz < 7) ? tid + 16 : z_slot;
+    const int i_pc = 4 * (tid ^ 1) + (xh ? 3 : 0);
 
-    // stage the data of list entry k into ring slot s
-    auto issue = [&](int k, int s) {
-        const unsigned t = (unsigned)__ldg(a.list + k);
-        const unsigned info = __ldg(a.info + k);
+    // stage list entry (t, info) into ring slot s
+    auto issue = [&](unsigned t, unsigned info, int s) {
         const unsigned base = t * TILE_PTS;
         const float* tp = src + base;
         Stage32& S = st[s];
@@ -169,18 +191,26 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
             S.meta = make_int4((int)t, (int)info, 0, 0);
             if (CLASSIFY) smin[s] = 0x7f800000u;
         }
-        cp_async16(&S.c[tid], tp + 4 * tid);
+        cp_async16(&S.v[tid], tp + 4 * tid);
         if (FIELD) cp_async16(&S.f[tid], Fp + base + 4 * tid);
-        if (info & x_bit) cp_async4(&S.xo[tid], tp + x_off);
-        if (info & y_bit) cp_async16(&S.yo[y_slot], tp + y_off);
-        if (info & z_bit) cp_async16(&S.zo[z_slot], tp + z_off);
+        const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0, pz = (info & z_bit) != 0;
+        cp_async4(&S.xo[tid], px ? tp + x_off : tp, px);
+        cp_async16(&S.v[y_slot], py ? tp + y_off : tp, py);
+        cp_async16(&S.v[z_slot], pz ? tp + z_off : tp, pz);
     };
 
+    int kn = blockIdx.x;  // next list entry to stage
 #pragma unroll
     for (int s = 0; s < S32 - 1; ++s) {
-        const int k = blockIdx.x + s * stride;
-        if (k < n) issue(k, s);
+        if (kn < n) issue((unsigned)__ldg(list + kn), __ldg(linfo + kn), s);
         cp_async_commit();
+        kn += stride;
+    }
+    // list entry after that, fetched one iteration ahead of its staging
+    unsigned t_next = 0, i_next = 0;
+    if (kn < n) {
+        t_next = (unsigned)__ldg(list + kn);
+        i_next = __ldg(linfo + kn);
     }
     int cur = 0;
     int prev = -1;
@@ -189,26 +219,30 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         cp_async_wait<S32 - 2>();
         __syncthreads();
         if (CLASSIFY && tid == 0 && prev >= 0)
-            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < in.gamma) ? 1 : 0;
+            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma) ? 1 : 0;
         {
-            const int kn = k + (S32 - 1) * stride;
             const int sn = (cur + S32 - 1) % S32;
-            if (kn < n) issue(kn, sn);
+            if (kn < n) issue(t_next, i_next, sn);
             cp_async_commit();
+            kn += stride;
+            if (kn < n) {
+                t_next = (unsigned)__ldg(list + kn);
+                i_next = __ldg(linfo + kn);
+            }
         }
         const Stage32& S = st[cur];
         const int t = S.meta.x;
         const unsigned info = (unsigned)S.meta.y;
-        const float4 c = S.c[tid];
+        const float4 c = S.v[tid];
         const float4 f = FIELD ? S.f[tid] : make_float4(Fc, Fc, Fc, Fc);
-        const float4 ym = (ly > 0) ? S.c[tid - 2] : S.yo[y_slot];
-        const float4 yp = (ly < 7) ? S.c[tid + 2] : S.yo[y_slot];
-        const float4 zm = (lz > 0) ? S.c[tid - 16] : S.zo[z_slot];
-        const float4 zp = (lz < 7) ? S.c[tid + 16] : S.zo[z_slot];
-        const float4 pc = S.c[tid ^ 1];
+        const float4 ym = S.v[i_ym];
+        const float4 yp = S.v[i_yp];
+        const float4 zm = S.v[i_zm];
+        const float4 zp = S.v[i_zp];
+        const float pcv = reinterpret_cast<const float*>(S.v)[i_pc];
         const float xo = S.xo[tid];
-        const float xm0 = xh ? pc.w : xo;
-        const float xp3 = xh ? xo : pc.x;
+        const float xm0 = xh ? pcv : xo;
+        const float xp3 = xh ? xo : pcv;
 
         float4 o;
         if (info == (NB_ALL | SG_POS)) {
@@ -241,7 +275,7 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     if (CLASSIFY) {
         __syncthreads();
         if (tid == 0 && prev >= 0)
-            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < in.gamma) ? 1 : 0;
+            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma) ? 1 : 0;
     }
     cp_async_wait<0>();
 }
