@@ -173,6 +173,45 @@ const char *ls_strerror(int status);
 /* Last CUDA error code seen by any call (0 = none), for diagnostics. */
 int ls_last_cuda_error(void);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free band tile list
+ * ------------------------------------------------------------------- */
+
+/* Largest tile count (nx/8 * ny/8 * nz/8) ls_band_tiles_noalloc accepts:
+ * 2^21 tiles, i.e. a 1024^3 grid. */
+#define LS_NOALLOC_MAX_TILES (1 << 21)
+
+/* The paper has no counterpart to this call.  It is for callers that cannot
+ * allocate device memory: code running while someone else captures a CUDA
+ * graph, allocation-free real-time sections, or hosts whose own memory pool
+ * owns the device.  It computes the same active-tile list as
+ * ls_band_rebuild + ls_get_active_tiles (tube test min |phi| < halfwidth*h
+ * per 8^3 tile in FP64, 26-neighbour dilation, ascending ids), straight from
+ * a caller-owned row-major phi, without a context and without any
+ * allocation: its scratch (about 4.2 MB of tile flags and block counts) is
+ * one fixed __device__ array that every device that loads the library holds
+ * until the process exits.
+ *   phi        device pointer, nx*ny*nz values of the precision's type,
+ *              row-major [z][y][x]; read only.
+ *   tiles_out  device pointer to tiles_cap ints (tiles_cap >= number of
+ *              tiles); receives the ascending active tile ids.
+ *   count_out  device pointer to one int; receives the active-tile count.
+ *   cuda_stream  stream the work is queued on (NULL = legacy default).
+ * The call is asynchronous: results are valid once the stream has reached
+ * the queued work.  The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * outside any stream capture.  All calls share the one scratch array: calls
+ * that overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  Every scratch byte a call reads it has
+ * written first, so nothing needs clearing between calls.
+ * Errors: LS_EINVAL (NULL pointer, sizes not multiples of 8 or < 8, h or
+ * halfwidth not positive, bad precision, more than LS_NOALLOC_MAX_TILES
+ * tiles, tiles_cap too small), LS_ECUDA (launch failure).  Never calls
+ * cudaMalloc, cudaFree or any allocating routine. */
+int ls_band_tiles_noalloc(const void *phi, int nx, int ny, int nz, double h, int precision,
+                          double halfwidth_in_h, int *tiles_out, long long tiles_cap,
+                          int *count_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

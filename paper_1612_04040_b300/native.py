@@ -53,6 +53,7 @@ SIGNATURES = {
     "ls_get_profile": (_i, [_vp, _vp]),
     "ls_reset_profile": (_i, [_vp]),
     "ls_get_status": (_i, [_vp]),
+    "ls_band_tiles_noalloc": (_i, [_vp, _i, _i, _i, _d, _i, _d, _vp, _ll, _vp, _vp]),
     "ls_strerror": (_c.c_char_p, [_i]),
     "ls_last_cuda_error": (_i, []),
 }
@@ -122,6 +123,29 @@ def array_ptr(a, dtype, count):
             raise ValueError("expected %d values, got %d" % (count, a.size))
         return ctypes.c_void_p(a.ctypes.data), 0
     raise TypeError("expected a torch tensor or numpy array")
+
+
+LS_NOALLOC_MAX_TILES = 1 << 21
+
+
+def band_tiles_noalloc(phi, h, halfwidth, tiles_out, count_out, stream=None):
+    """ls_band_tiles_noalloc: active-tile ids of a row-major device phi
+    (torch CUDA tensor of shape (nz, ny, nx)) into the caller's device
+    buffers tiles_out (int32, >= number of tiles) and count_out (int32, 1),
+    without any allocation by the library.  Asynchronous on `stream`."""
+    lib = load()
+    if phi.dim() != 3 or not phi.is_cuda or not phi.is_contiguous():
+        raise ValueError("phi must be a contiguous 3-D CUDA tensor")
+    prec = LS_FP32 if phi.dtype == torch.float32 else LS_FP64
+    nz, ny, nx = phi.shape
+    if tiles_out.dtype != torch.int32 or count_out.dtype != torch.int32:
+        raise TypeError("tiles_out and count_out must be int32")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib.ls_band_tiles_noalloc(ctypes.c_void_p(phi.data_ptr()), nx, ny, nz, float(h), prec,
+                                    float(halfwidth), ctypes.c_void_p(tiles_out.data_ptr()),
+                                    tiles_out.numel(), ctypes.c_void_p(count_out.data_ptr()),
+                                    ctypes.c_void_p(stream)), "ls_band_tiles_noalloc")
 
 
 class LevelSet:
