@@ -134,6 +134,16 @@ int ls_set_full_domain(ls_ctx *ctx, int on);
  * Synchronises the stream.  Errors: LS_EINVAL, LS_ESTATE (phi not set). */
 int ls_get_phi(ls_ctx *ctx, void *dst, int dst_on_device);
 
+/* Checkpoint: copy the current phi of every instance into a context-owned
+ * device buffer (allocated on the first call).  Errors: LS_ESTATE (phi not
+ * set), LS_ENOMEM. */
+int ls_snapshot(ls_ctx *ctx);
+
+/* Resume from the last ls_snapshot: phi is restored in both ping-pong
+ * buffers and the band becomes stale, exactly as after ls_set_phi with the
+ * saved values.  Errors: LS_ESTATE (no snapshot). */
+int ls_restore(ls_ctx *ctx);
+
 /* Copy the ascending active tile ids (tile id = (tz*(ny/8) + ty)*(nx/8) + tx)
  * to host array dst of capacity cap; *n receives the count (may exceed cap,
  * then only cap ids are written).  Synchronises the stream.
@@ -144,6 +154,27 @@ int ls_get_active_tiles(ls_ctx *ctx, int *dst, long long cap, long long *n);
 /* Total grid-point updates done by ls_step since creation (sum over steps of
  * 512 x active tiles).  Synchronises the stream. */
 int ls_get_updates(ls_ctx *ctx, unsigned long long *n);
+
+/* Record every later ls_step call as a CUDA graph (on = 1) and replay it
+ * when a call starts from the same schedule state with the same arguments;
+ * the graph is rebuilt after any change of phi, speed, band, face rule,
+ * stream or launch configuration.  Graphs are not used while profiling is
+ * enabled.  With the legacy default stream the context uses a private
+ * blocking stream for the replays. */
+int ls_set_graphs(ls_ctx *ctx, int on);
+
+/* Autotuner: time every launch configuration of the FP32 stencil (cp.async
+ * ring depth 2/3/4 x persistent grid 50/75/100 % of full occupancy) on the
+ * current active set, `reps` launches each, and keep the fastest for later
+ * steps.  The probes write only the buffer the next step overwrites, so
+ * the state is unchanged.  Outputs (nullable): the chosen stages and grid
+ * percentage.  Needs a valid band (LS_ESTATE otherwise).  FP64 contexts
+ * have a single configuration and return it. */
+int ls_autotune(ls_ctx *ctx, int reps, int *stages, int *grid_pct);
+
+/* Set the FP32 stencil launch configuration directly (stages 2..4, grid
+ * 1..100 % of full occupancy). */
+int ls_set_step_config(ls_ctx *ctx, int stages, int grid_pct);
 
 /* Profiling counters of a context. */
 typedef struct {
@@ -172,6 +203,43 @@ const char *ls_strerror(int status);
 
 /* Last CUDA error code seen by any call (0 = none), for diagnostics. */
 int ls_last_cuda_error(void);
+
+/* ---------------------------------------------------------------------
+ * Batched contexts: n independent grids advanced together
+ * ------------------------------------------------------------------- */
+
+/* Create one context for n independent grids (instance i: nx[i]*ny[i]*nz[i]
+ * points, spacing h[i]; same rules as ls_create per instance, 1 <= n <=
+ * 65535, total points <= 2^31, precision LS_FP32 only).  All instances share
+ * one set of buffers and one global active-tile queue: ls_band_rebuild,
+ * ls_step, ls_set_bc, ls_set_full_domain, ls_set_graphs, ls_autotune and the
+ * profiling calls act on every instance at once (one stencil launch per step
+ * for the whole batch); dt is per instance (CFL mode: CFL*h_i/M_i).  The
+ * speeds of all instances must be of one kind (all constant or all fields)
+ * when ls_step runs (LS_ESTATE otherwise).  ls_set_phi / ls_set_speed /
+ * ls_get_phi need n == 1; use the ls_inst_* calls.  ls_get_active_tiles
+ * returns global ids (instance i owns the ids after those of instances
+ * 0..i-1). */
+int ls_batch_create(int n, const int *nx, const int *ny, const int *nz, const double *h,
+                    int precision, ls_ctx **out);
+
+/* Number of instances of a context (1 for ls_create). */
+int ls_batch_size(ls_ctx *ctx, int *n);
+
+/* Per-instance versions of ls_set_phi, ls_set_speed, ls_set_speed_const and
+ * ls_get_phi (same layout, ownership and errors; i out of range ->
+ * LS_EINVAL). */
+int ls_inst_set_phi(ls_ctx *ctx, int i, const void *src, int src_on_device);
+int ls_inst_set_speed(ls_ctx *ctx, int i, const void *src, int src_on_device);
+int ls_inst_set_speed_const(ls_ctx *ctx, int i, double F);
+int ls_inst_get_phi(ls_ctx *ctx, int i, void *dst, int dst_on_device);
+
+/* Active tiles of instance i, as local tile ids (ascending); like
+ * ls_get_active_tiles. */
+int ls_inst_get_active_tiles(ls_ctx *ctx, int i, int *dst, long long cap, long long *n);
+
+/* dt of instance i's last step (synchronises the stream). */
+int ls_inst_last_dt(ls_ctx *ctx, int i, double *dt);
 
 /* ---------------------------------------------------------------------
  * Allocation-free band tile list

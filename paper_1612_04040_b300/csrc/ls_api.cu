@@ -8,17 +8,27 @@
 //      rebuild from the tube flags that the previous step computed on the
 //      tiles it updated (inactive tiles are frozen and were outside the tube
 //      at the last rebuild, so they cannot have entered it);
-//   2. rebuild = dilation (+ copy of tiles leaving the active set into the
-//      other ping-pong buffer) -> scan of block counts -> ascending scatter of
-//      active ids, folding max|F| of the active tiles -> dt in FP64;
+//   2. rebuild = dilation -> scan of block counts -> ascending scatter of
+//      active ids with their info bytes, folding max|F| of the active tiles
+//      and copying tiles that leave the active set into the other ping-pong
+//      buffer -> dt in FP64;
 //   3. one launch of the stencil over the active list, src -> dst, swap.
 // Nothing is read back to the host inside ls_step: counts, M and dt stay in
-// device memory and the persistent stencil grid reads the count there.
+// device memory and the persistent stencil grid reads the count there, so a
+// whole ls_step call can be captured once as a CUDA graph and replayed.
+//
+// A batched context holds n independent grids in one set of buffers: the
+// tiles of instance i occupy global tile ids [tile_base_i, tile_base_i +
+// ntiles_i); one rebuild and one stencil launch per step serve every
+// instance through a single global active-tile queue, with per-instance dt,
+// speed and band threshold.
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "ls.h"
@@ -28,23 +38,54 @@ using lsk::Inst;
 
 static thread_local int g_last_cuda_error = 0;
 
+namespace {
+
+// host state a captured ls_step graph starts from / leaves behind
+struct SchedState {
+    int cur = 0;
+    int since_rebuild = 0;
+    bool band_valid = false;
+    bool core_fresh = false;
+};
+
+using GraphKey = std::tuple<int, int, int, int, int, int, int, int, long long, int, int>;
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    SchedState after;
+    unsigned long long launches = 0;
+    unsigned long long stencil_launches = 0;
+};
+
+}  // namespace
+
 struct ls_ctx {
     int prec = 0;
     size_t esize = 4;
-    Inst in{};                    // single instance (n_inst == 1)
+    bool batched = false;
+    int n_inst = 1;
+    std::vector<Inst> insts;      // host copy of the per-instance parameters
+    std::vector<char> inst_phi_set;
+    Inst* d_inst = nullptr;       // device copy (batched contexts)
+    uint16_t* d_tile_inst = nullptr;  // instance of every global tile (batched)
+    uint16_t* d_list_inst = nullptr;  // instance of every list entry (batched)
+    int* d_inst_count = nullptr;      // per-instance active counts (batched)
     long long ntiles = 0;
     size_t npts = 0;
+    size_t max_inst_pts = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;  // used for graph capture when stream is NULL
     void* phi[2] = {nullptr, nullptr};
     int cur = 0;
     void* F = nullptr;            // bricked speed field (lazy)
     void* tile_maxF = nullptr;    // per-tile max |F| (lazy)
+    uint8_t* tile_sgn = nullptr;  // per-tile sign code of a speed field (lazy)
     void* staging = nullptr;      // row-major staging buffer (lazy)
+    void* snapshot = nullptr;     // ls_snapshot copy of phi (lazy)
     uint8_t* core = nullptr;
     uint8_t* act = nullptr;
     int* list = nullptr;
     uint8_t* list_info = nullptr;
-    uint8_t* tile_sgn = nullptr;  // per-tile sign code of a speed field (lazy)
     int* d_count = nullptr;
     int* block_counts = nullptr;
     int nblocks = 0;
@@ -54,7 +95,6 @@ struct ls_ctx {
     unsigned* d_status = nullptr;
     unsigned* d_nonfinite = nullptr;
     // host-side state
-    bool phi_set = false;
     bool band_valid = false;
     bool core_fresh = false;
     bool full_domain = false;
@@ -63,6 +103,10 @@ struct ls_ctx {
     int since_rebuild = 0;
     int dt_mode = LS_DT_FIXED;
     double dt_value = 0.0;
+    lsk::StepConfig cfg;
+    // graphs
+    bool use_graphs = false;
+    std::map<GraphKey, GraphEntry> graphs;
     // profiling
     unsigned long long launches = 0;
     unsigned long long stencil_launches = 0;
@@ -71,6 +115,10 @@ struct ls_ctx {
     unsigned long long stencil_timed = 0;
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+
+    Inst& in0() { return insts[0]; }
+    const Inst* dinst() const { return batched ? d_inst : nullptr; }
+    const uint16_t* tinst() const { return batched ? d_tile_inst : nullptr; }
 };
 
 namespace {
@@ -82,17 +130,23 @@ int cuda_fail(cudaError_t e)
     return LS_ECUDA;
 }
 
-#define CK(expr)                                    \
-    do {                                            \
-        cudaError_t e_ = (expr);                    \
+#define CK(expr)                                     \
+    do {                                             \
+        cudaError_t e_ = (expr);                     \
         if (e_ != cudaSuccess) return cuda_fail(e_); \
     } while (0)
 
 // a library kernel launch: counted, then checked
-#define KL(c, expr)          \
-    do {                     \
-        ++(c)->launches;     \
-        CK(expr);            \
+#define KL(c, expr)      \
+    do {                 \
+        ++(c)->launches; \
+        CK(expr);        \
+    } while (0)
+
+#define RET(expr)                \
+    do {                         \
+        int r_ = (expr);         \
+        if (r_ != LS_OK) return r_; \
     } while (0)
 
 cudaError_t take_event(ls_ctx* c, cudaEvent_t* e)
@@ -122,6 +176,22 @@ int drain_events(ls_ctx* c)
     return LS_OK;
 }
 
+void clear_graphs(ls_ctx* c)
+{
+    for (auto& kv : c->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+}
+
+// any change of state that kernels read by value (or that changes the launch
+// sequence) invalidates the cached graphs
+void state_changed(ls_ctx* c)
+{
+    c->band_valid = false;
+    c->core_fresh = false;
+    clear_graphs(c);
+}
+
 bool is_pow2(double h)
 {
     int e = 0;
@@ -136,93 +206,452 @@ cudaError_t dalloc(T** p, size_t bytes)
 
 void free_all(ls_ctx* c)
 {
+    clear_graphs(c);
     for (auto& p : c->ev_pending) {
         cudaEventDestroy(p.first);
         cudaEventDestroy(p.second);
     }
     for (auto e : c->ev_free) cudaEventDestroy(e);
-    void* ptrs[] = {c->phi[0], c->phi[1], c->F, c->tile_maxF, c->staging, c->core, c->act,
-                    c->list, c->list_info, c->tile_sgn, c->d_count, c->block_counts, c->d_sc, c->d_Mbits, c->d_updates,
-                    c->d_status, c->d_nonfinite};
+    void* ptrs[] = {c->phi[0], c->phi[1], c->F, c->tile_maxF, c->tile_sgn, c->staging, c->snapshot, c->core,
+                    c->act, c->list, c->list_info, c->d_count, c->block_counts, c->d_sc,
+                    c->d_Mbits, c->d_updates, c->d_status, c->d_nonfinite, c->d_inst,
+                    c->d_tile_inst, c->d_list_inst, c->d_inst_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
 }
 
 size_t grid_bytes(const ls_ctx* c) { return c->npts * c->esize; }
+size_t inst_bytes(const ls_ctx* c, const Inst& in) { return (size_t)in.ntiles * lsk::TILE_PTS * c->esize; }
+char* region(const ls_ctx* c, void* buf, const Inst& in)
+{
+    return (char*)buf + (size_t)in.tile_base * lsk::TILE_PTS * c->esize;
+}
 
 int ensure_staging(ls_ctx* c)
 {
-    if (!c->staging) CK(dalloc(&c->staging, grid_bytes(c)));
+    if (!c->staging) CK(dalloc(&c->staging, c->max_inst_pts * c->esize));
     return LS_OK;
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-// pack a row-major source (host or device) into the bricked buffer dst;
-// returns LS_ENONFINITE if any value is NaN/Inf (after a stream sync)
-int pack_from(ls_ctx* c, const void* src, int on_device, void* dst)
+int upload_insts(ls_ctx* c)
+{
+    if (c->batched)
+        CK(cudaMemcpyAsync(c->d_inst, c->insts.data(), sizeof(Inst) * c->n_inst,
+                           cudaMemcpyHostToDevice, c->stream));
+    return LS_OK;
+}
+
+// pack a row-major source (host or device) of instance `in` into the bricked
+// buffer dst (already offset to the instance); LS_ENONFINITE if any value is
+// NaN/Inf (after a stream sync)
+int pack_from(ls_ctx* c, const Inst& in, const void* src, int on_device, void* dst)
 {
     const void* dsrc = src;
     if (!on_device) {
-        int r = ensure_staging(c);
-        if (r) return r;
-        CK(cudaMemcpyAsync(c->staging, src, grid_bytes(c), cudaMemcpyHostToDevice, c->stream));
+        RET(ensure_staging(c));
+        CK(cudaMemcpyAsync(c->staging, src, inst_bytes(c, in), cudaMemcpyHostToDevice, c->stream));
         dsrc = c->staging;
     } else if (!aligned16(src)) {
         return LS_EINVAL;
     }
     CK(cudaMemsetAsync(c->d_nonfinite, 0, sizeof(unsigned), c->stream));
-    KL(c, lsk::launch_pack(dsrc, dst, c->in, c->prec, c->d_nonfinite, c->stream));
+    KL(c, lsk::launch_pack(dsrc, dst, in, c->prec, c->d_nonfinite, c->stream));
     unsigned bad = 0;
     CK(cudaMemcpyAsync(&bad, c->d_nonfinite, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return bad ? LS_ENONFINITE : LS_OK;
 }
 
-unsigned const_sign_bits(const ls_ctx* c)
+unsigned const_sign_bits(const ls_ctx* c) { return c->insts[0].Fc >= 0.0 ? lsk::SG_POS : lsk::SG_NEG; }
+
+int speed_mode(const ls_ctx* c)
 {
-    return c->in.Fc >= 0.0 ? lsk::SG_POS : lsk::SG_NEG;
+    // one mode for every instance (0 if unset or mixed)
+    const int m = c->insts[0].speed_mode;
+    for (const Inst& in : c->insts)
+        if (in.speed_mode != m) return 0;
+    return m;
 }
 
-const uint8_t* sign_table(const ls_ctx* c)
-{
-    return c->in.speed_mode == 2 ? c->tile_sgn : nullptr;
-}
+const uint8_t* sign_table(const ls_ctx* c) { return speed_mode(c) == 2 ? c->tile_sgn : nullptr; }
 
-int rebuild(ls_ctx* c, bool full_scan)
+int finish_rebuild(ls_ctx* c, cudaStream_t s)
 {
-    cudaStream_t s = c->stream;
     void* cur = c->phi[c->cur];
     void* other = c->phi[c->cur ^ 1];
-    if (full_scan || !c->core_fresh)
-        KL(c, lsk::launch_classify_all(cur, c->core, nullptr, nullptr, c->in, c->ntiles, c->prec, s));
-    KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, nullptr, nullptr, c->in, c->ntiles,
-                             s));
+    const void* tmf = speed_mode(c) == 2 ? c->tile_maxF : nullptr;
     KL(c, lsk::launch_scan(c->block_counts, c->nblocks, c->d_count, s));
-    const void* tmf = (c->in.speed_mode == 2) ? c->tile_maxF : nullptr;
-    KL(c, lsk::launch_scatter(c->act, c->block_counts, c->list, c->list_info, sign_table(c),
-                              const_sign_bits(c), c->in, c->ntiles, tmf, c->prec, c->d_Mbits, cur,
-                              other, s));
-    KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in, c->dt_mode, c->dt_value, 1, c->prec,
-                          c->d_Mbits, c->d_count, 0, s));
+    if (c->batched) {
+        KL(c, lsk::launch_scatter_batch(c->act, c->block_counts, c->list, c->list_info,
+                                        c->d_list_inst, sign_table(c), c->d_inst, c->d_tile_inst,
+                                        c->ntiles, tmf, c->prec, c->d_Mbits, c->d_inst_count, cur,
+                                        other, s));
+        KL(c, lsk::launch_set_dt_batch(c->d_sc, c->n_inst, c->d_inst, c->dt_mode, c->dt_value, 1,
+                                       c->prec, c->d_Mbits, c->d_inst_count, s));
+    } else {
+        KL(c, lsk::launch_scatter(c->act, c->block_counts, c->list, c->list_info, sign_table(c),
+                                  const_sign_bits(c), c->in0(), c->ntiles, tmf, c->prec,
+                                  c->d_Mbits, cur, other, s));
+        KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in0(), c->dt_mode, c->dt_value, 1,
+                                 c->prec, c->d_Mbits, c->d_count, 0, s));
+    }
+    return LS_OK;
+}
+
+int rebuild(ls_ctx* c, bool full_scan, cudaStream_t s)
+{
+    void* cur = c->phi[c->cur];
+    if (full_scan || !c->core_fresh)
+        KL(c, lsk::launch_classify_all(cur, c->core, c->dinst(), c->tinst(), c->in0(), c->ntiles,
+                                       c->prec, s));
+    KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, c->dinst(), c->tinst(), c->in0(),
+                             c->ntiles, s));
+    RET(finish_rebuild(c, s));
     c->band_valid = true;
     c->core_fresh = false;
     c->since_rebuild = 0;
     return LS_OK;
 }
 
-int full_domain_bound(ls_ctx* c)
+int full_domain_bound(ls_ctx* c, cudaStream_t s)
 {
-    // every tile counts as active, so a later switch back to a band copies
-    // every tile that leaves the active set into the other buffer
-    CK(cudaMemsetAsync(c->act, 1, c->ntiles, c->stream));
-    KL(c, lsk::launch_full_list(c->list, c->list_info, sign_table(c), const_sign_bits(c), c->in,
-                                c->ntiles, c->d_count, c->stream));
-    if (c->in.speed_mode == 2)
-        KL(c, lsk::launch_max_all(c->tile_maxF, c->ntiles, c->prec, c->d_Mbits, c->stream));
-    KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in, c->dt_mode, c->dt_value, 1, c->prec,
-                          c->d_Mbits, nullptr, c->ntiles, c->stream));
+    if (c->batched) {
+        // every tile in the tube: the dilation then marks every tile active
+        // and the regular scatter builds the full list, counts and bounds
+        CK(cudaMemsetAsync(c->core, 1, c->ntiles, s));
+        KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, c->d_inst, c->d_tile_inst,
+                                 c->in0(), c->ntiles, s));
+        RET(finish_rebuild(c, s));
+    } else {
+        // every tile counts as active, so a later switch back to a band copies
+        // every tile that leaves the active set into the other buffer
+        CK(cudaMemsetAsync(c->act, 1, c->ntiles, s));
+        KL(c, lsk::launch_full_list(c->list, c->list_info, sign_table(c), const_sign_bits(c),
+                                    c->in0(), c->ntiles, c->d_count, s));
+        if (speed_mode(c) == 2)
+            KL(c, lsk::launch_max_all(c->tile_maxF, c->ntiles, c->prec, c->d_Mbits, s));
+        KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in0(), c->dt_mode, c->dt_value, 1,
+                                 c->prec, c->d_Mbits, nullptr, c->ntiles, s));
+    }
     c->band_valid = true;
+    return LS_OK;
+}
+
+lsk::StepArgs step_args(ls_ctx* c, bool classify)
+{
+    lsk::StepArgs a{};
+    a.src = c->phi[c->cur];
+    a.dst = c->phi[c->cur ^ 1];
+    a.F = (speed_mode(c) == 2) ? c->F : nullptr;
+    a.list = c->list;
+    a.info = c->list_info;
+    a.list_inst = c->batched ? c->d_list_inst : nullptr;
+    a.count = c->d_count;
+    a.sc = c->d_sc;
+    a.insts = c->batched ? c->d_inst : nullptr;
+    a.core = classify ? c->core : nullptr;
+    a.updates = c->d_updates;
+    a.in = c->in0();
+    a.max_grid = c->full_domain ? (int)(c->ntiles < (1 << 30) ? c->ntiles : (1 << 30)) : 0;
+    return a;
+}
+
+// the step loop of ls_step (eager, or recorded into a graph by the caller)
+int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every, cudaStream_t s)
+{
+    bool dt_pending = true;
+    for (int k = 0; k < nsteps; ++k) {
+        bool rebuilt = false;
+        if (c->full_domain) {
+            if (!c->band_valid) {
+                RET(full_domain_bound(c, s));
+                rebuilt = true;
+            }
+        } else if (!c->band_valid) {
+            RET(rebuild(c, true, s));
+            rebuilt = true;
+        } else if (rebuild_every > 0 && c->since_rebuild >= rebuild_every) {
+            RET(rebuild(c, false, s));
+            rebuilt = true;
+        }
+        if (dt_pending && !rebuilt) {
+            if (c->batched)
+                KL(c, lsk::launch_set_dt_batch(c->d_sc, c->n_inst, c->d_inst, dt_mode, value, 0,
+                                               c->prec, c->d_Mbits, c->d_inst_count, s));
+            else
+                KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in0(), dt_mode, value, 0, c->prec,
+                                         c->d_Mbits, nullptr, 0, s));
+        }
+        dt_pending = false;
+        const bool classify = !c->full_domain && rebuild_every > 0 &&
+                              c->since_rebuild + 1 >= rebuild_every;
+        const lsk::StepArgs a = step_args(c, classify);
+        if (c->profiling && c->ev_pending.size() >= 4096) RET(drain_events(c));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->profiling) {
+            CK(take_event(c, &e0));
+            CK(take_event(c, &e1));
+            CK(cudaEventRecord(e0, s));
+        }
+        KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
+        ++c->stencil_launches;
+        if (c->profiling) {
+            CK(cudaEventRecord(e1, s));
+            c->ev_pending.emplace_back(e0, e1);
+        }
+        c->cur ^= 1;
+        c->since_rebuild += 1;
+        c->core_fresh = classify;
+    }
+    return LS_OK;
+}
+
+SchedState save_state(const ls_ctx* c)
+{
+    SchedState st;
+    st.cur = c->cur;
+    st.since_rebuild = c->since_rebuild;
+    st.band_valid = c->band_valid;
+    st.core_fresh = c->core_fresh;
+    return st;
+}
+
+void load_state(ls_ctx* c, const SchedState& st)
+{
+    c->cur = st.cur;
+    c->since_rebuild = st.since_rebuild;
+    c->band_valid = st.band_valid;
+    c->core_fresh = st.core_fresh;
+}
+
+cudaStream_t work_stream(ls_ctx* c)
+{
+    if (c->stream) return c->stream;
+    if (!c->own_stream) {
+        if (cudaStreamCreate(&c->own_stream) != cudaSuccess) return nullptr;
+    }
+    return c->own_stream;
+}
+
+// ls_step through a cached CUDA graph: the first call with a given starting
+// state records the launches, later calls replay them
+int run_steps_graph(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every)
+{
+    cudaStream_t s = work_stream(c);
+    if (!s) return cuda_fail(cudaErrorInvalidResourceHandle);
+    long long vbits = 0;
+    std::memcpy(&vbits, &value, sizeof(vbits));
+    const GraphKey key{c->cur, c->since_rebuild, (int)c->band_valid, (int)c->core_fresh,
+                       (int)c->full_domain, nsteps, rebuild_every, dt_mode, vbits, c->cfg.stages,
+                       c->cfg.grid_pct};
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        if (c->graphs.size() >= 16) clear_graphs(c);
+        const SchedState before = save_state(c);
+        const unsigned long long l0 = c->launches, s0 = c->stencil_launches;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int r = run_steps(c, nsteps, value, dt_mode, rebuild_every, s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (r != LS_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            load_state(c, before);
+            return r != LS_OK ? r : cuda_fail(e);
+        }
+        GraphEntry ent;
+        e = cudaGraphInstantiate(&ent.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            load_state(c, before);
+            return cuda_fail(e);
+        }
+        ent.after = save_state(c);
+        ent.launches = c->launches - l0;
+        ent.stencil_launches = c->stencil_launches - s0;
+        c->launches = l0;
+        c->stencil_launches = s0;
+        it = c->graphs.emplace(key, ent).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, s));
+    load_state(c, it->second.after);
+    c->launches += it->second.launches;
+    c->stencil_launches += it->second.stencil_launches;
+    return LS_OK;
+}
+
+int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h, int precision,
+             bool batched, ls_ctx** out)
+{
+    if (!out) return LS_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > 65535 || !nx || !ny || !nz || !h) return LS_EINVAL;
+    if (precision != LS_FP32 && precision != LS_FP64) return LS_EINVAL;
+    if (batched && precision != LS_FP32) return LS_EINVAL;
+    long long total_tiles = 0, total_pts = 0, max_pts = 0;
+    for (int i = 0; i < n; ++i) {
+        if (nx[i] < 8 || ny[i] < 8 || nz[i] < 8 || nx[i] % 8 || ny[i] % 8 || nz[i] % 8) return LS_EINVAL;
+        if (!(h[i] > 0.0) || !std::isfinite(h[i])) return LS_EINVAL;
+        const long long pts = (long long)nx[i] * ny[i] * nz[i];
+        total_pts += pts;
+        total_tiles += pts / lsk::TILE_PTS;
+        if (pts > max_pts) max_pts = pts;
+    }
+    if (total_pts > (1ll << 31)) return LS_EINVAL;
+    ls_ctx* c = new (std::nothrow) ls_ctx();
+    if (!c) return LS_ENOMEM;
+    c->prec = precision;
+    c->esize = precision == LS_FP32 ? 4 : 8;
+    c->batched = batched;
+    c->n_inst = n;
+    c->insts.resize(n);
+    c->inst_phi_set.assign(n, 0);
+    long long base = 0;
+    for (int i = 0; i < n; ++i) {
+        Inst& in = c->insts[i];
+        std::memset(&in, 0, sizeof(in));
+        in.nx = nx[i]; in.ny = ny[i]; in.nz = nz[i];
+        in.tnx = nx[i] / 8; in.tny = ny[i] / 8; in.tnz = nz[i] / 8;
+        in.tile_base = base;
+        in.ntiles = (long long)in.tnx * in.tny * in.tnz;
+        in.h = h[i];
+        in.inv_h = 1.0 / h[i];
+        in.pow2h = is_pow2(h[i]) ? 1 : 0;
+        in.bc = LS_BC_EXTRAPOLATE;
+        base += in.ntiles;
+    }
+    c->ntiles = total_tiles;
+    c->npts = (size_t)total_pts;
+    c->max_inst_pts = (size_t)max_pts;
+    c->nblocks = (int)((c->ntiles + 255) / 256);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess && r != cudaSuccess) e = r; };
+    A(dalloc(&c->phi[0], grid_bytes(c)));
+    A(dalloc(&c->phi[1], grid_bytes(c)));
+    A(dalloc(&c->core, c->ntiles));
+    A(dalloc(&c->act, c->ntiles));
+    A(dalloc(&c->list, c->ntiles * sizeof(int)));
+    A(dalloc(&c->list_info, c->ntiles));
+    A(dalloc(&c->d_count, sizeof(int)));
+    A(dalloc(&c->block_counts, c->nblocks * sizeof(int)));
+    A(dalloc(&c->d_sc, sizeof(lsk::StepScalars) * n));
+    A(dalloc(&c->d_Mbits, sizeof(unsigned long long) * n));
+    A(dalloc(&c->d_updates, sizeof(unsigned long long)));
+    A(dalloc(&c->d_status, sizeof(unsigned)));
+    A(dalloc(&c->d_nonfinite, sizeof(unsigned)));
+    if (batched) {
+        A(dalloc(&c->d_inst, sizeof(Inst) * n));
+        A(dalloc(&c->d_tile_inst, sizeof(uint16_t) * c->ntiles));
+        A(dalloc(&c->d_list_inst, sizeof(uint16_t) * c->ntiles));
+        A(dalloc(&c->d_inst_count, sizeof(int) * n));
+    }
+    if (e == cudaSuccess) {
+        A(cudaMemset(c->core, 0, c->ntiles));
+        A(cudaMemset(c->act, 0, c->ntiles));
+        A(cudaMemset(c->d_count, 0, sizeof(int)));
+        A(cudaMemset(c->d_sc, 0, sizeof(lsk::StepScalars) * n));
+        A(cudaMemset(c->d_Mbits, 0, sizeof(unsigned long long) * n));
+        A(cudaMemset(c->d_updates, 0, sizeof(unsigned long long)));
+        A(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+        if (batched) {
+            std::vector<uint16_t> ti((size_t)c->ntiles);
+            for (int i = 0; i < n; ++i)
+                for (long long t = 0; t < c->insts[i].ntiles; ++t)
+                    ti[(size_t)(c->insts[i].tile_base + t)] = (uint16_t)i;
+            A(cudaMemcpy(c->d_tile_inst, ti.data(), ti.size() * sizeof(uint16_t),
+                         cudaMemcpyHostToDevice));
+            A(cudaMemcpy(c->d_inst, c->insts.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice));
+            A(cudaMemset(c->d_inst_count, 0, sizeof(int) * n));
+        }
+        A(cudaDeviceSynchronize());
+    }
+    if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return cuda_fail(e);
+    }
+    *out = c;
+    return LS_OK;
+}
+
+bool all_phi_set(const ls_ctx* c)
+{
+    for (char f : c->inst_phi_set)
+        if (!f) return false;
+    return true;
+}
+
+int set_phi_inst(ls_ctx* c, int i, const void* src, int on_device)
+{
+    if (!c || !src || i < 0 || i >= c->n_inst) return LS_EINVAL;
+    state_changed(c);
+    const Inst& in = c->insts[i];
+    c->inst_phi_set[i] = 0;
+    RET(pack_from(c, in, src, on_device, region(c, c->phi[c->cur], in)));
+    CK(cudaMemcpyAsync(region(c, c->phi[c->cur ^ 1], in), region(c, c->phi[c->cur], in),
+                       inst_bytes(c, in), cudaMemcpyDeviceToDevice, c->stream));
+    c->inst_phi_set[i] = 1;
+    return LS_OK;
+}
+
+int set_speed_inst(ls_ctx* c, int i, const void* src, int on_device)
+{
+    if (!c || !src || i < 0 || i >= c->n_inst) return LS_EINVAL;
+    if (!c->F) CK(dalloc(&c->F, grid_bytes(c)));
+    if (!c->tile_maxF) CK(dalloc(&c->tile_maxF, c->ntiles * c->esize));
+    if (!c->tile_sgn) CK(dalloc(&c->tile_sgn, c->ntiles));
+    state_changed(c);
+    Inst& in = c->insts[i];
+    in.speed_mode = 0;
+    RET(pack_from(c, in, src, on_device, region(c, c->F, in)));
+    KL(c, lsk::launch_tile_speed(region(c, c->F, in),
+                                 (char*)c->tile_maxF + (size_t)in.tile_base * c->esize,
+                                 c->tile_sgn + in.tile_base, in.ntiles, c->prec, c->stream));
+    in.speed_mode = 2;
+    return upload_insts(c);
+}
+
+int set_speed_const_inst(ls_ctx* c, int i, double F)
+{
+    if (!c || i < 0 || i >= c->n_inst) return LS_EINVAL;
+    if (!std::isfinite(F)) return LS_ENONFINITE;
+    state_changed(c);
+    c->insts[i].Fc = F;
+    c->insts[i].speed_mode = 1;
+    return upload_insts(c);
+}
+
+int get_phi_inst(ls_ctx* c, int i, void* dst, int on_device)
+{
+    if (!c || !dst || i < 0 || i >= c->n_inst) return LS_EINVAL;
+    if (!c->inst_phi_set[i]) return LS_ESTATE;
+    const Inst& in = c->insts[i];
+    const void* srcb = region(c, c->phi[c->cur], in);
+    if (on_device) {
+        if (!aligned16(dst)) return LS_EINVAL;
+        KL(c, lsk::launch_unpack(srcb, dst, in, c->prec, c->stream));
+    } else {
+        RET(ensure_staging(c));
+        KL(c, lsk::launch_unpack(srcb, c->staging, in, c->prec, c->stream));
+        CK(cudaMemcpyAsync(dst, c->staging, inst_bytes(c, in), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LS_OK;
+}
+
+// copy the (global) active list to the host
+int fetch_list(ls_ctx* c, std::vector<int>& ids)
+{
+    int cnt = 0;
+    CK(cudaMemcpyAsync(&cnt, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    ids.resize((size_t)cnt);
+    if (cnt > 0) {
+        CK(cudaMemcpyAsync(ids.data(), c->list, sizeof(int) * cnt, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     return LS_OK;
 }
 
@@ -248,63 +677,19 @@ int ls_last_cuda_error(void) { return g_last_cuda_error; }
 
 int ls_create(int nx, int ny, int nz, double h, int precision, ls_ctx** out)
 {
-    if (!out) return LS_EINVAL;
-    *out = nullptr;
-    if (nx < 8 || ny < 8 || nz < 8 || nx % 8 || ny % 8 || nz % 8) return LS_EINVAL;
-    if ((long long)nx * ny * nz > (1ll << 31)) return LS_EINVAL;
-    if (!(h > 0.0) || !std::isfinite(h)) return LS_EINVAL;
-    if (precision != LS_FP32 && precision != LS_FP64) return LS_EINVAL;
-    ls_ctx* c = new (std::nothrow) ls_ctx();
-    if (!c) return LS_ENOMEM;
-    c->prec = precision;
-    c->esize = precision == LS_FP32 ? 4 : 8;
-    Inst& in = c->in;
-    in.nx = nx; in.ny = ny; in.nz = nz;
-    in.tnx = nx / 8; in.tny = ny / 8; in.tnz = nz / 8;
-    in.tile_base = 0;
-    in.ntiles = (long long)in.tnx * in.tny * in.tnz;
-    in.h = h;
-    in.inv_h = 1.0 / h;
-    in.gamma = 0.0;
-    in.Fc = 0.0;
-    in.speed_mode = 0;
-    in.pow2h = is_pow2(h) ? 1 : 0;
-    in.bc = LS_BC_EXTRAPOLATE;
-    c->ntiles = in.ntiles;
-    c->npts = (size_t)nx * ny * nz;
-    c->nblocks = (int)((c->ntiles + 255) / 256);
-    if (c->nblocks > 1024 * 32) { delete c; return LS_EINVAL; }
-    cudaError_t e = cudaSuccess;
-    auto A = [&](cudaError_t r) { if (e == cudaSuccess && r != cudaSuccess) e = r; };
-    A(dalloc(&c->phi[0], grid_bytes(c)));
-    A(dalloc(&c->phi[1], grid_bytes(c)));
-    A(dalloc(&c->core, c->ntiles));
-    A(dalloc(&c->act, c->ntiles));
-    A(dalloc(&c->list, c->ntiles * sizeof(int)));
-    A(dalloc(&c->list_info, c->ntiles));
-    A(dalloc(&c->d_count, sizeof(int)));
-    A(dalloc(&c->block_counts, c->nblocks * sizeof(int)));
-    A(dalloc(&c->d_sc, sizeof(lsk::StepScalars)));
-    A(dalloc(&c->d_Mbits, sizeof(unsigned long long)));
-    A(dalloc(&c->d_updates, sizeof(unsigned long long)));
-    A(dalloc(&c->d_status, sizeof(unsigned)));
-    A(dalloc(&c->d_nonfinite, sizeof(unsigned)));
-    if (e == cudaSuccess) {
-        A(cudaMemset(c->core, 0, c->ntiles));
-        A(cudaMemset(c->act, 0, c->ntiles));
-        A(cudaMemset(c->d_count, 0, sizeof(int)));
-        A(cudaMemset(c->d_sc, 0, sizeof(lsk::StepScalars)));
-        A(cudaMemset(c->d_Mbits, 0, sizeof(unsigned long long)));
-        A(cudaMemset(c->d_updates, 0, sizeof(unsigned long long)));
-        A(cudaMemset(c->d_status, 0, sizeof(unsigned)));
-        A(cudaDeviceSynchronize());
-    }
-    if (e != cudaSuccess) {
-        free_all(c);
-        delete c;
-        return cuda_fail(e);
-    }
-    *out = c;
+    return make_ctx(1, &nx, &ny, &nz, &h, precision, false, out);
+}
+
+int ls_batch_create(int n, const int* nx, const int* ny, const int* nz, const double* h,
+                    int precision, ls_ctx** out)
+{
+    return make_ctx(n, nx, ny, nz, h, precision, true, out);
+}
+
+int ls_batch_size(ls_ctx* c, int* n)
+{
+    if (!c || !n) return LS_EINVAL;
+    *n = c->n_inst;
     return LS_OK;
 }
 
@@ -322,61 +707,62 @@ int ls_set_stream(ls_ctx* c, void* stream)
 {
     if (!c) return LS_EINVAL;
     c->stream = (cudaStream_t)stream;
+    clear_graphs(c);
     return LS_OK;
 }
 
 int ls_set_bc(ls_ctx* c, int bc)
 {
     if (!c || (bc != LS_BC_EXTRAPOLATE && bc != LS_BC_NEUMANN)) return LS_EINVAL;
-    c->in.bc = bc;
-    return LS_OK;
+    for (Inst& in : c->insts) in.bc = bc;
+    clear_graphs(c);
+    return upload_insts(c);
 }
 
 int ls_set_phi(ls_ctx* c, const void* src, int on_device)
 {
-    if (!c || !src) return LS_EINVAL;
-    c->band_valid = false;
-    c->core_fresh = false;
-    int r = pack_from(c, src, on_device, c->phi[0]);
-    if (r) { c->phi_set = false; return r; }
-    CK(cudaMemcpyAsync(c->phi[1], c->phi[0], grid_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
-    c->cur = 0;
-    c->phi_set = true;
-    return LS_OK;
+    if (!c || c->n_inst != 1) return LS_EINVAL;
+    return set_phi_inst(c, 0, src, on_device);
+}
+
+int ls_inst_set_phi(ls_ctx* c, int i, const void* src, int on_device)
+{
+    return set_phi_inst(c, i, src, on_device);
 }
 
 int ls_set_speed(ls_ctx* c, const void* src, int on_device)
 {
-    if (!c || !src) return LS_EINVAL;
-    if (!c->F) CK(dalloc(&c->F, grid_bytes(c)));
-    if (!c->tile_maxF) CK(dalloc(&c->tile_maxF, c->ntiles * c->esize));
-    if (!c->tile_sgn) CK(dalloc(&c->tile_sgn, c->ntiles));
-    c->band_valid = false;
-    c->core_fresh = false;
-    int r = pack_from(c, src, on_device, c->F);
-    if (r) { c->in.speed_mode = 0; return r; }
-    KL(c, lsk::launch_tile_speed(c->F, c->tile_maxF, c->tile_sgn, c->ntiles, c->prec, c->stream));
-    c->in.speed_mode = 2;
-    return LS_OK;
+    if (!c || c->n_inst != 1) return LS_EINVAL;
+    return set_speed_inst(c, 0, src, on_device);
+}
+
+int ls_inst_set_speed(ls_ctx* c, int i, const void* src, int on_device)
+{
+    return set_speed_inst(c, i, src, on_device);
 }
 
 int ls_set_speed_const(ls_ctx* c, double F)
 {
     if (!c) return LS_EINVAL;
-    if (!std::isfinite(F)) return LS_ENONFINITE;
-    c->in.Fc = F;
-    c->in.speed_mode = 1;
-    c->band_valid = false;
-    c->core_fresh = false;
+    for (int i = 0; i < c->n_inst; ++i) RET(set_speed_const_inst(c, i, F));
     return LS_OK;
 }
+
+int ls_inst_set_speed_const(ls_ctx* c, int i, double F) { return set_speed_const_inst(c, i, F); }
 
 int ls_set_full_domain(ls_ctx* c, int on)
 {
     if (!c) return LS_EINVAL;
     c->full_domain = on != 0;
-    c->band_valid = false;
-    c->core_fresh = false;
+    state_changed(c);
+    return LS_OK;
+}
+
+int ls_set_graphs(ls_ctx* c, int on)
+{
+    if (!c) return LS_EINVAL;
+    c->use_graphs = on != 0;
+    if (!c->use_graphs) clear_graphs(c);
     return LS_OK;
 }
 
@@ -384,12 +770,13 @@ int ls_band_rebuild(ls_ctx* c, double halfwidth, long long* n_active)
 {
     if (!c) return LS_EINVAL;
     if (!(halfwidth > 0.0) || !std::isfinite(halfwidth)) return LS_EINVAL;
-    if (!c->phi_set) return LS_ESTATE;
+    if (!all_phi_set(c)) return LS_ESTATE;
     c->halfwidth = halfwidth;
     c->have_halfwidth = true;
-    c->in.gamma = halfwidth * c->in.h;
-    int r = rebuild(c, true);
-    if (r) return r;
+    for (Inst& in : c->insts) in.gamma = halfwidth * in.h;
+    clear_graphs(c);
+    RET(upload_insts(c));
+    RET(rebuild(c, true, c->stream));
     if (n_active) {
         int n = 0;
         CK(cudaMemcpyAsync(&n, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -405,113 +792,144 @@ int ls_step(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every,
     if (nsteps < 0 || rebuild_every < 0) return LS_EINVAL;
     if (dt_mode != LS_DT_FIXED && dt_mode != LS_DT_CFL) return LS_EINVAL;
     if (!(value > 0.0) || !std::isfinite(value)) return LS_EINVAL;
-    if (!c->phi_set || c->in.speed_mode == 0) return LS_ESTATE;
+    if (!all_phi_set(c) || speed_mode(c) == 0) return LS_ESTATE;
     if (!c->full_domain && !c->have_halfwidth) return LS_ESTATE;
-    cudaStream_t s = c->stream;
     c->dt_mode = dt_mode;
     c->dt_value = value;
-    bool dt_pending = true;
-    for (int k = 0; k < nsteps; ++k) {
-        bool rebuilt = false;
-        if (c->full_domain) {
-            if (!c->band_valid) {
-                int r = full_domain_bound(c);
-                if (r) return r;
-                rebuilt = true;
-            }
-        } else if (!c->band_valid) {
-            int r = rebuild(c, true);
-            if (r) return r;
-            rebuilt = true;
-        } else if (rebuild_every > 0 && c->since_rebuild >= rebuild_every) {
-            int r = rebuild(c, false);
-            if (r) return r;
-            rebuilt = true;
-        }
-        if (dt_pending && !rebuilt)
-            KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in, dt_mode, value, 0, c->prec,
-                                  c->d_Mbits, nullptr, 0, s));
-        dt_pending = false;
-        const bool classify = !c->full_domain && rebuild_every > 0 &&
-                              c->since_rebuild + 1 >= rebuild_every;
-        lsk::StepArgs a{};
-        a.src = c->phi[c->cur];
-        a.dst = c->phi[c->cur ^ 1];
-        a.F = (c->in.speed_mode == 2) ? c->F : nullptr;
-        a.list = c->list;
-        a.info = c->list_info;
-        a.count = c->d_count;
-        a.sc = c->d_sc;
-        a.core = classify ? c->core : nullptr;
-        a.updates = c->d_updates;
-        a.in = c->in;
-        int grid = lsk::step_grid_size(c->prec, classify);
-        if (c->full_domain && grid > c->ntiles) grid = (int)c->ntiles;
-        if (c->profiling && c->ev_pending.size() >= 4096) {
-            int r = drain_events(c);
-            if (r) return r;
-        }
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (c->profiling) {
-            CK(take_event(c, &e0));
-            CK(take_event(c, &e1));
-            CK(cudaEventRecord(e0, s));
-        }
-        KL(c, lsk::launch_step(a, c->prec, grid, s));
-        ++c->stencil_launches;
-        if (c->profiling) {
-            CK(cudaEventRecord(e1, s));
-            c->ev_pending.emplace_back(e0, e1);
-        }
-        c->cur ^= 1;
-        c->since_rebuild += 1;
-        c->core_fresh = classify;
+    if (nsteps > 0) {
+        if (c->use_graphs && !c->profiling) RET(run_steps_graph(c, nsteps, value, dt_mode, rebuild_every));
+        else RET(run_steps(c, nsteps, value, dt_mode, rebuild_every, c->stream));
     }
     if (last_dt) {
         lsk::StepScalars sc;
-        CK(cudaMemcpyAsync(&sc, c->d_sc, sizeof(sc), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        CK(cudaMemcpyAsync(&sc, c->d_sc, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
         *last_dt = sc.dt;
     }
     return LS_OK;
 }
 
+int ls_inst_last_dt(ls_ctx* c, int i, double* dt)
+{
+    if (!c || !dt || i < 0 || i >= c->n_inst) return LS_EINVAL;
+    lsk::StepScalars sc;
+    CK(cudaMemcpyAsync(&sc, c->d_sc + i, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *dt = sc.dt;
+    return LS_OK;
+}
+
+int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out)
+{
+    if (!c || reps < 1) return LS_EINVAL;
+    if (!c->band_valid) return LS_ESTATE;
+    cudaStream_t s = c->stream;
+    if (c->prec == LS_FP32) {
+        const int stages[] = {2, 3, 4};
+        const int pcts[] = {50, 75, 100};
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        lsk::StepConfig best_cfg = c->cfg;
+        lsk::StepArgs a = step_args(c, false);
+        a.updates = nullptr;  // probes write the other buffer only; the state is unchanged
+        for (int st : stages) {
+            for (int pct : pcts) {
+                lsk::StepConfig cfg;
+                cfg.stages = st;
+                cfg.grid_pct = pct;
+                KL(c, lsk::launch_step(a, c->prec, cfg, s));
+                CK(cudaEventRecord(e0, s));
+                for (int r = 0; r < reps; ++r) KL(c, lsk::launch_step(a, c->prec, cfg, s));
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    best_cfg = cfg;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->cfg = best_cfg;
+        clear_graphs(c);
+    }
+    if (stages_out) *stages_out = c->cfg.stages;
+    if (grid_pct_out) *grid_pct_out = c->cfg.grid_pct;
+    return LS_OK;
+}
+
+int ls_set_step_config(ls_ctx* c, int stages, int grid_pct)
+{
+    if (!c || (stages != 2 && stages != 3 && stages != 4) || grid_pct < 1 || grid_pct > 100)
+        return LS_EINVAL;
+    c->cfg.stages = stages;
+    c->cfg.grid_pct = grid_pct;
+    clear_graphs(c);
+    return LS_OK;
+}
+
+int ls_snapshot(ls_ctx* c)
+{
+    if (!c) return LS_EINVAL;
+    if (!all_phi_set(c)) return LS_ESTATE;
+    if (!c->snapshot) CK(dalloc(&c->snapshot, grid_bytes(c)));
+    CK(cudaMemcpyAsync(c->snapshot, c->phi[c->cur], grid_bytes(c), cudaMemcpyDeviceToDevice,
+                       c->stream));
+    return LS_OK;
+}
+
+int ls_restore(ls_ctx* c)
+{
+    if (!c) return LS_EINVAL;
+    if (!c->snapshot) return LS_ESTATE;
+    state_changed(c);
+    CK(cudaMemcpyAsync(c->phi[0], c->snapshot, grid_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->phi[1], c->snapshot, grid_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    c->cur = 0;
+    return LS_OK;
+}
+
 int ls_get_phi(ls_ctx* c, void* dst, int on_device)
 {
-    if (!c || !dst) return LS_EINVAL;
-    if (!c->phi_set) return LS_ESTATE;
-    if (on_device) {
-        if (!aligned16(dst)) return LS_EINVAL;
-        KL(c, lsk::launch_unpack(c->phi[c->cur], dst, c->in, c->prec, c->stream));
-    } else {
-        int r = ensure_staging(c);
-        if (r) return r;
-        KL(c, lsk::launch_unpack(c->phi[c->cur], c->staging, c->in, c->prec, c->stream));
-        CK(cudaMemcpyAsync(dst, c->staging, grid_bytes(c), cudaMemcpyDeviceToHost, c->stream));
-    }
-    CK(cudaStreamSynchronize(c->stream));
-    return LS_OK;
+    if (!c || c->n_inst != 1) return LS_EINVAL;
+    return get_phi_inst(c, 0, dst, on_device);
+}
+
+int ls_inst_get_phi(ls_ctx* c, int i, void* dst, int on_device)
+{
+    return get_phi_inst(c, i, dst, on_device);
 }
 
 int ls_get_active_tiles(ls_ctx* c, int* dst, long long cap, long long* n)
 {
     if (!c || !n || cap < 0 || (cap > 0 && !dst)) return LS_EINVAL;
-    if (!c->band_valid && !c->full_domain) return LS_ESTATE;
-    if (c->full_domain) {
-        *n = c->ntiles;
-        long long k = cap < c->ntiles ? cap : c->ntiles;
-        for (long long i = 0; i < k; ++i) dst[i] = (int)i;
-        return LS_OK;
+    if (!c->band_valid) return LS_ESTATE;
+    std::vector<int> ids;
+    RET(fetch_list(c, ids));
+    *n = (long long)ids.size();
+    const long long k = cap < *n ? cap : *n;
+    if (k > 0) std::memcpy(dst, ids.data(), sizeof(int) * k);
+    return LS_OK;
+}
+
+int ls_inst_get_active_tiles(ls_ctx* c, int i, int* dst, long long cap, long long* n)
+{
+    if (!c || !n || cap < 0 || (cap > 0 && !dst) || i < 0 || i >= c->n_inst) return LS_EINVAL;
+    if (!c->band_valid) return LS_ESTATE;
+    std::vector<int> ids;
+    RET(fetch_list(c, ids));
+    const Inst& in = c->insts[i];
+    long long k = 0;
+    for (int t : ids) {
+        if (t < in.tile_base || t >= in.tile_base + in.ntiles) continue;
+        if (k < cap) dst[k] = (int)(t - in.tile_base);
+        ++k;
     }
-    int cnt = 0;
-    CK(cudaMemcpyAsync(&cnt, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    *n = cnt;
-    long long k = cap < cnt ? cap : cnt;
-    if (k > 0) {
-        CK(cudaMemcpyAsync(dst, c->list, k * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-    }
+    *n = k;
     return LS_OK;
 }
 
@@ -533,8 +951,7 @@ int ls_profile_enable(ls_ctx* c, int on)
 int ls_get_profile(ls_ctx* c, ls_profile* out)
 {
     if (!c || !out) return LS_EINVAL;
-    int r = drain_events(c);
-    if (r) return r;
+    RET(drain_events(c));
     out->kernel_launches = c->launches;
     out->stencil_launches = c->stencil_launches;
     out->stencil_ms = c->stencil_ms;
@@ -545,8 +962,7 @@ int ls_get_profile(ls_ctx* c, ls_profile* out)
 int ls_reset_profile(ls_ctx* c)
 {
     if (!c) return LS_EINVAL;
-    int r = drain_events(c);
-    if (r) return r;
+    RET(drain_events(c));
     c->launches = 0;
     c->stencil_launches = 0;
     c->stencil_ms = 0.0;

@@ -344,6 +344,101 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
     }
 }
 
+// scatter for a batch of instances (FP32): as k_scatter, plus the instance
+// id of every entry, per-instance active counts and per-instance max |F|.
+// Lanes of a warp usually share an instance; each group of equal instance
+// ids folds its count / max with one atomic.
+__global__ void __launch_bounds__(256) k_scatter_batch(
+    const uint8_t* __restrict__ act, const int* __restrict__ offsets, int* list,
+    uint8_t* list_info, uint16_t* list_inst, const uint8_t* __restrict__ tile_sgn,
+    const Inst* __restrict__ d_inst, const uint16_t* __restrict__ tile_inst, long long ntiles,
+    const float* __restrict__ tile_maxF, unsigned long long* Mbits, int* inst_count,
+    const uint4* __restrict__ cur, uint4* other)
+{
+    __shared__ int warp_cnt[8];
+    __shared__ int warp_leave[8];
+    __shared__ int leave_ids[256];
+    const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+    const int fl = (t < ntiles) ? act[t] : 0;
+    const int on = fl & 1;
+    const int leaving = (fl & 2) && !on;
+    const unsigned b = __ballot_sync(0xffffffffu, on);
+    const unsigned bl = __ballot_sync(0xffffffffu, leaving);
+    const int w = threadIdx.x >> 5;
+    const unsigned inst = (t < ntiles) ? tile_inst[t] : 0xffffu;
+    if (lane_id() == 0) {
+        warp_cnt[w] = __popc(b);
+        warp_leave[w] = __popc(bl);
+    }
+    // per-instance count and max|F| of the active lanes
+    const unsigned key = on ? inst : 0x10000u + lane_id();
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const unsigned mbits = (on && tile_maxF) ? __float_as_uint(tile_maxF[t]) : 0u;
+    const unsigned gmax = __reduce_max_sync(grp, mbits);
+    if (on && (__ffs(grp) - 1) == (int)lane_id()) {
+        atomicAdd(&inst_count[inst], __popc(grp));
+        if (tile_maxF && gmax) atomicMax(&Mbits[inst], (unsigned long long)gmax);
+    }
+    __syncthreads();
+    int before = 0, lbefore = 0, ltotal = 0;
+    for (int k = 0; k < 8; ++k) {
+        if (k < w) {
+            before += warp_cnt[k];
+            lbefore += warp_leave[k];
+        }
+        ltotal += warp_leave[k];
+    }
+    const unsigned below = (1u << lane_id()) - 1u;
+    if (on) {
+        const int pos = offsets[blockIdx.x] + before + __popc(b & below);
+        const Inst& in = d_inst[inst];
+        const unsigned sg = tile_sgn ? tile_sgn[t] : (in.Fc >= 0.0 ? SG_POS : SG_NEG);
+        list[pos] = (int)t;
+        list_info[pos] = (uint8_t)(nb_bits(t, in) | sg);
+        list_inst[pos] = (uint16_t)inst;
+    }
+    if (leaving) leave_ids[lbefore + __popc(bl & below)] = (int)t;
+    if (ltotal == 0) return;
+    __syncthreads();
+    constexpr int VEC = TILE_PTS * 4 / 16;
+    const int total = ltotal * VEC;
+    for (int i = threadIdx.x; i < total; i += 256) {
+        const size_t off = (size_t)leave_ids[i / VEC] * VEC + (i % VEC);
+        other[off] = cur[off];
+    }
+}
+
+// per-instance dt (one thread per instance)
+__global__ void k_set_dt_batch(StepScalars* sc, int n_inst, const Inst* __restrict__ d_inst,
+                               int mode, double value, int finalize, unsigned long long* Mbits,
+                               int* inst_count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    const Inst& in = d_inst[i];
+    double M;
+    if (finalize) {
+        const int n = inst_count[i];
+        if (in.speed_mode == 1) M = (n > 0) ? fabs(in.Fc) : 0.0;
+        else M = (n > 0) ? (double)__uint_as_float((unsigned)Mbits[i]) : 0.0;
+        Mbits[i] = 0;
+        inst_count[i] = 0;
+        sc[i].M = M;
+        sc[i].active = n;
+    } else {
+        M = sc[i].M;
+    }
+    double dt;
+    if (mode == 1) {
+        const double ch = __dmul_rn(value, in.h);
+        dt = (M > 0.0) ? __ddiv_rn(ch, M) : ch;
+    } else {
+        dt = value;
+    }
+    sc[i].dt = dt;
+    sc[i].coef = __double2float_rn(__ddiv_rn(dt, in.h));
+}
+
 // full-domain list: every tile in ascending order
 __global__ void __launch_bounds__(256) k_full_list(int* list, uint8_t* list_info,
                                                    const uint8_t* __restrict__ tile_sgn,
@@ -508,6 +603,31 @@ cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* li
         k_scatter<double><<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, tile_sgn,
                                              const_sgn, single, ntiles, (const double*)tile_maxF,
                                              Mbits, (const uint4*)cur, (uint4*)other);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_batch(const uint8_t* act, const int* block_offsets, int* list,
+                                 uint8_t* list_info, uint16_t* list_inst,
+                                 const uint8_t* tile_sgn, const Inst* d_inst,
+                                 const uint16_t* tile_inst, long long ntiles,
+                                 const void* tile_maxF, int prec, unsigned long long* Mbits,
+                                 int* inst_count, const void* cur, void* other, cudaStream_t s)
+{
+    if (prec != 0) return cudaErrorInvalidValue;
+    const int nb = (int)((ntiles + 255) / 256);
+    k_scatter_batch<<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, list_inst, tile_sgn,
+                                       d_inst, tile_inst, ntiles, (const float*)tile_maxF, Mbits,
+                                       inst_count, (const uint4*)cur, (uint4*)other);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_dt_batch(StepScalars* sc, int n_inst, const Inst* d_inst, int mode,
+                                double value, int finalize, int prec, unsigned long long* Mbits,
+                                int* inst_count, cudaStream_t s)
+{
+    (void)prec;
+    k_set_dt_batch<<<(n_inst + 127) / 128, 128, 0, s>>>(sc, n_inst, d_inst, mode, value, finalize,
+                                                       Mbits, inst_count);
     return cudaGetLastError();
 }
 

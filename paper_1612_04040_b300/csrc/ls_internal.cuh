@@ -57,7 +57,7 @@ struct StepScalars {
     double M;      // max |F| over the active set at the last rebuild
     double dt;     // current time step
     float coef;    // (float)(dt / h), FP32 path
-    float pad;
+    int active;    // active tiles of this instance at the last rebuild (batched)
 };
 
 // ---------------------------------------------------------------------------
@@ -114,13 +114,39 @@ struct StepArgs {
     const void* F;            // field (bricked) or NULL for constant speed
     const int* list;          // active tile ids (ascending)
     const uint8_t* info;      // per-entry info byte (NB_* | SG_*)
+    const uint16_t* list_inst;  // per-entry instance (batched contexts), else NULL
     const int* count;         // number of active tiles (device)
-    const StepScalars* sc;
+    const StepScalars* sc;    // per-instance dt, dt/h
+    const Inst* insts;        // per-instance parameters (batched), device
     uint8_t* core;            // fused tube test output, or NULL
     unsigned long long* updates;
-    Inst in;                  // single instance parameters
+    Inst in;                  // single instance parameters (bc is read from here always)
+    int max_grid;             // cap on the persistent grid (0 = none)
 };
-cudaError_t launch_step(const StepArgs& a, int prec, int grid, cudaStream_t s);
-int step_grid_size(int prec, int classify);
+
+// launch configuration of the FP32 stencil, chosen by the autotuner
+struct StepConfig {
+    int stages = 3;           // cp.async ring depth (2, 3, 4)
+    int grid_pct = 100;       // persistent grid, percent of full occupancy
+};
+
+cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// batched rebuild helpers (ls_band.cu)
+// ---------------------------------------------------------------------------
+// scatter for a batch: list + info + instance id per entry; per-instance
+// active counts and max|F| bits; leaving-tile copy
+cudaError_t launch_scatter_batch(const uint8_t* act, const int* block_offsets, int* list,
+                                 uint8_t* list_info, uint16_t* list_inst,
+                                 const uint8_t* tile_sgn, const Inst* d_inst,
+                                 const uint16_t* tile_inst, long long ntiles,
+                                 const void* tile_maxF, int prec, unsigned long long* Mbits,
+                                 int* inst_count, const void* cur, void* other, cudaStream_t s);
+// per-instance dt from per-instance M (finalize: from Mbits / |Fc| and the
+// per-instance active counts, then clear both)
+cudaError_t launch_set_dt_batch(StepScalars* sc, int n_inst, const Inst* d_inst, int mode,
+                                double value, int finalize, int prec, unsigned long long* Mbits,
+                                int* inst_count, cudaStream_t s);
 
 }  // namespace lsk

@@ -34,7 +34,6 @@ namespace {
 // x-halo value, and the y/z-halo runs for threads on a tile face) into a
 // ring of S shared-memory stages, so the latency of the next tiles' loads
 // overlaps the arithmetic of the current one.
-constexpr int S32 = 3;  // pipeline stages
 
 // cp.async of 16 / 4 bytes into shared memory, predicated (no branch)
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred = true)
@@ -142,39 +141,49 @@ __device__ __forceinline__ float4 upd4(const float4& c, const float4& f, float x
     return make_float4(r[0], r[1], r[2], r[3]);
 }
 
-template <bool FIELD, bool CLASSIFY>
+// FIELD: speed field (else constant per instance); CLASSIFY: fused tube
+// test; BATCHED: list entries belong to different instances (per-entry
+// instance id, per-instance dt/h, speed, strides and gamma); S: stages.
+template <bool FIELD, bool CLASSIFY, bool BATCHED, int S>
 __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Stage32* st = reinterpret_cast<Stage32*>(smem_raw);
-    __shared__ unsigned smin[S32];
+    __shared__ unsigned smin[S];
     const int tid = threadIdx.x;
     const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
     const int n = *a.count;
     if (blockIdx.x == 0 && tid == 0 && a.updates)
         atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
-    const float coef = a.sc->coef;
     const float* __restrict__ src = (const float*)a.src;
     float* __restrict__ dst = (float*)a.dst;
     const float* __restrict__ Fp = (const float*)a.F;
     const int* __restrict__ list = a.list;
     const uint8_t* __restrict__ linfo = a.info;
-    const float Fc = (float)a.in.Fc;
-    const double gamma = a.in.gamma;
+    const uint16_t* __restrict__ linst = a.list_inst;
     const bool extrap = a.in.bc == 0;
-    const int sy = a.in.tnx * TILE_PTS;
-    const int sz = a.in.tnx * a.in.tny * TILE_PTS;
+    // single instance: uniform parameters
+    const float coef1 = BATCHED ? 0.f : a.sc->coef;
+    const float Fc1 = BATCHED ? 0.f : (float)a.in.Fc;
+    const double gamma1 = a.in.gamma;
+    const int sy1 = a.in.tnx * TILE_PTS;
+    const int sz1 = a.in.tnx * a.in.tny * TILE_PTS;
     const int stride = gridDim.x;
-    // per-thread halo sources (offsets from the tile start), the info bit that
-    // says the neighbour exists (0 = no halo on that axis) and the smem slots
+    // per-thread halo sources (offsets from the tile start, without the
+    // neighbour-tile stride for y/z), the info bit that says the neighbour
+    // exists (0 = no halo on that axis) and the smem slots
     const int x_off = xh ? (TILE_PTS + lz * 64 + ly * 8) : (-TILE_PTS + lz * 64 + ly * 8 + 7);
     const unsigned x_bit = xh ? NB_XP : NB_XM;
-    const int y_off = (ly == 0) ? (-sy + lz * 64 + 56 + 4 * xh) : (sy + lz * 64 + 4 * xh);
+    const int y_in = (ly == 0) ? (lz * 64 + 56 + 4 * xh) : (lz * 64 + 4 * xh);
+    const int y_sgn = (ly == 0) ? -1 : 1;
     const unsigned y_bit = (ly == 0) ? NB_YM : ((ly == 7) ? NB_YP : 0u);
     const int y_slot = 128 + ((ly == 7) ? 16 : 0) + 2 * lz + xh;
-    const int z_off = (lz == 0) ? (-sz + 448 + ly * 8 + 4 * xh) : (sz + ly * 8 + 4 * xh);
+    const int z_in = (lz == 0) ? (448 + ly * 8 + 4 * xh) : (ly * 8 + 4 * xh);
+    const int z_sgn = (lz == 0) ? -1 : 1;
     const unsigned z_bit = (lz == 0) ? NB_ZM : ((lz == 7) ? NB_ZP : 0u);
     const int z_slot = 160 + ((lz == 7) ? 16 : 0) + 2 * ly + xh;
+    const int y_off1 = y_sgn * sy1 + y_in;
+    const int z_off1 = z_sgn * sz1 + z_in;
     // smem indices of the four y/z neighbour quads and of the partner value
     const int i_ym = (ly > 0) ? tid - 2 : y_slot;
     const int i_yp = (ly < 7) ? tid + 2 : y_slot;
@@ -182,65 +191,78 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     const int i_zp = (lz < 7) ? tid + 16 : z_slot;
     const int i_pc = 4 * (tid ^ 1) + (xh ? 3 : 0);
 
-    // stage list entry (t, info) into ring slot s
-    auto issue = [&](unsigned t, unsigned info, int s) {
+    // stage list entry (t, info, instance) into ring slot s
+    auto issue = [&](unsigned t, unsigned info, unsigned inst, int s) {
         const unsigned base = t * TILE_PTS;
         const float* tp = src + base;
-        Stage32& S = st[s];
+        Stage32& Sg = st[s];
         if (tid == 0) {
-            S.meta = make_int4((int)t, (int)info, 0, 0);
+            Sg.meta = make_int4((int)t, (int)info, (int)inst, 0);
             if (CLASSIFY) smin[s] = 0x7f800000u;
         }
-        cp_async16(&S.v[tid], tp + 4 * tid);
-        if (FIELD) cp_async16(&S.f[tid], Fp + base + 4 * tid);
+        int y_off = y_off1, z_off = z_off1;
+        if (BATCHED) {
+            const int tnx = a.insts[inst].tnx, tny = a.insts[inst].tny;
+            y_off = y_sgn * (tnx * TILE_PTS) + y_in;
+            z_off = z_sgn * (tnx * tny * TILE_PTS) + z_in;
+        }
+        cp_async16(&Sg.v[tid], tp + 4 * tid);
+        if (FIELD) cp_async16(&Sg.f[tid], Fp + base + 4 * tid);
         const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0, pz = (info & z_bit) != 0;
-        cp_async4(&S.xo[tid], px ? tp + x_off : tp, px);
-        cp_async16(&S.v[y_slot], py ? tp + y_off : tp, py);
-        cp_async16(&S.v[z_slot], pz ? tp + z_off : tp, pz);
+        cp_async4(&Sg.xo[tid], px ? tp + x_off : tp, px);
+        cp_async16(&Sg.v[y_slot], py ? tp + y_off : tp, py);
+        cp_async16(&Sg.v[z_slot], pz ? tp + z_off : tp, pz);
     };
+    auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
+        t = (unsigned)__ldg(list + k);
+        info = __ldg(linfo + k);
+        inst = BATCHED ? (unsigned)__ldg(linst + k) : 0u;
+    };
+    auto gamma_of = [&](int inst) -> double { return BATCHED ? a.insts[inst].gamma : gamma1; };
 
     int kn = blockIdx.x;  // next list entry to stage
 #pragma unroll
-    for (int s = 0; s < S32 - 1; ++s) {
-        if (kn < n) issue((unsigned)__ldg(list + kn), __ldg(linfo + kn), s);
+    for (int s = 0; s < S - 1; ++s) {
+        if (kn < n) {
+            unsigned t, info, inst;
+            fetch(kn, t, info, inst);
+            issue(t, info, inst, s);
+        }
         cp_async_commit();
         kn += stride;
     }
     // list entry after that, fetched one iteration ahead of its staging
-    unsigned t_next = 0, i_next = 0;
-    if (kn < n) {
-        t_next = (unsigned)__ldg(list + kn);
-        i_next = __ldg(linfo + kn);
-    }
+    unsigned t_next = 0, i_next = 0, n_next = 0;
+    if (kn < n) fetch(kn, t_next, i_next, n_next);
     int cur = 0;
     int prev = -1;
-    int prev_t = -1;
+    int prev_t = -1, prev_inst = 0;
     for (int k = blockIdx.x; k < n; k += stride) {
-        cp_async_wait<S32 - 2>();
+        cp_async_wait<S - 2>();
         __syncthreads();
         if (CLASSIFY && tid == 0 && prev >= 0)
-            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma) ? 1 : 0;
+            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma_of(prev_inst)) ? 1 : 0;
         {
-            const int sn = (cur + S32 - 1) % S32;
-            if (kn < n) issue(t_next, i_next, sn);
+            const int sn = (cur + S - 1) % S;
+            if (kn < n) issue(t_next, i_next, n_next, sn);
             cp_async_commit();
             kn += stride;
-            if (kn < n) {
-                t_next = (unsigned)__ldg(list + kn);
-                i_next = __ldg(linfo + kn);
-            }
+            if (kn < n) fetch(kn, t_next, i_next, n_next);
         }
-        const Stage32& S = st[cur];
-        const int t = S.meta.x;
-        const unsigned info = (unsigned)S.meta.y;
-        const float4 c = S.v[tid];
-        const float4 f = FIELD ? S.f[tid] : make_float4(Fc, Fc, Fc, Fc);
-        const float4 ym = S.v[i_ym];
-        const float4 yp = S.v[i_yp];
-        const float4 zm = S.v[i_zm];
-        const float4 zp = S.v[i_zp];
-        const float pcv = reinterpret_cast<const float*>(S.v)[i_pc];
-        const float xo = S.xo[tid];
+        const Stage32& Sg = st[cur];
+        const int t = Sg.meta.x;
+        const unsigned info = (unsigned)Sg.meta.y;
+        const int inst = Sg.meta.z;
+        const float coef = BATCHED ? a.sc[inst].coef : coef1;
+        const float Fc = BATCHED ? (float)a.insts[inst].Fc : Fc1;
+        const float4 c = Sg.v[tid];
+        const float4 f = FIELD ? Sg.f[tid] : make_float4(Fc, Fc, Fc, Fc);
+        const float4 ym = Sg.v[i_ym];
+        const float4 yp = Sg.v[i_yp];
+        const float4 zm = Sg.v[i_zm];
+        const float4 zp = Sg.v[i_zp];
+        const float pcv = reinterpret_cast<const float*>(Sg.v)[i_pc];
+        const float xo = Sg.xo[tid];
         const float xm0 = xh ? pcv : xo;
         const float xp3 = xh ? xo : pcv;
 
@@ -270,17 +292,17 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         }
         prev = cur;
         prev_t = t;
-        cur = (cur + 1) % S32;
+        prev_inst = inst;
+        cur = (cur + 1) % S;
     }
     if (CLASSIFY) {
         __syncthreads();
         if (tid == 0 && prev >= 0)
-            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma) ? 1 : 0;
+            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma_of(prev_inst)) ? 1 : 0;
     }
     cp_async_wait<0>();
 }
 
-constexpr size_t SMEM32 = sizeof(Stage32) * S32;
 
 // ------------------------------------------------------------------ FP64 ----
 __device__ __forceinline__ double max0(double a) { return a > 0.0 ? a : 0.0; }
@@ -448,39 +470,58 @@ int occupancy_grid(K kernel, size_t smem)
     return sms * per;
 }
 
-}  // namespace
-
-int step_grid_size(int prec, int classify)
+template <bool FIELD, bool CLS, bool BAT, int S>
+cudaError_t launch32(const StepArgs& a, int grid_pct, cudaStream_t s)
 {
-    static int cache[2][2] = {{0, 0}, {0, 0}};
-    int& g = cache[prec ? 1 : 0][classify ? 1 : 0];
-    if (!g) {
-        if (prec == 0)
-            g = classify ? occupancy_grid(k_step_f32<true, true>, SMEM32)
-                         : occupancy_grid(k_step_f32<true, false>, SMEM32);
-        else
-            g = classify ? occupancy_grid(k_step_f64<true, true>, 0)
-                         : occupancy_grid(k_step_f64<true, false>, 0);
-    }
-    return g;
+    constexpr size_t smem = sizeof(Stage32) * S;
+    static int full = 0;
+    if (!full) full = occupancy_grid(k_step_f32<FIELD, CLS, BAT, S>, smem);
+    int grid = (int)((long long)full * grid_pct / 100);
+    if (grid < 1) grid = 1;
+    if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
+    k_step_f32<FIELD, CLS, BAT, S><<<grid, 128, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_step(const StepArgs& a, int prec, int grid, cudaStream_t s)
+template <bool FIELD, bool CLS, bool BAT>
+cudaError_t launch32_s(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
+{
+    switch (cfg.stages) {
+    case 2: return launch32<FIELD, CLS, BAT, 2>(a, cfg.grid_pct, s);
+    case 4: return launch32<FIELD, CLS, BAT, 4>(a, cfg.grid_pct, s);
+    default: return launch32<FIELD, CLS, BAT, 3>(a, cfg.grid_pct, s);
+    }
+}
+
+template <bool FIELD, bool CLS>
+cudaError_t launch64(const StepArgs& a, cudaStream_t s)
+{
+    static int full = 0;
+    if (!full) full = occupancy_grid(k_step_f64<FIELD, CLS>, 0);
+    int grid = full;
+    if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
+    k_step_f64<FIELD, CLS><<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cudaStream_t s)
 {
     const bool field = a.F != nullptr;
     const bool cls = a.core != nullptr;
+    const bool bat = a.list_inst != nullptr;
     if (prec == 0) {
-        if (field && cls) k_step_f32<true, true><<<grid, 128, SMEM32, s>>>(a);
-        else if (field) k_step_f32<true, false><<<grid, 128, SMEM32, s>>>(a);
-        else if (cls) k_step_f32<false, true><<<grid, 128, SMEM32, s>>>(a);
-        else k_step_f32<false, false><<<grid, 128, SMEM32, s>>>(a);
-    } else {
-        if (field && cls) k_step_f64<true, true><<<grid, 128, 0, s>>>(a);
-        else if (field) k_step_f64<true, false><<<grid, 128, 0, s>>>(a);
-        else if (cls) k_step_f64<false, true><<<grid, 128, 0, s>>>(a);
-        else k_step_f64<false, false><<<grid, 128, 0, s>>>(a);
+        if (bat) {
+            if (field) return cls ? launch32_s<true, true, true>(a, cfg, s) : launch32_s<true, false, true>(a, cfg, s);
+            return cls ? launch32_s<false, true, true>(a, cfg, s) : launch32_s<false, false, true>(a, cfg, s);
+        }
+        if (field) return cls ? launch32_s<true, true, false>(a, cfg, s) : launch32_s<true, false, false>(a, cfg, s);
+        return cls ? launch32_s<false, true, false>(a, cfg, s) : launch32_s<false, false, false>(a, cfg, s);
     }
-    return cudaGetLastError();
+    if (bat) return cudaErrorInvalidValue;  // batched contexts are FP32
+    if (field) return cls ? launch64<true, true>(a, s) : launch64<true, false>(a, s);
+    return cls ? launch64<false, true>(a, s) : launch64<false, false>(a, s);
 }
 
 }  // namespace lsk

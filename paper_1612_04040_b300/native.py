@@ -47,8 +47,21 @@ SIGNATURES = {
     "ls_step": (_i, [_vp, _i, _d, _i, _i, _c.POINTER(_d)]),
     "ls_set_full_domain": (_i, [_vp, _i]),
     "ls_get_phi": (_i, [_vp, _vp, _i]),
+    "ls_snapshot": (_i, [_vp]),
+    "ls_restore": (_i, [_vp]),
     "ls_get_active_tiles": (_i, [_vp, _c.POINTER(_c.c_int), _ll, _c.POINTER(_ll)]),
     "ls_get_updates": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
+    "ls_set_graphs": (_i, [_vp, _i]),
+    "ls_autotune": (_i, [_vp, _i, _c.POINTER(_i), _c.POINTER(_i)]),
+    "ls_set_step_config": (_i, [_vp, _i, _i]),
+    "ls_batch_create": (_i, [_i, _c.POINTER(_i), _c.POINTER(_i), _c.POINTER(_i), _c.POINTER(_d), _i, _pp]),
+    "ls_batch_size": (_i, [_vp, _c.POINTER(_i)]),
+    "ls_inst_set_phi": (_i, [_vp, _i, _vp, _i]),
+    "ls_inst_set_speed": (_i, [_vp, _i, _vp, _i]),
+    "ls_inst_set_speed_const": (_i, [_vp, _i, _d]),
+    "ls_inst_get_phi": (_i, [_vp, _i, _vp, _i]),
+    "ls_inst_get_active_tiles": (_i, [_vp, _i, _c.POINTER(_c.c_int), _ll, _c.POINTER(_ll)]),
+    "ls_inst_last_dt": (_i, [_vp, _i, _c.POINTER(_d)]),
     "ls_profile_enable": (_i, [_vp, _i]),
     "ls_get_profile": (_i, [_vp, _vp]),
     "ls_reset_profile": (_i, [_vp]),
@@ -216,6 +229,12 @@ class LevelSet:
                                ctypes.byref(d) if want_dt else None), "ls_step")
         return d.value if want_dt else None
 
+    def snapshot(self):
+        check(self.lib.ls_snapshot(self.ctx), "ls_snapshot")
+
+    def restore(self):
+        check(self.lib.ls_restore(self.ctx), "ls_restore")
+
     def get_phi(self, out=None):
         if out is None:
             out = np.empty(self.shape, dtype=self.dtype)
@@ -239,6 +258,17 @@ class LevelSet:
     def status(self):
         return self.lib.ls_get_status(self.ctx)
 
+    def set_graphs(self, on=True):
+        check(self.lib.ls_set_graphs(self.ctx, int(bool(on))), "ls_set_graphs")
+
+    def autotune(self, reps=5):
+        st, pct = ctypes.c_int(0), ctypes.c_int(0)
+        check(self.lib.ls_autotune(self.ctx, int(reps), ctypes.byref(st), ctypes.byref(pct)), "ls_autotune")
+        return st.value, pct.value
+
+    def set_step_config(self, stages, grid_pct):
+        check(self.lib.ls_set_step_config(self.ctx, int(stages), int(grid_pct)), "ls_set_step_config")
+
     def profile_enable(self, on=True):
         check(self.lib.ls_profile_enable(self.ctx, int(bool(on))), "ls_profile_enable")
 
@@ -249,3 +279,67 @@ class LevelSet:
 
     def reset_profile(self):
         check(self.lib.ls_reset_profile(self.ctx), "ls_reset_profile")
+
+
+class Batch(LevelSet):
+    """A batched context: n independent grids advanced by one stencil launch
+    per step (ls_batch_create).  Per-instance calls take the instance index."""
+
+    def __init__(self, edges, hs, precision=LS_FP32, stream=None):
+        self.lib = load()
+        self.n = len(edges)
+        nx = [int(e[0]) if hasattr(e, "__len__") else int(e) for e in edges]
+        ny = [int(e[1]) if hasattr(e, "__len__") else int(e) for e in edges]
+        nz = [int(e[2]) if hasattr(e, "__len__") else int(e) for e in edges]
+        self.shapes = [(z, y, x) for x, y, z in zip(nx, ny, nz)]
+        self.precision = precision
+        self.dtype = np.float32 if precision == LS_FP32 else np.float64
+        arr_i = ctypes.c_int * self.n
+        arr_d = ctypes.c_double * self.n
+        h_ = ctypes.c_void_p()
+        check(self.lib.ls_batch_create(self.n, arr_i(*nx), arr_i(*ny), arr_i(*nz),
+                                       arr_d(*[float(h) for h in hs]), int(precision), ctypes.byref(h_)),
+              "ls_batch_create")
+        self.ctx = h_
+        self.shape = None
+        self.count = None
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        if stream is not None:
+            check(self.lib.ls_set_stream(self.ctx, ctypes.c_void_p(stream)), "ls_set_stream")
+
+    def _count(self, i):
+        z, y, x = self.shapes[i]
+        return x * y * z
+
+    def set_phi_i(self, i, a):
+        p, dev = array_ptr(a, self.dtype, self._count(i))
+        check(self.lib.ls_inst_set_phi(self.ctx, int(i), p, dev), "ls_inst_set_phi")
+
+    def set_speed_i(self, i, a):
+        p, dev = array_ptr(a, self.dtype, self._count(i))
+        check(self.lib.ls_inst_set_speed(self.ctx, int(i), p, dev), "ls_inst_set_speed")
+
+    def set_speed_const_i(self, i, F):
+        check(self.lib.ls_inst_set_speed_const(self.ctx, int(i), float(F)), "ls_inst_set_speed_const")
+
+    def get_phi_i(self, i, out=None):
+        if out is None:
+            out = np.empty(self.shapes[i], dtype=self.dtype)
+        p, dev = array_ptr(out, self.dtype, self._count(i))
+        check(self.lib.ls_inst_get_phi(self.ctx, int(i), p, dev), "ls_inst_get_phi")
+        return out
+
+    def active_tiles_i(self, i):
+        n = ctypes.c_longlong(0)
+        check(self.lib.ls_inst_get_active_tiles(self.ctx, int(i), None, 0, ctypes.byref(n)),
+              "ls_inst_get_active_tiles")
+        buf = np.empty(max(n.value, 1), dtype=np.int32)
+        check(self.lib.ls_inst_get_active_tiles(self.ctx, int(i), buf.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                n.value, ctypes.byref(n)), "ls_inst_get_active_tiles")
+        return buf[:n.value].copy()
+
+    def last_dt_i(self, i):
+        d = ctypes.c_double(0.0)
+        check(self.lib.ls_inst_last_dt(self.ctx, int(i), ctypes.byref(d)), "ls_inst_last_dt")
+        return d.value

@@ -1,0 +1,170 @@
+"""Batched contexts (many independent grids, one stencil launch per step),
+CUDA-graph replay and the autotuner, against the FP64 CPU oracle run on each
+instance separately."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1612_04040_b300 import inputs
+from paper_1612_04040_b300 import native as ls
+
+pytestmark = pytest.mark.gpu
+
+
+def tile_mask(active, shape):
+    return np.repeat(np.repeat(np.repeat(active.astype(bool), 8, 0), 8, 1), 8, 2)[
+        :shape[0], :shape[1], :shape[2]]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(cuda_ok):
+    ls.load()
+
+
+def small_batch(count=7, seed=5):
+    """Seeded instances of the batch recipe, with small grid edges."""
+    return inputs.batch_instances(count=count, seed=seed, edges=(32, 40, 48, 56, 64))
+
+
+def make_batch(insts, graphs=False):
+    b = ls.Batch([i.edge for i in insts], [i.h for i in insts])
+    phis = []
+    for k, it in enumerate(insts):
+        p = it.phi().numpy().astype(np.float32)
+        phis.append(p)
+        b.set_phi_i(k, torch.from_numpy(p).cuda() if k % 2 else p)
+        b.set_speed_const_i(k, it.speed)
+    b.set_graphs(graphs)
+    return b, phis
+
+
+def test_batch_matches_per_instance_oracle():
+    insts = small_batch()
+    b, phis = make_batch(insts)
+    b.band_rebuild(4.0)
+    oracles = []
+    for it, p in zip(insts, phis):
+        o = oracle.Oracle(p.shape, it.h)
+        o.set_phi(p.astype(np.float64))
+        o.set_speed_const(float(np.float64(it.speed)))
+        o.band_rebuild(4.0)
+        oracles.append(o)
+    nsteps = 0
+    for chunk in (5, 5, 5, 5):
+        b.step(chunk, 0.5, ls.LS_DT_CFL, 5)
+        nsteps += chunk
+        for k, (it, o) in enumerate(zip(insts, oracles)):
+            do = o.step(chunk, 0.5, oracle.DT_CFL, 5)
+            assert b.last_dt_i(k) == do
+            assert np.array_equal(b.active_tiles_i(k), o.active_tiles()), k
+    for k, (it, o) in enumerate(zip(insts, oracles)):
+        out = b.get_phi_i(k).astype(np.float64)
+        m = tile_mask(o.active, o.shape)
+        if m.any():
+            assert np.max(np.abs(out[m] - o.phi[m])) <= 1e-5 * it.h * nsteps, k
+
+
+def test_batch_graph_replay_equals_eager():
+    insts = small_batch(count=5, seed=9)
+    outs = []
+    for graphs in (False, True):
+        b, _ = make_batch(insts, graphs=graphs)
+        b.band_rebuild(4.0)
+        for _ in range(3):
+            b.step(7, 0.5, ls.LS_DT_CFL, 5)   # the same call three times: replayed
+        outs.append([b.get_phi_i(k) for k in range(len(insts))])
+        b.close()
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+
+
+def test_single_grid_graph_and_autotune_bitwise():
+    """Graph replay and every autotuner configuration compute the same bits."""
+    w = inputs.SphereUnion(n=64, count=5)
+    p = w.phi().numpy().astype(np.float32)
+    F = w.speed().numpy().astype(np.float32)
+    outs = []
+    for mode in ("eager", "graph", "tuned"):
+        g = ls.LevelSet(64, 64, 64, w.h, ls.LS_FP32)
+        g.set_phi(p)
+        g.set_speed(F)
+        g.band_rebuild(6.0)
+        if mode == "graph":
+            g.set_graphs(True)
+        if mode == "tuned":
+            g.step(1, 0.5, ls.LS_DT_CFL, 5)
+            st, pct = g.autotune(reps=2)
+            assert st in (2, 3, 4) and pct in (50, 75, 100)
+            g.step(11, 0.5, ls.LS_DT_CFL, 5)
+        else:
+            g.step(1, 0.5, ls.LS_DT_CFL, 5)
+            for _ in range(2):
+                g.step(3, 0.5, ls.LS_DT_CFL, 5)
+            g.step(5, 0.5, ls.LS_DT_CFL, 5)
+        outs.append(g.get_phi())
+        g.close()
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("stages,pct", [(2, 50), (4, 100), (3, 75)])
+def test_step_configs_agree(stages, pct):
+    w = inputs.SphereUnion(n=48, count=4)
+    p = w.phi().numpy().astype(np.float32)
+    ref = None
+    for cfg in ((3, 100), (stages, pct)):
+        g = ls.LevelSet(48, 48, 48, w.h, ls.LS_FP32)
+        g.set_phi(p)
+        g.set_speed_const(-0.6)
+        g.set_step_config(*cfg)
+        g.band_rebuild(4.0)
+        g.step(10, 0.5, ls.LS_DT_CFL, 5)
+        out = g.get_phi()
+        if ref is None:
+            ref = out
+        else:
+            assert np.array_equal(out, ref)
+
+
+def test_batch_full_domain_matches_oracle():
+    insts = small_batch(count=3, seed=21)
+    b, phis = make_batch(insts)
+    b.set_full_domain(True)
+    b.step(6, 0.45, ls.LS_DT_CFL, 0)
+    for k, (it, p) in enumerate(zip(insts, phis)):
+        o = oracle.Oracle(p.shape, it.h)
+        o.set_phi(p.astype(np.float64))
+        o.set_speed_const(it.speed)
+        o.set_full_domain(True)
+        o.step(6, 0.45, oracle.DT_CFL)
+        assert np.max(np.abs(b.get_phi_i(k) - o.phi)) <= 1e-5 * it.h * 6
+
+
+def test_batch_rejects_mixed_speeds_and_fp64():
+    with pytest.raises(ls.LSError):
+        ls.Batch([16, 16], [1 / 16, 1 / 16], precision=ls.LS_FP64)
+    b = ls.Batch([16, 24], [1 / 16, 1 / 24])
+    b.set_phi_i(0, np.ones((16, 16, 16), np.float32))
+    b.set_phi_i(1, np.ones((24, 24, 24), np.float32))
+    b.set_speed_const_i(0, 1.0)
+    b.set_speed_i(1, np.ones((24, 24, 24), np.float32))
+    b.band_rebuild(2.0)
+    with pytest.raises(ls.LSError) as e:
+        b.step(1, 0.5, ls.LS_DT_CFL, 5)
+    assert e.value.status == ls.LS_ESTATE
+
+
+def test_snapshot_restore_resumes_exactly():
+    """Checkpoint / resume: restore + rerun equals the first run bit for bit."""
+    insts = small_batch(count=4, seed=33)
+    b, _ = make_batch(insts)
+    b.snapshot()
+    runs = []
+    for _ in range(2):
+        b.restore()
+        b.band_rebuild(4.0)
+        b.step(12, 0.5, ls.LS_DT_CFL, 5)
+        runs.append([b.get_phi_i(k) for k in range(len(insts))])
+    for a, c in zip(*runs):
+        assert np.array_equal(a, c)
