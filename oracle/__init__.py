@@ -75,6 +75,14 @@ def _load():
             lib.orc_compact.argtypes = [u8p, c64, i32p]
             lib.orc_max_abs_speed.restype = cd
             lib.orc_max_abs_speed.argtypes = [ci, ci, ci, ci, dp, cd, u8p]
+            lib.orc_conv3_fwd.restype = None
+            lib.orc_conv3_fwd.argtypes = [ci, ci, ci, ci, ci, dp, dp, dp, dp]
+            lib.orc_conv3_bwd_data.restype = None
+            lib.orc_conv3_bwd_data.argtypes = [ci, ci, ci, ci, ci, dp, dp, dp]
+            lib.orc_conv3_bwd_weight.restype = None
+            lib.orc_conv3_bwd_weight.argtypes = [ci, ci, ci, ci, ci, dp, dp, dp, dp]
+            lib.orc_restrict4.restype = None
+            lib.orc_restrict4.argtypes = [ci, ci, ci, dp, dp]
             _lib = lib
     return _lib
 
@@ -289,3 +297,90 @@ class Oracle:
             self.since_rebuild += 1
             self.last_dt = dt
         return self.last_dt
+
+
+# --------------------------------------------------------------------------
+# learned coarse-grid corrector (not in the paper): FP64 definitions
+# --------------------------------------------------------------------------
+
+def conv3_fwd(x, W, b=None):
+    """3x3x3 convolution, zero padding.  x: (nz, ny, nx, ci), W: (27, ci, co)
+    with tap = (dz+1)*9 + (dy+1)*3 + (dx+1), b: (co,) or None."""
+    lib = _load()
+    x = _f64(x)
+    W = _f64(W)
+    nz, ny, nx, ci = x.shape
+    co = W.shape[2]
+    y = np.empty((nz, ny, nx, co))
+    bb = None if b is None else _f64(b)
+    lib.orc_conv3_fwd(nx, ny, nz, ci, co, _ptr(x, ctypes.c_double), _ptr(W, ctypes.c_double),
+                      _ptr(bb, ctypes.c_double), _ptr(y, ctypes.c_double))
+    return y
+
+
+def conv3_bwd_data(dy, W):
+    """Gradient of conv3_fwd with respect to its input."""
+    lib = _load()
+    dy = _f64(dy)
+    W = _f64(W)
+    nz, ny, nx, co = dy.shape
+    ci = W.shape[1]
+    dx = np.empty((nz, ny, nx, ci))
+    lib.orc_conv3_bwd_data(nx, ny, nz, ci, co, _ptr(dy, ctypes.c_double), _ptr(W, ctypes.c_double),
+                           _ptr(dx, ctypes.c_double))
+    return dx
+
+
+def conv3_bwd_weight(x, dy):
+    """Gradients of conv3_fwd with respect to W (27, ci, co) and b (co,)."""
+    lib = _load()
+    x = _f64(x)
+    dy = _f64(dy)
+    nz, ny, nx, ci = x.shape
+    co = dy.shape[3]
+    dW = np.empty((27, ci, co))
+    db = np.empty((co,))
+    lib.orc_conv3_bwd_weight(nx, ny, nz, ci, co, _ptr(x, ctypes.c_double), _ptr(dy, ctypes.c_double),
+                             _ptr(dW, ctypes.c_double), _ptr(db, ctypes.c_double))
+    return dW, db
+
+
+def restrict4(fine):
+    """Fine -> coarse (factor 4): the trilinear value at each coarse cell
+    centre, i.e. the mean of the 2^3 fine points around it."""
+    lib = _load()
+    f = _f64(fine)
+    nfz, nfy, nfx = f.shape
+    c = np.empty((nfz // 4, nfy // 4, nfx // 4))
+    lib.orc_restrict4(nfx, nfy, nfz, _ptr(f, ctypes.c_double), _ptr(c, ctypes.c_double))
+    return c
+
+
+def relu(a):
+    return np.maximum(a, 0.0)
+
+
+def cnn_forward(x, params):
+    """The corrector network: conv-ReLU-conv-ReLU-conv-ReLU-conv.
+    params: list of (W, b).  Returns the list of layer outputs [a1, a2, a3, z4]
+    (post-ReLU for the hidden layers)."""
+    acts = []
+    a = x
+    for k, (W, b) in enumerate(params):
+        z = conv3_fwd(a, W, b)
+        a = relu(z) if k < len(params) - 1 else z
+        acts.append(a)
+    return acts
+
+
+def cnn_backward(x, params, acts, dz_out):
+    """Gradients of sum(dz_out * z4) with respect to every (W, b)."""
+    grads = [None] * len(params)
+    g = dz_out
+    for k in range(len(params) - 1, -1, -1):
+        inp = x if k == 0 else acts[k - 1]
+        dW, db = conv3_bwd_weight(inp, g)
+        grads[k] = (dW, db)
+        if k > 0:
+            g = conv3_bwd_data(g, params[k][0]) * (acts[k - 1] > 0)
+    return grads

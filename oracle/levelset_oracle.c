@@ -223,3 +223,107 @@ double orc_max_abs_speed(int nx, int ny, int nz, int tile, const double *F,
             }
     return m;
 }
+
+/* ------------------------------------------------------------------------
+ * Learned coarse-grid corrector (not in the paper): plain FP64 building
+ * blocks, written from their definitions.
+ *
+ * Layout: activations channels-last x[(z*ny + y)*nx + x][c]; weights
+ * W[tap][ci][co] with tap = (dz+1)*9 + (dy+1)*3 + (dx+1), dx, dy, dz in
+ * {-1, 0, 1}; zero padding outside the grid.
+ * ---------------------------------------------------------------------- */
+
+/* y[p][o] = b[o] + sum_tap sum_ci x[p + off(tap)][ci] * W[tap][ci][o] */
+void orc_conv3_fwd(int nx, int ny, int nz, int ci, int co, const double *x, const double *W,
+                   const double *b, double *y)
+{
+    int z;
+#pragma omp parallel for schedule(static)
+    for (z = 0; z < nz; ++z)
+        for (int yy = 0; yy < ny; ++yy)
+            for (int xx = 0; xx < nx; ++xx) {
+                double *out = y + idx3(nx, ny, xx, yy, z) * (size_t)co;
+                for (int o = 0; o < co; ++o) out[o] = b ? b[o] : 0.0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int X = xx + dx, Y = yy + dy, Z = z + dz;
+                            if (X < 0 || Y < 0 || Z < 0 || X >= nx || Y >= ny || Z >= nz) continue;
+                            const int tap = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                            const double *in = x + idx3(nx, ny, X, Y, Z) * (size_t)ci;
+                            const double *w = W + (size_t)tap * ci * co;
+                            for (int c = 0; c < ci; ++c)
+                                for (int o = 0; o < co; ++o) out[o] += in[c] * w[c * co + o];
+                        }
+            }
+}
+
+/* dx[q][ci] = sum_tap sum_o dy[q - off(tap)][o] * W[tap][ci][o]  (the adjoint
+ * of orc_conv3_fwd with respect to x) */
+void orc_conv3_bwd_data(int nx, int ny, int nz, int ci, int co, const double *dy,
+                        const double *W, double *dxo)
+{
+    int z;
+#pragma omp parallel for schedule(static)
+    for (z = 0; z < nz; ++z)
+        for (int yy = 0; yy < ny; ++yy)
+            for (int xx = 0; xx < nx; ++xx) {
+                double *out = dxo + idx3(nx, ny, xx, yy, z) * (size_t)ci;
+                for (int c = 0; c < ci; ++c) out[c] = 0.0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dyy = -1; dyy <= 1; ++dyy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            /* output point p with p + off(tap) = q */
+                            const int X = xx - dx, Y = yy - dyy, Z = z - dz;
+                            if (X < 0 || Y < 0 || Z < 0 || X >= nx || Y >= ny || Z >= nz) continue;
+                            const int tap = (dz + 1) * 9 + (dyy + 1) * 3 + (dx + 1);
+                            const double *g = dy + idx3(nx, ny, X, Y, Z) * (size_t)co;
+                            const double *w = W + (size_t)tap * ci * co;
+                            for (int c = 0; c < ci; ++c)
+                                for (int o = 0; o < co; ++o) out[c] += g[o] * w[c * co + o];
+                        }
+            }
+}
+
+/* dW[tap][ci][o] = sum_p x[p + off(tap)][ci] * dy[p][o];  db[o] = sum_p dy[p][o] */
+void orc_conv3_bwd_weight(int nx, int ny, int nz, int ci, int co, const double *x,
+                          const double *dy, double *dW, double *db)
+{
+    memset(dW, 0, sizeof(double) * 27 * (size_t)ci * co);
+    if (db) memset(db, 0, sizeof(double) * (size_t)co);
+    for (int z = 0; z < nz; ++z)
+        for (int yy = 0; yy < ny; ++yy)
+            for (int xx = 0; xx < nx; ++xx) {
+                const double *g = dy + idx3(nx, ny, xx, yy, z) * (size_t)co;
+                if (db)
+                    for (int o = 0; o < co; ++o) db[o] += g[o];
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dyy = -1; dyy <= 1; ++dyy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int X = xx + dx, Y = yy + dyy, Z = z + dz;
+                            if (X < 0 || Y < 0 || Z < 0 || X >= nx || Y >= ny || Z >= nz) continue;
+                            const int tap = (dz + 1) * 9 + (dyy + 1) * 3 + (dx + 1);
+                            const double *in = x + idx3(nx, ny, X, Y, Z) * (size_t)ci;
+                            double *w = dW + (size_t)tap * ci * co;
+                            for (int c = 0; c < ci; ++c)
+                                for (int o = 0; o < co; ++o) w[c * co + o] += in[c] * g[o];
+                        }
+            }
+}
+
+/* restriction by 4: coarse value at the coarse cell centre (4I+2)h_f, i.e.
+ * the trilinear value there = mean of the fine points 4I+1, 4I+2 per axis */
+void orc_restrict4(int nfx, int nfy, int nfz, const double *fine, double *coarse)
+{
+    const int ncx = nfx / 4, ncy = nfy / 4, ncz = nfz / 4;
+    for (int Z = 0; Z < ncz; ++Z)
+        for (int Y = 0; Y < ncy; ++Y)
+            for (int X = 0; X < ncx; ++X) {
+                double s = 0.0;
+                for (int k = 1; k <= 2; ++k)
+                    for (int j = 1; j <= 2; ++j)
+                        for (int i = 1; i <= 2; ++i)
+                            s += fine[idx3(nfx, nfy, 4 * X + i, 4 * Y + j, 4 * Z + k)];
+                coarse[idx3(ncx, ncy, X, Y, Z)] = s / 8.0;
+            }
+}
