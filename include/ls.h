@@ -242,6 +242,75 @@ int ls_inst_get_active_tiles(ls_ctx *ctx, int i, int *dst, long long cap, long l
 int ls_inst_last_dt(ls_ctx *ctx, int i, double *dt);
 
 /* ---------------------------------------------------------------------
+ * Learned coarse-grid corrector (no counterpart in the paper)
+ *
+ * A small 3-D CNN (4 convolutions 3x3x3: 3 -> 16 -> 16 -> 16 -> 1 channels,
+ * ReLU between; BF16 weights and activations on the tensor cores, FP32
+ * accumulation, FP32 master parameters) corrects the plain step on a coarse
+ * grid: phi~ = plain step of phi^n (Eq. 3), features = [clamp(phi^n/h, +-8),
+ * F, (phi~ - phi^n)/h], phi^{n+1} = phi~ + h * CNN(features) on the points of
+ * the active tiles.  A residual check rejects a step's correction (keeping
+ * phi~, the plain method as fallback) when a corrected value is not finite
+ * or |h * CNN| exceeds dt * max|F|.  Training pairs are (phi^n, phi_ref,
+ * F) on the coarse grid, phi_ref = the restricted fine-grid plain solution
+ * one coarse step later.  Single FP32 contexts with nx a multiple of 128 and
+ * ny, nz even; LS_EINVAL otherwise.
+ * ------------------------------------------------------------------- */
+
+/* Number of FP32 parameters of the network (layer l = 0..3: W_l
+ * [27][ci][co] with tap = (dz+1)*9 + (dy+1)*3 + (dx+1), then b_l [co]). */
+int ls_learned_num_params(long long *n);
+
+/* Seeded Kaiming-uniform weights, zero biases (the last layer scaled by 0.01
+ * so the corrector starts near zero); resets the optimiser. */
+int ls_learned_init(ls_ctx *ctx, unsigned long long seed);
+
+/* Copy the parameters from / to host memory (n = ls_learned_num_params). */
+int ls_learned_set_params(ls_ctx *ctx, const float *src, long long n);
+int ls_learned_get_params(ls_ctx *ctx, float *dst, long long n);
+
+/* Store one training pair on the device: coarse row-major FP32 phi^n, the
+ * reference phi one coarse step later, and the speed field F. */
+int ls_learned_add_pair(ls_ctx *ctx, const float *phi_n, const float *phi_ref, const float *F,
+                        int on_device);
+int ls_learned_num_pairs(ls_ctx *ctx, long long *n);
+
+/* iters Adam steps (learning rate lr), each on one stored pair drawn with a
+ * seeded generator: plain coarse step with fixed dt, forward, MSE of the
+ * network output against (phi_ref - phi~)/h over the points with
+ * |phi^n| < halfwidth*h, backward, update.  Uses the context's phi and
+ * speed as scratch (phi must be set again afterwards).  *final_loss
+ * (nullable) = the last iteration's loss. */
+int ls_learned_train(ls_ctx *ctx, int iters, double lr, double dt, double halfwidth_in_h,
+                     unsigned long long seed, double *final_loss);
+
+/* LS_PLAIN (default) or LS_LEARNED for the steps of ls_step; LS_LEARNED
+ * needs initialised parameters (LS_ESTATE). */
+int ls_set_step_mode(ls_ctx *ctx, int mode);
+
+/* Number of steps whose correction the residual check rejected. */
+int ls_learned_fallbacks(ls_ctx *ctx, unsigned long long *n);
+
+/* Layer primitives on caller-owned device buffers (no allocation):
+ * ls_conv3_bf16: x = BF16 [p][16] channels-last (nx a multiple of 128, ny
+ * and nz even), W = FP32 [27][ci][co] (ci, co <= 16), work = device scratch
+ * of LS_CONV3_WORK_BYTES, status = device word that records LS_ETIMEOUT-type
+ * failures (bit 1).  mode 0: out = BF16 [p][16] relu(conv(x) + b);
+ * mode 1: out = FP32 [p] conv(x)[0] + b[0]; mode 2 (input gradient): out =
+ * BF16 [p][16] conv^T(x) * [mask > 0], x = gradient of the layer output,
+ * W = the forward weights, mask = BF16 [p][16].
+ * ls_conv3_wgrad: dW [27][ci][co] += sum_p x[p + off(tap)] dy[p],
+ * db[co] += sum_p dy[p] (nx a multiple of 64; caller zeroes dW, db).
+ * ls_restrict4: coarse[I] = mean of the fine points 4I+1, 4I+2 per axis. */
+#define LS_CONV3_WORK_BYTES 13824
+int ls_conv3_bf16(const void *x, int nx, int ny, int nz, const float *W, int ci, int co,
+                  const float *bias, int mode, const void *mask, void *out, void *work,
+                  unsigned *status, void *cuda_stream);
+int ls_conv3_wgrad(const void *x, const void *dy, int nx, int ny, int nz, int ci, int co,
+                   float *dW, float *db, void *cuda_stream);
+int ls_restrict4(const float *fine, int nfx, int nfy, int nfz, float *coarse, void *cuda_stream);
+
+/* ---------------------------------------------------------------------
  * Allocation-free band tile list
  * ------------------------------------------------------------------- */
 

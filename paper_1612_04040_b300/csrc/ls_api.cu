@@ -31,95 +31,13 @@
 #include <tuple>
 #include <vector>
 
-#include "ls.h"
-#include "ls_internal.cuh"
+#include "ls_ctx.cuh"
 
-using lsk::Inst;
+using lsk::GraphEntry;
+using lsk::GraphKey;
+using lsk::SchedState;
 
 static thread_local int g_last_cuda_error = 0;
-
-namespace {
-
-// host state a captured ls_step graph starts from / leaves behind
-struct SchedState {
-    int cur = 0;
-    int since_rebuild = 0;
-    bool band_valid = false;
-    bool core_fresh = false;
-};
-
-using GraphKey = std::tuple<int, int, int, int, int, int, int, int, long long, int, int>;
-
-struct GraphEntry {
-    cudaGraphExec_t exec = nullptr;
-    SchedState after;
-    unsigned long long launches = 0;
-    unsigned long long stencil_launches = 0;
-};
-
-}  // namespace
-
-struct ls_ctx {
-    int prec = 0;
-    size_t esize = 4;
-    bool batched = false;
-    int n_inst = 1;
-    std::vector<Inst> insts;      // host copy of the per-instance parameters
-    std::vector<char> inst_phi_set;
-    Inst* d_inst = nullptr;       // device copy (batched contexts)
-    uint16_t* d_tile_inst = nullptr;  // instance of every global tile (batched)
-    uint16_t* d_list_inst = nullptr;  // instance of every list entry (batched)
-    int* d_inst_count = nullptr;      // per-instance active counts (batched)
-    long long ntiles = 0;
-    size_t npts = 0;
-    size_t max_inst_pts = 0;
-    cudaStream_t stream = nullptr;
-    cudaStream_t own_stream = nullptr;  // used for graph capture when stream is NULL
-    void* phi[2] = {nullptr, nullptr};
-    int cur = 0;
-    void* F = nullptr;            // bricked speed field (lazy)
-    void* tile_maxF = nullptr;    // per-tile max |F| (lazy)
-    uint8_t* tile_sgn = nullptr;  // per-tile sign code of a speed field (lazy)
-    void* staging = nullptr;      // row-major staging buffer (lazy)
-    void* snapshot = nullptr;     // ls_snapshot copy of phi (lazy)
-    uint8_t* core = nullptr;
-    uint8_t* act = nullptr;
-    int* list = nullptr;
-    uint8_t* list_info = nullptr;
-    int* d_count = nullptr;
-    int* block_counts = nullptr;
-    int nblocks = 0;
-    lsk::StepScalars* d_sc = nullptr;
-    unsigned long long* d_Mbits = nullptr;
-    unsigned long long* d_updates = nullptr;
-    unsigned* d_status = nullptr;
-    unsigned* d_nonfinite = nullptr;
-    // host-side state
-    bool band_valid = false;
-    bool core_fresh = false;
-    bool full_domain = false;
-    bool have_halfwidth = false;
-    double halfwidth = 0.0;
-    int since_rebuild = 0;
-    int dt_mode = LS_DT_FIXED;
-    double dt_value = 0.0;
-    lsk::StepConfig cfg;
-    // graphs
-    bool use_graphs = false;
-    std::map<GraphKey, GraphEntry> graphs;
-    // profiling
-    unsigned long long launches = 0;
-    unsigned long long stencil_launches = 0;
-    bool profiling = false;
-    double stencil_ms = 0.0;
-    unsigned long long stencil_timed = 0;
-    std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
-
-    Inst& in0() { return insts[0]; }
-    const Inst* dinst() const { return batched ? d_inst : nullptr; }
-    const uint16_t* tinst() const { return batched ? d_tile_inst : nullptr; }
-};
 
 namespace {
 
@@ -219,6 +137,8 @@ void free_all(ls_ctx* c)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    if (c->learned) lsk::learned_free(c->learned);
+    c->learned = nullptr;
 }
 
 size_t grid_bytes(const ls_ctx* c) { return c->npts * c->esize; }
@@ -386,8 +306,10 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
                                          c->d_Mbits, nullptr, 0, s));
         }
         dt_pending = false;
+        // the fused tube test sees the plain step's values; with the learned
+        // correction applied afterwards the rebuild classifies again instead
         const bool classify = !c->full_domain && rebuild_every > 0 &&
-                              c->since_rebuild + 1 >= rebuild_every;
+                              c->since_rebuild + 1 >= rebuild_every && c->step_mode == LS_PLAIN;
         const lsk::StepArgs a = step_args(c, classify);
         if (c->profiling && c->ev_pending.size() >= 4096) RET(drain_events(c));
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -402,6 +324,7 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
             CK(cudaEventRecord(e1, s));
             c->ev_pending.emplace_back(e0, e1);
         }
+        if (c->step_mode == LS_LEARNED) RET(ls_engine_learned_after_step(c, s));
         c->cur ^= 1;
         c->since_rebuild += 1;
         c->core_fresh = classify;
@@ -445,7 +368,7 @@ int run_steps_graph(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuil
     long long vbits = 0;
     std::memcpy(&vbits, &value, sizeof(vbits));
     const GraphKey key{c->cur, c->since_rebuild, (int)c->band_valid, (int)c->core_fresh,
-                       (int)c->full_domain, nsteps, rebuild_every, dt_mode, vbits, c->cfg.stages,
+                       (int)c->full_domain | (c->step_mode << 1), nsteps, rebuild_every, dt_mode, vbits, c->cfg.stages,
                        c->cfg.grid_pct};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
@@ -656,6 +579,13 @@ int fetch_list(ls_ctx* c, std::vector<int>& ids)
 }
 
 }  // namespace
+
+int ls_engine_cuda_fail(cudaError_t e) { return cuda_fail(e); }
+
+int ls_engine_pack(ls_ctx* c, const Inst& in, const void* src, int on_device, void* dst)
+{
+    return pack_from(c, in, src, on_device, dst);
+}
 
 extern "C" {
 

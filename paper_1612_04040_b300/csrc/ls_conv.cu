@@ -1,0 +1,394 @@
+// ls_conv.cu -- 3x3x3 convolution (16 -> 16 channels, zero padding) as an
+// implicit GEMM on the 5th-generation tensor cores (tcgen05), for the learned
+// coarse-grid corrector.  This part is not in the paper.
+//
+// Data: activations are BF16, channels-last act[(z*ny + y)*nx + x][16]; the
+// GEMM for one output point m and one tap t is  D[m][n] += sum_k
+// X[m + off(t)][k] * W[t][k][n]  with K = N = 16 channels, accumulated in FP32
+// over the 27 taps.
+//
+// One CTA (128 threads) handles a block of BY x BZ output x-rows of 128
+// points (x0..x0+127).  The TMA engine loads the halo'd input block
+// (130 x (BY+2) x (BZ+2) points x 16 channels) as two 4-D boxes (8 channels,
+// x, y, z), one per half of the channels (the second tensor map starts 16
+// bytes into the activations), so shared memory holds
+// X_s[half][z][y][x][8]: every run of 8 consecutive
+// points x 8 channels is one contiguous 128-byte "core matrix" of the
+// canonical no-swizzle K-major operand layout.  The A operand of any tap is
+// then just a descriptor whose start address is shifted by the tap's offset
+// (SBO = 128 B between 8-point groups, LBO = one channel-half plane): no
+// im2col copy.  Points outside the grid are zero-filled by the TMA (zero
+// padding for free).  Weights are packed once per launch into the B layout.
+// Each M-tile (one x-row) accumulates its 27 MMAs (M=128, N=16, K=16) in its
+// own 16 TMEM columns; the epilogue reads TMEM with tcgen05.ld (warp w owns
+// lanes 32w..32w+31 = points x0+32w..) and applies bias + ReLU, bias only
+// (last layer), or the ReLU mask of the backward pass.
+//
+// Every wait on an mbarrier is bounded; on timeout the kernel records
+// ST_TIMEOUT in the status word, stops issuing work, frees its TMEM and
+// returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "ls.h"
+#include "ls_internal.cuh"
+
+namespace lsk {
+
+namespace {
+
+constexpr int CX = 128;            // output points per x-row tile (= MMA M)
+constexpr int BY = 2, BZ = 2;      // x-rows per block in y and z
+constexpr int PX = CX + 2, PY = BY + 2, PZ = BZ + 2;
+constexpr int PB = PX * PY * PZ;   // points in the halo'd block
+constexpr int HALF_BYTES = PB * 16;
+constexpr int XS_BYTES = 2 * HALF_BYTES;
+constexpr int W_BYTES = 27 * 512;  // 27 taps x (16 x 16 bf16)
+constexpr int MT = BY * BZ;        // M-tiles per block
+constexpr int TMEM_COLS = 64;      // MT * 16, rounded to a power of two >= 32
+constexpr long long WAIT_LIMIT = 1ll << 26;
+
+static_assert(MT * 16 <= TMEM_COLS, "TMEM columns");
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait for the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+        unsigned ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "  selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// shared-memory matrix descriptor, no swizzle (canonical K-major layout):
+// start address, leading (K-direction) and stride (M/N-direction) byte
+// offsets of the 8-row x 16-byte core matrices
+__device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr & 0x3FFFFu) >> 4);
+    d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;  // descriptor version for this architecture
+    return d;         // base offset 0, swizzle mode 0 (none)
+}
+
+// instruction descriptor, kind::f16: D F32, A and B BF16, both K-major,
+// N = 16, M = 128
+constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(unsigned d_tmem, unsigned long long a, unsigned long long b,
+                                         unsigned accumulate)
+{
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+        "  tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16])
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+struct ConvArgs {
+    const __nv_bfloat16* wpack;  // packed B operand, 27 x 512 bytes
+    const float* bias;           // 16 (fwd modes) or NULL
+    const __nv_bfloat16* mask;   // backward mode: forward activation of the input layer
+    __nv_bfloat16* out_bf16;     // hidden / backward modes: [p][16]
+    float* out_f32;              // last-layer mode: [p] (channel 0)
+    unsigned* status;
+    int nx, ny, nz;
+    int mode;                    // 0 bias+ReLU, 1 bias (channel 0, FP32), 2 ReLU mask
+};
+
+__global__ void __launch_bounds__(128, 1) k_conv3_tc(const __grid_constant__ CUtensorMap map0,
+                                                     const __grid_constant__ CUtensorMap map1,
+                                                     ConvArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* xs = smem;                     // X block, XS_BYTES
+    unsigned char* ws = smem + XS_BYTES;          // packed weights, W_BYTES
+    __shared__ __align__(8) unsigned long long tma_bar, mma_bar;
+    __shared__ unsigned tmem_base_s;
+    __shared__ int abort_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // weights -> shared memory (generic proxy), then make them visible to the
+    // tensor core's async proxy
+    for (int i = tid; i < W_BYTES / 16; i += 128)
+        reinterpret_cast<uint4*>(ws)[i] = reinterpret_cast<const uint4*>(a.wpack)[i];
+    if (tid == 0) {
+        mbar_init(&tma_bar, 1);
+        mbar_init(&mma_bar, 1);
+        abort_s = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_s)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = tmem_base_s;
+
+    const int nbx = a.nx / CX, nby = a.ny / BY, nbz = a.nz / BZ;
+    const int nblocks = nbx * nby * nbz;
+    unsigned phase = 0;
+    const unsigned xs_addr = smem_u32(xs), ws_addr = smem_u32(ws);
+    for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        const int bx = blk % nbx;
+        const int by = (blk / nbx) % nby;
+        const int bz = blk / (nbx * nby);
+        const int x0 = bx * CX, y0 = by * BY, z0 = bz * BZ;
+        if (tid == 0) {
+            mbar_expect_tx(&tma_bar, XS_BYTES);
+            tma_load_4d(xs, &map0, 0, x0 - 1, y0 - 1, z0 - 1, &tma_bar);
+            tma_load_4d(xs + HALF_BYTES, &map1, 0, x0 - 1, y0 - 1, z0 - 1, &tma_bar);
+        }
+        if (!mbar_wait(&tma_bar, phase)) {
+            if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+            abort_s = 1;
+        }
+        __syncthreads();
+        if (abort_s) break;
+        if (tid == 0) {
+            fence_after();
+            for (int j = 0; j < MT; ++j) {
+                const int jy = j % BY, jz = j / BY;
+                for (int t = 0; t < 27; ++t) {
+                    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+                    const int p = ((jz + 1 + dz) * PY + (jy + 1 + dy)) * PX + (1 + dx);
+                    const unsigned long long ad = smem_desc(xs_addr + p * 16, HALF_BYTES, 128);
+                    const unsigned long long bd = smem_desc(ws_addr + t * 512, 256, 128);
+                    mma_bf16(tmem + 16 * j, ad, bd, t > 0 ? 1u : 0u);
+                }
+            }
+            mma_commit(&mma_bar);
+        }
+        if (!mbar_wait(&mma_bar, phase)) {
+            if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+            abort_s = 2;
+        }
+        __syncthreads();
+        if (abort_s) {
+            // MMAs may still be in flight: give them one more bounded wait
+            // before the TMEM is released
+            mbar_wait(&mma_bar, phase);
+            break;
+        }
+        fence_after();
+        // epilogue: warp w reads TMEM lanes 32w.. = points x0 + 32w + lane
+        const int x = x0 + 32 * warp + lane;
+        for (int j = 0; j < MT; ++j) {
+            const int y = y0 + j % BY, z = z0 + j / BY;
+            float v[16];
+            tmem_ld16(tmem + ((unsigned)(32 * warp) << 16) + 16 * j, v);
+            const size_t p = ((size_t)z * a.ny + y) * a.nx + x;
+            if (a.mode == 1) {
+                a.out_f32[p] = v[0] + a.bias[0];
+                continue;
+            }
+            if (a.mode == 0) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + a.bias[c], 0.f);
+            } else {
+                const uint4* mp = reinterpret_cast<const uint4*>(a.mask + p * 16);
+                const uint4 m0 = mp[0], m1 = mp[1];
+                const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
+                const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if (!(__bfloat162float(mb0[c]) > 0.f)) v[c] = 0.f;
+                    if (!(__bfloat162float(mb1[c]) > 0.f)) v[8 + c] = 0.f;
+                }
+            }
+            uint4 o[2];
+            __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(o);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) ob[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+            uint4* dp = reinterpret_cast<uint4*>(a.out_bf16 + p * 16);
+            dp[0] = o[0];
+            dp[1] = o[1];
+        }
+        fence_before();
+        __syncthreads();
+        phase ^= 1u;
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// pack W (FP32 [27][ci][co], ci, co <= 16) into the canonical K-major B
+// layout per tap: [kb][nb][8 n][8 k] bf16, B[n][k] = W[t][k][n].  flip: the
+// backward-data operator, B[n][k] = W[26 - t][n][k] (taps mirrored, channels
+// swapped).  Missing channels are zero.
+__global__ void k_pack_weights(const float* __restrict__ W, int ci, int co, int flip,
+                               __nv_bfloat16* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 27*256 entries
+    if (i >= 27 * 256) return;
+    const int t = i / 256, r = i % 256;
+    const int kb = r / 128, nb = (r / 64) % 2, n8 = (r / 8) % 8, k8 = r % 8;
+    const int n = nb * 8 + n8, k = kb * 8 + k8;
+    float v = 0.f;
+    if (!flip) {
+        if (k < ci && n < co) v = W[((size_t)t * ci + k) * co + n];
+    } else {
+        // forward weights W[t][c][o] with c < ci, o < co; here k = o, n = c
+        if (n < ci && k < co) v = W[((size_t)(26 - t) * ci + n) * co + k];
+    }
+    out[i] = __float2bfloat16_rn(v);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+}  // namespace
+
+bool conv3_shape_ok(int nx, int ny, int nz)
+{
+    return nx >= CX && nx % CX == 0 && ny % BY == 0 && nz % BZ == 0 && ny >= BY && nz >= BZ;
+}
+
+// tensor maps over act[nz][ny][nx][16] bf16 viewed as (8 channels, x, y, z):
+// map[h] covers channels 8h..8h+7 (base address + 16 h bytes)
+cudaError_t make_act_maps(CUtensorMap* maps, const void* act, int nx, int ny, int nz)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    if (((uintptr_t)act & 15u) != 0) return cudaErrorInvalidValue;
+    const cuuint64_t dims[4] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[3] = {32, (cuuint64_t)32 * nx, (cuuint64_t)32 * nx * ny};
+    const cuuint32_t box[4] = {8, PX, PY, PZ};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int h = 0; h < 2; ++h) {
+        CUresult r = fn(&maps[h], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
+                        (void*)((const char*)act + 16 * h), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_pack_weights(const float* W, int ci, int co, int flip, void* out, cudaStream_t s)
+{
+    k_pack_weights<<<(27 * 256 + 255) / 256, 256, 0, s>>>(W, ci, co, flip, (__nv_bfloat16*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float* bias,
+                         const void* mask, void* out_bf16, float* out_f32, int nx, int ny, int nz,
+                         int mode, unsigned* status, cudaStream_t s)
+{
+    static bool attr = false;
+    const int smem = XS_BYTES + W_BYTES;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    ConvArgs a;
+    a.wpack = (const __nv_bfloat16*)wpack;
+    a.bias = bias;
+    a.mask = (const __nv_bfloat16*)mask;
+    a.out_bf16 = (__nv_bfloat16*)out_bf16;
+    a.out_f32 = out_f32;
+    a.status = status;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.mode = mode;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nblocks = (nx / CX) * (ny / BY) * (nz / BZ);
+    int grid = 2 * sms;
+    if (grid > nblocks) grid = nblocks;
+    k_conv3_tc<<<grid, 128, smem, s>>>(maps[0], maps[1], a);
+    return cudaGetLastError();
+}
+
+}  // namespace lsk

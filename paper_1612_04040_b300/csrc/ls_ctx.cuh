@@ -1,0 +1,111 @@
+// ls_ctx.cuh -- the context object behind the C ABI (host engine state and
+// device buffers), shared by the engine (ls_api.cu) and the learned
+// corrector's engine (ls_learned_api.cu).
+#pragma once
+
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "ls.h"
+#include "ls_internal.cuh"
+
+using lsk::Inst;
+
+namespace lsk {
+struct Learned;  // corrector state (ls_learned_api.cu)
+void learned_free(Learned* L);
+}  // namespace lsk
+
+namespace lsk {
+
+// host state a captured ls_step graph starts from / leaves behind
+struct SchedState {
+    int cur = 0;
+    int since_rebuild = 0;
+    bool band_valid = false;
+    bool core_fresh = false;
+};
+
+using GraphKey = std::tuple<int, int, int, int, int, int, int, int, long long, int, int>;
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    SchedState after;
+    unsigned long long launches = 0;
+    unsigned long long stencil_launches = 0;
+};
+
+}  // namespace lsk
+
+struct ls_ctx {
+    int prec = 0;
+    size_t esize = 4;
+    bool batched = false;
+    int n_inst = 1;
+    std::vector<Inst> insts;      // host copy of the per-instance parameters
+    std::vector<char> inst_phi_set;
+    Inst* d_inst = nullptr;       // device copy (batched contexts)
+    uint16_t* d_tile_inst = nullptr;  // instance of every global tile (batched)
+    uint16_t* d_list_inst = nullptr;  // instance of every list entry (batched)
+    int* d_inst_count = nullptr;      // per-instance active counts (batched)
+    long long ntiles = 0;
+    size_t npts = 0;
+    size_t max_inst_pts = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;  // used for graph capture when stream is NULL
+    void* phi[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* F = nullptr;            // bricked speed field (lazy)
+    void* tile_maxF = nullptr;    // per-tile max |F| (lazy)
+    uint8_t* tile_sgn = nullptr;  // per-tile sign code of a speed field (lazy)
+    void* staging = nullptr;      // row-major staging buffer (lazy)
+    void* snapshot = nullptr;     // ls_snapshot copy of phi (lazy)
+    uint8_t* core = nullptr;
+    uint8_t* act = nullptr;
+    int* list = nullptr;
+    uint8_t* list_info = nullptr;
+    int* d_count = nullptr;
+    int* block_counts = nullptr;
+    int nblocks = 0;
+    lsk::StepScalars* d_sc = nullptr;
+    unsigned long long* d_Mbits = nullptr;
+    unsigned long long* d_updates = nullptr;
+    unsigned* d_status = nullptr;
+    unsigned* d_nonfinite = nullptr;
+    // host-side state
+    bool band_valid = false;
+    bool core_fresh = false;
+    bool full_domain = false;
+    bool have_halfwidth = false;
+    double halfwidth = 0.0;
+    int since_rebuild = 0;
+    int dt_mode = LS_DT_FIXED;
+    double dt_value = 0.0;
+    lsk::StepConfig cfg;
+    // graphs
+    bool use_graphs = false;
+    std::map<lsk::GraphKey, lsk::GraphEntry> graphs;
+    // profiling
+    unsigned long long launches = 0;
+    unsigned long long stencil_launches = 0;
+    bool profiling = false;
+    double stencil_ms = 0.0;
+    unsigned long long stencil_timed = 0;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+
+    // learned corrector
+    int step_mode = LS_PLAIN;
+    lsk::Learned* learned = nullptr;
+
+    Inst& in0() { return insts[0]; }
+    const Inst* dinst() const { return batched ? d_inst : nullptr; }
+    const uint16_t* tinst() const { return batched ? d_tile_inst : nullptr; }
+};
+
+
+// engine helpers used by the learned corrector's engine
+int ls_engine_cuda_fail(cudaError_t e);
+int ls_engine_pack(ls_ctx* c, const Inst& in, const void* src, int on_device, void* dst);
+int ls_engine_learned_after_step(ls_ctx* c, cudaStream_t s);

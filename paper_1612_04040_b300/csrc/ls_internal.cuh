@@ -10,6 +10,7 @@
 // the device by the pack / unpack kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -148,5 +149,32 @@ cudaError_t launch_scatter_batch(const uint8_t* act, const int* block_offsets, i
 cudaError_t launch_set_dt_batch(StepScalars* sc, int n_inst, const Inst* d_inst, int mode,
                                 double value, int finalize, int prec, unsigned long long* Mbits,
                                 int* inst_count, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// learned corrector (ls_conv.cu, ls_learned.cu)
+// ---------------------------------------------------------------------------
+bool conv3_shape_ok(int nx, int ny, int nz);
+cudaError_t make_act_maps(CUtensorMap* maps, const void* act, int nx, int ny, int nz);
+cudaError_t launch_pack_weights(const float* W, int ci, int co, int flip, void* out, cudaStream_t s);
+// mode 0: out_bf16 = relu(conv + b); 1: out_f32 = (conv + b) channel 0;
+// 2: out_bf16 = conv(x) * [mask > 0] (x: gradient, weights packed flipped)
+cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float* bias,
+                         const void* mask, void* out_bf16, float* out_f32, int nx, int ny, int nz,
+                         int mode, unsigned* status, cudaStream_t s);
+cudaError_t launch_features(const float* phi, const float* phit, const float* F, float Fc,
+                            float inv_h, long long n, void* X, cudaStream_t s);
+cudaError_t launch_count_mask(const float* phi, float gamma, long long n, int* count, cudaStream_t s);
+cudaError_t launch_loss_grad(const float* z, const float* phi, const float* phit,
+                             const float* phiref, float inv_h, float gamma, const int* count,
+                             long long n, void* dz, double* loss, cudaStream_t s);
+cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci,
+                               int co, float* dW, float* db, cudaStream_t s);
+cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, float lr, int step,
+                        cudaStream_t s);
+cudaError_t launch_residual(float* phit, const float* z, const int* list, const int* count,
+                            const Inst& in, const StepScalars* sc, float hc, unsigned* flag,
+                            unsigned long long* fallbacks, cudaStream_t s);
+cudaError_t launch_restrict4(const float* fine, int nfx, int nfy, int nfz, float* coarse,
+                             cudaStream_t s);
 
 }  // namespace lsk

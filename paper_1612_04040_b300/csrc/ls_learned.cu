@@ -1,0 +1,312 @@
+// ls_learned.cu -- the learned coarse-grid corrector's non-convolution
+// kernels (not in the paper): feature assembly, loss and its gradient,
+// weight / bias gradients of a 3x3x3 convolution, Adam, the band-residual
+// check with plain-step fallback, and the fine -> coarse restriction.
+//
+// Corrector: z = CNN(features), phi^{n+1} = phi~ + h * z on band points,
+// where phi~ = the plain upwind step (Eq. 3) of phi^n and the features are
+// [clamp(phi^n / h, +-8), F, (phi~ - phi^n) / h] (BF16, channels-last, padded
+// to 16 channels).  The check rejects the correction of a step (keeping phi~)
+// if any corrected band value is not finite or |h z| exceeds one plain step's
+// motion dt * max|F|.
+#include <cuda_bf16.h>
+
+#include "ls_internal.cuh"
+
+namespace lsk {
+
+namespace {
+
+__device__ __forceinline__ size_t rm_index(int x, int y, int z, int nx, int ny)
+{
+    return ((size_t)z * ny + y) * nx + x;
+}
+
+// row-major features from row-major phi^n, phi~ and F (field or constant)
+__global__ void k_features(const float* __restrict__ phi, const float* __restrict__ phit,
+                           const float* __restrict__ F, float Fc, float inv_h, long long n,
+                           __nv_bfloat16* __restrict__ X)
+{
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const float a = phi[p];
+        const float f = F ? F[p] : Fc;
+        const float c0 = fminf(fmaxf(a * inv_h, -8.f), 8.f);
+        const float c2 = (phit[p] - a) * inv_h;
+        uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(o);
+        ob[0] = __float2bfloat16_rn(c0);
+        ob[1] = __float2bfloat16_rn(f);
+        ob[2] = __float2bfloat16_rn(c2);
+        uint4* d = reinterpret_cast<uint4*>(X + p * 16);
+        d[0] = o[0];
+        d[1] = o[1];
+    }
+}
+
+// loss = sum over masked points of (z - t)^2 / count;  dz = 2 (z - t) / count
+// on masked points (channel 0 of a 16-channel BF16 gradient), 0 elsewhere.
+// mask: |phi^n| < gamma (the tube of Eq. 6).  target t = (phi_ref - phi~) / h.
+__global__ void k_loss_grad(const float* __restrict__ z, const float* __restrict__ phi,
+                            const float* __restrict__ phit, const float* __restrict__ phiref,
+                            float inv_h, float gamma, const int* __restrict__ count, long long n,
+                            __nv_bfloat16* __restrict__ dz, double* loss)
+{
+    double local = 0.0;
+    const float inv_cnt = 1.f / fmaxf((float)*count, 1.f);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        float g = 0.f;
+        if (fabsf(phi[p]) < gamma) {
+            const float t = (phiref[p] - phit[p]) * inv_h;
+            const float r = z[p] - t;
+            local += (double)r * r * inv_cnt;
+            g = 2.f * r * inv_cnt;
+        }
+        uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        reinterpret_cast<__nv_bfloat16*>(o)[0] = __float2bfloat16_rn(g);
+        uint4* d = reinterpret_cast<uint4*>(dz + p * 16);
+        d[0] = o[0];
+        d[1] = o[1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local != 0.0) atomicAdd(loss, local);
+}
+
+__global__ void k_count_mask(const float* __restrict__ phi, float gamma, long long n, int* count)
+{
+    int local = 0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        local += fabsf(phi[p]) < gamma;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
+}
+
+// Weight and bias gradients of a 3x3x3 convolution on CUDA cores (FP32):
+// dW[t][c][o] = sum_p x[p + off(t)][c] * dy[p][o],  db[o] = sum_p dy[p][o].
+// One block per chunk of 64 consecutive x points of one (y, z) row; the input
+// rows (x0-1 .. x0+64) of the 9 (y, z) neighbours and the dy row are staged in
+// shared memory as FP32; thread (t, cb, ob) accumulates a 4x4 block of
+// (c, o) for tap t over the chunk, then adds it to dW with atomics.
+constexpr int WG_X = 64;
+__global__ void __launch_bounds__(448) k_conv3_wgrad(const __nv_bfloat16* __restrict__ x,
+                                                     const __nv_bfloat16* __restrict__ dy,
+                                                     int nx, int ny, int nz, int ci, int co,
+                                                     float* dW, float* db)
+{
+    __shared__ float xs[9][WG_X + 2][16];
+    __shared__ float gs[WG_X][16];
+    const int nchunks = nx / WG_X;
+    const long long nblk = (long long)nchunks * ny * nz;
+    const int tid = threadIdx.x;
+    const int t = tid / 16, cb = (tid % 16) / 4, ob = tid % 4;  // tid < 432
+    float acc[4][4] = {};
+    float bacc = 0.f;
+    for (long long b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int cx = (int)(b % nchunks);
+        const int y = (int)((b / nchunks) % ny);
+        const int z = (int)(b / ((long long)nchunks * ny));
+        const int x0 = cx * WG_X;
+        __syncthreads();
+        for (int i = tid; i < 9 * (WG_X + 2) * 16; i += blockDim.x) {
+            const int c = i % 16, xi = (i / 16) % (WG_X + 2), r = i / (16 * (WG_X + 2));
+            const int yy = y + r % 3 - 1, zz = z + r / 3 - 1, xx = x0 + xi - 1;
+            float v = 0.f;
+            if (xx >= 0 && xx < nx && yy >= 0 && yy < ny && zz >= 0 && zz < nz)
+                v = __bfloat162float(x[rm_index(xx, yy, zz, nx, ny) * 16 + c]);
+            xs[r][xi][c] = v;
+        }
+        for (int i = tid; i < WG_X * 16; i += blockDim.x) {
+            const int c = i % 16, xi = i / 16;
+            gs[xi][c] = __bfloat162float(dy[rm_index(x0 + xi, y, z, nx, ny) * 16 + c]);
+        }
+        __syncthreads();
+        if (t < 27) {
+            const int dx = t % 3 - 1, r = (t / 3);  // r = (dz+1)*3 + (dy+1)
+            for (int xi = 0; xi < WG_X; ++xi) {
+                const float* xr = &xs[r][xi + 1 + dx][4 * cb];
+                const float* gr = &gs[xi][4 * ob];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xr[i], gr[j], acc[i][j]);
+            }
+        } else if (tid < 432 + 16) {
+            const int o = tid - 432;
+            for (int xi = 0; xi < WG_X; ++xi) bacc += gs[xi][o];
+        }
+    }
+    if (t < 27) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = 4 * cb + i, o = 4 * ob + j;
+                if (c < ci && o < co && acc[i][j] != 0.f)
+                    atomicAdd(&dW[((size_t)t * ci + c) * co + o], acc[i][j]);
+            }
+    } else if (tid < 432 + 16 && db) {
+        const int o = tid - 432;
+        if (o < co && bacc != 0.f) atomicAdd(&db[o], bacc);
+    }
+}
+
+// Adam (decoupled moments, bias-corrected) on a flat parameter vector
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// band-residual check: over the points of active tiles, flag[0] |= the
+// corrected value h z is not finite or exceeds bound = dt * M (one plain
+// step's motion).  phit is bricked; z is row-major.
+__global__ void k_residual_check(const float* __restrict__ z, const int* __restrict__ list,
+                                 const int* __restrict__ count, Inst in, const StepScalars* sc,
+                                 float hc, unsigned* flag)
+{
+    const int n = *count;
+    const double bound = sc->dt * sc->M;
+    const int tid = threadIdx.x;
+    const int lx = tid & 7, ly = (tid >> 3) & 7, lz0 = tid >> 6;  // 128 threads, 2 z per pass
+    bool bad = false;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int t = list[k];
+        const int tpl = in.tnx * in.tny;
+        const int tz = t / tpl, r = t - tz * tpl, ty = r / in.tnx, tx = r - ty * in.tnx;
+        for (int lz = lz0; lz < 8; lz += 2) {
+            const float c = hc * z[rm_index(tx * 8 + lx, ty * 8 + ly, tz * 8 + lz, in.nx, in.ny)];
+            if (!isfinite(c) || fabs((double)c) > bound) bad = true;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(flag, 1u);
+}
+
+// apply phi~ += h z on the active tiles unless the check failed; count the
+// fallbacks (flag is cleared by the last block of the next check round)
+__global__ void k_residual_apply(float* __restrict__ phit, const float* __restrict__ z,
+                                 const int* __restrict__ list, const int* __restrict__ count,
+                                 Inst in, float hc, const unsigned* flag)
+{
+    if (*flag) return;
+    const int n = *count;
+    const int tid = threadIdx.x;
+    const int lx = tid & 7, ly = (tid >> 3) & 7, lz0 = tid >> 6;
+    for (int k = blockIdx.x; k < n; k += gridDim.x) {
+        const int t = list[k];
+        const int tpl = in.tnx * in.tny;
+        const int tz = t / tpl, r = t - tz * tpl, ty = r / in.tnx, tx = r - ty * in.tnx;
+        for (int lz = lz0; lz < 8; lz += 2) {
+            const float c = hc * z[rm_index(tx * 8 + lx, ty * 8 + ly, tz * 8 + lz, in.nx, in.ny)];
+            phit[(size_t)t * TILE_PTS + (lz * 8 + ly) * 8 + lx] += c;
+        }
+    }
+}
+
+__global__ void k_flag_account(unsigned* flag, unsigned long long* fallbacks)
+{
+    if (*flag) atomicAdd(fallbacks, 1ull);
+    *flag = 0;
+}
+
+// fine (row-major) -> coarse (row-major), factor 4: mean of the fine points
+// 4I+1, 4I+2 per axis (the trilinear value at the coarse cell centre)
+__global__ void k_restrict4(const float* __restrict__ fine, int nfx, int nfy, int nfz,
+                            float* __restrict__ coarse)
+{
+    const int ncx = nfx / 4, ncy = nfy / 4, ncz = nfz / 4;
+    const long long n = (long long)ncx * ncy * ncz;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int X = (int)(p % ncx), Y = (int)((p / ncx) % ncy), Z = (int)(p / ((long long)ncx * ncy));
+        float s = 0.f;
+        for (int k = 1; k <= 2; ++k)
+            for (int j = 1; j <= 2; ++j)
+                for (int i = 1; i <= 2; ++i)
+                    s += fine[rm_index(4 * X + i, 4 * Y + j, 4 * Z + k, nfx, nfy)];
+        coarse[p] = s * 0.125f;
+    }
+}
+
+int grid_for(long long n, int threads)
+{
+    long long g = (n + threads - 1) / threads;
+    if (g > 148 * 16) g = 148 * 16;
+    return (int)(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_features(const float* phi, const float* phit, const float* F, float Fc,
+                            float inv_h, long long n, void* X, cudaStream_t s)
+{
+    k_features<<<grid_for(n, 256), 256, 0, s>>>(phi, phit, F, Fc, inv_h, n, (__nv_bfloat16*)X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_mask(const float* phi, float gamma, long long n, int* count, cudaStream_t s)
+{
+    k_count_mask<<<grid_for(n, 256), 256, 0, s>>>(phi, gamma, n, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss_grad(const float* z, const float* phi, const float* phit,
+                             const float* phiref, float inv_h, float gamma, const int* count,
+                             long long n, void* dz, double* loss, cudaStream_t s)
+{
+    k_loss_grad<<<grid_for(n, 256), 256, 0, s>>>(z, phi, phit, phiref, inv_h, gamma, count, n,
+                                                 (__nv_bfloat16*)dz, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci,
+                               int co, float* dW, float* db, cudaStream_t s)
+{
+    if (nx % WG_X) return cudaErrorInvalidValue;
+    const long long nblk = (long long)(nx / WG_X) * ny * nz;
+    long long g = nblk < 148 * 4 ? nblk : 148 * 4;
+    k_conv3_wgrad<<<(int)g, 448, 0, s>>>((const __nv_bfloat16*)x, (const __nv_bfloat16*)dy, nx, ny,
+                                         nz, ci, co, dW, db);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, float lr, int step,
+                        cudaStream_t s)
+{
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    k_adam<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, lr, b1, b2, 1e-8f, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(float* phit, const float* z, const int* list, const int* count,
+                            const Inst& in, const StepScalars* sc, float hc, unsigned* flag,
+                            unsigned long long* fallbacks, cudaStream_t s)
+{
+    const int g = 148 * 8;
+    k_residual_check<<<g, 128, 0, s>>>(z, list, count, in, sc, hc, flag);
+    k_residual_apply<<<g, 128, 0, s>>>(phit, z, list, count, in, hc, flag);
+    k_flag_account<<<1, 1, 0, s>>>(flag, fallbacks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict4(const float* fine, int nfx, int nfy, int nfz, float* coarse,
+                             cudaStream_t s)
+{
+    const long long n = (long long)(nfx / 4) * (nfy / 4) * (nfz / 4);
+    k_restrict4<<<grid_for(n, 256), 256, 0, s>>>(fine, nfx, nfy, nfz, coarse);
+    return cudaGetLastError();
+}
+
+}  // namespace lsk

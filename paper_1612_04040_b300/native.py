@@ -62,6 +62,18 @@ SIGNATURES = {
     "ls_inst_get_phi": (_i, [_vp, _i, _vp, _i]),
     "ls_inst_get_active_tiles": (_i, [_vp, _i, _c.POINTER(_c.c_int), _ll, _c.POINTER(_ll)]),
     "ls_inst_last_dt": (_i, [_vp, _i, _c.POINTER(_d)]),
+    "ls_learned_num_params": (_i, [_c.POINTER(_ll)]),
+    "ls_learned_init": (_i, [_vp, _c.c_ulonglong]),
+    "ls_learned_set_params": (_i, [_vp, _vp, _ll]),
+    "ls_learned_get_params": (_i, [_vp, _vp, _ll]),
+    "ls_learned_add_pair": (_i, [_vp, _vp, _vp, _vp, _i]),
+    "ls_learned_num_pairs": (_i, [_vp, _c.POINTER(_ll)]),
+    "ls_learned_train": (_i, [_vp, _i, _d, _d, _d, _c.c_ulonglong, _c.POINTER(_d)]),
+    "ls_set_step_mode": (_i, [_vp, _i]),
+    "ls_learned_fallbacks": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
+    "ls_conv3_bf16": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "ls_conv3_wgrad": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "ls_restrict4": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "ls_profile_enable": (_i, [_vp, _i]),
     "ls_get_profile": (_i, [_vp, _vp]),
     "ls_reset_profile": (_i, [_vp]),
@@ -159,6 +171,55 @@ def band_tiles_noalloc(phi, h, halfwidth, tiles_out, count_out, stream=None):
                                     float(halfwidth), ctypes.c_void_p(tiles_out.data_ptr()),
                                     tiles_out.numel(), ctypes.c_void_p(count_out.data_ptr()),
                                     ctypes.c_void_p(stream)), "ls_band_tiles_noalloc")
+
+
+LS_CONV3_WORK_BYTES = 13824
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def conv3_bf16(x, W, bias, mode, mask=None, out=None, stream=None):
+    """ls_conv3_bf16 on torch CUDA tensors: x bf16 (nz, ny, nx, 16), W float32
+    (27, ci, co), bias float32 (co,).  Returns (out, status word)."""
+    lib = load()
+    nz, ny, nx, _ = x.shape
+    ci, co = W.shape[1], W.shape[2]
+    if out is None:
+        out = (torch.empty((nz, ny, nx), dtype=torch.float32, device=x.device) if mode == 1
+               else torch.empty((nz, ny, nx, 16), dtype=torch.bfloat16, device=x.device))
+    work = torch.empty(LS_CONV3_WORK_BYTES, dtype=torch.uint8, device=x.device)
+    status = torch.zeros(1, dtype=torch.int32, device=x.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib.ls_conv3_bf16(_dptr(x), nx, ny, nz, _dptr(W), ci, co, _dptr(bias), int(mode), _dptr(mask),
+                            _dptr(out), _dptr(work), _dptr(status), ctypes.c_void_p(stream)), "ls_conv3_bf16")
+    return out, status
+
+
+def conv3_wgrad(x, dy, ci, co, stream=None):
+    """ls_conv3_wgrad: returns (dW (27, ci, co), db (co,)) as float32 tensors."""
+    lib = load()
+    nz, ny, nx, _ = x.shape
+    dW = torch.zeros((27, ci, co), dtype=torch.float32, device=x.device)
+    db = torch.zeros((co,), dtype=torch.float32, device=x.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib.ls_conv3_wgrad(_dptr(x), _dptr(dy), nx, ny, nz, ci, co, _dptr(dW), _dptr(db),
+                             ctypes.c_void_p(stream)), "ls_conv3_wgrad")
+    return dW, db
+
+
+def restrict4(fine, stream=None):
+    """ls_restrict4 on a float32 CUDA tensor (nz, ny, nx)."""
+    lib = load()
+    nz, ny, nx = fine.shape
+    out = torch.empty((nz // 4, ny // 4, nx // 4), dtype=torch.float32, device=fine.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib.ls_restrict4(_dptr(fine), nx, ny, nz, _dptr(out), ctypes.c_void_p(stream)), "ls_restrict4")
+    return out
 
 
 class LevelSet:
@@ -268,6 +329,44 @@ class LevelSet:
 
     def set_step_config(self, stages, grid_pct):
         check(self.lib.ls_set_step_config(self.ctx, int(stages), int(grid_pct)), "ls_set_step_config")
+
+    # -- learned corrector --------------------------------------------------
+    def learned_init(self, seed=0):
+        check(self.lib.ls_learned_init(self.ctx, ctypes.c_ulonglong(seed)), "ls_learned_init")
+
+    def learned_params(self):
+        n = ctypes.c_longlong(0)
+        check(self.lib.ls_learned_num_params(ctypes.byref(n)), "ls_learned_num_params")
+        out = np.empty(n.value, dtype=np.float32)
+        check(self.lib.ls_learned_get_params(self.ctx, ctypes.c_void_p(out.ctypes.data), n.value),
+              "ls_learned_get_params")
+        return out
+
+    def learned_set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        check(self.lib.ls_learned_set_params(self.ctx, ctypes.c_void_p(p.ctypes.data), p.size),
+              "ls_learned_set_params")
+
+    def learned_add_pair(self, phi_n, phi_ref, F):
+        ptrs, devs = zip(*(array_ptr(a, np.float32, self.count) for a in (phi_n, phi_ref, F)))
+        if len(set(devs)) != 1:
+            raise ValueError("pair arrays must all be on the device or all on the host")
+        check(self.lib.ls_learned_add_pair(self.ctx, ptrs[0], ptrs[1], ptrs[2], devs[0]),
+              "ls_learned_add_pair")
+
+    def learned_train(self, iters, lr, dt, halfwidth, seed=0):
+        loss = ctypes.c_double(0.0)
+        check(self.lib.ls_learned_train(self.ctx, int(iters), float(lr), float(dt), float(halfwidth),
+                                        ctypes.c_ulonglong(seed), ctypes.byref(loss)), "ls_learned_train")
+        return loss.value
+
+    def set_step_mode(self, mode):
+        check(self.lib.ls_set_step_mode(self.ctx, int(mode)), "ls_set_step_mode")
+
+    def learned_fallbacks(self):
+        n = ctypes.c_ulonglong(0)
+        check(self.lib.ls_learned_fallbacks(self.ctx, ctypes.byref(n)), "ls_learned_fallbacks")
+        return n.value
 
     def profile_enable(self, on=True):
         check(self.lib.ls_profile_enable(self.ctx, int(bool(on))), "ls_profile_enable")
