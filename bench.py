@@ -58,9 +58,12 @@ def parse():
     p.add_argument("--n", type=int, default=512, help="grid edge (512 = the standard workload)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", choices=["sphere-union", "batch"], default="sphere-union",
+    p.add_argument("--workload", choices=["sphere-union", "batch", "learned"], default="sphere-union",
                    help="sphere-union: the standard 512^3 run (the default line); "
-                        "batch: 256 independent grids in one batched context")
+                        "batch: 256 independent grids in one batched context; "
+                        "learned: corrector training + learned-coarse vs plain at equal error")
+    p.add_argument("--pairs", type=int, default=2000)
+    p.add_argument("--train-iters", type=int, default=2000)
     return p.parse_args()
 
 
@@ -311,8 +314,129 @@ def run_batch(args):
     b.close()
 
 
+def restrict_to(a, factor):
+    """Mean of the 2^3 points around each coarse cell centre (evaluation only)."""
+    import torch
+    if factor == 1:
+        return a
+    lo = factor // 2 - 1
+    nz, ny, nx = a.shape
+    v = a.view(nz // factor, factor, ny // factor, factor, nx // factor, factor)
+    return v[:, lo:lo + 2, :, lo:lo + 2, :, lo:lo + 2].mean(dim=(1, 3, 5))
+
+
+def run_learned(args):
+    """Learned corrector on the 128^3 coarse grid, trained on pairs from
+    512^3 plain runs (random sphere unions, 8-mode Fourier F), judged against
+    the 512^3 plain run; plain runs at 128^3, 256^3 and 512^3 give the
+    error/wall-time curve the learned run is placed on."""
+    import numpy as np
+    import torch
+    from paper_1612_04040_b300 import corrector
+    from paper_1612_04040_b300 import native as ls
+    torch.cuda.set_device(0)
+    n_c = 128
+    h_c = 1.0 / n_c
+    cs = (n_c, n_c, n_c)
+    t0 = time.perf_counter()
+    gen = corrector.PairGenerator(cs, h_c)
+    ctx = ls.LevelSet(n_c, n_c, n_c, h_c, ls.LS_FP32)
+    ctx.learned_init(seed=1)
+    rng = np.random.default_rng(1004)
+    per_run = 50
+    runs = max(1, args.pairs // per_run)
+    for _ in range(runs):
+        c, r, m = corrector.random_problem(rng, gen.box())
+        for a, b, F in gen.run(c, r, m, per_run):
+            ctx.learned_add_pair(a, b, F)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    final = ctx.learned_train(args.train_iters, 1e-3, gen.dt_c, 6.0, seed=7)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    nsteps = 64
+    results = []
+    for k in range(2):
+        c, r, m = corrector.random_problem(np.random.default_rng(5000 + k), gen.box())
+        phi_f, F_f = gen.fields(c, r, m)
+        # reference: the 512^3 plain run (band as wide as the pair runs)
+        runs_out = {}
+        for n in (512, 256, 128):
+            f = n // n_c
+            h = 1.0 / n
+            g = ls.LevelSet(n, n, n, h, ls.LS_FP32)
+            phi = restrict_to(phi_f, 4 // f) if n < 512 else phi_f
+            F = restrict_to(F_f, 4 // f) if n < 512 else F_f
+            g.set_phi(phi.contiguous())
+            g.set_speed(F.contiguous())
+            hw = 6.0 * f
+            g.band_rebuild(hw)
+            g.step(4, 0.5 * h, ls.LS_DT_FIXED, 4)  # warm-up (first-call costs)
+            g.set_phi(phi.contiguous())
+            g.band_rebuild(hw)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.step(nsteps * f, 0.5 * h, ls.LS_DT_FIXED, 4)
+            e1.record()
+            torch.cuda.synchronize()
+            out = torch.empty_like(phi)
+            g.get_phi(out)
+            runs_out[n] = (restrict_to(out, f), e0.elapsed_time(e1))
+            g.close()
+        ref = runs_out[512][0]
+        phi0_c = restrict_to(phi_f, 4).contiguous()
+        F_c = restrict_to(F_f, 4).contiguous()
+        ctx.set_phi(phi0_c)
+        ctx.set_speed(F_c)
+        ctx.set_step_mode(ls.LS_LEARNED)
+        ctx.band_rebuild(6.0)
+        ctx.step(4, gen.dt_c, ls.LS_DT_FIXED, 4)  # warm-up
+        ctx.set_phi(phi0_c)
+        ctx.band_rebuild(6.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.step(nsteps, gen.dt_c, ls.LS_DT_FIXED, 4)
+        e1.record()
+        torch.cuda.synchronize()
+        out = torch.empty_like(phi0_c)
+        ctx.get_phi(out)
+        ctx.set_step_mode(ls.LS_PLAIN)
+        res = {"learned_128": {"err_h": corrector.front_error(out, ref, h_c), "ms": e0.elapsed_time(e1)}}
+        for n in (128, 256):
+            res["plain_%d" % n] = {"err_h": corrector.front_error(runs_out[n][0], ref, h_c),
+                                   "ms": runs_out[n][1]}
+        res["plain_512_ms"] = runs_out[512][1]
+        results.append(res)
+    # equal-error comparison: the coarsest plain resolution whose mean error is
+    # at most the learned mean error (512 = the reference itself otherwise)
+    cmp = []
+    for res in results:
+        le = res["learned_128"]["err_h"][1]
+        match = next((n for n in (128, 256) if res["plain_%d" % n]["err_h"][1] <= le), 512)
+        plain_ms = res["plain_512_ms"] if match == 512 else res["plain_%d" % match]["ms"]
+        cmp.append({"plain_resolution_at_equal_error": match,
+                    "speedup_learned_vs_plain": plain_ms / res["learned_128"]["ms"]})
+    print(json.dumps({
+        "metric": "learned-coarse vs plain at equal error", "workload": "learned corrector 128^3 / 512^3",
+        "unit": "wall-time ratio (plain at equal error / learned)", "value": float(np.mean(
+            [c["speedup_learned_vs_plain"] for c in cmp])), "higher_is_better": True,
+        "pairs": runs * per_run, "train_iters": args.train_iters, "final_loss": final,
+        "pair_generation_s": t_pairs, "training_s": t_train, "coarse_steps": nsteps,
+        "error_unit": "coarse cells h_c (max, mean of |phi - ref| within 1.5 h_c of the reference front)",
+        "problems": results, "comparison": cmp, "fallbacks": ctx.learned_fallbacks(),
+        "data": "synthetic (seeded)"}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.workload == "learned":
+        run_learned(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
