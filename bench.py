@@ -102,11 +102,15 @@ def kernel_source_hash():
 def recorded_traffic():
     """DRAM bytes per grid-point update of the step kernel from the last ncu
     capture, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "stencil_traffic.json")
+    path = os.path.join(ROOT, "profiles", "stencil_traffic.txt")
     if not os.path.exists(path):
         return None
+    d = {}
     with open(path) as f:
-        d = json.load(f)
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                d[k.strip()] = v.strip()
     if d.get("ls_step_cu_sha256_16") != kernel_source_hash():
         return None
     return float(d["dram_bytes_per_update"])
