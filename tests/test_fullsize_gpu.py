@@ -1,0 +1,173 @@
+"""Parity at the standard workloads' full sizes, in the launch configuration
+the benchmark times.  The oracle cannot run these grids end to end, so the
+checks are (a) one step of Eq. 3-5 recomputed by the oracle on sampled tiles
+of the GPU's own state (each sampled tile with its one-cell halo, clipped at
+the domain faces so the face rule applies there), within 1e-5 h for FP32
+and bit for bit for FP64; (b) frozen points unchanged; (c) the band
+rebuilt from that state equals the oracle's tube test + dilation of it."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1612_04040_b300 import inputs
+from paper_1612_04040_b300 import native as ls
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(cuda_ok):
+    ls.load()
+
+
+def tile_block(a, tz, ty, tx):
+    """Tile (tz, ty, tx) of a (nz, ny, nx) tensor with a one-cell halo,
+    clipped to the domain; returns (block, offsets of the tile inside it)."""
+    nz, ny, nx = a.shape
+    lo = [max(0, 8 * t - 1) for t in (tz, ty, tx)]
+    hi = [min(n, 8 * t + 9) for t, n in zip((tz, ty, tx), (nz, ny, nx))]
+    blk = a[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+    return blk, [8 * t - l for t, l in zip((tz, ty, tx), lo)]
+
+
+def check_sampled_step(before, after, F, Fc, h, dt, tiles, tshape, ntiles_sample, seed, exact,
+                       band=None):
+    """before/after: device tensors (nz, ny, nx); F: device tensor or None.
+    band: compare only points with |phi| < band (full-domain FP32 runs, where
+    far from the front |phi| ~ 1 and one FP32 ulp exceeds the band bar)."""
+    tnz, tny, tnx = tshape
+    g = np.random.default_rng(seed)
+    pick = g.choice(tiles, size=min(ntiles_sample, len(tiles)), replace=False)
+    # always include tiles touching the domain faces if there are any
+    edge = [t for t in tiles if (t % tnx in (0, tnx - 1)) or ((t // tnx) % tny in (0, tny - 1))
+            or (t // (tnx * tny) in (0, tnz - 1))]
+    pick = np.unique(np.concatenate([pick, np.asarray(edge[:16], dtype=pick.dtype)]))
+    worst = 0.0
+    for t in pick:
+        tz, ty, tx = int(t) // (tnx * tny), (int(t) // tnx) % tny, int(t) % tnx
+        blk, o = tile_block(before, tz, ty, tx)
+        b = blk.double().cpu().numpy()
+        Fb = None if F is None else tile_block(F, tz, ty, tx)[0].double().cpu().numpy()
+        ref = oracle.step(b, h, dt, F=Fb, Fc=Fc)[o[0]:o[0] + 8, o[1]:o[1] + 8, o[2]:o[2] + 8]
+        got = after[8 * tz:8 * tz + 8, 8 * ty:8 * ty + 8, 8 * tx:8 * tx + 8].double().cpu().numpy()
+        if exact:
+            assert np.array_equal(got.view(np.int64), ref.view(np.int64)), int(t)
+        else:
+            d = np.abs(got - ref)
+            if band is not None:
+                near = np.abs(b[o[0]:o[0] + 8, o[1]:o[1] + 8, o[2]:o[2] + 8]) < band
+                d = d[near] if near.any() else np.zeros(1)
+            worst = max(worst, float(np.max(d)))
+    return worst
+
+
+def band_from(state, gamma):
+    core = oracle.classify(state.double().cpu().numpy(), gamma)
+    return oracle.compact(oracle.dilate(core, 26))
+
+
+def test_sphere_union_512():
+    """512^3 FP32, 20 spheres, sinusoidal F, band 6h, rebuild every 5, CFL 0.5."""
+    w = inputs.SphereUnion()
+    dev = torch.device("cuda")
+    phi0 = w.phi(device=dev).to(torch.float32).contiguous()
+    F = w.speed(device=dev).to(torch.float32).contiguous()
+    g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32)
+    g.set_speed(F)
+    g.set_phi(phi0)
+    g.band_rebuild(w.halfwidth)
+    g.step(23, w.cfl, ls.LS_DT_CFL, w.rebuild_every)   # since the last rebuild: 3 steps
+    before = torch.empty_like(phi0)
+    g.get_phi(before)
+    tiles = g.active_tiles()
+    dt = g.step(1, w.cfl, ls.LS_DT_CFL, w.rebuild_every, want_dt=True)
+    after = torch.empty_like(phi0)
+    g.get_phi(after)
+    worst = check_sampled_step(before, after, F, 0.0, w.h, dt, tiles, (64, 64, 64), 300, 1, False)
+    assert worst <= 1e-5 * w.h, worst
+    # frozen points: everything outside the active tiles is unchanged
+    act = np.zeros(64 ** 3, dtype=bool)
+    act[tiles] = True
+    mask = torch.from_numpy(np.repeat(np.repeat(np.repeat(act.reshape(64, 64, 64), 8, 0), 8, 1), 8, 2)).cuda()
+    assert torch.equal(before[~mask], after[~mask])
+    # the next rebuild (after one more step) equals the oracle's band of the
+    # state it is built from
+    g.step(1, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+    state = torch.empty_like(phi0)
+    g.get_phi(state)
+    g.step(1, w.cfl, ls.LS_DT_CFL, w.rebuild_every)   # rebuilds from `state`, then steps
+    assert np.array_equal(g.active_tiles(), band_from(state, w.halfwidth * w.h))
+
+
+@pytest.fixture(scope="module")
+def perturbed_1024():
+    w = inputs.PerturbedSphere()
+    dev = torch.device("cuda")
+    return w, w.phi(device=dev).contiguous(), w.speed(device=dev).contiguous()
+
+
+@pytest.mark.parametrize("prec", [ls.LS_FP32, ls.LS_FP64])
+@pytest.mark.parametrize("full_domain", [False, True])
+def test_perturbed_sphere_1024(perturbed_1024, prec, full_domain):
+    """1024^3, spherical-harmonic sphere, F = cos 4 pi x cos 4 pi y
+    (sign-changing), band 6h; FP32 and FP64, narrow band and full domain."""
+    w, phi64, F64 = perturbed_1024
+    dev = torch.device("cuda")
+    dt_t = torch.float32 if prec == ls.LS_FP32 else torch.float64
+    F = F64.to(dt_t).contiguous()
+    g = ls.LevelSet(w.n, w.n, w.n, w.h, prec)
+    g.set_speed(F)
+    g.set_phi(phi64.to(dt_t).contiguous())
+    if full_domain:
+        g.set_full_domain(True)
+    else:
+        g.band_rebuild(w.halfwidth)
+    g.step(8, 0.5, ls.LS_DT_CFL, 5)
+    before = torch.empty((w.n,) * 3, dtype=dt_t, device=dev)
+    g.get_phi(before)
+    tiles = g.active_tiles()
+    dt = g.step(1, 0.5, ls.LS_DT_CFL, 5, want_dt=True)
+    after = torch.empty_like(before)
+    g.get_phi(after)
+    exact = prec == ls.LS_FP64
+    # band points: within the band (6h) plus the one-tile dilation (<= 16h more)
+    band = 22 * w.h if full_domain else None
+    worst = check_sampled_step(before, after, F, 0.0, w.h, dt, tiles, (128, 128, 128), 120, 2, exact,
+                               band)
+    if not exact:
+        assert worst <= 1e-5 * w.h, worst
+    g.close()
+
+
+def test_batch_256_in_bench_configuration():
+    """The 256-instance batch with the autotuned stencil and graph replay:
+    sampled instances against the oracle on their whole grid, one step from
+    the GPU's own state, plus their band sets."""
+    insts = inputs.batch_instances()
+    dev = torch.device("cuda")
+    b = ls.Batch([i.edge for i in insts], [i.h for i in insts])
+    for k, it in enumerate(insts):
+        b.set_phi_i(k, it.phi(device=dev).to(torch.float32).contiguous())
+        b.set_speed_const_i(k, it.speed)
+    b.band_rebuild(4.0)
+    b.step(5, 0.5, ls.LS_DT_CFL, 5)
+    b.autotune(reps=3)
+    b.set_graphs(True)
+    for _ in range(3):
+        b.step(6, 0.5, ls.LS_DT_CFL, 5)   # since the last rebuild: 3 steps
+    sample = np.random.default_rng(3).choice(len(insts), size=10, replace=False)
+    before = {int(k): b.get_phi_i(int(k)) for k in sample}
+    tiles = {int(k): b.active_tiles_i(int(k)) for k in sample}
+    b.set_graphs(False)
+    b.step(1, 0.5, ls.LS_DT_CFL, 5)
+    for k in sample:
+        k = int(k)
+        it = insts[k]
+        out = b.get_phi_i(k).astype(np.float64)
+        e = it.edge
+        act = np.zeros((e // 8) ** 3, dtype=np.uint8)
+        act[tiles[k]] = 1
+        ref = oracle.step(before[k].astype(np.float64), it.h, b.last_dt_i(k), Fc=it.speed,
+                          tile_active=act.reshape((e // 8,) * 3))
+        assert np.max(np.abs(out - ref)) <= 1e-5 * it.h, k
