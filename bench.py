@@ -58,7 +58,8 @@ def parse():
     p.add_argument("--n", type=int, default=512, help="grid edge (512 = the standard workload)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", choices=["sphere-union", "batch", "learned"], default="sphere-union",
+    p.add_argument("--workload", choices=["sphere-union", "batch", "learned", "perturbed", "sphere64"],
+                   default="sphere-union",
                    help="sphere-union: the standard 512^3 run (the default line); "
                         "batch: 256 independent grids in one batched context; "
                         "learned: corrector training + learned-coarse vs plain at equal error")
@@ -257,7 +258,7 @@ def run_batch(args):
     b.snapshot()
     b.band_rebuild(4.0)
     b.step(5, 0.5, ls.LS_DT_CFL, 5)
-    stages, pct = b.autotune(reps=5)
+    stages, pct, ppt = b.autotune(reps=5)
 
     def run_once():
         b.restore()
@@ -305,7 +306,7 @@ def run_batch(args):
             "config": {"workload": "batch of 256 grids (edges 32..192, sphere/torus, constant F in "
                                    "[-1,1]), band 4h, rebuild/5, 200 steps CFL 0.5",
                        "total_points": total_pts, "graphs": True,
-                       "autotuned": {"stages": stages, "grid_pct": pct},
+                       "autotuned": {"stages": stages, "grid_pct": pct, "points_per_thread": ppt},
                        "l2": "inputs larger than L2 (phi 2 x 2.3 GB)"},
             "updates_per_step": updates / max(args.steps, 1),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -436,8 +437,96 @@ def run_learned(args):
     ctx.close()
 
 
+def run_perturbed(args):
+    """1024^3 perturbed sphere, F = cos 4 pi x cos 4 pi y, band 6h: GLUPS of
+    FP32 and FP64, narrow band and full domain (one line per combination;
+    steps = level-set steps timed after 5 warm-up steps)."""
+    import torch
+    from paper_1612_04040_b300 import inputs
+    from paper_1612_04040_b300 import native as ls
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda")
+    w = inputs.PerturbedSphere()
+    phi64 = w.phi(device=dev).contiguous()
+    F64 = w.speed(device=dev).contiguous()
+    nsteps = max(args.steps, 1) * 10
+    for prec, name, bpu in ((ls.LS_FP32, "f32", 12), (ls.LS_FP64, "f64", 24)):
+        dt_t = torch.float32 if prec == ls.LS_FP32 else torch.float64
+        for full in (False, True):
+            g = ls.LevelSet(w.n, w.n, w.n, w.h, prec)
+            g.set_speed(F64.to(dt_t).contiguous())
+            g.set_phi(phi64.to(dt_t).contiguous())
+            if full:
+                g.set_full_domain(True)
+            else:
+                g.band_rebuild(w.halfwidth)
+            g.step(5, 0.5, ls.LS_DT_CFL, 5)
+            torch.cuda.synchronize()
+            u0 = g.updates()
+            g.reset_profile()
+            g.profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.step(nsteps, 0.5, ls.LS_DT_CFL, 5)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            prof = g.profile()
+            u = g.updates() - u0
+            st = prof["stencil_ms"] / 1e3
+            print(json.dumps({
+                "metric": "upwind GLUPS", "workload": "perturbed sphere 1024^3 %s %s" % (
+                    name, "full domain" if full else "band 6h"),
+                "value": u / (ms / 1e3) / 1e9, "unit": "GLUPS", "dtype": name, "steps": nsteps,
+                "ms_per_level_set_step": ms / nsteps, "updates_per_step": u / nsteps,
+                "stencil_GBps_algorithmic": u * bpu / 1e9 / st if st > 0 else None,
+                "stencil_share": st / (ms / 1e3)}), flush=True)
+            g.close()
+
+
+def run_sphere64(args):
+    """64^3 single sphere, F = 1, dt = h/2, 100 full-domain steps, FP64."""
+    import torch
+    from paper_1612_04040_b300 import inputs
+    from paper_1612_04040_b300 import native as ls
+    torch.cuda.set_device(0)
+    w = inputs.SingleSphere()
+    g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP64)
+    phi = w.phi(device="cuda").contiguous()
+    g.set_speed_const(w.speed)
+    g.set_full_domain(True)
+    g.set_graphs(True)
+    for _ in range(max(args.warmup, 1)):
+        g.set_phi(phi)
+        g.step(w.steps, w.h / 2, ls.LS_DT_FIXED)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 1)
+    u0 = g.updates()
+    t_ms = 0.0
+    for _ in range(reps):
+        g.set_phi(phi)
+        e0.record()
+        g.step(w.steps, w.h / 2, ls.LS_DT_FIXED)
+        e1.record()
+        torch.cuda.synchronize()
+        t_ms += e0.elapsed_time(e1)
+    u = g.updates() - u0
+    print(json.dumps({"metric": "upwind GLUPS", "workload": "single sphere 64^3 FP64, 100 full-domain steps",
+                      "value": u / (t_ms / 1e3) / 1e9, "unit": "GLUPS", "dtype": "f64",
+                      "ms_per_run": t_ms / reps, "graphs": True,
+                      "note": "whole state (4 MiB) sits in L2: launch/latency-bound, no HBM claim"}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "perturbed":
+        run_perturbed(args)
+        return
+    if args.workload == "sphere64":
+        run_sphere64(args)
+        return
     if args.workload == "learned":
         run_learned(args)
         return
@@ -468,6 +557,12 @@ def main():
         g.band_rebuild(w.halfwidth, want_count=False)
         g.step(w.steps, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
 
+    # autotune the stencil launch configuration on a band from the middle of
+    # the run (setup, before the timed region)
+    g.set_phi(phi0)
+    g.band_rebuild(w.halfwidth, want_count=False)
+    g.step(w.steps // 2, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+    tuned = g.autotune(reps=5)
     for _ in range(max(args.warmup, 0)):
         run_once()
     torch.cuda.synchronize()
@@ -563,6 +658,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
             "config": {"workload": WORKLOAD, "grid": w.n, "halfwidth_h": w.halfwidth,
+                       "autotuned": {"stages": tuned[0], "grid_pct": tuned[1], "points_per_thread": tuned[2]},
                        "rebuild_every": w.rebuild_every, "level_set_steps_per_bench_step": w.steps,
                        "cfl": w.cfl, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (phi + F 1.5 GB; active set per step ~0.2 GB)"},

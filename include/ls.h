@@ -163,18 +163,19 @@ int ls_get_updates(ls_ctx *ctx, unsigned long long *n);
  * blocking stream for the replays. */
 int ls_set_graphs(ls_ctx *ctx, int on);
 
-/* Autotuner: time every launch configuration of the FP32 stencil (cp.async
- * ring depth 2/3/4 x persistent grid 50/75/100 % of full occupancy) on the
- * current active set, `reps` launches each, and keep the fastest for later
- * steps.  The probes write only the buffer the next step overwrites, so
- * the state is unchanged.  Outputs (nullable): the chosen stages and grid
- * percentage.  Needs a valid band (LS_ESTATE otherwise).  FP64 contexts
- * have a single configuration and return it. */
-int ls_autotune(ls_ctx *ctx, int reps, int *stages, int *grid_pct);
+/* Autotuner: time every launch configuration of the FP32 stencil (points
+ * per thread 4 (128-thread CTAs) or 8 (64-thread CTAs) x cp.async ring depth
+ * 2/3/4 x persistent grid 50/75/100 % of full occupancy) on the current
+ * active set, `reps` launches each, and keep the fastest for later steps.
+ * Every configuration computes the same bits.  The probes write only the
+ * buffer the next step overwrites, so the state is unchanged.  Outputs
+ * (nullable): the chosen configuration.  Needs a valid band (LS_ESTATE
+ * otherwise).  FP64 contexts have a single configuration and return it. */
+int ls_autotune(ls_ctx *ctx, int reps, int *stages, int *grid_pct, int *points_per_thread);
 
 /* Set the FP32 stencil launch configuration directly (stages 2..4, grid
- * 1..100 % of full occupancy). */
-int ls_set_step_config(ls_ctx *ctx, int stages, int grid_pct);
+ * 1..100 % of full occupancy, points per thread 4 or 8; default 3, 100, 8). */
+int ls_set_step_config(ls_ctx *ctx, int stages, int grid_pct, int points_per_thread);
 
 /* Profiling counters of a context. */
 typedef struct {

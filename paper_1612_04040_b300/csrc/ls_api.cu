@@ -368,8 +368,8 @@ int run_steps_graph(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuil
     long long vbits = 0;
     std::memcpy(&vbits, &value, sizeof(vbits));
     const GraphKey key{c->cur, c->since_rebuild, (int)c->band_valid, (int)c->core_fresh,
-                       (int)c->full_domain | (c->step_mode << 1), nsteps, rebuild_every, dt_mode, vbits, c->cfg.stages,
-                       c->cfg.grid_pct};
+                       (int)c->full_domain | (c->step_mode << 1), nsteps, rebuild_every, dt_mode, vbits,
+                       c->cfg.stages * 16 + c->cfg.ppt, c->cfg.grid_pct};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         if (c->graphs.size() >= 16) clear_graphs(c);
@@ -749,7 +749,7 @@ int ls_inst_last_dt(ls_ctx* c, int i, double* dt)
     return LS_OK;
 }
 
-int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out)
+int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out, int* ppt_out)
 {
     if (!c || reps < 1) return LS_EINVAL;
     if (!c->band_valid) return LS_ESTATE;
@@ -757,6 +757,7 @@ int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out)
     if (c->prec == LS_FP32) {
         const int stages[] = {2, 3, 4};
         const int pcts[] = {50, 75, 100};
+        const int ppts[] = {4, 8};
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
@@ -764,11 +765,13 @@ int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out)
         lsk::StepConfig best_cfg = c->cfg;
         lsk::StepArgs a = step_args(c, false);
         a.updates = nullptr;  // probes write the other buffer only; the state is unchanged
+        for (int ppt : ppts)
         for (int st : stages) {
             for (int pct : pcts) {
                 lsk::StepConfig cfg;
                 cfg.stages = st;
                 cfg.grid_pct = pct;
+                cfg.ppt = ppt;
                 KL(c, lsk::launch_step(a, c->prec, cfg, s));
                 CK(cudaEventRecord(e0, s));
                 for (int r = 0; r < reps; ++r) KL(c, lsk::launch_step(a, c->prec, cfg, s));
@@ -789,15 +792,18 @@ int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out)
     }
     if (stages_out) *stages_out = c->cfg.stages;
     if (grid_pct_out) *grid_pct_out = c->cfg.grid_pct;
+    if (ppt_out) *ppt_out = c->cfg.ppt;
     return LS_OK;
 }
 
-int ls_set_step_config(ls_ctx* c, int stages, int grid_pct)
+int ls_set_step_config(ls_ctx* c, int stages, int grid_pct, int ppt)
 {
-    if (!c || (stages != 2 && stages != 3 && stages != 4) || grid_pct < 1 || grid_pct > 100)
+    if (!c || (stages != 2 && stages != 3 && stages != 4) || grid_pct < 1 || grid_pct > 100 ||
+        (ppt != 4 && ppt != 8))
         return LS_EINVAL;
     c->cfg.stages = stages;
     c->cfg.grid_pct = grid_pct;
+    c->cfg.ppt = ppt;
     clear_graphs(c);
     return LS_OK;
 }

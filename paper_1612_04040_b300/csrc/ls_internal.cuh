@@ -129,6 +129,7 @@ struct StepArgs {
 struct StepConfig {
     int stages = 3;           // cp.async ring depth (2, 3, 4)
     int grid_pct = 100;       // persistent grid, percent of full occupancy
+    int ppt = 8;              // points per thread: 4 (128-thread CTAs) or 8 (64-thread CTAs)
 };
 
 cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cudaStream_t s);

@@ -304,6 +304,175 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
 }
 
 
+// 8 points per thread: 64-thread CTAs, thread (xh, ly, lzp) owns the quads of
+// planes lz = 2 lzp and 2 lzp + 1, so each quad's z-neighbour on the other
+// plane is already in registers and the per-tile work (staging addresses,
+// branching, barrier, store) is spread over twice as many points.  Same
+// stage layout, same arithmetic per point (bit-identical results).
+template <bool FIELD, bool CLASSIFY, bool BATCHED, int S>
+__global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Stage32* st = reinterpret_cast<Stage32*>(smem_raw);
+    __shared__ unsigned smin[S];
+    const int tid = threadIdx.x;
+    const int xh = tid & 1, ly = (tid >> 1) & 7, lzp = tid >> 4;
+    const int q0 = tid + 16 * lzp, q1 = q0 + 16;
+    const int lz0 = 2 * lzp;
+    const int n = *a.count;
+    if (blockIdx.x == 0 && tid == 0 && a.updates)
+        atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
+    const float* __restrict__ src = (const float*)a.src;
+    float* __restrict__ dst = (float*)a.dst;
+    const float* __restrict__ Fp = (const float*)a.F;
+    const int* __restrict__ list = a.list;
+    const uint8_t* __restrict__ linfo = a.info;
+    const uint16_t* __restrict__ linst = a.list_inst;
+    const bool extrap = a.in.bc == 0;
+    const float coef1 = BATCHED ? 0.f : a.sc->coef;
+    const float Fc1 = BATCHED ? 0.f : (float)a.in.Fc;
+    const double gamma1 = a.in.gamma;
+    const int sy1 = a.in.tnx * TILE_PTS;
+    const int sz1 = a.in.tnx * a.in.tny * TILE_PTS;
+    const int stride = gridDim.x;
+    const int x_off0 = xh ? (TILE_PTS + lz0 * 64 + ly * 8) : (-TILE_PTS + lz0 * 64 + ly * 8 + 7);
+    const unsigned x_bit = xh ? NB_XP : NB_XM;
+    const int y_in = (ly == 0) ? (lz0 * 64 + 56 + 4 * xh) : (lz0 * 64 + 4 * xh);
+    const int y_sgn = (ly == 0) ? -1 : 1;
+    const unsigned y_bit = (ly == 0) ? NB_YM : ((ly == 7) ? NB_YP : 0u);
+    const int y_slot0 = 128 + ((ly == 7) ? 16 : 0) + 2 * lz0 + xh;
+    const int y_slot1 = y_slot0 + 2;
+    const int z_in = (lzp == 0) ? (448 + ly * 8 + 4 * xh) : (ly * 8 + 4 * xh);
+    const int z_sgn = (lzp == 0) ? -1 : 1;
+    const unsigned z_bit = (lzp == 0) ? NB_ZM : ((lzp == 3) ? NB_ZP : 0u);
+    const int z_slot = 160 + ((lzp == 3) ? 16 : 0) + 2 * ly + xh;
+    const int y_off1 = y_sgn * sy1 + y_in;
+    const int z_off1 = z_sgn * sz1 + z_in;
+    const int i_ym0 = (ly > 0) ? q0 - 2 : y_slot0;
+    const int i_yp0 = (ly < 7) ? q0 + 2 : y_slot0;
+    const int i_ym1 = (ly > 0) ? q1 - 2 : y_slot1;
+    const int i_yp1 = (ly < 7) ? q1 + 2 : y_slot1;
+    const int i_zm0 = (lzp > 0) ? q0 - 16 : z_slot;
+    const int i_zp1 = (lzp < 3) ? q1 + 16 : z_slot;
+    const int i_pc0 = 4 * (q0 ^ 1) + (xh ? 3 : 0);
+    const int i_pc1 = 4 * (q1 ^ 1) + (xh ? 3 : 0);
+
+    auto issue = [&](unsigned t, unsigned info, unsigned inst, int s) {
+        const unsigned base = t * TILE_PTS;
+        const float* tp = src + base;
+        Stage32& Sg = st[s];
+        if (tid == 0) {
+            Sg.meta = make_int4((int)t, (int)info, (int)inst, 0);
+            if (CLASSIFY) smin[s] = 0x7f800000u;
+        }
+        int y_off = y_off1, z_off = z_off1;
+        if (BATCHED) {
+            const int tnx = a.insts[inst].tnx, tny = a.insts[inst].tny;
+            y_off = y_sgn * (tnx * TILE_PTS) + y_in;
+            z_off = z_sgn * (tnx * tny * TILE_PTS) + z_in;
+        }
+        cp_async16(&Sg.v[q0], tp + 4 * q0);
+        cp_async16(&Sg.v[q1], tp + 4 * q1);
+        if (FIELD) {
+            cp_async16(&Sg.f[q0], Fp + base + 4 * q0);
+            cp_async16(&Sg.f[q1], Fp + base + 4 * q1);
+        }
+        const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0, pz = (info & z_bit) != 0;
+        cp_async4(&Sg.xo[q0], px ? tp + x_off0 : tp, px);
+        cp_async4(&Sg.xo[q1], px ? tp + x_off0 + 64 : tp, px);
+        cp_async16(&Sg.v[y_slot0], py ? tp + y_off : tp, py);
+        cp_async16(&Sg.v[y_slot1], py ? tp + y_off + 64 : tp, py);
+        cp_async16(&Sg.v[z_slot], pz ? tp + z_off : tp, pz);
+    };
+    auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
+        t = (unsigned)__ldg(list + k);
+        info = __ldg(linfo + k);
+        inst = BATCHED ? (unsigned)__ldg(linst + k) : 0u;
+    };
+    auto gamma_of = [&](int inst) -> double { return BATCHED ? a.insts[inst].gamma : gamma1; };
+
+    int kn = blockIdx.x;
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s) {
+        if (kn < n) {
+            unsigned t, info, inst;
+            fetch(kn, t, info, inst);
+            issue(t, info, inst, s);
+        }
+        cp_async_commit();
+        kn += stride;
+    }
+    unsigned t_next = 0, i_next = 0, n_next = 0;
+    if (kn < n) fetch(kn, t_next, i_next, n_next);
+    int cur = 0, prev = -1, prev_t = -1, prev_inst = 0;
+    for (int k = blockIdx.x; k < n; k += stride) {
+        cp_async_wait<S - 2>();
+        __syncthreads();
+        if (CLASSIFY && tid == 0 && prev >= 0)
+            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma_of(prev_inst)) ? 1 : 0;
+        {
+            const int sn = (cur + S - 1) % S;
+            if (kn < n) issue(t_next, i_next, n_next, sn);
+            cp_async_commit();
+            kn += stride;
+            if (kn < n) fetch(kn, t_next, i_next, n_next);
+        }
+        const Stage32& Sg = st[cur];
+        const int t = Sg.meta.x;
+        const unsigned info = (unsigned)Sg.meta.y;
+        const int inst = Sg.meta.z;
+        const float coef = BATCHED ? a.sc[inst].coef : coef1;
+        const float Fc = BATCHED ? (float)a.insts[inst].Fc : Fc1;
+        const float4 c0 = Sg.v[q0], c1 = Sg.v[q1];
+        const float4 f0 = FIELD ? Sg.f[q0] : make_float4(Fc, Fc, Fc, Fc);
+        const float4 f1 = FIELD ? Sg.f[q1] : make_float4(Fc, Fc, Fc, Fc);
+        const float4 ym0 = Sg.v[i_ym0], yp0 = Sg.v[i_yp0];
+        const float4 ym1 = Sg.v[i_ym1], yp1 = Sg.v[i_yp1];
+        const float4 zm0 = Sg.v[i_zm0], zp1 = Sg.v[i_zp1];
+        const float pc0 = reinterpret_cast<const float*>(Sg.v)[i_pc0];
+        const float pc1 = reinterpret_cast<const float*>(Sg.v)[i_pc1];
+        const float xo0 = Sg.xo[q0], xo1 = Sg.xo[q1];
+        const float xm0a = xh ? pc0 : xo0, xp3a = xh ? xo0 : pc0;
+        const float xm0b = xh ? pc1 : xo1, xp3b = xh ? xo1 : pc1;
+        float4 o0, o1;
+        if (info == (NB_ALL | SG_POS)) {
+            o0 = upd4<1, false>(c0, f0, xm0a, xp3a, ym0, yp0, zm0, c1, coef, extrap, false, false, false, false, false, false);
+            o1 = upd4<1, false>(c1, f1, xm0b, xp3b, ym1, yp1, c0, zp1, coef, extrap, false, false, false, false, false, false);
+        } else if (info == (NB_ALL | SG_NEG)) {
+            o0 = upd4<-1, false>(c0, f0, xm0a, xp3a, ym0, yp0, zm0, c1, coef, extrap, false, false, false, false, false, false);
+            o1 = upd4<-1, false>(c1, f1, xm0b, xp3b, ym1, yp1, c0, zp1, coef, extrap, false, false, false, false, false, false);
+        } else {
+            const bool xlo = (xh == 0) && !(info & NB_XM);
+            const bool xhi = (xh == 1) && !(info & NB_XP);
+            const bool ylo = (ly == 0) && !(info & NB_YM);
+            const bool yhi = (ly == 7) && !(info & NB_YP);
+            const bool zlo = (lzp == 0) && !(info & NB_ZM);
+            const bool zhi = (lzp == 3) && !(info & NB_ZP);
+            o0 = upd4<0, true>(c0, f0, xm0a, xp3a, ym0, yp0, zm0, c1, coef, extrap, xlo, xhi, ylo, yhi, zlo, false);
+            o1 = upd4<0, true>(c1, f1, xm0b, xp3b, ym1, yp1, c0, zp1, coef, extrap, xlo, xhi, ylo, yhi, false, zhi);
+        }
+        float* dp = dst + (unsigned)t * TILE_PTS;
+        *reinterpret_cast<float4*>(dp + 4 * q0) = o0;
+        *reinterpret_cast<float4*>(dp + 4 * q1) = o1;
+        if (CLASSIFY) {
+            const float mn = fminf(fminf(fminf(fabsf(o0.x), fabsf(o0.y)), fminf(fabsf(o0.z), fabsf(o0.w))),
+                                   fminf(fminf(fabsf(o1.x), fabsf(o1.y)), fminf(fabsf(o1.z), fabsf(o1.w))));
+            const unsigned wm = __reduce_min_sync(0xffffffffu, __float_as_uint(mn));
+            if ((tid & 31) == 0) atomicMin(&smin[cur], wm);
+        }
+        prev = cur;
+        prev_t = t;
+        prev_inst = inst;
+        cur = (cur + 1) % S;
+    }
+    if (CLASSIFY) {
+        __syncthreads();
+        if (tid == 0 && prev >= 0)
+            a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma_of(prev_inst)) ? 1 : 0;
+    }
+    cp_async_wait<0>();
+}
+
 // ------------------------------------------------------------------ FP64 ----
 __device__ __forceinline__ double max0(double a) { return a > 0.0 ? a : 0.0; }
 __device__ __forceinline__ double min0(double a) { return a < 0.0 ? a : 0.0; }
@@ -460,26 +629,30 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
 }
 
 template <typename K>
-int occupancy_grid(K kernel, size_t smem)
+int occupancy_grid(K kernel, size_t smem, int threads = 128)
 {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 128, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
     if (per < 1) per = 1;
     return sms * per;
 }
 
 template <bool FIELD, bool CLS, bool BAT, int S>
-cudaError_t launch32(const StepArgs& a, int grid_pct, cudaStream_t s)
+cudaError_t launch32(const StepArgs& a, int grid_pct, int ppt, cudaStream_t s)
 {
     constexpr size_t smem = sizeof(Stage32) * S;
-    static int full = 0;
-    if (!full) full = occupancy_grid(k_step_f32<FIELD, CLS, BAT, S>, smem);
+    static int full4 = 0, full8 = 0;
+    int& full = ppt == 8 ? full8 : full4;
+    if (!full)
+        full = ppt == 8 ? occupancy_grid(k_step_f32_z2<FIELD, CLS, BAT, S>, smem, 64)
+                        : occupancy_grid(k_step_f32<FIELD, CLS, BAT, S>, smem, 128);
     int grid = (int)((long long)full * grid_pct / 100);
     if (grid < 1) grid = 1;
     if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
-    k_step_f32<FIELD, CLS, BAT, S><<<grid, 128, smem, s>>>(a);
+    if (ppt == 8) k_step_f32_z2<FIELD, CLS, BAT, S><<<grid, 64, smem, s>>>(a);
+    else k_step_f32<FIELD, CLS, BAT, S><<<grid, 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -487,9 +660,9 @@ template <bool FIELD, bool CLS, bool BAT>
 cudaError_t launch32_s(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
 {
     switch (cfg.stages) {
-    case 2: return launch32<FIELD, CLS, BAT, 2>(a, cfg.grid_pct, s);
-    case 4: return launch32<FIELD, CLS, BAT, 4>(a, cfg.grid_pct, s);
-    default: return launch32<FIELD, CLS, BAT, 3>(a, cfg.grid_pct, s);
+    case 2: return launch32<FIELD, CLS, BAT, 2>(a, cfg.grid_pct, cfg.ppt, s);
+    case 4: return launch32<FIELD, CLS, BAT, 4>(a, cfg.grid_pct, cfg.ppt, s);
+    default: return launch32<FIELD, CLS, BAT, 3>(a, cfg.grid_pct, cfg.ppt, s);
     }
 }
 

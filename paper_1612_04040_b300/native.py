@@ -52,8 +52,8 @@ SIGNATURES = {
     "ls_get_active_tiles": (_i, [_vp, _c.POINTER(_c.c_int), _ll, _c.POINTER(_ll)]),
     "ls_get_updates": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
     "ls_set_graphs": (_i, [_vp, _i]),
-    "ls_autotune": (_i, [_vp, _i, _c.POINTER(_i), _c.POINTER(_i)]),
-    "ls_set_step_config": (_i, [_vp, _i, _i]),
+    "ls_autotune": (_i, [_vp, _i, _c.POINTER(_i), _c.POINTER(_i), _c.POINTER(_i)]),
+    "ls_set_step_config": (_i, [_vp, _i, _i, _i]),
     "ls_batch_create": (_i, [_i, _c.POINTER(_i), _c.POINTER(_i), _c.POINTER(_i), _c.POINTER(_d), _i, _pp]),
     "ls_batch_size": (_i, [_vp, _c.POINTER(_i)]),
     "ls_inst_set_phi": (_i, [_vp, _i, _vp, _i]),
@@ -323,12 +323,13 @@ class LevelSet:
         check(self.lib.ls_set_graphs(self.ctx, int(bool(on))), "ls_set_graphs")
 
     def autotune(self, reps=5):
-        st, pct = ctypes.c_int(0), ctypes.c_int(0)
-        check(self.lib.ls_autotune(self.ctx, int(reps), ctypes.byref(st), ctypes.byref(pct)), "ls_autotune")
-        return st.value, pct.value
+        st, pct, ppt = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        check(self.lib.ls_autotune(self.ctx, int(reps), ctypes.byref(st), ctypes.byref(pct), ctypes.byref(ppt)),
+              "ls_autotune")
+        return st.value, pct.value, ppt.value
 
-    def set_step_config(self, stages, grid_pct):
-        check(self.lib.ls_set_step_config(self.ctx, int(stages), int(grid_pct)), "ls_set_step_config")
+    def set_step_config(self, stages, grid_pct, ppt=8):
+        check(self.lib.ls_set_step_config(self.ctx, int(stages), int(grid_pct), int(ppt)), "ls_set_step_config")
 
     # -- learned corrector --------------------------------------------------
     def learned_init(self, seed=0):

@@ -94,8 +94,8 @@ def test_single_grid_graph_and_autotune_bitwise():
             g.set_graphs(True)
         if mode == "tuned":
             g.step(1, 0.5, ls.LS_DT_CFL, 5)
-            st, pct = g.autotune(reps=2)
-            assert st in (2, 3, 4) and pct in (50, 75, 100)
+            st, pct, ppt = g.autotune(reps=2)
+            assert st in (2, 3, 4) and pct in (50, 75, 100) and ppt in (4, 8)
             g.step(11, 0.5, ls.LS_DT_CFL, 5)
         else:
             g.step(1, 0.5, ls.LS_DT_CFL, 5)
@@ -108,15 +108,17 @@ def test_single_grid_graph_and_autotune_bitwise():
     assert np.array_equal(outs[0], outs[2])
 
 
-@pytest.mark.parametrize("stages,pct", [(2, 50), (4, 100), (3, 75)])
-def test_step_configs_agree(stages, pct):
+@pytest.mark.parametrize("stages,pct,ppt", [(2, 50, 4), (4, 100, 8), (3, 75, 4), (2, 100, 8)])
+def test_step_configs_agree(stages, pct, ppt):
+    """Every launch configuration computes the same bits (both stencil
+    decompositions, constant and field speeds)."""
     w = inputs.SphereUnion(n=48, count=4)
     p = w.phi().numpy().astype(np.float32)
     ref = None
-    for cfg in ((3, 100), (stages, pct)):
+    for cfg in ((3, 100, 8), (stages, pct, ppt)):
         g = ls.LevelSet(48, 48, 48, w.h, ls.LS_FP32)
         g.set_phi(p)
-        g.set_speed_const(-0.6)
+        g.set_speed(w.speed().numpy().astype(np.float32) - 1.0)  # sign-changing field
         g.set_step_config(*cfg)
         g.band_rebuild(4.0)
         g.step(10, 0.5, ls.LS_DT_CFL, 5)
