@@ -6,8 +6,9 @@ phi^0 = signed distance to the union of 20 seeded spheres (centres
 U[0.15,0.85]^3, radii U[0.05,0.15]), F = 1 + 0.5 sin(2 pi x) sin(2 pi y)
 sin(2 pi z), band half-width 6h on 8^3 tiles, band rebuilt every 5 steps,
 500 steps at CFL 0.5.  One bench step = one whole run of that workload
-through the C ABI: ls_set_phi(phi^0 from device memory) -> ls_band_rebuild(6)
--> ls_step(500, CFL 0.5, rebuild every 5).  The metric is grid-point updates
+through the C ABI: ls_restore(phi^0, a device snapshot made after the
+library's own Step 0 kernels generated it) -> ls_band_rebuild(6) ->
+ls_step(500, CFL 0.5, rebuild every 5).  The metric is grid-point updates
 per second over the band (GLUPS: sum over steps of the points of the active
 tiles, divided by the device time).
 
@@ -545,21 +546,24 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
     w = inputs.SphereUnion(n=args.n)
-    phi0 = w.phi(device=dev).to(torch.float32).contiguous()
-    F = w.speed(device=dev).to(torch.float32).contiguous()
+    g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32, stream=stream.cuda_stream)
+    # Step 0 on the device: the library's own SDF / speed generators (FP64
+    # evaluation, stored FP32); phi^0 kept as a device snapshot for the runs
+    g.init_speed(ls.LS_SPEED_SINUSOID)
+    g.init_phi(ls.LS_SHAPE_SPHERES, inputs.spheres_params(w.centres, w.radii))
+    g.snapshot()
+    phi0 = torch.empty((w.n,) * 3, dtype=torch.float32, device=dev)
+    g.get_phi(phi0)
     torch.cuda.synchronize()
 
-    g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32, stream=stream.cuda_stream)
-    g.set_speed(F)
-
     def run_once():
-        g.set_phi(phi0)
+        g.restore()
         g.band_rebuild(w.halfwidth, want_count=False)
         g.step(w.steps, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
 
     # autotune the stencil launch configuration on a band from the middle of
     # the run (setup, before the timed region)
-    g.set_phi(phi0)
+    g.restore()
     g.band_rebuild(w.halfwidth, want_count=False)
     g.step(w.steps // 2, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
     tuned = g.autotune(reps=5)
@@ -628,7 +632,7 @@ def main():
     e2e = None
     if args.e2e_steps > 0:
         phi_h = phi0.cpu().pin_memory()
-        F_h = F.cpu().pin_memory()
+        F_h = w.speed(out_dtype=torch.float32).contiguous().pin_memory()
         out_h = torch.empty_like(phi_h).pin_memory()
         u1 = g.updates()
         torch.cuda.synchronize()
@@ -650,7 +654,8 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(phi0.cpu().numpy(), F.cpu().numpy(), w)
+        cpu = cpu_baseline(phi0.cpu().numpy(), F_h.numpy() if args.e2e_steps > 0 else
+                           w.speed(out_dtype=torch.float32).numpy(), w)
 
     if rank == 0:
         line = {

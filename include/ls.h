@@ -89,6 +89,33 @@ int ls_set_stream(ls_ctx *ctx, void *cuda_stream);
  * guaranteed, the band stays stale), LS_ECUDA. */
 int ls_set_phi(ls_ctx *ctx, const void *src, int src_on_device);
 
+/* Step 0 on the device (section 1.1; Eq. 1: phi(x,0) = +-d, negative
+ * inside), evaluated in FP64 at the cell centres ((i+1/2)h, (j+1/2)h,
+ * (k+1/2)h) and stored in the context's precision.  params: host array of
+ * nparams doubles, copied before the call returns.
+ *   LS_SHAPE_SPHERES  [n, (cx, cy, cz, r) x n]: min_i |x - c_i| - r_i
+ *   LS_SHAPE_TORUS    [cx, cy, cz, ax, ay, az, R, r], unit axis a:
+ *                     sqrt((rho - R)^2 + s^2) - r, s = (x-c).a,
+ *                     rho = distance from the axis line
+ *   LS_SHAPE_SH       [cx, cy, cz, base, amp, lmax, a_lm..., N_lm...]
+ *                     ((lmax+1)^2 - 1 modes each, l = 1..lmax, m = -l..l):
+ *                     |x - c| - (base + amp sum a_lm N_lm P_l^|m|(cos theta)
+ *                     T_m(phi)), T_m = cos(m phi) / 1 / sin(|m| phi) for
+ *                     m > 0 / m = 0 / m < 0 (a radial level-set function)
+ * Marks the band stale.  Errors: LS_EINVAL (kind or parameter count). */
+enum { LS_SHAPE_SPHERES = 0, LS_SHAPE_TORUS = 1, LS_SHAPE_SH = 2 };
+int ls_init_phi(ls_ctx *ctx, int shape, const double *params, int nparams);
+
+/* Speed fields on the device (FP64 evaluation, stored in the context's
+ * precision, per-tile max|F| computed as by ls_set_speed):
+ *   LS_SPEED_SINUSOID  1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z)
+ *   LS_SPEED_COSCOS    cos(4 pi x) cos(4 pi y)
+ *   LS_SPEED_FOURIER   [n, (a, kx, ky, kz, theta) x n]:
+ *                      sum a cos(2 pi k.x + theta) / sum |a|  (|F| <= 1)
+ * params may be NULL for the first two. */
+enum { LS_SPEED_SINUSOID = 0, LS_SPEED_COSCOS = 1, LS_SPEED_FOURIER = 2 };
+int ls_init_speed(ls_ctx *ctx, int kind, const double *params, int nparams);
+
 /* Speed field F (Eq. 2/3), same layout and precision as phi.  Also computes
  * the per-tile max|F| used by the CFL rule.  Errors as ls_set_phi. */
 int ls_set_speed(ls_ctx *ctx, const void *src, int src_on_device);
@@ -199,6 +226,12 @@ int ls_reset_profile(ls_ctx *ctx);
 /* Sticky device status word: LS_OK, or the first device-side error. */
 int ls_get_status(ls_ctx *ctx);
 
+/* Self-test of the bounded device wait used by the tensor-core kernels: a
+ * kernel waits on a barrier that nothing completes, gives up after `polls`
+ * polls and sets bit 1 (timeout) in the device word *status; the context and
+ * the device stay usable.  For failure-detection tests. */
+int ls_selftest_bounded_wait(unsigned *status, long long polls, void *cuda_stream);
+
 /* Static message for a status code. */
 const char *ls_strerror(int status);
 
@@ -238,6 +271,10 @@ int ls_inst_get_phi(ls_ctx *ctx, int i, void *dst, int dst_on_device);
 /* Active tiles of instance i, as local tile ids (ascending); like
  * ls_get_active_tiles. */
 int ls_inst_get_active_tiles(ls_ctx *ctx, int i, int *dst, long long cap, long long *n);
+
+/* Per-instance Step 0 fields (as ls_init_phi / ls_init_speed). */
+int ls_inst_init_phi(ls_ctx *ctx, int i, int shape, const double *params, int nparams);
+int ls_inst_init_speed(ls_ctx *ctx, int i, int kind, const double *params, int nparams);
 
 /* dt of instance i's last step (synchronises the stream). */
 int ls_inst_last_dt(ls_ctx *ctx, int i, double *dt);

@@ -133,7 +133,7 @@ void free_all(ls_ctx* c)
     void* ptrs[] = {c->phi[0], c->phi[1], c->F, c->tile_maxF, c->tile_sgn, c->staging, c->snapshot, c->core,
                     c->act, c->list, c->list_info, c->d_count, c->block_counts, c->d_sc,
                     c->d_Mbits, c->d_updates, c->d_status, c->d_nonfinite, c->d_inst,
-                    c->d_tile_inst, c->d_list_inst, c->d_inst_count};
+                    c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -826,6 +826,94 @@ int ls_restore(ls_ctx* c)
     CK(cudaMemcpyAsync(c->phi[0], c->snapshot, grid_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemcpyAsync(c->phi[1], c->snapshot, grid_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
     c->cur = 0;
+    return LS_OK;
+}
+
+static int upload_params(ls_ctx* c, const double* params, int n, double** dev)
+{
+    static_assert(sizeof(double) == 8, "double");
+    if (n > c->init_params_cap) {
+        if (c->init_params) cudaFree(c->init_params);
+        c->init_params = nullptr;
+        c->init_params_cap = 0;
+        CK(cudaMalloc(&c->init_params, sizeof(double) * n));
+        c->init_params_cap = n;
+    }
+    CK(cudaMemcpyAsync(c->init_params, params, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // params is caller memory: copy before returning
+    *dev = c->init_params;
+    return LS_OK;
+}
+
+static int shape_params_ok(int kind, const double* p, int n)
+{
+    if (!p || n < 1) return 0;
+    if (kind == LS_SHAPE_SPHERES) return n >= 1 && p[0] >= 1 && n == 1 + 4 * (int)p[0];
+    if (kind == LS_SHAPE_TORUS) return n == 8;
+    if (kind == LS_SHAPE_SH) {
+        if (n < 6) return 0;
+        const int lmax = (int)p[5];
+        if (lmax < 1 || lmax > 16) return 0;
+        const int modes = (lmax + 1) * (lmax + 1) - 1;
+        return n == 6 + 2 * modes;
+    }
+    return 0;
+}
+
+static int speed_params_ok(int kind, const double* p, int n)
+{
+    if (kind == LS_SPEED_SINUSOID || kind == LS_SPEED_COSCOS) return 1;
+    if (kind == LS_SPEED_FOURIER) return p && n >= 1 && p[0] >= 1 && n == 1 + 5 * (int)p[0];
+    return 0;
+}
+
+int ls_inst_init_phi(ls_ctx* c, int i, int shape, const double* params, int nparams)
+{
+    if (!c || i < 0 || i >= c->n_inst || !shape_params_ok(shape, params, nparams)) return LS_EINVAL;
+    double* dp = nullptr;
+    RET(upload_params(c, params, nparams, &dp));
+    state_changed(c);
+    const Inst& in = c->insts[i];
+    KL(c, lsk::launch_init_field(region(c, c->phi[c->cur], in), region(c, c->phi[c->cur ^ 1], in), in,
+                                 c->prec, 0, shape, dp, c->stream));
+    c->inst_phi_set[i] = 1;
+    return LS_OK;
+}
+
+int ls_init_phi(ls_ctx* c, int shape, const double* params, int nparams)
+{
+    if (!c || c->n_inst != 1) return LS_EINVAL;
+    return ls_inst_init_phi(c, 0, shape, params, nparams);
+}
+
+int ls_inst_init_speed(ls_ctx* c, int i, int kind, const double* params, int nparams)
+{
+    if (!c || i < 0 || i >= c->n_inst || !speed_params_ok(kind, params, nparams)) return LS_EINVAL;
+    if (!c->F) CK(dalloc(&c->F, grid_bytes(c)));
+    if (!c->tile_maxF) CK(dalloc(&c->tile_maxF, c->ntiles * c->esize));
+    if (!c->tile_sgn) CK(dalloc(&c->tile_sgn, c->ntiles));
+    double* dp = nullptr;
+    static const double none = 0.0;
+    RET(upload_params(c, params ? params : &none, params ? nparams : 1, &dp));
+    state_changed(c);
+    Inst& in = c->insts[i];
+    KL(c, lsk::launch_init_field(region(c, c->F, in), nullptr, in, c->prec, 1, kind, dp, c->stream));
+    KL(c, lsk::launch_tile_speed(region(c, c->F, in), (char*)c->tile_maxF + (size_t)in.tile_base * c->esize,
+                                 c->tile_sgn + in.tile_base, in.ntiles, c->prec, c->stream));
+    in.speed_mode = 2;
+    return upload_insts(c);
+}
+
+int ls_init_speed(ls_ctx* c, int kind, const double* params, int nparams)
+{
+    if (!c || c->n_inst != 1) return LS_EINVAL;
+    return ls_inst_init_speed(c, 0, kind, params, nparams);
+}
+
+int ls_selftest_bounded_wait(unsigned* status, long long polls, void* stream)
+{
+    if (!status || polls < 1) return LS_EINVAL;
+    CK(lsk::launch_selftest_wait(status, polls, (cudaStream_t)stream));
     return LS_OK;
 }
 

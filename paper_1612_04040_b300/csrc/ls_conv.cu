@@ -68,10 +68,11 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
 }
 
 // bounded wait for the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          long long limit = WAIT_LIMIT)
 {
     const unsigned a = smem_u32(bar);
-    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    for (long long i = 0; i < limit; ++i) {
         unsigned ok;
         asm volatile(
             "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -284,6 +285,16 @@ __global__ void __launch_bounds__(128, 1) k_conv3_tc(const __grid_constant__ CUt
                      : "memory");
 }
 
+// self-test of the bounded wait: an mbarrier nobody arrives at; the wait
+// must give up after `polls` polls and record ST_TIMEOUT
+__global__ void k_selftest_wait(unsigned* status, long long polls)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, polls)) atomicOr(status, ST_TIMEOUT);
+}
+
 // pack W (FP32 [27][ci][co], ci, co <= 16) into the canonical K-major B
 // layout per tap: [kb][nb][8 n][8 k] bf16, B[n][k] = W[t][k][n].  flip: the
 // backward-data operator, B[n][k] = W[26 - t][n][k] (taps mirrored, channels
@@ -351,6 +362,12 @@ cudaError_t make_act_maps(CUtensorMap* maps, const void* act, int nx, int ny, in
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_selftest_wait(unsigned* status, long long polls, cudaStream_t s)
+{
+    k_selftest_wait<<<1, 32, 0, s>>>(status, polls);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_weights(const float* W, int ci, int co, int flip, void* out, cudaStream_t s)

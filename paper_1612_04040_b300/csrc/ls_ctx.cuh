@@ -61,6 +61,8 @@ struct ls_ctx {
     uint8_t* tile_sgn = nullptr;  // per-tile sign code of a speed field (lazy)
     void* staging = nullptr;      // row-major staging buffer (lazy)
     void* snapshot = nullptr;     // ls_snapshot copy of phi (lazy)
+    double* init_params = nullptr;  // device copy of Step 0 shape / speed parameters
+    int init_params_cap = 0;
     uint8_t* core = nullptr;
     uint8_t* act = nullptr;
     int* list = nullptr;

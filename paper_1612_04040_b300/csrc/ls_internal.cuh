@@ -177,5 +177,10 @@ cudaError_t launch_residual(float* phit, const float* z, const int* list, const 
                             unsigned long long* fallbacks, cudaStream_t s);
 cudaError_t launch_restrict4(const float* fine, int nfx, int nfy, int nfz, float* coarse,
                              cudaStream_t s);
+cudaError_t launch_selftest_wait(unsigned* status, long long polls, cudaStream_t s);
+// Step 0 fields (ls_init.cu): evaluate shape / speed `kind` with device
+// params into out (and out2 if not NULL), bricked, context precision
+cudaError_t launch_init_field(void* out, void* out2, const Inst& in, int prec, int is_speed,
+                              int kind, const double* params, cudaStream_t s);
 
 }  // namespace lsk

@@ -339,3 +339,37 @@ def random_sphere_union(g: np.random.Generator, count_range=(3, 12)):
     centres = [tuple(float(v) for v in g.uniform(0.2, 0.8, 3)) for _ in range(k)]
     radii = [float(g.uniform(0.06, 0.16)) for _ in range(k)]
     return centres, radii
+
+
+# --------------------------------------------------------------------------
+# parameter vectors of the library's device-side Step 0 generators
+# (ls_init_phi / ls_init_speed); same formulas as the functions above
+# --------------------------------------------------------------------------
+
+def spheres_params(centres, radii):
+    out = [float(len(radii))]
+    for c, r in zip(centres, radii):
+        out += [float(c[0]), float(c[1]), float(c[2]), float(r)]
+    return np.asarray(out, dtype=np.float64)
+
+
+def torus_params(centre, axis, R, r):
+    return np.asarray(list(centre) + list(axis) + [R, r], dtype=np.float64)
+
+
+def sh_params(w: "PerturbedSphere", centre=(0.5, 0.5, 0.5)):
+    norms = []
+    for l in range(1, w.lmax + 1):
+        for m in range(-l, l + 1):
+            am = abs(m)
+            nv = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
+            norms.append(nv if m == 0 else math.sqrt(2.0) * nv)
+    return np.asarray(list(centre) + [w.base, w.amp * w.scale, float(w.lmax)] + list(w.coeffs) + norms,
+                      dtype=np.float64)
+
+
+def fourier_params(modes):
+    out = [float(len(modes))]
+    for a, k, th in modes:
+        out += [float(a), float(k[0]), float(k[1]), float(k[2]), float(th)]
+    return np.asarray(out, dtype=np.float64)

@@ -28,6 +28,8 @@ LS_FP32, LS_FP64 = 0, 1
 LS_DT_FIXED, LS_DT_CFL = 0, 1
 LS_PLAIN, LS_LEARNED = 0, 1
 LS_BC_EXTRAPOLATE, LS_BC_NEUMANN = 0, 1
+LS_SHAPE_SPHERES, LS_SHAPE_TORUS, LS_SHAPE_SH = 0, 1, 2
+LS_SPEED_SINUSOID, LS_SPEED_COSCOS, LS_SPEED_FOURIER = 0, 1, 2
 
 _lib = None
 
@@ -43,6 +45,11 @@ SIGNATURES = {
     "ls_set_speed": (_i, [_vp, _vp, _i]),
     "ls_set_speed_const": (_i, [_vp, _d]),
     "ls_set_bc": (_i, [_vp, _i]),
+    "ls_init_phi": (_i, [_vp, _i, _vp, _i]),
+    "ls_init_speed": (_i, [_vp, _i, _vp, _i]),
+    "ls_inst_init_phi": (_i, [_vp, _i, _i, _vp, _i]),
+    "ls_inst_init_speed": (_i, [_vp, _i, _i, _vp, _i]),
+    "ls_selftest_bounded_wait": (_i, [_vp, _ll, _vp]),
     "ls_band_rebuild": (_i, [_vp, _d, _c.POINTER(_ll)]),
     "ls_step": (_i, [_vp, _i, _d, _i, _i, _c.POINTER(_d)]),
     "ls_set_full_domain": (_i, [_vp, _i]),
@@ -198,6 +205,18 @@ def conv3_bf16(x, W, bias, mode, mask=None, out=None, stream=None):
     return out, status
 
 
+def selftest_bounded_wait(polls, stream=None):
+    """ls_selftest_bounded_wait: returns the status word after the wait gave up."""
+    lib = load()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib.ls_selftest_bounded_wait(_dptr(status), int(polls), ctypes.c_void_p(stream)),
+          "ls_selftest_bounded_wait")
+    torch.cuda.synchronize()
+    return int(status.item())
+
+
 def conv3_wgrad(x, dy, ci, co, stream=None):
     """ls_conv3_wgrad: returns (dW (27, ci, co), db (co,)) as float32 tensors."""
     lib = load()
@@ -268,6 +287,15 @@ class LevelSet:
     def set_speed(self, a):
         p, dev = array_ptr(a, self.dtype, self.count)
         check(self.lib.ls_set_speed(self.ctx, p, dev), "ls_set_speed")
+
+    def init_phi(self, shape, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        check(self.lib.ls_init_phi(self.ctx, int(shape), ctypes.c_void_p(p.ctypes.data), p.size), "ls_init_phi")
+
+    def init_speed(self, kind, params=None):
+        p = np.ascontiguousarray(params if params is not None else [0.0], dtype=np.float64)
+        check(self.lib.ls_init_speed(self.ctx, int(kind), ctypes.c_void_p(p.ctypes.data), p.size),
+              "ls_init_speed")
 
     def set_speed_const(self, F):
         check(self.lib.ls_set_speed_const(self.ctx, float(F)), "ls_set_speed_const")
@@ -419,6 +447,11 @@ class Batch(LevelSet):
     def set_speed_i(self, i, a):
         p, dev = array_ptr(a, self.dtype, self._count(i))
         check(self.lib.ls_inst_set_speed(self.ctx, int(i), p, dev), "ls_inst_set_speed")
+
+    def init_phi_i(self, i, shape, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        check(self.lib.ls_inst_init_phi(self.ctx, int(i), int(shape), ctypes.c_void_p(p.ctypes.data), p.size),
+              "ls_inst_init_phi")
 
     def set_speed_const_i(self, i, F):
         check(self.lib.ls_inst_set_speed_const(self.ctx, int(i), float(F)), "ls_inst_set_speed_const")

@@ -1,0 +1,93 @@
+"""Step 0 on the device (ls_init_phi / ls_init_speed) against the closed
+forms evaluated on the host in FP64, and the bounded-wait self-test."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1612_04040_b300 import inputs
+from paper_1612_04040_b300 import native as ls
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(cuda_ok):
+    ls.load()
+
+
+def device_field(shape, h, prec, init):
+    nz, ny, nx = shape
+    g = ls.LevelSet(nx, ny, nz, h, prec)
+    init(g)
+    out = g.get_phi()
+    g.close()
+    return out
+
+
+def compare(dev, ref, prec):
+    if prec == ls.LS_FP64:
+        assert np.max(np.abs(dev - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+    else:
+        # FP64 value rounded once to FP32: at most one FP32 ulp apart
+        r32 = ref.astype(np.float32)
+        ulp = np.spacing(np.abs(r32))
+        assert np.all(np.abs(dev.astype(np.float64) - r32.astype(np.float64)) <= ulp)
+
+
+@pytest.mark.parametrize("prec", [ls.LS_FP32, ls.LS_FP64])
+def test_sphere_union_and_torus(prec):
+    shape, h = (40, 48, 64), 1.0 / 64
+    w = inputs.SphereUnion(n=64, count=7)
+    ref = inputs.sphere_union_sdf(shape, h, w.centres, w.radii).numpy()
+    dev = device_field(shape, h, prec, lambda g: g.init_phi(ls.LS_SHAPE_SPHERES,
+                                                            inputs.spheres_params(w.centres, w.radii)))
+    compare(dev, ref, prec)
+    c, a, R, r = (0.5, 0.4, 0.3), (0.0, 0.6, 0.8), 0.2, 0.07
+    ref = inputs.torus_sdf(shape, h, c, a, R, r).numpy()
+    dev = device_field(shape, h, prec, lambda g: g.init_phi(ls.LS_SHAPE_TORUS, inputs.torus_params(c, a, R, r)))
+    compare(dev, ref, prec)
+
+
+def test_spherical_harmonic_sphere():
+    w = inputs.PerturbedSphere(n=64)
+    shape, h = (64, 64, 64), 1.0 / 64
+    ref = w.phi().numpy()
+    dev = device_field(shape, h, ls.LS_FP64, lambda g: g.init_phi(ls.LS_SHAPE_SH, inputs.sh_params(w)))
+    assert np.max(np.abs(dev - ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("kind", ["sinusoid", "coscos", "fourier"])
+def test_speed_fields(kind):
+    shape, h = (32, 40, 48), 1.0 / 48
+    modes = inputs.fourier_modes(np.random.default_rng(3))
+    if kind == "sinusoid":
+        ref, k, p = inputs.speed_sinusoid(shape, h).numpy(), ls.LS_SPEED_SINUSOID, None
+    elif kind == "coscos":
+        ref, k, p = inputs.speed_cos_cos(shape, h).numpy(), ls.LS_SPEED_COSCOS, None
+    else:
+        ref, k, p = inputs.speed_fourier(shape, h, modes).numpy(), ls.LS_SPEED_FOURIER, inputs.fourier_params(modes)
+    nz, ny, nx = shape
+    g = ls.LevelSet(nx, ny, nz, h, ls.LS_FP64)
+    g.init_speed(k, p)
+    # read F back through a zero-phi single step? F is internal: advance phi = x
+    # by one fixed step and recover F from the exact plane motion instead
+    x = ((np.arange(nx) + 0.5) * h)[None, None, :] * np.ones(shape)
+    g.set_phi(np.ascontiguousarray(x))
+    g.set_full_domain(True)
+    dt = h / 4
+    g.step(1, dt, ls.LS_DT_FIXED)
+    F = (x - g.get_phi()) / dt   # plane phi = x: |grad| = 1, so phi drops by F dt
+    assert np.max(np.abs(F - ref)) <= 1e-9
+
+
+def test_bounded_wait_times_out_and_device_stays_usable():
+    st = ls.selftest_bounded_wait(1000)
+    assert st & 1
+    g = ls.LevelSet(16, 16, 16, 1 / 16, ls.LS_FP32)
+    g.init_phi(ls.LS_SHAPE_SPHERES, inputs.spheres_params([(0.5, 0.5, 0.5)], [0.3]))
+    g.set_speed_const(1.0)
+    g.band_rebuild(3.0)
+    g.step(3, 0.5, ls.LS_DT_CFL, 2)
+    assert g.status() == ls.LS_OK
