@@ -45,10 +45,7 @@ constexpr int HALF_BYTES = PB * 16;
 constexpr int XS_BYTES = 2 * HALF_BYTES;
 constexpr int W_BYTES = 27 * 512;  // 27 taps x (16 x 16 bf16)
 constexpr int MT = BY * BZ;        // M-tiles per block
-constexpr int TMEM_COLS = 64;      // MT * 16, rounded to a power of two >= 32
 constexpr long long WAIT_LIMIT = 1ll << 26;
-
-static_assert(MT * 16 <= TMEM_COLS, "TMEM columns");
 
 __device__ __forceinline__ unsigned smem_u32(const void* p)
 {
@@ -159,31 +156,52 @@ struct ConvArgs {
     int mode;                    // 0 bias+ReLU, 1 bias (channel 0, FP32), 2 ReLU mask
 };
 
-__global__ void __launch_bounds__(128, 1) k_conv3_tc(const __grid_constant__ CUtensorMap map0,
-                                                     const __grid_constant__ CUtensorMap map1,
-                                                     ConvArgs a)
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised pipeline, one CTA per SM, 6 warps:
+//   warp 0      TMA producer: halo'd input block -> shared stage s (2 stages)
+//   warp 1      TMEM owner and MMA issuer: 4 M-tiles x 27 taps into TMEM
+//               accumulator buffer b (2 buffers x 64 columns)
+//   warps 2..5  epilogue: TMEM -> registers -> global (warp w reads lane
+//               quadrant w % 4)
+// Barriers: full[s] (TMA bytes landed), empty[s] (MMAs reading stage s
+// finished), acc_full[b] (accumulators ready), acc_empty[b] (epilogue done,
+// 4 arrivals).  Block i of this CTA uses stage and buffer i % 2.
+constexpr int NSTAGE = 2;
+constexpr int CONV_THREADS = 192;
+constexpr int ACC_COLS = 64;  // per accumulator buffer
+
+__global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_constant__ CUtensorMap map0,
+                                                              const __grid_constant__ CUtensorMap map1,
+                                                              ConvArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* xs = smem;                     // X block, XS_BYTES
-    unsigned char* ws = smem + XS_BYTES;          // packed weights, W_BYTES
-    __shared__ __align__(8) unsigned long long tma_bar, mma_bar;
+    unsigned char* ws = smem + NSTAGE * XS_BYTES;  // packed weights
+    __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE], acc_full[2], acc_empty[2];
     __shared__ unsigned tmem_base_s;
-    __shared__ int abort_s;
+    __shared__ volatile int abort_s;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // weights -> shared memory (generic proxy), then make them visible to the
-    // tensor core's async proxy
-    for (int i = tid; i < W_BYTES / 16; i += 128)
+    for (int i = tid; i < W_BYTES / 16; i += CONV_THREADS)
         reinterpret_cast<uint4*>(ws)[i] = reinterpret_cast<const uint4*>(a.wpack)[i];
     if (tid == 0) {
-        mbar_init(&tma_bar, 1);
-        mbar_init(&mma_bar, 1);
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);
+        }
         abort_s = 0;
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_s)),
-                     "r"(TMEM_COLS)
+                     "r"(2 * ACC_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -192,96 +210,122 @@ __global__ void __launch_bounds__(128, 1) k_conv3_tc(const __grid_constant__ CUt
     __syncthreads();
     fence_after();
     const unsigned tmem = tmem_base_s;
-
     const int nbx = a.nx / CX, nby = a.ny / BY, nbz = a.nz / BZ;
     const int nblocks = nbx * nby * nbz;
-    unsigned phase = 0;
-    const unsigned xs_addr = smem_u32(xs), ws_addr = smem_u32(ws);
-    for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
-        const int bx = blk % nbx;
-        const int by = (blk / nbx) % nby;
-        const int bz = blk / (nbx * nby);
-        const int x0 = bx * CX, y0 = by * BY, z0 = bz * BZ;
-        if (tid == 0) {
-            mbar_expect_tx(&tma_bar, XS_BYTES);
-            tma_load_4d(xs, &map0, 0, x0 - 1, y0 - 1, z0 - 1, &tma_bar);
-            tma_load_4d(xs + HALF_BYTES, &map1, 0, x0 - 1, y0 - 1, z0 - 1, &tma_bar);
+    const unsigned xs_addr = smem_u32(smem), ws_addr = smem_u32(ws);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int i = 0;
+            for (int blk = blockIdx.x; blk < nblocks && !abort_s; blk += gridDim.x, ++i) {
+                const int s = i % NSTAGE, u = i / NSTAGE;
+                if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    abort_s = 1;
+                    break;
+                }
+                const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
+                unsigned char* xs = smem + s * XS_BYTES;
+                mbar_expect_tx(&full[s], XS_BYTES);
+                tma_load_4d(xs, &map0, 0, bx * CX - 1, by * BY - 1, bz * BZ - 1, &full[s]);
+                tma_load_4d(xs + HALF_BYTES, &map1, 0, bx * CX - 1, by * BY - 1, bz * BZ - 1, &full[s]);
+            }
         }
-        if (!mbar_wait(&tma_bar, phase)) {
-            if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
-            abort_s = 1;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int i = 0;
+            for (int blk = blockIdx.x; blk < nblocks && !abort_s; blk += gridDim.x, ++i) {
+                const int s = i % NSTAGE, u = i / NSTAGE;
+                const int b = i % 2, ub = i / 2;
+                if (!mbar_wait(&full[s], u & 1) || (ub > 0 && !mbar_wait(&acc_empty[b], (ub - 1) & 1))) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    abort_s = 1;
+                    break;
+                }
+                fence_after();
+                // descriptors are linear in the start address (field =
+                // address >> 4, all shared addresses < 256 KB): the 108 MMAs
+                // of a block differ only by compile-time offsets
+                const unsigned long long da = smem_desc(xs_addr + s * XS_BYTES, HALF_BYTES, 128);
+                const unsigned long long db = smem_desc(ws_addr, 256, 128);
+                const unsigned acc = tmem + b * ACC_COLS;
+#pragma unroll
+                for (int j = 0; j < MT; ++j) {
+#pragma unroll
+                    for (int t = 0; t < 27; ++t) {
+                        const int pofs = ((j / BY + 1 + t / 9 - 1) * PY + (j % BY + 1 + (t / 3) % 3 - 1)) * PX +
+                                         (1 + t % 3 - 1);
+                        mma_bf16(acc + 16 * j, da + (unsigned long long)pofs,
+                                 db + (unsigned long long)(t * 32), t > 0 ? 1u : 0u);
+                    }
+                }
+                mma_commit(&empty[s]);
+                mma_commit(&acc_full[b]);
+            }
         }
-        __syncthreads();
-        if (abort_s) break;
-        if (tid == 0) {
+    } else {
+        // epilogue warps: lane quadrant q = warp % 4 -> points x0 + 32 q + lane
+        const int q = warp & 3;
+        int i = 0;
+        for (int blk = blockIdx.x; blk < nblocks && !abort_s; blk += gridDim.x, ++i) {
+            const int b = i % 2, ub = i / 2;
+            if (!mbar_wait(&acc_full[b], ub & 1)) {
+                if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+                abort_s = 1;
+                break;
+            }
             fence_after();
+            const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
+            const int x = bx * CX + 32 * q + lane;
             for (int j = 0; j < MT; ++j) {
-                const int jy = j % BY, jz = j / BY;
-                for (int t = 0; t < 27; ++t) {
-                    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-                    const int p = ((jz + 1 + dz) * PY + (jy + 1 + dy)) * PX + (1 + dx);
-                    const unsigned long long ad = smem_desc(xs_addr + p * 16, HALF_BYTES, 128);
-                    const unsigned long long bd = smem_desc(ws_addr + t * 512, 256, 128);
-                    mma_bf16(tmem + 16 * j, ad, bd, t > 0 ? 1u : 0u);
+                const int y = by * BY + j % BY, z = bz * BZ + j / BY;
+                float v[16];
+                tmem_ld16(tmem + b * ACC_COLS + ((unsigned)(32 * q) << 16) + 16 * j, v);
+                const size_t pidx = ((size_t)z * a.ny + y) * a.nx + x;
+                if (a.mode == 1) {
+                    a.out_f32[pidx] = v[0] + a.bias[0];
+                    continue;
                 }
-            }
-            mma_commit(&mma_bar);
-        }
-        if (!mbar_wait(&mma_bar, phase)) {
-            if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
-            abort_s = 2;
-        }
-        __syncthreads();
-        if (abort_s) {
-            // MMAs may still be in flight: give them one more bounded wait
-            // before the TMEM is released
-            mbar_wait(&mma_bar, phase);
-            break;
-        }
-        fence_after();
-        // epilogue: warp w reads TMEM lanes 32w.. = points x0 + 32w + lane
-        const int x = x0 + 32 * warp + lane;
-        for (int j = 0; j < MT; ++j) {
-            const int y = y0 + j % BY, z = z0 + j / BY;
-            float v[16];
-            tmem_ld16(tmem + ((unsigned)(32 * warp) << 16) + 16 * j, v);
-            const size_t p = ((size_t)z * a.ny + y) * a.nx + x;
-            if (a.mode == 1) {
-                a.out_f32[p] = v[0] + a.bias[0];
-                continue;
-            }
-            if (a.mode == 0) {
+                if (a.mode == 0) {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + a.bias[c], 0.f);
-            } else {
-                const uint4* mp = reinterpret_cast<const uint4*>(a.mask + p * 16);
-                const uint4 m0 = mp[0], m1 = mp[1];
-                const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
-                const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+                    for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + a.bias[c], 0.f);
+                } else {
+                    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + pidx * 16);
+                    const uint4 m0 = mp[0], m1 = mp[1];
+                    const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
+                    const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if (!(__bfloat162float(mb0[c]) > 0.f)) v[c] = 0.f;
-                    if (!(__bfloat162float(mb1[c]) > 0.f)) v[8 + c] = 0.f;
+                    for (int c = 0; c < 8; ++c) {
+                        if (!(__bfloat162float(mb0[c]) > 0.f)) v[c] = 0.f;
+                        if (!(__bfloat162float(mb1[c]) > 0.f)) v[8 + c] = 0.f;
+                    }
                 }
-            }
-            uint4 o[2];
-            __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(o);
+                uint4 o[2];
+                __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(o);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) ob[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
-            uint4* dp = reinterpret_cast<uint4*>(a.out_bf16 + p * 16);
-            dp[0] = o[0];
-            dp[1] = o[1];
+                for (int c = 0; c < 8; ++c) ob[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+                uint4* dp = reinterpret_cast<uint4*>(a.out_bf16 + pidx * 16);
+                dp[0] = o[0];
+                dp[1] = o[1];
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
-        fence_before();
-        __syncthreads();
-        phase ^= 1u;
     }
+    // all roles done (or aborted): MMAs issued by warp 1 have completed once
+    // the epilogue has consumed every accumulator; on abort, give in-flight
+    // work one more bounded wait before releasing TMEM
     fence_before();
     __syncthreads();
+    if (abort_s && tid == 32) {
+        for (int b = 0; b < 2; ++b) mbar_wait(&acc_full[b], 0, 1 << 20);
+    }
+    __syncthreads();
     fence_after();
-    if (warp == 0)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS)
+                     "r"(2 * ACC_COLS)
                      : "memory");
 }
 
@@ -381,7 +425,7 @@ cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float
                          int mode, unsigned* status, cudaStream_t s)
 {
     static bool attr = false;
-    const int smem = XS_BYTES + W_BYTES;
+    const int smem = NSTAGE * XS_BYTES + W_BYTES;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -402,9 +446,9 @@ cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int nblocks = (nx / CX) * (ny / BY) * (nz / BZ);
-    int grid = 2 * sms;
+    int grid = sms;
     if (grid > nblocks) grid = nblocks;
-    k_conv3_tc<<<grid, 128, smem, s>>>(maps[0], maps[1], a);
+    k_conv3_tc<<<grid, CONV_THREADS, smem, s>>>(maps[0], maps[1], a);
     return cudaGetLastError();
 }
 
