@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    p.add_argument("--n", type=int, default=512, help="grid edge (512 = the standard workload)")
+    p.add_argument("--grid", type=int, default=512, help="grid edge (512 = the standard workload)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", choices=["sphere-union", "batch", "learned", "perturbed", "sphere64"],
@@ -85,6 +85,19 @@ def dist_setup(args):
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return world, rank, local, pg
+
+
+def aggregate(pg, t_s, updates, device="cpu"):
+    """Whole-job time and work over the ranks: the slowest rank's time and the
+    sum of all ranks' updates (replicas: every rank did its own work)."""
+    if pg is None:
+        return t_s, updates
+    import torch
+    t = torch.tensor([t_s], dtype=torch.float64, device=device)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(u, op=pg.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def measured_peaks():
@@ -199,7 +212,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = inputs.SphereUnion(n=args.n)
+    w = inputs.SphereUnion(n=args.grid)
     phi = w.phi(out_dtype=inputs.torch.float32).numpy().astype(np.float64)
     F = w.speed(out_dtype=inputs.torch.float32).numpy().astype(np.float64)
     o = oracle.Oracle(phi.shape, w.h)
@@ -228,10 +241,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)",
-        "config": {"workload": WORKLOAD, "grid": args.n, "reference_step": "5 level-set steps (one rebuild period)"},
+        "config": {"workload": WORKLOAD, "grid": args.grid, "reference_step": "5 level-set steps (one rebuild period)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "%d x 5 level-set steps of the %d^3 workload after %d warm-up periods"
-                                   % (args.steps, args.n, args.warmup)},
+                                   % (args.steps, args.grid, args.warmup)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -545,7 +558,7 @@ def main():
     world, rank, local, pg = dist_setup(args)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    w = inputs.SphereUnion(n=args.n)
+    w = inputs.SphereUnion(n=args.grid)
     g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32, stream=stream.cuda_stream)
     # Step 0 on the device: the library's own SDF / speed generators (FP64
     # evaluation, stored FP32); phi^0 kept as a device snapshot for the runs
@@ -602,16 +615,7 @@ def main():
     prof = g.profile()
     updates = g.updates() - u0
 
-    t_s = ms / 1e3
-    if pg:
-        tt = torch.tensor([t_s, float(updates)], dtype=torch.float64, device=dev)
-        tmax = tt[:1].clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        usum = tt[1:].clone()
-        pg.all_reduce(usum, op=pg.ReduceOp.SUM)
-        t_s, total_updates = float(tmax.item()), float(usum.item())
-    else:
-        total_updates = float(updates)
+    t_s, total_updates = aggregate(pg, ms / 1e3, float(updates), dev)
     value = total_updates / t_s / 1e9
 
     # dominant kernel: the upwind step, timed by events around every launch
