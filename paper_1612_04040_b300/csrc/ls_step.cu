@@ -22,6 +22,8 @@
 // Optionally (CLASSIFY) the kernel also evaluates the tube test of Eq. 6 on
 // the values it has just written: min |phi^{n+1}| over the tile < gamma in
 // FP64.  That saves the rebuild a full re-read of the active tiles.
+#include <cstddef>
+
 #include "ls_internal.cuh"
 
 namespace lsk {
@@ -47,6 +49,22 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pr
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred = true)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %2, 0;\n"
+        "  @p cp.async.ca.shared.global [%0], [%1], 4; }\n" ::"r"(s), "l"(gmem), "r"((int)pred)
+        : "memory");
+}
+// same, with a precomputed shared-memory address; when pred is false the
+// instruction is not executed, so the global address is never dereferenced
+__device__ __forceinline__ void cp_async16s(unsigned s, const void* gmem, bool pred = true)
+{
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %2, 0;\n"
+        "  @p cp.async.cg.shared.global [%0], [%1], 16; }\n" ::"r"(s), "l"(gmem), "r"((int)pred)
+        : "memory");
+}
+__device__ __forceinline__ void cp_async4s(unsigned s, const void* gmem, bool pred = true)
+{
     asm volatile(
         "{ .reg .pred p; setp.ne.b32 p, %2, 0;\n"
         "  @p cp.async.ca.shared.global [%0], [%1], 4; }\n" ::"r"(s), "l"(gmem), "r"((int)pred)
@@ -191,10 +209,20 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     const int i_zp = (lz < 7) ? tid + 16 : z_slot;
     const int i_pc = 4 * (tid ^ 1) + (xh ? 3 : 0);
 
+    // shared addresses of this thread's slots in stage 0
+    const unsigned sm0 = (unsigned)__cvta_generic_to_shared(st);
+    constexpr unsigned SB = (unsigned)sizeof(Stage32);
+    const unsigned a_c = sm0 + (unsigned)offsetof(Stage32, v) + 16u * tid;
+    const unsigned a_f = sm0 + (unsigned)offsetof(Stage32, f) + 16u * tid;
+    const unsigned a_x = sm0 + (unsigned)offsetof(Stage32, xo) + 4u * tid;
+    const unsigned a_y = sm0 + (unsigned)offsetof(Stage32, v) + 16u * y_slot;
+    const unsigned a_z = sm0 + (unsigned)offsetof(Stage32, v) + 16u * z_slot;
+
     // stage list entry (t, info, instance) into ring slot s
     auto issue = [&](unsigned t, unsigned info, unsigned inst, int s) {
         const unsigned base = t * TILE_PTS;
         const float* tp = src + base;
+        const unsigned so = (unsigned)s * SB;
         Stage32& Sg = st[s];
         if (tid == 0) {
             Sg.meta = make_int4((int)t, (int)info, (int)inst, 0);
@@ -206,12 +234,11 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
             y_off = y_sgn * (tnx * TILE_PTS) + y_in;
             z_off = z_sgn * (tnx * tny * TILE_PTS) + z_in;
         }
-        cp_async16(&Sg.v[tid], tp + 4 * tid);
-        if (FIELD) cp_async16(&Sg.f[tid], Fp + base + 4 * tid);
-        const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0, pz = (info & z_bit) != 0;
-        cp_async4(&Sg.xo[tid], px ? tp + x_off : tp, px);
-        cp_async16(&Sg.v[y_slot], py ? tp + y_off : tp, py);
-        cp_async16(&Sg.v[z_slot], pz ? tp + z_off : tp, pz);
+        cp_async16s(a_c + so, tp + 4 * tid);
+        if (FIELD) cp_async16s(a_f + so, Fp + base + 4 * tid);
+        cp_async4s(a_x + so, tp + x_off, (info & x_bit) != 0);
+        cp_async16s(a_y + so, tp + y_off, (info & y_bit) != 0);
+        cp_async16s(a_z + so, tp + z_off, (info & z_bit) != 0);
     };
     auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
         t = (unsigned)__ldg(list + k);
@@ -231,9 +258,10 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         cp_async_commit();
         kn += stride;
     }
-    // list entry after that, fetched one iteration ahead of its staging
-    unsigned t_next = 0, i_next = 0, n_next = 0;
-    if (kn < n) fetch(kn, t_next, i_next, n_next);
+    // the next two list entries, fetched two iterations ahead of their staging
+    unsigned t1 = 0, i1 = 0, n1 = 0, t2 = 0, i2 = 0, n2 = 0;
+    if (kn < n) fetch(kn, t1, i1, n1);
+    if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
     int cur = 0;
     int prev = -1;
     int prev_t = -1, prev_inst = 0;
@@ -243,11 +271,14 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         if (CLASSIFY && tid == 0 && prev >= 0)
             a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma_of(prev_inst)) ? 1 : 0;
         {
-            const int sn = (cur + S - 1) % S;
-            if (kn < n) issue(t_next, i_next, n_next, sn);
+            const int sn = cur == 0 ? S - 1 : cur - 1;
+            if (kn < n) issue(t1, i1, n1, sn);
             cp_async_commit();
             kn += stride;
-            if (kn < n) fetch(kn, t_next, i_next, n_next);
+            t1 = t2;
+            i1 = i2;
+            n1 = n2;
+            if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
         }
         const Stage32& Sg = st[cur];
         const int t = Sg.meta.x;
@@ -293,7 +324,7 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         prev = cur;
         prev_t = t;
         prev_inst = inst;
-        cur = (cur + 1) % S;
+        cur = cur + 1 == S ? 0 : cur + 1;
     }
     if (CLASSIFY) {
         __syncthreads();
@@ -357,9 +388,18 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
     const int i_pc0 = 4 * (q0 ^ 1) + (xh ? 3 : 0);
     const int i_pc1 = 4 * (q1 ^ 1) + (xh ? 3 : 0);
 
+    const unsigned sm0 = (unsigned)__cvta_generic_to_shared(st);
+    constexpr unsigned SB = (unsigned)sizeof(Stage32);
+    const unsigned a_c0 = sm0 + (unsigned)offsetof(Stage32, v) + 16u * q0;
+    const unsigned a_f0 = sm0 + (unsigned)offsetof(Stage32, f) + 16u * q0;
+    const unsigned a_x0 = sm0 + (unsigned)offsetof(Stage32, xo) + 4u * q0;
+    const unsigned a_y0 = sm0 + (unsigned)offsetof(Stage32, v) + 16u * y_slot0;
+    const unsigned a_z = sm0 + (unsigned)offsetof(Stage32, v) + 16u * z_slot;
+
     auto issue = [&](unsigned t, unsigned info, unsigned inst, int s) {
         const unsigned base = t * TILE_PTS;
         const float* tp = src + base;
+        const unsigned so = (unsigned)s * SB;
         Stage32& Sg = st[s];
         if (tid == 0) {
             Sg.meta = make_int4((int)t, (int)info, (int)inst, 0);
@@ -371,18 +411,18 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
             y_off = y_sgn * (tnx * TILE_PTS) + y_in;
             z_off = z_sgn * (tnx * tny * TILE_PTS) + z_in;
         }
-        cp_async16(&Sg.v[q0], tp + 4 * q0);
-        cp_async16(&Sg.v[q1], tp + 4 * q1);
+        cp_async16s(a_c0 + so, tp + 4 * q0);
+        cp_async16s(a_c0 + so + 256u, tp + 4 * q1);
         if (FIELD) {
-            cp_async16(&Sg.f[q0], Fp + base + 4 * q0);
-            cp_async16(&Sg.f[q1], Fp + base + 4 * q1);
+            cp_async16s(a_f0 + so, Fp + base + 4 * q0);
+            cp_async16s(a_f0 + so + 256u, Fp + base + 4 * q1);
         }
-        const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0, pz = (info & z_bit) != 0;
-        cp_async4(&Sg.xo[q0], px ? tp + x_off0 : tp, px);
-        cp_async4(&Sg.xo[q1], px ? tp + x_off0 + 64 : tp, px);
-        cp_async16(&Sg.v[y_slot0], py ? tp + y_off : tp, py);
-        cp_async16(&Sg.v[y_slot1], py ? tp + y_off + 64 : tp, py);
-        cp_async16(&Sg.v[z_slot], pz ? tp + z_off : tp, pz);
+        const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0;
+        cp_async4s(a_x0 + so, tp + x_off0, px);
+        cp_async4s(a_x0 + so + 64u, tp + x_off0 + 64, px);
+        cp_async16s(a_y0 + so, tp + y_off, py);
+        cp_async16s(a_y0 + so + 32u, tp + y_off + 64, py);
+        cp_async16s(a_z + so, tp + z_off, (info & z_bit) != 0);
     };
     auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
         t = (unsigned)__ldg(list + k);
@@ -402,8 +442,9 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
         cp_async_commit();
         kn += stride;
     }
-    unsigned t_next = 0, i_next = 0, n_next = 0;
-    if (kn < n) fetch(kn, t_next, i_next, n_next);
+    unsigned t1 = 0, i1 = 0, n1 = 0, t2 = 0, i2 = 0, n2 = 0;
+    if (kn < n) fetch(kn, t1, i1, n1);
+    if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
     int cur = 0, prev = -1, prev_t = -1, prev_inst = 0;
     for (int k = blockIdx.x; k < n; k += stride) {
         cp_async_wait<S - 2>();
@@ -411,11 +452,14 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
         if (CLASSIFY && tid == 0 && prev >= 0)
             a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma_of(prev_inst)) ? 1 : 0;
         {
-            const int sn = (cur + S - 1) % S;
-            if (kn < n) issue(t_next, i_next, n_next, sn);
+            const int sn = cur == 0 ? S - 1 : cur - 1;
+            if (kn < n) issue(t1, i1, n1, sn);
             cp_async_commit();
             kn += stride;
-            if (kn < n) fetch(kn, t_next, i_next, n_next);
+            t1 = t2;
+            i1 = i2;
+            n1 = n2;
+            if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
         }
         const Stage32& Sg = st[cur];
         const int t = Sg.meta.x;
@@ -463,7 +507,7 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
         prev = cur;
         prev_t = t;
         prev_inst = inst;
-        cur = (cur + 1) % S;
+        cur = cur + 1 == S ? 0 : cur + 1;
     }
     if (CLASSIFY) {
         __syncthreads();
