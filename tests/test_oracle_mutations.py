@@ -1,0 +1,45 @@
+"""The pins are strong enough to catch plausible slips: each test plants one
+mistake in a copy of the oracle's C source (on the CPU, in a temporary
+directory), rebuilds it, and checks that the pin tests then fail."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "max_min_swapped_in_G_plus": ("const double ax = max0(dmx), bx = min0(dpx);",
+                                  "const double ax = min0(dmx), bx = max0(dpx);"),
+    "dropped_z_term": ("const double spz = az * az + bz * bz;", "const double spz = az * az;"),
+    "F_sign_routed_wrong": ("max0(F) * gplus + min0(F) * gminus", "max0(F) * gminus + min0(F) * gplus"),
+    "wrong_y_stride": ("one_sided(phi, i, (size_t)nx, y, ny", "one_sided(phi, i, (size_t)ny, y, ny"),
+    "high_face_rule_missing": ("if (!has_p && has_m) p = m;", ""),
+    "tube_not_strict": ("fabs(phi[idx3(nx, ny, x, y, z)]) < gamma", "fabs(phi[idx3(nx, ny, x, y, z)]) <= gamma"),
+    "dilation_6_for_26": ("if (conn == 6 && manhattan > 1) continue;", "if (manhattan > 1) continue;"),
+    "transposed_conv_weight": ("out[o] += in[c] * w[c * co + o];", "out[o] += in[c] * w[o * ci + c];"),
+    "unflipped_conv_adjoint": ("const int X = xx - dx, Y = yy - dyy, Z = z - dz;",
+                               "const int X = xx + dx, Y = yy + dyy, Z = z + dz;"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "levelset_oracle.c")).read()
+    assert src.count(old) >= 1, name
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    (tmp_path / "oracle" / "levelset_oracle.c").write_text(src.replace(old, new, 1))
+    shutil.copytree(os.path.join(ROOT, "paper_1612_04040_b300"), tmp_path / "paper_1612_04040_b300",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__", "_build", "csrc"))
+    shutil.copytree(os.path.join(ROOT, "tests"), tmp_path / "tests",
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py", "tests/test_oracle_learned_pins.py"],
+                       cwd=tmp_path, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "mutation %s was not caught:\n%s" % (name, r.stdout[-1500:])
