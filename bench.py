@@ -66,7 +66,19 @@ def parse():
                         "learned: corrector training + learned-coarse vs plain at equal error")
     p.add_argument("--pairs", type=int, default=2000)
     p.add_argument("--train-iters", type=int, default=2000)
+    p.add_argument("--step-config", default=None, metavar="STAGES,GRID_PCT,PPT",
+                   help="fix the stencil launch configuration instead of autotuning it "
+                        "(so that a profiler run times the same kernel as the plain run)")
     return p.parse_args()
+
+
+def tune(obj, args):
+    """Autotune the stencil launch configuration, or apply --step-config."""
+    if args.step_config:
+        st, pct, ppt = (int(v) for v in args.step_config.split(","))
+        obj.set_step_config(st, pct, ppt)
+        return st, pct, ppt
+    return obj.autotune(reps=5)
 
 
 def dist_setup(args):
@@ -272,7 +284,7 @@ def run_batch(args):
     b.snapshot()
     b.band_rebuild(4.0)
     b.step(5, 0.5, ls.LS_DT_CFL, 5)
-    stages, pct, ppt = b.autotune(reps=5)
+    stages, pct, ppt = tune(b, args)
 
     def run_once():
         b.restore()
@@ -579,7 +591,7 @@ def main():
     g.restore()
     g.band_rebuild(w.halfwidth, want_count=False)
     g.step(w.steps // 2, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
-    tuned = g.autotune(reps=5)
+    tuned = tune(g, args)
     for _ in range(max(args.warmup, 0)):
         run_once()
     torch.cuda.synchronize()

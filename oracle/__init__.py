@@ -13,6 +13,14 @@ What it computes, and where the paper defines it (arXiv 1612.04040):
 * ``dilate``          -- Eq. 11 (section 1.1), region N as a one-tile dilation.
 * ``compact``         -- the array of active points (section 2), as tile ids.
 * ``max_abs_speed``   -- CFL bound (the paper gives no rule for dt in Eq. 3).
+* ``cutoff``, ``cut_step`` -- Eq. 7 and Eq. 8 (section 1.1): the advance of the
+                         local scheme with the cut-off factor c(|phi|).
+* ``region_n``        -- Eq. 11 pointwise: T plus its one-cell face ring.
+* ``reinit_iter``, ``clamp`` -- Eq. 12-13 (one pseudo-time iteration of the
+                         reinitialisation) and Eq. 10 (section 1.1).
+* ``local_step``      -- Steps 1-3 of the narrow-band algorithm (section 1.1)
+                         as one step: N, cut-off advance, reinitialisation on
+                         N, clamp.
 * ``Oracle``          -- the rebuild / step schedule of Steps 0-2 of the
                          narrow-band algorithm (section 1.1), with the same
                          call semantics as the C ABI of the library.
@@ -83,6 +91,19 @@ def _load():
             lib.orc_conv3_bwd_weight.argtypes = [ci, ci, ci, ci, ci, dp, dp, dp, dp]
             lib.orc_restrict4.restype = None
             lib.orc_restrict4.argtypes = [ci, ci, ci, dp, dp]
+            lib.orc_cutoff.restype = cd
+            lib.orc_cutoff.argtypes = [cd, cd, cd]
+            lib.orc_cut_step.restype = None
+            lib.orc_cut_step.argtypes = [ci, ci, ci, cd, ci, dp, dp, cd, cd, cd, cd, dp]
+            lib.orc_region_n.restype = None
+            lib.orc_region_n.argtypes = [ci, ci, ci, dp, cd, u8p]
+            lib.orc_reinit_iter.restype = None
+            lib.orc_reinit_iter.argtypes = [ci, ci, ci, cd, ci, dp, u8p, cd, dp]
+            lib.orc_clamp.restype = None
+            lib.orc_clamp.argtypes = [c64, dp, u8p, cd]
+            lib.orc_local_step.restype = None
+            lib.orc_local_step.argtypes = [ci, ci, ci, cd, ci, dp, dp, cd, cd, cd, cd, ci, cd, dp, dp,
+                                           u8p]
             _lib = lib
     return _lib
 
@@ -182,7 +203,73 @@ def max_abs_speed(shape, F=None, Fc=0.0, tile_active=None, tile=8):
                                        float(Fc), _ptr(ta, ctypes.c_uint8)))
 
 
+def cutoff(a, beta, gamma):
+    """Eq. 7: c at a = |phi| (scalar)."""
+    return float(_load().orc_cutoff(float(a), float(beta), float(gamma)))
+
+
+def cut_step(phi, h, dt, beta, gamma, F=None, Fc=0.0, bc="extrapolate"):
+    """Eq. 8 as Eq. 3 with the speed c(|phi|) F, at every point."""
+    lib = _load()
+    phi = _f64(phi)
+    nz, ny, nx = phi.shape
+    Fa = None if F is None else _f64(F)
+    out = np.empty_like(phi)
+    lib.orc_cut_step(nx, ny, nz, float(h), BC[bc], _ptr(phi, ctypes.c_double),
+                     _ptr(Fa, ctypes.c_double), float(Fc), float(beta), float(gamma), float(dt),
+                     _ptr(out, ctypes.c_double))
+    return out
+
+
+def region_n(phi, gamma):
+    """Eq. 11 pointwise: 1 where the point or a face neighbour has |phi| < gamma."""
+    lib = _load()
+    phi = _f64(phi)
+    nz, ny, nx = phi.shape
+    m = np.empty(phi.shape, dtype=np.uint8)
+    lib.orc_region_n(nx, ny, nz, _ptr(phi, ctypes.c_double), float(gamma), _ptr(m, ctypes.c_uint8))
+    return m
+
+
+def reinit_iter(d, h, dtau, nmask=None, bc="extrapolate"):
+    """One pseudo-time iteration of Eq. 12 on the points of nmask (all if None)."""
+    lib = _load()
+    d = _f64(d)
+    nz, ny, nx = d.shape
+    m = None if nmask is None else np.ascontiguousarray(nmask, dtype=np.uint8)
+    out = np.empty_like(d)
+    lib.orc_reinit_iter(nx, ny, nz, float(h), BC[bc], _ptr(d, ctypes.c_double),
+                        _ptr(m, ctypes.c_uint8), float(dtau), _ptr(out, ctypes.c_double))
+    return out
+
+
+def clamp(d, gamma, nmask=None):
+    """Eq. 10 on the points of nmask (all if None); returns a new array."""
+    lib = _load()
+    out = _f64(d).copy()
+    m = None if nmask is None else np.ascontiguousarray(nmask, dtype=np.uint8)
+    lib.orc_clamp(out.size, _ptr(out, ctypes.c_double), _ptr(m, ctypes.c_uint8), float(gamma))
+    return out
+
+
+def local_step(phi, h, dt, beta, gamma, iters, dtau, F=None, Fc=0.0, bc="extrapolate"):
+    """Steps 1-3 of section 1.1 as one step; returns (phi^{n+1}, N mask)."""
+    lib = _load()
+    phi = _f64(phi)
+    nz, ny, nx = phi.shape
+    Fa = None if F is None else _f64(F)
+    out = np.empty_like(phi)
+    work = np.empty(2 * phi.size)
+    m = np.empty(phi.shape, dtype=np.uint8)
+    lib.orc_local_step(nx, ny, nz, float(h), BC[bc], _ptr(phi, ctypes.c_double),
+                       _ptr(Fa, ctypes.c_double), float(Fc), float(beta), float(gamma), float(dt),
+                       int(iters), float(dtau), _ptr(out, ctypes.c_double),
+                       _ptr(work, ctypes.c_double), _ptr(m, ctypes.c_uint8))
+    return out, m
+
+
 DT_FIXED, DT_CFL = 0, 1
+SCHEME_PLAIN, SCHEME_LOCAL = 0, 1
 
 
 class Oracle:
@@ -197,6 +284,10 @@ class Oracle:
       ``rebuild_every`` steps have run since the last rebuild.  dt = CFL*h/M
       (CFL*h when M = 0) in DT_CFL mode, else dt_or_cfl.
     * full-domain mode: every tile active, no rebuilds, M over the whole grid.
+    * ``set_scheme(SCHEME_LOCAL, beta_in_h, iters, dtau_in_h)``: each step is
+      ``local_step`` (section 1.1, Steps 1-3) over the whole grid; the tiles
+      serve only the CFL bound.  ``breaches`` counts N points that lay in
+      inactive tiles (where a tiled engine would not update them).
     """
 
     def __init__(self, shape, h, tile=8, conn=26, bc="extrapolate"):
@@ -217,6 +308,9 @@ class Oracle:
         self.M = None
         self.last_dt = None
         self.rebuild_log = []  # active-tile id arrays, one per rebuild
+        self.scheme = SCHEME_PLAIN
+        self.local = None      # (beta_in_h, iters, dtau_in_h)
+        self.breaches = 0
 
     # -- state -----------------------------------------------------------
     def set_phi(self, phi):
@@ -240,6 +334,11 @@ class Oracle:
     def set_full_domain(self, on):
         self.full_domain = bool(on)
         self.band_valid = False
+
+    def set_scheme(self, scheme, beta_in_h=None, iters=None, dtau_in_h=None):
+        self.scheme = int(scheme)
+        if self.scheme == SCHEME_LOCAL:
+            self.local = (float(beta_in_h), int(iters), float(dtau_in_h))
 
     # -- band ------------------------------------------------------------
     def _speed_bound(self, active):
@@ -293,7 +392,19 @@ class Oracle:
                 dt = float(dt_or_cfl) * self.h / self.M if self.M > 0 else float(dt_or_cfl) * self.h
             else:
                 dt = float(dt_or_cfl)
-            self.phi = step(self.phi, self.h, dt, self.F, self.Fc or 0.0, active, self.tile, self.bc)
+            if self.scheme == SCHEME_LOCAL:
+                b_h, iters, dtau_h = self.local
+                gamma = self.halfwidth * self.h
+                self.phi, nmask = local_step(self.phi, self.h, dt, b_h * self.h, gamma, iters,
+                                             dtau_h * self.h, self.F, self.Fc or 0.0, self.bc)
+                if active is not None:
+                    t = self.tile
+                    act_pts = np.repeat(np.repeat(np.repeat(active, t, 0), t, 1), t, 2)
+                    act_pts = act_pts[:self.shape[0], :self.shape[1], :self.shape[2]]
+                    self.breaches += int(np.count_nonzero(nmask.astype(bool) & ~act_pts.astype(bool)))
+            else:
+                self.phi = step(self.phi, self.h, dt, self.F, self.Fc or 0.0, active, self.tile,
+                                self.bc)
             self.since_rebuild += 1
             self.last_dt = dt
         return self.last_dt

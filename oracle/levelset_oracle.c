@@ -15,7 +15,12 @@
  *   Eq. 4  G+ = sqrt(sum over axes of max(D-,0)^2 + min(D+,0)^2)
  *   Eq. 5  G- = sqrt(sum over axes of max(D+,0)^2 + min(D-,0)^2)
  *   Eq. 6  tube T = {x : |phi(x)| < gamma}                (section 1.1)
+ *   Eq. 7  cut-off c(|phi|): 1 up to beta, cubic to 0 at gamma (section 1.1)
+ *   Eq. 8  phi_t + c(phi) F |grad phi| = 0 on T           (section 1.1)
+ *   Eq. 10 clamp of the reinitialised d to [-gamma, gamma] (section 1.1)
  *   Eq. 11 region N = points with a +-dx neighbour in T    (section 1.1)
+ *   Eq. 12 d_tau + S(d)(|grad d| - 1) = 0, d(x,0) = phi-bar (section 1.1)
+ *   Eq. 13 S = d / sqrt(d^2 + |Dd|^2 dx^2)                 (section 1.1)
  *
  * Readings where the paper is silent (each one is listed in the design notes):
  *   - D-x = (phi_i - phi_{i-1})/h, D+x = (phi_{i+1} - phi_i)/h, and the same
@@ -31,6 +36,15 @@
  *     active set is the core set dilated by one tile (26 or 6 neighbours).
  *     tile = 1 with the 6-neighbour dilation gives exactly the pointwise T
  *     and N of Eq. 6 and Eq. 11.  Points outside active tiles do not change.
+ *
+ *   - Local scheme (Steps 1-3 of section 1.1): Eq. 8 is discretised as
+ *     Eq. 3 with the speed c(|phi^n|) F; N (Eq. 11) is the point set whose
+ *     point or one of its six face neighbours is in T, taken from phi^n;
+ *     Eq. 12 is iterated a given number of times with the upwind gradient of
+ *     Eq. 4 where d > 0 and of Eq. 5 where d < 0 (S carries the sign of d),
+ *     |Dd| in Eq. 13 is that same gradient, the pseudo time step is a given
+ *     dtau; then Eq. 10 clamps the values on N.  Points outside N keep
+ *     their value throughout.
  *
  * Layout: phi[z][y][x], x fastest: index = (z*ny + y)*nx + x.
  * Build: -O2 -ffp-contract=off (no fused multiply-add anywhere), optional
@@ -326,4 +340,143 @@ void orc_restrict4(int nfx, int nfy, int nfz, const double *fine, double *coarse
                             s += fine[idx3(nfx, nfy, 4 * X + i, 4 * Y + j, 4 * Z + k)];
                 coarse[idx3(ncx, ncy, X, Y, Z)] = s / 8.0;
             }
+}
+
+/* ------------------------------------------------------------------------
+ * Local level-set scheme of section 1.1 (Steps 1-3): cut-off advance,
+ * reinitialisation on N, clamp.
+ * ---------------------------------------------------------------------- */
+
+/* Eq. 7: the cut-off factor at a = |phi| for 0 < beta < gamma. */
+double orc_cutoff(double a, double beta, double gamma)
+{
+    if (a <= beta) return 1.0;
+    if (a < gamma) {
+        const double u = a - gamma;
+        const double w = gamma - beta;
+        return (u * u) * ((2.0 * a + gamma) - 3.0 * beta) / ((w * w) * w);
+    }
+    return 0.0;
+}
+
+/* Eq. 8 discretised as Eq. 3 with the speed c(|phi^n|) F at every point
+ * (c = 0 outside T, so those points keep their value). */
+void orc_cut_step(int nx, int ny, int nz, double h, int bc, const double *phi,
+                  const double *F, double Fc, double beta, double gamma, double dt,
+                  double *out)
+{
+    int z;
+#pragma omp parallel for schedule(static)
+    for (z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t i = idx3(nx, ny, x, y, z);
+                const double f = F ? F[i] : Fc;
+                const double c = orc_cutoff(fabs(phi[i]), beta, gamma);
+                out[i] = orc_point_update(nx, ny, nz, h, bc, phi, f * c, dt, x, y, z);
+            }
+}
+
+/* Eq. 11: nmask[i] = 1 when point i or one of its six face neighbours
+ * (inside the domain) is in T, i.e. has |phi| < gamma. */
+void orc_region_n(int nx, int ny, int nz, const double *phi, double gamma, uint8_t *nmask)
+{
+    int z;
+#pragma omp parallel for schedule(static)
+    for (z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int in = fabs(phi[idx3(nx, ny, x, y, z)]) < gamma;
+                if (!in && x > 0) in = fabs(phi[idx3(nx, ny, x - 1, y, z)]) < gamma;
+                if (!in && x < nx - 1) in = fabs(phi[idx3(nx, ny, x + 1, y, z)]) < gamma;
+                if (!in && y > 0) in = fabs(phi[idx3(nx, ny, x, y - 1, z)]) < gamma;
+                if (!in && y < ny - 1) in = fabs(phi[idx3(nx, ny, x, y + 1, z)]) < gamma;
+                if (!in && z > 0) in = fabs(phi[idx3(nx, ny, x, y, z - 1)]) < gamma;
+                if (!in && z < nz - 1) in = fabs(phi[idx3(nx, ny, x, y, z + 1)]) < gamma;
+                nmask[idx3(nx, ny, x, y, z)] = (uint8_t)in;
+            }
+}
+
+/* One pseudo-time iteration of Eq. 12 at one point:
+ *   g = G+ (Eq. 4) if d > 0, G- (Eq. 5) if d < 0;
+ *   S = d / sqrt(d^2 + g^2 h^2)                      (Eq. 13, |Dd| = g)
+ *   d_new = d - dtau * (S * (g - 1)).
+ * d = 0 gives S = 0: the value stays. */
+double orc_reinit_point(int nx, int ny, int nz, double h, int bc, const double *d,
+                        double dtau, int x, int y, int z)
+{
+    const size_t i = idx3(nx, ny, x, y, z);
+    const double di = d[i];
+    if (di == 0.0) return di;
+    double dmx, dpx, dmy, dpy, dmz, dpz;
+    one_sided(d, i, 1, x, nx, h, bc, &dmx, &dpx);
+    one_sided(d, i, (size_t)nx, y, ny, h, bc, &dmy, &dpy);
+    one_sided(d, i, (size_t)nx * (size_t)ny, z, nz, h, bc, &dmz, &dpz);
+    double g;
+    if (di > 0.0) {
+        const double ax = max0(dmx), bx = min0(dpx);
+        const double ay = max0(dmy), by = min0(dpy);
+        const double az = max0(dmz), bz = min0(dpz);
+        g = sqrt(((ax * ax + bx * bx) + (ay * ay + by * by)) + (az * az + bz * bz));
+    } else {
+        const double cx = max0(dpx), ex = min0(dmx);
+        const double cy = max0(dpy), ey = min0(dmy);
+        const double cz = max0(dpz), ez = min0(dmz);
+        g = sqrt(((cx * cx + ex * ex) + (cy * cy + ey * ey)) + (cz * cz + ez * ez));
+    }
+    const double S = di / sqrt(di * di + (g * g) * (h * h));
+    return di - dtau * (S * (g - 1.0));
+}
+
+/* One iteration of Eq. 12 on the points with nmask set (every point when
+ * nmask is NULL); the others are copied. */
+void orc_reinit_iter(int nx, int ny, int nz, double h, int bc, const double *d,
+                     const uint8_t *nmask, double dtau, double *out)
+{
+    int z;
+#pragma omp parallel for schedule(static)
+    for (z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t i = idx3(nx, ny, x, y, z);
+                if (nmask && !nmask[i]) {
+                    out[i] = d[i];
+                    continue;
+                }
+                out[i] = orc_reinit_point(nx, ny, nz, h, bc, d, dtau, x, y, z);
+            }
+}
+
+/* Eq. 10 on the points with nmask set (every point when nmask is NULL). */
+void orc_clamp(int64_t n, double *d, const uint8_t *nmask, double gamma)
+{
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; ++i) {
+        if (nmask && !nmask[i]) continue;
+        if (d[i] < -gamma) d[i] = -gamma;
+        else if (d[i] > gamma) d[i] = gamma;
+    }
+}
+
+/* One step of the local scheme: N from phi^n (Eq. 11), the cut-off advance
+ * (Eq. 8) to phi-bar, `iters` iterations of Eq. 12 on N starting from
+ * phi-bar, and the clamp of Eq. 10 on N.  work: 2 * n doubles, nmask_out:
+ * n bytes (the N of this step). */
+void orc_local_step(int nx, int ny, int nz, double h, int bc, const double *phi,
+                    const double *F, double Fc, double beta, double gamma, double dt,
+                    int iters, double dtau, double *out, double *work, uint8_t *nmask_out)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    double *a = work, *b = work + n;
+    orc_region_n(nx, ny, nz, phi, gamma, nmask_out);
+    orc_cut_step(nx, ny, nz, h, bc, phi, F, Fc, beta, gamma, dt, a);
+    for (int m = 0; m < iters; ++m) {
+        orc_reinit_iter(nx, ny, nz, h, bc, a, nmask_out, dtau, b);
+        double *t = a;
+        a = b;
+        b = t;
+    }
+    orc_clamp((int64_t)n, a, nmask_out, gamma);
+    memcpy(out, a, n * sizeof(double));
 }

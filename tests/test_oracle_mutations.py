@@ -22,6 +22,13 @@ MUTATIONS = {
     "transposed_conv_weight": ("out[o] += in[c] * w[c * co + o];", "out[o] += in[c] * w[o * ci + c];"),
     "unflipped_conv_adjoint": ("const int X = xx - dx, Y = yy - dyy, Z = z - dz;",
                                "const int X = xx + dx, Y = yy + dyy, Z = z + dz;"),
+    "cutoff_wrong_beta_factor": ("((2.0 * a + gamma) - 3.0 * beta)", "((2.0 * a + gamma) - 2.0 * beta)"),
+    "cutoff_of_signed_phi": ("orc_cutoff(fabs(phi[i]), beta, gamma)", "orc_cutoff(phi[i], beta, gamma)"),
+    "reinit_upwind_swapped": ("if (di > 0.0) {", "if (di < 0.0) {"),
+    "reinit_S_without_dx": ("(g * g) * (h * h)", "(g * g)"),
+    "reinit_source_sign": ("di - dtau * (S * (g - 1.0))", "di + dtau * (S * (g - 1.0))"),
+    "region_n_missing_z_plus": ("if (!in && z < nz - 1) in = fabs(phi[idx3(nx, ny, x, y, z + 1)]) < gamma;", ""),
+    "clamp_lower_side_missing": ("if (d[i] < -gamma) d[i] = -gamma;\n        else ", ""),
 }
 
 
@@ -40,6 +47,7 @@ def test_planted_mistake_is_caught(name, tmp_path):
                     ignore=shutil.ignore_patterns("__pycache__"))
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "tests/test_oracle_pins.py", "tests/test_oracle_learned_pins.py"],
+                        "tests/test_oracle_pins.py", "tests/test_oracle_learned_pins.py",
+                        "tests/test_oracle_local_pins.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "mutation %s was not caught:\n%s" % (name, r.stdout[-1500:])
