@@ -62,6 +62,7 @@ typedef enum {
 enum { LS_FP32 = 0, LS_FP64 = 1 };               /* storage + arithmetic precision */
 enum { LS_DT_FIXED = 0, LS_DT_CFL = 1 };         /* meaning of dt_or_cfl           */
 enum { LS_PLAIN = 0, LS_LEARNED = 1 };           /* step flavour                   */
+enum { LS_SCHEME_PLAIN = 0, LS_SCHEME_LOCAL = 1 }; /* advance scheme (ls_set_scheme) */
 enum { LS_BC_EXTRAPOLATE = 0, LS_BC_NEUMANN = 1 };
 
 /* ---------------------------------------------------------------------
@@ -153,6 +154,41 @@ int ls_band_rebuild(ls_ctx *ctx, double halfwidth_in_h, long long *n_active_tile
 int ls_step(ls_ctx *ctx, int nsteps, double dt_or_cfl, int dt_mode,
             int rebuild_every, double *last_dt);
 
+/* Advance scheme of ls_step.
+ *
+ * LS_SCHEME_PLAIN (default): Eq. 3 with speed F on the active tiles.
+ *
+ * LS_SCHEME_LOCAL: the paper's local level-set algorithm (section 1.1,
+ * Steps 1-3), one ls_step step being
+ *   1. N = the points whose point or one of its six face neighbours has
+ *      |phi^n| < gamma (Eq. 11; T of Eq. 6 plus its one-cell ring);
+ *   2. the cut-off advance phi-bar = Eq. 3 with the speed c(|phi^n|) F,
+ *      c of Eq. 7 with beta = beta_in_h * h and gamma = halfwidth * h (so
+ *      points with |phi| >= gamma keep their value: Eq. 8 on T);
+ *   3. reinit_iters pseudo-time iterations of Eq. 12 on N from d = phi-bar:
+ *      d <- d - dtau S (g - 1), g = the upwind |grad d| of Eq. 4 where d > 0
+ *      and of Eq. 5 where d < 0, S = d / sqrt(d^2 + g^2 h^2) (Eq. 13),
+ *      dtau = dtau_in_h * h; points outside N keep their value;
+ *   4. the clamp of Eq. 10 on N: phi^{n+1} = min(max(d, -gamma), gamma).
+ * The passes run on the active tiles (band, rebuilds, CFL and frozen tiles
+ * as in the plain scheme); the result equals the pointwise algorithm
+ * while the active tiles contain N, which ls_band_breaches checks.
+ * reinit_iters = -1 selects ceil(halfwidth / dtau_in_h) iterations (enough
+ * for the pseudo-time front to cross the band once; "steady state").
+ * Single FP32 / FP64 contexts; not with the learned step mode.  Takes effect
+ * at the next ls_step; beta_in_h must be below the band's halfwidth then
+ * (LS_ESTATE otherwise).
+ * Errors: LS_EINVAL (unknown scheme, beta_in_h or dtau_in_h <= 0 or not
+ * finite, reinit_iters < -1, batched context), LS_ESTATE (learned mode on),
+ * LS_ENOMEM, LS_ECUDA. */
+int ls_set_scheme(ls_ctx *ctx, int scheme, double beta_in_h, int reinit_iters, double dtau_in_h);
+
+/* Number of (point of T, inactive face-neighbour tile) pairs met by the
+ * local scheme's advance passes since ls_set_scheme: 0 means every point of
+ * N lay inside the active tiles, so the tiled passes computed exactly the
+ * pointwise algorithm.  Synchronises the stream. */
+int ls_band_breaches(ls_ctx *ctx, unsigned long long *n);
+
 /* Full-domain mode on/off: every tile is active and no rebuild happens
  * (the O(n^3) variant the narrow band of section 1.1 replaces). */
 int ls_set_full_domain(ls_ctx *ctx, int on);
@@ -211,6 +247,9 @@ typedef struct {
     double stencil_ms;                   /* summed device time of the step launches
                                             made while profiling was enabled         */
     unsigned long long stencil_timed;    /* number of launches stencil_ms covers     */
+    double reinit_ms;                    /* of stencil_ms: reinitialisation passes of
+                                            the local scheme (Eq. 12)                */
+    unsigned long long reinit_timed;     /* number of launches reinit_ms covers      */
 } ls_profile;
 
 /* Enable (1) or disable (0) CUDA-event timing of every upwind-step launch

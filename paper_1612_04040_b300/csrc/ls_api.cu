@@ -84,11 +84,15 @@ int drain_events(ls_ctx* c)
     CK(cudaStreamSynchronize(c->stream));
     for (auto& p : c->ev_pending) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, p.first, p.second));
+        CK(cudaEventElapsedTime(&ms, p.e0, p.e1));
         c->stencil_ms += ms;
         c->stencil_timed += 1;
-        c->ev_free.push_back(p.first);
-        c->ev_free.push_back(p.second);
+        if (p.reinit) {
+            c->reinit_ms += ms;
+            c->reinit_timed += 1;
+        }
+        c->ev_free.push_back(p.e0);
+        c->ev_free.push_back(p.e1);
     }
     c->ev_pending.clear();
     return LS_OK;
@@ -126,14 +130,15 @@ void free_all(ls_ctx* c)
 {
     clear_graphs(c);
     for (auto& p : c->ev_pending) {
-        cudaEventDestroy(p.first);
-        cudaEventDestroy(p.second);
+        cudaEventDestroy(p.e0);
+        cudaEventDestroy(p.e1);
     }
     for (auto e : c->ev_free) cudaEventDestroy(e);
     void* ptrs[] = {c->phi[0], c->phi[1], c->F, c->tile_maxF, c->tile_sgn, c->staging, c->snapshot, c->core,
                     c->act, c->list, c->list_info, c->d_count, c->block_counts, c->d_sc,
                     c->d_Mbits, c->d_updates, c->d_status, c->d_nonfinite, c->d_inst,
-                    c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params};
+                    c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params, c->nmask,
+                    c->d_breaches};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -279,6 +284,36 @@ lsk::StepArgs step_args(ls_ctx* c, bool classify)
     return a;
 }
 
+int local_iters(const ls_ctx* c)
+{
+    if (c->reinit_iters >= 0) return c->reinit_iters;
+    return (int)std::ceil(c->halfwidth / c->dtau_in_h - 1e-12);
+}
+
+// FP32 copies of the local scheme's thresholds: the branch thresholds are
+// rounded outward so that float comparisons decide as the FP64 ones do
+lsk::LocalParams local_params(const ls_ctx* c)
+{
+    const Inst& in = c->insts[0];
+    lsk::LocalParams lp{};
+    lp.gamma = in.gamma;
+    lp.beta = c->beta_in_h * in.h;
+    lp.dtau = c->dtau_in_h * in.h;
+    float b = (float)lp.beta;
+    if ((double)b > lp.beta) b = std::nextafter(b, -INFINITY);
+    float g = (float)lp.gamma;
+    if ((double)g < lp.gamma) g = std::nextafter(g, INFINITY);
+    lp.beta_dn = b;
+    lp.gamma_up = g;
+    lp.beta_n = (float)lp.beta;
+    lp.gamma_n = (float)lp.gamma;
+    const double w = lp.gamma - lp.beta;
+    lp.inv_w3 = (float)(1.0 / (w * w * w));
+    lp.lam = (float)c->dtau_in_h;
+    lp.dtau_f = (float)lp.dtau;
+    return lp;
+}
+
 // the step loop of ls_step (eager, or recorded into a graph by the caller)
 int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every, cudaStream_t s)
 {
@@ -310,22 +345,43 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
         // correction applied afterwards the rebuild classifies again instead
         const bool classify = !c->full_domain && rebuild_every > 0 &&
                               c->since_rebuild + 1 >= rebuild_every && c->step_mode == LS_PLAIN;
-        const lsk::StepArgs a = step_args(c, classify);
-        if (c->profiling && c->ev_pending.size() >= 4096) RET(drain_events(c));
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (c->profiling) {
-            CK(take_event(c, &e0));
-            CK(take_event(c, &e1));
-            CK(cudaEventRecord(e0, s));
+        // plain: one pass; local scheme: the cut-off advance, then the
+        // reinitialisation passes (the last one clamps); the fused tube test
+        // goes with the last pass of the step
+        const bool local = c->scheme == LS_SCHEME_LOCAL;
+        const int K = local ? local_iters(c) : 0;
+        const int npass = 1 + K;
+        for (int p = 0; p < npass; ++p) {
+            const bool last = p == npass - 1;
+            lsk::StepArgs a = step_args(c, classify && last);
+            if (local) {
+                a.op = p == 0 ? (K == 0 ? lsk::OP_CUT_CLAMP : lsk::OP_CUT)
+                              : (last ? lsk::OP_REINIT_CLAMP : lsk::OP_REINIT);
+                a.lp = local_params(c);
+                a.nmask = c->nmask;
+                a.act = c->act;
+                a.breaches = p == 0 ? c->d_breaches : nullptr;
+                if (p > 0) {
+                    a.F = nullptr;
+                    a.updates = nullptr;  // updates count the advance (Eq. 8) only
+                }
+            }
+            if (c->profiling && c->ev_pending.size() >= 4096) RET(drain_events(c));
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (c->profiling) {
+                CK(take_event(c, &e0));
+                CK(take_event(c, &e1));
+                CK(cudaEventRecord(e0, s));
+            }
+            KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
+            ++c->stencil_launches;
+            if (c->profiling) {
+                CK(cudaEventRecord(e1, s));
+                c->ev_pending.push_back({e0, e1, p > 0});
+            }
+            if (c->step_mode == LS_LEARNED) RET(ls_engine_learned_after_step(c, s));
+            c->cur ^= 1;
         }
-        KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
-        ++c->stencil_launches;
-        if (c->profiling) {
-            CK(cudaEventRecord(e1, s));
-            c->ev_pending.emplace_back(e0, e1);
-        }
-        if (c->step_mode == LS_LEARNED) RET(ls_engine_learned_after_step(c, s));
-        c->cur ^= 1;
         c->since_rebuild += 1;
         c->core_fresh = classify;
     }
@@ -368,7 +424,8 @@ int run_steps_graph(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuil
     long long vbits = 0;
     std::memcpy(&vbits, &value, sizeof(vbits));
     const GraphKey key{c->cur, c->since_rebuild, (int)c->band_valid, (int)c->core_fresh,
-                       (int)c->full_domain | (c->step_mode << 1), nsteps, rebuild_every, dt_mode, vbits,
+                       (int)c->full_domain | (c->step_mode << 1) | (c->scheme << 3), nsteps,
+                       rebuild_every, dt_mode, vbits,
                        c->cfg.stages * 16 + c->cfg.ppt, c->cfg.grid_pct};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
@@ -724,6 +781,8 @@ int ls_step(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every,
     if (!(value > 0.0) || !std::isfinite(value)) return LS_EINVAL;
     if (!all_phi_set(c) || speed_mode(c) == 0) return LS_ESTATE;
     if (!c->full_domain && !c->have_halfwidth) return LS_ESTATE;
+    if (c->scheme == LS_SCHEME_LOCAL && (!c->have_halfwidth || !(c->beta_in_h < c->halfwidth)))
+        return LS_ESTATE;
     c->dt_mode = dt_mode;
     c->dt_value = value;
     if (nsteps > 0) {
@@ -980,6 +1039,8 @@ int ls_get_profile(ls_ctx* c, ls_profile* out)
     out->stencil_launches = c->stencil_launches;
     out->stencil_ms = c->stencil_ms;
     out->stencil_timed = c->stencil_timed;
+    out->reinit_ms = c->reinit_ms;
+    out->reinit_timed = c->reinit_timed;
     return LS_OK;
 }
 
@@ -991,6 +1052,42 @@ int ls_reset_profile(ls_ctx* c)
     c->stencil_launches = 0;
     c->stencil_ms = 0.0;
     c->stencil_timed = 0;
+    c->reinit_ms = 0.0;
+    c->reinit_timed = 0;
+    return LS_OK;
+}
+
+int ls_set_scheme(ls_ctx* c, int scheme, double beta_in_h, int reinit_iters, double dtau_in_h)
+{
+    if (!c) return LS_EINVAL;
+    if (scheme == LS_SCHEME_PLAIN) {
+        c->scheme = LS_SCHEME_PLAIN;
+        clear_graphs(c);
+        return LS_OK;
+    }
+    if (scheme != LS_SCHEME_LOCAL || c->batched) return LS_EINVAL;
+    if (!(beta_in_h > 0.0) || !std::isfinite(beta_in_h)) return LS_EINVAL;
+    if (!(dtau_in_h > 0.0) || !std::isfinite(dtau_in_h)) return LS_EINVAL;
+    if (reinit_iters < -1) return LS_EINVAL;
+    if (c->step_mode != LS_PLAIN) return LS_ESTATE;
+    if (!c->nmask) CK(dalloc(&c->nmask, (size_t)c->ntiles * 16 * sizeof(uint32_t)));
+    if (!c->d_breaches) CK(dalloc(&c->d_breaches, sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(c->d_breaches, 0, sizeof(unsigned long long), c->stream));
+    c->scheme = LS_SCHEME_LOCAL;
+    c->beta_in_h = beta_in_h;
+    c->reinit_iters = reinit_iters;
+    c->dtau_in_h = dtau_in_h;
+    clear_graphs(c);
+    return LS_OK;
+}
+
+int ls_band_breaches(ls_ctx* c, unsigned long long* n)
+{
+    if (!c || !n) return LS_EINVAL;
+    *n = 0;
+    if (!c->d_breaches) return LS_OK;
+    CK(cudaMemcpyAsync(n, c->d_breaches, sizeof(*n), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return LS_OK;
 }
 

@@ -95,7 +95,18 @@ struct ls_ctx {
     double stencil_ms = 0.0;
     unsigned long long stencil_timed = 0;
     std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    double reinit_ms = 0.0;
+    unsigned long long reinit_timed = 0;
+    struct EvPair { cudaEvent_t e0, e1; bool reinit; };
+    std::vector<EvPair> ev_pending;
+
+    // local scheme (section 1.1, Steps 1-3)
+    int scheme = LS_SCHEME_PLAIN;
+    double beta_in_h = 0.0;
+    double dtau_in_h = 0.5;
+    int reinit_iters = -1;
+    uint32_t* nmask = nullptr;                 // N bits, 16 words per list entry
+    unsigned long long* d_breaches = nullptr;
 
     // learned corrector
     int step_mode = LS_PLAIN;

@@ -109,6 +109,26 @@ cudaError_t launch_set_dt(StepScalars* sc, int n_inst, const Inst* d_inst, const
 // ---------------------------------------------------------------------------
 // launchers (ls_step.cu)
 // ---------------------------------------------------------------------------
+// Passes of the local scheme (section 1.1, Steps 1-3).  One step is OP_CUT
+// (Eq. 8 as Eq. 3 with the speed c(|phi|) F, writing the mask of N of
+// Eq. 11) and then K passes OP_REINIT (one pseudo-time iteration of Eq. 12
+// on N), the last one OP_REINIT_CLAMP (plus Eq. 10 on N); with K = 0 the
+// advance is OP_CUT_CLAMP.
+enum : int { OP_PLAIN = 0, OP_CUT = 1, OP_CUT_CLAMP = 2, OP_REINIT = 3, OP_REINIT_CLAMP = 4 };
+
+struct LocalParams {
+    double beta, gamma;   // Eq. 7 thresholds (FP64)
+    double dtau;          // pseudo-time step of Eq. 12
+    float beta_dn;        // largest float <= beta: FP32 |phi| <= beta decided as in FP64
+    float gamma_up;       // smallest float >= gamma: FP32 |phi| < gamma decided as in FP64,
+                          // and the clamp bound (a clamped value is not in T)
+    float beta_n, gamma_n;  // nearest floats (the cubic of Eq. 7)
+    float inv_w3;         // 1 / (gamma - beta)^3
+    float lam;            // dtau / h
+    float dtau_f;         // dtau
+    int pad;
+};
+
 struct StepArgs {
     const void* src;
     void* dst;
@@ -123,6 +143,12 @@ struct StepArgs {
     unsigned long long* updates;
     Inst in;                  // single instance parameters (bc is read from here always)
     int max_grid;             // cap on the persistent grid (0 = none)
+    // local scheme (single instance, 4 points per thread)
+    int op;                   // OP_*
+    LocalParams lp;
+    uint32_t* nmask;          // N of Eq. 11: 16 words (512 bits) per list entry
+    const uint8_t* act;       // per-tile flags, bit 0 = active (breach test)
+    unsigned long long* breaches;  // N points found in inactive tiles
 };
 
 // launch configuration of the FP32 stencil, chosen by the autotuner

@@ -369,6 +369,7 @@ int ls_set_step_mode(ls_ctx* c, int mode)
 {
     if (!c || (mode != LS_PLAIN && mode != LS_LEARNED)) return LS_EINVAL;
     if (mode == LS_LEARNED && (!c->learned || !c->learned->initialised)) return LS_ESTATE;
+    if (mode == LS_LEARNED && c->scheme != LS_SCHEME_PLAIN) return LS_ESTATE;
     c->step_mode = mode;
     return LS_OK;
 }

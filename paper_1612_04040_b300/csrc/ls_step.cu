@@ -159,12 +159,121 @@ __device__ __forceinline__ float4 upd4(const float4& c, const float4& f, float x
     return make_float4(r[0], r[1], r[2], r[3]);
 }
 
+// ------------------------------------------------- local scheme, FP32 ----
+// Eq. 7 at a = |phi|.  The branch tests use thresholds rounded outward on the
+// host (largest float <= beta, smallest float >= gamma), so they decide
+// exactly as the FP64 comparisons with beta and gamma do.
+__device__ __forceinline__ float cut32(float a, const LocalParams& lp)
+{
+    if (a <= lp.beta_dn) return 1.f;
+    if (a < lp.gamma_up) {
+        const float u = a - lp.gamma_n;
+        return u * u * (2.f * a + lp.gamma_n - 3.f * lp.beta_n) * lp.inv_w3;
+    }
+    return 0.f;
+}
+
+// Eq. 11 for the thread's four points: bit j set when point j or one of its
+// face neighbours inside the domain is in T (|phi| < gamma, FP64-exact test).
+__device__ __forceinline__ unsigned n_nibble(const float4& c, float xm0, float xp3, const float4& ym,
+                                             const float4& yp, const float4& zm, const float4& zp,
+                                             bool xlo, bool xhi, bool ylo, bool yhi, bool zlo,
+                                             bool zhi, float g)
+{
+    const float xs[6] = {xm0, c.x, c.y, c.z, c.w, xp3};
+    unsigned nb = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        bool in = fabsf(xs[j + 1]) < g;
+        in |= (j > 0 || !xlo) && fabsf(xs[j]) < g;
+        in |= (j < 3 || !xhi) && fabsf(xs[j + 2]) < g;
+        in |= !ylo && fabsf(comp(ym, j)) < g;
+        in |= !yhi && fabsf(comp(yp, j)) < g;
+        in |= !zlo && fabsf(comp(zm, j)) < g;
+        in |= !zhi && fabsf(comp(zp, j)) < g;
+        nb |= (in ? 1u : 0u) << j;
+    }
+    return nb;
+}
+
+// One pseudo-time iteration of Eq. 12 at the thread's four points (those
+// with their N bit set; the others keep their value): the upwind gradient of
+// Eq. 4 where d > 0 and of Eq. 5 where d < 0 (through G-(d) = G+(-d)),
+// S = d / sqrt(d^2 + |Dd|^2 h^2) (Eq. 13) with unscaled differences, then
+// d - dtau S (|grad d| - 1); CLAMP: Eq. 10 afterwards, to +-(smallest float
+// >= gamma), so that a clamped value stays outside T as in FP64.
+template <bool FACES, bool CLAMP>
+__device__ __forceinline__ float4 rei4(const float4& c, float xm0, float xp3, const float4& ym,
+                                       const float4& yp, const float4& zm, const float4& zp,
+                                       unsigned nb, const LocalParams& lp, bool extrap, bool xlo,
+                                       bool xhi, bool ylo, bool yhi, bool zlo, bool zhi)
+{
+    const float xs[6] = {xm0, c.x, c.y, c.z, c.w, xp3};
+    float r[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float d = xs[j + 1];
+        float dmx = d - xs[j], dpx = xs[j + 2] - d;
+        float dmy = d - comp(ym, j), dpy = comp(yp, j) - d;
+        float dmz = d - comp(zm, j), dpz = comp(zp, j) - d;
+        if (FACES) {
+            if (j == 0 && xlo) dmx = extrap ? dpx : 0.f;
+            if (j == 3 && xhi) dpx = extrap ? dmx : 0.f;
+            if (ylo) dmy = extrap ? dpy : 0.f;
+            if (yhi) dpy = extrap ? dmy : 0.f;
+            if (zlo) dmz = extrap ? dpz : 0.f;
+            if (zhi) dpz = extrap ? dmz : 0.f;
+        }
+        const float s = d > 0.f ? 1.f : -1.f;
+        const float ax = fmaxf(s * dmx, 0.f), bx = fminf(s * dpx, 0.f);
+        const float ay = fmaxf(s * dmy, 0.f), by = fminf(s * dpy, 0.f);
+        const float az = fmaxf(s * dmz, 0.f), bz = fminf(s * dpz, 0.f);
+        float q = ax * ax;
+        q = fmaf(bx, bx, q);
+        q = fmaf(ay, ay, q);
+        q = fmaf(by, by, q);
+        q = fmaf(az, az, q);
+        q = fmaf(bz, bz, q);
+        const float gu = q * rsqrt_hw(fmaxf(q, 1e-30f));
+        const float S = d * rsqrt_hw(fmaxf(fmaf(d, d, gu * gu), 1e-30f));
+        float v = fmaf(-S, fmaf(lp.lam, gu, -lp.dtau_f), d);
+        if (CLAMP) v = fminf(fmaxf(v, -lp.gamma_up), lp.gamma_up);
+        r[j] = ((nb >> j) & 1u) ? v : d;
+    }
+    return make_float4(r[0], r[1], r[2], r[3]);
+}
+
+// N points that fall in inactive tiles: points of T on a face of this tile
+// whose face neighbour tile is inside the domain but not active, counted once
+// per (point, face).  Zero while the active tiles cover N (the tiled step
+// then equals the pointwise one).
+__device__ __forceinline__ void count_breaches(const StepArgs& a, const float4& c, int t,
+                                               unsigned info, int xh, int ly, int lz)
+{
+    const float g = a.lp.gamma_up;
+    const unsigned tb = (fabsf(c.x) < g ? 1u : 0u) | (fabsf(c.y) < g ? 2u : 0u) |
+                        (fabsf(c.z) < g ? 4u : 0u) | (fabsf(c.w) < g ? 8u : 0u);
+    if (!tb) return;
+    const int tnx = a.in.tnx, tpl = a.in.tnx * a.in.tny;
+    const unsigned nt = __popc(tb);
+    unsigned bad = 0;
+    if (xh == 0 && (tb & 1u) && (info & NB_XM) && !(__ldg(a.act + t - 1) & 1)) bad += 1;
+    if (xh == 1 && (tb & 8u) && (info & NB_XP) && !(__ldg(a.act + t + 1) & 1)) bad += 1;
+    if (ly == 0 && (info & NB_YM) && !(__ldg(a.act + t - tnx) & 1)) bad += nt;
+    if (ly == 7 && (info & NB_YP) && !(__ldg(a.act + t + tnx) & 1)) bad += nt;
+    if (lz == 0 && (info & NB_ZM) && !(__ldg(a.act + t - tpl) & 1)) bad += nt;
+    if (lz == 7 && (info & NB_ZP) && !(__ldg(a.act + t + tpl) & 1)) bad += nt;
+    if (bad) atomicAdd(a.breaches, (unsigned long long)bad);
+}
+
 // FIELD: speed field (else constant per instance); CLASSIFY: fused tube
 // test; BATCHED: list entries belong to different instances (per-entry
-// instance id, per-instance dt/h, speed, strides and gamma); S: stages.
-template <bool FIELD, bool CLASSIFY, bool BATCHED, int S>
+// instance id, per-instance dt/h, speed, strides and gamma); S: stages;
+// OP: OP_PLAIN (Eq. 3) or a pass of the local scheme (single instance).
+template <bool FIELD, bool CLASSIFY, bool BATCHED, int S, int OP = OP_PLAIN>
 __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
 {
+
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Stage32* st = reinterpret_cast<Stage32*>(smem_raw);
     __shared__ unsigned smin[S];
@@ -217,9 +326,12 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     const unsigned a_x = sm0 + (unsigned)offsetof(Stage32, xo) + 4u * tid;
     const unsigned a_y = sm0 + (unsigned)offsetof(Stage32, v) + 16u * y_slot;
     const unsigned a_z = sm0 + (unsigned)offsetof(Stage32, v) + 16u * z_slot;
+    // N masks of the staged entries (reinitialisation passes)
+    __shared__ __align__(16) uint32_t nmk[OP >= OP_REINIT ? S : 1][16];
+    const unsigned a_m = (unsigned)__cvta_generic_to_shared(&nmk[0][0]) + 16u * (tid & 3);
 
-    // stage list entry (t, info, instance) into ring slot s
-    auto issue = [&](unsigned t, unsigned info, unsigned inst, int s) {
+    // stage list entry kk = (t, info, instance) into ring slot s
+    auto issue = [&](unsigned t, unsigned info, unsigned inst, int s, int kk) {
         const unsigned base = t * TILE_PTS;
         const float* tp = src + base;
         const unsigned so = (unsigned)s * SB;
@@ -239,6 +351,8 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         cp_async4s(a_x + so, tp + x_off, (info & x_bit) != 0);
         cp_async16s(a_y + so, tp + y_off, (info & y_bit) != 0);
         cp_async16s(a_z + so, tp + z_off, (info & z_bit) != 0);
+        if (OP >= OP_REINIT && tid < 4)
+            cp_async16s(a_m + 64u * (unsigned)s, a.nmask + (size_t)kk * 16 + 4 * tid);
     };
     auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
         t = (unsigned)__ldg(list + k);
@@ -253,7 +367,7 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         if (kn < n) {
             unsigned t, info, inst;
             fetch(kn, t, info, inst);
-            issue(t, info, inst, s);
+            issue(t, info, inst, s, kn);
         }
         cp_async_commit();
         kn += stride;
@@ -272,7 +386,7 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
             a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma_of(prev_inst)) ? 1 : 0;
         {
             const int sn = cur == 0 ? S - 1 : cur - 1;
-            if (kn < n) issue(t1, i1, n1, sn);
+            if (kn < n) issue(t1, i1, n1, sn, kn);
             cp_async_commit();
             kn += stride;
             t1 = t2;
@@ -298,12 +412,23 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         const float xp3 = xh ? xo : pcv;
 
         float4 o;
-        if (info == (NB_ALL | SG_POS)) {
-            o = upd4<1, false>(c, f, xm0, xp3, ym, yp, zm, zp, coef, extrap, false, false, false,
-                               false, false, false);
-        } else if (info == (NB_ALL | SG_NEG)) {
-            o = upd4<-1, false>(c, f, xm0, xp3, ym, yp, zm, zp, coef, extrap, false, false, false,
-                                false, false, false);
+        if constexpr (OP == OP_PLAIN) {
+            if (info == (NB_ALL | SG_POS)) {
+                o = upd4<1, false>(c, f, xm0, xp3, ym, yp, zm, zp, coef, extrap, false, false,
+                                   false, false, false, false);
+            } else if (info == (NB_ALL | SG_NEG)) {
+                o = upd4<-1, false>(c, f, xm0, xp3, ym, yp, zm, zp, coef, extrap, false, false,
+                                    false, false, false, false);
+            } else {
+                const bool xlo = (xh == 0) && !(info & NB_XM);
+                const bool xhi = (xh == 1) && !(info & NB_XP);
+                const bool ylo = (ly == 0) && !(info & NB_YM);
+                const bool yhi = (ly == 7) && !(info & NB_YP);
+                const bool zlo = (lz == 0) && !(info & NB_ZM);
+                const bool zhi = (lz == 7) && !(info & NB_ZP);
+                o = upd4<0, true>(c, f, xm0, xp3, ym, yp, zm, zp, coef, extrap, xlo, xhi, ylo,
+                                  yhi, zlo, zhi);
+            }
         } else {
             const bool xlo = (xh == 0) && !(info & NB_XM);
             const bool xhi = (xh == 1) && !(info & NB_XP);
@@ -311,8 +436,47 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
             const bool yhi = (ly == 7) && !(info & NB_YP);
             const bool zlo = (lz == 0) && !(info & NB_ZM);
             const bool zhi = (lz == 7) && !(info & NB_ZP);
-            o = upd4<0, true>(c, f, xm0, xp3, ym, yp, zm, zp, coef, extrap, xlo, xhi, ylo, yhi,
-                              zlo, zhi);
+            if constexpr (OP == OP_CUT || OP == OP_CUT_CLAMP) {
+                // Eq. 8: the plain update with the speed c(|phi^n|) F (c >= 0
+                // keeps the tile's speed-sign class)
+                const float4 fs = make_float4(f.x * cut32(fabsf(c.x), a.lp), f.y * cut32(fabsf(c.y), a.lp),
+                                              f.z * cut32(fabsf(c.z), a.lp), f.w * cut32(fabsf(c.w), a.lp));
+                if (info == (NB_ALL | SG_POS))
+                    o = upd4<1, false>(c, fs, xm0, xp3, ym, yp, zm, zp, coef, extrap, false, false,
+                                       false, false, false, false);
+                else if (info == (NB_ALL | SG_NEG))
+                    o = upd4<-1, false>(c, fs, xm0, xp3, ym, yp, zm, zp, coef, extrap, false, false,
+                                        false, false, false, false);
+                else
+                    o = upd4<0, true>(c, fs, xm0, xp3, ym, yp, zm, zp, coef, extrap, xlo, xhi, ylo,
+                                      yhi, zlo, zhi);
+                const unsigned nb = n_nibble(c, xm0, xp3, ym, yp, zm, zp, xlo, xhi, ylo, yhi, zlo,
+                                             zhi, a.lp.gamma_up);
+                if constexpr (OP == OP_CUT) {
+                    // 16 words of N bits per entry; bit 4*tid + j = point j
+                    uint32_t w = nb << (4 * (tid & 7));
+                    w |= __shfl_xor_sync(0xffffffffu, w, 1);
+                    w |= __shfl_xor_sync(0xffffffffu, w, 2);
+                    w |= __shfl_xor_sync(0xffffffffu, w, 4);
+                    if ((tid & 7) == 0) a.nmask[(size_t)k * 16 + (tid >> 3)] = w;
+                } else {
+                    const float gn = a.lp.gamma_up;
+                    if (nb & 1u) o.x = fminf(fmaxf(o.x, -gn), gn);
+                    if (nb & 2u) o.y = fminf(fmaxf(o.y, -gn), gn);
+                    if (nb & 4u) o.z = fminf(fmaxf(o.z, -gn), gn);
+                    if (nb & 8u) o.w = fminf(fmaxf(o.w, -gn), gn);
+                }
+                if (a.breaches) count_breaches(a, c, t, info, xh, ly, lz);
+            } else {
+                const unsigned nb = (nmk[cur][tid >> 3] >> (4 * (tid & 7))) & 15u;
+                constexpr bool CL = OP == OP_REINIT_CLAMP;
+                if ((info & NB_ALL) == NB_ALL)
+                    o = rei4<false, CL>(c, xm0, xp3, ym, yp, zm, zp, nb, a.lp, extrap, false, false,
+                                        false, false, false, false);
+                else
+                    o = rei4<true, CL>(c, xm0, xp3, ym, yp, zm, zp, nb, a.lp, extrap, xlo, xhi, ylo,
+                                       yhi, zlo, zhi);
+            }
         }
         *reinterpret_cast<float4*>(dst + (unsigned)t * TILE_PTS + 4 * tid) = o;
 
@@ -567,7 +731,43 @@ __device__ __forceinline__ D4 ld4(const double* p)
     return r;
 }
 
-template <bool FIELD, bool CLASSIFY>
+// ---------------------------------------------------- local scheme, FP64 --
+// The oracle's expressions in its order, round-to-nearest intrinsics.
+__device__ __forceinline__ double cut64(double a, double beta, double gamma)
+{
+    if (a <= beta) return 1.0;
+    if (a < gamma) {
+        const double u = __dsub_rn(a, gamma);
+        const double w = __dsub_rn(gamma, beta);
+        const double p = __dsub_rn(__dadd_rn(__dmul_rn(2.0, a), gamma), __dmul_rn(3.0, beta));
+        return __ddiv_rn(__dmul_rn(__dmul_rn(u, u), p), __dmul_rn(__dmul_rn(w, w), w));
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ double rei64(double d, double dmx, double dpx, double dmy, double dpy,
+                                        double dmz, double dpz, double h, double dtau)
+{
+    if (d == 0.0) return d;
+    double q;
+    if (d > 0.0)
+        q = __dadd_rn(__dadd_rn(sq_sum(max0(dmx), min0(dpx)), sq_sum(max0(dmy), min0(dpy))),
+                      sq_sum(max0(dmz), min0(dpz)));
+    else
+        q = __dadd_rn(__dadd_rn(sq_sum(max0(dpx), min0(dmx)), sq_sum(max0(dpy), min0(dmy))),
+                      sq_sum(max0(dpz), min0(dmz)));
+    const double g = __dsqrt_rn(q);
+    const double S = __ddiv_rn(d, __dsqrt_rn(__dadd_rn(__dmul_rn(d, d),
+                                                         __dmul_rn(__dmul_rn(g, g), __dmul_rn(h, h)))));
+    return __dsub_rn(d, __dmul_rn(dtau, __dmul_rn(S, __dsub_rn(g, 1.0))));
+}
+
+__device__ __forceinline__ double clamp64(double d, double gamma)
+{
+    return d < -gamma ? -gamma : (d > gamma ? gamma : d);
+}
+
+template <bool FIELD, bool CLASSIFY, int OP = OP_PLAIN>
 __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
 {
     __shared__ D4 sm[2][8][8][2];
@@ -633,6 +833,48 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
         xn[1] = c.v[0]; xn[2] = c.v[1]; xn[3] = c.v[2]; xn[4] = c.v[3];
         xn[5] = xh ? xo : part;
 
+        // Eq. 11 bits of the thread's four points (local scheme)
+        unsigned nb = 0;
+        if constexpr (OP == OP_CUT || OP == OP_CUT_CLAMP) {
+            const double g = in.gamma;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                bool inn = fabs(c.v[j]) < g;
+                inn |= (j > 0 || !xlo_face) && fabs(xn[j]) < g;
+                inn |= (j < 3 || !xhi_face) && fabs(xn[j + 2]) < g;
+                inn |= !ylo_face && fabs(ym.v[j]) < g;
+                inn |= !yhi_face && fabs(yp.v[j]) < g;
+                inn |= !zlo_face && fabs(zm.v[j]) < g;
+                inn |= !zhi_face && fabs(zp.v[j]) < g;
+                nb |= (inn ? 1u : 0u) << j;
+            }
+            if constexpr (OP == OP_CUT) {
+                uint32_t w = nb << (4 * (tid & 7));
+                w |= __shfl_xor_sync(0xffffffffu, w, 1);
+                w |= __shfl_xor_sync(0xffffffffu, w, 2);
+                w |= __shfl_xor_sync(0xffffffffu, w, 4);
+                if ((tid & 7) == 0) a.nmask[(size_t)k * 16 + (tid >> 3)] = w;
+            }
+            if (a.breaches) {
+                const unsigned tb = (fabs(c.v[0]) < g ? 1u : 0u) | (fabs(c.v[1]) < g ? 2u : 0u) |
+                                    (fabs(c.v[2]) < g ? 4u : 0u) | (fabs(c.v[3]) < g ? 8u : 0u);
+                if (tb) {
+                    const long long tpl = (long long)in.tnx * in.tny;
+                    const unsigned nt = __popc(tb);
+                    unsigned bad = 0;
+                    if (xh == 0 && (tb & 1u) && (info & NB_XM) && !(__ldg(a.act + t - 1) & 1)) bad += 1;
+                    if (xh == 1 && (tb & 8u) && (info & NB_XP) && !(__ldg(a.act + t + 1) & 1)) bad += 1;
+                    if (ly == 0 && (info & NB_YM) && !(__ldg(a.act + t - in.tnx) & 1)) bad += nt;
+                    if (ly == 7 && (info & NB_YP) && !(__ldg(a.act + t + in.tnx) & 1)) bad += nt;
+                    if (lz == 0 && (info & NB_ZM) && !(__ldg(a.act + t - tpl) & 1)) bad += nt;
+                    if (lz == 7 && (info & NB_ZP) && !(__ldg(a.act + t + tpl) & 1)) bad += nt;
+                    if (bad) atomicAdd(a.breaches, (unsigned long long)bad);
+                }
+            }
+        } else if constexpr (OP == OP_REINIT || OP == OP_REINIT_CLAMP) {
+            nb = (__ldg(a.nmask + (size_t)k * 16 + (tid >> 3)) >> (4 * (tid & 7))) & 15u;
+        }
+
         D4 o;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -649,7 +891,18 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
             if (yhi_face) dpy = extrap ? dmy : 0.0;
             if (zlo_face) dmz = extrap ? dpz : 0.0;
             if (zhi_face) dpz = extrap ? dmz : 0.0;
-            o.v[j] = upd64(cj, f.v[j], dmx, dpx, dmy, dpy, dmz, dpz, dt);
+            if constexpr (OP == OP_PLAIN) {
+                o.v[j] = upd64(cj, f.v[j], dmx, dpx, dmy, dpy, dmz, dpz, dt);
+            } else if constexpr (OP == OP_CUT || OP == OP_CUT_CLAMP) {
+                const double fe = __dmul_rn(f.v[j], cut64(fabs(cj), a.lp.beta, in.gamma));
+                double r = upd64(cj, fe, dmx, dpx, dmy, dpy, dmz, dpz, dt);
+                if (OP == OP_CUT_CLAMP && ((nb >> j) & 1u)) r = clamp64(r, in.gamma);
+                o.v[j] = r;
+            } else {
+                double r = rei64(cj, dmx, dpx, dmy, dpy, dmz, dpz, h, a.lp.dtau);
+                if (OP == OP_REINIT_CLAMP) r = clamp64(r, in.gamma);
+                o.v[j] = ((nb >> j) & 1u) ? r : cj;
+            }
         }
         double* dp = dst + (size_t)t * TILE_PTS + off;
         *reinterpret_cast<double2*>(dp) = make_double2(o.v[0], o.v[1]);
@@ -710,6 +963,78 @@ cudaError_t launch32_s(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
     }
 }
 
+// local-scheme passes: 4 points per thread, 3-stage ring
+template <bool FIELD, bool CLS, int OP>
+cudaError_t launch32_op(const StepArgs& a, int grid_pct, cudaStream_t s)
+{
+    constexpr int S = 3;
+    constexpr size_t smem = sizeof(Stage32) * S;
+    static int full = 0;
+    if (!full) full = occupancy_grid(k_step_f32<FIELD, CLS, false, S, OP>, smem, 128);
+    int grid = (int)((long long)full * grid_pct / 100);
+    if (grid < 1) grid = 1;
+    if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
+    k_step_f32<FIELD, CLS, false, S, OP><<<grid, 128, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local32(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
+{
+    const bool field = a.F != nullptr;
+    const bool cls = a.core != nullptr;
+    const int pct = cfg.grid_pct;
+    switch (a.op) {
+    case OP_CUT:
+        if (cls) return cudaErrorInvalidValue;  // the tube test follows the last pass
+        return field ? launch32_op<true, false, OP_CUT>(a, pct, s) : launch32_op<false, false, OP_CUT>(a, pct, s);
+    case OP_CUT_CLAMP:
+        if (field) return cls ? launch32_op<true, true, OP_CUT_CLAMP>(a, pct, s)
+                              : launch32_op<true, false, OP_CUT_CLAMP>(a, pct, s);
+        return cls ? launch32_op<false, true, OP_CUT_CLAMP>(a, pct, s)
+                   : launch32_op<false, false, OP_CUT_CLAMP>(a, pct, s);
+    case OP_REINIT:
+        if (cls) return cudaErrorInvalidValue;
+        return launch32_op<false, false, OP_REINIT>(a, pct, s);
+    case OP_REINIT_CLAMP:
+        return cls ? launch32_op<false, true, OP_REINIT_CLAMP>(a, pct, s)
+                   : launch32_op<false, false, OP_REINIT_CLAMP>(a, pct, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <bool FIELD, bool CLS, int OP>
+cudaError_t launch64_op(const StepArgs& a, cudaStream_t s)
+{
+    static int full = 0;
+    if (!full) full = occupancy_grid(k_step_f64<FIELD, CLS, OP>, 0);
+    int grid = full;
+    if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
+    k_step_f64<FIELD, CLS, OP><<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_local64(const StepArgs& a, cudaStream_t s)
+{
+    const bool field = a.F != nullptr;
+    const bool cls = a.core != nullptr;
+    switch (a.op) {
+    case OP_CUT:
+        if (cls) return cudaErrorInvalidValue;
+        return field ? launch64_op<true, false, OP_CUT>(a, s) : launch64_op<false, false, OP_CUT>(a, s);
+    case OP_CUT_CLAMP:
+        if (field) return cls ? launch64_op<true, true, OP_CUT_CLAMP>(a, s) : launch64_op<true, false, OP_CUT_CLAMP>(a, s);
+        return cls ? launch64_op<false, true, OP_CUT_CLAMP>(a, s) : launch64_op<false, false, OP_CUT_CLAMP>(a, s);
+    case OP_REINIT:
+        if (cls) return cudaErrorInvalidValue;
+        return launch64_op<false, false, OP_REINIT>(a, s);
+    case OP_REINIT_CLAMP:
+        return cls ? launch64_op<false, true, OP_REINIT_CLAMP>(a, s) : launch64_op<false, false, OP_REINIT_CLAMP>(a, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <bool FIELD, bool CLS>
 cudaError_t launch64(const StepArgs& a, cudaStream_t s)
 {
@@ -728,6 +1053,10 @@ cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cuda
     const bool field = a.F != nullptr;
     const bool cls = a.core != nullptr;
     const bool bat = a.list_inst != nullptr;
+    if (a.op != OP_PLAIN) {
+        if (bat || !a.nmask) return cudaErrorInvalidValue;  // single-instance contexts only
+        return prec == 0 ? launch_local32(a, cfg, s) : launch_local64(a, s);
+    }
     if (prec == 0) {
         if (bat) {
             if (field) return cls ? launch32_s<true, true, true>(a, cfg, s) : launch32_s<true, false, true>(a, cfg, s);

@@ -27,6 +27,7 @@ LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ETIMEOUT, LS_ENONFINITE, LS_ESTATE = 0
 LS_FP32, LS_FP64 = 0, 1
 LS_DT_FIXED, LS_DT_CFL = 0, 1
 LS_PLAIN, LS_LEARNED = 0, 1
+LS_SCHEME_PLAIN, LS_SCHEME_LOCAL = 0, 1
 LS_BC_EXTRAPOLATE, LS_BC_NEUMANN = 0, 1
 LS_SHAPE_SPHERES, LS_SHAPE_TORUS, LS_SHAPE_SH = 0, 1, 2
 LS_SPEED_SINUSOID, LS_SPEED_COSCOS, LS_SPEED_FOURIER = 0, 1, 2
@@ -77,6 +78,8 @@ SIGNATURES = {
     "ls_learned_num_pairs": (_i, [_vp, _c.POINTER(_ll)]),
     "ls_learned_train": (_i, [_vp, _i, _d, _d, _d, _c.c_ulonglong, _c.POINTER(_d)]),
     "ls_set_step_mode": (_i, [_vp, _i]),
+    "ls_set_scheme": (_i, [_vp, _i, _c.c_double, _i, _c.c_double]),
+    "ls_band_breaches": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
     "ls_learned_fallbacks": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
     "ls_conv3_bf16": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "ls_conv3_wgrad": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
@@ -94,7 +97,8 @@ SIGNATURES = {
 class Profile(ctypes.Structure):
     """ls_profile of include/ls.h."""
     _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("stencil_launches", ctypes.c_ulonglong),
-                ("stencil_ms", ctypes.c_double), ("stencil_timed", ctypes.c_ulonglong)]
+                ("stencil_ms", ctypes.c_double), ("stencil_timed", ctypes.c_ulonglong),
+                ("reinit_ms", ctypes.c_double), ("reinit_timed", ctypes.c_ulonglong)]
 
 
 class LSError(RuntimeError):
@@ -391,6 +395,15 @@ class LevelSet:
 
     def set_step_mode(self, mode):
         check(self.lib.ls_set_step_mode(self.ctx, int(mode)), "ls_set_step_mode")
+
+    def set_scheme(self, scheme, beta_in_h=0.0, reinit_iters=-1, dtau_in_h=0.5):
+        check(self.lib.ls_set_scheme(self.ctx, int(scheme), float(beta_in_h), int(reinit_iters),
+                                     float(dtau_in_h)), "ls_set_scheme")
+
+    def band_breaches(self):
+        n = ctypes.c_ulonglong(0)
+        check(self.lib.ls_band_breaches(self.ctx, ctypes.byref(n)), "ls_band_breaches")
+        return n.value
 
     def learned_fallbacks(self):
         n = ctypes.c_ulonglong(0)
