@@ -48,6 +48,9 @@ METRIC = "narrow-band upwind GLUPS"
 UNIT = "GLUPS"
 BYTES_PER_UPDATE = 12  # FP32: read phi (4) + read F (4) + write phi (4)
 WORKLOAD = "sphere-union 512^3 FP32, band 6h on 8^3 tiles, rebuild/5, 500 steps CFL 0.5"
+WORKLOAD_LOCAL = ("sphere-union 512^3 FP32, local scheme (cut-off advance beta 3h, gamma 6h; %d "
+                  "reinitialisation iterations dtau h/2; clamp), 8^3 tiles, rebuild/5, 500 steps CFL 0.5")
+METRIC_LOCAL = "local-scheme GLUPS (advance point updates per second, reinitialisation included)"
 
 
 def parse():
@@ -59,11 +62,15 @@ def parse():
     p.add_argument("--grid", type=int, default=512, help="grid edge (512 = the standard workload)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", choices=["sphere-union", "batch", "learned", "perturbed", "sphere64"],
+    p.add_argument("--workload", choices=["sphere-union", "batch", "learned", "perturbed", "sphere64", "local"],
                    default="sphere-union",
                    help="sphere-union: the standard 512^3 run (the default line); "
                         "batch: 256 independent grids in one batched context; "
-                        "learned: corrector training + learned-coarse vs plain at equal error")
+                        "learned: corrector training + learned-coarse vs plain at equal error; "
+                        "local: the 512^3 run with the paper's local scheme (cut-off advance, "
+                        "reinitialisation on N, clamp)")
+    p.add_argument("--reinit-iters", type=int, default=-1,
+                   help="local workload: reinitialisation iterations per step (-1: ceil(halfwidth/dtau))")
     p.add_argument("--pairs", type=int, default=2000)
     p.add_argument("--train-iters", type=int, default=2000)
     p.add_argument("--step-config", default=None, metavar="STAGES,GRID_PCT,PPT",
@@ -212,6 +219,30 @@ def cpu_baseline(phi0_f32, F_f32, w, steps=10):
             "sample": "first %d level-set steps (%d band rebuilds) of the %d^3 workload, FP64 C oracle "
                       "with OpenMP on %d host threads, %.1f s" % (steps, (steps + w.rebuild_every - 1)
                                                                     // w.rebuild_every, w.n, cores, t)}
+
+
+def cpu_baseline_local(phi0_f32, F_f32, w, beta_h, iters, dtau_h, steps=2):
+    """The FP64 CPU oracle's local scheme, as it stands (pointwise over the
+    whole grid), on the first `steps` steps of the local workload; counted
+    like the library: points of the oracle's own active tiles per step."""
+    import numpy as np
+    import oracle
+    o = oracle.Oracle(phi0_f32.shape, w.h)
+    o.set_phi(phi0_f32.astype(np.float64))
+    o.set_speed(F_f32.astype(np.float64))
+    o.set_scheme(oracle.SCHEME_LOCAL, beta_h, iters, dtau_h)
+    t0 = time.perf_counter()
+    o.band_rebuild(w.halfwidth)
+    updates = 0
+    for _ in range(steps):
+        o.step(1, w.cfl, oracle.DT_CFL, w.rebuild_every)
+        updates += int(o.active.sum()) * 512
+    t = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return {"value": updates / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d local-scheme steps (advance + %d reinitialisation iterations + clamp, "
+                      "pointwise over the whole grid) of the %d^3 workload, FP64 C oracle with OpenMP "
+                      "on %d host threads, %.1f s" % (steps, iters, w.n, cores, t)}
 
 
 def run_reference(args):
@@ -572,6 +603,12 @@ def main():
     stream = torch.cuda.current_stream()
     w = inputs.SphereUnion(n=args.grid)
     g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32, stream=stream.cuda_stream)
+    local_scheme = args.workload == "local"
+    if local_scheme:
+        # beta = gamma/2, dtau = h/2; iterations default to ceil(halfwidth / dtau)
+        beta_h, dtau_h = w.halfwidth / 2, 0.5
+        iters = args.reinit_iters if args.reinit_iters >= 0 else int(np.ceil(w.halfwidth / dtau_h))
+        g.set_scheme(ls.LS_SCHEME_LOCAL, beta_h, iters, dtau_h)
     # Step 0 on the device: the library's own SDF / speed generators (FP64
     # evaluation, stored FP32); phi^0 kept as a device snapshot for the runs
     g.init_speed(ls.LS_SPEED_SINUSOID)
@@ -608,6 +645,7 @@ def main():
 
     u0 = g.updates()
     g.reset_profile()
+    r0 = g.profile()["reinit_updates"]
     g.profile_enable(True)
     if pg:
         pg.barrier()
@@ -632,17 +670,43 @@ def main():
 
     # dominant kernel: the upwind step, timed by events around every launch
     peak, peak_kind = measured_peaks()
-    stencil_s = prof["stencil_ms"] / 1e3
-    n_launch = max(prof["stencil_timed"], 1)
-    achieved = (updates * BYTES_PER_UPDATE / 1e9) / stencil_s if stencil_s > 0 else None
-    tpu = recorded_traffic()
-    traffic = tpu * updates / n_launch if tpu is not None else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "peak_kind": peak_kind, "kernel": "k_step_f32 (upwind step over the active 8^3 tiles)",
-                "bytes_per_update": BYTES_PER_UPDATE,
-                "avg_launch_us": 1e6 * stencil_s / n_launch, "launches": prof["stencil_timed"],
-                "share_of_step_time": stencil_s / t_s if t_s > 0 else None}
+    roofline_advance = None
+    if not local_scheme:
+        stencil_s = prof["stencil_ms"] / 1e3
+        n_launch = max(prof["stencil_timed"], 1)
+        achieved = (updates * BYTES_PER_UPDATE / 1e9) / stencil_s if stencil_s > 0 else None
+        tpu = recorded_traffic()
+        traffic = tpu * updates / n_launch if tpu is not None else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                    "peak_kind": peak_kind, "kernel": "k_step_f32 (upwind step over the active 8^3 tiles)",
+                    "bytes_per_update": BYTES_PER_UPDATE,
+                    "avg_launch_us": 1e6 * stencil_s / n_launch, "launches": prof["stencil_timed"],
+                    "share_of_step_time": stencil_s / t_s if t_s > 0 else None}
+    else:
+        # the advance covers the active tiles: read phi and F, write phi and the
+        # N mask (64 B per tile); the reinitialisation passes (K per step)
+        # cover the tiles holding N points: read d + write d + the mask
+        rein_s = prof["reinit_ms"] / 1e3
+        adv_s = (prof["stencil_ms"] - prof["reinit_ms"]) / 1e3
+        n_rein = max(prof["reinit_timed"], 1)
+        n_adv = max(prof["stencil_timed"] - prof["reinit_timed"], 1)
+        b_rein, b_adv = 8 + 64 / 512, 12 + 64 / 512
+        rupd = prof["reinit_updates"] - r0   # point-iterations over the tiles holding N points
+        a_rein = (rupd * b_rein / 1e9) / rein_s if rein_s > 0 else None
+        a_adv = (updates * b_adv / 1e9) / adv_s if adv_s > 0 else None
+        roofline = {"bound": "hbm", "achieved": a_rein, "peak": peak, "unit": "GB/s",
+                    "frac": (a_rein / peak) if a_rein else None, "traffic": None,
+                    "peak_kind": peak_kind,
+                    "kernel": "k_step_f32<..., OP_REINIT> (Eq. 12 iteration on N over the active tiles)",
+                    "bytes_per_update": b_rein, "avg_launch_us": 1e6 * rein_s / n_rein,
+                    "launches": prof["reinit_timed"], "point_iterations": rupd,
+                    "share_of_step_time": rein_s / t_s if t_s > 0 else None}
+        roofline_advance = {"bound": "hbm", "achieved": a_adv, "peak": peak, "unit": "GB/s",
+                            "frac": (a_adv / peak) if a_adv else None,
+                            "kernel": "k_step_f32<..., OP_CUT> (Eq. 8 advance + N mask)",
+                            "bytes_per_update": b_adv, "avg_launch_us": 1e6 * adv_s / n_adv,
+                            "launches": n_adv, "share_of_step_time": adv_s / t_s if t_s > 0 else None}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -670,23 +734,37 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(phi0.cpu().numpy(), F_h.numpy() if args.e2e_steps > 0 else
-                           w.speed(out_dtype=torch.float32).numpy(), w)
+        F_np = F_h.numpy() if args.e2e_steps > 0 else w.speed(out_dtype=torch.float32).numpy()
+        if local_scheme:
+            cpu = cpu_baseline_local(phi0.cpu().numpy(), F_np, w, beta_h, iters, dtau_h)
+        else:
+            cpu = cpu_baseline(phi0.cpu().numpy(), F_np, w)
+
+    # band points (|phi| < gamma) of the final state of the last run
+    fin = torch.empty((w.n,) * 3, dtype=torch.float32, device=dev)
+    g.get_phi(fin)
+    band_points = int((fin.abs().double() < w.halfwidth * w.h).sum().item())
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "grid": w.n, "halfwidth_h": w.halfwidth,
+            "config": {"workload": WORKLOAD if not local_scheme else WORKLOAD_LOCAL % iters,
+                       "grid": w.n, "halfwidth_h": w.halfwidth,
                        "autotuned": {"stages": tuned[0], "grid_pct": tuned[1], "points_per_thread": tuned[2]},
                        "rebuild_every": w.rebuild_every, "level_set_steps_per_bench_step": w.steps,
                        "cfl": w.cfl, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (phi + F 1.5 GB; active set per step ~0.2 GB)"},
             "updates_per_step": updates / max(args.steps, 1),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
-            "gpu_launches": prof["kernel_launches"],
+            "gpu_launches": prof["kernel_launches"], "band_points_final": band_points,
         }
+        if local_scheme:
+            line["metric"] = METRIC_LOCAL
+            line["config"]["local_scheme"] = {"beta_h": beta_h, "reinit_iters": iters, "dtau_h": dtau_h}
+            line["roofline_advance"] = roofline_advance
+            line["band_breaches"] = g.band_breaches()
         print(json.dumps(line), flush=True)
     g.close()
     if pg:

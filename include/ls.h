@@ -170,9 +170,11 @@ int ls_step(ls_ctx *ctx, int nsteps, double dt_or_cfl, int dt_mode,
  *      and of Eq. 5 where d < 0, S = d / sqrt(d^2 + g^2 h^2) (Eq. 13),
  *      dtau = dtau_in_h * h; points outside N keep their value;
  *   4. the clamp of Eq. 10 on N: phi^{n+1} = min(max(d, -gamma), gamma).
- * The passes run on the active tiles (band, rebuilds, CFL and frozen tiles
- * as in the plain scheme); the result equals the pointwise algorithm
- * while the active tiles contain N, which ls_band_breaches checks.
+ * The advance runs on the active tiles (band, rebuilds, CFL and frozen
+ * tiles as in the plain scheme) and flags the tiles holding a point of N;
+ * the reinitialisation passes visit only those (the other tiles cannot
+ * change in the step).  The result equals the pointwise algorithm while the
+ * active tiles contain N, which ls_band_breaches checks.
  * reinit_iters = -1 selects ceil(halfwidth / dtau_in_h) iterations (enough
  * for the pseudo-time front to cross the band once; "steady state").
  * Single FP32 / FP64 contexts; not with the learned step mode.  Takes effect
@@ -228,7 +230,7 @@ int ls_set_graphs(ls_ctx *ctx, int on);
 
 /* Autotuner: time every launch configuration of the FP32 stencil (points
  * per thread 4 (128-thread CTAs) or 8 (64-thread CTAs) x cp.async ring depth
- * 2/3/4 x persistent grid 50/75/100 % of full occupancy) on the current
+ * 2/3/4/6 x persistent grid 50/75/100 % of full occupancy) on the current
  * active set, `reps` launches each, and keep the fastest for later steps.
  * Every configuration computes the same bits.  The probes write only the
  * buffer the next step overwrites, so the state is unchanged.  Outputs
@@ -236,7 +238,7 @@ int ls_set_graphs(ls_ctx *ctx, int on);
  * otherwise).  FP64 contexts have a single configuration and return it. */
 int ls_autotune(ls_ctx *ctx, int reps, int *stages, int *grid_pct, int *points_per_thread);
 
-/* Set the FP32 stencil launch configuration directly (stages 2..4, grid
+/* Set the FP32 stencil launch configuration directly (stages 2, 3, 4 or 6, grid
  * 1..100 % of full occupancy, points per thread 4 or 8; default 3, 100, 8). */
 int ls_set_step_config(ls_ctx *ctx, int stages, int grid_pct, int points_per_thread);
 
@@ -250,6 +252,10 @@ typedef struct {
     double reinit_ms;                    /* of stencil_ms: reinitialisation passes of
                                             the local scheme (Eq. 12)                */
     unsigned long long reinit_timed;     /* number of launches reinit_ms covers      */
+    unsigned long long reinit_updates;   /* point-iterations of the reinitialisation
+                                            passes since the local scheme was first
+                                            set (they visit only tiles holding a
+                                            point of N)                             */
 } ls_profile;
 
 /* Enable (1) or disable (0) CUDA-event timing of every upwind-step launch

@@ -138,7 +138,8 @@ void free_all(ls_ctx* c)
                     c->act, c->list, c->list_info, c->d_count, c->block_counts, c->d_sc,
                     c->d_Mbits, c->d_updates, c->d_status, c->d_nonfinite, c->d_inst,
                     c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params, c->nmask,
-                    c->d_breaches};
+                    c->d_breaches, c->list_nact, c->nmask2, c->nflag, c->nl, c->nl_info,
+                    c->d_ncount, c->d_rupdates};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -219,7 +220,7 @@ int finish_rebuild(ls_ctx* c, cudaStream_t s)
     } else {
         KL(c, lsk::launch_scatter(c->act, c->block_counts, c->list, c->list_info, sign_table(c),
                                   const_sign_bits(c), c->in0(), c->ntiles, tmf, c->prec,
-                                  c->d_Mbits, cur, other, s));
+                                  c->d_Mbits, cur, other, c->list_nact, s));
         KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in0(), c->dt_mode, c->dt_value, 1,
                                  c->prec, c->d_Mbits, c->d_count, 0, s));
     }
@@ -255,7 +256,7 @@ int full_domain_bound(ls_ctx* c, cudaStream_t s)
         // every tile that leaves the active set into the other buffer
         CK(cudaMemsetAsync(c->act, 1, c->ntiles, s));
         KL(c, lsk::launch_full_list(c->list, c->list_info, sign_table(c), const_sign_bits(c),
-                                    c->in0(), c->ntiles, c->d_count, s));
+                                    c->in0(), c->ntiles, c->d_count, c->list_nact, s));
         if (speed_mode(c) == 2)
             KL(c, lsk::launch_max_all(c->tile_maxF, c->ntiles, c->prec, c->d_Mbits, s));
         KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in0(), c->dt_mode, c->dt_value, 1,
@@ -308,7 +309,7 @@ lsk::LocalParams local_params(const ls_ctx* c)
     lp.beta_n = (float)lp.beta;
     lp.gamma_n = (float)lp.gamma;
     const double w = lp.gamma - lp.beta;
-    lp.inv_w3 = (float)(1.0 / (w * w * w));
+    lp.inv_w = (float)(1.0 / w);
     lp.lam = (float)c->dtau_in_h;
     lp.dtau_f = (float)lp.dtau;
     return lp;
@@ -359,11 +360,18 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
                               : (last ? lsk::OP_REINIT_CLAMP : lsk::OP_REINIT);
                 a.lp = local_params(c);
                 a.nmask = c->nmask;
-                a.act = c->act;
+                a.nact = c->list_nact;
+                a.nflag = c->nflag;
                 a.breaches = p == 0 ? c->d_breaches : nullptr;
                 if (p > 0) {
+                    // the reinitialisation passes visit only the tiles that
+                    // hold a point of N (compacted after the advance)
                     a.F = nullptr;
-                    a.updates = nullptr;  // updates count the advance (Eq. 8) only
+                    a.list = c->nl;
+                    a.info = c->nl_info;
+                    a.count = c->d_ncount;
+                    a.nmask = c->nmask2;
+                    a.updates = c->d_rupdates;
                 }
             }
             if (c->profiling && c->ev_pending.size() >= 4096) RET(drain_events(c));
@@ -381,6 +389,14 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
             }
             if (c->step_mode == LS_LEARNED) RET(ls_engine_learned_after_step(c, s));
             c->cur ^= 1;
+            if (local && p == 0 && K > 0) {
+                KL(c, lsk::launch_nflag_count(c->nflag, c->d_count, c->block_counts, c->nblocks, s));
+                KL(c, lsk::launch_scan(c->block_counts, c->nblocks, c->d_ncount, s));
+                KL(c, lsk::launch_nflag_scatter(c->nflag, c->d_count, c->block_counts, c->list,
+                                                c->list_info, c->nmask, c->nl, c->nl_info,
+                                                c->nmask2, classify ? c->core : nullptr,
+                                                c->nblocks, s));
+            }
         }
         c->since_rebuild += 1;
         c->core_fresh = classify;
@@ -814,7 +830,7 @@ int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out, int* pp
     if (!c->band_valid) return LS_ESTATE;
     cudaStream_t s = c->stream;
     if (c->prec == LS_FP32) {
-        const int stages[] = {2, 3, 4};
+        const int stages[] = {2, 3, 4, 6};
         const int pcts[] = {50, 75, 100};
         const int ppts[] = {4, 8};
         cudaEvent_t e0, e1;
@@ -857,7 +873,7 @@ int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out, int* pp
 
 int ls_set_step_config(ls_ctx* c, int stages, int grid_pct, int ppt)
 {
-    if (!c || (stages != 2 && stages != 3 && stages != 4) || grid_pct < 1 || grid_pct > 100 ||
+    if (!c || (stages != 2 && stages != 3 && stages != 4 && stages != 6) || grid_pct < 1 || grid_pct > 100 ||
         (ppt != 4 && ppt != 8))
         return LS_EINVAL;
     c->cfg.stages = stages;
@@ -1041,6 +1057,12 @@ int ls_get_profile(ls_ctx* c, ls_profile* out)
     out->stencil_timed = c->stencil_timed;
     out->reinit_ms = c->reinit_ms;
     out->reinit_timed = c->reinit_timed;
+    out->reinit_updates = 0;
+    if (c->d_rupdates) {
+        CK(cudaMemcpyAsync(&out->reinit_updates, c->d_rupdates, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     return LS_OK;
 }
 
@@ -1071,6 +1093,19 @@ int ls_set_scheme(ls_ctx* c, int scheme, double beta_in_h, int reinit_iters, dou
     if (reinit_iters < -1) return LS_EINVAL;
     if (c->step_mode != LS_PLAIN) return LS_ESTATE;
     if (!c->nmask) CK(dalloc(&c->nmask, (size_t)c->ntiles * 16 * sizeof(uint32_t)));
+    if (!c->nmask2) CK(dalloc(&c->nmask2, (size_t)c->ntiles * 16 * sizeof(uint32_t)));
+    if (!c->nflag) CK(dalloc(&c->nflag, (size_t)c->ntiles));
+    if (!c->nl) CK(dalloc(&c->nl, (size_t)c->ntiles * sizeof(int)));
+    if (!c->nl_info) CK(dalloc(&c->nl_info, (size_t)c->ntiles));
+    if (!c->d_ncount) CK(dalloc(&c->d_ncount, sizeof(int)));
+    if (!c->d_rupdates) {
+        CK(dalloc(&c->d_rupdates, sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(c->d_rupdates, 0, sizeof(unsigned long long), c->stream));
+    }
+    if (!c->list_nact) {
+        CK(dalloc(&c->list_nact, (size_t)c->ntiles));
+        state_changed(c);  // the next rebuild writes the neighbour bits
+    }
     if (!c->d_breaches) CK(dalloc(&c->d_breaches, sizeof(unsigned long long)));
     CK(cudaMemsetAsync(c->d_breaches, 0, sizeof(unsigned long long), c->stream));
     c->scheme = LS_SCHEME_LOCAL;

@@ -170,6 +170,22 @@ __device__ __forceinline__ unsigned nb_bits(long long t, const Inst& in)
     return b;
 }
 
+// the face neighbours of tile t (single instance) inside the domain whose
+// active flag (bit 0 of act) is set
+__device__ __forceinline__ unsigned active_nb_bits(long long t, unsigned nb, const Inst& in,
+                                                   const uint8_t* __restrict__ act)
+{
+    const long long tpl = (long long)in.tnx * in.tny;
+    unsigned b = 0;
+    if ((nb & NB_XM) && (act[t - 1] & 1)) b |= NB_XM;
+    if ((nb & NB_XP) && (act[t + 1] & 1)) b |= NB_XP;
+    if ((nb & NB_YM) && (act[t - in.tnx] & 1)) b |= NB_YM;
+    if ((nb & NB_YP) && (act[t + in.tnx] & 1)) b |= NB_YP;
+    if ((nb & NB_ZM) && (act[t - tpl] & 1)) b |= NB_ZM;
+    if ((nb & NB_ZP) && (act[t + tpl] & 1)) b |= NB_ZP;
+    return b;
+}
+
 
 // Eq. 6 per tile: core = (min |phi| over the tile) < gamma, compared in FP64
 template <typename T>
@@ -227,6 +243,52 @@ __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core
     }
     const int cnt = __syncthreads_count(on);
     if (threadIdx.x == 0) block_counts[blockIdx.x] = cnt;
+}
+
+// Reinitialisation list of the local scheme: the entries of the active list
+// whose tile holds a point of N (nflag, written by the advance pass).  Tiles
+// without N points do not change during the step's reinitialisation
+// passes, and both ping-pong buffers already hold their values after the
+// advance, so those passes skip them.
+__global__ void __launch_bounds__(256) k_nflag_count(const uint8_t* __restrict__ nflag,
+                                                     const int* __restrict__ count,
+                                                     int* block_counts)
+{
+    const int n = *count;
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const int on = (k < n) ? (nflag[k] != 0) : 0;
+    const int cnt = __syncthreads_count(on);
+    if (threadIdx.x == 0) block_counts[blockIdx.x] = cnt;
+}
+
+// ascending compaction of the flagged entries: tile id, info byte and the 64
+// bytes of N bits; unflagged entries hold no point of T, so when the tube
+// test is due their core flag is 0
+__global__ void __launch_bounds__(256) k_nflag_scatter(
+    const uint8_t* __restrict__ nflag, const int* __restrict__ count,
+    const int* __restrict__ offsets, const int* __restrict__ list,
+    const uint8_t* __restrict__ list_info, const uint4* __restrict__ nmask, int* nl,
+    uint8_t* nl_info, uint4* nl_mask, uint8_t* core)
+{
+    __shared__ int warp_cnt[8];
+    const int n = *count;
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const int on = (k < n) ? (nflag[k] != 0) : 0;
+    const unsigned b = __ballot_sync(0xffffffffu, on);
+    const int w = threadIdx.x >> 5;
+    if (lane_id() == 0) warp_cnt[w] = __popc(b);
+    __syncthreads();
+    int before = 0;
+    for (int i = 0; i < w; ++i) before += warp_cnt[i];
+    if (on) {
+        const int pos = offsets[blockIdx.x] + before + __popc(b & ((1u << lane_id()) - 1u));
+        nl[pos] = list[k];
+        nl_info[pos] = list_info[k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) nl_mask[(size_t)pos * 4 + q] = nmask[(size_t)k * 4 + q];
+    } else if (k < n && core) {
+        core[list[k]] = 0;
+    }
 }
 
 // exclusive scan of up to 1024*32 block counts by one 1024-thread block
@@ -288,7 +350,8 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
                                                  unsigned const_sgn, Inst single,
                                                  long long ntiles, const T* __restrict__ tile_maxF,
                                                  unsigned long long* Mbits,
-                                                 const uint4* __restrict__ cur, uint4* other)
+                                                 const uint4* __restrict__ cur, uint4* other,
+                                                 uint8_t* list_nact)
 {
     __shared__ int warp_cnt[8];
     __shared__ int warp_leave[8];
@@ -326,7 +389,9 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
     if (on) {
         const int pos = offsets[blockIdx.x] + before + __popc(b & below);
         list[pos] = (int)t;
-        list_info[pos] = (uint8_t)(nb_bits(t, single) | (tile_sgn ? tile_sgn[t] : const_sgn));
+        const unsigned nb = nb_bits(t, single);
+        list_info[pos] = (uint8_t)(nb | (tile_sgn ? tile_sgn[t] : const_sgn));
+        if (list_nact) list_nact[pos] = (uint8_t)active_nb_bits(t, nb, single, act);
     }
     if (leaving) leave_ids[lbefore + __popc(bl & below)] = (int)t;
     if (threadIdx.x == 0 && tile_maxF) {
@@ -443,12 +508,15 @@ __global__ void k_set_dt_batch(StepScalars* sc, int n_inst, const Inst* __restri
 __global__ void __launch_bounds__(256) k_full_list(int* list, uint8_t* list_info,
                                                    const uint8_t* __restrict__ tile_sgn,
                                                    unsigned const_sgn, Inst single,
-                                                   long long ntiles, int* count)
+                                                   long long ntiles, int* count,
+                                                   uint8_t* list_nact)
 {
     for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < ntiles;
          t += (long long)gridDim.x * 256) {
         list[t] = (int)t;
-        list_info[t] = (uint8_t)(nb_bits(t, single) | (tile_sgn ? tile_sgn[t] : const_sgn));
+        const unsigned nb = nb_bits(t, single);
+        list_info[t] = (uint8_t)(nb | (tile_sgn ? tile_sgn[t] : const_sgn));
+        if (list_nact) list_nact[t] = (uint8_t)nb;  // every tile is active
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) *count = (int)ntiles;
 }
@@ -582,6 +650,23 @@ cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
     return cudaGetLastError();
 }
 
+cudaError_t launch_nflag_count(const uint8_t* nflag, const int* count, int* block_counts,
+                               int nblocks, cudaStream_t s)
+{
+    k_nflag_count<<<nblocks, 256, 0, s>>>(nflag, count, block_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nflag_scatter(const uint8_t* nflag, const int* count, const int* block_offsets,
+                                 const int* list, const uint8_t* list_info, const uint32_t* nmask,
+                                 int* nl, uint8_t* nl_info, uint32_t* nl_mask, uint8_t* core,
+                                 int nblocks, cudaStream_t s)
+{
+    k_nflag_scatter<<<nblocks, 256, 0, s>>>(nflag, count, block_offsets, list, list_info,
+                                            (const uint4*)nmask, nl, nl_info, (uint4*)nl_mask, core);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scan(int* block_counts, int nblocks, int* count, cudaStream_t s)
 {
     k_scan<<<1, 1024, 0, s>>>(block_counts, nblocks, count);
@@ -592,17 +677,17 @@ cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* li
                            uint8_t* list_info, const uint8_t* tile_sgn, unsigned const_sgn,
                            const Inst& single, long long ntiles, const void* tile_maxF, int prec,
                            unsigned long long* Mbits, const void* cur, void* other,
-                           cudaStream_t s)
+                           uint8_t* list_nact, cudaStream_t s)
 {
     const int nb = (int)((ntiles + 255) / 256);
     if (prec == 0)
         k_scatter<float><<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, tile_sgn,
                                             const_sgn, single, ntiles, (const float*)tile_maxF,
-                                            Mbits, (const uint4*)cur, (uint4*)other);
+                                            Mbits, (const uint4*)cur, (uint4*)other, list_nact);
     else
         k_scatter<double><<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, tile_sgn,
                                              const_sgn, single, ntiles, (const double*)tile_maxF,
-                                             Mbits, (const uint4*)cur, (uint4*)other);
+                                             Mbits, (const uint4*)cur, (uint4*)other, list_nact);
     return cudaGetLastError();
 }
 
@@ -633,12 +718,12 @@ cudaError_t launch_set_dt_batch(StepScalars* sc, int n_inst, const Inst* d_inst,
 
 cudaError_t launch_full_list(int* list, uint8_t* list_info, const uint8_t* tile_sgn,
                              unsigned const_sgn, const Inst& single, long long ntiles, int* count,
-                             cudaStream_t s)
+                             uint8_t* list_nact, cudaStream_t s)
 {
     long long g = (ntiles + 255) / 256;
     if (g > 148 * 16) g = 148 * 16;
     k_full_list<<<(int)(g > 0 ? g : 1), 256, 0, s>>>(list, list_info, tile_sgn, const_sgn, single,
-                                                     ntiles, count);
+                                                     ntiles, count, list_nact);
     return cudaGetLastError();
 }
 

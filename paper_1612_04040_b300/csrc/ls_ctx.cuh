@@ -106,6 +106,13 @@ struct ls_ctx {
     double dtau_in_h = 0.5;
     int reinit_iters = -1;
     uint32_t* nmask = nullptr;                 // N bits, 16 words per list entry
+    uint8_t* list_nact = nullptr;              // active face neighbours per list entry
+    uint8_t* nflag = nullptr;                  // per list entry: the tile holds a point of N
+    int* nl = nullptr;                         // tiles holding N points (ascending) ...
+    uint8_t* nl_info = nullptr;                // ... their info bytes ...
+    uint32_t* nmask2 = nullptr;                // ... and N bits
+    int* d_ncount = nullptr;                   // their number
+    unsigned long long* d_rupdates = nullptr;  // reinitialisation point-iterations
     unsigned long long* d_breaches = nullptr;
 
     // learned corrector

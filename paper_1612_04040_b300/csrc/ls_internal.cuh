@@ -82,19 +82,31 @@ cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
                           long long ntiles, cudaStream_t s);
 // exclusive scan of block counts, writes total to *count
 cudaError_t launch_scan(int* block_counts, int nblocks, int* count, cudaStream_t s);
+// local scheme: the active-list entries whose tile holds a point of N
+// (nflag), compacted in ascending order with their info bytes and N bits
+// (block counts -> launch_scan -> scatter); core[t] = 0 for the others when
+// core is not NULL
+cudaError_t launch_nflag_count(const uint8_t* nflag, const int* count, int* block_counts,
+                               int nblocks, cudaStream_t s);
+cudaError_t launch_nflag_scatter(const uint8_t* nflag, const int* count, const int* block_offsets,
+                                 const int* list, const uint8_t* list_info, const uint32_t* nmask,
+                                 int* nl, uint8_t* nl_info, uint32_t* nl_mask, uint8_t* core,
+                                 int nblocks, cudaStream_t s);
 // scatter active ids (ascending) with their info bytes, fold max |F| of the
 // active tiles into *Mbits (ordered bits of a non-negative float / double),
 // and copy the tiles leaving the active set from cur into other.
 // tile_sgn == NULL: constant speed, sign bits const_sgn.
+// list_nact (may be NULL): per entry, the face neighbours inside the domain
+// that are active (NB_* bits)
 cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* list,
                            uint8_t* list_info, const uint8_t* tile_sgn, unsigned const_sgn,
                            const Inst& single, long long ntiles, const void* tile_maxF, int prec,
                            unsigned long long* Mbits, const void* cur, void* other,
-                           cudaStream_t s);
+                           uint8_t* list_nact, cudaStream_t s);
 // full-domain list: every tile, ascending, with info bytes; *count = ntiles
 cudaError_t launch_full_list(int* list, uint8_t* list_info, const uint8_t* tile_sgn,
                              unsigned const_sgn, const Inst& single, long long ntiles, int* count,
-                             cudaStream_t s);
+                             uint8_t* list_nact, cudaStream_t s);
 // max of tile max|F| over all tiles (full-domain mode)
 cudaError_t launch_max_all(const void* tile_maxF, long long ntiles, int prec,
                            unsigned long long* Mbits, cudaStream_t s);
@@ -123,7 +135,7 @@ struct LocalParams {
     float gamma_up;       // smallest float >= gamma: FP32 |phi| < gamma decided as in FP64,
                           // and the clamp bound (a clamped value is not in T)
     float beta_n, gamma_n;  // nearest floats (the cubic of Eq. 7)
-    float inv_w3;         // 1 / (gamma - beta)^3
+    float inv_w;          // 1 / (gamma - beta)
     float lam;            // dtau / h
     float dtau_f;         // dtau
     int pad;
@@ -147,7 +159,9 @@ struct StepArgs {
     int op;                   // OP_*
     LocalParams lp;
     uint32_t* nmask;          // N of Eq. 11: 16 words (512 bits) per list entry
-    const uint8_t* act;       // per-tile flags, bit 0 = active (breach test)
+    uint8_t* nflag;           // advance: per entry, 1 when the tile holds a point of N
+    const uint8_t* nact;      // per entry: face neighbours inside the domain that are
+                              // active (NB_* bits; breach test)
     unsigned long long* breaches;  // N points found in inactive tiles
 };
 

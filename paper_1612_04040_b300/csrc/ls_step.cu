@@ -37,23 +37,6 @@ namespace {
 // ring of S shared-memory stages, so the latency of the next tiles' loads
 // overlaps the arithmetic of the current one.
 
-// cp.async of 16 / 4 bytes into shared memory, predicated (no branch)
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred = true)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile(
-        "{ .reg .pred p; setp.ne.b32 p, %2, 0;\n"
-        "  @p cp.async.cg.shared.global [%0], [%1], 16; }\n" ::"r"(s), "l"(gmem), "r"((int)pred)
-        : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred = true)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile(
-        "{ .reg .pred p; setp.ne.b32 p, %2, 0;\n"
-        "  @p cp.async.ca.shared.global [%0], [%1], 4; }\n" ::"r"(s), "l"(gmem), "r"((int)pred)
-        : "memory");
-}
 // same, with a precomputed shared-memory address; when pred is false the
 // instruction is not executed, so the global address is never dereferenced
 __device__ __forceinline__ void cp_async16s(unsigned s, const void* gmem, bool pred = true)
@@ -83,13 +66,16 @@ __device__ __forceinline__ float rsqrt_hw(float x)
     return r;
 }
 
-struct Stage32 {
+// one ring stage; without a speed field the stage has no speed block, so a
+// deeper ring fits in the same shared memory
+template <bool FIELD>
+struct Stage32T {
     float4 v[192];   // [0,128): centre values (element offset 4*tid of the tile);
                      // [128,160): y-halo runs [16*(ly==7) + 2*lz + xh];
                      // [160,192): z-halo runs [16*(lz==7) + 2*ly + xh]
-    float4 f[128];   // speeds (field speed only)
+    float4 f[FIELD ? 128 : 1];  // speeds (field speed only)
     float xo[128];   // x-halo value of each thread
-    int4 meta;       // tile id, info byte
+    int4 meta;       // tile id, info byte, instance, face neighbours not active
 };
 
 // Eq. 3-5 at one point, FP32.  Differences are unscaled (1/h is folded into
@@ -160,49 +146,63 @@ __device__ __forceinline__ float4 upd4(const float4& c, const float4& f, float x
 }
 
 // ------------------------------------------------- local scheme, FP32 ----
-// Eq. 7 at a = |phi|.  The branch tests use thresholds rounded outward on the
-// host (largest float <= beta, smallest float >= gamma), so they decide
-// exactly as the FP64 comparisons with beta and gamma do.
+// Eq. 7 at a = |phi|, branch-free: with s = (a - beta)/(gamma - beta) the
+// cubic is 1 - 3 s^2 + 2 s^3 (the paper's (a-gamma)^2 (2a + gamma - 3 beta)
+// / (gamma - beta)^3 expanded), s clamped to [0, 1].  The two end tests use
+// thresholds rounded outward on the host (largest float <= beta, smallest
+// float >= gamma), so they decide exactly as the FP64 comparisons do.
 __device__ __forceinline__ float cut32(float a, const LocalParams& lp)
 {
-    if (a <= lp.beta_dn) return 1.f;
-    if (a < lp.gamma_up) {
-        const float u = a - lp.gamma_n;
-        return u * u * (2.f * a + lp.gamma_n - 3.f * lp.beta_n) * lp.inv_w3;
-    }
-    return 0.f;
+    const float s = __saturatef((a - lp.beta_n) * lp.inv_w);
+    float c = fmaf(s * s, fmaf(2.f, s, -3.f), 1.f);
+    c = a < lp.gamma_up ? c : 0.f;
+    return a <= lp.beta_dn ? 1.f : c;
 }
 
 // Eq. 11 for the thread's four points: bit j set when point j or one of its
-// face neighbours inside the domain is in T (|phi| < gamma, FP64-exact test).
+// face neighbours inside the domain is in T (|phi| < gamma, FP64-exact
+// test), i.e. when the minimum of those |phi| is below gamma.  FACES: mask
+// the neighbours beyond the domain faces.
+template <bool FACES>
 __device__ __forceinline__ unsigned n_nibble(const float4& c, float xm0, float xp3, const float4& ym,
                                              const float4& yp, const float4& zm, const float4& zp,
                                              bool xlo, bool xhi, bool ylo, bool yhi, bool zlo,
                                              bool zhi, float g)
 {
-    const float xs[6] = {xm0, c.x, c.y, c.z, c.w, xp3};
+    const float inf = __int_as_float(0x7f800000);
+    float a0 = fabsf(xm0), a5 = fabsf(xp3);
+    float4 Ym = ym, Yp = yp, Zm = zm, Zp = zp;
+    if (FACES) {
+        a0 = xlo ? inf : a0;
+        a5 = xhi ? inf : a5;
+        if (ylo) Ym = make_float4(inf, inf, inf, inf);
+        if (yhi) Yp = make_float4(inf, inf, inf, inf);
+        if (zlo) Zm = make_float4(inf, inf, inf, inf);
+        if (zhi) Zp = make_float4(inf, inf, inf, inf);
+    }
+    const float a1 = fabsf(c.x), a2 = fabsf(c.y), a3 = fabsf(c.z), a4 = fabsf(c.w);
+    const float p0 = fminf(a0, a1), p1 = fminf(a1, a2), p2 = fminf(a2, a3), p3 = fminf(a3, a4),
+                p4 = fminf(a4, a5);
+    const float px[4] = {fminf(p0, p1), fminf(p1, p2), fminf(p2, p3), fminf(p3, p4)};
     unsigned nb = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        bool in = fabsf(xs[j + 1]) < g;
-        in |= (j > 0 || !xlo) && fabsf(xs[j]) < g;
-        in |= (j < 3 || !xhi) && fabsf(xs[j + 2]) < g;
-        in |= !ylo && fabsf(comp(ym, j)) < g;
-        in |= !yhi && fabsf(comp(yp, j)) < g;
-        in |= !zlo && fabsf(comp(zm, j)) < g;
-        in |= !zhi && fabsf(comp(zp, j)) < g;
-        nb |= (in ? 1u : 0u) << j;
+        const float yz = fminf(fminf(fabsf(comp(Ym, j)), fabsf(comp(Yp, j))),
+                               fminf(fabsf(comp(Zm, j)), fabsf(comp(Zp, j))));
+        nb |= (fminf(px[j], yz) < g ? 1u : 0u) << j;
     }
     return nb;
 }
 
 // One pseudo-time iteration of Eq. 12 at the thread's four points (those
 // with their N bit set; the others keep their value): the upwind gradient of
-// Eq. 4 where d > 0 and of Eq. 5 where d < 0 (through G-(d) = G+(-d)),
-// S = d / sqrt(d^2 + |Dd|^2 h^2) (Eq. 13) with unscaled differences, then
+// Eq. 4 where d > 0 and of Eq. 5 where d < 0, S = d / sqrt(d^2 + |Dd|^2 h^2)
+// (Eq. 13) with unscaled differences (|Dd| h = sqrt(q)), then
 // d - dtau S (|grad d| - 1); CLAMP: Eq. 10 afterwards, to +-(smallest float
 // >= gamma), so that a clamped value stays outside T as in FP64.
-template <bool FACES, bool CLAMP>
+// SGN = +1 / -1: every N point of the warp has d >= 0 / d <= 0 (d = 0 gives
+// S = 0 on either path); SGN = 0: per point, through G-(d) = G+(-d).
+template <int SGN, bool FACES, bool CLAMP>
 __device__ __forceinline__ float4 rei4(const float4& c, float xm0, float xp3, const float4& ym,
                                        const float4& yp, const float4& zm, const float4& zp,
                                        unsigned nb, const LocalParams& lp, bool extrap, bool xlo,
@@ -224,10 +224,21 @@ __device__ __forceinline__ float4 rei4(const float4& c, float xm0, float xp3, co
             if (zlo) dmz = extrap ? dpz : 0.f;
             if (zhi) dpz = extrap ? dmz : 0.f;
         }
-        const float s = d > 0.f ? 1.f : -1.f;
-        const float ax = fmaxf(s * dmx, 0.f), bx = fminf(s * dpx, 0.f);
-        const float ay = fmaxf(s * dmy, 0.f), by = fminf(s * dpy, 0.f);
-        const float az = fmaxf(s * dmz, 0.f), bz = fminf(s * dpz, 0.f);
+        float ax, bx, ay, by, az, bz;
+        if (SGN > 0) {
+            ax = fmaxf(dmx, 0.f); bx = fminf(dpx, 0.f);
+            ay = fmaxf(dmy, 0.f); by = fminf(dpy, 0.f);
+            az = fmaxf(dmz, 0.f); bz = fminf(dpz, 0.f);
+        } else if (SGN < 0) {
+            ax = fminf(dmx, 0.f); bx = fmaxf(dpx, 0.f);
+            ay = fminf(dmy, 0.f); by = fmaxf(dpy, 0.f);
+            az = fminf(dmz, 0.f); bz = fmaxf(dpz, 0.f);
+        } else {
+            const float s = d > 0.f ? 1.f : -1.f;
+            ax = fmaxf(s * dmx, 0.f); bx = fminf(s * dpx, 0.f);
+            ay = fmaxf(s * dmy, 0.f); by = fminf(s * dpy, 0.f);
+            az = fmaxf(s * dmz, 0.f); bz = fminf(s * dpz, 0.f);
+        }
         float q = ax * ax;
         q = fmaf(bx, bx, q);
         q = fmaf(ay, ay, q);
@@ -235,7 +246,7 @@ __device__ __forceinline__ float4 rei4(const float4& c, float xm0, float xp3, co
         q = fmaf(az, az, q);
         q = fmaf(bz, bz, q);
         const float gu = q * rsqrt_hw(fmaxf(q, 1e-30f));
-        const float S = d * rsqrt_hw(fmaxf(fmaf(d, d, gu * gu), 1e-30f));
+        const float S = d * rsqrt_hw(fmaxf(fmaf(d, d, q), 1e-30f));
         float v = fmaf(-S, fmaf(lp.lam, gu, -lp.dtau_f), d);
         if (CLAMP) v = fminf(fmaxf(v, -lp.gamma_up), lp.gamma_up);
         r[j] = ((nb >> j) & 1u) ? v : d;
@@ -243,27 +254,49 @@ __device__ __forceinline__ float4 rei4(const float4& c, float xm0, float xp3, co
     return make_float4(r[0], r[1], r[2], r[3]);
 }
 
+// the reinitialisation pass for one tile: warps without N points copy, warps
+// whose N points share one sign take the sign-specialised path
+template <bool FACES, bool CLAMP>
+__device__ __forceinline__ float4 rei_tile(const float4& c, float xm0, float xp3, const float4& ym,
+                                           const float4& yp, const float4& zm, const float4& zp,
+                                           unsigned nb, const LocalParams& lp, bool extrap,
+                                           bool xlo, bool xhi, bool ylo, bool yhi, bool zlo,
+                                           bool zhi)
+{
+    if (!__any_sync(0xffffffffu, nb != 0u)) return c;
+    const unsigned neg = (c.x < 0.f ? 1u : 0u) | (c.y < 0.f ? 2u : 0u) | (c.z < 0.f ? 4u : 0u) |
+                         (c.w < 0.f ? 8u : 0u);
+    const unsigned pos = (c.x > 0.f ? 1u : 0u) | (c.y > 0.f ? 2u : 0u) | (c.z > 0.f ? 4u : 0u) |
+                         (c.w > 0.f ? 8u : 0u);
+    if (__all_sync(0xffffffffu, (nb & neg) == 0u))
+        return rei4<1, FACES, CLAMP>(c, xm0, xp3, ym, yp, zm, zp, nb, lp, extrap, xlo, xhi, ylo,
+                                     yhi, zlo, zhi);
+    if (__all_sync(0xffffffffu, (nb & pos) == 0u))
+        return rei4<-1, FACES, CLAMP>(c, xm0, xp3, ym, yp, zm, zp, nb, lp, extrap, xlo, xhi, ylo,
+                                      yhi, zlo, zhi);
+    return rei4<0, FACES, CLAMP>(c, xm0, xp3, ym, yp, zm, zp, nb, lp, extrap, xlo, xhi, ylo, yhi,
+                                 zlo, zhi);
+}
+
 // N points that fall in inactive tiles: points of T on a face of this tile
-// whose face neighbour tile is inside the domain but not active, counted once
-// per (point, face).  Zero while the active tiles cover N (the tiled step
-// then equals the pointwise one).
-__device__ __forceinline__ void count_breaches(const StepArgs& a, const float4& c, int t,
-                                               unsigned info, int xh, int ly, int lz)
+// whose face neighbour tile (bits `inact`: inside the domain, not active)
+// takes no part in the step, counted once per (point, face).  Zero while
+// the active tiles cover N (the tiled step then equals the pointwise one).
+__device__ __forceinline__ void count_breaches(const StepArgs& a, const float4& c, unsigned inact,
+                                               int xh, int ly, int lz)
 {
     const float g = a.lp.gamma_up;
     const unsigned tb = (fabsf(c.x) < g ? 1u : 0u) | (fabsf(c.y) < g ? 2u : 0u) |
                         (fabsf(c.z) < g ? 4u : 0u) | (fabsf(c.w) < g ? 8u : 0u);
-    if (!tb) return;
-    const int tnx = a.in.tnx, tpl = a.in.tnx * a.in.tny;
     const unsigned nt = __popc(tb);
     unsigned bad = 0;
-    if (xh == 0 && (tb & 1u) && (info & NB_XM) && !(__ldg(a.act + t - 1) & 1)) bad += 1;
-    if (xh == 1 && (tb & 8u) && (info & NB_XP) && !(__ldg(a.act + t + 1) & 1)) bad += 1;
-    if (ly == 0 && (info & NB_YM) && !(__ldg(a.act + t - tnx) & 1)) bad += nt;
-    if (ly == 7 && (info & NB_YP) && !(__ldg(a.act + t + tnx) & 1)) bad += nt;
-    if (lz == 0 && (info & NB_ZM) && !(__ldg(a.act + t - tpl) & 1)) bad += nt;
-    if (lz == 7 && (info & NB_ZP) && !(__ldg(a.act + t + tpl) & 1)) bad += nt;
-    if (bad) atomicAdd(a.breaches, (unsigned long long)bad);
+    if (xh == 0 && (tb & 1u) && (inact & NB_XM)) bad += 1;
+    if (xh == 1 && (tb & 8u) && (inact & NB_XP)) bad += 1;
+    if (ly == 0 && (inact & NB_YM)) bad += nt;
+    if (ly == 7 && (inact & NB_YP)) bad += nt;
+    if (lz == 0 && (inact & NB_ZM)) bad += nt;
+    if (lz == 7 && (inact & NB_ZP)) bad += nt;
+    if (bad && a.breaches) atomicAdd(a.breaches, (unsigned long long)bad);
 }
 
 // FIELD: speed field (else constant per instance); CLASSIFY: fused tube
@@ -275,8 +308,10 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
 {
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    using Stage32 = Stage32T<FIELD>;
     Stage32* st = reinterpret_cast<Stage32*>(smem_raw);
     __shared__ unsigned smin[S];
+    __shared__ unsigned nfl[OP == OP_CUT ? S : 1];  // advance: some point of the tile is in N
     const int tid = threadIdx.x;
     const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
     const int n = *a.count;
@@ -339,6 +374,7 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         if (tid == 0) {
             Sg.meta = make_int4((int)t, (int)info, (int)inst, 0);
             if (CLASSIFY) smin[s] = 0x7f800000u;
+            if (OP == OP_CUT) nfl[s] = 0u;
         }
         int y_off = y_off1, z_off = z_off1;
         if (BATCHED) {
@@ -354,10 +390,14 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         if (OP >= OP_REINIT && tid < 4)
             cp_async16s(a_m + 64u * (unsigned)s, a.nmask + (size_t)kk * 16 + 4 * tid);
     };
+    // inst: the entry's instance (batched); for the local scheme's advance
+    // (single instance) the entry's active face-neighbour bits instead
     auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
         t = (unsigned)__ldg(list + k);
         info = __ldg(linfo + k);
-        inst = BATCHED ? (unsigned)__ldg(linst + k) : 0u;
+        if (BATCHED) inst = (unsigned)__ldg(linst + k);
+        else if (OP == OP_CUT || OP == OP_CUT_CLAMP) inst = __ldg(a.nact + k);
+        else inst = 0u;
     };
     auto gamma_of = [&](int inst) -> double { return BATCHED ? a.insts[inst].gamma : gamma1; };
 
@@ -378,12 +418,13 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
     int cur = 0;
     int prev = -1;
-    int prev_t = -1, prev_inst = 0;
+    int prev_t = -1, prev_k = -1, prev_inst = 0;
     for (int k = blockIdx.x; k < n; k += stride) {
         cp_async_wait<S - 2>();
         __syncthreads();
         if (CLASSIFY && tid == 0 && prev >= 0)
             a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma_of(prev_inst)) ? 1 : 0;
+        if (OP == OP_CUT && tid == 0 && prev >= 0) a.nflag[prev_k] = (uint8_t)nfl[prev];
         {
             const int sn = cur == 0 ? S - 1 : cur - 1;
             if (kn < n) issue(t1, i1, n1, sn, kn);
@@ -450,8 +491,12 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
                 else
                     o = upd4<0, true>(c, fs, xm0, xp3, ym, yp, zm, zp, coef, extrap, xlo, xhi, ylo,
                                       yhi, zlo, zhi);
-                const unsigned nb = n_nibble(c, xm0, xp3, ym, yp, zm, zp, xlo, xhi, ylo, yhi, zlo,
-                                             zhi, a.lp.gamma_up);
+                const unsigned nb =
+                    (info & NB_ALL) == NB_ALL
+                        ? n_nibble<false>(c, xm0, xp3, ym, yp, zm, zp, false, false, false, false,
+                                          false, false, a.lp.gamma_up)
+                        : n_nibble<true>(c, xm0, xp3, ym, yp, zm, zp, xlo, xhi, ylo, yhi, zlo, zhi,
+                                         a.lp.gamma_up);
                 if constexpr (OP == OP_CUT) {
                     // 16 words of N bits per entry; bit 4*tid + j = point j
                     uint32_t w = nb << (4 * (tid & 7));
@@ -459,6 +504,7 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
                     w |= __shfl_xor_sync(0xffffffffu, w, 2);
                     w |= __shfl_xor_sync(0xffffffffu, w, 4);
                     if ((tid & 7) == 0) a.nmask[(size_t)k * 16 + (tid >> 3)] = w;
+                    if (__any_sync(0xffffffffu, nb != 0u) && (tid & 31) == 0) nfl[cur] = 1u;
                 } else {
                     const float gn = a.lp.gamma_up;
                     if (nb & 1u) o.x = fminf(fmaxf(o.x, -gn), gn);
@@ -466,16 +512,18 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
                     if (nb & 4u) o.z = fminf(fmaxf(o.z, -gn), gn);
                     if (nb & 8u) o.w = fminf(fmaxf(o.w, -gn), gn);
                 }
-                if (a.breaches) count_breaches(a, c, t, info, xh, ly, lz);
+                // face neighbours inside the domain but not active
+                const unsigned inact = info & NB_ALL & ~(unsigned)inst;
+                if (inact) count_breaches(a, c, inact, xh, ly, lz);
             } else {
                 const unsigned nb = (nmk[cur][tid >> 3] >> (4 * (tid & 7))) & 15u;
                 constexpr bool CL = OP == OP_REINIT_CLAMP;
                 if ((info & NB_ALL) == NB_ALL)
-                    o = rei4<false, CL>(c, xm0, xp3, ym, yp, zm, zp, nb, a.lp, extrap, false, false,
-                                        false, false, false, false);
+                    o = rei_tile<false, CL>(c, xm0, xp3, ym, yp, zm, zp, nb, a.lp, extrap, false,
+                                            false, false, false, false, false);
                 else
-                    o = rei4<true, CL>(c, xm0, xp3, ym, yp, zm, zp, nb, a.lp, extrap, xlo, xhi, ylo,
-                                       yhi, zlo, zhi);
+                    o = rei_tile<true, CL>(c, xm0, xp3, ym, yp, zm, zp, nb, a.lp, extrap, xlo, xhi,
+                                           ylo, yhi, zlo, zhi);
             }
         }
         *reinterpret_cast<float4*>(dst + (unsigned)t * TILE_PTS + 4 * tid) = o;
@@ -487,13 +535,15 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         }
         prev = cur;
         prev_t = t;
+        prev_k = k;
         prev_inst = inst;
         cur = cur + 1 == S ? 0 : cur + 1;
     }
-    if (CLASSIFY) {
+    if (CLASSIFY || OP == OP_CUT) {
         __syncthreads();
-        if (tid == 0 && prev >= 0)
+        if (CLASSIFY && tid == 0 && prev >= 0)
             a.core[prev_t] = ((double)__uint_as_float(smin[prev]) < gamma_of(prev_inst)) ? 1 : 0;
+        if (OP == OP_CUT && tid == 0 && prev >= 0) a.nflag[prev_k] = (uint8_t)nfl[prev];
     }
     cp_async_wait<0>();
 }
@@ -508,6 +558,7 @@ template <bool FIELD, bool CLASSIFY, bool BATCHED, int S>
 __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    using Stage32 = Stage32T<FIELD>;
     Stage32* st = reinterpret_cast<Stage32*>(smem_raw);
     __shared__ unsigned smin[S];
     const int tid = threadIdx.x;
@@ -772,6 +823,8 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
 {
     __shared__ D4 sm[2][8][8][2];
     __shared__ unsigned long long smin[2];
+    __shared__ unsigned nfl[2];   // advance: some point of the tile is in N
+    long long prev_k = -1;
     const int tid = threadIdx.x;
     const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
     const Inst in = a.in;
@@ -819,9 +872,11 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
 
         sm[buf][lz][ly][xh] = c;
         if (CLASSIFY && tid == 0) smin[buf] = 0x7ff0000000000000ull;
+        if (OP == OP_CUT && tid == 0) nfl[buf] = 0u;
         __syncthreads();
         if (CLASSIFY && tid == 0 && prev_t >= 0)
             a.core[prev_t] = (__longlong_as_double((long long)smin[buf ^ 1]) < in.gamma) ? 1 : 0;
+        if (OP == OP_CUT && tid == 0 && prev_k >= 0) a.nflag[prev_k] = (uint8_t)nfl[buf ^ 1];
 
         const D4 ym = (ly > 0) ? sm[buf][lz][ly - 1][xh] : yo;
         const D4 yp = (ly < 7) ? sm[buf][lz][ly + 1][xh] : yo;
@@ -854,22 +909,21 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
                 w |= __shfl_xor_sync(0xffffffffu, w, 2);
                 w |= __shfl_xor_sync(0xffffffffu, w, 4);
                 if ((tid & 7) == 0) a.nmask[(size_t)k * 16 + (tid >> 3)] = w;
+                if (__any_sync(0xffffffffu, nb != 0u) && (tid & 31) == 0) nfl[buf] = 1u;
             }
-            if (a.breaches) {
+            const unsigned inact = info & NB_ALL & ~(unsigned)__ldg(a.nact + k);
+            if (inact && a.breaches) {
                 const unsigned tb = (fabs(c.v[0]) < g ? 1u : 0u) | (fabs(c.v[1]) < g ? 2u : 0u) |
                                     (fabs(c.v[2]) < g ? 4u : 0u) | (fabs(c.v[3]) < g ? 8u : 0u);
-                if (tb) {
-                    const long long tpl = (long long)in.tnx * in.tny;
-                    const unsigned nt = __popc(tb);
-                    unsigned bad = 0;
-                    if (xh == 0 && (tb & 1u) && (info & NB_XM) && !(__ldg(a.act + t - 1) & 1)) bad += 1;
-                    if (xh == 1 && (tb & 8u) && (info & NB_XP) && !(__ldg(a.act + t + 1) & 1)) bad += 1;
-                    if (ly == 0 && (info & NB_YM) && !(__ldg(a.act + t - in.tnx) & 1)) bad += nt;
-                    if (ly == 7 && (info & NB_YP) && !(__ldg(a.act + t + in.tnx) & 1)) bad += nt;
-                    if (lz == 0 && (info & NB_ZM) && !(__ldg(a.act + t - tpl) & 1)) bad += nt;
-                    if (lz == 7 && (info & NB_ZP) && !(__ldg(a.act + t + tpl) & 1)) bad += nt;
-                    if (bad) atomicAdd(a.breaches, (unsigned long long)bad);
-                }
+                const unsigned nt = __popc(tb);
+                unsigned bad = 0;
+                if (xh == 0 && (tb & 1u) && (inact & NB_XM)) bad += 1;
+                if (xh == 1 && (tb & 8u) && (inact & NB_XP)) bad += 1;
+                if (ly == 0 && (inact & NB_YM)) bad += nt;
+                if (ly == 7 && (inact & NB_YP)) bad += nt;
+                if (lz == 0 && (inact & NB_ZM)) bad += nt;
+                if (lz == 7 && (inact & NB_ZP)) bad += nt;
+                if (bad) atomicAdd(a.breaches, (unsigned long long)bad);
             }
         } else if constexpr (OP == OP_REINIT || OP == OP_REINIT_CLAMP) {
             nb = (__ldg(a.nmask + (size_t)k * 16 + (tid >> 3)) >> (4 * (tid & 7))) & 15u;
@@ -917,11 +971,13 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
         }
         buf ^= 1;
         prev_t = t;
+        prev_k = k;
     }
-    if (CLASSIFY) {
+    if (CLASSIFY || OP == OP_CUT) {
         __syncthreads();
-        if (tid == 0 && prev_t >= 0)
+        if (CLASSIFY && tid == 0 && prev_t >= 0)
             a.core[prev_t] = (__longlong_as_double((long long)smin[buf ^ 1]) < in.gamma) ? 1 : 0;
+        if (OP == OP_CUT && tid == 0 && prev_k >= 0) a.nflag[prev_k] = (uint8_t)nfl[buf ^ 1];
     }
 }
 
@@ -939,7 +995,7 @@ int occupancy_grid(K kernel, size_t smem, int threads = 128)
 template <bool FIELD, bool CLS, bool BAT, int S>
 cudaError_t launch32(const StepArgs& a, int grid_pct, int ppt, cudaStream_t s)
 {
-    constexpr size_t smem = sizeof(Stage32) * S;
+    constexpr size_t smem = sizeof(Stage32T<FIELD>) * S;
     static int full4 = 0, full8 = 0;
     int& full = ppt == 8 ? full8 : full4;
     if (!full)
@@ -959,16 +1015,17 @@ cudaError_t launch32_s(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
     switch (cfg.stages) {
     case 2: return launch32<FIELD, CLS, BAT, 2>(a, cfg.grid_pct, cfg.ppt, s);
     case 4: return launch32<FIELD, CLS, BAT, 4>(a, cfg.grid_pct, cfg.ppt, s);
+    case 6: return launch32<FIELD, CLS, BAT, 6>(a, cfg.grid_pct, cfg.ppt, s);
     default: return launch32<FIELD, CLS, BAT, 3>(a, cfg.grid_pct, cfg.ppt, s);
     }
 }
 
-// local-scheme passes: 4 points per thread, 3-stage ring
+// local-scheme passes: 4 points per thread; ring depth by stage size
 template <bool FIELD, bool CLS, int OP>
 cudaError_t launch32_op(const StepArgs& a, int grid_pct, cudaStream_t s)
 {
-    constexpr int S = 3;
-    constexpr size_t smem = sizeof(Stage32) * S;
+    constexpr int S = FIELD ? 3 : 6;  // the same bytes in flight per CTA
+    constexpr size_t smem = sizeof(Stage32T<FIELD>) * S;
     static int full = 0;
     if (!full) full = occupancy_grid(k_step_f32<FIELD, CLS, false, S, OP>, smem, 128);
     int grid = (int)((long long)full * grid_pct / 100);

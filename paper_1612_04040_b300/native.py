@@ -98,7 +98,8 @@ class Profile(ctypes.Structure):
     """ls_profile of include/ls.h."""
     _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("stencil_launches", ctypes.c_ulonglong),
                 ("stencil_ms", ctypes.c_double), ("stencil_timed", ctypes.c_ulonglong),
-                ("reinit_ms", ctypes.c_double), ("reinit_timed", ctypes.c_ulonglong)]
+                ("reinit_ms", ctypes.c_double), ("reinit_timed", ctypes.c_ulonglong),
+                ("reinit_updates", ctypes.c_ulonglong)]
 
 
 class LSError(RuntimeError):

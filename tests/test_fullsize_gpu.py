@@ -171,3 +171,49 @@ def test_batch_256_in_bench_configuration():
         ref = oracle.step(before[k].astype(np.float64), it.h, b.last_dt_i(k), Fc=it.speed,
                           tile_active=act.reshape((e // 8,) * 3))
         assert np.max(np.abs(out - ref)) <= 1e-5 * it.h, k
+
+
+def test_local_scheme_sphere_union_512():
+    """The 512^3 sphere-union run with the local scheme (beta 3h, gamma 6h,
+    12 reinitialisation iterations of dtau = h/2, clamp) in the benchmark's
+    configuration: one step recomputed by the oracle on sampled tiles, each
+    with a halo of 1 + 12 cells (one cell per pass), within (1 + 12) 1e-5 h;
+    frozen points unchanged; no N point outside the active tiles."""
+    w = inputs.SphereUnion()
+    dev = torch.device("cuda")
+    K = 12
+    g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32)
+    g.init_speed(ls.LS_SPEED_SINUSOID)
+    g.init_phi(ls.LS_SHAPE_SPHERES, inputs.spheres_params(w.centres, w.radii))
+    g.set_scheme(ls.LS_SCHEME_LOCAL, 3.0, K, 0.5)
+    g.band_rebuild(w.halfwidth)
+    g.step(23, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+    F = torch.empty((w.n,) * 3, dtype=torch.float32, device=dev)
+    before = torch.empty_like(F)
+    g.get_phi(before)
+    tiles = g.active_tiles()
+    dt = g.step(1, w.cfl, ls.LS_DT_CFL, w.rebuild_every, want_dt=True)
+    after = torch.empty_like(before)
+    g.get_phi(after)
+    Fh = w.speed(out_dtype=torch.float32).numpy().astype(np.float64)
+    pick = np.random.default_rng(4).choice(tiles, size=60, replace=False)
+    halo = 1 + K
+    worst = 0.0
+    for t in pick:
+        tz, ty, tx = int(t) // 4096, (int(t) // 64) % 64, int(t) % 64
+        lo = [max(0, 8 * v - halo) for v in (tz, ty, tx)]
+        hi = [min(w.n, 8 * v + 8 + halo) for v in (tz, ty, tx)]
+        sl = tuple(slice(a, b) for a, b in zip(lo, hi))
+        blk = before[sl].double().cpu().numpy()
+        ref, _ = oracle.local_step(blk, w.h, dt, 3.0 * w.h, w.halfwidth * w.h, K, 0.5 * w.h, F=Fh[sl])
+        o = [8 * v - a for v, a in zip((tz, ty, tx), lo)]
+        ref = ref[o[0]:o[0] + 8, o[1]:o[1] + 8, o[2]:o[2] + 8]
+        got = after[8 * tz:8 * tz + 8, 8 * ty:8 * ty + 8, 8 * tx:8 * tx + 8].double().cpu().numpy()
+        worst = max(worst, float(np.max(np.abs(got - ref))))
+    assert worst <= (1 + K) * 1e-5 * w.h, worst
+    act = np.zeros(64 ** 3, dtype=bool)
+    act[tiles] = True
+    mask = torch.from_numpy(np.repeat(np.repeat(np.repeat(act.reshape(64, 64, 64), 8, 0), 8, 1), 8, 2)).cuda()
+    assert torch.equal(before[~mask], after[~mask])
+    assert g.band_breaches() == 0
+    g.close()

@@ -168,6 +168,8 @@ def test_profile_counts_reinit_passes():
     assert p["stencil_timed"] == 5 * (1 + K)
     assert p["reinit_timed"] == 5 * K
     assert 0.0 < p["reinit_ms"] < p["stencil_ms"]
+    # the reinitialisation passes visit only the tiles holding points of N
+    assert 0 < p["reinit_updates"] < K * g.updates()
 
 
 def test_argument_and_state_errors():
