@@ -358,14 +358,46 @@ int ls_learned_add_pair(ls_ctx *ctx, const float *phi_n, const float *phi_ref, c
                         int on_device);
 int ls_learned_num_pairs(ls_ctx *ctx, long long *n);
 
+/* Load the parameters from a BF16 image (n = ls_learned_num_params values
+ * in the parameter layout above, 2 * n bytes, host memory); resets the
+ * optimiser.  ls_learned_save writes the current parameters as BF16 (round
+ * to nearest even).  Errors: LS_EINVAL (NULL, wrong byte count, unsupported
+ * context), LS_ESTATE (save before any parameters exist). */
+int ls_learned_load(ls_ctx *ctx, const void *bf16_weights, size_t bytes);
+int ls_learned_save(ls_ctx *ctx, void *bf16_weights, size_t bytes);
+
+/* Copy stored pair i out (row-major FP32, host or device memory). */
+int ls_learned_get_pair(ls_ctx *ctx, long long i, float *phi_n, float *phi_ref, float *F,
+                        int on_device);
+
 /* iters Adam steps (learning rate lr), each on one stored pair drawn with a
  * seeded generator: plain coarse step with fixed dt, forward, MSE of the
  * network output against (phi_ref - phi~)/h over the points with
  * |phi^n| < halfwidth*h, backward, update.  Uses the context's phi and
  * speed as scratch (phi must be set again afterwards).  *final_loss
  * (nullable) = the last iteration's loss. */
-int ls_learned_train(ls_ctx *ctx, int iters, double lr, double dt, double halfwidth_in_h,
-                     unsigned long long seed, double *final_loss);
+int ls_learned_train_stored(ls_ctx *ctx, int iters, double lr, double dt, double halfwidth_in_h,
+                            unsigned long long seed, double *final_loss);
+
+/* Training driven by a pair specification: "key=value" items separated by
+ * ',' or ';' (pairs_spec may be NULL or empty):
+ *   source=stored  train on the stored pairs (default); needs dt
+ *   source=fine    first generate pairs on the device and store them: per
+ *                  problem a seeded sphere union (2..5 spheres in the middle
+ *                  60 % of the box) and an 8-mode Fourier speed (|k|_inf <= 2,
+ *                  |F| <= 1), a plain narrow-band run on the 4x finer grid
+ *                  (band 4 * halfwidth fine cells, dt_f = cfl * h_f), every 4
+ *                  fine steps restricted to this grid as one pair
+ *   dt=<double>         coarse step (default for source=fine: cfl * h)
+ *   halfwidth=<double>  loss tube and coarse band in cells (default 6)
+ *   seed=<integer>      order of the pairs drawn (default 0)
+ *   problems=<n>, pairs=<n>, gen_seed=<integer>, cfl=<double>
+ *                       generation (defaults 8, 24 per problem, 1, 0.5)
+ * then as ls_learned_train_stored.  Needs initialised parameters.  Errors:
+ * LS_EINVAL (unknown key, malformed value, missing dt for stored pairs),
+ * LS_ESTATE, LS_ENOMEM, LS_ECUDA. */
+int ls_learned_train(ls_ctx *ctx, const char *pairs_spec, int iters, double lr,
+                     double *final_loss);
 
 /* LS_PLAIN (default) or LS_LEARNED for the steps of ls_step; LS_LEARNED
  * needs initialised parameters (LS_ESTATE). */

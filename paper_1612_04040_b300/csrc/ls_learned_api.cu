@@ -8,8 +8,10 @@
 // accumulation and FP32 master parameters.  Parameter vector layout: for
 // layer l = 0..3: W_l [27][ci_l][co_l] then b_l [co_l].
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "ls_ctx.cuh"
@@ -297,8 +299,8 @@ int ls_learned_num_pairs(ls_ctx* c, long long* n)
 // plain coarse step uses the fixed dt; the loss is the mean squared error
 // of z against (phi_ref - phi~)/h over the points with |phi^n| < gamma,
 // gamma = halfwidth * h.
-int ls_learned_train(ls_ctx* c, int iters, double lr, double dt, double halfwidth,
-                     unsigned long long seed, double* final_loss)
+int ls_learned_train_stored(ls_ctx* c, int iters, double lr, double dt, double halfwidth,
+                            unsigned long long seed, double* final_loss)
 {
     if (!c || iters < 0 || !(lr > 0) || !(dt > 0) || !(halfwidth > 0)) return LS_EINVAL;
     Learned* L = c->learned;
@@ -363,6 +365,266 @@ int ls_learned_train(ls_ctx* c, int iters, double lr, double dt, double halfwidt
     c->inst_phi_set[0] = 0;  // phi holds a training sample now
     c->graphs.clear();
     return LS_OK;
+}
+
+int ls_learned_load(ls_ctx* c, const void* bf16_weights, size_t bytes)
+{
+    if (!c || !bf16_weights || bytes != (size_t)lsk::n_params() * 2) return LS_EINVAL;
+    Learned* L = nullptr;
+    int r = ensure_learned(c, &L);
+    if (r) return r;
+    const uint16_t* w = (const uint16_t*)bf16_weights;
+    std::vector<float> p((size_t)lsk::n_params());
+    for (size_t i = 0; i < p.size(); ++i) {
+        const uint32_t u = (uint32_t)w[i] << 16;  // a BF16 value is the top half of an FP32
+        std::memcpy(&p[i], &u, 4);
+    }
+    LCK(cudaMemcpy(L->params, p.data(), p.size() * 4, cudaMemcpyHostToDevice));
+    LCK(cudaMemset(L->adam_m, 0, p.size() * 4));
+    LCK(cudaMemset(L->adam_v, 0, p.size() * 4));
+    L->adam_step = 0;
+    L->initialised = true;
+    c->graphs.clear();
+    return LS_OK;
+}
+
+int ls_learned_save(ls_ctx* c, void* bf16_weights, size_t bytes)
+{
+    if (!c || !bf16_weights || bytes != (size_t)lsk::n_params() * 2) return LS_EINVAL;
+    if (!c->learned || !c->learned->initialised) return LS_ESTATE;
+    std::vector<float> p((size_t)lsk::n_params());
+    LCK(cudaMemcpy(p.data(), c->learned->params, p.size() * 4, cudaMemcpyDeviceToHost));
+    uint16_t* w = (uint16_t*)bf16_weights;
+    for (size_t i = 0; i < p.size(); ++i) {
+        uint32_t u;
+        std::memcpy(&u, &p[i], 4);
+        if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) {
+            w[i] = (uint16_t)((u >> 16) | 0x40u);  // NaN stays NaN
+        } else {
+            u += 0x7fffu + ((u >> 16) & 1u);       // round to nearest, ties to even
+            w[i] = (uint16_t)(u >> 16);
+        }
+    }
+    return LS_OK;
+}
+
+int ls_learned_get_pair(ls_ctx* c, long long i, float* phi_n, float* phi_ref, float* F, int on_device)
+{
+    if (!c || !phi_n || !phi_ref || !F) return LS_EINVAL;
+    if (!c->learned || i < 0 || i >= (long long)c->learned->pairs.size()) return LS_EINVAL;
+    const lsk::Pair& P = c->learned->pairs[(size_t)i];
+    const size_t bytes = (size_t)c->learned->npts * 4;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    LCK(cudaMemcpyAsync(phi_n, P.phi, bytes, k, c->stream));
+    LCK(cudaMemcpyAsync(phi_ref, P.ref, bytes, k, c->stream));
+    LCK(cudaMemcpyAsync(F, P.F, bytes, k, c->stream));
+    LCK(cudaStreamSynchronize(c->stream));
+    return LS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// "key=value" items separated by ',' or ';'
+struct Spec {
+    double dt = -1.0, halfwidth = 6.0, cfl = 0.5;
+    unsigned long long seed = 0, gen_seed = 1;
+    int fine = 0, problems = 8, pairs = 24;
+};
+
+int parse_spec(const char* text, Spec* sp)
+{
+    if (!text) return LS_OK;
+    std::string t(text);
+    size_t pos = 0;
+    while (pos <= t.size()) {
+        size_t end = t.find_first_of(",;", pos);
+        if (end == std::string::npos) end = t.size();
+        std::string item = t.substr(pos, end - pos);
+        pos = end + 1;
+        const size_t a = item.find_first_not_of(" \t");
+        if (a == std::string::npos) continue;
+        item = item.substr(a, item.find_last_not_of(" \t") - a + 1);
+        const size_t eq = item.find('=');
+        if (eq == std::string::npos) return LS_EINVAL;
+        std::string key = item.substr(0, eq), val = item.substr(eq + 1);
+        while (!key.empty() && (key.back() == ' ' || key.back() == '\t')) key.pop_back();
+        while (!val.empty() && (val.front() == ' ' || val.front() == '\t')) val.erase(0, 1);
+        if (val.empty()) return LS_EINVAL;
+        char* e = nullptr;
+        if (key == "source") {
+            if (val == "stored") sp->fine = 0;
+            else if (val == "fine") sp->fine = 1;
+            else return LS_EINVAL;
+            continue;
+        }
+        if (key == "seed" || key == "gen_seed") {
+            const unsigned long long v = std::strtoull(val.c_str(), &e, 10);
+            if (*e) return LS_EINVAL;
+            (key == "seed" ? sp->seed : sp->gen_seed) = v;
+            continue;
+        }
+        if (key == "problems" || key == "pairs") {
+            const long v = std::strtol(val.c_str(), &e, 10);
+            if (*e || v < 1 || v > 100000) return LS_EINVAL;
+            (key == "problems" ? sp->problems : sp->pairs) = (int)v;
+            continue;
+        }
+        const double v = std::strtod(val.c_str(), &e);
+        if (*e || !std::isfinite(v) || !(v > 0.0)) return LS_EINVAL;
+        if (key == "dt") sp->dt = v;
+        else if (key == "halfwidth") sp->halfwidth = v;
+        else if (key == "cfl") sp->cfl = v;
+        else return LS_EINVAL;
+    }
+    return LS_OK;
+}
+
+// seeded splitmix64 stream (uniform doubles in [0, 1))
+struct Rng {
+    unsigned long long st;
+    explicit Rng(unsigned long long s) : st(s ^ 0x6a09e667f3bcc909ull) {}
+    double next()
+    {
+        unsigned long long z = (st += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    }
+    double uniform(double a, double b) { return a + (b - a) * next(); }
+};
+
+#define GCK(expr)                                                     \
+    do {                                                              \
+        int r_ = (expr);                                              \
+        if (r_ != LS_OK) { ls_destroy(fine); cudaFree(scratch); return r_; } \
+    } while (0)
+
+// Training pairs from plain runs on the 4x finer grid, restricted to this
+// context's grid: per problem a seeded sphere union (2..5 spheres inside the
+// middle 60 % of the box) and an 8-mode Fourier speed with |k|_inf <= 2 and
+// |F| <= 1; the fine band is 4x as wide in fine cells; dt_f = cfl * h_f and
+// every 4 fine steps give one pair (R(phi_f^n), R(phi_f^{n+4}), R(F_f)).
+int generate_pairs(ls_ctx* c, Learned* L, const Spec& sp)
+{
+    const Inst in = c->in0();
+    const int fx = 4 * in.nx, fy = 4 * in.ny, fz = 4 * in.nz;
+    const double hf = in.h / 4.0;
+    const double box[3] = {fx * hf, fy * hf, fz * hf};
+    const double bmin = std::fmin(box[0], std::fmin(box[1], box[2]));
+    ls_ctx* fine = nullptr;
+    float* scratch = nullptr;
+    int r = ls_create(fx, fy, fz, hf, LS_FP32, &fine);
+    if (r) return r;
+    const size_t fpts = (size_t)fx * fy * fz;
+    if (cudaMalloc(&scratch, fpts * 4) != cudaSuccess) {
+        ls_destroy(fine);
+        return LS_ENOMEM;
+    }
+    GCK(ls_set_stream(fine, c->stream));
+    const size_t cbytes = (size_t)L->npts * 4;
+    Rng g(sp.gen_seed);
+    for (int prob = 0; prob < sp.problems; ++prob) {
+        const int k = 2 + (int)(g.next() * 4.0);
+        std::vector<double> sph(1 + 4 * (size_t)k);
+        sph[0] = k;
+        const double rmax = 0.35 * bmin;
+        for (int i = 0; i < k; ++i) {
+            for (int d = 0; d < 3; ++d) sph[1 + 4 * i + d] = g.uniform(0.2 * box[d], 0.8 * box[d]);
+            sph[1 + 4 * i + 3] = g.uniform(0.3 * rmax, rmax);
+        }
+        std::vector<double> four(1 + 5 * 8);
+        four[0] = 8;
+        for (int m = 0; m < 8;) {
+            int kv[3];
+            for (int d = 0; d < 3; ++d) kv[d] = (int)(g.next() * 5.0) - 2;
+            if (!kv[0] && !kv[1] && !kv[2]) continue;
+            double* q = &four[1 + 5 * m];
+            q[0] = g.uniform(-1.0, 1.0);
+            q[1] = kv[0];
+            q[2] = kv[1];
+            q[3] = kv[2];
+            q[4] = g.uniform(0.0, 6.283185307179586);
+            ++m;
+        }
+        GCK(ls_init_phi(fine, LS_SHAPE_SPHERES, sph.data(), (int)sph.size()));
+        GCK(ls_init_speed(fine, LS_SPEED_FOURIER, four.data(), (int)four.size()));
+        GCK(ls_band_rebuild(fine, 4.0 * sp.halfwidth, nullptr));
+        cudaStream_t s = c->stream;
+        // coarse speed and the first state
+        lsk::Pair P;
+        auto alloc_pair = [&](lsk::Pair& q) -> int {
+            if (cudaMalloc(&q.phi, cbytes) != cudaSuccess || cudaMalloc(&q.ref, cbytes) != cudaSuccess ||
+                cudaMalloc(&q.F, cbytes) != cudaSuccess) {
+                cudaFree(q.phi); cudaFree(q.ref); cudaFree(q.F);
+                return LS_ENOMEM;
+            }
+            return LS_OK;
+        };
+        float* Fc = nullptr;
+        float* prev = nullptr;
+        if (cudaMalloc(&Fc, cbytes) != cudaSuccess || cudaMalloc(&prev, cbytes) != cudaSuccess) {
+            cudaFree(Fc);
+            GCK(LS_ENOMEM);
+        }
+        auto restrict_field = [&](const void* bricked, float* out) -> int {
+            cudaError_t e = lsk::launch_unpack(bricked, scratch, fine->in0(), 0, s);
+            if (e == cudaSuccess) e = lsk::launch_restrict4(scratch, fx, fy, fz, out, s);
+            c->launches += 2;
+            return e == cudaSuccess ? LS_OK : ls_engine_cuda_fail(e);
+        };
+        int rr = restrict_field(fine->F, Fc);
+        if (!rr) rr = restrict_field(fine->phi[fine->cur], prev);
+        for (int j = 0; !rr && j < sp.pairs; ++j) {
+            rr = ls_step(fine, 4, sp.cfl * hf, LS_DT_FIXED, 4, nullptr);
+            if (rr) break;
+            rr = alloc_pair(P);
+            if (rr) break;
+            rr = restrict_field(fine->phi[fine->cur], P.ref);
+            if (rr) { cudaFree(P.phi); cudaFree(P.ref); cudaFree(P.F); break; }
+            if (cudaMemcpyAsync(P.phi, prev, cbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(P.F, Fc, cbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(prev, P.ref, cbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                cudaFree(P.phi); cudaFree(P.ref); cudaFree(P.F);
+                rr = LS_ECUDA;
+                break;
+            }
+            L->pairs.push_back(P);
+        }
+        cudaStreamSynchronize(s);
+        cudaFree(Fc);
+        cudaFree(prev);
+        GCK(rr);
+    }
+    cudaStreamSynchronize(c->stream);
+    ls_destroy(fine);
+    cudaFree(scratch);
+    return LS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ls_learned_train(ls_ctx* c, const char* pairs_spec, int iters, double lr, double* final_loss)
+{
+    if (!c || iters < 0 || !(lr > 0)) return LS_EINVAL;
+    Spec sp;
+    int r = parse_spec(pairs_spec, &sp);
+    if (r) return r;
+    if (!sp.fine && !(sp.dt > 0.0)) return LS_EINVAL;  // stored pairs: their coarse step is needed
+    if (sp.fine) {
+        Learned* L = nullptr;
+        r = ensure_learned(c, &L);
+        if (r) return r;
+        if (!L->initialised) return LS_ESTATE;
+        r = generate_pairs(c, L, sp);
+        if (r) return r;
+        if (!(sp.dt > 0.0)) sp.dt = sp.cfl * c->in0().h;  // 4 fine steps of cfl * h / 4
+    }
+    return ls_learned_train_stored(c, iters, lr, sp.dt, sp.halfwidth, sp.seed, final_loss);
 }
 
 int ls_set_step_mode(ls_ctx* c, int mode)

@@ -76,7 +76,11 @@ SIGNATURES = {
     "ls_learned_get_params": (_i, [_vp, _vp, _ll]),
     "ls_learned_add_pair": (_i, [_vp, _vp, _vp, _vp, _i]),
     "ls_learned_num_pairs": (_i, [_vp, _c.POINTER(_ll)]),
-    "ls_learned_train": (_i, [_vp, _i, _d, _d, _d, _c.c_ulonglong, _c.POINTER(_d)]),
+    "ls_learned_train_stored": (_i, [_vp, _i, _d, _d, _d, _c.c_ulonglong, _c.POINTER(_d)]),
+    "ls_learned_train": (_i, [_vp, _c.c_char_p, _i, _d, _c.POINTER(_d)]),
+    "ls_learned_load": (_i, [_vp, _vp, _c.c_size_t]),
+    "ls_learned_save": (_i, [_vp, _vp, _c.c_size_t]),
+    "ls_learned_get_pair": (_i, [_vp, _c.c_longlong, _vp, _vp, _vp, _i]),
     "ls_set_step_mode": (_i, [_vp, _i]),
     "ls_set_scheme": (_i, [_vp, _i, _c.c_double, _i, _c.c_double]),
     "ls_band_breaches": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
@@ -389,10 +393,43 @@ class LevelSet:
               "ls_learned_add_pair")
 
     def learned_train(self, iters, lr, dt, halfwidth, seed=0):
+        """Adam on the stored pairs (ls_learned_train_stored); returns the last loss."""
         loss = ctypes.c_double(0.0)
-        check(self.lib.ls_learned_train(self.ctx, int(iters), float(lr), float(dt), float(halfwidth),
-                                        ctypes.c_ulonglong(seed), ctypes.byref(loss)), "ls_learned_train")
+        check(self.lib.ls_learned_train_stored(self.ctx, int(iters), float(lr), float(dt), float(halfwidth),
+                                               ctypes.c_ulonglong(seed), ctypes.byref(loss)),
+              "ls_learned_train_stored")
         return loss.value
+
+    def learned_num_pairs(self):
+        n = ctypes.c_longlong(0)
+        check(self.lib.ls_learned_num_pairs(self.ctx, ctypes.byref(n)), "ls_learned_num_pairs")
+        return n.value
+
+    def learned_train_spec(self, spec, iters, lr):
+        """ls_learned_train with a pair specification string; returns the last loss."""
+        loss = ctypes.c_double(0.0)
+        check(self.lib.ls_learned_train(self.ctx, None if spec is None else spec.encode(), int(iters),
+                                        float(lr), ctypes.byref(loss)), "ls_learned_train")
+        return loss.value
+
+    def learned_load(self, bf16):
+        """Parameters from a BF16 image (numpy uint16 / bytes of 2 * num_params bytes)."""
+        buf = np.ascontiguousarray(np.frombuffer(bytes(bf16), dtype=np.uint16))
+        check(self.lib.ls_learned_load(self.ctx, buf.ctypes.data, buf.nbytes), "ls_learned_load")
+
+    def learned_save(self):
+        n = ctypes.c_longlong(0)
+        check(self.lib.ls_learned_num_params(ctypes.byref(n)), "ls_learned_num_params")
+        out = np.empty(n.value, dtype=np.uint16)
+        check(self.lib.ls_learned_save(self.ctx, out.ctypes.data, out.nbytes), "ls_learned_save")
+        return out
+
+    def learned_get_pair(self, i):
+        shape = self.shape
+        a, b, f = (np.empty(shape, dtype=np.float32) for _ in range(3))
+        check(self.lib.ls_learned_get_pair(self.ctx, int(i), a.ctypes.data, b.ctypes.data, f.ctypes.data, 0),
+              "ls_learned_get_pair")
+        return a, b, f
 
     def set_step_mode(self, mode):
         check(self.lib.ls_set_step_mode(self.ctx, int(mode)), "ls_set_step_mode")
