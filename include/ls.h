@@ -258,8 +258,12 @@ typedef struct {
                                             point of N)                             */
 } ls_profile;
 
-/* Enable (1) or disable (0) CUDA-event timing of every upwind-step launch
- * (one event pair per launch, recorded on the context's stream). */
+/* Enable (1) or disable (0) CUDA-event timing of the upwind-step launches:
+ * one event pair, recorded on the context's stream, brackets each run of
+ * back-to-back stencil launches of one kind (the plain step or the local
+ * scheme's advance; the reinitialisation passes), so stencil_ms is their
+ * summed device time including the gaps between them and stencil_timed the
+ * number of launches it covers.  Any other kernel ends a run. */
 int ls_profile_enable(ls_ctx *ctx, int on);
 
 /* Read the counters (synchronises the stream).  Errors: LS_EINVAL. */

@@ -86,10 +86,10 @@ int drain_events(ls_ctx* c)
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, p.e0, p.e1));
         c->stencil_ms += ms;
-        c->stencil_timed += 1;
+        c->stencil_timed += (unsigned long long)p.count;
         if (p.reinit) {
             c->reinit_ms += ms;
-            c->reinit_timed += 1;
+            c->reinit_timed += (unsigned long long)p.count;
         }
         c->ev_free.push_back(p.e0);
         c->ev_free.push_back(p.e1);
@@ -315,12 +315,47 @@ lsk::LocalParams local_params(const ls_ctx* c)
     return lp;
 }
 
+// Profiling: one event pair brackets each run of back-to-back stencil
+// launches of one kind (plain / advance, or reinitialisation); any other
+// kernel closes the run.  The time per launch is then the run's time over
+// its launches (gaps between them included), without an event record
+// between every two launches.
+int prof_close(ls_ctx* c, cudaStream_t s)
+{
+    if (!c->ev_open) return LS_OK;
+    cudaEvent_t e1 = nullptr;
+    CK(take_event(c, &e1));
+    CK(cudaEventRecord(e1, s));
+    c->ev_pending.push_back({c->ev_open_e0, e1, c->ev_open_kind == 1, c->ev_open_n});
+    c->ev_open = false;
+    return LS_OK;
+}
+
+int prof_before_stencil(ls_ctx* c, int kind, cudaStream_t s)
+{
+    if (!c->profiling) return LS_OK;
+    if (c->ev_open && c->ev_open_kind != kind) RET(prof_close(c, s));
+    if (!c->ev_open) {
+        if (c->ev_pending.size() >= 4096) RET(drain_events(c));
+        CK(take_event(c, &c->ev_open_e0));
+        CK(cudaEventRecord(c->ev_open_e0, s));
+        c->ev_open = true;
+        c->ev_open_kind = kind;
+        c->ev_open_n = 0;
+    }
+    ++c->ev_open_n;
+    return LS_OK;
+}
+
 // the step loop of ls_step (eager, or recorded into a graph by the caller)
 int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every, cudaStream_t s)
 {
     bool dt_pending = true;
     for (int k = 0; k < nsteps; ++k) {
         bool rebuilt = false;
+        if (c->profiling && (!c->band_valid || (rebuild_every > 0 && c->since_rebuild >= rebuild_every) ||
+                             (dt_pending && k == 0)))
+            RET(prof_close(c, s));
         if (c->full_domain) {
             if (!c->band_valid) {
                 RET(full_domain_bound(c, s));
@@ -374,22 +409,16 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
                     a.updates = c->d_rupdates;
                 }
             }
-            if (c->profiling && c->ev_pending.size() >= 4096) RET(drain_events(c));
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (c->profiling) {
-                CK(take_event(c, &e0));
-                CK(take_event(c, &e1));
-                CK(cudaEventRecord(e0, s));
-            }
+            RET(prof_before_stencil(c, p > 0 ? 1 : 0, s));
             KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
             ++c->stencil_launches;
-            if (c->profiling) {
-                CK(cudaEventRecord(e1, s));
-                c->ev_pending.push_back({e0, e1, p > 0});
+            if (c->step_mode == LS_LEARNED) {
+                if (c->profiling) RET(prof_close(c, s));
+                RET(ls_engine_learned_after_step(c, s));
             }
-            if (c->step_mode == LS_LEARNED) RET(ls_engine_learned_after_step(c, s));
             c->cur ^= 1;
             if (local && p == 0 && K > 0) {
+                if (c->profiling) RET(prof_close(c, s));
                 KL(c, lsk::launch_nflag_count(c->nflag, c->d_count, c->block_counts, c->nblocks, s));
                 KL(c, lsk::launch_scan(c->block_counts, c->nblocks, c->d_ncount, s));
                 KL(c, lsk::launch_nflag_scatter(c->nflag, c->d_count, c->block_counts, c->list,
@@ -401,6 +430,7 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
         c->since_rebuild += 1;
         c->core_fresh = classify;
     }
+    if (c->profiling) RET(prof_close(c, s));
     return LS_OK;
 }
 
@@ -1043,6 +1073,7 @@ int ls_get_updates(ls_ctx* c, unsigned long long* n)
 int ls_profile_enable(ls_ctx* c, int on)
 {
     if (!c) return LS_EINVAL;
+    if (!on && c->ev_open) RET(prof_close(c, c->stream));
     c->profiling = on != 0;
     return LS_OK;
 }

@@ -97,8 +97,12 @@ struct ls_ctx {
     std::vector<cudaEvent_t> ev_free;
     double reinit_ms = 0.0;
     unsigned long long reinit_timed = 0;
-    struct EvPair { cudaEvent_t e0, e1; bool reinit; };
+    struct EvPair { cudaEvent_t e0, e1; bool reinit; int count; };
     std::vector<EvPair> ev_pending;
+    bool ev_open = false;          // an event run of stencil launches is open
+    int ev_open_kind = 0;          // 0 plain / advance, 1 reinitialisation
+    int ev_open_n = 0;             // launches in the open run
+    cudaEvent_t ev_open_e0 = nullptr;
 
     // local scheme (section 1.1, Steps 1-3)
     int scheme = LS_SCHEME_PLAIN;
