@@ -66,6 +66,16 @@ __device__ __forceinline__ float rsqrt_hw(float x)
     return r;
 }
 
+// Programmatic dependent launch: a stencil launch may start while the
+// previous one drains.  Every CTA lets the next grid launch at once (it can
+// only take the slots this grid frees), then waits for the previous grid's
+// completion and memory before it reads anything.
+__device__ __forceinline__ void pdl_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // one ring stage; without a speed field the stage has no speed block, so a
 // deeper ring fits in the same shared memory
 template <bool FIELD>
@@ -314,6 +324,9 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     __shared__ unsigned nfl[OP == OP_CUT ? S : 1];  // advance: some point of the tile is in N
     const int tid = threadIdx.x;
     const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
+    // everything this grid reads may come from the previous grid
+    pdl_launch_dependents();
+    pdl_wait();
     const int n = *a.count;
     if (blockIdx.x == 0 && tid == 0 && a.updates)
         atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
@@ -565,6 +578,9 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
     const int xh = tid & 1, ly = (tid >> 1) & 7, lzp = tid >> 4;
     const int q0 = tid + 16 * lzp, q1 = q0 + 16;
     const int lz0 = 2 * lzp;
+    // everything this grid reads may come from the previous grid
+    pdl_launch_dependents();
+    pdl_wait();
     const int n = *a.count;
     if (blockIdx.x == 0 && tid == 0 && a.updates)
         atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
@@ -981,6 +997,23 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
     }
 }
 
+// launch with programmatic stream serialisation (see pdl_wait)
+template <typename K>
+cudaError_t launch_pdl(K kernel, int grid, int block, size_t smem, const StepArgs& a, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <typename K>
 int occupancy_grid(K kernel, size_t smem, int threads = 128)
 {
@@ -1004,9 +1037,8 @@ cudaError_t launch32(const StepArgs& a, int grid_pct, int ppt, cudaStream_t s)
     int grid = (int)((long long)full * grid_pct / 100);
     if (grid < 1) grid = 1;
     if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
-    if (ppt == 8) k_step_f32_z2<FIELD, CLS, BAT, S><<<grid, 64, smem, s>>>(a);
-    else k_step_f32<FIELD, CLS, BAT, S><<<grid, 128, smem, s>>>(a);
-    return cudaGetLastError();
+    if (ppt == 8) return launch_pdl(k_step_f32_z2<FIELD, CLS, BAT, S>, grid, 64, smem, a, s);
+    return launch_pdl(k_step_f32<FIELD, CLS, BAT, S>, grid, 128, smem, a, s);
 }
 
 template <bool FIELD, bool CLS, bool BAT>
@@ -1031,8 +1063,7 @@ cudaError_t launch32_op(const StepArgs& a, int grid_pct, cudaStream_t s)
     int grid = (int)((long long)full * grid_pct / 100);
     if (grid < 1) grid = 1;
     if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
-    k_step_f32<FIELD, CLS, false, S, OP><<<grid, 128, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_step_f32<FIELD, CLS, false, S, OP>, grid, 128, smem, a, s);
 }
 
 cudaError_t launch_local32(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
