@@ -139,7 +139,7 @@ void free_all(ls_ctx* c)
                     c->d_Mbits, c->d_updates, c->d_status, c->d_nonfinite, c->d_inst,
                     c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params, c->nmask,
                     c->d_breaches, c->list_nact, c->nmask2, c->nflag, c->nl, c->nl_info,
-                    c->d_ncount, c->d_rupdates};
+                    c->d_ncount, c->d_rupdates, c->d_done};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -209,7 +209,6 @@ int finish_rebuild(ls_ctx* c, cudaStream_t s)
     void* cur = c->phi[c->cur];
     void* other = c->phi[c->cur ^ 1];
     const void* tmf = speed_mode(c) == 2 ? c->tile_maxF : nullptr;
-    KL(c, lsk::launch_scan(c->block_counts, c->nblocks, c->d_count, s));
     if (c->batched) {
         KL(c, lsk::launch_scatter_batch(c->act, c->block_counts, c->list, c->list_info,
                                         c->d_list_inst, sign_table(c), c->d_inst, c->d_tile_inst,
@@ -220,9 +219,8 @@ int finish_rebuild(ls_ctx* c, cudaStream_t s)
     } else {
         KL(c, lsk::launch_scatter(c->act, c->block_counts, c->list, c->list_info, sign_table(c),
                                   const_sign_bits(c), c->in0(), c->ntiles, tmf, c->prec,
-                                  c->d_Mbits, cur, other, c->list_nact, s));
-        KL(c, lsk::launch_set_dt(c->d_sc, 1, nullptr, c->in0(), c->dt_mode, c->dt_value, 1,
-                                 c->prec, c->d_Mbits, c->d_count, 0, s));
+                                  c->d_Mbits, cur, other, c->list_nact, c->d_sc, c->dt_mode,
+                                  c->dt_value, c->d_count, c->d_done + 1, s));
     }
     return LS_OK;
 }
@@ -234,7 +232,7 @@ int rebuild(ls_ctx* c, bool full_scan, cudaStream_t s)
         KL(c, lsk::launch_classify_all(cur, c->core, c->dinst(), c->tinst(), c->in0(), c->ntiles,
                                        c->prec, s));
     KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, c->dinst(), c->tinst(), c->in0(),
-                             c->ntiles, s));
+                             c->ntiles, c->d_done, c->d_count, s));
     RET(finish_rebuild(c, s));
     c->band_valid = true;
     c->core_fresh = false;
@@ -249,7 +247,7 @@ int full_domain_bound(ls_ctx* c, cudaStream_t s)
         // and the regular scatter builds the full list, counts and bounds
         CK(cudaMemsetAsync(c->core, 1, c->ntiles, s));
         KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, c->d_inst, c->d_tile_inst,
-                                 c->in0(), c->ntiles, s));
+                                 c->in0(), c->ntiles, c->d_done, c->d_count, s));
         RET(finish_rebuild(c, s));
     } else {
         // every tile counts as active, so a later switch back to a band copies
@@ -419,8 +417,8 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
             c->cur ^= 1;
             if (local && p == 0 && K > 0) {
                 if (c->profiling) RET(prof_close(c, s));
-                KL(c, lsk::launch_nflag_count(c->nflag, c->d_count, c->block_counts, c->nblocks, s));
-                KL(c, lsk::launch_scan(c->block_counts, c->nblocks, c->d_ncount, s));
+                KL(c, lsk::launch_nflag_count(c->nflag, c->d_count, c->block_counts, c->nblocks,
+                                              c->d_done + 2, c->d_ncount, s));
                 KL(c, lsk::launch_nflag_scatter(c->nflag, c->d_count, c->block_counts, c->list,
                                                 c->list_info, c->nmask, c->nl, c->nl_info,
                                                 c->nmask2, classify ? c->core : nullptr,
@@ -561,6 +559,8 @@ int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h
     A(dalloc(&c->list, c->ntiles * sizeof(int)));
     A(dalloc(&c->list_info, c->ntiles));
     A(dalloc(&c->d_count, sizeof(int)));
+    A(dalloc(&c->d_done, 4 * sizeof(unsigned)));
+    if (e == cudaSuccess) e = cudaMemset(c->d_done, 0, 4 * sizeof(unsigned));
     A(dalloc(&c->block_counts, c->nblocks * sizeof(int)));
     A(dalloc(&c->d_sc, sizeof(lsk::StepScalars) * n));
     A(dalloc(&c->d_Mbits, sizeof(unsigned long long) * n));

@@ -210,10 +210,65 @@ __global__ void __launch_bounds__(256) k_classify_all(const T* __restrict__ phi,
 // flag in bit 0 and the previous one in bit 1 (the scatter pass uses both to
 // find the tiles that leave the active set).
 // ---------------------------------------------------------------------------
+// The block that finishes last (every block fences its writes before it
+// counts itself) sees the results of all blocks; true in all its threads.
+// That block resets the counter for the next launch.  No block waits.
+__device__ __forceinline__ bool last_block(unsigned* done)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+        if (last) *done = 0u;
+    }
+    __syncthreads();
+    return last;
+}
+
+// exclusive scan in place of n block counts by one 256-thread block (the
+// counts of other blocks are read from L2); total -> *total
+__device__ void block_scan256(int* counts, int n, int* total)
+{
+    __shared__ int warp_sums[8];
+    const int per = (n + 255) / 256;
+    const int b0 = threadIdx.x * per;
+    int local = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < n) local += __ldcg(counts + b0 + k);
+    int v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane_id() >= o) v += u;
+    }
+    if (lane_id() == 31) warp_sums[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int w = threadIdx.x < 8 ? warp_sums[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, w, o);
+            if ((int)threadIdx.x >= o) w += u;
+        }
+        if (threadIdx.x < 8) warp_sums[threadIdx.x] = w;
+    }
+    __syncthreads();
+    int run = v - local + ((threadIdx.x >> 5) ? warp_sums[(threadIdx.x >> 5) - 1] : 0);
+    for (int k = 0; k < per; ++k) {
+        if (b0 + k < n) {
+            const int c = __ldcg(counts + b0 + k);
+            counts[b0 + k] = run;
+            run += c;
+        }
+    }
+    if (threadIdx.x == 255) *total = run;
+}
+
 __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core, uint8_t* act,
                                                 int* block_counts, const Inst* d_inst,
                                                 const uint16_t* tile_inst, Inst single,
-                                                long long ntiles)
+                                                long long ntiles, unsigned* done, int* total)
 {
     const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
     int on = 0;
@@ -243,6 +298,8 @@ __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core
     }
     const int cnt = __syncthreads_count(on);
     if (threadIdx.x == 0) block_counts[blockIdx.x] = cnt;
+    // the last block turns the counts into offsets and the active count
+    if (last_block(done)) block_scan256(block_counts, (int)gridDim.x, total);
 }
 
 // Reinitialisation list of the local scheme: the entries of the active list
@@ -252,13 +309,15 @@ __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core
 // advance, so those passes skip them.
 __global__ void __launch_bounds__(256) k_nflag_count(const uint8_t* __restrict__ nflag,
                                                      const int* __restrict__ count,
-                                                     int* block_counts)
+                                                     int* block_counts, unsigned* done,
+                                                     int* total)
 {
     const int n = *count;
     const int k = blockIdx.x * 256 + threadIdx.x;
     const int on = (k < n) ? (nflag[k] != 0) : 0;
     const int cnt = __syncthreads_count(on);
     if (threadIdx.x == 0) block_counts[blockIdx.x] = cnt;
+    if (last_block(done)) block_scan256(block_counts, (int)gridDim.x, total);
 }
 
 // ascending compaction of the flagged entries: tile id, info byte and the 64
@@ -330,6 +389,37 @@ __global__ void __launch_bounds__(1024) k_scan(int* counts, int n, int* total)
     if (threadIdx.x == 1023) *total = run;
 }
 
+// dt of instance i (Eq. 3 has no rule; CFL: dt = value * h / M, value * h
+// when M = 0).  finalize: M from the max|F| bits of the rebuild (or |Fc| for a
+// constant speed; 0 for an empty band), bits cleared for the next rebuild.
+__device__ void set_dt_one(StepScalars* sc, int i, const Inst& in, int mode, double value,
+                           int finalize, int prec, unsigned long long* Mbits, long long n)
+{
+    double M;
+    if (finalize) {
+        if (in.speed_mode == 1) {
+            M = (n > 0) ? fabs(in.Fc) : 0.0;
+        } else {
+            const unsigned long long b = __ldcg(Mbits + i);
+            M = prec == 0 ? (double)__uint_as_float((unsigned)b) : __longlong_as_double((long long)b);
+            if (n == 0) M = 0.0;
+        }
+        Mbits[i] = 0;
+        sc[i].M = M;
+    } else {
+        M = sc[i].M;
+    }
+    double dt;
+    if (mode == 1) {
+        const double ch = __dmul_rn(value, in.h);
+        dt = (M > 0.0) ? __ddiv_rn(ch, M) : ch;
+    } else {
+        dt = value;
+    }
+    sc[i].dt = dt;
+    sc[i].coef = __double2float_rn(__ddiv_rn(dt, in.h));
+}
+
 template <typename T>
 __device__ __forceinline__ unsigned long long ordered_bits(T v)
 {
@@ -351,7 +441,9 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
                                                  long long ntiles, const T* __restrict__ tile_maxF,
                                                  unsigned long long* Mbits,
                                                  const uint4* __restrict__ cur, uint4* other,
-                                                 uint8_t* list_nact)
+                                                 uint8_t* list_nact, StepScalars* sc, int dt_mode,
+                                                 double dt_value, const int* count,
+                                                 unsigned* done)
 {
     __shared__ int warp_cnt[8];
     __shared__ int warp_leave[8];
@@ -399,14 +491,19 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
         for (int k = 0; k < 8; ++k) m = warp_max_bits[k] > m ? warp_max_bits[k] : m;
         if (m) atomicMax(Mbits, m);
     }
-    if (ltotal == 0) return;
-    __syncthreads();
-    constexpr int VEC = TILE_PTS * sizeof(T) / 16;  // uint4 per tile
-    const int total = ltotal * VEC;
-    for (int i = threadIdx.x; i < total; i += 256) {
-        const size_t off = (size_t)leave_ids[i / VEC] * VEC + (i % VEC);
-        other[off] = cur[off];
+    if (ltotal > 0) {
+        __syncthreads();
+        constexpr int VEC = TILE_PTS * sizeof(T) / 16;  // uint4 per tile
+        const int total = ltotal * VEC;
+        for (int i = threadIdx.x; i < total; i += 256) {
+            const size_t off = (size_t)leave_ids[i / VEC] * VEC + (i % VEC);
+            other[off] = cur[off];
+        }
     }
+    // the last block has every block's max|F| bits: the step's dt
+    if (last_block(done) && threadIdx.x == 0)
+        set_dt_one(sc, 0, single, dt_mode, dt_value, 1, sizeof(T) == 4 ? 0 : 1, Mbits,
+                   (long long)__ldcg(count));
 }
 
 // scatter for a batch of instances (FP32): as k_scatter, plus the instance
@@ -549,30 +646,8 @@ __global__ void k_set_dt(StepScalars* sc, int n_inst, const Inst* d_inst, Inst s
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_inst) return;
     const Inst& in = d_inst ? d_inst[i] : single;
-    double M;
-    if (finalize) {
-        const long long n = count ? (long long)*count : fixed_count;
-        if (in.speed_mode == 1) {
-            M = (n > 0) ? fabs(in.Fc) : 0.0;
-        } else {
-            const unsigned long long b = Mbits[i];
-            M = prec == 0 ? (double)__uint_as_float((unsigned)b) : __longlong_as_double((long long)b);
-            if (n == 0) M = 0.0;
-        }
-        Mbits[i] = 0;
-        sc[i].M = M;
-    } else {
-        M = sc[i].M;
-    }
-    double dt;
-    if (mode == 1) {
-        const double ch = __dmul_rn(value, in.h);
-        dt = (M > 0.0) ? __ddiv_rn(ch, M) : ch;
-    } else {
-        dt = value;
-    }
-    sc[i].dt = dt;
-    sc[i].coef = __double2float_rn(__ddiv_rn(dt, in.h));
+    const long long n = count ? (long long)*count : fixed_count;
+    set_dt_one(sc, i, in, mode, value, finalize, prec, Mbits, n);
 }
 
 }  // namespace
@@ -643,17 +718,18 @@ cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_in
 
 cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
                           const Inst* d_inst, const uint16_t* tile_inst, const Inst& single,
-                          long long ntiles, cudaStream_t s)
+                          long long ntiles, unsigned* done, int* count, cudaStream_t s)
 {
     const int nb = (int)((ntiles + 255) / 256);
-    k_dilate<<<nb, 256, 0, s>>>(core, act, block_counts, d_inst, tile_inst, single, ntiles);
+    k_dilate<<<nb, 256, 0, s>>>(core, act, block_counts, d_inst, tile_inst, single, ntiles, done,
+                                count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_nflag_count(const uint8_t* nflag, const int* count, int* block_counts,
-                               int nblocks, cudaStream_t s)
+                               int nblocks, unsigned* done, int* total, cudaStream_t s)
 {
-    k_nflag_count<<<nblocks, 256, 0, s>>>(nflag, count, block_counts);
+    k_nflag_count<<<nblocks, 256, 0, s>>>(nflag, count, block_counts, done, total);
     return cudaGetLastError();
 }
 
@@ -677,17 +753,20 @@ cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* li
                            uint8_t* list_info, const uint8_t* tile_sgn, unsigned const_sgn,
                            const Inst& single, long long ntiles, const void* tile_maxF, int prec,
                            unsigned long long* Mbits, const void* cur, void* other,
-                           uint8_t* list_nact, cudaStream_t s)
+                           uint8_t* list_nact, StepScalars* sc, int dt_mode, double dt_value,
+                           const int* count, unsigned* done, cudaStream_t s)
 {
     const int nb = (int)((ntiles + 255) / 256);
     if (prec == 0)
         k_scatter<float><<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, tile_sgn,
                                             const_sgn, single, ntiles, (const float*)tile_maxF,
-                                            Mbits, (const uint4*)cur, (uint4*)other, list_nact);
+                                            Mbits, (const uint4*)cur, (uint4*)other, list_nact,
+                                            sc, dt_mode, dt_value, count, done);
     else
         k_scatter<double><<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, tile_sgn,
                                              const_sgn, single, ntiles, (const double*)tile_maxF,
-                                             Mbits, (const uint4*)cur, (uint4*)other, list_nact);
+                                             Mbits, (const uint4*)cur, (uint4*)other, list_nact,
+                                             sc, dt_mode, dt_value, count, done);
     return cudaGetLastError();
 }
 

@@ -68,6 +68,7 @@ struct ls_ctx {
     int* list = nullptr;
     uint8_t* list_info = nullptr;
     int* d_count = nullptr;
+    unsigned* d_done = nullptr;   // last-block counters: dilate, scatter, N-flag count
     int* block_counts = nullptr;
     int nblocks = 0;
     lsk::StepScalars* d_sc = nullptr;

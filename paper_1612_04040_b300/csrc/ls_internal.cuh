@@ -76,25 +76,29 @@ cudaError_t launch_tile_speed(const void* F, void* tile_maxF, uint8_t* tile_sgn,
 cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_inst,
                                 const uint16_t* tile_inst, const Inst& single, long long ntiles,
                                 int prec, cudaStream_t s);
-// band rebuild: dilation (act bit 0 = new flag, bit 1 = previous) + block counts
+// band rebuild: dilation (act bit 0 = new flag, bit 1 = previous) + block
+// counts, turned into exclusive offsets and the active count *count by the
+// last block to finish (done: a zeroed device counter, reset by that block)
 cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
                           const Inst* d_inst, const uint16_t* tile_inst, const Inst& single,
-                          long long ntiles, cudaStream_t s);
+                          long long ntiles, unsigned* done, int* count, cudaStream_t s);
 // exclusive scan of block counts, writes total to *count
 cudaError_t launch_scan(int* block_counts, int nblocks, int* count, cudaStream_t s);
 // local scheme: the active-list entries whose tile holds a point of N
 // (nflag), compacted in ascending order with their info bytes and N bits
-// (block counts -> launch_scan -> scatter); core[t] = 0 for the others when
-// core is not NULL
+// (block counts, scanned by the last block -> scatter); core[t] = 0 for the
+// others when core is not NULL
 cudaError_t launch_nflag_count(const uint8_t* nflag, const int* count, int* block_counts,
-                               int nblocks, cudaStream_t s);
+                               int nblocks, unsigned* done, int* total, cudaStream_t s);
 cudaError_t launch_nflag_scatter(const uint8_t* nflag, const int* count, const int* block_offsets,
                                  const int* list, const uint8_t* list_info, const uint32_t* nmask,
                                  int* nl, uint8_t* nl_info, uint32_t* nl_mask, uint8_t* core,
                                  int nblocks, cudaStream_t s);
 // scatter active ids (ascending) with their info bytes, fold max |F| of the
 // active tiles into *Mbits (ordered bits of a non-negative float / double),
-// and copy the tiles leaving the active set from cur into other.
+// and copy the tiles leaving the active set from cur into other; the last
+// block to finish sets the step scalars (dt from M as launch_set_dt with
+// finalize = 1; done: a zeroed device counter).
 // tile_sgn == NULL: constant speed, sign bits const_sgn.
 // list_nact (may be NULL): per entry, the face neighbours inside the domain
 // that are active (NB_* bits)
@@ -102,7 +106,8 @@ cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* li
                            uint8_t* list_info, const uint8_t* tile_sgn, unsigned const_sgn,
                            const Inst& single, long long ntiles, const void* tile_maxF, int prec,
                            unsigned long long* Mbits, const void* cur, void* other,
-                           uint8_t* list_nact, cudaStream_t s);
+                           uint8_t* list_nact, StepScalars* sc, int dt_mode, double dt_value,
+                           const int* count, unsigned* done, cudaStream_t s);
 // full-domain list: every tile, ascending, with info bytes; *count = ntiles
 cudaError_t launch_full_list(int* list, uint8_t* list_info, const uint8_t* tile_sgn,
                              unsigned const_sgn, const Inst& single, long long ntiles, int* count,
