@@ -69,6 +69,10 @@ def parse():
                         "learned: corrector training + learned-coarse vs plain at equal error; "
                         "local: the 512^3 run with the paper's local scheme (cut-off advance, "
                         "reinitialisation on N, clamp)")
+    p.add_argument("--output-every", type=int, default=0,
+                   help="sphere-union / local: write phi every N steps during the timed runs with the "
+                        "library's overlapped output (host writer thread) into a temporary directory")
+    p.add_argument("--output-format", choices=["vts", "vti"], default="vts")
     p.add_argument("--reinit-iters", type=int, default=-1,
                    help="local workload: reinitialisation iterations per step (-1: ceil(halfwidth/dtau))")
     p.add_argument("--pairs", type=int, default=2000)
@@ -643,6 +647,12 @@ def main():
     sampler = ClockSampler(uuid)
     time.sleep(0.3)
 
+    out_dir = None
+    if args.output_every > 0:
+        import tempfile
+        out_dir = tempfile.mkdtemp(prefix="ls_out_")
+        g.output_open(os.path.join(out_dir, "phi_"), args.output_every,
+                      ls.LS_OUTPUT_VTS if args.output_format == "vts" else ls.LS_OUTPUT_VTI, slots=2)
     u0 = g.updates()
     g.reset_profile()
     r0 = g.profile()["reinit_updates"]
@@ -664,6 +674,16 @@ def main():
     g.profile_enable(False)
     prof = g.profile()
     updates = g.updates() - u0
+    output = None
+    if out_dir is not None:
+        import shutil
+        rep_ = g.output_stats()
+        fin = g.output_close()
+        shutil.rmtree(out_dir, ignore_errors=True)
+        output = {"every": args.output_every, "format": args.output_format,
+                  "files_in_timed_region": rep_["files"], "files": fin["files"], "bytes": fin["bytes"],
+                  "writer_seconds": fin["write_seconds"], "step_wait_seconds": fin["wait_seconds"],
+                  "status": fin["status"]}
 
     t_s, total_updates = aggregate(pg, ms / 1e3, float(updates), dev)
     value = total_updates / t_s / 1e9
@@ -760,6 +780,8 @@ def main():
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": prof["kernel_launches"], "band_points_final": band_points,
         }
+        if output is not None:
+            line["output"] = output
         if local_scheme:
             line["metric"] = METRIC_LOCAL
             line["config"]["local_scheme"] = {"beta_h": beta_h, "reinit_iters": iters, "dtau_h": dtau_h}

@@ -56,7 +56,8 @@ typedef enum {
     LS_ECUDA = -3,      /* a CUDA call failed (see ls_last_cuda_error)     */
     LS_ETIMEOUT = -4,   /* a bounded device wait ran out                   */
     LS_ENONFINITE = -5, /* NaN or Inf in phi or F                          */
-    LS_ESTATE = -6      /* call not valid in the context's current state   */
+    LS_ESTATE = -6,     /* call not valid in the context's current state   */
+    LS_EIO = -7         /* an output file could not be written              */
 } ls_status;
 
 enum { LS_FP32 = 0, LS_FP64 = 1 };               /* storage + arithmetic precision */
@@ -327,6 +328,49 @@ int ls_inst_init_speed(ls_ctx *ctx, int i, int kind, const double *params, int n
 
 /* dt of instance i's last step (synchronises the stream). */
 int ls_inst_last_dt(ls_ctx *ctx, int i, double *dt);
+
+/* ---------------------------------------------------------------------
+ * Overlapped output (section 2: results are written while the computation
+ * goes on, by a worker that does nothing else)
+ *
+ * With an output attached, every `every`-th step of ls_step (counted over
+ * the context's lifetime) copies phi into a free device snapshot slot on the
+ * context's stream; a copy stream moves it to pinned host memory and a host
+ * writer thread writes <prefix><step, 8 digits>.vts (VTK XML StructuredGrid
+ * with the point coordinates (i + 1/2) h, as the paper's files) or .vti
+ * (ImageData, origin h/2, spacing h), raw appended little-endian data in the
+ * context's precision, point data "phi", x fastest.  When all `slots`
+ * snapshots are still being written, ls_step waits for one (counted in
+ * wait_seconds).  Steps with an output attached run eagerly (no graph
+ * replay).  Single-instance contexts only.
+ * ------------------------------------------------------------------- */
+enum { LS_OUTPUT_VTS = 0, LS_OUTPUT_VTI = 1 };
+
+typedef struct {
+    unsigned long long files;   /* files written                                  */
+    unsigned long long bytes;   /* bytes written                                  */
+    double write_seconds;       /* writer thread time (waiting for the copy, writing) */
+    double wait_seconds;        /* time ls_step waited for a free snapshot slot   */
+    int status;                 /* first error (LS_EIO, LS_ECUDA) or LS_OK        */
+} ls_output_report;
+
+/* Attach the output (1 <= slots <= 8 snapshot buffers of the grid's size on
+ * the device and in pinned host memory).  Errors: LS_EINVAL (bad argument or
+ * batched context), LS_ESTATE (an output is attached already), LS_ENOMEM. */
+int ls_output_open(ls_ctx *ctx, const char *prefix, int every, int format, int slots);
+
+/* Counters so far (the writer may still be busy). */
+int ls_output_stats(ls_ctx *ctx, ls_output_report *report);
+
+/* Wait for every queued snapshot to be written, detach the output and
+ * release its buffers; report (nullable) gets the final counters.  Returns
+ * the first write error (LS_EIO) or LS_OK. */
+int ls_output_close(ls_ctx *ctx, ls_output_report *report);
+
+/* Write one row-major host array (context-free; the same file layout as the
+ * output above).  Errors: LS_EINVAL, LS_EIO. */
+int ls_write_vtk(const char *path, const void *phi, int nx, int ny, int nz, double h,
+                 int precision, int format);
 
 /* ---------------------------------------------------------------------
  * Learned coarse-grid corrector (no counterpart in the paper)

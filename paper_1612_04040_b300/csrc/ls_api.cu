@@ -145,6 +145,8 @@ void free_all(ls_ctx* c)
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     if (c->learned) lsk::learned_free(c->learned);
     c->learned = nullptr;
+    if (c->output) lsk::output_free(c->output);
+    c->output = nullptr;
 }
 
 size_t grid_bytes(const ls_ctx* c) { return c->npts * c->esize; }
@@ -427,6 +429,11 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
         }
         c->since_rebuild += 1;
         c->core_fresh = classify;
+        c->step_count += 1;
+        if (c->output && c->step_count % c->output_every == 0) {
+            if (c->profiling) RET(prof_close(c, s));
+            RET(ls_engine_output_after_step(c, s));
+        }
     }
     if (c->profiling) RET(prof_close(c, s));
     return LS_OK;
@@ -702,6 +709,7 @@ const char* ls_strerror(int st)
     case LS_ETIMEOUT: return "bounded device wait timed out";
     case LS_ENONFINITE: return "non-finite value in input";
     case LS_ESTATE: return "call not valid in the current state";
+    case LS_EIO: return "output file could not be written";
     default: return "unknown status";
     }
 }
@@ -832,7 +840,8 @@ int ls_step(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every,
     c->dt_mode = dt_mode;
     c->dt_value = value;
     if (nsteps > 0) {
-        if (c->use_graphs && !c->profiling) RET(run_steps_graph(c, nsteps, value, dt_mode, rebuild_every));
+        if (c->use_graphs && !c->profiling && !c->output)
+            RET(run_steps_graph(c, nsteps, value, dt_mode, rebuild_every));
         else RET(run_steps(c, nsteps, value, dt_mode, rebuild_every, c->stream));
     }
     if (last_dt) {

@@ -15,6 +15,8 @@ using lsk::Inst;
 namespace lsk {
 struct Learned;  // corrector state (ls_learned_api.cu)
 void learned_free(Learned* L);
+struct Output;   // overlapped output (ls_output.cu)
+void output_free(Output* O);
 }  // namespace lsk
 
 namespace lsk {
@@ -120,6 +122,11 @@ struct ls_ctx {
     unsigned long long* d_rupdates = nullptr;  // reinitialisation point-iterations
     unsigned long long* d_breaches = nullptr;
 
+    // overlapped output
+    lsk::Output* output = nullptr;
+    int output_every = 0;
+    long long step_count = 0;     // steps taken over the context's lifetime
+
     // learned corrector
     int step_mode = LS_PLAIN;
     lsk::Learned* learned = nullptr;
@@ -134,3 +141,4 @@ struct ls_ctx {
 int ls_engine_cuda_fail(cudaError_t e);
 int ls_engine_pack(ls_ctx* c, const Inst& in, const void* src, int on_device, void* dst);
 int ls_engine_learned_after_step(ls_ctx* c, cudaStream_t s);
+int ls_engine_output_after_step(ls_ctx* c, cudaStream_t s);

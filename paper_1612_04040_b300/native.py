@@ -23,11 +23,12 @@ except ImportError:  # pragma: no cover - torch is part of the image
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libls.so")
 
-LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ETIMEOUT, LS_ENONFINITE, LS_ESTATE = 0, -1, -2, -3, -4, -5, -6
+LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ETIMEOUT, LS_ENONFINITE, LS_ESTATE, LS_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 LS_FP32, LS_FP64 = 0, 1
 LS_DT_FIXED, LS_DT_CFL = 0, 1
 LS_PLAIN, LS_LEARNED = 0, 1
 LS_SCHEME_PLAIN, LS_SCHEME_LOCAL = 0, 1
+LS_OUTPUT_VTS, LS_OUTPUT_VTI = 0, 1
 LS_BC_EXTRAPOLATE, LS_BC_NEUMANN = 0, 1
 LS_SHAPE_SPHERES, LS_SHAPE_TORUS, LS_SHAPE_SH = 0, 1, 2
 LS_SPEED_SINUSOID, LS_SPEED_COSCOS, LS_SPEED_FOURIER = 0, 1, 2
@@ -83,6 +84,10 @@ SIGNATURES = {
     "ls_learned_get_pair": (_i, [_vp, _c.c_longlong, _vp, _vp, _vp, _i]),
     "ls_set_step_mode": (_i, [_vp, _i]),
     "ls_set_scheme": (_i, [_vp, _i, _c.c_double, _i, _c.c_double]),
+    "ls_output_open": (_i, [_vp, _c.c_char_p, _i, _i, _i]),
+    "ls_output_stats": (_i, [_vp, _vp]),
+    "ls_output_close": (_i, [_vp, _vp]),
+    "ls_write_vtk": (_i, [_c.c_char_p, _vp, _i, _i, _i, _c.c_double, _i, _i]),
     "ls_band_breaches": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
     "ls_learned_fallbacks": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
     "ls_conv3_bf16": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -104,6 +109,13 @@ class Profile(ctypes.Structure):
                 ("stencil_ms", ctypes.c_double), ("stencil_timed", ctypes.c_ulonglong),
                 ("reinit_ms", ctypes.c_double), ("reinit_timed", ctypes.c_ulonglong),
                 ("reinit_updates", ctypes.c_ulonglong)]
+
+
+class OutputReport(ctypes.Structure):
+    """ls_output_report of include/ls.h."""
+    _fields_ = [("files", ctypes.c_ulonglong), ("bytes", ctypes.c_ulonglong),
+                ("write_seconds", ctypes.c_double), ("wait_seconds", ctypes.c_double),
+                ("status", ctypes.c_int)]
 
 
 class LSError(RuntimeError):
@@ -248,6 +260,18 @@ def restrict4(fine, stream=None):
         stream = torch.cuda.current_stream().cuda_stream
     check(lib.ls_restrict4(_dptr(fine), nx, ny, nz, _dptr(out), ctypes.c_void_p(stream)), "ls_restrict4")
     return out
+
+
+def write_vtk(path, phi, h, fmt=LS_OUTPUT_VTS):
+    """ls_write_vtk of a row-major host array (nz, ny, nx), float32 or float64."""
+    lib = load()
+    a = np.ascontiguousarray(phi)
+    if a.dtype not in (np.float32, np.float64) or a.ndim != 3:
+        raise ValueError("phi: 3-D float32 / float64 array")
+    nz, ny, nx = a.shape
+    prec = LS_FP32 if a.dtype == np.float32 else LS_FP64
+    check(lib.ls_write_vtk(str(path).encode(), a.ctypes.data, nx, ny, nz, float(h), prec, int(fmt)),
+          "ls_write_vtk")
 
 
 class LevelSet:
@@ -433,6 +457,20 @@ class LevelSet:
 
     def set_step_mode(self, mode):
         check(self.lib.ls_set_step_mode(self.ctx, int(mode)), "ls_set_step_mode")
+
+    def output_open(self, prefix, every, fmt=LS_OUTPUT_VTS, slots=2):
+        check(self.lib.ls_output_open(self.ctx, str(prefix).encode(), int(every), int(fmt), int(slots)),
+              "ls_output_open")
+
+    def output_stats(self):
+        r = OutputReport()
+        check(self.lib.ls_output_stats(self.ctx, ctypes.byref(r)), "ls_output_stats")
+        return {k: getattr(r, k) for k, _ in OutputReport._fields_}
+
+    def output_close(self):
+        r = OutputReport()
+        check(self.lib.ls_output_close(self.ctx, ctypes.byref(r)), "ls_output_close")
+        return {k: getattr(r, k) for k, _ in OutputReport._fields_}
 
     def set_scheme(self, scheme, beta_in_h=0.0, reinit_iters=-1, dtau_in_h=0.5):
         check(self.lib.ls_set_scheme(self.ctx, int(scheme), float(beta_in_h), int(reinit_iters),
