@@ -410,8 +410,10 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
                 }
             }
             RET(prof_before_stencil(c, p > 0 ? 1 : 0, s));
+            a.reverse = c->dir;
             KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
             ++c->stencil_launches;
+            c->dir ^= 1;
             if (c->step_mode == LS_LEARNED) {
                 if (c->profiling) RET(prof_close(c, s));
                 RET(ls_engine_learned_after_step(c, s));
@@ -446,6 +448,7 @@ SchedState save_state(const ls_ctx* c)
     st.since_rebuild = c->since_rebuild;
     st.band_valid = c->band_valid;
     st.core_fresh = c->core_fresh;
+    st.dir = c->dir;
     return st;
 }
 
@@ -455,6 +458,7 @@ void load_state(ls_ctx* c, const SchedState& st)
     c->since_rebuild = st.since_rebuild;
     c->band_valid = st.band_valid;
     c->core_fresh = st.core_fresh;
+    c->dir = st.dir;
 }
 
 cudaStream_t work_stream(ls_ctx* c)
@@ -477,7 +481,7 @@ int run_steps_graph(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuil
     const GraphKey key{c->cur, c->since_rebuild, (int)c->band_valid, (int)c->core_fresh,
                        (int)c->full_domain | (c->step_mode << 1) | (c->scheme << 3), nsteps,
                        rebuild_every, dt_mode, vbits,
-                       c->cfg.stages * 16 + c->cfg.ppt, c->cfg.grid_pct};
+                       c->cfg.stages * 16 + c->cfg.ppt, c->cfg.grid_pct, c->dir};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         if (c->graphs.size() >= 16) clear_graphs(c);

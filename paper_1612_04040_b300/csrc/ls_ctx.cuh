@@ -27,9 +27,10 @@ struct SchedState {
     int since_rebuild = 0;
     bool band_valid = false;
     bool core_fresh = false;
+    int dir = 0;
 };
 
-using GraphKey = std::tuple<int, int, int, int, int, int, int, int, long long, int, int>;
+using GraphKey = std::tuple<int, int, int, int, int, int, int, int, long long, int, int, int>;
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -85,6 +86,7 @@ struct ls_ctx {
     bool have_halfwidth = false;
     double halfwidth = 0.0;
     int since_rebuild = 0;
+    int dir = 0;                  // traversal direction of the next stencil launch
     int dt_mode = LS_DT_FIXED;
     double dt_value = 0.0;
     lsk::StepConfig cfg;

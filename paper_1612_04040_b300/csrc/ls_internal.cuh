@@ -160,6 +160,7 @@ struct StepArgs {
     unsigned long long* updates;
     Inst in;                  // single instance parameters (bc is read from here always)
     int max_grid;             // cap on the persistent grid (0 = none)
+    int reverse;              // FP32: walk the list from its end (L2 reuse across launches)
     // local scheme (single instance, 4 points per thread)
     int op;                   // OP_*
     LocalParams lp;

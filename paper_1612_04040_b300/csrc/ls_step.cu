@@ -328,6 +328,11 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
     pdl_launch_dependents();
     pdl_wait();
     const int n = *a.count;
+    // list position of the k-th entry processed: every other launch walks the
+    // list backwards, so it starts on the tiles the previous launch wrote
+    // last, which are still in L2
+    const bool rev = a.reverse != 0;
+    auto ent = [&](int k) { return rev ? n - 1 - k : k; };
     if (blockIdx.x == 0 && tid == 0 && a.updates)
         atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
     const float* __restrict__ src = (const float*)a.src;
@@ -401,11 +406,12 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         cp_async16s(a_y + so, tp + y_off, (info & y_bit) != 0);
         cp_async16s(a_z + so, tp + z_off, (info & z_bit) != 0);
         if (OP >= OP_REINIT && tid < 4)
-            cp_async16s(a_m + 64u * (unsigned)s, a.nmask + (size_t)kk * 16 + 4 * tid);
+            cp_async16s(a_m + 64u * (unsigned)s, a.nmask + (size_t)ent(kk) * 16 + 4 * tid);
     };
     // inst: the entry's instance (batched); for the local scheme's advance
     // (single instance) the entry's active face-neighbour bits instead
     auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
+        k = ent(k);
         t = (unsigned)__ldg(list + k);
         info = __ldg(linfo + k);
         if (BATCHED) inst = (unsigned)__ldg(linst + k);
@@ -516,7 +522,7 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
                     w |= __shfl_xor_sync(0xffffffffu, w, 1);
                     w |= __shfl_xor_sync(0xffffffffu, w, 2);
                     w |= __shfl_xor_sync(0xffffffffu, w, 4);
-                    if ((tid & 7) == 0) a.nmask[(size_t)k * 16 + (tid >> 3)] = w;
+                    if ((tid & 7) == 0) a.nmask[(size_t)ent(k) * 16 + (tid >> 3)] = w;
                     if (__any_sync(0xffffffffu, nb != 0u) && (tid & 31) == 0) nfl[cur] = 1u;
                 } else {
                     const float gn = a.lp.gamma_up;
@@ -548,7 +554,7 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         }
         prev = cur;
         prev_t = t;
-        prev_k = k;
+        prev_k = ent(k);
         prev_inst = inst;
         cur = cur + 1 == S ? 0 : cur + 1;
     }
@@ -582,6 +588,11 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
     pdl_launch_dependents();
     pdl_wait();
     const int n = *a.count;
+    // list position of the k-th entry processed: every other launch walks the
+    // list backwards, so it starts on the tiles the previous launch wrote
+    // last, which are still in L2
+    const bool rev = a.reverse != 0;
+    auto ent = [&](int k) { return rev ? n - 1 - k : k; };
     if (blockIdx.x == 0 && tid == 0 && a.updates)
         atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
     const float* __restrict__ src = (const float*)a.src;
@@ -656,6 +667,7 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
         cp_async16s(a_z + so, tp + z_off, (info & z_bit) != 0);
     };
     auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
+        k = ent(k);
         t = (unsigned)__ldg(list + k);
         info = __ldg(linfo + k);
         inst = BATCHED ? (unsigned)__ldg(linst + k) : 0u;
