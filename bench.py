@@ -47,6 +47,10 @@ sys.path.insert(0, ROOT)
 METRIC = "narrow-band upwind GLUPS"
 UNIT = "GLUPS"
 BYTES_PER_UPDATE = 12  # FP32: read phi (4) + read F (4) + write phi (4)
+# FP64 operations of one update of Eq. 3-5 as defined (one upwind branch):
+# 6 differences and 6 divisions by h, 6 squares + 3 per-axis sums + 2 sums
+# + 1 square root (Eq. 4 or 5), F * G, dt * (.), phi - (.)
+FLOPS_PER_UPDATE_F64 = 27
 WORKLOAD = "sphere-union 512^3 FP32, band 6h on 8^3 tiles, rebuild/5, 500 steps CFL 0.5"
 WORKLOAD_LOCAL = ("sphere-union 512^3 FP32, local scheme (cut-off advance beta 3h, gamma 6h; %d "
                   "reinitialisation iterations dtau h/2; clamp), 8^3 tiles, rebuild/5, 500 steps CFL 0.5")
@@ -73,6 +77,8 @@ def parse():
                    help="sphere-union / local: write phi every N steps during the timed runs with the "
                         "library's overlapped output (host writer thread) into a temporary directory")
     p.add_argument("--output-format", choices=["vts", "vti"], default="vts")
+    p.add_argument("--perturbed-n", type=int, default=1024,
+                   help="perturbed workload: grid edge (1024 = the standard workload)")
     p.add_argument("--reinit-iters", type=int, default=-1,
                    help="local workload: reinitialisation iterations per step (-1: ceil(halfwidth/dtau))")
     p.add_argument("--pairs", type=int, default=2000)
@@ -507,10 +513,11 @@ def run_perturbed(args):
     from paper_1612_04040_b300 import native as ls
     torch.cuda.set_device(0)
     dev = torch.device("cuda")
-    w = inputs.PerturbedSphere()
+    w = inputs.PerturbedSphere(n=args.perturbed_n)
     phi64 = w.phi(device=dev).contiguous()
     F64 = w.speed(device=dev).contiguous()
     nsteps = max(args.steps, 1) * 10
+    dfma = ls.probe_dfma()
     for prec, name, bpu in ((ls.LS_FP32, "f32", 12), (ls.LS_FP64, "f64", 24)):
         dt_t = torch.float32 if prec == ls.LS_FP32 else torch.float64
         for full in (False, True):
@@ -535,13 +542,20 @@ def run_perturbed(args):
             prof = g.profile()
             u = g.updates() - u0
             st = prof["stencil_ms"] / 1e3
-            print(json.dumps({
-                "metric": "upwind GLUPS", "workload": "perturbed sphere 1024^3 %s %s" % (
-                    name, "full domain" if full else "band 6h"),
+            line = {
+                "metric": "upwind GLUPS", "workload": "perturbed sphere %d^3 %s %s" % (
+                    w.n, name, "full domain" if full else "band 6h"),
                 "value": u / (ms / 1e3) / 1e9, "unit": "GLUPS", "dtype": name, "steps": nsteps,
                 "ms_per_level_set_step": ms / nsteps, "updates_per_step": u / nsteps,
                 "stencil_GBps_algorithmic": u * bpu / 1e9 / st if st > 0 else None,
-                "stencil_share": st / (ms / 1e3)}), flush=True)
+                "stencil_share": st / (ms / 1e3)}
+            if prec == ls.LS_FP64 and st > 0:
+                ach = u * FLOPS_PER_UPDATE_F64 / st / 1e12
+                line["roofline"] = {"bound": "fp64", "achieved": ach, "peak": dfma, "unit": "TFLOP/s",
+                                    "frac": ach / dfma if dfma else None,
+                                    "peak_kind": "measured (DFMA probe, this run; FMA = 2)",
+                                    "flops_per_update": FLOPS_PER_UPDATE_F64}
+            print(json.dumps(line), flush=True)
             g.close()
 
 
@@ -573,9 +587,15 @@ def run_sphere64(args):
         torch.cuda.synchronize()
         t_ms += e0.elapsed_time(e1)
     u = g.updates() - u0
+    dfma = ls.probe_dfma()
+    ach = u * FLOPS_PER_UPDATE_F64 / (t_ms / 1e3) / 1e12
     print(json.dumps({"metric": "upwind GLUPS", "workload": "single sphere 64^3 FP64, 100 full-domain steps",
                       "value": u / (t_ms / 1e3) / 1e9, "unit": "GLUPS", "dtype": "f64",
                       "ms_per_run": t_ms / reps, "graphs": True,
+                      "roofline": {"bound": "fp64", "achieved": ach, "peak": dfma, "unit": "TFLOP/s",
+                                   "frac": ach / dfma if dfma else None,
+                                   "peak_kind": "measured (DFMA probe, this run; FMA = 2)",
+                                   "flops_per_update": FLOPS_PER_UPDATE_F64, "time": "whole run"},
                       "note": "whole state (4 MiB) sits in L2: launch/latency-bound, no HBM claim"}),
           flush=True)
 

@@ -282,6 +282,12 @@ int ls_get_status(ls_ctx *ctx);
  * the device stay usable.  For failure-detection tests. */
 int ls_selftest_bounded_wait(unsigned *status, long long polls, void *cuda_stream);
 
+/* Measured FP64 peak of the current device in TFLOP/s (a fused multiply-add
+ * counted as 2): independent FMA chains on every SM for `iters` iterations,
+ * timed with CUDA events on `cuda_stream` (NULL: the default stream).  The
+ * FP64 stencil's roofline is taken against it. */
+int ls_probe_dfma(long long iters, double *tflops, void *cuda_stream);
+
 /* Static message for a status code. */
 const char *ls_strerror(int status);
 

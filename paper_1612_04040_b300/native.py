@@ -88,6 +88,7 @@ SIGNATURES = {
     "ls_output_stats": (_i, [_vp, _vp]),
     "ls_output_close": (_i, [_vp, _vp]),
     "ls_write_vtk": (_i, [_c.c_char_p, _vp, _i, _i, _i, _c.c_double, _i, _i]),
+    "ls_probe_dfma": (_i, [_ll, _c.POINTER(_d), _vp]),
     "ls_band_breaches": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
     "ls_learned_fallbacks": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
     "ls_conv3_bf16": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
@@ -260,6 +261,15 @@ def restrict4(fine, stream=None):
         stream = torch.cuda.current_stream().cuda_stream
     check(lib.ls_restrict4(_dptr(fine), nx, ny, nz, _dptr(out), ctypes.c_void_p(stream)), "ls_restrict4")
     return out
+
+
+def probe_dfma(iters=1 << 16, stream=None):
+    """Measured FP64 peak of the current device (TFLOP/s, FMA = 2)."""
+    lib = load()
+    t = ctypes.c_double(0.0)
+    check(lib.ls_probe_dfma(int(iters), ctypes.byref(t), None if stream is None else ctypes.c_void_p(stream)),
+          "ls_probe_dfma")
+    return t.value
 
 
 def write_vtk(path, phi, h, fmt=LS_OUTPUT_VTS):

@@ -91,3 +91,10 @@ def test_bounded_wait_times_out_and_device_stays_usable():
     g.band_rebuild(3.0)
     g.step(3, 0.5, ls.LS_DT_CFL, 2)
     assert g.status() == ls.LS_OK
+
+
+def test_dfma_probe_reports_a_plausible_fp64_peak():
+    """The FP64 roofline's denominator: a positive, finite rate of the right
+    order for a data-centre GPU (0.05 .. 200 TFLOP/s)."""
+    t = ls.probe_dfma(iters=1 << 12)
+    assert 0.05 < t < 200.0, t
