@@ -192,6 +192,11 @@ int ls_set_scheme(ls_ctx *ctx, int scheme, double beta_in_h, int reinit_iters, d
  * pointwise algorithm.  Synchronises the stream. */
 int ls_band_breaches(ls_ctx *ctx, unsigned long long *n);
 
+/* Band dilation of the rebuild: the core tiles plus their 26 (default) or
+ * only 6 face neighbours (a smaller band: fronts that move diagonally reach
+ * its edge sooner).  Marks the band stale.  Errors: LS_EINVAL. */
+int ls_set_dilation(ls_ctx *ctx, int neighbours);
+
 /* Full-domain mode on/off: every tile is active and no rebuild happens
  * (the O(n^3) variant the narrow band of section 1.1 replaces). */
 int ls_set_full_domain(ls_ctx *ctx, int on);

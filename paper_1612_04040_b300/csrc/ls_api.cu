@@ -31,6 +31,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ls_ctx.cuh"
 
 using lsk::GraphEntry;
@@ -227,14 +229,22 @@ int finish_rebuild(ls_ctx* c, cudaStream_t s)
     return LS_OK;
 }
 
+// an NVTX range around a host-side phase (visible to nsys / ncu timelines;
+// a no-op without a tool attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 int rebuild(ls_ctx* c, bool full_scan, cudaStream_t s)
 {
+    NvtxRange range("ls band rebuild");
     void* cur = c->phi[c->cur];
     if (full_scan || !c->core_fresh)
         KL(c, lsk::launch_classify_all(cur, c->core, c->dinst(), c->tinst(), c->in0(), c->ntiles,
                                        c->prec, s));
     KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, c->dinst(), c->tinst(), c->in0(),
-                             c->ntiles, c->d_done, c->d_count, s));
+                             c->ntiles, c->d_done, c->d_count, c->dilation, s));
     RET(finish_rebuild(c, s));
     c->band_valid = true;
     c->core_fresh = false;
@@ -249,7 +259,7 @@ int full_domain_bound(ls_ctx* c, cudaStream_t s)
         // and the regular scatter builds the full list, counts and bounds
         CK(cudaMemsetAsync(c->core, 1, c->ntiles, s));
         KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, c->d_inst, c->d_tile_inst,
-                                 c->in0(), c->ntiles, c->d_done, c->d_count, s));
+                                 c->in0(), c->ntiles, c->d_done, c->d_count, 26, s));
         RET(finish_rebuild(c, s));
     } else {
         // every tile counts as active, so a later switch back to a band copies
@@ -843,6 +853,7 @@ int ls_step(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every,
         return LS_ESTATE;
     c->dt_mode = dt_mode;
     c->dt_value = value;
+    NvtxRange range("ls_step");
     if (nsteps > 0) {
         if (c->use_graphs && !c->profiling && !c->output)
             RET(run_steps_graph(c, nsteps, value, dt_mode, rebuild_every));
@@ -1157,6 +1168,14 @@ int ls_set_scheme(ls_ctx* c, int scheme, double beta_in_h, int reinit_iters, dou
     c->reinit_iters = reinit_iters;
     c->dtau_in_h = dtau_in_h;
     clear_graphs(c);
+    return LS_OK;
+}
+
+int ls_set_dilation(ls_ctx* c, int neighbours)
+{
+    if (!c || (neighbours != 6 && neighbours != 26)) return LS_EINVAL;
+    c->dilation = neighbours;
+    state_changed(c);
     return LS_OK;
 }
 

@@ -268,7 +268,8 @@ __device__ void block_scan256(int* counts, int n, int* total)
 __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core, uint8_t* act,
                                                 int* block_counts, const Inst* d_inst,
                                                 const uint16_t* tile_inst, Inst single,
-                                                long long ntiles, unsigned* done, int* total)
+                                                long long ntiles, unsigned* done, int* total,
+                                                int conn)
 {
     const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
     int on = 0;
@@ -289,6 +290,7 @@ __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int x = tx + dx;
                     if (x < 0 || x >= in.tnx) continue;
+                    if (conn == 6 && abs(dx) + abs(dy) + abs(dz) > 1) continue;
                     if (core[row + x]) { on = 1; break; }
                 }
             }
@@ -718,11 +720,11 @@ cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_in
 
 cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
                           const Inst* d_inst, const uint16_t* tile_inst, const Inst& single,
-                          long long ntiles, unsigned* done, int* count, cudaStream_t s)
+                          long long ntiles, unsigned* done, int* count, int conn, cudaStream_t s)
 {
     const int nb = (int)((ntiles + 255) / 256);
     k_dilate<<<nb, 256, 0, s>>>(core, act, block_counts, d_inst, tile_inst, single, ntiles, done,
-                                count);
+                                count, conn);
     return cudaGetLastError();
 }
 

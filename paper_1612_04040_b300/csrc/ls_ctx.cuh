@@ -87,6 +87,7 @@ struct ls_ctx {
     double halfwidth = 0.0;
     int since_rebuild = 0;
     int dir = 0;                  // traversal direction of the next stencil launch
+    int dilation = 26;            // band dilation: 26 or 6 face neighbours
     int dt_mode = LS_DT_FIXED;
     double dt_value = 0.0;
     lsk::StepConfig cfg;

@@ -76,12 +76,14 @@ cudaError_t launch_tile_speed(const void* F, void* tile_maxF, uint8_t* tile_sgn,
 cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_inst,
                                 const uint16_t* tile_inst, const Inst& single, long long ntiles,
                                 int prec, cudaStream_t s);
-// band rebuild: dilation (act bit 0 = new flag, bit 1 = previous) + block
-// counts, turned into exclusive offsets and the active count *count by the
-// last block to finish (done: a zeroed device counter, reset by that block)
+// band rebuild: dilation by one tile over 26 or 6 neighbours (conn; act bit
+// 0 = new flag, bit 1 = previous) + block counts, turned into exclusive
+// offsets and the active count *count by the last block to finish (done: a
+// zeroed device counter, reset by that block)
 cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
                           const Inst* d_inst, const uint16_t* tile_inst, const Inst& single,
-                          long long ntiles, unsigned* done, int* count, cudaStream_t s);
+                          long long ntiles, unsigned* done, int* count, int conn,
+                          cudaStream_t s);
 // exclusive scan of block counts, writes total to *count
 cudaError_t launch_scan(int* block_counts, int nblocks, int* count, cudaStream_t s);
 // local scheme: the active-list entries whose tile holds a point of N

@@ -84,6 +84,7 @@ SIGNATURES = {
     "ls_learned_get_pair": (_i, [_vp, _c.c_longlong, _vp, _vp, _vp, _i]),
     "ls_set_step_mode": (_i, [_vp, _i]),
     "ls_set_scheme": (_i, [_vp, _i, _c.c_double, _i, _c.c_double]),
+    "ls_set_dilation": (_i, [_vp, _i]),
     "ls_output_open": (_i, [_vp, _c.c_char_p, _i, _i, _i]),
     "ls_output_stats": (_i, [_vp, _vp]),
     "ls_output_close": (_i, [_vp, _vp]),
@@ -485,6 +486,9 @@ class LevelSet:
     def set_scheme(self, scheme, beta_in_h=0.0, reinit_iters=-1, dtau_in_h=0.5):
         check(self.lib.ls_set_scheme(self.ctx, int(scheme), float(beta_in_h), int(reinit_iters),
                                      float(dtau_in_h)), "ls_set_scheme")
+
+    def set_dilation(self, neighbours):
+        check(self.lib.ls_set_dilation(self.ctx, int(neighbours)), "ls_set_dilation")
 
     def band_breaches(self):
         n = ctypes.c_ulonglong(0)

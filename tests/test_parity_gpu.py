@@ -98,6 +98,30 @@ def test_fp64_narrow_band_field_bitwise(device_inputs):
     assert np.array_equal(bits(g.get_phi()), bits(o.phi))
 
 
+def test_fp64_six_neighbour_dilation_bitwise():
+    """The band dilated over the 6 face neighbours only (ls_set_dilation):
+    the same trajectory and tile sets as the oracle's 6-neighbour dilation,
+    and a smaller band than the 26-neighbour one."""
+    shape = (64, 48, 80)
+    h = 1.0 / 64
+    w = inputs.SphereUnion(n=64, count=6)
+    phi0 = inputs.sphere_union_sdf(shape, h, w.centres, w.radii).numpy()
+    F = inputs.speed_sinusoid(shape, h).numpy()
+    g, _ = make_pair(shape, h, ls.LS_FP64, phi0, F=F)
+    o = oracle.Oracle(shape, h, conn=6)
+    o.set_phi(phi0)
+    o.set_speed(F)
+    g.set_dilation(6)
+    n6 = g.band_rebuild(6.0)
+    assert n6 == o.band_rebuild(6.0)
+    g26, _ = make_pair(shape, h, ls.LS_FP64, phi0, F=F)
+    assert n6 < g26.band_rebuild(6.0)
+    run_chunks(g, o, [5, 5, 3, 7], 0.5, ls.LS_DT_CFL, 5)
+    assert np.array_equal(bits(g.get_phi()), bits(o.phi))
+    with pytest.raises(ls.LSError):
+        g.set_dilation(8)
+
+
 def test_fp64_non_power_of_two_h_bitwise():
     """h = 1/48 (not a power of two: the kernel divides by h like the
     definition) with a sign-changing F."""
