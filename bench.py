@@ -77,6 +77,9 @@ def parse():
                    help="sphere-union / local: write phi every N steps during the timed runs with the "
                         "library's overlapped output (host writer thread) into a temporary directory")
     p.add_argument("--output-format", choices=["vts", "vti"], default="vts")
+    p.add_argument("--steps-per-pass", type=int, choices=[1, 2], default=None,
+                   help="sphere-union: force one or two upwind steps per stencil pass instead of "
+                        "the autotuner's choice")
     p.add_argument("--perturbed-n", type=int, default=1024,
                    help="perturbed workload: grid edge (1024 = the standard workload)")
     p.add_argument("--reinit-iters", type=int, default=-1,
@@ -653,6 +656,9 @@ def main():
     g.band_rebuild(w.halfwidth, want_count=False)
     g.step(w.steps // 2, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
     tuned = tune(g, args)
+    if args.steps_per_pass is not None:
+        g.set_steps_per_pass(args.steps_per_pass)
+    spp = g.steps_per_pass()
     for _ in range(max(args.warmup, 0)):
         run_once()
     torch.cuda.synchronize()
@@ -676,6 +682,7 @@ def main():
     u0 = g.updates()
     g.reset_profile()
     r0 = g.profile()["reinit_updates"]
+    tsp0 = g.profile()["two_step_points"]
     g.profile_enable(True)
     if pg:
         pg.barrier()
@@ -714,13 +721,18 @@ def main():
     if not local_scheme:
         stencil_s = prof["stencil_ms"] / 1e3
         n_launch = max(prof["stencil_timed"], 1)
-        achieved = (updates * BYTES_PER_UPDATE / 1e9) / stencil_s if stencil_s > 0 else None
-        tpu = recorded_traffic()
+        # a two-step pass reads phi and F and writes phi once for two updates
+        tsp = prof["two_step_points"] - tsp0
+        point_passes = updates - tsp
+        achieved = (point_passes * BYTES_PER_UPDATE / 1e9) / stencil_s if stencil_s > 0 else None
+        tpu = recorded_traffic() if tsp == 0 else None
         traffic = tpu * updates / n_launch if tpu is not None else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                    "peak_kind": peak_kind, "kernel": "k_step_f32 (upwind step over the active 8^3 tiles)",
-                    "bytes_per_update": BYTES_PER_UPDATE,
+                    "peak_kind": peak_kind,
+                    "kernel": "k_step_f32 (upwind step over the active 8^3 tiles)" if tsp == 0 else
+                              "k_step2_f32 / k_step_f32 (two / one upwind steps per pass)",
+                    "bytes_per_update": BYTES_PER_UPDATE * point_passes / max(updates, 1),
                     "avg_launch_us": 1e6 * stencil_s / n_launch, "launches": prof["stencil_timed"],
                     "share_of_step_time": stencil_s / t_s if t_s > 0 else None}
     else:
@@ -792,7 +804,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
             "config": {"workload": WORKLOAD if not local_scheme else WORKLOAD_LOCAL % iters,
                        "grid": w.n, "halfwidth_h": w.halfwidth,
-                       "autotuned": {"stages": tuned[0], "grid_pct": tuned[1], "points_per_thread": tuned[2]},
+                       "autotuned": {"stages": tuned[0], "grid_pct": tuned[1], "points_per_thread": tuned[2],
+                                     "steps_per_pass": spp},
                        "rebuild_every": w.rebuild_every, "level_set_steps_per_bench_step": w.steps,
                        "cfl": w.cfl, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (phi + F 1.5 GB; active set per step ~0.2 GB)"},

@@ -244,6 +244,16 @@ int ls_set_graphs(ls_ctx *ctx, int on);
  * otherwise).  FP64 contexts have a single configuration and return it. */
 int ls_autotune(ls_ctx *ctx, int reps, int *stages, int *grid_pct, int *points_per_thread);
 
+/* Steps per stencil pass (FP32 single grids, plain scheme): 1, or 2 -- two
+ * upwind steps per pass over the active tiles (temporal blocking: the
+ * intermediate step is also computed on the one-cell face layers around
+ * each tile, so a pass reads phi and F and writes phi once for two steps);
+ * a pair of steps is taken whenever both fall inside one rebuild period,
+ * the other steps run one per pass.  The results are the same bits either
+ * way.  ls_autotune includes this choice.  Errors: LS_EINVAL. */
+int ls_set_steps_per_pass(ls_ctx *ctx, int steps);
+int ls_get_steps_per_pass(ls_ctx *ctx, int *steps);
+
 /* Set the FP32 stencil launch configuration directly (stages 2, 3, 4 or 6, grid
  * 1..100 % of full occupancy, points per thread 4 or 8; default 3, 100, 8). */
 int ls_set_step_config(ls_ctx *ctx, int stages, int grid_pct, int points_per_thread);
@@ -262,6 +272,9 @@ typedef struct {
                                             passes since the local scheme was first
                                             set (they visit only tiles holding a
                                             point of N)                             */
+    unsigned long long two_step_points;  /* points passed by two-step passes (each
+                                            counted once, updated twice) since the
+                                            context was created                     */
 } ls_profile;
 
 /* Enable (1) or disable (0) CUDA-event timing of the upwind-step launches:

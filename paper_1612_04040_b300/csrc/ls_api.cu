@@ -141,7 +141,7 @@ void free_all(ls_ctx* c)
                     c->d_Mbits, c->d_updates, c->d_status, c->d_nonfinite, c->d_inst,
                     c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params, c->nmask,
                     c->d_breaches, c->list_nact, c->nmask2, c->nflag, c->nl, c->nl_info,
-                    c->d_ncount, c->d_rupdates, c->d_done};
+                    c->d_ncount, c->d_rupdates, c->d_done, c->d_updates2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -357,11 +357,17 @@ int prof_before_stencil(ls_ctx* c, int kind, cudaStream_t s)
     return LS_OK;
 }
 
+bool two_step_ok(const ls_ctx* c)
+{
+    return c->prec == LS_FP32 && !c->batched && c->scheme == LS_SCHEME_PLAIN &&
+           c->step_mode == LS_PLAIN && c->list_nact != nullptr;
+}
+
 // the step loop of ls_step (eager, or recorded into a graph by the caller)
 int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every, cudaStream_t s)
 {
     bool dt_pending = true;
-    for (int k = 0; k < nsteps; ++k) {
+    for (int k = 0; k < nsteps;) {
         bool rebuilt = false;
         if (c->profiling && (!c->band_valid || (rebuild_every > 0 && c->since_rebuild >= rebuild_every) ||
                              (dt_pending && k == 0)))
@@ -387,10 +393,38 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
                                          c->d_Mbits, nullptr, 0, s));
         }
         dt_pending = false;
+        // two steps per pass (temporal blocking) when configured and both
+        // steps fall inside one rebuild period (one dt) with no snapshot after
+        // the first of them
+        const bool two = c->cfg.spp == 2 && two_step_ok(c) && k + 1 < nsteps &&
+                         (rebuild_every == 0 || c->full_domain ||
+                          c->since_rebuild + 2 <= rebuild_every) &&
+                         !(c->output && (c->step_count + 1) % c->output_every == 0);
+        const int adv = two ? 2 : 1;
         // the fused tube test sees the plain step's values; with the learned
         // correction applied afterwards the rebuild classifies again instead
         const bool classify = !c->full_domain && rebuild_every > 0 &&
-                              c->since_rebuild + 1 >= rebuild_every && c->step_mode == LS_PLAIN;
+                              c->since_rebuild + adv >= rebuild_every && c->step_mode == LS_PLAIN;
+        if (two) {
+            lsk::StepArgs a = step_args(c, classify);
+            a.nact = c->list_nact;
+            a.updates2 = c->d_updates2;
+            RET(prof_before_stencil(c, 0, s));
+            a.reverse = c->dir;
+            KL(c, lsk::launch_step2(a, c->cfg, s));
+            c->stencil_launches += 1;
+            c->dir ^= 1;
+            c->cur ^= 1;
+            c->since_rebuild += 2;
+            c->core_fresh = classify;
+            c->step_count += 2;
+            k += 2;
+            if (c->output && c->step_count % c->output_every == 0) {
+                if (c->profiling) RET(prof_close(c, s));
+                RET(ls_engine_output_after_step(c, s));
+            }
+            continue;
+        }
         // plain: one pass; local scheme: the cut-off advance, then the
         // reinitialisation passes (the last one clamps); the fused tube test
         // goes with the last pass of the step
@@ -442,6 +476,7 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
         c->since_rebuild += 1;
         c->core_fresh = classify;
         c->step_count += 1;
+        k += 1;
         if (c->output && c->step_count % c->output_every == 0) {
             if (c->profiling) RET(prof_close(c, s));
             RET(ls_engine_output_after_step(c, s));
@@ -491,7 +526,7 @@ int run_steps_graph(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuil
     const GraphKey key{c->cur, c->since_rebuild, (int)c->band_valid, (int)c->core_fresh,
                        (int)c->full_domain | (c->step_mode << 1) | (c->scheme << 3), nsteps,
                        rebuild_every, dt_mode, vbits,
-                       c->cfg.stages * 16 + c->cfg.ppt, c->cfg.grid_pct, c->dir};
+                       c->cfg.stages * 16 + c->cfg.ppt + 256 * c->cfg.spp, c->cfg.grid_pct, c->dir};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         if (c->graphs.size() >= 16) clear_graphs(c);
@@ -581,6 +616,9 @@ int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h
     A(dalloc(&c->list_info, c->ntiles));
     A(dalloc(&c->d_count, sizeof(int)));
     A(dalloc(&c->d_done, 4 * sizeof(unsigned)));
+    A(dalloc(&c->d_updates2, sizeof(unsigned long long)));
+    if (e == cudaSuccess) e = cudaMemset(c->d_updates2, 0, sizeof(unsigned long long));
+    if (!batched && precision == LS_FP32) A(dalloc(&c->list_nact, c->ntiles));
     if (e == cudaSuccess) e = cudaMemset(c->d_done, 0, 4 * sizeof(unsigned));
     A(dalloc(&c->block_counts, c->nblocks * sizeof(int)));
     A(dalloc(&c->d_sc, sizeof(lsk::StepScalars) * n));
@@ -914,6 +952,29 @@ int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out, int* pp
                 }
             }
         }
+        // two steps per pass: the time of one pass counts for two steps
+        best_cfg.spp = 1;
+        if (two_step_ok(c)) {
+            lsk::StepArgs a2 = step_args(c, false);
+            a2.updates = nullptr;
+            a2.nact = c->list_nact;
+            for (int pct : pcts) {
+                lsk::StepConfig cfg = best_cfg;
+                cfg.spp = 2;
+                cfg.grid_pct2 = pct;
+                KL(c, lsk::launch_step2(a2, cfg, s));
+                CK(cudaEventRecord(e0, s));
+                for (int r = 0; r < reps; ++r) KL(c, lsk::launch_step2(a2, cfg, s));
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (0.5f * ms < best) {
+                    best = 0.5f * ms;
+                    best_cfg = cfg;
+                }
+            }
+        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         c->cfg = best_cfg;
@@ -922,6 +983,21 @@ int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out, int* pp
     if (stages_out) *stages_out = c->cfg.stages;
     if (grid_pct_out) *grid_pct_out = c->cfg.grid_pct;
     if (ppt_out) *ppt_out = c->cfg.ppt;
+    return LS_OK;
+}
+
+int ls_set_steps_per_pass(ls_ctx* c, int steps)
+{
+    if (!c || (steps != 1 && steps != 2)) return LS_EINVAL;
+    c->cfg.spp = steps;
+    clear_graphs(c);
+    return LS_OK;
+}
+
+int ls_get_steps_per_pass(ls_ctx* c, int* steps)
+{
+    if (!c || !steps) return LS_EINVAL;
+    *steps = c->cfg.spp;
     return LS_OK;
 }
 
@@ -1113,6 +1189,9 @@ int ls_get_profile(ls_ctx* c, ls_profile* out)
     out->reinit_ms = c->reinit_ms;
     out->reinit_timed = c->reinit_timed;
     out->reinit_updates = 0;
+    CK(cudaMemcpyAsync(&out->two_step_points, c->d_updates2, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     if (c->d_rupdates) {
         CK(cudaMemcpyAsync(&out->reinit_updates, c->d_rupdates, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, c->stream));

@@ -77,6 +77,7 @@ struct ls_ctx {
     lsk::StepScalars* d_sc = nullptr;
     unsigned long long* d_Mbits = nullptr;
     unsigned long long* d_updates = nullptr;
+    unsigned long long* d_updates2 = nullptr;  // points of two-step passes
     unsigned* d_status = nullptr;
     unsigned* d_nonfinite = nullptr;
     // host-side state

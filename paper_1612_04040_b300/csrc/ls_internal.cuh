@@ -160,6 +160,7 @@ struct StepArgs {
     const Inst* insts;        // per-instance parameters (batched), device
     uint8_t* core;            // fused tube test output, or NULL
     unsigned long long* updates;
+    unsigned long long* updates2;  // two-step passes: points passed (each updated twice)
     Inst in;                  // single instance parameters (bc is read from here always)
     int max_grid;             // cap on the persistent grid (0 = none)
     int reverse;              // FP32: walk the list from its end (L2 reuse across launches)
@@ -178,9 +179,14 @@ struct StepConfig {
     int stages = 3;           // cp.async ring depth (2, 3, 4)
     int grid_pct = 100;       // persistent grid, percent of full occupancy
     int ppt = 8;              // points per thread: 4 (128-thread CTAs) or 8 (64-thread CTAs)
+    int spp = 1;              // steps per pass: 1, or 2 (temporal blocking, ls_step2.cu)
+    int grid_pct2 = 100;      // persistent grid of the two-step passes
 };
 
 cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cudaStream_t s);
+// two steps per pass (FP32 single grid, plain scheme; a.nact required);
+// grid from cfg.grid_pct2
+cudaError_t launch_step2(const StepArgs& a, const StepConfig& cfg, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // batched rebuild helpers (ls_band.cu)

@@ -85,6 +85,8 @@ SIGNATURES = {
     "ls_set_step_mode": (_i, [_vp, _i]),
     "ls_set_scheme": (_i, [_vp, _i, _c.c_double, _i, _c.c_double]),
     "ls_set_dilation": (_i, [_vp, _i]),
+    "ls_set_steps_per_pass": (_i, [_vp, _i]),
+    "ls_get_steps_per_pass": (_i, [_vp, _c.POINTER(_i)]),
     "ls_output_open": (_i, [_vp, _c.c_char_p, _i, _i, _i]),
     "ls_output_stats": (_i, [_vp, _vp]),
     "ls_output_close": (_i, [_vp, _vp]),
@@ -110,7 +112,7 @@ class Profile(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("stencil_launches", ctypes.c_ulonglong),
                 ("stencil_ms", ctypes.c_double), ("stencil_timed", ctypes.c_ulonglong),
                 ("reinit_ms", ctypes.c_double), ("reinit_timed", ctypes.c_ulonglong),
-                ("reinit_updates", ctypes.c_ulonglong)]
+                ("reinit_updates", ctypes.c_ulonglong), ("two_step_points", ctypes.c_ulonglong)]
 
 
 class OutputReport(ctypes.Structure):
@@ -486,6 +488,14 @@ class LevelSet:
     def set_scheme(self, scheme, beta_in_h=0.0, reinit_iters=-1, dtau_in_h=0.5):
         check(self.lib.ls_set_scheme(self.ctx, int(scheme), float(beta_in_h), int(reinit_iters),
                                      float(dtau_in_h)), "ls_set_scheme")
+
+    def set_steps_per_pass(self, steps):
+        check(self.lib.ls_set_steps_per_pass(self.ctx, int(steps)), "ls_set_steps_per_pass")
+
+    def steps_per_pass(self):
+        k = ctypes.c_int(0)
+        check(self.lib.ls_get_steps_per_pass(self.ctx, ctypes.byref(k)), "ls_get_steps_per_pass")
+        return k.value
 
     def set_dilation(self, neighbours):
         check(self.lib.ls_set_dilation(self.ctx, int(neighbours)), "ls_set_dilation")
