@@ -142,8 +142,13 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_1612_04040_b300", "csrc", "ls_step.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the one-step stencil's source (the kernel file and the shared
+    per-point arithmetic it includes)."""
+    h = hashlib.sha256()
+    for name in ("ls_step.cu", "ls_stencil.cuh"):
+        with open(os.path.join(ROOT, "paper_1612_04040_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic():
@@ -158,7 +163,7 @@ def recorded_traffic():
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 d[k.strip()] = v.strip()
-    if d.get("ls_step_cu_sha256_16") != kernel_source_hash():
+    if d.get("stencil_source_sha256_16") != kernel_source_hash():
         return None
     return float(d["dram_bytes_per_update"])
 
