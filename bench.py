@@ -537,6 +537,7 @@ def run_perturbed(args):
             else:
                 g.band_rebuild(w.halfwidth)
             g.step(5, 0.5, ls.LS_DT_CFL, 5)
+            tuned = g.autotune(reps=3) if prec == ls.LS_FP32 else None
             torch.cuda.synchronize()
             u0 = g.updates()
             g.reset_profile()
@@ -557,6 +558,9 @@ def run_perturbed(args):
                 "ms_per_level_set_step": ms / nsteps, "updates_per_step": u / nsteps,
                 "stencil_GBps_algorithmic": u * bpu / 1e9 / st if st > 0 else None,
                 "stencil_share": st / (ms / 1e3)}
+            if tuned is not None:
+                line["autotuned"] = {"stages": tuned[0], "grid_pct": tuned[1], "points_per_thread": tuned[2],
+                                     "steps_per_pass": g.steps_per_pass()}
             if prec == ls.LS_FP64 and st > 0:
                 ach = u * FLOPS_PER_UPDATE_F64 / st / 1e12
                 line["roofline"] = {"bound": "fp64", "achieved": ach, "peak": dfma, "unit": "TFLOP/s",

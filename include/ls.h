@@ -197,6 +197,13 @@ int ls_band_breaches(ls_ctx *ctx, unsigned long long *n);
  * its edge sooner).  Marks the band stale.  Errors: LS_EINVAL. */
 int ls_set_dilation(ls_ctx *ctx, int neighbours);
 
+/* Full-domain mode, FP32 single grids, plain scheme: on, every step streams
+ * tile columns along z (each tile's z halos are the neighbouring tiles of
+ * its column, staged once); off (default): the active-list kernel over all
+ * tiles, which measured faster.  The results are the same bits.  Errors:
+ * LS_EINVAL. */
+int ls_set_dense_kernel(ls_ctx *ctx, int on);
+
 /* Full-domain mode on/off: every tile is active and no rebuild happens
  * (the O(n^3) variant the narrow band of section 1.1 replaces). */
 int ls_set_full_domain(ls_ctx *ctx, int on);
@@ -255,7 +262,7 @@ int ls_set_steps_per_pass(ls_ctx *ctx, int steps);
 int ls_get_steps_per_pass(ls_ctx *ctx, int *steps);
 
 /* Set the FP32 stencil launch configuration directly (stages 2, 3, 4 or 6, grid
- * 1..100 % of full occupancy, points per thread 4 or 8; default 3, 100, 8). */
+ * 1..100 % of full occupancy, points per thread 4 or 8; default 3, 100, 4). */
 int ls_set_step_config(ls_ctx *ctx, int stages, int grid_pct, int points_per_thread);
 
 /* Profiling counters of a context. */

@@ -455,7 +455,12 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
             }
             RET(prof_before_stencil(c, p > 0 ? 1 : 0, s));
             a.reverse = c->dir;
-            KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
+            if (!local && c->full_domain && c->cfg.dense && two_step_ok(c)) {
+                a.tile_sgn = sign_table(c);
+                KL(c, lsk::launch_dense_step(a, c->cfg, s));
+            } else {
+                KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
+            }
             ++c->stencil_launches;
             c->dir ^= 1;
             if (c->step_mode == LS_LEARNED) {
@@ -983,6 +988,14 @@ int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out, int* pp
     if (stages_out) *stages_out = c->cfg.stages;
     if (grid_pct_out) *grid_pct_out = c->cfg.grid_pct;
     if (ppt_out) *ppt_out = c->cfg.ppt;
+    return LS_OK;
+}
+
+int ls_set_dense_kernel(ls_ctx* c, int on)
+{
+    if (!c) return LS_EINVAL;
+    c->cfg.dense = on != 0;
+    clear_graphs(c);
     return LS_OK;
 }
 

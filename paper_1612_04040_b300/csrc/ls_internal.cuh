@@ -164,6 +164,7 @@ struct StepArgs {
     Inst in;                  // single instance parameters (bc is read from here always)
     int max_grid;             // cap on the persistent grid (0 = none)
     int reverse;              // FP32: walk the list from its end (L2 reuse across launches)
+    const uint8_t* tile_sgn;  // full-domain column kernel: per-tile sign class of F, or NULL
     // local scheme (single instance, 4 points per thread)
     int op;                   // OP_*
     LocalParams lp;
@@ -178,15 +179,19 @@ struct StepArgs {
 struct StepConfig {
     int stages = 3;           // cp.async ring depth (2, 3, 4)
     int grid_pct = 100;       // persistent grid, percent of full occupancy
-    int ppt = 8;              // points per thread: 4 (128-thread CTAs) or 8 (64-thread CTAs)
+    int ppt = 4;              // points per thread: 4 (128-thread CTAs) or 8 (64-thread CTAs)
     int spp = 1;              // steps per pass: 1, or 2 (temporal blocking, ls_step2.cu)
     int grid_pct2 = 100;      // persistent grid of the two-step passes
+    int dense = 0;            // full domain: the column-streaming kernel (ls_dense.cu)
 };
 
 cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cudaStream_t s);
 // two steps per pass (FP32 single grid, plain scheme; a.nact required);
 // grid from cfg.grid_pct2
 cudaError_t launch_step2(const StepArgs& a, const StepConfig& cfg, cudaStream_t s);
+// full-domain mode, FP32 single grid, plain scheme: tile columns streamed
+// along z (ls_dense.cu); every tile, no list
+cudaError_t launch_dense_step(const StepArgs& a, const StepConfig& cfg, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // batched rebuild helpers (ls_band.cu)

@@ -85,6 +85,7 @@ SIGNATURES = {
     "ls_set_step_mode": (_i, [_vp, _i]),
     "ls_set_scheme": (_i, [_vp, _i, _c.c_double, _i, _c.c_double]),
     "ls_set_dilation": (_i, [_vp, _i]),
+    "ls_set_dense_kernel": (_i, [_vp, _i]),
     "ls_set_steps_per_pass": (_i, [_vp, _i]),
     "ls_get_steps_per_pass": (_i, [_vp, _c.POINTER(_i)]),
     "ls_output_open": (_i, [_vp, _c.c_char_p, _i, _i, _i]),
@@ -496,6 +497,9 @@ class LevelSet:
         k = ctypes.c_int(0)
         check(self.lib.ls_get_steps_per_pass(self.ctx, ctypes.byref(k)), "ls_get_steps_per_pass")
         return k.value
+
+    def set_dense_kernel(self, on=True):
+        check(self.lib.ls_set_dense_kernel(self.ctx, int(bool(on))), "ls_set_dense_kernel")
 
     def set_dilation(self, neighbours):
         check(self.lib.ls_set_dilation(self.ctx, int(neighbours)), "ls_set_dilation")
