@@ -215,7 +215,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def cpu_baseline(phi0_f32, F_f32, w, steps=10):
+def cpu_baseline(phi0_f32, F_f32, w, steps=40):
     """The FP64 CPU oracle, as it stands, on the first `steps` level-set steps
     of the same workload (inputs: the same FP32 arrays, widened)."""
     import numpy as np

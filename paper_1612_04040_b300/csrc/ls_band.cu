@@ -6,13 +6,37 @@
 // All band decisions are exact: min |phi| over a tile is exact in any
 // precision, and the tube test min|phi| < gamma is done in FP64 against
 // gamma = halfwidth * h computed in FP64 on the host.
+#include <utility>
+
 #include "ls_internal.cuh"
+#include "ls_stencil.cuh"
 
 namespace lsk {
 
 namespace {
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// The rebuild kernels that follow a stencil launch (dilate) or another
+// rebuild kernel (scatter) are launched with programmatic stream
+// serialisation: their CTAs are scheduled as the previous grid drains and
+// wait (pdl_wait, their first statement) for its completion and memory.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_after(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s,
+                         Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 template <typename T>
 __device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
@@ -155,10 +179,10 @@ __global__ void __launch_bounds__(256) k_tile_speed(const T* __restrict__ F, T* 
 // neighbour-existence bits of tile t (single instance or batched table)
 __device__ __forceinline__ unsigned nb_bits(long long t, const Inst& in)
 {
-    const long long loc = t - in.tile_base;
-    const long long tpl = (long long)in.tnx * in.tny;
-    const int tz = (int)(loc / tpl);
-    const int rem = (int)(loc - (long long)tz * tpl);
+    const int loc = (int)(t - in.tile_base);  // < 2^31 tiles per instance
+    const int tpl = in.tnx * in.tny;
+    const int tz = loc / tpl;
+    const int rem = loc - tz * tpl;
     const int ty = rem / in.tnx, tx = rem - ty * in.tnx;
     unsigned b = 0;
     if (tx > 0) b |= NB_XM;
@@ -271,30 +295,36 @@ __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core
                                                 long long ntiles, unsigned* done, int* total,
                                                 int conn)
 {
+    pdl_wait();
     const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
     int on = 0;
     if (t < ntiles) {
         const Inst& in = inst_of(t, d_inst, tile_inst, single);
-        const long long loc = t - in.tile_base;
-        const long long tpl = (long long)in.tnx * in.tny;
-        const int tz = (int)(loc / tpl);
-        const int rem = (int)(loc - (long long)tz * tpl);
+        // tile ids of one instance fit in 32 bits (the active list is int)
+        const int loc = (int)(t - in.tile_base);
+        const int tpl = in.tnx * in.tny;
+        const int tz = loc / tpl;
+        const int rem = loc - tz * tpl;
         const int ty = rem / in.tnx, tx = rem - ty * in.tnx;
-        for (int dz = -1; dz <= 1 && !on; ++dz) {
-            const int z = tz + dz;
-            if (z < 0 || z >= in.tnz) continue;
-            for (int dy = -1; dy <= 1 && !on; ++dy) {
-                const int y = ty + dy;
-                if (y < 0 || y >= in.tny) continue;
-                const long long row = in.tile_base + ((long long)z * in.tny + y) * in.tnx;
+        const uint8_t* c0 = core + in.tile_base;
+        // all 27 (or 7) flags are loaded independently, then OR-ed: no
+        // chain of dependent loads
+        unsigned acc = 0;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
                 for (int dx = -1; dx <= 1; ++dx) {
-                    const int x = tx + dx;
-                    if (x < 0 || x >= in.tnx) continue;
-                    if (conn == 6 && abs(dx) + abs(dy) + abs(dz) > 1) continue;
-                    if (core[row + x]) { on = 1; break; }
+                    const int z = tz + dz, y = ty + dy, x = tx + dx;
+                    const bool in_dom = z >= 0 && z < in.tnz && y >= 0 && y < in.tny && x >= 0 &&
+                                        x < in.tnx;
+                    const bool in_conn = conn != 6 || abs(dx) + abs(dy) + abs(dz) <= 1;
+                    if (in_dom && in_conn) acc |= c0[(z * in.tny + y) * in.tnx + x];
                 }
             }
         }
+        on = acc != 0;
         const int old = act[t] & 1;
         act[t] = (uint8_t)(on | (old << 1));
     }
@@ -451,6 +481,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
     __shared__ int warp_leave[8];
     __shared__ unsigned long long warp_max_bits[8];
     __shared__ int leave_ids[256];
+    pdl_wait();
     const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
     const int fl = (t < ntiles) ? act[t] : 0;
     const int on = fl & 1;
@@ -522,6 +553,7 @@ __global__ void __launch_bounds__(256) k_scatter_batch(
     __shared__ int warp_cnt[8];
     __shared__ int warp_leave[8];
     __shared__ int leave_ids[256];
+    pdl_wait();
     const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
     const int fl = (t < ntiles) ? act[t] : 0;
     const int on = fl & 1;
@@ -723,9 +755,8 @@ cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
                           long long ntiles, unsigned* done, int* count, int conn, cudaStream_t s)
 {
     const int nb = (int)((ntiles + 255) / 256);
-    k_dilate<<<nb, 256, 0, s>>>(core, act, block_counts, d_inst, tile_inst, single, ntiles, done,
-                                count, conn);
-    return cudaGetLastError();
+    return launch_after(k_dilate, nb, 256, s, core, act, block_counts, d_inst, tile_inst, single,
+                        ntiles, done, count, conn);
 }
 
 cudaError_t launch_nflag_count(const uint8_t* nflag, const int* count, int* block_counts,
@@ -760,16 +791,14 @@ cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* li
 {
     const int nb = (int)((ntiles + 255) / 256);
     if (prec == 0)
-        k_scatter<float><<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, tile_sgn,
-                                            const_sgn, single, ntiles, (const float*)tile_maxF,
-                                            Mbits, (const uint4*)cur, (uint4*)other, list_nact,
-                                            sc, dt_mode, dt_value, count, done);
-    else
-        k_scatter<double><<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, tile_sgn,
-                                             const_sgn, single, ntiles, (const double*)tile_maxF,
-                                             Mbits, (const uint4*)cur, (uint4*)other, list_nact,
-                                             sc, dt_mode, dt_value, count, done);
-    return cudaGetLastError();
+        return launch_after(k_scatter<float>, nb, 256, s, act, block_offsets, list, list_info,
+                            tile_sgn, const_sgn, single, ntiles, (const float*)tile_maxF, Mbits,
+                            (const uint4*)cur, (uint4*)other, list_nact, sc, dt_mode, dt_value,
+                            count, done);
+    return launch_after(k_scatter<double>, nb, 256, s, act, block_offsets, list, list_info,
+                        tile_sgn, const_sgn, single, ntiles, (const double*)tile_maxF, Mbits,
+                        (const uint4*)cur, (uint4*)other, list_nact, sc, dt_mode, dt_value, count,
+                        done);
 }
 
 cudaError_t launch_scatter_batch(const uint8_t* act, const int* block_offsets, int* list,

@@ -186,6 +186,8 @@ struct StepConfig {
 };
 
 cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cudaStream_t s);
+// FP64 step and local-scheme passes (ls_step64.cu)
+cudaError_t launch_step64(const StepArgs& a, cudaStream_t s);
 // two steps per pass (FP32 single grid, plain scheme; a.nact required);
 // grid from cfg.grid_pct2
 cudaError_t launch_step2(const StepArgs& a, const StepConfig& cfg, cudaStream_t s);

@@ -15,9 +15,8 @@
 // FP32 path: differences are taken unscaled and 1/h folded into
 // coef = dt/h; the sign of F selects G+ (Eq. 4) or G- (Eq. 5) through
 // G-(phi) = G+(-phi), i.e. the one-sided differences are multiplied by
-// sign(F).  FP64 path: every operation of the reference definition in the
-// same order with explicit round-to-nearest intrinsics (no contraction), so
-// it reproduces an FP64 CPU evaluation of the definition bit for bit.
+// sign(F).  The FP64 path (bit-identical to the definition) is in
+// ls_step64.cu.
 //
 // Optionally (CLASSIFY) the kernel also evaluates the tube test of Eq. 6 on
 // the values it has just written: min |phi^{n+1}| over the tile < gamma in
@@ -655,255 +654,6 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
     cp_async_wait<0>();
 }
 
-// ------------------------------------------------------------------ FP64 ----
-__device__ __forceinline__ double max0(double a) { return a > 0.0 ? a : 0.0; }
-__device__ __forceinline__ double min0(double a) { return a < 0.0 ? a : 0.0; }
-
-// one-sided difference (a - b)/h; for a power-of-two h the product with the
-// exact reciprocal is the same IEEE result as the division
-__device__ __forceinline__ double dq(double a, double b, bool pow2h, double h, double inv_h)
-{
-    const double d = __dsub_rn(a, b);
-    return pow2h ? __dmul_rn(d, inv_h) : __ddiv_rn(d, h);
-}
-
-__device__ __forceinline__ double sq_sum(double a, double b)
-{
-    return __dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b));
-}
-
-// Eq. 3-5 in the order of the definition: per-axis sums, ((x + y) + z)
-__device__ __forceinline__ double upd64(double c, double F, double dmx, double dpx, double dmy,
-                                        double dpy, double dmz, double dpz, double dt)
-{
-    double t;
-    if (F > 0.0) {
-        const double sx = sq_sum(max0(dmx), min0(dpx));
-        const double sy = sq_sum(max0(dmy), min0(dpy));
-        const double sz = sq_sum(max0(dmz), min0(dpz));
-        t = __dmul_rn(F, __dsqrt_rn(__dadd_rn(__dadd_rn(sx, sy), sz)));
-    } else if (F < 0.0) {
-        const double sx = sq_sum(max0(dpx), min0(dmx));
-        const double sy = sq_sum(max0(dpy), min0(dmy));
-        const double sz = sq_sum(max0(dpz), min0(dmz));
-        // + 0.0: the inactive term max(F,0) G+ is +0, which turns a -0 into +0
-        t = __dadd_rn(__dmul_rn(F, __dsqrt_rn(__dadd_rn(__dadd_rn(sx, sy), sz))), 0.0);
-    } else {
-        t = 0.0;
-    }
-    return __dsub_rn(c, __dmul_rn(dt, t));
-}
-
-struct D4 { double v[4]; };
-
-__device__ __forceinline__ D4 ld4(const double* p)
-{
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
-    D4 r;
-    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = b.x; r.v[3] = b.y;
-    return r;
-}
-
-// ---------------------------------------------------- local scheme, FP64 --
-// The oracle's expressions in its order, round-to-nearest intrinsics.
-__device__ __forceinline__ double cut64(double a, double beta, double gamma)
-{
-    if (a <= beta) return 1.0;
-    if (a < gamma) {
-        const double u = __dsub_rn(a, gamma);
-        const double w = __dsub_rn(gamma, beta);
-        const double p = __dsub_rn(__dadd_rn(__dmul_rn(2.0, a), gamma), __dmul_rn(3.0, beta));
-        return __ddiv_rn(__dmul_rn(__dmul_rn(u, u), p), __dmul_rn(__dmul_rn(w, w), w));
-    }
-    return 0.0;
-}
-
-__device__ __forceinline__ double rei64(double d, double dmx, double dpx, double dmy, double dpy,
-                                        double dmz, double dpz, double h, double dtau)
-{
-    if (d == 0.0) return d;
-    double q;
-    if (d > 0.0)
-        q = __dadd_rn(__dadd_rn(sq_sum(max0(dmx), min0(dpx)), sq_sum(max0(dmy), min0(dpy))),
-                      sq_sum(max0(dmz), min0(dpz)));
-    else
-        q = __dadd_rn(__dadd_rn(sq_sum(max0(dpx), min0(dmx)), sq_sum(max0(dpy), min0(dmy))),
-                      sq_sum(max0(dpz), min0(dmz)));
-    const double g = __dsqrt_rn(q);
-    const double S = __ddiv_rn(d, __dsqrt_rn(__dadd_rn(__dmul_rn(d, d),
-                                                         __dmul_rn(__dmul_rn(g, g), __dmul_rn(h, h)))));
-    return __dsub_rn(d, __dmul_rn(dtau, __dmul_rn(S, __dsub_rn(g, 1.0))));
-}
-
-__device__ __forceinline__ double clamp64(double d, double gamma)
-{
-    return d < -gamma ? -gamma : (d > gamma ? gamma : d);
-}
-
-template <bool FIELD, bool CLASSIFY, int OP = OP_PLAIN>
-__global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
-{
-    __shared__ D4 sm[2][8][8][2];
-    __shared__ unsigned long long smin[2];
-    __shared__ unsigned nfl[2];   // advance: some point of the tile is in N
-    long long prev_k = -1;
-    const int tid = threadIdx.x;
-    const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
-    const Inst in = a.in;
-    const long long n = *a.count;
-    if (blockIdx.x == 0 && tid == 0 && a.updates)
-        atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
-    const double dt = a.sc->dt;
-    const double* __restrict__ src = (const double*)a.src;
-    double* __restrict__ dst = (double*)a.dst;
-    const double* __restrict__ Fp = (const double*)a.F;
-    const bool extrap = in.bc == 0;
-    const bool pow2h = in.pow2h != 0;
-    const double h = in.h, inv_h = in.inv_h;
-    const long long sy = (long long)in.tnx * TILE_PTS;
-    const long long sz = (long long)in.tnx * in.tny * TILE_PTS;
-    const int off = tid * 4;
-    int buf = 0;
-    int prev_t = -1;
-    for (long long k = blockIdx.x; k < n; k += gridDim.x) {
-        const int t = __ldg(a.list + k);
-        const unsigned info = __ldg(a.info + k);
-        const double* tp = src + (size_t)t * TILE_PTS;
-        const D4 c = ld4(tp + off);
-        D4 f;
-        if (FIELD) f = ld4(Fp + (size_t)t * TILE_PTS + off);
-        else { f.v[0] = f.v[1] = f.v[2] = f.v[3] = in.Fc; }
-        const bool xlo_face = (xh == 0) && !(info & NB_XM);
-        const bool xhi_face = (xh == 1) && !(info & NB_XP);
-        double xo = 0.0;
-        if (xh == 0) {
-            if (!xlo_face) xo = __ldg(tp - TILE_PTS + lz * 64 + ly * 8 + 7);
-        } else {
-            if (!xhi_face) xo = __ldg(tp + TILE_PTS + lz * 64 + ly * 8);
-        }
-        const bool ylo_face = (ly == 0) && !(info & NB_YM);
-        const bool yhi_face = (ly == 7) && !(info & NB_YP);
-        D4 yo = c;
-        if (ly == 0 && !ylo_face) yo = ld4(tp - sy + lz * 64 + 56 + 4 * xh);
-        if (ly == 7 && !yhi_face) yo = ld4(tp + sy + lz * 64 + 4 * xh);
-        const bool zlo_face = (lz == 0) && !(info & NB_ZM);
-        const bool zhi_face = (lz == 7) && !(info & NB_ZP);
-        D4 zo = c;
-        if (lz == 0 && !zlo_face) zo = ld4(tp - sz + 448 + ly * 8 + 4 * xh);
-        if (lz == 7 && !zhi_face) zo = ld4(tp + sz + ly * 8 + 4 * xh);
-
-        sm[buf][lz][ly][xh] = c;
-        if (CLASSIFY && tid == 0) smin[buf] = 0x7ff0000000000000ull;
-        if (OP == OP_CUT && tid == 0) nfl[buf] = 0u;
-        __syncthreads();
-        if (CLASSIFY && tid == 0 && prev_t >= 0)
-            a.core[prev_t] = (__longlong_as_double((long long)smin[buf ^ 1]) < in.gamma) ? 1 : 0;
-        if (OP == OP_CUT && tid == 0 && prev_k >= 0) a.nflag[prev_k] = (uint8_t)nfl[buf ^ 1];
-
-        const D4 ym = (ly > 0) ? sm[buf][lz][ly - 1][xh] : yo;
-        const D4 yp = (ly < 7) ? sm[buf][lz][ly + 1][xh] : yo;
-        const D4 zm = (lz > 0) ? sm[buf][lz - 1][ly][xh] : zo;
-        const D4 zp = (lz < 7) ? sm[buf][lz + 1][ly][xh] : zo;
-        const double part = __shfl_xor_sync(0xffffffffu, xh ? c.v[0] : c.v[3], 1);
-        double xn[6];  // x values at x0-1 .. x0+4
-        xn[0] = xh ? part : xo;
-        xn[1] = c.v[0]; xn[2] = c.v[1]; xn[3] = c.v[2]; xn[4] = c.v[3];
-        xn[5] = xh ? xo : part;
-
-        // Eq. 11 bits of the thread's four points (local scheme)
-        unsigned nb = 0;
-        if constexpr (OP == OP_CUT || OP == OP_CUT_CLAMP) {
-            const double g = in.gamma;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                bool inn = fabs(c.v[j]) < g;
-                inn |= (j > 0 || !xlo_face) && fabs(xn[j]) < g;
-                inn |= (j < 3 || !xhi_face) && fabs(xn[j + 2]) < g;
-                inn |= !ylo_face && fabs(ym.v[j]) < g;
-                inn |= !yhi_face && fabs(yp.v[j]) < g;
-                inn |= !zlo_face && fabs(zm.v[j]) < g;
-                inn |= !zhi_face && fabs(zp.v[j]) < g;
-                nb |= (inn ? 1u : 0u) << j;
-            }
-            if constexpr (OP == OP_CUT) {
-                uint32_t w = nb << (4 * (tid & 7));
-                w |= __shfl_xor_sync(0xffffffffu, w, 1);
-                w |= __shfl_xor_sync(0xffffffffu, w, 2);
-                w |= __shfl_xor_sync(0xffffffffu, w, 4);
-                if ((tid & 7) == 0) a.nmask[(size_t)k * 16 + (tid >> 3)] = w;
-                if (__any_sync(0xffffffffu, nb != 0u) && (tid & 31) == 0) nfl[buf] = 1u;
-            }
-            const unsigned inact = info & NB_ALL & ~(unsigned)__ldg(a.nact + k);
-            if (inact && a.breaches) {
-                const unsigned tb = (fabs(c.v[0]) < g ? 1u : 0u) | (fabs(c.v[1]) < g ? 2u : 0u) |
-                                    (fabs(c.v[2]) < g ? 4u : 0u) | (fabs(c.v[3]) < g ? 8u : 0u);
-                const unsigned nt = __popc(tb);
-                unsigned bad = 0;
-                if (xh == 0 && (tb & 1u) && (inact & NB_XM)) bad += 1;
-                if (xh == 1 && (tb & 8u) && (inact & NB_XP)) bad += 1;
-                if (ly == 0 && (inact & NB_YM)) bad += nt;
-                if (ly == 7 && (inact & NB_YP)) bad += nt;
-                if (lz == 0 && (inact & NB_ZM)) bad += nt;
-                if (lz == 7 && (inact & NB_ZP)) bad += nt;
-                if (bad) atomicAdd(a.breaches, (unsigned long long)bad);
-            }
-        } else if constexpr (OP == OP_REINIT || OP == OP_REINIT_CLAMP) {
-            nb = (__ldg(a.nmask + (size_t)k * 16 + (tid >> 3)) >> (4 * (tid & 7))) & 15u;
-        }
-
-        D4 o;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const double cj = c.v[j];
-            double dmx = dq(cj, xn[j], pow2h, h, inv_h);
-            double dpx = dq(xn[j + 2], cj, pow2h, h, inv_h);
-            double dmy = dq(cj, ym.v[j], pow2h, h, inv_h);
-            double dpy = dq(yp.v[j], cj, pow2h, h, inv_h);
-            double dmz = dq(cj, zm.v[j], pow2h, h, inv_h);
-            double dpz = dq(zp.v[j], cj, pow2h, h, inv_h);
-            if (j == 0 && xlo_face) dmx = extrap ? dpx : 0.0;
-            if (j == 3 && xhi_face) dpx = extrap ? dmx : 0.0;
-            if (ylo_face) dmy = extrap ? dpy : 0.0;
-            if (yhi_face) dpy = extrap ? dmy : 0.0;
-            if (zlo_face) dmz = extrap ? dpz : 0.0;
-            if (zhi_face) dpz = extrap ? dmz : 0.0;
-            if constexpr (OP == OP_PLAIN) {
-                o.v[j] = upd64(cj, f.v[j], dmx, dpx, dmy, dpy, dmz, dpz, dt);
-            } else if constexpr (OP == OP_CUT || OP == OP_CUT_CLAMP) {
-                const double fe = __dmul_rn(f.v[j], cut64(fabs(cj), a.lp.beta, in.gamma));
-                double r = upd64(cj, fe, dmx, dpx, dmy, dpy, dmz, dpz, dt);
-                if (OP == OP_CUT_CLAMP && ((nb >> j) & 1u)) r = clamp64(r, in.gamma);
-                o.v[j] = r;
-            } else {
-                double r = rei64(cj, dmx, dpx, dmy, dpy, dmz, dpz, h, a.lp.dtau);
-                if (OP == OP_REINIT_CLAMP) r = clamp64(r, in.gamma);
-                o.v[j] = ((nb >> j) & 1u) ? r : cj;
-            }
-        }
-        double* dp = dst + (size_t)t * TILE_PTS + off;
-        *reinterpret_cast<double2*>(dp) = make_double2(o.v[0], o.v[1]);
-        *reinterpret_cast<double2*>(dp + 2) = make_double2(o.v[2], o.v[3]);
-
-        if (CLASSIFY) {
-            double m = fmin(fmin(fabs(o.v[0]), fabs(o.v[1])), fmin(fabs(o.v[2]), fabs(o.v[3])));
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, s));
-            if ((tid & 31) == 0)
-                atomicMin(&smin[buf], (unsigned long long)__double_as_longlong(m));
-        }
-        buf ^= 1;
-        prev_t = t;
-        prev_k = k;
-    }
-    if (CLASSIFY || OP == OP_CUT) {
-        __syncthreads();
-        if (CLASSIFY && tid == 0 && prev_t >= 0)
-            a.core[prev_t] = (__longlong_as_double((long long)smin[buf ^ 1]) < in.gamma) ? 1 : 0;
-        if (OP == OP_CUT && tid == 0 && prev_k >= 0) a.nflag[prev_k] = (uint8_t)nfl[buf ^ 1];
-    }
-}
-
 // launch with programmatic stream serialisation (see pdl_wait)
 template <typename K>
 cudaError_t launch_pdl(K kernel, int grid, int block, size_t smem, const StepArgs& a, cudaStream_t s)
@@ -998,49 +748,6 @@ cudaError_t launch_local32(const StepArgs& a, const StepConfig& cfg, cudaStream_
     }
 }
 
-template <bool FIELD, bool CLS, int OP>
-cudaError_t launch64_op(const StepArgs& a, cudaStream_t s)
-{
-    static int full = 0;
-    if (!full) full = occupancy_grid(k_step_f64<FIELD, CLS, OP>, 0);
-    int grid = full;
-    if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
-    k_step_f64<FIELD, CLS, OP><<<grid, 128, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_local64(const StepArgs& a, cudaStream_t s)
-{
-    const bool field = a.F != nullptr;
-    const bool cls = a.core != nullptr;
-    switch (a.op) {
-    case OP_CUT:
-        if (cls) return cudaErrorInvalidValue;
-        return field ? launch64_op<true, false, OP_CUT>(a, s) : launch64_op<false, false, OP_CUT>(a, s);
-    case OP_CUT_CLAMP:
-        if (field) return cls ? launch64_op<true, true, OP_CUT_CLAMP>(a, s) : launch64_op<true, false, OP_CUT_CLAMP>(a, s);
-        return cls ? launch64_op<false, true, OP_CUT_CLAMP>(a, s) : launch64_op<false, false, OP_CUT_CLAMP>(a, s);
-    case OP_REINIT:
-        if (cls) return cudaErrorInvalidValue;
-        return launch64_op<false, false, OP_REINIT>(a, s);
-    case OP_REINIT_CLAMP:
-        return cls ? launch64_op<false, true, OP_REINIT_CLAMP>(a, s) : launch64_op<false, false, OP_REINIT_CLAMP>(a, s);
-    default:
-        return cudaErrorInvalidValue;
-    }
-}
-
-template <bool FIELD, bool CLS>
-cudaError_t launch64(const StepArgs& a, cudaStream_t s)
-{
-    static int full = 0;
-    if (!full) full = occupancy_grid(k_step_f64<FIELD, CLS>, 0);
-    int grid = full;
-    if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
-    k_step_f64<FIELD, CLS><<<grid, 128, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cudaStream_t s)
@@ -1050,7 +757,7 @@ cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cuda
     const bool bat = a.list_inst != nullptr;
     if (a.op != OP_PLAIN) {
         if (bat || !a.nmask) return cudaErrorInvalidValue;  // single-instance contexts only
-        return prec == 0 ? launch_local32(a, cfg, s) : launch_local64(a, s);
+        return prec == 0 ? launch_local32(a, cfg, s) : launch_step64(a, s);
     }
     if (prec == 0) {
         if (bat) {
@@ -1061,8 +768,7 @@ cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cuda
         return cls ? launch32_s<false, true, false>(a, cfg, s) : launch32_s<false, false, false>(a, cfg, s);
     }
     if (bat) return cudaErrorInvalidValue;  // batched contexts are FP32
-    if (field) return cls ? launch64<true, true>(a, s) : launch64<true, false>(a, s);
-    return cls ? launch64<false, true>(a, s) : launch64<false, false>(a, s);
+    return launch_step64(a, s);
 }
 
 }  // namespace lsk

@@ -136,6 +136,36 @@ def test_fp64_non_power_of_two_h_bitwise():
     assert np.array_equal(bits(g.get_phi()), bits(o.phi))
 
 
+def test_fp64_extreme_magnitudes_bitwise():
+    """For a power-of-two h the kernel works on unscaled differences while
+    every intermediate stays a normal number, and falls back to the scaled
+    sequence otherwise. Blocks of phi scaled so that the squares of the
+    differences are subnormal (1e-155), underflow (1e-300) or are huge
+    (1e149), and speeds that are tiny (1e-130), +0 or -0, mix both paths
+    inside warps; every point must still match the oracle bit for bit."""
+    shape = (32, 32, 32)
+    h = 1.0 / 32
+    phi0 = inputs.sphere_union_sdf(shape, h, [(0.5, 0.5, 0.5)], [0.3]).numpy()
+    phi0[0:8, 0:8, 0:16] *= 1e-155
+    phi0[8:16, 0:8, 0:16] *= 1e-300
+    phi0[16:24, 8:16, 4:28] *= 1e149
+    phi0[24:32, 24:32, 3:29] *= 1e-155
+    F = inputs.speed_cos_cos(shape, h).numpy()
+    F[:, :, 5] = 1e-130
+    F[:, 3, :] = 0.0
+    F[7, :, :] = -0.0
+    F[:, 20:24, 9] = -3e-140
+    g, o = make_pair(shape, h, ls.LS_FP64, phi0, F=F)
+    g.set_full_domain(True)
+    o.set_full_domain(True)
+    for n in (1, 2):
+        g.step(n, h / 4, ls.LS_DT_FIXED)
+        o.step(n, h / 4, oracle.DT_FIXED)
+        out = g.get_phi()
+        assert np.isfinite(out).all()
+        assert np.array_equal(bits(out), bits(o.phi))
+
+
 def test_fp64_neumann_faces_bitwise():
     """The neumann face rule, with a front that reaches the domain faces."""
     shape = (32, 32, 32)
