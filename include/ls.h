@@ -212,6 +212,32 @@ int ls_set_full_domain(ls_ctx *ctx, int on);
  * Synchronises the stream.  Errors: LS_EINVAL, LS_ESTATE (phi not set). */
 int ls_get_phi(ls_ctx *ctx, void *dst, int dst_on_device);
 
+/* Stream-ordered host input/output, for a sequence of problems on one
+ * single-grid context: the next problem's inputs travel to the device and
+ * the previous result travels back while the current one computes (one
+ * copy stream per direction; the transfers overlap the stencil only when
+ * the host buffers are page-locked).
+ *
+ * ls_stage_inputs: start copying phi (row-major, nx*ny*nz values of the
+ *   context precision) and, if speed_host is not NULL, the speed field into
+ *   device staging buffers; returns at once.  The host buffers must stay
+ *   unchanged until ls_load_staged has returned.  LS_ESTATE if inputs are
+ *   already staged and not loaded.
+ * ls_load_staged: on the context's stream, after those copies, make the
+ *   staged arrays the context's phi (and speed field), as ls_set_phi /
+ *   ls_set_speed with device sources do (the band is rebuilt at the next
+ *   step; LS_ENONFINITE on NaN/Inf; synchronises the context's stream).
+ *   LS_ESTATE if nothing is staged.
+ * ls_get_phi_async: after the work enqueued so far on the context's
+ *   stream, copy the current phi to host_dst (row-major); returns at once.
+ *   host_dst is written when ls_wait_host returns.
+ * ls_wait_host: wait for every staged copy and read-back to finish.
+ * Errors: LS_EINVAL (NULL arguments, batched contexts), LS_ESTATE, LS_ECUDA. */
+int ls_stage_inputs(ls_ctx *ctx, const void *phi_host, const void *speed_host);
+int ls_load_staged(ls_ctx *ctx);
+int ls_get_phi_async(ls_ctx *ctx, void *host_dst);
+int ls_wait_host(ls_ctx *ctx);
+
 /* Checkpoint: copy the current phi of every instance into a context-owned
  * device buffer (allocated on the first call).  Errors: LS_ESTATE (phi not
  * set), LS_ENOMEM. */

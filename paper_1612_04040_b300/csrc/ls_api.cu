@@ -138,17 +138,31 @@ void free_all(ls_ctx* c)
     for (auto e : c->ev_free) cudaEventDestroy(e);
     void* ptrs[] = {c->phi[0], c->phi[1], c->F, c->tile_maxF, c->tile_sgn, c->staging, c->snapshot, c->core,
                     c->act, c->list, c->list_info, c->d_count, c->block_counts, c->d_sc,
-                    c->d_Mbits, c->d_updates, c->d_status, c->d_nonfinite, c->d_inst,
+                    c->d_Mbits, c->d_updates, c->d_status, c->d_inst,
                     c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params, c->nmask,
                     c->d_breaches, c->list_nact, c->nmask2, c->nflag, c->nl, c->nl_info,
                     c->d_ncount, c->d_rupdates, c->d_done, c->d_updates2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (c->h_nonfinite) cudaFreeHost(c->h_nonfinite);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     if (c->learned) lsk::learned_free(c->learned);
     c->learned = nullptr;
     if (c->output) lsk::output_free(c->output);
     c->output = nullptr;
+    if (c->hio) {
+        lsk::HostIO* H = c->hio;
+        if (H->h2d) cudaStreamSynchronize(H->h2d);
+        if (H->d2h) cudaStreamSynchronize(H->d2h);
+        for (cudaEvent_t e : {H->staged, H->consumed, H->unpacked, H->drained})
+            if (e) cudaEventDestroy(e);
+        for (void* p : {H->in_phi, H->in_F, H->out})
+            if (p) cudaFree(p);
+        if (H->h2d) cudaStreamDestroy(H->h2d);
+        if (H->d2h) cudaStreamDestroy(H->d2h);
+        delete H;
+        c->hio = nullptr;
+    }
 }
 
 size_t grid_bytes(const ls_ctx* c) { return c->npts * c->esize; }
@@ -187,12 +201,13 @@ int pack_from(ls_ctx* c, const Inst& in, const void* src, int on_device, void* d
     } else if (!aligned16(src)) {
         return LS_EINVAL;
     }
-    CK(cudaMemsetAsync(c->d_nonfinite, 0, sizeof(unsigned), c->stream));
+    // the flag is a mapped host word: no copy-engine transfer, so the check
+    // does not wait behind a read-back in flight on another stream
+    volatile unsigned* flag = c->h_nonfinite;
+    *flag = 0u;
     KL(c, lsk::launch_pack(dsrc, dst, in, c->prec, c->d_nonfinite, c->stream));
-    unsigned bad = 0;
-    CK(cudaMemcpyAsync(&bad, c->d_nonfinite, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    return bad ? LS_ENONFINITE : LS_OK;
+    return *flag ? LS_ENONFINITE : LS_OK;
 }
 
 unsigned const_sign_bits(const ls_ctx* c) { return c->insts[0].Fc >= 0.0 ? lsk::SG_POS : lsk::SG_NEG; }
@@ -630,7 +645,8 @@ int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h
     A(dalloc(&c->d_Mbits, sizeof(unsigned long long) * n));
     A(dalloc(&c->d_updates, sizeof(unsigned long long)));
     A(dalloc(&c->d_status, sizeof(unsigned)));
-    A(dalloc(&c->d_nonfinite, sizeof(unsigned)));
+    A(cudaHostAlloc((void**)&c->h_nonfinite, sizeof(unsigned), cudaHostAllocMapped | cudaHostAllocPortable));
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->d_nonfinite, c->h_nonfinite, 0);
     if (batched) {
         A(dalloc(&c->d_inst, sizeof(Inst) * n));
         A(dalloc(&c->d_tile_inst, sizeof(uint16_t) * c->ntiles));
@@ -680,8 +696,8 @@ int set_phi_inst(ls_ctx* c, int i, const void* src, int on_device)
     const Inst& in = c->insts[i];
     c->inst_phi_set[i] = 0;
     RET(pack_from(c, in, src, on_device, region(c, c->phi[c->cur], in)));
-    CK(cudaMemcpyAsync(region(c, c->phi[c->cur ^ 1], in), region(c, c->phi[c->cur], in),
-                       inst_bytes(c, in), cudaMemcpyDeviceToDevice, c->stream));
+    KL(c, lsk::launch_copy(region(c, c->phi[c->cur ^ 1], in), region(c, c->phi[c->cur], in),
+                           inst_bytes(c, in), c->stream));
     c->inst_phi_set[i] = 1;
     return LS_OK;
 }
@@ -1144,6 +1160,85 @@ int ls_get_phi(ls_ctx* c, void* dst, int on_device)
 int ls_inst_get_phi(ls_ctx* c, int i, void* dst, int on_device)
 {
     return get_phi_inst(c, i, dst, on_device);
+}
+
+// ---- stream-ordered host input/output ----
+static int hostio(ls_ctx* c, lsk::HostIO** out)
+{
+    if (!c->hio) {
+        lsk::HostIO* H = new lsk::HostIO();
+        c->hio = H;  // freed with the context even if a step below fails
+        CK(cudaStreamCreateWithFlags(&H->h2d, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&H->d2h, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&H->staged, &H->consumed, &H->unpacked, &H->drained})
+            CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        // recorded once so that the first waits on them pass
+        CK(cudaEventRecord(H->consumed, c->stream));
+        CK(cudaEventRecord(H->drained, H->d2h));
+    }
+    *out = c->hio;
+    return LS_OK;
+}
+
+int ls_stage_inputs(ls_ctx* c, const void* phi_host, const void* speed_host)
+{
+    if (!c || c->n_inst != 1 || !phi_host) return LS_EINVAL;
+    lsk::HostIO* H = nullptr;
+    RET(hostio(c, &H));
+    if (H->have_phi) return LS_ESTATE;  // the staged inputs were not loaded yet
+    const size_t bytes = grid_bytes(c);
+    if (!H->in_phi) CK(dalloc(&H->in_phi, bytes));
+    if (speed_host && !H->in_F) CK(dalloc(&H->in_F, bytes));
+    // the previous ls_load_staged must have read the buffers
+    CK(cudaStreamWaitEvent(H->h2d, H->consumed, 0));
+    CK(cudaMemcpyAsync(H->in_phi, phi_host, bytes, cudaMemcpyHostToDevice, H->h2d));
+    if (speed_host) CK(cudaMemcpyAsync(H->in_F, speed_host, bytes, cudaMemcpyHostToDevice, H->h2d));
+    CK(cudaEventRecord(H->staged, H->h2d));
+    H->have_phi = true;
+    H->have_F = speed_host != nullptr;
+    return LS_OK;
+}
+
+int ls_load_staged(ls_ctx* c)
+{
+    if (!c || c->n_inst != 1) return LS_EINVAL;
+    lsk::HostIO* H = c->hio;
+    if (!H || !H->have_phi) return LS_ESTATE;
+    CK(cudaStreamWaitEvent(c->stream, H->staged, 0));
+    H->have_phi = false;
+    const bool F = H->have_F;
+    H->have_F = false;
+    int st = set_phi_inst(c, 0, H->in_phi, 1);
+    if (st == LS_OK && F) st = set_speed_inst(c, 0, H->in_F, 1);
+    CK(cudaEventRecord(H->consumed, c->stream));
+    return st;
+}
+
+int ls_get_phi_async(ls_ctx* c, void* host_dst)
+{
+    if (!c || c->n_inst != 1 || !host_dst) return LS_EINVAL;
+    if (!c->inst_phi_set[0]) return LS_ESTATE;
+    lsk::HostIO* H = nullptr;
+    RET(hostio(c, &H));
+    const size_t bytes = grid_bytes(c);
+    if (!H->out) CK(dalloc(&H->out, bytes));
+    // the previous read-back must have left the staging buffer
+    CK(cudaStreamWaitEvent(c->stream, H->drained, 0));
+    KL(c, lsk::launch_unpack(c->phi[c->cur], H->out, c->insts[0], c->prec, c->stream));
+    CK(cudaEventRecord(H->unpacked, c->stream));
+    CK(cudaStreamWaitEvent(H->d2h, H->unpacked, 0));
+    CK(cudaMemcpyAsync(host_dst, H->out, bytes, cudaMemcpyDeviceToHost, H->d2h));
+    CK(cudaEventRecord(H->drained, H->d2h));
+    return LS_OK;
+}
+
+int ls_wait_host(ls_ctx* c)
+{
+    if (!c) return LS_EINVAL;
+    if (!c->hio) return LS_OK;
+    CK(cudaStreamSynchronize(c->hio->h2d));
+    CK(cudaStreamSynchronize(c->hio->d2h));
+    return LS_OK;
 }
 
 int ls_get_active_tiles(ls_ctx* c, int* dst, long long cap, long long* n)

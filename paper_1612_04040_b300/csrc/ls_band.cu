@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(128) k_convert(const T* __restrict__ src, T* _
         }
         if (PACK && nonfinite) {
             const bool bad = !(finite_val(v0) && finite_val(v1) && finite_val(v2) && finite_val(v3));
-            if (bad) atomicAdd(nonfinite, 1u);
+            if (bad) *nonfinite = 1u;  // a flag (host-mapped memory): any writer sets it
         }
     }
 }
@@ -704,6 +704,23 @@ cudaError_t launch_pack(const void* src, void* dst, const Inst& in, int prec, un
     else
         k_convert<double, true><<<conv_grid(in.ntiles), 128, 0, s>>>(
             (const double*)src, (double*)dst, in, nonfinite);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256)
+        dst[i] = src[i];
+}
+
+cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s)
+{
+    const size_t n = bytes / 16;
+    if (n == 0) return cudaSuccess;
+    size_t g = (n + 255) / 256;
+    if (g > 148 * 16) g = 148 * 16;
+    k_copy16<<<(int)g, 256, 0, s>>>((const uint4*)src, (uint4*)dst, n);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,22 @@ struct Learned;  // corrector state (ls_learned_api.cu)
 void learned_free(Learned* L);
 struct Output;   // overlapped output (ls_output.cu)
 void output_free(Output* O);
+
+// stream-ordered host input/output (ls_stage_inputs, ls_load_staged,
+// ls_get_phi_async, ls_wait_host): device staging buffers in row-major
+// order, one copy stream per direction, and the events that order them
+// against the context's stream
+struct HostIO {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    void* in_phi = nullptr;
+    void* in_F = nullptr;
+    void* out = nullptr;
+    cudaEvent_t staged = nullptr;    // h2d: the staged inputs have arrived
+    cudaEvent_t consumed = nullptr;  // context stream: ls_load_staged read them
+    cudaEvent_t unpacked = nullptr;  // context stream: out holds the result
+    cudaEvent_t drained = nullptr;   // d2h: out has been copied to the host
+    bool have_phi = false, have_F = false;
+};
 }  // namespace lsk
 
 namespace lsk {
@@ -79,7 +95,8 @@ struct ls_ctx {
     unsigned long long* d_updates = nullptr;
     unsigned long long* d_updates2 = nullptr;  // points of two-step passes
     unsigned* d_status = nullptr;
-    unsigned* d_nonfinite = nullptr;
+    unsigned* h_nonfinite = nullptr;  // pack's non-finite flag: page-locked host word
+    unsigned* d_nonfinite = nullptr;  // the same word as the kernels address it
     // host-side state
     bool band_valid = false;
     bool core_fresh = false;
@@ -128,6 +145,7 @@ struct ls_ctx {
 
     // overlapped output
     lsk::Output* output = nullptr;
+    lsk::HostIO* hio = nullptr;
     int output_every = 0;
     long long step_count = 0;     // steps taken over the context's lifetime
 

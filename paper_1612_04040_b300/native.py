@@ -56,6 +56,10 @@ SIGNATURES = {
     "ls_step": (_i, [_vp, _i, _d, _i, _i, _c.POINTER(_d)]),
     "ls_set_full_domain": (_i, [_vp, _i]),
     "ls_get_phi": (_i, [_vp, _vp, _i]),
+    "ls_stage_inputs": (_i, [_vp, _vp, _vp]),
+    "ls_load_staged": (_i, [_vp]),
+    "ls_get_phi_async": (_i, [_vp, _vp]),
+    "ls_wait_host": (_i, [_vp]),
     "ls_snapshot": (_i, [_vp]),
     "ls_restore": (_i, [_vp]),
     "ls_get_active_tiles": (_i, [_vp, _c.POINTER(_c.c_int), _ll, _c.POINTER(_ll)]),
@@ -377,6 +381,37 @@ class LevelSet:
         p, dev = array_ptr(out, self.dtype, self.count)
         check(self.lib.ls_get_phi(self.ctx, p, dev), "ls_get_phi")
         return out
+
+    # stream-ordered host input/output (ls_stage_inputs ... ls_wait_host);
+    # the arrays must be host (CPU) arrays, page-locked for the copies to
+    # overlap the computation, and stay alive until the copies are done
+    def _host_ptr(self, a):
+        p, dev = array_ptr(a, self.dtype, self.count)
+        if dev:
+            raise ValueError("expected a host array")
+        return p
+
+    def stage_inputs(self, phi, speed=None):
+        """Start copying the next problem's phi (and speed field) to the device."""
+        self._staged = (phi, speed)  # keep the host arrays alive
+        check(self.lib.ls_stage_inputs(self.ctx, self._host_ptr(phi),
+                                       None if speed is None else self._host_ptr(speed)),
+              "ls_stage_inputs")
+
+    def load_staged(self):
+        """Make the staged arrays the context's phi (and speed field)."""
+        check(self.lib.ls_load_staged(self.ctx), "ls_load_staged")
+        self._staged = None
+
+    def get_phi_async(self, out):
+        """Start copying the current phi into the host array `out`."""
+        self._pending = getattr(self, "_pending", []) + [out]
+        check(self.lib.ls_get_phi_async(self.ctx, self._host_ptr(out)), "ls_get_phi_async")
+
+    def wait_host(self):
+        """Wait for every staged copy and read-back."""
+        check(self.lib.ls_wait_host(self.ctx), "ls_wait_host")
+        self._pending = []
 
     def active_tiles(self):
         n = ctypes.c_longlong(0)
