@@ -213,10 +213,12 @@ int ls_set_full_domain(ls_ctx *ctx, int on);
 int ls_get_phi(ls_ctx *ctx, void *dst, int dst_on_device);
 
 /* Stream-ordered host input/output, for a sequence of problems on one
- * single-grid context: the next problem's inputs travel to the device and
- * the previous result travels back while the current one computes (one
- * copy stream per direction; the transfers overlap the stencil only when
- * the host buffers are page-locked).
+ * single-grid context (Eq. 1 inputs in, Eq. 3 results out; the transfers
+ * overlap the computation as the output of section 2 does): the next
+ * problem's inputs travel to the device and the previous result travels
+ * back while the current one computes (one copy stream per direction; the
+ * transfers overlap the stencil only when the host buffers are
+ * page-locked).
  *
  * ls_stage_inputs: start copying phi (row-major, nx*ny*nz values of the
  *   context precision) and, if speed_host is not NULL, the speed field into
