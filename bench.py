@@ -233,10 +233,30 @@ def cpu_baseline(phi0_f32, F_f32, w, steps=40):
         updates += int(o.active.sum()) * 512
     t = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0))
-    return {"value": updates / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d level-set steps (%d band rebuilds) of the %d^3 workload, FP64 C oracle "
-                      "with OpenMP on %d host threads, %.1f s" % (steps, (steps + w.rebuild_every - 1)
-                                                                    // w.rebuild_every, w.n, cores, t)}
+    out = {"value": updates / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "first %d level-set steps (%d band rebuilds) of the %d^3 workload, FP64 C oracle "
+                     "with OpenMP on %d host threads, %.1f s" % (steps, (steps + w.rebuild_every - 1)
+                                                                   // w.rebuild_every, w.n, cores, t)}
+    return out, o
+
+
+def parity_vs_oracle(g, o, w, steps):
+    """The GPU's state after the same first `steps` steps, against the
+    oracle's: max |phi_gpu - phi_oracle| over the points of the oracle's
+    active tiles (bar 1e-5 h steps) and whether the active-tile sets agree."""
+    import numpy as np
+    from paper_1612_04040_b300 import native as ls
+    g.restore()
+    g.band_rebuild(w.halfwidth, want_count=False)
+    g.step(steps, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+    got = g.get_phi().astype(np.float64)
+    act = o.active.astype(bool)
+    m = np.repeat(np.repeat(np.repeat(act, 8, 0), 8, 1), 8, 2)
+    err = float(np.max(np.abs(got[m] - o.phi[m]))) if m.any() else 0.0
+    bar = 1e-5 * w.h * steps
+    same = bool(np.array_equal(np.sort(g.active_tiles()), np.flatnonzero(act.ravel())))
+    return {"steps": steps, "max_abs_err_on_band": err, "bar": bar, "within_bar": err <= bar,
+            "active_tiles_equal": same, "active_tiles": int(act.sum())}
 
 
 def cpu_baseline_local(phi0_f32, F_f32, w, beta_h, iters, dtau_h, steps=2):
@@ -808,7 +828,9 @@ def main():
         if local_scheme:
             cpu = cpu_baseline_local(phi0.cpu().numpy(), F_np, w, beta_h, iters, dtau_h)
         else:
-            cpu = cpu_baseline(phi0.cpu().numpy(), F_np, w)
+            cpu, orc = cpu_baseline(phi0.cpu().numpy(), F_np, w)
+            cpu["parity"] = parity_vs_oracle(g, orc, w, 40)
+            del orc
 
     # band points (|phi| < gamma) of the final state of the last run
     fin = torch.empty((w.n,) * 3, dtype=torch.float32, device=dev)
