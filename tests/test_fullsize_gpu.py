@@ -100,6 +100,42 @@ def test_sphere_union_512():
     assert np.array_equal(g.active_tiles(), band_from(state, w.halfwidth * w.h))
 
 
+def test_maximum_grid_fp32():
+    """The largest grid the ABI accepts: 2^31 points (nx = ny = 1024,
+    nz = 2048; 2^22 tiles, element offsets up to 2^31 - 1), FP32, three
+    spheres, one of them cut by the top z face so that the highest tile ids
+    are active; sampled one-step parity, frozen points unchanged."""
+    nz, ny, nx = 2048, 1024, 1024
+    h = 1.0 / 1024
+    shape = (nz, ny, nx)
+    dev = torch.device("cuda")
+    centres = [(0.5, 0.5, 0.5), (0.3, 0.6, 1.2), (0.55, 0.45, 1.9)]
+    radii = [0.2, 0.15, 0.2]
+    phi0 = inputs.sphere_union_sdf(shape, h, centres, radii, device=dev, out_dtype=torch.float32)
+    F = inputs.speed_sinusoid(shape, h, device=dev, out_dtype=torch.float32)
+    g = ls.LevelSet(nx, ny, nz, h, ls.LS_FP32)
+    g.set_speed(F)
+    g.set_phi(phi0)
+    del phi0
+    g.band_rebuild(6.0)
+    g.step(3, 0.5, ls.LS_DT_CFL, 5)
+    before = torch.empty(shape, dtype=torch.float32, device=dev)
+    g.get_phi(before)
+    tiles = g.active_tiles()
+    tshape = (nz // 8, ny // 8, nx // 8)
+    assert tiles.max() >= tshape[0] * tshape[1] * tshape[2] - tshape[1] * tshape[2]  # top layer
+    dt = g.step(1, 0.5, ls.LS_DT_CFL, 5, want_dt=True)
+    after = torch.empty_like(before)
+    g.get_phi(after)
+    worst = check_sampled_step(before, after, F, 0.0, h, dt, tiles, tshape, 200, 3, False)
+    assert worst <= 1e-5 * h, worst
+    act = torch.zeros(tshape[0] * tshape[1] * tshape[2], dtype=torch.bool, device=dev)
+    act[torch.from_numpy(tiles.astype(np.int64)).to(dev)] = True
+    mask = act.view(tshape).repeat_interleave(8, 0).repeat_interleave(8, 1).repeat_interleave(8, 2)
+    assert torch.equal(before[~mask], after[~mask])
+    assert g.status() == ls.LS_OK
+
+
 @pytest.fixture(scope="module")
 def perturbed_1024():
     w = inputs.PerturbedSphere()
