@@ -450,6 +450,7 @@ __device__ void set_dt_one(StepScalars* sc, int i, const Inst& in, int mode, dou
     }
     sc[i].dt = dt;
     sc[i].coef = __double2float_rn(__ddiv_rn(dt, in.h));
+    sc[i].Fc = __double2float_rn(in.Fc);
 }
 
 template <typename T>
@@ -633,6 +634,7 @@ __global__ void k_set_dt_batch(StepScalars* sc, int n_inst, const Inst* __restri
     }
     sc[i].dt = dt;
     sc[i].coef = __double2float_rn(__ddiv_rn(dt, in.h));
+    sc[i].Fc = __double2float_rn(in.Fc);
 }
 
 // full-domain list: every tile in ascending order

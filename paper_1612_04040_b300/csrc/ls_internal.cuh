@@ -59,6 +59,7 @@ struct StepScalars {
     double dt;     // current time step
     float coef;    // (float)(dt / h), FP32 path
     int active;    // active tiles of this instance at the last rebuild (batched)
+    float Fc;      // (float) constant speed, FP32 path (batched: read per tile)
 };
 
 // ---------------------------------------------------------------------------

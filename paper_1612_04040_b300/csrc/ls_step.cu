@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
         const unsigned info = (unsigned)Sg.meta.y;
         const int inst = Sg.meta.z;
         const float coef = BATCHED ? a.sc[inst].coef : coef1;
-        const float Fc = BATCHED ? (float)a.insts[inst].Fc : Fc1;
+        const float Fc = BATCHED ? a.sc[inst].Fc : Fc1;
         const float4 c = Sg.v[tid];
         const float4 f = FIELD ? Sg.f[tid] : make_float4(Fc, Fc, Fc, Fc);
         const float4 ym = Sg.v[i_ym];
@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
         const unsigned info = (unsigned)Sg.meta.y;
         const int inst = Sg.meta.z;
         const float coef = BATCHED ? a.sc[inst].coef : coef1;
-        const float Fc = BATCHED ? (float)a.insts[inst].Fc : Fc1;
+        const float Fc = BATCHED ? a.sc[inst].Fc : Fc1;
         const float4 c0 = Sg.v[q0], c1 = Sg.v[q1];
         const float4 f0 = FIELD ? Sg.f[q0] : make_float4(Fc, Fc, Fc, Fc);
         const float4 f1 = FIELD ? Sg.f[q1] : make_float4(Fc, Fc, Fc, Fc);
