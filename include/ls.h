@@ -270,8 +270,9 @@ int ls_get_updates(ls_ctx *ctx, unsigned long long *n);
 int ls_set_graphs(ls_ctx *ctx, int on);
 
 /* Autotuner: time every launch configuration of the FP32 stencil (points
- * per thread 4 (128-thread CTAs) or 8 (64-thread CTAs) x cp.async ring depth
- * 2/3/4/6 x persistent grid 50/75/100 % of full occupancy) on the current
+ * per thread 4 (128-thread CTAs), 8 (64-thread CTAs) or 16 (one warp per
+ * tile) x cp.async ring depth 2/3/4/6 x persistent grid 50/75/100 % of full
+ * occupancy) on the current
  * active set, `reps` launches each, and keep the fastest for later steps.
  * Every configuration computes the same bits.  The probes write only the
  * buffer the next step overwrites, so the state is unchanged.  Outputs
@@ -290,7 +291,7 @@ int ls_set_steps_per_pass(ls_ctx *ctx, int steps);
 int ls_get_steps_per_pass(ls_ctx *ctx, int *steps);
 
 /* Set the FP32 stencil launch configuration directly (stages 2, 3, 4 or 6, grid
- * 1..100 % of full occupancy, points per thread 4 or 8; default 3, 100, 4). */
+ * 1..100 % of full occupancy, points per thread 4, 8 or 16; default 3, 100, 4). */
 int ls_set_step_config(ls_ctx *ctx, int stages, int grid_pct, int points_per_thread);
 
 /* Profiling counters of a context. */

@@ -945,7 +945,7 @@ int ls_autotune(ls_ctx* c, int reps, int* stages_out, int* grid_pct_out, int* pp
     if (c->prec == LS_FP32) {
         const int stages[] = {2, 3, 4, 6};
         const int pcts[] = {50, 75, 100};
-        const int ppts[] = {4, 8};
+        const int ppts[] = {4, 8, 16};
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
@@ -1033,7 +1033,7 @@ int ls_get_steps_per_pass(ls_ctx* c, int* steps)
 int ls_set_step_config(ls_ctx* c, int stages, int grid_pct, int ppt)
 {
     if (!c || (stages != 2 && stages != 3 && stages != 4 && stages != 6) || grid_pct < 1 || grid_pct > 100 ||
-        (ppt != 4 && ppt != 8))
+        (ppt != 4 && ppt != 8 && ppt != 16))
         return LS_EINVAL;
     c->cfg.stages = stages;
     c->cfg.grid_pct = grid_pct;

@@ -183,13 +183,16 @@ struct StepArgs {
 struct StepConfig {
     int stages = 3;           // cp.async ring depth (2, 3, 4)
     int grid_pct = 100;       // persistent grid, percent of full occupancy
-    int ppt = 4;              // points per thread: 4 (128-thread CTAs) or 8 (64-thread CTAs)
+    int ppt = 4;              // points per thread: 4 (128-thread CTAs), 8 (64-thread CTAs) or
+                              // 16 (one warp per tile, ls_step_z4.cu)
     int spp = 1;              // steps per pass: 1, or 2 (temporal blocking, ls_step2.cu)
     int grid_pct2 = 100;      // persistent grid of the two-step passes
     int dense = 0;            // full domain: the column-streaming kernel (ls_dense.cu)
 };
 
 cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cudaStream_t s);
+// FP32 plain step with one warp per tile, 16 points per thread (ls_step_z4.cu)
+cudaError_t launch_step_z4(const StepArgs& a, const StepConfig& cfg, cudaStream_t s);
 // FP64 step and local-scheme passes (ls_step64.cu)
 cudaError_t launch_step64(const StepArgs& a, cudaStream_t s);
 // two steps per pass (FP32 single grid, plain scheme; a.nact required);

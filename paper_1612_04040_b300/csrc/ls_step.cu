@@ -701,6 +701,7 @@ cudaError_t launch32(const StepArgs& a, int grid_pct, int ppt, cudaStream_t s)
 template <bool FIELD, bool CLS, bool BAT>
 cudaError_t launch32_s(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
 {
+    if (cfg.ppt == 16) return launch_step_z4(a, cfg, s);
     switch (cfg.stages) {
     case 2: return launch32<FIELD, CLS, BAT, 2>(a, cfg.grid_pct, cfg.ppt, s);
     case 4: return launch32<FIELD, CLS, BAT, 4>(a, cfg.grid_pct, cfg.ppt, s);

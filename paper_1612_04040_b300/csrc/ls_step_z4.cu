@@ -1,0 +1,270 @@
+// ls_step_z4.cu -- the upwind step (Eq. 3-5) with one warp per 8^3 tile and
+// 16 points per thread.
+//
+// Thread (xh, ly, lzq) of the warp owns the four z-adjacent quads of planes
+// lz = 4 lzq .. 4 lzq + 3 at (ly, 4 xh .. 4 xh + 3), so three of each
+// quad's z neighbours are in its own registers, and the per-tile work
+// (list entry, staging addresses, branch on the tile's class, barrier) is
+// spread over 16 points instead of 4 (ls_step.cu) or 8.  The tube-test
+// minimum of a tile is one warp reduction (no shared-memory atomics).  Same
+// shared-memory stage layout as the 4-point kernel, same per-point arithmetic
+// (ls_stencil.cuh), so the results are the same bits for every choice of
+// points per thread.
+#include <cstddef>
+
+#include "ls_internal.cuh"
+#include "ls_stencil.cuh"
+
+namespace lsk {
+
+namespace {
+
+// one ring stage (the layout of the 4-point kernel's stage)
+template <bool FIELD>
+struct StageZ4 {
+    float4 v[192];   // [0,128): centre quads; [128,160): y-halo runs [16*(ly==7) + 2*lz + xh];
+                     // [160,192): z-halo runs [16*(lz==7) + 2*ly + xh]
+    float4 f[FIELD ? 128 : 1];
+    float xo[128];   // x-halo value of each quad
+    int4 meta;       // tile id, info byte, instance
+};
+
+// the four quads of one thread, one class of tile (SGN, FACES as upd4)
+template <int SGN, bool FACES, bool FIELD, bool CLASSIFY>
+__device__ __forceinline__ void quads4(const StageZ4<FIELD>& Sg, const float4 (&c)[4], float Fc,
+                                       float coef, bool extrap, int q0, int xh, int ly, int lzq,
+                                       int y_slot0, int z_slot, bool xlo, bool xhi, bool ylo,
+                                       bool yhi, bool zlo, bool zhi, float* dp, float& mn)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int qj = q0 + 16 * j;
+        const float4 f = FIELD ? Sg.f[qj] : make_float4(Fc, Fc, Fc, Fc);
+        const float4 ym = Sg.v[ly > 0 ? qj - 2 : y_slot0 + 2 * j];
+        const float4 yp = Sg.v[ly < 7 ? qj + 2 : y_slot0 + 2 * j];
+        const float4 zm = j > 0 ? c[j - 1] : Sg.v[lzq > 0 ? q0 - 16 : z_slot];
+        const float4 zp = j < 3 ? c[j + 1] : Sg.v[lzq < 1 ? q0 + 64 : z_slot];
+        const float pcv = reinterpret_cast<const float*>(Sg.v)[4 * (qj ^ 1) + (xh ? 3 : 0)];
+        const float xo = Sg.xo[qj];
+        const float xm0 = xh ? pcv : xo, xp3 = xh ? xo : pcv;
+        const float4 o = upd4<SGN, FACES>(c[j], f, xm0, xp3, ym, yp, zm, zp, coef, extrap, xlo, xhi,
+                                          ylo, yhi, zlo && j == 0, zhi && j == 3);
+        *reinterpret_cast<float4*>(dp + 4 * qj) = o;
+        if (CLASSIFY)
+            mn = fminf(mn, fminf(fminf(fabsf(o.x), fabsf(o.y)), fminf(fabsf(o.z), fabsf(o.w))));
+    }
+}
+
+// FIELD: speed field (else constant per instance); CLASSIFY: fused tube test
+// (Eq. 6); BATCHED: per-entry instance; S: ring stages
+template <bool FIELD, bool CLASSIFY, bool BATCHED, int S>
+__global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using Stage = StageZ4<FIELD>;
+    Stage* st = reinterpret_cast<Stage*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int xh = tid & 1, ly = (tid >> 1) & 7, lzq = tid >> 4;
+    const int lz0 = 4 * lzq;
+    const int q0 = (tid & 15) + 64 * lzq;  // quad of plane lz0; plane lz0 + j: q0 + 16 j
+    // everything this grid reads may come from the previous grid
+    pdl_launch_dependents();
+    pdl_wait();
+    const int n = *a.count;
+    // every other launch walks the list backwards (L2 reuse across launches)
+    const bool rev = a.reverse != 0;
+    auto ent = [&](int k) { return rev ? n - 1 - k : k; };
+    if (blockIdx.x == 0 && tid == 0 && a.updates)
+        atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
+    const float* __restrict__ src = (const float*)a.src;
+    float* __restrict__ dst = (float*)a.dst;
+    const float* __restrict__ Fp = (const float*)a.F;
+    const int* __restrict__ list = a.list;
+    const uint8_t* __restrict__ linfo = a.info;
+    const uint16_t* __restrict__ linst = a.list_inst;
+    const bool extrap = a.in.bc == 0;
+    const float coef1 = BATCHED ? 0.f : a.sc->coef;
+    const float Fc1 = BATCHED ? 0.f : (float)a.in.Fc;
+    const double gamma1 = a.in.gamma;
+    const int sy1 = a.in.tnx * TILE_PTS;
+    const int sz1 = a.in.tnx * a.in.tny * TILE_PTS;
+    const int stride = gridDim.x;
+    // halo sources of plane lz0 (plane lz0 + j: + 64 j elements)
+    const int x_off0 = xh ? (TILE_PTS + lz0 * 64 + ly * 8) : (-TILE_PTS + lz0 * 64 + ly * 8 + 7);
+    const unsigned x_bit = xh ? NB_XP : NB_XM;
+    const int y_in = (ly == 0) ? (lz0 * 64 + 56 + 4 * xh) : (lz0 * 64 + 4 * xh);
+    const int y_sgn = (ly == 0) ? -1 : 1;
+    const unsigned y_bit = (ly == 0) ? NB_YM : ((ly == 7) ? NB_YP : 0u);
+    const int y_slot0 = 128 + ((ly == 7) ? 16 : 0) + 2 * lz0 + xh;
+    // the lower half-warp stages the -z face, the upper half-warp the +z face
+    const int z_in = (lzq == 0) ? (448 + ly * 8 + 4 * xh) : (ly * 8 + 4 * xh);
+    const int z_sgn = (lzq == 0) ? -1 : 1;
+    const unsigned z_bit = (lzq == 0) ? NB_ZM : NB_ZP;
+    const int z_slot = 160 + ((lzq == 1) ? 16 : 0) + 2 * ly + xh;
+    const int y_off1 = y_sgn * sy1 + y_in;
+    const int z_off1 = z_sgn * sz1 + z_in;
+
+    const unsigned sm0 = (unsigned)__cvta_generic_to_shared(st);
+    constexpr unsigned SB = (unsigned)sizeof(Stage);
+    const unsigned a_c0 = sm0 + (unsigned)offsetof(Stage, v) + 16u * q0;
+    const unsigned a_f0 = sm0 + (unsigned)offsetof(Stage, f) + 16u * q0;
+    const unsigned a_x0 = sm0 + (unsigned)offsetof(Stage, xo) + 4u * q0;
+    const unsigned a_y0 = sm0 + (unsigned)offsetof(Stage, v) + 16u * y_slot0;
+    const unsigned a_z = sm0 + (unsigned)offsetof(Stage, v) + 16u * z_slot;
+
+    auto issue = [&](unsigned t, unsigned info, unsigned inst, int s) {
+        const unsigned base = t * TILE_PTS;
+        const float* tp = src + base;
+        const unsigned so = (unsigned)s * SB;
+        if (tid == 0) st[s].meta = make_int4((int)t, (int)info, (int)inst, 0);
+        int y_off = y_off1, z_off = z_off1;
+        if (BATCHED) {
+            const int tnx = a.insts[inst].tnx, tny = a.insts[inst].tny;
+            y_off = y_sgn * (tnx * TILE_PTS) + y_in;
+            z_off = z_sgn * (tnx * tny * TILE_PTS) + z_in;
+        }
+        const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cp_async16s(a_c0 + so + 256u * j, tp + 4 * q0 + 64 * j);
+            if (FIELD) cp_async16s(a_f0 + so + 256u * j, Fp + base + 4 * q0 + 64 * j);
+            cp_async4s(a_x0 + so + 64u * j, tp + x_off0 + 64 * j, px);
+            cp_async16s(a_y0 + so + 32u * j, tp + y_off + 64 * j, py);
+        }
+        cp_async16s(a_z + so, tp + z_off, (info & z_bit) != 0);
+    };
+    auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
+        k = ent(k);
+        t = (unsigned)__ldg(list + k);
+        info = __ldg(linfo + k);
+        inst = BATCHED ? (unsigned)__ldg(linst + k) : 0u;
+    };
+
+    int kn = blockIdx.x;
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s) {
+        if (kn < n) {
+            unsigned t, info, inst;
+            fetch(kn, t, info, inst);
+            issue(t, info, inst, s);
+        }
+        cp_async_commit();
+        kn += stride;
+    }
+    unsigned t1 = 0, i1 = 0, n1 = 0, t2 = 0, i2 = 0, n2 = 0;
+    if (kn < n) fetch(kn, t1, i1, n1);
+    if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
+    int cur = 0;
+    for (int k = blockIdx.x; k < n; k += stride) {
+        cp_async_wait<S - 2>();
+        __syncthreads();
+        {
+            const int sn = cur == 0 ? S - 1 : cur - 1;
+            if (kn < n) issue(t1, i1, n1, sn);
+            cp_async_commit();
+            kn += stride;
+            t1 = t2;
+            i1 = i2;
+            n1 = n2;
+            if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
+        }
+        const Stage& Sg = st[cur];
+        const int t = Sg.meta.x;
+        const unsigned info = (unsigned)Sg.meta.y;
+        const int inst = Sg.meta.z;
+        const float coef = BATCHED ? a.sc[inst].coef : coef1;
+        const float Fc = BATCHED ? a.sc[inst].Fc : Fc1;
+        float4 c[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[j] = Sg.v[q0 + 16 * j];
+        float* dp = dst + (unsigned)t * TILE_PTS;
+        float mn = __int_as_float(0x7f800000);
+        if (info == (NB_ALL | SG_POS)) {
+            quads4<1, false, FIELD, CLASSIFY>(Sg, c, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,
+                                              false, false, false, false, false, false, dp, mn);
+        } else if (info == (NB_ALL | SG_NEG)) {
+            quads4<-1, false, FIELD, CLASSIFY>(Sg, c, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,
+                                               false, false, false, false, false, false, dp, mn);
+        } else {
+            const bool xlo = (xh == 0) && !(info & NB_XM);
+            const bool xhi = (xh == 1) && !(info & NB_XP);
+            const bool ylo = (ly == 0) && !(info & NB_YM);
+            const bool yhi = (ly == 7) && !(info & NB_YP);
+            const bool zlo = (lzq == 0) && !(info & NB_ZM);
+            const bool zhi = (lzq == 1) && !(info & NB_ZP);
+            quads4<0, true, FIELD, CLASSIFY>(Sg, c, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,
+                                             xlo, xhi, ylo, yhi, zlo, zhi, dp, mn);
+        }
+        if (CLASSIFY) {
+            // the warp holds the whole tile: its minimum is the tile's
+            const unsigned wm = __reduce_min_sync(0xffffffffu, __float_as_uint(mn));
+            if (tid == 0) {
+                const double g = BATCHED ? a.insts[inst].gamma : gamma1;
+                a.core[t] = ((double)__uint_as_float(wm) < g) ? 1 : 0;
+            }
+        }
+        cur = cur + 1 == S ? 0 : cur + 1;
+    }
+    cp_async_wait<0>();
+}
+
+template <typename K>
+int occupancy_grid_z4(K kernel, size_t smem)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, 32, smem);
+    if (per < 1) per = 1;
+    return sms * per;
+}
+
+template <bool FIELD, bool CLS, bool BAT, int S>
+cudaError_t launch_z4(const StepArgs& a, int grid_pct, cudaStream_t s)
+{
+    constexpr size_t smem = sizeof(StageZ4<FIELD>) * S;
+    static int full = 0;
+    if (!full) full = occupancy_grid_z4(k_step_f32_z4<FIELD, CLS, BAT, S>, smem);
+    int grid = (int)((long long)full * grid_pct / 100);
+    if (grid < 1) grid = 1;
+    if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(32u);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step_f32_z4<FIELD, CLS, BAT, S>, a);
+}
+
+template <bool FIELD, bool CLS, bool BAT>
+cudaError_t launch_z4_s(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
+{
+    switch (cfg.stages) {
+    case 2: return launch_z4<FIELD, CLS, BAT, 2>(a, cfg.grid_pct, s);
+    case 4: return launch_z4<FIELD, CLS, BAT, 4>(a, cfg.grid_pct, s);
+    case 6: return launch_z4<FIELD, CLS, BAT, 6>(a, cfg.grid_pct, s);
+    default: return launch_z4<FIELD, CLS, BAT, 3>(a, cfg.grid_pct, s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_step_z4(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
+{
+    const bool field = a.F != nullptr;
+    const bool cls = a.core != nullptr;
+    const bool bat = a.list_inst != nullptr;
+    if (bat) {
+        if (field) return cls ? launch_z4_s<true, true, true>(a, cfg, s) : launch_z4_s<true, false, true>(a, cfg, s);
+        return cls ? launch_z4_s<false, true, true>(a, cfg, s) : launch_z4_s<false, false, true>(a, cfg, s);
+    }
+    if (field) return cls ? launch_z4_s<true, true, false>(a, cfg, s) : launch_z4_s<true, false, false>(a, cfg, s);
+    return cls ? launch_z4_s<false, true, false>(a, cfg, s) : launch_z4_s<false, false, false>(a, cfg, s);
+}
+
+}  // namespace lsk

@@ -65,6 +65,27 @@ def test_batch_matches_per_instance_oracle():
             assert np.max(np.abs(out[m] - o.phi[m])) <= 1e-5 * it.h * nsteps, k
 
 
+@pytest.mark.parametrize("ppt", [4, 16])
+def test_batch_step_configs_agree(ppt):
+    """The batched stencil with 4 or 16 points per thread computes the bits
+    of the 8-point one (constant speeds of both signs, instances whose bands
+    touch the domain faces, the tube test before each rebuild)."""
+    insts = small_batch(count=6, seed=11)
+    outs = []
+    for p in (8, ppt):
+        b, _ = make_batch(insts)
+        b.set_step_config(3, 100, p)
+        b.band_rebuild(4.0)
+        b.step(12, 0.5, ls.LS_DT_CFL, 5)
+        outs.append([b.get_phi_i(k) for k in range(len(insts))])
+        outs[-1].append([b.active_tiles_i(k) for k in range(len(insts))])
+        b.close()
+    for a, c in zip(outs[0][:-1], outs[1][:-1]):
+        assert np.array_equal(a, c)
+    for a, c in zip(outs[0][-1], outs[1][-1]):
+        assert np.array_equal(a, c)
+
+
 def test_batch_graph_replay_equals_eager():
     insts = small_batch(count=5, seed=9)
     outs = []
@@ -95,7 +116,7 @@ def test_single_grid_graph_and_autotune_bitwise():
         if mode == "tuned":
             g.step(1, 0.5, ls.LS_DT_CFL, 5)
             st, pct, ppt = g.autotune(reps=2)
-            assert st in (2, 3, 4, 6) and pct in (50, 75, 100) and ppt in (4, 8)
+            assert st in (2, 3, 4, 6) and pct in (50, 75, 100) and ppt in (4, 8, 16)
             g.step(11, 0.5, ls.LS_DT_CFL, 5)
         else:
             g.step(1, 0.5, ls.LS_DT_CFL, 5)
@@ -108,7 +129,8 @@ def test_single_grid_graph_and_autotune_bitwise():
     assert np.array_equal(outs[0], outs[2])
 
 
-@pytest.mark.parametrize("stages,pct,ppt", [(2, 50, 4), (4, 100, 8), (3, 75, 4), (2, 100, 8), (6, 100, 4), (6, 75, 8)])
+@pytest.mark.parametrize("stages,pct,ppt", [(2, 50, 4), (4, 100, 8), (3, 75, 4), (2, 100, 8), (6, 100, 4), (6, 75, 8),
+                                             (2, 100, 16), (3, 50, 16), (4, 75, 16), (6, 100, 16)])
 def test_step_configs_agree(stages, pct, ppt):
     """Every launch configuration computes the same bits (both stencil
     decompositions, constant and field speeds)."""
