@@ -142,30 +142,46 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the one-step stencil's source (the kernel file and the shared
-    per-point arithmetic it includes)."""
+    """Hash of the one-step FP32 stencils' source (the kernel files of the 4/8
+    and 16 points-per-thread decompositions and the shared per-point
+    arithmetic they include)."""
     h = hashlib.sha256()
-    for name in ("ls_step.cu", "ls_stencil.cuh"):
+    for name in ("ls_step.cu", "ls_step_z4.cu", "ls_stencil.cuh"):
         with open(os.path.join(ROOT, "paper_1612_04040_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per grid-point update of the step kernel from the last ncu
-    capture, if it was taken on the current kernel source (else None)."""
+STENCIL_KERNELS = {4: "k_step_f32 (128 threads per 8^3 tile, 4 points per thread)",
+                   8: "k_step_f32_z2 (64 threads per 8^3 tile, 8 points per thread)",
+                   16: "k_step_f32_z4 (one warp per 8^3 tile, 16 points per thread)"}
+
+
+def recorded_traffic(ppt):
+    """DRAM bytes per grid-point update of the step kernel with `ppt` points
+    per thread from the last ncu capture of that decomposition, if it was
+    taken on the current kernel source (else None).  The records in
+    profiles/stencil_traffic.txt are separated by blank lines."""
     path = os.path.join(ROOT, "profiles", "stencil_traffic.txt")
     if not os.path.exists(path):
         return None
-    d = {}
+    recs, d = [], {}
     with open(path) as f:
         for line in f:
-            if ":" in line and not line.startswith("#"):
+            if not line.strip():
+                if d:
+                    recs.append(d)
+                d = {}
+            elif ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 d[k.strip()] = v.strip()
-    if d.get("stencil_source_sha256_16") != kernel_source_hash():
-        return None
-    return float(d["dram_bytes_per_update"])
+    if d:
+        recs.append(d)
+    for d in recs:
+        if (d.get("stencil_source_sha256_16") == kernel_source_hash()
+                and int(d.get("points_per_thread", "0")) == int(ppt)):
+            return float(d["dram_bytes_per_update"])
+    return None
 
 
 class ClockSampler:
@@ -754,12 +770,12 @@ def main():
         tsp = prof["two_step_points"] - tsp0
         point_passes = updates - tsp
         achieved = (point_passes * BYTES_PER_UPDATE / 1e9) / stencil_s if stencil_s > 0 else None
-        tpu = recorded_traffic() if tsp == 0 else None
+        tpu = recorded_traffic(tuned[2]) if tsp == 0 else None
         traffic = tpu * updates / n_launch if tpu is not None else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                     "peak_kind": peak_kind,
-                    "kernel": "k_step_f32 (upwind step over the active 8^3 tiles)" if tsp == 0 else
+                    "kernel": STENCIL_KERNELS.get(tuned[2], "k_step_f32") if tsp == 0 else
                               "k_step2_f32 / k_step_f32 (two / one upwind steps per pass)",
                     "bytes_per_update": BYTES_PER_UPDATE * point_passes / max(updates, 1),
                     "avg_launch_us": 1e6 * stencil_s / n_launch, "launches": prof["stencil_timed"],
