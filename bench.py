@@ -423,7 +423,7 @@ def run_batch(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None, "traffic": None,
                          "peak_kind": peak_kind, "bytes_per_update": 8,
-                         "kernel": "k_step_f32 batched (eager profiled pass)",
+                         "kernel": STENCIL_KERNELS.get(ppt, "k_step_f32") + ", batched (eager profiled pass)",
                          "avg_launch_us": 1e6 * st_s / max(prof["stencil_timed"], 1)},
             "gpu_launches": launches,
         }), flush=True)
