@@ -193,6 +193,9 @@ struct StepConfig {
 cudaError_t launch_step(const StepArgs& a, int prec, const StepConfig& cfg, cudaStream_t s);
 // FP32 plain step with one warp per tile, 16 points per thread (ls_step_z4.cu)
 cudaError_t launch_step_z4(const StepArgs& a, const StepConfig& cfg, cudaStream_t s);
+// FP32 cut-off advance of the local scheme (a.op = OP_CUT / OP_CUT_CLAMP)
+// with one warp per tile (ls_local_z4.cu)
+cudaError_t launch_local_z4(const StepArgs& a, const StepConfig& cfg, cudaStream_t s);
 // FP64 step and local-scheme passes (ls_step64.cu)
 cudaError_t launch_step64(const StepArgs& a, cudaStream_t s);
 // two steps per pass (FP32 single grid, plain scheme; a.nact required);

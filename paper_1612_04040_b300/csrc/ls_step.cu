@@ -49,160 +49,6 @@ struct Stage32T {
     int4 meta;       // tile id, info byte, instance, face neighbours not active
 };
 
-// ------------------------------------------------- local scheme, FP32 ----
-// Eq. 7 at a = |phi|, branch-free: with s = (a - beta)/(gamma - beta) the
-// cubic is 1 - 3 s^2 + 2 s^3 (the paper's (a-gamma)^2 (2a + gamma - 3 beta)
-// / (gamma - beta)^3 expanded), s clamped to [0, 1].  The two end tests use
-// thresholds rounded outward on the host (largest float <= beta, smallest
-// float >= gamma), so they decide exactly as the FP64 comparisons do.
-__device__ __forceinline__ float cut32(float a, const LocalParams& lp)
-{
-    const float s = __saturatef((a - lp.beta_n) * lp.inv_w);
-    float c = fmaf(s * s, fmaf(2.f, s, -3.f), 1.f);
-    c = a < lp.gamma_up ? c : 0.f;
-    return a <= lp.beta_dn ? 1.f : c;
-}
-
-// Eq. 11 for the thread's four points: bit j set when point j or one of its
-// face neighbours inside the domain is in T (|phi| < gamma, FP64-exact
-// test), i.e. when the minimum of those |phi| is below gamma.  FACES: mask
-// the neighbours beyond the domain faces.
-template <bool FACES>
-__device__ __forceinline__ unsigned n_nibble(const float4& c, float xm0, float xp3, const float4& ym,
-                                             const float4& yp, const float4& zm, const float4& zp,
-                                             bool xlo, bool xhi, bool ylo, bool yhi, bool zlo,
-                                             bool zhi, float g)
-{
-    const float inf = __int_as_float(0x7f800000);
-    float a0 = fabsf(xm0), a5 = fabsf(xp3);
-    float4 Ym = ym, Yp = yp, Zm = zm, Zp = zp;
-    if (FACES) {
-        a0 = xlo ? inf : a0;
-        a5 = xhi ? inf : a5;
-        if (ylo) Ym = make_float4(inf, inf, inf, inf);
-        if (yhi) Yp = make_float4(inf, inf, inf, inf);
-        if (zlo) Zm = make_float4(inf, inf, inf, inf);
-        if (zhi) Zp = make_float4(inf, inf, inf, inf);
-    }
-    const float a1 = fabsf(c.x), a2 = fabsf(c.y), a3 = fabsf(c.z), a4 = fabsf(c.w);
-    const float p0 = fminf(a0, a1), p1 = fminf(a1, a2), p2 = fminf(a2, a3), p3 = fminf(a3, a4),
-                p4 = fminf(a4, a5);
-    const float px[4] = {fminf(p0, p1), fminf(p1, p2), fminf(p2, p3), fminf(p3, p4)};
-    unsigned nb = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float yz = fminf(fminf(fabsf(comp(Ym, j)), fabsf(comp(Yp, j))),
-                               fminf(fabsf(comp(Zm, j)), fabsf(comp(Zp, j))));
-        nb |= (fminf(px[j], yz) < g ? 1u : 0u) << j;
-    }
-    return nb;
-}
-
-// One pseudo-time iteration of Eq. 12 at the thread's four points (those
-// with their N bit set; the others keep their value): the upwind gradient of
-// Eq. 4 where d > 0 and of Eq. 5 where d < 0, S = d / sqrt(d^2 + |Dd|^2 h^2)
-// (Eq. 13) with unscaled differences (|Dd| h = sqrt(q)), then
-// d - dtau S (|grad d| - 1); CLAMP: Eq. 10 afterwards, to +-(smallest float
-// >= gamma), so that a clamped value stays outside T as in FP64.
-// SGN = +1 / -1: every N point of the warp has d >= 0 / d <= 0 (d = 0 gives
-// S = 0 on either path); SGN = 0: per point, through G-(d) = G+(-d).
-template <int SGN, bool FACES, bool CLAMP>
-__device__ __forceinline__ float4 rei4(const float4& c, float xm0, float xp3, const float4& ym,
-                                       const float4& yp, const float4& zm, const float4& zp,
-                                       unsigned nb, const LocalParams& lp, bool extrap, bool xlo,
-                                       bool xhi, bool ylo, bool yhi, bool zlo, bool zhi)
-{
-    const float xs[6] = {xm0, c.x, c.y, c.z, c.w, xp3};
-    float r[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float d = xs[j + 1];
-        float dmx = d - xs[j], dpx = xs[j + 2] - d;
-        float dmy = d - comp(ym, j), dpy = comp(yp, j) - d;
-        float dmz = d - comp(zm, j), dpz = comp(zp, j) - d;
-        if (FACES) {
-            if (j == 0 && xlo) dmx = extrap ? dpx : 0.f;
-            if (j == 3 && xhi) dpx = extrap ? dmx : 0.f;
-            if (ylo) dmy = extrap ? dpy : 0.f;
-            if (yhi) dpy = extrap ? dmy : 0.f;
-            if (zlo) dmz = extrap ? dpz : 0.f;
-            if (zhi) dpz = extrap ? dmz : 0.f;
-        }
-        float ax, bx, ay, by, az, bz;
-        if (SGN > 0) {
-            ax = fmaxf(dmx, 0.f); bx = fminf(dpx, 0.f);
-            ay = fmaxf(dmy, 0.f); by = fminf(dpy, 0.f);
-            az = fmaxf(dmz, 0.f); bz = fminf(dpz, 0.f);
-        } else if (SGN < 0) {
-            ax = fminf(dmx, 0.f); bx = fmaxf(dpx, 0.f);
-            ay = fminf(dmy, 0.f); by = fmaxf(dpy, 0.f);
-            az = fminf(dmz, 0.f); bz = fmaxf(dpz, 0.f);
-        } else {
-            const float s = d > 0.f ? 1.f : -1.f;
-            ax = fmaxf(s * dmx, 0.f); bx = fminf(s * dpx, 0.f);
-            ay = fmaxf(s * dmy, 0.f); by = fminf(s * dpy, 0.f);
-            az = fmaxf(s * dmz, 0.f); bz = fminf(s * dpz, 0.f);
-        }
-        float q = ax * ax;
-        q = fmaf(bx, bx, q);
-        q = fmaf(ay, ay, q);
-        q = fmaf(by, by, q);
-        q = fmaf(az, az, q);
-        q = fmaf(bz, bz, q);
-        const float gu = q * rsqrt_hw(fmaxf(q, 1e-30f));
-        const float S = d * rsqrt_hw(fmaxf(fmaf(d, d, q), 1e-30f));
-        float v = fmaf(-S, fmaf(lp.lam, gu, -lp.dtau_f), d);
-        if (CLAMP) v = fminf(fmaxf(v, -lp.gamma_up), lp.gamma_up);
-        r[j] = ((nb >> j) & 1u) ? v : d;
-    }
-    return make_float4(r[0], r[1], r[2], r[3]);
-}
-
-// the reinitialisation pass for one tile: warps without N points copy, warps
-// whose N points share one sign take the sign-specialised path
-template <bool FACES, bool CLAMP>
-__device__ __forceinline__ float4 rei_tile(const float4& c, float xm0, float xp3, const float4& ym,
-                                           const float4& yp, const float4& zm, const float4& zp,
-                                           unsigned nb, const LocalParams& lp, bool extrap,
-                                           bool xlo, bool xhi, bool ylo, bool yhi, bool zlo,
-                                           bool zhi)
-{
-    if (!__any_sync(0xffffffffu, nb != 0u)) return c;
-    const unsigned neg = (c.x < 0.f ? 1u : 0u) | (c.y < 0.f ? 2u : 0u) | (c.z < 0.f ? 4u : 0u) |
-                         (c.w < 0.f ? 8u : 0u);
-    const unsigned pos = (c.x > 0.f ? 1u : 0u) | (c.y > 0.f ? 2u : 0u) | (c.z > 0.f ? 4u : 0u) |
-                         (c.w > 0.f ? 8u : 0u);
-    if (__all_sync(0xffffffffu, (nb & neg) == 0u))
-        return rei4<1, FACES, CLAMP>(c, xm0, xp3, ym, yp, zm, zp, nb, lp, extrap, xlo, xhi, ylo,
-                                     yhi, zlo, zhi);
-    if (__all_sync(0xffffffffu, (nb & pos) == 0u))
-        return rei4<-1, FACES, CLAMP>(c, xm0, xp3, ym, yp, zm, zp, nb, lp, extrap, xlo, xhi, ylo,
-                                      yhi, zlo, zhi);
-    return rei4<0, FACES, CLAMP>(c, xm0, xp3, ym, yp, zm, zp, nb, lp, extrap, xlo, xhi, ylo, yhi,
-                                 zlo, zhi);
-}
-
-// N points that fall in inactive tiles: points of T on a face of this tile
-// whose face neighbour tile (bits `inact`: inside the domain, not active)
-// takes no part in the step, counted once per (point, face).  Zero while
-// the active tiles cover N (the tiled step then equals the pointwise one).
-__device__ __forceinline__ void count_breaches(const StepArgs& a, const float4& c, unsigned inact,
-                                               int xh, int ly, int lz)
-{
-    const float g = a.lp.gamma_up;
-    const unsigned tb = (fabsf(c.x) < g ? 1u : 0u) | (fabsf(c.y) < g ? 2u : 0u) |
-                        (fabsf(c.z) < g ? 4u : 0u) | (fabsf(c.w) < g ? 8u : 0u);
-    const unsigned nt = __popc(tb);
-    unsigned bad = 0;
-    if (xh == 0 && (tb & 1u) && (inact & NB_XM)) bad += 1;
-    if (xh == 1 && (tb & 8u) && (inact & NB_XP)) bad += 1;
-    if (ly == 0 && (inact & NB_YM)) bad += nt;
-    if (ly == 7 && (inact & NB_YP)) bad += nt;
-    if (lz == 0 && (inact & NB_ZM)) bad += nt;
-    if (lz == 7 && (inact & NB_ZP)) bad += nt;
-    if (bad && a.breaches) atomicAdd(a.breaches, (unsigned long long)bad);
-}
-
 // FIELD: speed field (else constant per instance); CLASSIFY: fused tube
 // test; BATCHED: list entries belong to different instances (per-entry
 // instance id, per-instance dt/h, speed, strides and gamma); S: stages;
@@ -726,6 +572,9 @@ cudaError_t launch32_op(const StepArgs& a, int grid_pct, cudaStream_t s)
 
 cudaError_t launch_local32(const StepArgs& a, const StepConfig& cfg, cudaStream_t s)
 {
+    // the advance with one warp per tile when the stencil uses it; the
+    // reinitialisation passes keep 4 points per thread (measured faster)
+    if (cfg.ppt == 16 && (a.op == OP_CUT || a.op == OP_CUT_CLAMP)) return launch_local_z4(a, cfg, s);
     const bool field = a.F != nullptr;
     const bool cls = a.core != nullptr;
     const int pct = cfg.grid_pct;

@@ -136,6 +136,30 @@ def test_fp32_trajectory():
     assert g.band_breaches() == 0 and o.breaches == 0
 
 
+@pytest.mark.parametrize("iters,full,Fc", [(K, False, None), (0, False, None), (-1, False, None),
+                                           (K, True, -0.8), (3, False, 0.6)])
+def test_one_warp_per_tile_passes_bitwise(iters, full, Fc):
+    """With 16 points per thread the cut-off advance runs one warp per tile
+    and computes the bits of the 4-point advance (the N bits and tile flags
+    that the reinitialisation passes then use, the clamp when there are no
+    reinitialisation iterations, the tube test, the breach count); speed
+    field and constant speeds, the full domain."""
+    phi, F = case(16)
+    outs = []
+    for ppt in (4, 16):
+        g, _ = make(ls.LS_FP32, phi, None if Fc is not None else F, Fc=Fc, full=full, iters=iters)
+        g.set_step_config(2, 100, ppt)
+        for n in (2, 3, 4):
+            g.step(n, 0.45, ls.LS_DT_CFL, 0 if full else 3)
+        outs.append((g.get_phi(), None if full else g.active_tiles(), g.band_breaches(),
+                     g.profile()["reinit_updates"]))
+    a, b = outs
+    assert np.array_equal(a[0].view(np.int32), b[0].view(np.int32))
+    if a[1] is not None:
+        assert np.array_equal(a[1], b[1])
+    assert a[2] == b[2] and a[3] == b[3]
+
+
 def test_graph_replay_matches_eager_bitwise():
     phi, F = case(15)
     a, _ = make(ls.LS_FP32, phi, F)
