@@ -67,13 +67,17 @@ def band_from(state, gamma):
     return oracle.compact(oracle.dilate(core, 26))
 
 
-def test_sphere_union_512():
-    """512^3 FP32, 20 spheres, sinusoidal F, band 6h, rebuild every 5, CFL 0.5."""
+@pytest.mark.parametrize("config", [(3, 100, 4), (2, 100, 16)])
+def test_sphere_union_512(config):
+    """512^3 FP32, 20 spheres, sinusoidal F, band 6h, rebuild every 5, CFL 0.5,
+    with 4 points per thread and with the one-warp-per-tile decomposition the
+    autotuner picks for this workload."""
     w = inputs.SphereUnion()
     dev = torch.device("cuda")
     phi0 = w.phi(device=dev).to(torch.float32).contiguous()
     F = w.speed(device=dev).to(torch.float32).contiguous()
     g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32)
+    g.set_step_config(*config)
     g.set_speed(F)
     g.set_phi(phi0)
     g.band_rebuild(w.halfwidth)
@@ -114,6 +118,7 @@ def test_maximum_grid_fp32():
     phi0 = inputs.sphere_union_sdf(shape, h, centres, radii, device=dev, out_dtype=torch.float32)
     F = inputs.speed_sinusoid(shape, h, device=dev, out_dtype=torch.float32)
     g = ls.LevelSet(nx, ny, nz, h, ls.LS_FP32)
+    g.set_step_config(2, 100, 16)  # the largest element offsets in the one-warp kernel
     g.set_speed(F)
     g.set_phi(phi0)
     del phi0
@@ -153,6 +158,8 @@ def test_perturbed_sphere_1024(perturbed_1024, prec, full_domain):
     dt_t = torch.float32 if prec == ls.LS_FP32 else torch.float64
     F = F64.to(dt_t).contiguous()
     g = ls.LevelSet(w.n, w.n, w.n, w.h, prec)
+    if prec == ls.LS_FP32:
+        g.set_step_config(2, 100 if not full_domain else 50, 16)  # the benchmark's picks
     g.set_speed(F)
     g.set_phi(phi64.to(dt_t).contiguous())
     if full_domain:
