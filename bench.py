@@ -157,11 +157,12 @@ STENCIL_KERNELS = {4: "k_step_f32 (128 threads per 8^3 tile, 4 points per thread
                    16: "k_step_f32_z4 (one warp per 8^3 tile, 16 points per thread)"}
 
 
-def recorded_traffic(ppt):
+def recorded_traffic(ppt, workload="sphere-union"):
     """DRAM bytes per grid-point update of the step kernel with `ppt` points
-    per thread from the last ncu capture of that decomposition, if it was
-    taken on the current kernel source (else None).  The records in
-    profiles/stencil_traffic.txt are separated by blank lines."""
+    per thread on `workload` from the last ncu capture of that
+    decomposition, if it was taken on the current kernel source (else
+    None).  The records in profiles/stencil_traffic.txt are separated by
+    blank lines; a record without a workload line is the sphere union's."""
     path = os.path.join(ROOT, "profiles", "stencil_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -179,7 +180,8 @@ def recorded_traffic(ppt):
         recs.append(d)
     for d in recs:
         if (d.get("stencil_source_sha256_16") == kernel_source_hash()
-                and int(d.get("points_per_thread", "0")) == int(ppt)):
+                and int(d.get("points_per_thread", "0")) == int(ppt)
+                and d.get("workload", "sphere-union") == workload):
             return float(d["dram_bytes_per_update"])
     return None
 
@@ -409,6 +411,7 @@ def run_batch(args):
     peak, peak_kind = measured_peaks()
     st_s = prof["stencil_ms"] / 1e3
     achieved = upd_prof * 8 / 1e9 / st_s if st_s > 0 else None
+    tpu_b = recorded_traffic(ppt, "batch")
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -421,7 +424,9 @@ def run_batch(args):
                        "l2": "inputs larger than L2 (phi 2 x 2.3 GB)"},
             "updates_per_step": updates / max(args.steps, 1),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "frac": achieved / peak if achieved else None,
+                         "traffic": (tpu_b * upd_prof / max(prof["stencil_timed"], 1))
+                                    if tpu_b is not None else None,
                          "peak_kind": peak_kind, "bytes_per_update": 8,
                          "kernel": STENCIL_KERNELS.get(ppt, "k_step_f32") + ", batched (eager profiled pass)",
                          "avg_launch_us": 1e6 * st_s / max(prof["stencil_timed"], 1)},
