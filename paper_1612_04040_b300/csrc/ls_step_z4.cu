@@ -6,10 +6,10 @@
 // quad's z neighbours are in its own registers, and the per-tile work
 // (list entry, staging addresses, branch on the tile's class, barrier) is
 // spread over 16 points instead of 4 (ls_step.cu) or 8.  The tube-test
-// minimum of a tile is one warp reduction (no shared-memory atomics).  Same
-// shared-memory stage layout as the 4-point kernel, same per-point arithmetic
-// (ls_stencil.cuh), so the results are the same bits for every choice of
-// points per thread.
+// minimum of a tile is one warp reduction (no shared-memory atomics).  The
+// 4-point kernel's stage layout without its speed block, the same per-point
+// arithmetic (ls_stencil.cuh), so the results are the same bits for every
+// choice of points per thread.
 #include <cstddef>
 
 #include "ls_internal.cuh"
@@ -19,27 +19,30 @@ namespace lsk {
 
 namespace {
 
-// one ring stage (the layout of the 4-point kernel's stage)
+// one ring stage (the layout of the 4-point kernel's stage, without the
+// speed block: each thread reads its own 16 speeds straight into registers
+// when it computes the tile -- they are nobody's neighbours -- which keeps
+// the stage at 3.6 KB and measured 5 % faster than staging them)
 template <bool FIELD>
 struct StageZ4 {
     float4 v[192];   // [0,128): centre quads; [128,160): y-halo runs [16*(ly==7) + 2*lz + xh];
                      // [160,192): z-halo runs [16*(lz==7) + 2*ly + xh]
-    float4 f[FIELD ? 128 : 1];
     float xo[128];   // x-halo value of each quad
     int4 meta;       // tile id, info byte, instance
 };
 
 // the four quads of one thread, one class of tile (SGN, FACES as upd4)
 template <int SGN, bool FACES, bool FIELD, bool CLASSIFY>
-__device__ __forceinline__ void quads4(const StageZ4<FIELD>& Sg, const float4 (&c)[4], float Fc,
-                                       float coef, bool extrap, int q0, int xh, int ly, int lzq,
+__device__ __forceinline__ void quads4(const StageZ4<FIELD>& Sg, const float4 (&c)[4],
+                                       const float4 (&fr)[4], float Fc, float coef, bool extrap,
+                                       int q0, int xh, int ly, int lzq,
                                        int y_slot0, int z_slot, bool xlo, bool xhi, bool ylo,
                                        bool yhi, bool zlo, bool zhi, float* dp, float& mn)
 {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int qj = q0 + 16 * j;
-        const float4 f = FIELD ? Sg.f[qj] : make_float4(Fc, Fc, Fc, Fc);
+        const float4 f = FIELD ? fr[j] : make_float4(Fc, Fc, Fc, Fc);
         const float4 ym = Sg.v[ly > 0 ? qj - 2 : y_slot0 + 2 * j];
         const float4 yp = Sg.v[ly < 7 ? qj + 2 : y_slot0 + 2 * j];
         const float4 zm = j > 0 ? c[j - 1] : Sg.v[lzq > 0 ? q0 - 16 : z_slot];
@@ -107,7 +110,6 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     const unsigned sm0 = (unsigned)__cvta_generic_to_shared(st);
     constexpr unsigned SB = (unsigned)sizeof(Stage);
     const unsigned a_c0 = sm0 + (unsigned)offsetof(Stage, v) + 16u * q0;
-    const unsigned a_f0 = sm0 + (unsigned)offsetof(Stage, f) + 16u * q0;
     const unsigned a_x0 = sm0 + (unsigned)offsetof(Stage, xo) + 4u * q0;
     const unsigned a_y0 = sm0 + (unsigned)offsetof(Stage, v) + 16u * y_slot0;
     const unsigned a_z = sm0 + (unsigned)offsetof(Stage, v) + 16u * z_slot;
@@ -127,7 +129,6 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             cp_async16s(a_c0 + so + 256u * j, tp + 4 * q0 + 64 * j);
-            if (FIELD) cp_async16s(a_f0 + so + 256u * j, Fp + base + 4 * q0 + 64 * j);
             cp_async4s(a_x0 + so + 64u * j, tp + x_off0 + 64 * j, px);
             cp_async16s(a_y0 + so + 32u * j, tp + y_off + 64 * j, py);
         }
@@ -174,16 +175,22 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         const int inst = Sg.meta.z;
         const float coef = BATCHED ? a.sc[inst].coef : coef1;
         const float Fc = BATCHED ? a.sc[inst].Fc : Fc1;
+        float4 fr[4];
+        if (FIELD) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                fr[j] = __ldg(reinterpret_cast<const float4*>(Fp + (size_t)t * TILE_PTS + 4 * q0 + 64 * j));
+        }
         float4 c[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[j] = Sg.v[q0 + 16 * j];
         float* dp = dst + (unsigned)t * TILE_PTS;
         float mn = __int_as_float(0x7f800000);
         if (info == (NB_ALL | SG_POS)) {
-            quads4<1, false, FIELD, CLASSIFY>(Sg, c, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,
+            quads4<1, false, FIELD, CLASSIFY>(Sg, c, fr, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,
                                               false, false, false, false, false, false, dp, mn);
         } else if (info == (NB_ALL | SG_NEG)) {
-            quads4<-1, false, FIELD, CLASSIFY>(Sg, c, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,
+            quads4<-1, false, FIELD, CLASSIFY>(Sg, c, fr, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,
                                                false, false, false, false, false, false, dp, mn);
         } else {
             const bool xlo = (xh == 0) && !(info & NB_XM);
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
             const bool yhi = (ly == 7) && !(info & NB_YP);
             const bool zlo = (lzq == 0) && !(info & NB_ZM);
             const bool zhi = (lzq == 1) && !(info & NB_ZP);
-            quads4<0, true, FIELD, CLASSIFY>(Sg, c, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,
+            quads4<0, true, FIELD, CLASSIFY>(Sg, c, fr, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,
                                              xlo, xhi, ylo, yhi, zlo, zhi, dp, mn);
         }
         if (CLASSIFY) {
