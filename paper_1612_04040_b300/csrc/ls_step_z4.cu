@@ -141,13 +141,18 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         inst = BATCHED ? (unsigned)__ldg(linst + k) : 0u;
     };
 
+    // tile ids of the staged entries in the order they are computed, so
+    // that a tile's speeds can be requested before the ring wait
+    unsigned tq[S - 1];
     int kn = blockIdx.x;
 #pragma unroll
     for (int s = 0; s < S - 1; ++s) {
+        tq[s] = 0u;
         if (kn < n) {
             unsigned t, info, inst;
             fetch(kn, t, info, inst);
             issue(t, info, inst, s);
+            tq[s] = t;
         }
         cp_async_commit();
         kn += stride;
@@ -157,12 +162,23 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
     int cur = 0;
     for (int k = blockIdx.x; k < n; k += stride) {
+        // this tile's speeds (each thread its own 16: nobody's neighbours),
+        // requested before the ring wait so that their latency overlaps it
+        float4 fr[4];
+        if (FIELD) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                fr[j] = __ldg(reinterpret_cast<const float4*>(Fp + (size_t)tq[0] * TILE_PTS + 4 * q0 + 64 * j));
+        }
         cp_async_wait<S - 2>();
         __syncthreads();
         {
             const int sn = cur == 0 ? S - 1 : cur - 1;
             if (kn < n) issue(t1, i1, n1, sn);
             cp_async_commit();
+#pragma unroll
+            for (int i = 0; i + 1 < S - 1; ++i) tq[i] = tq[i + 1];
+            tq[S - 2] = t1;
             kn += stride;
             t1 = t2;
             i1 = i2;
@@ -175,12 +191,6 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         const int inst = Sg.meta.z;
         const float coef = BATCHED ? a.sc[inst].coef : coef1;
         const float Fc = BATCHED ? a.sc[inst].Fc : Fc1;
-        float4 fr[4];
-        if (FIELD) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                fr[j] = __ldg(reinterpret_cast<const float4*>(Fp + (size_t)t * TILE_PTS + 4 * q0 + 64 * j));
-        }
         float4 c[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[j] = Sg.v[q0 + 16 * j];
