@@ -143,10 +143,11 @@ def measured_peaks():
 
 def kernel_source_hash():
     """Hash of the one-step FP32 stencils' source (the kernel files of the 4/8
-    and 16 points-per-thread decompositions and the shared per-point
-    arithmetic they include)."""
+    and 16 points-per-thread decompositions, the shared per-point
+    arithmetic they include, and the band kernels, which mark the frozen
+    x-faces the one-warp kernel reads from their copies)."""
     h = hashlib.sha256()
-    for name in ("ls_step.cu", "ls_step_z4.cu", "ls_stencil.cuh"):
+    for name in ("ls_step.cu", "ls_step_z4.cu", "ls_stencil.cuh", "ls_band.cu"):
         with open(os.path.join(ROOT, "paper_1612_04040_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -602,6 +603,13 @@ def run_perturbed(args):
             if tuned is not None:
                 line["autotuned"] = {"stages": tuned[0], "grid_pct": tuned[1], "points_per_thread": tuned[2],
                                      "steps_per_pass": g.steps_per_pass()}
+            if prec == ls.LS_FP32 and st > 0:
+                peak, peak_kind = measured_peaks()
+                gbps = u * bpu / 1e9 / st
+                line["roofline"] = {"bound": "hbm", "achieved": gbps, "peak": peak, "unit": "GB/s",
+                                    "frac": gbps / peak, "traffic": None, "peak_kind": peak_kind,
+                                    "kernel": STENCIL_KERNELS.get(tuned[2], "k_step_f32") if tuned
+                                              else "k_step_f32", "bytes_per_update": bpu}
             if prec == ls.LS_FP64 and st > 0:
                 ach = u * FLOPS_PER_UPDATE_F64 / st / 1e12
                 line["roofline"] = {"bound": "fp64", "achieved": ach, "peak": dfma, "unit": "TFLOP/s",

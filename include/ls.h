@@ -73,7 +73,9 @@ enum { LS_BC_EXTRAPOLATE = 0, LS_BC_NEUMANN = 1 };
 /* Create a context for an nx*ny*nz grid with spacing h (section 1, Eq. 3).
  * nx, ny, nz: multiples of 8, >= 8, nx*ny*nz <= 2^31; h > 0 and finite;
  * precision LS_FP32 or LS_FP64.  Allocates two phi buffers (ping-pong), the
- * speed field and the tile tables on the current CUDA device.
+ * speed field and the tile tables on the current CUDA device (FP32: also 512
+ * bytes per tile for copies of the x-faces of frozen tiles next to the band,
+ * one eighth of a phi buffer).
  * Errors: LS_EINVAL (sizes, h, precision, out == NULL), LS_ENOMEM, LS_ECUDA. */
 int ls_create(int nx, int ny, int nz, double h, int precision, ls_ctx **out);
 

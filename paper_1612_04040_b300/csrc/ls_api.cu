@@ -141,7 +141,7 @@ void free_all(ls_ctx* c)
                     c->d_Mbits, c->d_updates, c->d_status, c->d_inst,
                     c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params, c->nmask,
                     c->d_breaches, c->list_nact, c->nmask2, c->nflag, c->nl, c->nl_info,
-                    c->d_ncount, c->d_rupdates, c->d_done, c->d_updates2};
+                    c->d_ncount, c->d_rupdates, c->d_done, c->d_updates2, c->xface};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_nonfinite) cudaFreeHost(c->h_nonfinite);
@@ -223,8 +223,13 @@ int speed_mode(const ls_ctx* c)
 
 const uint8_t* sign_table(const ls_ctx* c) { return speed_mode(c) == 2 ? c->tile_sgn : nullptr; }
 
-int finish_rebuild(ls_ctx* c, cudaStream_t s)
+// incr: the band was valid before this rebuild (no value changed since the
+// previous one other than by the steps)
+int finish_rebuild(ls_ctx* c, bool incr, cudaStream_t s)
 {
+    // the frozen x-face copies: only the new faces are filled when every face
+    // of the previous band was (a filling step ran since that rebuild)
+    const int xmode = c->xface ? (incr && !c->xface_pending ? 2 : 1) : 0;
     void* cur = c->phi[c->cur];
     void* other = c->phi[c->cur ^ 1];
     const void* tmf = speed_mode(c) == 2 ? c->tile_maxF : nullptr;
@@ -239,7 +244,8 @@ int finish_rebuild(ls_ctx* c, cudaStream_t s)
         KL(c, lsk::launch_scatter(c->act, c->block_counts, c->list, c->list_info, sign_table(c),
                                   const_sign_bits(c), c->in0(), c->ntiles, tmf, c->prec,
                                   c->d_Mbits, cur, other, c->list_nact, c->d_sc, c->dt_mode,
-                                  c->dt_value, c->d_count, c->d_done + 1, s));
+                                  c->dt_value, c->d_count, c->d_done + 1, xmode, s));
+        c->xface_pending = xmode != 0;
     }
     return LS_OK;
 }
@@ -254,13 +260,14 @@ struct NvtxRange {
 int rebuild(ls_ctx* c, bool full_scan, cudaStream_t s)
 {
     NvtxRange range("ls band rebuild");
+    const bool incr = c->band_valid;
     void* cur = c->phi[c->cur];
     if (full_scan || !c->core_fresh)
         KL(c, lsk::launch_classify_all(cur, c->core, c->dinst(), c->tinst(), c->in0(), c->ntiles,
                                        c->prec, s));
     KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, c->dinst(), c->tinst(), c->in0(),
                              c->ntiles, c->d_done, c->d_count, c->dilation, s));
-    RET(finish_rebuild(c, s));
+    RET(finish_rebuild(c, incr, s));
     c->band_valid = true;
     c->core_fresh = false;
     c->since_rebuild = 0;
@@ -275,7 +282,7 @@ int full_domain_bound(ls_ctx* c, cudaStream_t s)
         CK(cudaMemsetAsync(c->core, 1, c->ntiles, s));
         KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, c->d_inst, c->d_tile_inst,
                                  c->in0(), c->ntiles, c->d_done, c->d_count, 26, s));
-        RET(finish_rebuild(c, s));
+        RET(finish_rebuild(c, false, s));
     } else {
         // every tile counts as active, so a later switch back to a band copies
         // every tile that leaves the active set into the other buffer
@@ -307,6 +314,16 @@ lsk::StepArgs step_args(ls_ctx* c, bool classify)
     a.updates = c->d_updates;
     a.in = c->in0();
     a.max_grid = c->full_domain ? (int)(c->ntiles < (1 << 30) ? c->ntiles : (1 << 30)) : 0;
+    // copies of the frozen x-faces (plain scheme: no pass between rebuilds
+    // writes a tile outside the list), read by the DRAM-bound one-warp
+    // kernel; the 4- and 8-point kernels, bound by instruction issue, read
+    // every x-face in place (the copies measured no faster there)
+    if (c->xface && !c->full_domain && c->scheme == LS_SCHEME_PLAIN && c->step_mode == LS_PLAIN &&
+        c->cfg.ppt == 16) {
+        a.xface = c->xface;
+        a.xface_fill = c->xface_pending ? 1 : 0;
+        a.nact = c->list_nact;
+    }
     return a;
 }
 
@@ -475,6 +492,7 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
                 KL(c, lsk::launch_dense_step(a, c->cfg, s));
             } else {
                 KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
+                if (a.xface_fill) c->xface_pending = false;  // this step wrote the copies
             }
             ++c->stencil_launches;
             c->dir ^= 1;
@@ -514,6 +532,7 @@ SchedState save_state(const ls_ctx* c)
     st.band_valid = c->band_valid;
     st.core_fresh = c->core_fresh;
     st.dir = c->dir;
+    st.xface_pending = c->xface_pending;
     return st;
 }
 
@@ -524,6 +543,7 @@ void load_state(ls_ctx* c, const SchedState& st)
     c->band_valid = st.band_valid;
     c->core_fresh = st.core_fresh;
     c->dir = st.dir;
+    c->xface_pending = st.xface_pending;
 }
 
 cudaStream_t work_stream(ls_ctx* c)
@@ -544,7 +564,9 @@ int run_steps_graph(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuil
     long long vbits = 0;
     std::memcpy(&vbits, &value, sizeof(vbits));
     const GraphKey key{c->cur, c->since_rebuild, (int)c->band_valid, (int)c->core_fresh,
-                       (int)c->full_domain | (c->step_mode << 1) | (c->scheme << 3), nsteps,
+                       (int)c->full_domain | (c->step_mode << 1) | (c->scheme << 3) |
+                           ((int)c->xface_pending << 5),
+                       nsteps,
                        rebuild_every, dt_mode, vbits,
                        c->cfg.stages * 16 + c->cfg.ppt + 256 * c->cfg.spp, c->cfg.grid_pct, c->dir};
     auto it = c->graphs.find(key);
@@ -639,6 +661,8 @@ int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h
     A(dalloc(&c->d_updates2, sizeof(unsigned long long)));
     if (e == cudaSuccess) e = cudaMemset(c->d_updates2, 0, sizeof(unsigned long long));
     if (!batched && precision == LS_FP32) A(dalloc(&c->list_nact, c->ntiles));
+    if (!batched && precision == LS_FP32)
+        A(dalloc(&c->xface, (size_t)c->ntiles * lsk::XFACE_FLOATS * sizeof(float)));
     if (e == cudaSuccess) e = cudaMemset(c->d_done, 0, 4 * sizeof(unsigned));
     A(dalloc(&c->block_counts, c->nblocks * sizeof(int)));
     A(dalloc(&c->d_sc, sizeof(lsk::StepScalars) * n));

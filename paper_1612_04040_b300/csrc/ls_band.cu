@@ -465,6 +465,15 @@ __device__ __forceinline__ unsigned long long ordered_bits(T v)
 // leaving the active set get their current values copied into the other
 // ping-pong buffer (the whole block copies them together), so both buffers
 // agree on every inactive tile.
+// xface_mode (FP32 single grid; the steps read the x-faces of frozen x
+// neighbours from a compact copy, see StepArgs::xface): 0 off; 1 every
+// entry's frozen x-faces get their fill bit in list_nact (NACT_FILL_XM /
+// _XP: the next filling step reads them in place and writes the copy);
+// 2 the copies of the previous band are complete and no value has changed
+// since other than by the steps, so only faces whose tile was not active
+// before or whose neighbour was (bit 1 of act: active at the previous
+// rebuild) get the bit -- a frozen tile keeps its values while it stays
+// frozen.
 template <typename T>
 __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act,
                                                  const int* __restrict__ offsets, int* list,
@@ -476,7 +485,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
                                                  const uint4* __restrict__ cur, uint4* other,
                                                  uint8_t* list_nact, StepScalars* sc, int dt_mode,
                                                  double dt_value, const int* count,
-                                                 unsigned* done)
+                                                 unsigned* done, int xface_mode)
 {
     __shared__ int warp_cnt[8];
     __shared__ int warp_leave[8];
@@ -517,7 +526,14 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
         list[pos] = (int)t;
         const unsigned nb = nb_bits(t, single);
         list_info[pos] = (uint8_t)(nb | (tile_sgn ? tile_sgn[t] : const_sgn));
-        if (list_nact) list_nact[pos] = (uint8_t)active_nb_bits(t, nb, single, act);
+        if (list_nact) {
+            unsigned an = active_nb_bits(t, nb, single, act);
+            const unsigned fz = nb & ~an;
+            const bool was = xface_mode == 2 && (fl & 2);
+            if (xface_mode && (fz & NB_XM) && !(was && !(act[t - 1] & 2))) an |= NACT_FILL_XM;
+            if (xface_mode && (fz & NB_XP) && !(was && !(act[t + 1] & 2))) an |= NACT_FILL_XP;
+            list_nact[pos] = (uint8_t)an;
+        }
     }
     if (leaving) leave_ids[lbefore + __popc(bl & below)] = (int)t;
     if (threadIdx.x == 0 && tile_maxF) {
@@ -806,18 +822,18 @@ cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* li
                            const Inst& single, long long ntiles, const void* tile_maxF, int prec,
                            unsigned long long* Mbits, const void* cur, void* other,
                            uint8_t* list_nact, StepScalars* sc, int dt_mode, double dt_value,
-                           const int* count, unsigned* done, cudaStream_t s)
+                           const int* count, unsigned* done, int xface_mode, cudaStream_t s)
 {
     const int nb = (int)((ntiles + 255) / 256);
     if (prec == 0)
         return launch_after(k_scatter<float>, nb, 256, s, act, block_offsets, list, list_info,
                             tile_sgn, const_sgn, single, ntiles, (const float*)tile_maxF, Mbits,
                             (const uint4*)cur, (uint4*)other, list_nact, sc, dt_mode, dt_value,
-                            count, done);
+                            count, done, xface_mode);
     return launch_after(k_scatter<double>, nb, 256, s, act, block_offsets, list, list_info,
                         tile_sgn, const_sgn, single, ntiles, (const double*)tile_maxF, Mbits,
                         (const uint4*)cur, (uint4*)other, list_nact, sc, dt_mode, dt_value, count,
-                        done);
+                        done, 0);
 }
 
 cudaError_t launch_scatter_batch(const uint8_t* act, const int* block_offsets, int* list,

@@ -44,6 +44,7 @@ struct SchedState {
     bool band_valid = false;
     bool core_fresh = false;
     int dir = 0;
+    bool xface_pending = false;
 };
 
 using GraphKey = std::tuple<int, int, int, int, int, int, int, int, long long, int, int, int>;
@@ -135,6 +136,8 @@ struct ls_ctx {
     int reinit_iters = -1;
     uint32_t* nmask = nullptr;                 // N bits, 16 words per list entry
     uint8_t* list_nact = nullptr;              // active face neighbours per list entry
+    float* xface = nullptr;                    // frozen x-face copies per tile (FP32 single grid)
+    bool xface_pending = false;                // some copy of the current band is unwritten
     uint8_t* nflag = nullptr;                  // per list entry: the tile holds a point of N
     int* nl = nullptr;                         // tiles holding N points (ascending) ...
     uint8_t* nl_info = nullptr;                // ... their info bytes ...

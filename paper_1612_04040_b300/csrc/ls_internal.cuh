@@ -18,6 +18,7 @@ namespace lsk {
 
 constexpr int TILE = 8;
 constexpr int TILE_PTS = TILE * TILE * TILE;
+constexpr int XFACE_FLOATS = 2 * TILE * TILE;  // two x-faces of one tile
 
 // Per-instance parameters (one entry per independent grid).
 struct Inst {
@@ -51,6 +52,9 @@ enum : unsigned {
     NB_ALL = 63u,
     SG_POS = 64u,   // every F >= 0 in the tile (G+ of Eq. 4 everywhere)
     SG_NEG = 128u,  // every F < 0 in the tile (G- of Eq. 5 everywhere)
+    // list_nact bits above the NB_* bits: the x-face copy of the frozen
+    // -x / +x neighbour is still to be written (StepArgs::xface_fill)
+    NACT_FILL_XM = NB_XM << 6, NACT_FILL_XP = NB_XP << 6,
 };
 
 // Per-step scalars on the device, one per instance.
@@ -113,7 +117,7 @@ cudaError_t launch_scatter(const uint8_t* act, const int* block_offsets, int* li
                            const Inst& single, long long ntiles, const void* tile_maxF, int prec,
                            unsigned long long* Mbits, const void* cur, void* other,
                            uint8_t* list_nact, StepScalars* sc, int dt_mode, double dt_value,
-                           const int* count, unsigned* done, cudaStream_t s);
+                           const int* count, unsigned* done, int xface_mode, cudaStream_t s);
 // full-domain list: every tile, ascending, with info bytes; *count = ntiles
 cudaError_t launch_full_list(int* list, uint8_t* list_info, const uint8_t* tile_sgn,
                              unsigned const_sgn, const Inst& single, long long ntiles, int* count,
@@ -177,6 +181,17 @@ struct StepArgs {
     const uint8_t* nact;      // per entry: face neighbours inside the domain that are
                               // active (NB_* bits; breach test)
     unsigned long long* breaches;  // N points found in inactive tiles
+    // FP32 plain step, single grid: copies of the x-faces of the entries'
+    // frozen x neighbours (inside the domain, not active: bits of nact),
+    // XFACE_FLOATS per tile id, [side][lz][ly] (side 0: the x = 7 column of
+    // tile t - 1, side 1: the x = 0 column of tile t + 1).  A frozen tile
+    // keeps its values until the next rebuild, so the copy is read in 256-byte
+    // runs by every step instead of one 32-byte sector per value.  NULL: every
+    // x-halo value is read from the neighbour tile.
+    float* xface;
+    // 1: faces whose NACT_FILL bit is set are read from the neighbour and
+    // their copy written (the first plain step after a rebuild)
+    int xface_fill;
 };
 
 // launch configuration of the FP32 stencil, chosen by the autotuner

@@ -106,6 +106,13 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     const int z_slot = 160 + ((lzq == 1) ? 16 : 0) + 2 * ly + xh;
     const int y_off1 = y_sgn * sy1 + y_in;
     const int z_off1 = z_sgn * sz1 + z_in;
+    // a frozen x neighbour's face from its copy (single grid): value
+    // (lz0 + j, ly) of this thread's side at xf_off0 + 8 j; faces with their
+    // fill bit are read in place by a filling launch, which writes the copy
+    float* __restrict__ xf = BATCHED ? nullptr : a.xface;
+    const bool xfill = a.xface_fill != 0;
+    const int xf_off0 = xh * 64 + lz0 * 8 + ly;
+    const unsigned fill_bit = x_bit << 6;  // NACT_FILL_XM / _XP
 
     const unsigned sm0 = (unsigned)__cvta_generic_to_shared(st);
     constexpr unsigned SB = (unsigned)sizeof(Stage);
@@ -126,10 +133,14 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
             z_off = z_sgn * (tnx * tny * TILE_PTS) + z_in;
         }
         const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0;
+        // inst: the entry's active face-neighbour and fill bits when xf is set
+        const bool fz = !BATCHED && xf && (info & ~inst & x_bit) != 0 && !(xfill && (inst & fill_bit));
+        const float* xs = fz ? xf + (size_t)t * XFACE_FLOATS + xf_off0 : tp + x_off0;
+        const int xstep = fz ? 8 : 64;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             cp_async16s(a_c0 + so + 256u * j, tp + 4 * q0 + 64 * j);
-            cp_async4s(a_x0 + so + 64u * j, tp + x_off0 + 64 * j, px);
+            cp_async4s(a_x0 + so + 64u * j, xs + xstep * j, px);
             cp_async16s(a_y0 + so + 32u * j, tp + y_off + 64 * j, py);
         }
         cp_async16s(a_z + so, tp + z_off, (info & z_bit) != 0);
@@ -138,7 +149,7 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         k = ent(k);
         t = (unsigned)__ldg(list + k);
         info = __ldg(linfo + k);
-        inst = BATCHED ? (unsigned)__ldg(linst + k) : 0u;
+        inst = BATCHED ? (unsigned)__ldg(linst + k) : (xf ? (unsigned)__ldg(a.nact + k) : 0u);
     };
 
     // tile ids of the staged entries in the order they are computed, so
@@ -195,6 +206,10 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[j] = Sg.v[q0 + 16 * j];
         float* dp = dst + (unsigned)t * TILE_PTS;
+        if (!BATCHED && xfill && ((unsigned)inst & fill_bit)) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xf[(size_t)t * XFACE_FLOATS + xf_off0 + 8 * j] = Sg.xo[q0 + 16 * j];
+        }
         float mn = __int_as_float(0x7f800000);
         if (info == (NB_ALL | SG_POS)) {
             quads4<1, false, FIELD, CLASSIFY>(Sg, c, fr, Fc, coef, extrap, q0, xh, ly, lzq, y_slot0, z_slot,

@@ -180,13 +180,18 @@ def test_fp64_neumann_faces_bitwise():
 
 # ------------------------------------------------------------------ FP32 ----
 
-def test_fp32_sphere_union_reduced_size():
+@pytest.mark.parametrize("config", [None, (2, 100, 8), (2, 100, 16)])
+def test_fp32_sphere_union_reduced_size(config):
     """The 512^3 sphere-union recipe at 128^3 (same seeds, centres, radii and
     F), 60 steps: band sets identical at every rebuild, phi within
-    1e-5 h nsteps on the final band."""
+    1e-5 h nsteps on the final band.  Each stencil decomposition (4, 8, 16
+    points per thread), all of which read the x-faces of frozen neighbours
+    from the copy the rebuild makes."""
     w = inputs.SphereUnion(n=128)
     shape = (w.n,) * 3
     g, o = make_pair(shape, w.h, ls.LS_FP32, w.phi().numpy(), F=w.speed().numpy())
+    if config:
+        g.set_step_config(*config)
     assert g.band_rebuild(w.halfwidth) == o.band_rebuild(w.halfwidth)
     nsteps = 0
     for n in (5,) * 12:
@@ -199,6 +204,37 @@ def test_fp32_sphere_union_reduced_size():
     m = tile_mask(o.active, shape)
     err = np.max(np.abs(out[m] - o.phi[m]))
     assert err <= 1e-5 * w.h * nsteps, err
+
+
+@pytest.mark.parametrize("ppt", [4, 8, 16])
+def test_fp32_frozen_face_copies_follow_the_band(ppt):
+    """The steps read the x-faces of frozen neighbours from copies made after
+    each rebuild; the copies stay right through rebuilds with no step
+    between them, graph replay in uneven chunks, the autotuner's probe
+    launches and a new phi in the middle of a run (oracle parity on the
+    band, identical band sets)."""
+    w = inputs.SphereUnion(n=64, count=6)
+    shape = (w.n,) * 3
+    F = w.speed().numpy()
+    g, o = make_pair(shape, w.h, ls.LS_FP32, w.phi().numpy(), F=F)
+    g.set_step_config(2, 100, ppt)
+    for _ in range(2):  # two rebuilds, no step between them
+        assert g.band_rebuild(w.halfwidth) == o.band_rebuild(w.halfwidth)
+    g.set_graphs(True)
+    run_chunks(g, o, [3, 4, 3, 5, 5, 2], w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+    g.autotune(reps=1)
+    g.set_step_config(2, 100, ppt)
+    run_chunks(g, o, [6, 4], w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+    # a new level set (the spheres moved by 3h): a full rebuild, new copies
+    w2 = inputs.SphereUnion(n=64, count=6)
+    w2.centres = [(x + 3 * w.h, y, z) for (x, y, z) in w2.centres]
+    p2 = w2.phi().numpy().astype(np.float32)
+    g.set_phi(p2)
+    o.set_phi(p2.astype(np.float64))
+    run_chunks(g, o, [5, 5, 1, 4], w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+    out = g.get_phi().astype(np.float64)
+    m = tile_mask(o.active, shape)
+    assert np.max(np.abs(out[m] - o.phi[m])) <= 1e-5 * w.h * 15
 
 
 def test_fp32_tube_test_matches_oracle_on_gpu_snapshot():
