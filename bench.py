@@ -64,7 +64,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["mine", "reference"], default="mine")
     p.add_argument("--grid", type=int, default=512, help="grid edge (512 = the standard workload)")
-    p.add_argument("--e2e-steps", type=int, default=6)
+    p.add_argument("--e2e-steps", type=int, default=-1,
+                   help="problems in the end-to-end measurement (-1: as many as --steps; 0: skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", choices=["sphere-union", "batch", "learned", "perturbed", "sphere64", "local"],
                    default="sphere-union",
@@ -89,7 +90,10 @@ def parse():
     p.add_argument("--step-config", default=None, metavar="STAGES,GRID_PCT,PPT",
                    help="fix the stencil launch configuration instead of autotuning it "
                         "(so that a profiler run times the same kernel as the plain run)")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.e2e_steps < 0:
+        a.e2e_steps = a.steps  # the end-to-end run covers as many problems as the timed one
+    return a
 
 
 def tune(obj, args):
