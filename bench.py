@@ -145,6 +145,9 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+PROFILE_EVERY = 5  # plain scheme: one run of stencil launches in 5 timed with CUDA events
+
+
 def kernel_source_hash():
     """Hash of the one-step FP32 stencils' source (the kernel files of the 4/8
     and 16 points-per-thread decompositions, the shared per-point
@@ -745,7 +748,13 @@ def main():
     g.reset_profile()
     r0 = g.profile()["reinit_updates"]
     tsp0 = g.profile()["two_step_points"]
-    g.profile_enable(True)
+    # the plain scheme's runs of stencil launches (the up to 5 steps between
+    # two rebuilds) are timed one in PROFILE_EVERY: an event record between
+    # two launches costs the next one its overlap with the previous one
+    # (measured: 2 % of the step with every run timed); the local scheme and
+    # two steps per pass time every run
+    prof_every = PROFILE_EVERY if (not local_scheme and spp == 1) else 1
+    g.profile_enable(prof_every)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -783,20 +792,25 @@ def main():
     if not local_scheme:
         stencil_s = prof["stencil_ms"] / 1e3
         n_launch = max(prof["stencil_timed"], 1)
+        upd_timed = prof["stencil_updates"]
         # a two-step pass reads phi and F and writes phi once for two updates
+        # (with two steps per pass every run is timed)
         tsp = prof["two_step_points"] - tsp0
-        point_passes = updates - tsp
+        point_passes = upd_timed - tsp if prof_every == 1 else upd_timed
         achieved = (point_passes * BYTES_PER_UPDATE / 1e9) / stencil_s if stencil_s > 0 else None
         tpu = recorded_traffic(tuned[2]) if tsp == 0 else None
-        traffic = tpu * updates / n_launch if tpu is not None else None
+        traffic = tpu * upd_timed / n_launch if tpu is not None else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                     "peak_kind": peak_kind,
                     "kernel": STENCIL_KERNELS.get(tuned[2], "k_step_f32") if tsp == 0 else
                               "k_step2_f32 / k_step_f32 (two / one upwind steps per pass)",
-                    "bytes_per_update": BYTES_PER_UPDATE * point_passes / max(updates, 1),
-                    "avg_launch_us": 1e6 * stencil_s / n_launch, "launches": prof["stencil_timed"],
-                    "share_of_step_time": stencil_s / t_s if t_s > 0 else None}
+                    "bytes_per_update": BYTES_PER_UPDATE * point_passes / max(upd_timed, 1),
+                    "avg_launch_us": 1e6 * stencil_s / n_launch,
+                    "launches": prof["stencil_launches"], "launches_timed": prof["stencil_timed"],
+                    "timed_runs": "one run of back-to-back stencil launches in %d" % prof_every,
+                    "share_of_step_time": (stencil_s / n_launch * prof["stencil_launches"] / t_s)
+                                          if t_s > 0 else None}
     else:
         # the advance covers the active tiles: read phi and F, write phi and the
         # N mask (64 B per tile); the reinitialisation passes (K per step)

@@ -313,14 +313,21 @@ typedef struct {
     unsigned long long two_step_points;  /* points passed by two-step passes (each
                                             counted once, updated twice) since the
                                             context was created                     */
+    unsigned long long stencil_updates;  /* point updates of the launches stencil_ms
+                                            covers (reinitialisation point-iterations
+                                            included)                               */
 } ls_profile;
 
-/* Enable (1) or disable (0) CUDA-event timing of the upwind-step launches:
- * one event pair, recorded on the context's stream, brackets each run of
- * back-to-back stencil launches of one kind (the plain step or the local
+/* Enable (on >= 1) or disable (0) CUDA-event timing of the upwind-step
+ * launches: one event pair, recorded on the context's stream, brackets a run
+ * of back-to-back stencil launches of one kind (the plain step or the local
  * scheme's advance; the reinitialisation passes), so stencil_ms is their
- * summed device time including the gaps between them and stencil_timed the
- * number of launches it covers.  Any other kernel ends a run. */
+ * summed device time including the gaps between them, stencil_timed the
+ * number of launches it covers and stencil_updates their point updates.  Any
+ * other kernel ends a run.  on = N times one run in N (the first of every N
+ * since the call): an event record between two launches costs the next
+ * launch its overlap with the previous one, so sampling disturbs the timed
+ * work less.  Errors: LS_EINVAL (on < 0). */
 int ls_profile_enable(ls_ctx *ctx, int on);
 
 /* Read the counters (synchronises the stream).  Errors: LS_EINVAL. */

@@ -141,7 +141,8 @@ void free_all(ls_ctx* c)
                     c->d_Mbits, c->d_updates, c->d_status, c->d_inst,
                     c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params, c->nmask,
                     c->d_breaches, c->list_nact, c->nmask2, c->nflag, c->nl, c->nl_info,
-                    c->d_ncount, c->d_rupdates, c->d_done, c->d_updates2, c->xface};
+                    c->d_ncount, c->d_rupdates, c->d_done, c->d_updates2, c->xface,
+                    c->d_updates_timed};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_nonfinite) cudaFreeHost(c->h_nonfinite);
@@ -365,6 +366,11 @@ lsk::LocalParams local_params(const ls_ctx* c)
 int prof_close(ls_ctx* c, cudaStream_t s)
 {
     if (!c->ev_open) return LS_OK;
+    if (c->ev_skip) {
+        c->ev_open = false;
+        c->ev_skip = false;
+        return LS_OK;
+    }
     cudaEvent_t e1 = nullptr;
     CK(take_event(c, &e1));
     CK(cudaEventRecord(e1, s));
@@ -373,10 +379,22 @@ int prof_close(ls_ctx* c, cudaStream_t s)
     return LS_OK;
 }
 
-int prof_before_stencil(ls_ctx* c, int kind, cudaStream_t s)
+// a: the launch about to be made; its updates also go to the timed counter
+// when its run is timed.  With prof_every = N > 1 one run in N is timed
+// (fewer event records between launches, which otherwise cost their overlap).
+int prof_before_stencil(ls_ctx* c, int kind, cudaStream_t s, lsk::StepArgs& a)
 {
+    a.updates_timed = nullptr;
     if (!c->profiling) return LS_OK;
     if (c->ev_open && c->ev_open_kind != kind) RET(prof_close(c, s));
+    if (!c->ev_open && (c->prof_runs++ % (unsigned long long)c->prof_every) != 0) {
+        c->ev_open = true;
+        c->ev_skip = true;
+        c->ev_open_kind = kind;
+        return LS_OK;
+    }
+    if (c->ev_skip) return LS_OK;
+    a.updates_timed = c->d_updates_timed;
     if (!c->ev_open) {
         if (c->ev_pending.size() >= 4096) RET(drain_events(c));
         CK(take_event(c, &c->ev_open_e0));
@@ -441,7 +459,7 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
             lsk::StepArgs a = step_args(c, classify);
             a.nact = c->list_nact;
             a.updates2 = c->d_updates2;
-            RET(prof_before_stencil(c, 0, s));
+            RET(prof_before_stencil(c, 0, s, a));
             a.reverse = c->dir;
             KL(c, lsk::launch_step2(a, c->cfg, s));
             c->stencil_launches += 1;
@@ -485,7 +503,7 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
                     a.updates = c->d_rupdates;
                 }
             }
-            RET(prof_before_stencil(c, p > 0 ? 1 : 0, s));
+            RET(prof_before_stencil(c, p > 0 ? 1 : 0, s, a));
             a.reverse = c->dir;
             if (!local && c->full_domain && c->cfg.dense && two_step_ok(c)) {
                 a.tile_sgn = sign_table(c);
@@ -660,6 +678,8 @@ int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h
     A(dalloc(&c->d_done, 4 * sizeof(unsigned)));
     A(dalloc(&c->d_updates2, sizeof(unsigned long long)));
     if (e == cudaSuccess) e = cudaMemset(c->d_updates2, 0, sizeof(unsigned long long));
+    A(dalloc(&c->d_updates_timed, sizeof(unsigned long long)));
+    if (e == cudaSuccess) e = cudaMemset(c->d_updates_timed, 0, sizeof(unsigned long long));
     if (!batched && precision == LS_FP32) A(dalloc(&c->list_nact, c->ntiles));
     if (!batched && precision == LS_FP32)
         A(dalloc(&c->xface, (size_t)c->ntiles * lsk::XFACE_FLOATS * sizeof(float)));
@@ -1305,8 +1325,11 @@ int ls_get_updates(ls_ctx* c, unsigned long long* n)
 int ls_profile_enable(ls_ctx* c, int on)
 {
     if (!c) return LS_EINVAL;
-    if (!on && c->ev_open) RET(prof_close(c, c->stream));
+    if (on < 0) return LS_EINVAL;
+    if (c->ev_open) RET(prof_close(c, c->stream));
     c->profiling = on != 0;
+    c->prof_every = on > 0 ? on : 1;
+    c->prof_runs = 0;
     return LS_OK;
 }
 
@@ -1329,6 +1352,9 @@ int ls_get_profile(ls_ctx* c, ls_profile* out)
                            cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
+    CK(cudaMemcpyAsync(&out->stencil_updates, c->d_updates_timed, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return LS_OK;
 }
 
@@ -1342,6 +1368,7 @@ int ls_reset_profile(ls_ctx* c)
     c->stencil_timed = 0;
     c->reinit_ms = 0.0;
     c->reinit_timed = 0;
+    CK(cudaMemsetAsync(c->d_updates_timed, 0, sizeof(unsigned long long), c->stream));
     return LS_OK;
 }
 

@@ -125,6 +125,10 @@ struct ls_ctx {
     struct EvPair { cudaEvent_t e0, e1; bool reinit; int count; };
     std::vector<EvPair> ev_pending;
     bool ev_open = false;          // an event run of stencil launches is open
+    bool ev_skip = false;          // the open run is not timed (sampled profile)
+    int prof_every = 1;            // time one run of stencil launches in prof_every
+    unsigned long long prof_runs = 0;        // runs opened since profiling was enabled
+    unsigned long long* d_updates_timed = nullptr;  // updates of the timed launches
     int ev_open_kind = 0;          // 0 plain / advance, 1 reinitialisation
     int ev_open_n = 0;             // launches in the open run
     cudaEvent_t ev_open_e0 = nullptr;

@@ -47,8 +47,10 @@ __global__ void __launch_bounds__(128, 8) k_dense_f32(StepArgs a)
     const int G = gridDim.x;
     const int mycols = (int)blockIdx.x < ncol ? (ncol - (int)blockIdx.x + G - 1) / G : 0;
     const long long total = (long long)mycols * tnz;
-    if (blockIdx.x == 0 && tid == 0 && a.updates)
-        atomicAdd(a.updates, (unsigned long long)ncol * tnz * TILE_PTS);
+    if (blockIdx.x == 0 && tid == 0) {
+        if (a.updates) atomicAdd(a.updates, (unsigned long long)ncol * tnz * TILE_PTS);
+        if (a.updates_timed) atomicAdd(a.updates_timed, (unsigned long long)ncol * tnz * TILE_PTS);
+    }
     const float* __restrict__ src = (const float*)a.src;
     float* __restrict__ dst = (float*)a.dst;
     const float* __restrict__ Fp = (const float*)a.F;
@@ -194,8 +196,10 @@ __global__ void __launch_bounds__(64, 16) k_dense2_f32(StepArgs a)
     const int G = gridDim.x;
     const int mycols = (int)blockIdx.x < ncol ? (ncol - (int)blockIdx.x + G - 1) / G : 0;
     const long long total = (long long)mycols * tnz;
-    if (blockIdx.x == 0 && tid == 0 && a.updates)
-        atomicAdd(a.updates, (unsigned long long)ncol * tnz * TILE_PTS);
+    if (blockIdx.x == 0 && tid == 0) {
+        if (a.updates) atomicAdd(a.updates, (unsigned long long)ncol * tnz * TILE_PTS);
+        if (a.updates_timed) atomicAdd(a.updates_timed, (unsigned long long)ncol * tnz * TILE_PTS);
+    }
     const float* __restrict__ src = (const float*)a.src;
     float* __restrict__ dst = (float*)a.dst;
     const float* __restrict__ Fp = (const float*)a.F;

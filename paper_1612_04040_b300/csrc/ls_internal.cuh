@@ -168,6 +168,8 @@ struct StepArgs {
     const Inst* insts;        // per-instance parameters (batched), device
     uint8_t* core;            // fused tube test output, or NULL
     unsigned long long* updates;
+    unsigned long long* updates_timed;  // also counts this launch's updates when the
+                                        // profile times it (else NULL)
     unsigned long long* updates2;  // two-step passes: points passed (each updated twice)
     Inst in;                  // single instance parameters (bc is read from here always)
     int max_grid;             // cap on the persistent grid (0 = none)

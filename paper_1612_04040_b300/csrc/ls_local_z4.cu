@@ -40,8 +40,10 @@ __global__ void __launch_bounds__(32, 16) k_local_z4(StepArgs a)
     const int n = *a.count;
     const bool rev = a.reverse != 0;
     auto ent = [&](int k) { return rev ? n - 1 - k : k; };
-    if (blockIdx.x == 0 && tid == 0 && a.updates)
-        atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
+    if (blockIdx.x == 0 && tid == 0) {
+        if (a.updates) atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
+        if (a.updates_timed) atomicAdd(a.updates_timed, (unsigned long long)n * TILE_PTS);
+    }
     const float* __restrict__ src = (const float*)a.src;
     float* __restrict__ dst = (float*)a.dst;
     const float* __restrict__ Fp = (const float*)a.F;

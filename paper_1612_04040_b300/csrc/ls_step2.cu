@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(128, 6) k_step2_f32(StepArgs a)
     const int n = *a.count;
     if (blockIdx.x == 0 && tid == 0) {
         if (a.updates) atomicAdd(a.updates, 2ull * (unsigned long long)n * TILE_PTS);
+        if (a.updates_timed) atomicAdd(a.updates_timed, 2ull * (unsigned long long)n * TILE_PTS);
         if (a.updates2) atomicAdd(a.updates2, (unsigned long long)n * TILE_PTS);
     }
     const bool rev = a.reverse != 0;

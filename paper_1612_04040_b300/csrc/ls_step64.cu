@@ -191,8 +191,10 @@ __global__ void __launch_bounds__(128, 4) k_step_f64(StepArgs a)
     const int xh = tid & 1, ly = (tid >> 1) & 7, lz = tid >> 4;
     const Inst in = a.in;
     const long long n = *a.count;
-    if (blockIdx.x == 0 && tid == 0 && a.updates)
-        atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
+    if (blockIdx.x == 0 && tid == 0) {
+        if (a.updates) atomicAdd(a.updates, (unsigned long long)n * TILE_PTS);
+        if (a.updates_timed) atomicAdd(a.updates_timed, (unsigned long long)n * TILE_PTS);
+    }
     const double dt = a.sc->dt;
     const double* __restrict__ src = (const double*)a.src;
     double* __restrict__ dst = (double*)a.dst;

@@ -117,7 +117,8 @@ class Profile(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_ulonglong), ("stencil_launches", ctypes.c_ulonglong),
                 ("stencil_ms", ctypes.c_double), ("stencil_timed", ctypes.c_ulonglong),
                 ("reinit_ms", ctypes.c_double), ("reinit_timed", ctypes.c_ulonglong),
-                ("reinit_updates", ctypes.c_ulonglong), ("two_step_points", ctypes.c_ulonglong)]
+                ("reinit_updates", ctypes.c_ulonglong), ("two_step_points", ctypes.c_ulonglong),
+                ("stencil_updates", ctypes.c_ulonglong)]
 
 
 class OutputReport(ctypes.Structure):
@@ -550,7 +551,8 @@ class LevelSet:
         return n.value
 
     def profile_enable(self, on=True):
-        check(self.lib.ls_profile_enable(self.ctx, int(bool(on))), "ls_profile_enable")
+        """True / False, or an int N >= 1: time one run of stencil launches in N."""
+        check(self.lib.ls_profile_enable(self.ctx, int(on)), "ls_profile_enable")
 
     def profile(self):
         p = Profile()

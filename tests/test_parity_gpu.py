@@ -237,6 +237,32 @@ def test_fp32_frozen_face_copies_follow_the_band(ppt):
     assert np.max(np.abs(out[m] - o.phi[m])) <= 1e-5 * w.h * 15
 
 
+def test_profile_sampling_counts():
+    """Event timing of every run of stencil launches, and of one run in N:
+    the timed launches and their point updates are counted exactly."""
+    w = inputs.SphereUnion(n=64, count=5)
+    g, _ = make_pair((64,) * 3, w.h, ls.LS_FP32, w.phi().numpy(), F=w.speed().numpy())
+    g.band_rebuild(w.halfwidth)
+    g.step(1, w.cfl, ls.LS_DT_CFL, 5)  # the next call starts at a rebuild
+    g.step(4, w.cfl, ls.LS_DT_CFL, 5)
+    for every, runs_timed in ((1, 6), (4, 2)):
+        g.reset_profile()
+        g.profile_enable(every)
+        u0 = g.updates()
+        g.step(30, w.cfl, ls.LS_DT_CFL, 5)  # 6 runs of 5 launches, a rebuild before each
+        p = g.profile()
+        g.profile_enable(False)
+        assert p["stencil_launches"] == 30
+        assert p["stencil_timed"] == 5 * runs_timed
+        assert p["stencil_ms"] > 0.0
+        if every == 1:
+            assert p["stencil_updates"] == g.updates() - u0
+        else:
+            assert 0 < p["stencil_updates"] < g.updates() - u0
+    with pytest.raises(ls.LSError):
+        g.profile_enable(-1)
+
+
 def test_fp32_tube_test_matches_oracle_on_gpu_snapshot():
     """The GPU's band decision on its own FP32 state equals the oracle's FP64
     tube test + dilation applied to that same state (exact)."""
