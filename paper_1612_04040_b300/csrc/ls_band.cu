@@ -194,23 +194,6 @@ __device__ __forceinline__ unsigned nb_bits(long long t, const Inst& in)
     return b;
 }
 
-// the face neighbours of tile t (single instance) inside the domain whose
-// active flag (bit 0 of act) is set
-__device__ __forceinline__ unsigned active_nb_bits(long long t, unsigned nb, const Inst& in,
-                                                   const uint8_t* __restrict__ act)
-{
-    const long long tpl = (long long)in.tnx * in.tny;
-    unsigned b = 0;
-    if ((nb & NB_XM) && (act[t - 1] & 1)) b |= NB_XM;
-    if ((nb & NB_XP) && (act[t + 1] & 1)) b |= NB_XP;
-    if ((nb & NB_YM) && (act[t - in.tnx] & 1)) b |= NB_YM;
-    if ((nb & NB_YP) && (act[t + in.tnx] & 1)) b |= NB_YP;
-    if ((nb & NB_ZM) && (act[t - tpl] & 1)) b |= NB_ZM;
-    if ((nb & NB_ZP) && (act[t + tpl] & 1)) b |= NB_ZP;
-    return b;
-}
-
-
 // Eq. 6 per tile: core = (min |phi| over the tile) < gamma, compared in FP64
 template <typename T>
 __global__ void __launch_bounds__(256) k_classify_all(const T* __restrict__ phi, uint8_t* core,
@@ -306,21 +289,27 @@ __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core
         const int tz = loc / tpl;
         const int rem = loc - tz * tpl;
         const int ty = rem / in.tnx, tx = rem - ty * in.tnx;
-        const uint8_t* c0 = core + in.tile_base;
-        // all 27 (or 7) flags are loaded independently, then OR-ed: no
-        // chain of dependent loads
+        const uint8_t* ct = core + t;
+        // which neighbours exist, per axis and side; a neighbour is read when
+        // its three axis tests hold (and, with 6-connectivity, when it is a
+        // face neighbour).  All 27 (or 7) flags are loaded independently,
+        // then OR-ed: no chain of dependent loads; the offsets are the row
+        // pointers' plus a constant.
+        const bool ex[3] = {tx > 0, true, tx < in.tnx - 1};
+        const bool ey[3] = {ty > 0, true, ty < in.tny - 1};
+        const bool ez[3] = {tz > 0, true, tz < in.tnz - 1};
+        const bool all26 = conn != 6;
         unsigned acc = 0;
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
 #pragma unroll
             for (int dy = -1; dy <= 1; ++dy) {
+                const uint8_t* row = ct + (long long)dz * tpl + (long long)dy * in.tnx;
+                const bool vzy = ez[dz + 1] && ey[dy + 1];
 #pragma unroll
                 for (int dx = -1; dx <= 1; ++dx) {
-                    const int z = tz + dz, y = ty + dy, x = tx + dx;
-                    const bool in_dom = z >= 0 && z < in.tnz && y >= 0 && y < in.tny && x >= 0 &&
-                                        x < in.tnx;
-                    const bool in_conn = conn != 6 || abs(dx) + abs(dy) + abs(dz) <= 1;
-                    if (in_dom && in_conn) acc |= c0[(z * in.tny + y) * in.tnx + x];
+                    const bool face = abs(dx) + abs(dy) + abs(dz) <= 1;
+                    if (vzy && ex[dx + 1] && (face || all26)) acc |= row[dx];
                 }
             }
         }
@@ -493,14 +482,32 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
     __shared__ int leave_ids[256];
     pdl_wait();
     const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
-    const int fl = (t < ntiles) ? act[t] : 0;
+    const bool inb = t < ntiles;
+    // every load this thread may need is issued here, independently of the
+    // tile's own flag (one round trip instead of a chain of three): the
+    // block's offset, the flags of the face neighbours, max|F| and the sign
+    const int blk_off = offsets[blockIdx.x];
+    const unsigned nb = inb ? nb_bits(t, single) : 0u;
+    const long long tpl = (long long)single.tnx * single.tny;
+    unsigned nf[6] = {0u, 0u, 0u, 0u, 0u, 0u};  // act of the -x, +x, -y, +y, -z, +z neighbours
+    if (list_nact) {
+        if (nb & NB_XM) nf[0] = act[t - 1];
+        if (nb & NB_XP) nf[1] = act[t + 1];
+        if (nb & NB_YM) nf[2] = act[t - single.tnx];
+        if (nb & NB_YP) nf[3] = act[t + single.tnx];
+        if (nb & NB_ZM) nf[4] = act[t - tpl];
+        if (nb & NB_ZP) nf[5] = act[t + tpl];
+    }
+    const T maxF = (inb && tile_maxF) ? tile_maxF[t] : T(0);
+    const unsigned sgn = (inb && tile_sgn) ? (unsigned)tile_sgn[t] : const_sgn;
+    const int fl = inb ? act[t] : 0;
     const int on = fl & 1;
     const int leaving = (fl & 2) && !on;
     const unsigned b = __ballot_sync(0xffffffffu, on);
     const unsigned bl = __ballot_sync(0xffffffffu, leaving);
     const int w = threadIdx.x >> 5;
     unsigned long long mb = 0;
-    if (on && tile_maxF) mb = ordered_bits(tile_maxF[t]);
+    if (on && tile_maxF) mb = ordered_bits(maxF);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long u = __shfl_xor_sync(0xffffffffu, mb, o);
@@ -522,16 +529,19 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ act
     }
     const unsigned below = (1u << lane_id()) - 1u;
     if (on) {
-        const int pos = offsets[blockIdx.x] + before + __popc(b & below);
+        const int pos = blk_off + before + __popc(b & below);
         list[pos] = (int)t;
-        const unsigned nb = nb_bits(t, single);
-        list_info[pos] = (uint8_t)(nb | (tile_sgn ? tile_sgn[t] : const_sgn));
+        list_info[pos] = (uint8_t)(nb | sgn);
         if (list_nact) {
-            unsigned an = active_nb_bits(t, nb, single, act);
+            // the face neighbours inside the domain that are active
+            unsigned an = 0u;
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+                if (nf[k] & 1u) an |= 1u << k;  // NB_XM, NB_XP, NB_YM, NB_YP, NB_ZM, NB_ZP
             const unsigned fz = nb & ~an;
             const bool was = xface_mode == 2 && (fl & 2);
-            if (xface_mode && (fz & NB_XM) && !(was && !(act[t - 1] & 2))) an |= NACT_FILL_XM;
-            if (xface_mode && (fz & NB_XP) && !(was && !(act[t + 1] & 2))) an |= NACT_FILL_XP;
+            if (xface_mode && (fz & NB_XM) && !(was && !(nf[0] & 2u))) an |= NACT_FILL_XM;
+            if (xface_mode && (fz & NB_XP) && !(was && !(nf[1] & 2u))) an |= NACT_FILL_XP;
             list_nact[pos] = (uint8_t)an;
         }
     }
