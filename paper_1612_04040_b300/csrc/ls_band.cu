@@ -6,6 +6,7 @@
 // All band decisions are exact: min |phi| over a tile is exact in any
 // precision, and the tube test min|phi| < gamma is done in FP64 against
 // gamma = halfwidth * h computed in FP64 on the host.
+#include <cuda/atomic>
 #include <utility>
 
 #include "ls_internal.cuh"
@@ -217,17 +218,23 @@ __global__ void __launch_bounds__(256) k_classify_all(const T* __restrict__ phi,
 // flag in bit 0 and the previous one in bit 1 (the scatter pass uses both to
 // find the tiles that leave the active set).
 // ---------------------------------------------------------------------------
-// The block that finishes last (every block fences its writes before it
-// counts itself) sees the results of all blocks; true in all its threads.
+// The block that finishes last (every block's thread 0 releases its writes
+// when it counts itself) sees the results of all blocks; true in all its
+// threads.
 // That block resets the counter for the next launch.  No block waits.
 __device__ __forceinline__ bool last_block(unsigned* done)
 {
+    // what the last block reads of the other blocks (their count, their max
+    // |F| bits) is written by each block's thread 0, so only that thread
+    // orders its writes before the counter moves (release) and the last one
+    // orders its reads after it (acquire); the other threads wait at the
+    // barrier instead of at a fence of their own
     __shared__ bool last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        last = atomicAdd(done, 1u) == gridDim.x - 1;
-        if (last) *done = 0u;
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> d(*done);
+        last = d.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1;
+        if (last) d.store(0u, cuda::memory_order_relaxed);
     }
     __syncthreads();
     return last;
