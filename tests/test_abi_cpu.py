@@ -64,3 +64,19 @@ def test_host_side_argument_errors(lib):
     assert lib.ls_step(None, 1, 0.5, 1, 5, None) == native.LS_EINVAL
     assert lib.ls_get_status(None) == native.LS_EINVAL
     assert lib.ls_strerror(native.LS_ENONFINITE).decode() == "non-finite value in input"
+
+
+def _struct_fields(header, name):
+    """Field names of `typedef struct { ... } name;` in the header, in order."""
+    body = re.search(r"typedef struct \{([^{}]*)\} %s;" % name, header).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return [m.group(1) for m in re.finditer(r"(\w+)\s*;", body)]
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of ls_profile and ls_output_report list the
+    header's fields in the header's order (a field added on one side only
+    would shift every later one)."""
+    header = open(os.path.join(ROOT, "include", "ls.h")).read()
+    assert [f for f, _ in native.Profile._fields_] == _struct_fields(header, "ls_profile")
+    assert [f for f, _ in native.OutputReport._fields_] == _struct_fields(header, "ls_output_report")
