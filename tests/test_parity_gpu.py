@@ -237,6 +237,29 @@ def test_fp32_frozen_face_copies_follow_the_band(ppt):
     assert np.max(np.abs(out[m] - o.phi[m])) <= 1e-5 * w.h * 15
 
 
+@pytest.mark.parametrize("ppt", [4, 8, 16])
+def test_fp32_non_cubic_band_each_decomposition(ppt):
+    """A non-cubic grid (7 x 5 x 9 tiles, every tile count odd, h fixed by
+    the z edge) with two spheres whose band reaches domain faces: the band sets
+    agree with the oracle at every rebuild and phi stays within the FP32 bar
+    on the band, for each stencil decomposition (the one-warp kernel with
+    its frozen x-face copies included)."""
+    nz, ny, nx = 72, 40, 56
+    h = 1.0 / 72
+    shape = (nz, ny, nx)
+    phi0 = inputs.sphere_union_sdf(shape, h, [(0.30, 0.28, 0.35), (0.55, 0.30, 0.70)],
+                                   [0.22, 0.18]).numpy()
+    F = inputs.speed_sinusoid(shape, h).numpy()
+    g, o = make_pair(shape, h, ls.LS_FP32, phi0, F=F)
+    g.set_step_config(2, 100, ppt)
+    assert g.band_rebuild(5.0) == o.band_rebuild(5.0)
+    run_chunks(g, o, [5, 5, 3, 7], 0.5, ls.LS_DT_CFL, 5)
+    out = g.get_phi().astype(np.float64)
+    m = tile_mask(o.active, shape)
+    assert m.any()
+    assert np.max(np.abs(out[m] - o.phi[m])) <= 1e-5 * h * 20
+
+
 def test_profile_sampling_counts():
     """Event timing of every run of stencil launches, and of one run in N:
     the timed launches and their point updates are counted exactly."""
