@@ -1101,8 +1101,9 @@ int ls_restore(ls_ctx* c)
     if (!c) return LS_EINVAL;
     if (!c->snapshot) return LS_ESTATE;
     state_changed(c);
-    CK(cudaMemcpyAsync(c->phi[0], c->snapshot, grid_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->phi[1], c->snapshot, grid_bytes(c), cudaMemcpyDeviceToDevice, c->stream));
+    // one read of the snapshot, both buffers written (16-byte multiples:
+    // grids are whole 8^3 tiles)
+    KL(c, lsk::launch_copy(c->phi[0], c->snapshot, grid_bytes(c), c->stream, c->phi[1]));
     c->cur = 0;
     return LS_OK;
 }

@@ -743,19 +743,22 @@ cudaError_t launch_pack(const void* src, void* dst, const Inst& in, int prec, un
 }
 
 __global__ void __launch_bounds__(256) k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst,
-                                                size_t n)
+                                                uint4* __restrict__ dst2, size_t n)
 {
-    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256)
-        dst[i] = src[i];
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256) {
+        const uint4 v = src[i];
+        dst[i] = v;
+        if (dst2) dst2[i] = v;
+    }
 }
 
-cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s)
+cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s, void* dst2)
 {
     const size_t n = bytes / 16;
     if (n == 0) return cudaSuccess;
     size_t g = (n + 255) / 256;
     if (g > 148 * 16) g = 148 * 16;
-    k_copy16<<<(int)g, 256, 0, s>>>((const uint4*)src, (uint4*)dst, n);
+    k_copy16<<<(int)g, 256, 0, s>>>((const uint4*)src, (uint4*)dst, (uint4*)dst2, n);
     return cudaGetLastError();
 }
 

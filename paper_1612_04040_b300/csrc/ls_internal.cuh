@@ -73,9 +73,11 @@ struct StepScalars {
 // into *nonfinite (may be NULL)
 cudaError_t launch_pack(const void* src, void* dst, const Inst& in, int prec, unsigned* nonfinite,
                         cudaStream_t s);
-// device-to-device copy of `bytes` (a multiple of 16, 16-byte aligned) by a
+// device-to-device copy of `bytes` (a multiple of 16, 16-byte aligned; also
+// into dst2 when it is not NULL: one read, two writes) by a
 // kernel, so that it does not queue behind host transfers on a copy engine
-cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s);
+cudaError_t launch_copy(void* dst, const void* src, size_t bytes, cudaStream_t s,
+                        void* dst2 = nullptr);
 cudaError_t launch_unpack(const void* src, void* dst, const Inst& in, int prec, cudaStream_t s);
 // tile_maxF[t] = max |F| over tile t; tile_sgn[t] = SG_POS / SG_NEG / 0
 cudaError_t launch_tile_speed(const void* F, void* tile_maxF, uint8_t* tile_sgn, long long ntiles,
