@@ -567,16 +567,26 @@ int ls_restrict4(const float *fine, int nfx, int nfy, int nfz, float *coarse, vo
  *   count_out  device pointer to one int; receives the active-tile count.
  *   cuda_stream  stream the work is queued on (NULL = legacy default).
  * The call is asynchronous: results are valid once the stream has reached
- * the queued work.  The first call on a device looks up the scratch array's
- * device address (cudaGetSymbolAddress) and caches it; make that first call
- * outside any stream capture.  All calls share the one scratch array: calls
- * that overlap on the GPU (other streams, other host threads) race and must
- * be serialised by the caller.  Every scratch byte a call reads it has
- * written first, so nothing needs clearing between calls.
+ * the queued work.
+ * First call per device: it looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and caches it.  Under CUDA's lazy module loading
+ * (the default) that lookup loads the library's module on the device and
+ * reserves the array there, so the first call does allocate; make it
+ * outside any stream capture and outside any allocation-free section (one
+ * throwaway call warms a device up).  Later calls on that device allocate
+ * nothing.
+ * All calls share the one scratch array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Every scratch byte a call reads it has written first, so nothing
+ * needs clearing between calls.
  * Errors: LS_EINVAL (NULL pointer, sizes not multiples of 8 or < 8, h or
- * halfwidth not positive, bad precision, more than LS_NOALLOC_MAX_TILES
- * tiles, tiles_cap too small), LS_ECUDA (launch failure).  Never calls
- * cudaMalloc, cudaFree or any allocating routine. */
+ * halfwidth not finite and positive, bad precision, more than
+ * LS_NOALLOC_MAX_TILES tiles, tiles_cap too small), all decided on the host
+ * before any CUDA call; LS_ECUDA (device query or launch failure).  The
+ * call takes each launch's status from the launch itself: it neither reads
+ * nor clears the CUDA runtime's pending-error state left by earlier work
+ * (a failed launch of its own is also recorded there, as for any runtime
+ * call).  Never calls cudaMalloc, cudaFree or any allocating routine. */
 int ls_band_tiles_noalloc(const void *phi, int nx, int ny, int nz, double h, int precision,
                           double halfwidth_in_h, int *tiles_out, long long tiles_cap,
                           int *count_out, void *cuda_stream);

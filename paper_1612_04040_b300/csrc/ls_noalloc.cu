@@ -8,12 +8,16 @@
 // whose memory pool owns the whole device.  This entry point serves them:
 // the caller passes phi and the output buffers, and the only scratch the
 // kernels need (tile flags and per-block counts) lives in one file-scope
-// __device__ array of fixed size, reserved when the library is loaded on a
-// device and held until the process exits.
+// __device__ array of fixed size.  With CUDA's lazy module loading (the
+// default) the array is reserved when this file's module is first loaded
+// on a device, i.e. by the first call there (its cudaGetSymbolAddress); it
+// is then held until the process exits.  A caller warms a device up with
+// one throwaway call made outside any capture and allocation-free section.
 //
 // The kernels are separate copies of the band-rebuild steps (tube test per
 // tile, 26-neighbour dilation, count, scan, ascending scatter) that read phi
 // in the caller's row-major layout; the context-based path is untouched.
+#include <cmath>
 #include <mutex>
 
 #include "ls.h"
@@ -162,44 +166,66 @@ __global__ void __launch_bounds__(NA_BLOCK) k_na_scatter(const uint8_t* __restri
     if (on) ids[offsets[blockIdx.x] + before + __popc(b & ((1u << lane) - 1u))] = (int)t;
 }
 
+// Launches one kernel and returns that launch's own status: the runtime
+// call's return value, not cudaGetLastError, so an error left pending by
+// the caller's earlier work is neither reported as ours nor cleared.
+template <typename... P, typename... A>
+cudaError_t na_launch(void (*kernel)(P...), int grid, int block, cudaStream_t s, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    return cudaLaunchKernelEx(&cfg, kernel, (P)args...);
+}
+
 }  // namespace
 
 extern "C" int ls_band_tiles_noalloc(const void* phi, int nx, int ny, int nz, double h,
                                      int precision, double halfwidth_in_h, int* tiles_out,
                                      long long tiles_cap, int* count_out, void* cuda_stream)
 {
+    // every argument is checked on the host before the first CUDA call
     if (!phi || !tiles_out || !count_out) return LS_EINVAL;
     if (nx < 8 || ny < 8 || nz < 8 || nx % 8 || ny % 8 || nz % 8) return LS_EINVAL;
-    if (!(h > 0.0) || !(halfwidth_in_h > 0.0) || h != h || halfwidth_in_h != halfwidth_in_h)
+    if (!std::isfinite(h) || !(h > 0.0) || !std::isfinite(halfwidth_in_h) || !(halfwidth_in_h > 0.0))
         return LS_EINVAL;
     if (precision != LS_FP32 && precision != LS_FP64) return LS_EINVAL;
     const int tnx = nx / 8, tny = ny / 8, tnz = nz / 8;
     const long long ntiles = (long long)tnx * tny * tnz;
     if (ntiles > NA_MAX_TILES) return LS_EINVAL;  // beyond the fixed scratch size
     if (tiles_cap < ntiles) return LS_EINVAL;
+    const double gamma = halfwidth_in_h * h;
+    if (!std::isfinite(gamma)) return LS_EINVAL;
     void* base = nullptr;
     cudaError_t e = na_scratch(&base);
     if (e != cudaSuccess) return LS_ECUDA;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return LS_ECUDA;
     uint8_t* core = (uint8_t*)base + NA_CORE_OFF;
     uint8_t* act = (uint8_t*)base + NA_ACT_OFF;
     int* counts = (int*)((uint8_t*)base + NA_CNT_OFF);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const double gamma = halfwidth_in_h * h;
-    long long g = (ntiles + 7) / 8;
-    if (g > 148 * 64) g = 148 * 64;
+    long long g = (ntiles + 7) / 8;  // grid-stride: 8 tiles (warps) per block
+    if (g > (long long)sms * 64) g = (long long)sms * 64;
     if (precision == LS_FP32)
-        k_na_classify<float><<<(int)g, 256, 0, s>>>((const float*)phi, nx, ny, tnx, tny, ntiles,
-                                                    gamma, core);
+        e = na_launch(k_na_classify<float>, (int)g, 256, s, (const float*)phi, nx, ny, tnx, tny,
+                      ntiles, gamma, core);
     else
-        k_na_classify<double><<<(int)g, 256, 0, s>>>((const double*)phi, nx, ny, tnx, tny, ntiles,
-                                                     gamma, core);
-    if (cudaGetLastError() != cudaSuccess) return LS_ECUDA;
+        e = na_launch(k_na_classify<double>, (int)g, 256, s, (const double*)phi, nx, ny, tnx, tny,
+                      ntiles, gamma, core);
+    if (e != cudaSuccess) return LS_ECUDA;
     const int nb = (int)((ntiles + NA_BLOCK - 1) / NA_BLOCK);
-    k_na_dilate<<<nb, NA_BLOCK, 0, s>>>(core, act, tnx, tny, tnz, ntiles, counts);
-    if (cudaGetLastError() != cudaSuccess) return LS_ECUDA;
-    k_na_scan<<<1, 1024, 0, s>>>(counts, nb, count_out);
-    if (cudaGetLastError() != cudaSuccess) return LS_ECUDA;
-    k_na_scatter<<<nb, NA_BLOCK, 0, s>>>(act, counts, ntiles, tiles_out);
-    if (cudaGetLastError() != cudaSuccess) return LS_ECUDA;
+    e = na_launch(k_na_dilate, nb, NA_BLOCK, s, (const uint8_t*)core, act, tnx, tny, tnz, ntiles,
+                  counts);
+    if (e != cudaSuccess) return LS_ECUDA;
+    e = na_launch(k_na_scan, 1, 1024, s, counts, nb, count_out);
+    if (e != cudaSuccess) return LS_ECUDA;
+    e = na_launch(k_na_scatter, nb, NA_BLOCK, s, (const uint8_t*)act, (const int*)counts, ntiles,
+                  tiles_out);
+    if (e != cudaSuccess) return LS_ECUDA;
     return LS_OK;
 }

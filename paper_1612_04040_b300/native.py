@@ -197,12 +197,22 @@ def band_tiles_noalloc(phi, h, halfwidth, tiles_out, count_out, stream=None):
     buffers tiles_out (int32, >= number of tiles) and count_out (int32, 1),
     without any allocation by the library.  Asynchronous on `stream`."""
     lib = load()
-    if phi.dim() != 3 or not phi.is_cuda or not phi.is_contiguous():
-        raise ValueError("phi must be a contiguous 3-D CUDA tensor")
-    prec = LS_FP32 if phi.dtype == torch.float32 else LS_FP64
-    nz, ny, nx = phi.shape
+    if phi.dtype == torch.float32:
+        prec = LS_FP32
+    elif phi.dtype == torch.float64:
+        prec = LS_FP64
+    else:
+        raise TypeError("phi must be float32 or float64, got %s" % phi.dtype)
     if tiles_out.dtype != torch.int32 or count_out.dtype != torch.int32:
         raise TypeError("tiles_out and count_out must be int32")
+    if phi.dim() != 3 or not phi.is_cuda or not phi.is_contiguous():
+        raise ValueError("phi must be a contiguous 3-D CUDA tensor")
+    for name, t in (("tiles_out", tiles_out), ("count_out", count_out)):
+        if not t.is_cuda or not t.is_contiguous() or t.device != phi.device:
+            raise ValueError("%s must be a contiguous CUDA tensor on %s" % (name, phi.device))
+    if count_out.numel() < 1:
+        raise ValueError("count_out must hold at least one int32")
+    nz, ny, nx = phi.shape
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     check(lib.ls_band_tiles_noalloc(ctypes.c_void_p(phi.data_ptr()), nx, ny, nz, float(h), prec,

@@ -50,10 +50,23 @@ def test_noalloc_matches_context_path_twice(cuda_ok):
         assert np.array_equal(tiles[:n].cpu().numpy(), expect)
 
 
-def test_noalloc_rejects_oversize(cuda_ok):
-    lib = ls.load()
-    import ctypes
-    # 2^21 + 1 tiles would exceed the fixed scratch: rejected before any work
-    st = lib.ls_band_tiles_noalloc(ctypes.c_void_p(16), 8, 8, 8 * ((1 << 21) + 1), 1.0, 0, 2.0,
-                                   ctypes.c_void_p(16), (1 << 21) + 1, ctypes.c_void_p(16), None)
-    assert st == ls.LS_EINVAL
+def test_noalloc_rejects_bad_scalars_with_real_buffers(cuda_ok):
+    """Arguments the host rejects (non-finite or non-positive h or halfwidth,
+    too small an output) come back as LS_EINVAL with nothing queued; the
+    buffers are real device memory, so a broken check could not reach a
+    wild address either."""
+    ls.load()
+    phi = torch.ones((16, 16, 16), dtype=torch.float32, device="cuda")
+    tiles = torch.full((8,), -7, dtype=torch.int32, device="cuda")
+    count = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    inf, nan = float("inf"), float("nan")
+    for h, hw in ((inf, 2.0), (-inf, 2.0), (nan, 2.0), (0.0, 2.0), (1.0 / 16, inf), (1.0 / 16, nan),
+                  (1.0 / 16, -1.0), (1e300, 1e300)):
+        with pytest.raises(ls.LSError) as e:
+            ls.band_tiles_noalloc(phi, h, hw, tiles, count)
+        assert e.value.status == ls.LS_EINVAL, (h, hw)
+    with pytest.raises(ls.LSError) as e:
+        ls.band_tiles_noalloc(phi, 1.0 / 16, 2.0, tiles[:7], count)   # 8 tiles need tiles_cap >= 8
+    assert e.value.status == ls.LS_EINVAL
+    torch.cuda.synchronize()
+    assert int(count.item()) == -7 and int(tiles.min().item()) == -7
