@@ -25,8 +25,17 @@ What it computes, and where the paper defines it (arXiv 1612.04040):
                          narrow-band algorithm (section 1.1), with the same
                          call semantics as the C ABI of the library.
 
-The arithmetic lives in ``levelset_oracle.c`` (plain C, no FMA contraction);
-this module only marshals arrays and runs the schedule.  Parity pins are in
+Learned coarse-grid corrector (not in the paper; the readings are this
+project's): ``conv3_*``, ``cnn_forward`` / ``cnn_backward`` (network),
+``restrict4`` (fine -> coarse), ``features``, ``correction``,
+``residual_check``, ``learned_step`` (one corrected step with the plain
+fallback), ``mse_loss_grad``, ``adam_step``, ``train_iteration``.
+
+The arithmetic of the scheme and of the convolutions lives in
+``levelset_oracle.c`` (plain C, no FMA contraction); this module marshals
+arrays and runs the schedule, and writes the corrector's element-wise
+definitions (features, correction, check, loss, Adam) as numpy
+expressions.  Parity pins are in
 ``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
@@ -495,3 +504,137 @@ def cnn_backward(x, params, acts, dz_out):
         if k > 0:
             g = conv3_bwd_data(g, params[k][0]) * (acts[k - 1] > 0)
     return grads
+
+
+# --------------------------------------------------------------------------
+# the corrected coarse step and its training step (not in the paper): FP64
+# numpy definitions, written out one expression per reading
+# --------------------------------------------------------------------------
+
+FEATURE_CLAMP = 8.0
+
+
+def features(phi, phit, h, F=None, Fc=0.0):
+    """Corrector inputs, channels-last (nz, ny, nx, 3):
+    [clamp(phi^n / h, -8, 8), F, (phi~ - phi^n) / h], where phi~ is the plain
+    step (Eq. 3) of phi^n.  phi is scaled by the grid spacing so the network
+    sees cell units; F keeps its own units."""
+    phi = _f64(phi)
+    phit = _f64(phit)
+    Fa = np.full(phi.shape, float(Fc)) if F is None else _f64(F)
+    return np.stack([np.clip(phi / h, -FEATURE_CLAMP, FEATURE_CLAMP), Fa, (phit - phi) / h], axis=-1)
+
+
+def tile_points(active, tile=8):
+    """Point mask (nz, ny, nx) of the points of the flagged tiles."""
+    a = np.asarray(active, dtype=bool)
+    return np.repeat(np.repeat(np.repeat(a, tile, 0), tile, 1), tile, 2)
+
+
+def correction(z, h, active, tile=8):
+    """The corrector's output in phi units: h * z on the points of active
+    tiles, 0 elsewhere (points outside the band stay frozen)."""
+    return np.where(tile_points(active, tile), float(h) * _f64(z), 0.0)
+
+
+def residual_check(corr, active, dt, M, tile=8):
+    """True when the correction must be rejected: some value on the points of
+    active tiles is not finite, or its magnitude exceeds dt * M, the motion of
+    one plain step (M = max |F| over the band)."""
+    c = _f64(corr)[tile_points(active, tile)]
+    if c.size == 0:
+        return False
+    if not np.all(np.isfinite(c)):
+        return True
+    return bool(np.max(np.abs(c)) > float(dt) * float(M))
+
+
+def learned_step(phi, h, dt, active, params, F=None, Fc=0.0, M=None, bc="extrapolate", tile=8,
+                 round_features=None):
+    """One corrected coarse step: phi~ = Eq. 3 on the active tiles;
+    z = network(features); the correction h z on the active tiles is applied
+    unless residual_check rejects it, in which case the result is phi~ (the
+    plain fallback).  M defaults to max |F| over the active points.
+    round_features, if given, is applied to the features before the network
+    (a test uses it to feed the network the same rounded inputs as the
+    device).  Returns (phi^{n+1}, phi~, z, rejected)."""
+    phit = step(phi, h, dt, F, Fc, active, tile, bc)
+    X = features(phi, phit, h, F, Fc)
+    if round_features is not None:
+        X = round_features(X)
+    z = cnn_forward(X, params)[-1][..., 0]
+    corr = correction(z, h, active, tile)
+    if M is None:
+        M = max_abs_speed(np.shape(phi), F, Fc, active, tile)
+    rejected = residual_check(corr, active, dt, M, tile)
+    return (phit if rejected else phit + corr), phit, z, rejected
+
+
+def mse_loss_grad(z, phi, phit, phiref, h, gamma):
+    """Training loss and its gradient with respect to z.  Target
+    t = (phi_ref - phi~) / h, the correction (in cells) that would turn the
+    plain step into the reference; loss = mean over the tube T of Eq. 6
+    (|phi^n| < gamma) of (z - t)^2; dloss/dz = 2 (z - t) / |T| on T, 0 off T.
+    An empty tube gives loss 0 and a zero gradient."""
+    z = _f64(z)
+    t = (_f64(phiref) - _f64(phit)) / h
+    mask = np.abs(_f64(phi)) < gamma
+    n = int(np.count_nonzero(mask))
+    r = np.where(mask, z - t, 0.0)
+    cnt = max(n, 1)
+    return float(np.sum(r * r) / cnt), 2.0 * r / cnt, n
+
+
+ADAM_BETA1, ADAM_BETA2, ADAM_EPS = 0.9, 0.999, 1e-8
+
+
+def adam_step(w, g, m, v, t, lr, beta1=ADAM_BETA1, beta2=ADAM_BETA2, eps=ADAM_EPS):
+    """Adam (Kingma and Ba): m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+    m^ = m / (1 - b1^t), v^ = v / (1 - b2^t), w <- w - lr m^ / (sqrt(v^) + eps),
+    for step number t >= 1.  Returns (w, m, v)."""
+    g = _f64(g)
+    m = beta1 * _f64(m) + (1.0 - beta1) * g
+    v = beta2 * _f64(v) + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return _f64(w) - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def unpack_params(flat, chans=(3, 16, 16, 16, 1)):
+    """Split the library's flat parameter vector (per layer W [27][ci][co]
+    then b [co]) into [(W, b), ...]."""
+    flat = _f64(flat)
+    out, o = [], 0
+    for k in range(len(chans) - 1):
+        ci, co = chans[k], chans[k + 1]
+        W = flat[o:o + 27 * ci * co].reshape(27, ci, co)
+        o += 27 * ci * co
+        b = flat[o:o + co]
+        o += co
+        out.append((W, b))
+    if o != flat.size:
+        raise ValueError("parameter vector has %d values, the network %d" % (flat.size, o))
+    return out
+
+
+def pack_params(params):
+    return np.concatenate([np.concatenate([_f64(W).reshape(-1), _f64(b).reshape(-1)]) for W, b in params])
+
+
+def train_iteration(phi, phiref, F, h, dt, gamma, flat, m, v, t, lr, bc="extrapolate",
+                    round_features=None):
+    """One training iteration on one pair (phi^n, phi_ref, F) over the whole
+    grid: phi~ = Eq. 3 everywhere, features, network forward, masked MSE
+    gradient, backward through the network, Adam step t.  Returns
+    (flat', m', v', loss, flat gradient)."""
+    phit = step(phi, h, dt, F, 0.0, None, 8, bc)
+    X = features(phi, phit, h, F)
+    if round_features is not None:
+        X = round_features(X)
+    params = unpack_params(flat)
+    acts = cnn_forward(X, params)
+    loss, dz, _ = mse_loss_grad(acts[-1][..., 0], phi, phit, phiref, h, gamma)
+    grads = cnn_backward(X, params, acts, dz[..., None])
+    gflat = pack_params(grads)
+    w2, m2, v2 = adam_step(flat, gflat, m, v, t, lr)
+    return w2, m2, v2, loss, gflat
