@@ -101,11 +101,15 @@ int ls_set_phi(ls_ctx *ctx, const void *src, int src_on_device);
  *   LS_SHAPE_TORUS    [cx, cy, cz, ax, ay, az, R, r], unit axis a:
  *                     sqrt((rho - R)^2 + s^2) - r, s = (x-c).a,
  *                     rho = distance from the axis line
- *   LS_SHAPE_SH       [cx, cy, cz, base, amp, lmax, a_lm..., N_lm...]
- *                     ((lmax+1)^2 - 1 modes each, l = 1..lmax, m = -l..l):
- *                     |x - c| - (base + amp sum a_lm N_lm P_l^|m|(cos theta)
- *                     T_m(phi)), T_m = cos(m phi) / 1 / sin(|m| phi) for
- *                     m > 0 / m = 0 / m < 0 (a radial level-set function)
+ *   LS_SHAPE_SH       [cx, cy, cz, base, amp, lmax, a_lm...]
+ *                     ((lmax+1)^2 - 1 coefficients, l = 1..lmax, m = -l..l,
+ *                     1 <= lmax <= 16): |x - c| - (base + amp sum a_lm Y_lm)
+ *                     with the real orthonormal spherical harmonics
+ *                     Y_lm = N_lm P_l^|m|(cos theta) T_m(phi),
+ *                     N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!),
+ *                     T_m = sqrt2 cos(m phi) / 1 / sqrt2 sin(|m| phi) for
+ *                     m > 0 / m = 0 / m < 0, P without the Condon-Shortley
+ *                     phase (a radial level-set function)
  * Marks the band stale.  Errors: LS_EINVAL (kind or parameter count). */
 enum { LS_SHAPE_SPHERES = 0, LS_SHAPE_TORUS = 1, LS_SHAPE_SH = 2 };
 int ls_init_phi(ls_ctx *ctx, int shape, const double *params, int nparams);
@@ -213,6 +217,11 @@ int ls_set_full_domain(ls_ctx *ctx, int on);
 /* Copy the current phi out (row-major, context precision) to dst.
  * Synchronises the stream.  Errors: LS_EINVAL, LS_ESTATE (phi not set). */
 int ls_get_phi(ls_ctx *ctx, void *dst, int dst_on_device);
+
+/* Copy the speed field F out (row-major, context precision) to dst, as
+ * ls_get_phi.  Errors: LS_EINVAL (NULL, batch context, misaligned device
+ * dst), LS_ESTATE (no speed field: none set, or a constant speed). */
+int ls_get_speed(ls_ctx *ctx, void *dst, int dst_on_device);
 
 /* Stream-ordered host input/output, for a sequence of problems on one
  * single-grid context (Eq. 1 inputs in, Eq. 3 results out; the transfers
@@ -541,6 +550,32 @@ int ls_conv3_bf16(const void *x, int nx, int ny, int nz, const float *W, int ci,
 int ls_conv3_wgrad(const void *x, const void *dy, int nx, int ny, int nz, int ci, int co,
                    float *dW, float *db, void *cuda_stream);
 int ls_restrict4(const float *fine, int nfx, int nfy, int nfz, float *coarse, void *cuda_stream);
+
+/* The corrector's element-wise steps on caller-owned device buffers (no
+ * allocation; asynchronous on cuda_stream).  Not in the paper.
+ * ls_learned_features: X = BF16 [n][16] channels-last (16-byte aligned),
+ *   channels [clamp(phi / h, -8, 8), F, (phit - phi) / h, 0 ... 0] from FP32
+ *   [n] arrays phi (phi^n), phit (the plain step of phi^n, Eq. 3) and F
+ *   (NULL: the constant Fc).  LS_EINVAL on NULL inputs, n < 1, h not
+ *   finite and positive, Fc not finite, X misaligned.
+ * ls_learned_loss_grad: over the tube |phi| < gamma (Eq. 6, compared in
+ *   FP64), target t = (phiref - phit) / h; *count = tube size (int),
+ *   *loss = sum (z - t)^2 / max(count, 1) (double, summed in FP64),
+ *   dz = BF16 [n][16] with channel 0 = 2 (z - t) / max(count, 1) on the
+ *   tube and 0 elsewhere, channels 1..15 = 0.  count and loss are device
+ *   pointers the call zeroes first.  LS_EINVAL on NULL pointers, n < 1, h
+ *   or gamma not finite and positive, dz misaligned.
+ * ls_adam_step: one Adam step t >= 1 on FP32 [n] parameters w with
+ *   gradient g and moments m, v (updated in place): beta1 0.9, beta2
+ *   0.999, eps 1e-8, bias-corrected.  LS_EINVAL on NULL pointers, n < 1,
+ *   t < 1, lr not finite and positive. */
+int ls_learned_features(const float *phi, const float *phit, const float *F, double Fc, double h,
+                        long long n, void *X, void *cuda_stream);
+int ls_learned_loss_grad(const float *z, const float *phi, const float *phit, const float *phiref,
+                         long long n, double h, double gamma, void *dz, int *count, double *loss,
+                         void *cuda_stream);
+int ls_adam_step(float *w, const float *g, float *m, float *v, int n, double lr, int t,
+                 void *cuda_stream);
 
 /* ---------------------------------------------------------------------
  * Allocation-free band tile list

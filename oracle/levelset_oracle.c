@@ -299,30 +299,35 @@ void orc_conv3_bwd_data(int nx, int ny, int nz, int ci, int co, const double *dy
             }
 }
 
-/* dW[tap][ci][o] = sum_p x[p + off(tap)][ci] * dy[p][o];  db[o] = sum_p dy[p][o] */
+/* dW[tap][ci][o] = sum_p x[p + off(tap)][ci] * dy[p][o];  db[o] = sum_p dy[p][o].
+ * Each tap's sums run over the points in ascending order; the taps are
+ * independent (one OpenMP task each), so the result does not depend on the
+ * thread count. */
 void orc_conv3_bwd_weight(int nx, int ny, int nz, int ci, int co, const double *x,
                           const double *dy, double *dW, double *db)
 {
+    int tap;
     memset(dW, 0, sizeof(double) * 27 * (size_t)ci * co);
-    if (db) memset(db, 0, sizeof(double) * (size_t)co);
-    for (int z = 0; z < nz; ++z)
-        for (int yy = 0; yy < ny; ++yy)
-            for (int xx = 0; xx < nx; ++xx) {
-                const double *g = dy + idx3(nx, ny, xx, yy, z) * (size_t)co;
-                if (db)
-                    for (int o = 0; o < co; ++o) db[o] += g[o];
-                for (int dz = -1; dz <= 1; ++dz)
-                    for (int dyy = -1; dyy <= 1; ++dyy)
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const int X = xx + dx, Y = yy + dyy, Z = z + dz;
-                            if (X < 0 || Y < 0 || Z < 0 || X >= nx || Y >= ny || Z >= nz) continue;
-                            const int tap = (dz + 1) * 9 + (dyy + 1) * 3 + (dx + 1);
-                            const double *in = x + idx3(nx, ny, X, Y, Z) * (size_t)ci;
-                            double *w = dW + (size_t)tap * ci * co;
-                            for (int c = 0; c < ci; ++c)
-                                for (int o = 0; o < co; ++o) w[c * co + o] += in[c] * g[o];
-                        }
-            }
+    if (db) {
+        memset(db, 0, sizeof(double) * (size_t)co);
+        for (size_t p = 0; p < (size_t)nx * ny * nz; ++p)
+            for (int o = 0; o < co; ++o) db[o] += dy[p * (size_t)co + o];
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (tap = 0; tap < 27; ++tap) {
+        const int dx = tap % 3 - 1, dyy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
+        double *w = dW + (size_t)tap * ci * co;
+        for (int z = 0; z < nz; ++z)
+            for (int yy = 0; yy < ny; ++yy)
+                for (int xx = 0; xx < nx; ++xx) {
+                    const int X = xx + dx, Y = yy + dyy, Z = z + dz;
+                    if (X < 0 || Y < 0 || Z < 0 || X >= nx || Y >= ny || Z >= nz) continue;
+                    const double *g = dy + idx3(nx, ny, xx, yy, z) * (size_t)co;
+                    const double *in = x + idx3(nx, ny, X, Y, Z) * (size_t)ci;
+                    for (int c = 0; c < ci; ++c)
+                        for (int o = 0; o < co; ++o) w[c * co + o] += in[c] * g[o];
+                }
+    }
 }
 
 /* restriction by 4: coarse value at the coarse cell centre (4I+2)h_f, i.e.

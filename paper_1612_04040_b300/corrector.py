@@ -59,9 +59,15 @@ class PairGenerator:
         return (nx * self.h_f, ny * self.h_f, nz * self.h_f)
 
     def fields(self, centres, radii, modes):
-        phi = inputs.sphere_union_sdf(self.fs, self.h_f, centres, radii, self.device, torch.float32)
-        F = inputs.speed_fourier(self.fs, self.h_f, modes, self.device, torch.float32)
-        return phi.contiguous(), F.contiguous()
+        """Step 0 on the fine grid by the library's device generators
+        (ls_init_phi / ls_init_speed); returns (phi, F) as device tensors."""
+        self.fine.init_phi(ls.LS_SHAPE_SPHERES, inputs.spheres_params(centres, radii))
+        self.fine.init_speed(ls.LS_SPEED_FOURIER, inputs.fourier_params(modes))
+        phi = torch.empty(self.fs, dtype=torch.float32, device=self.device)
+        F = torch.empty(self.fs, dtype=torch.float32, device=self.device)
+        self.fine.get_phi(phi)
+        self.fine.get_speed(F)
+        return phi, F
 
     def restrict(self, a):
         return ls.restrict4(a)
@@ -69,9 +75,7 @@ class PairGenerator:
     def run(self, centres, radii, modes, npairs):
         """Yields (phi_c^n, phi_c^{n+4}, F_c) for n = 0, 4, ... (coarse device
         tensors), plus the coarse initial state first."""
-        phi, F = self.fields(centres, radii, modes)
-        self.fine.set_phi(phi)
-        self.fine.set_speed(F)
+        phi, F = self.fields(centres, radii, modes)   # also the fine context's phi and F
         self.fine.band_rebuild(self.hw_f)
         F_c = self.restrict(F)
         prev = self.restrict(phi)

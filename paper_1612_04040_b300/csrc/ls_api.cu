@@ -1134,7 +1134,7 @@ static int shape_params_ok(int kind, const double* p, int n)
         const int lmax = (int)p[5];
         if (lmax < 1 || lmax > 16) return 0;
         const int modes = (lmax + 1) * (lmax + 1) - 1;
-        return n == 6 + 2 * modes;
+        return n == 6 + modes;
     }
     return 0;
 }
@@ -1205,6 +1205,24 @@ int ls_get_phi(ls_ctx* c, void* dst, int on_device)
 int ls_inst_get_phi(ls_ctx* c, int i, void* dst, int on_device)
 {
     return get_phi_inst(c, i, dst, on_device);
+}
+
+int ls_get_speed(ls_ctx* c, void* dst, int on_device)
+{
+    if (!c || !dst || c->n_inst != 1) return LS_EINVAL;
+    const Inst& in = c->insts[0];
+    if (!c->F || in.speed_mode != 2) return LS_ESTATE;
+    const void* srcb = region(c, c->F, in);
+    if (on_device) {
+        if (!aligned16(dst)) return LS_EINVAL;
+        KL(c, lsk::launch_unpack(srcb, dst, in, c->prec, c->stream));
+    } else {
+        RET(ensure_staging(c));
+        KL(c, lsk::launch_unpack(srcb, c->staging, in, c->prec, c->stream));
+        CK(cudaMemcpyAsync(dst, c->staging, inst_bytes(c, in), cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return LS_OK;
 }
 
 // ---- stream-ordered host input/output ----

@@ -7,10 +7,13 @@
 //   LS_SHAPE_SPHERES  params = [n, (cx, cy, cz, r) x n]: min_i |x - c_i| - r_i
 //   LS_SHAPE_TORUS    params = [cx, cy, cz, ax, ay, az, R, r] (unit axis a):
 //                     sqrt((rho - R)^2 + s^2) - r, s = (x-c).a, rho = |x-c - s a|
-//   LS_SHAPE_SH       params = [cx, cy, cz, base, amp, lmax, a_lm..., N_lm...]:
-//                     |x - c| - (base + amp * sum_lm a_lm N_lm P_l^|m|(cos t) T_m(p))
-//                     with T_m = cos(m p) (m > 0), 1 (m = 0), sin(|m| p) (m < 0),
-//                     modes ordered l = 1..lmax, m = -l..l
+//   LS_SHAPE_SH       params = [cx, cy, cz, base, amp, lmax, a_lm...]:
+//                     |x - c| - (base + amp * sum_lm a_lm Y_lm(direction)),
+//                     Y_lm the real orthonormal spherical harmonics
+//                     N_lm P_l^|m|(cos t) T_m(p), T_m = sqrt2 cos(m p) (m > 0),
+//                     1 (m = 0), sqrt2 sin(|m| p) (m < 0), with
+//                     N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) computed
+//                     here; modes ordered l = 1..lmax, m = -l..l
 // Speeds:
 //   LS_SPEED_SINUSOID 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z)
 //   LS_SPEED_COSCOS   cos(4 pi x) cos(4 pi y)
@@ -31,20 +34,23 @@ __device__ double sh_radius(const double* p, double ux, double uy, double uz)
 {
     const double base = p[3], amp = p[4];
     const int lmax = (int)p[5];
-    const int nmodes = (lmax + 1) * (lmax + 1) - 1;
     const double* a = p + 6;
-    const double* nrm = p + 6 + nmodes;
     const double ct = fmin(fmax(uz, -1.0), 1.0);
     const double st = sqrt(fmax(1.0 - ct * ct, 0.0));
     const double ph = atan2(uy, ux);
     double s = 0.0;
-    // P_l^m by the standard recurrences (no Condon-Shortley phase)
+    // P_l^m by the standard recurrences (no Condon-Shortley phase); the
+    // normalisation N_lm from the factorial ratio (l+m)!/(l-m)!, carried
+    // along l for fixed m: ratio(m, m) = (2m)!, ratio(l+1, m) = ratio(l, m)
+    // (l+1+m)/(l+1-m)
     for (int m = 0; m <= lmax; ++m) {
-        double pmm = 1.0, fact = 1.0;
+        double pmm = 1.0, fact = 1.0, ratio = 1.0;
         for (int k = 0; k < m; ++k) {
             pmm = pmm * fact * st;
             fact += 2.0;
         }
+        for (int k = 2; k <= 2 * m; ++k) ratio *= (double)k;
+        const double tm = m > 0 ? sqrt(2.0) : 1.0;
         double p_lm2 = 0.0, p_lm1 = 0.0;
         for (int l = m; l <= lmax; ++l) {
             double plm;
@@ -53,13 +59,15 @@ __device__ double sh_radius(const double* p, double ux, double uy, double uz)
             else plm = ((2 * l - 1) * ct * p_lm1 - (l + m - 1) * p_lm2) / (l - m);
             p_lm2 = p_lm1;
             p_lm1 = plm;
+            if (l > m) ratio *= (double)(l + m) / (double)(l - m);
             if (l < 1) continue;
+            const double nrm = tm * sqrt((2 * l + 1) / (4.0 * PI) / ratio);
             const int base_idx = l * l - 1;  // index of (l, m = -l)
             if (m == 0) {
-                s += a[base_idx + l] * nrm[base_idx + l] * plm;
+                s += a[base_idx + l] * nrm * plm;
             } else {
-                s += a[base_idx + l + m] * nrm[base_idx + l + m] * plm * cos(m * ph);
-                s += a[base_idx + l - m] * nrm[base_idx + l - m] * plm * sin(m * ph);
+                s += a[base_idx + l + m] * nrm * plm * cos(m * ph);
+                s += a[base_idx + l - m] * nrm * plm * sin(m * ph);
             }
         }
     }

@@ -254,9 +254,9 @@ cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float
                          int mode, unsigned* status, cudaStream_t s);
 cudaError_t launch_features(const float* phi, const float* phit, const float* F, float Fc,
                             float inv_h, long long n, void* X, cudaStream_t s);
-cudaError_t launch_count_mask(const float* phi, float gamma, long long n, int* count, cudaStream_t s);
+cudaError_t launch_count_mask(const float* phi, double gamma, long long n, int* count, cudaStream_t s);
 cudaError_t launch_loss_grad(const float* z, const float* phi, const float* phit,
-                             const float* phiref, float inv_h, float gamma, const int* count,
+                             const float* phiref, float inv_h, double gamma, const int* count,
                              long long n, void* dz, double* loss, cudaStream_t s);
 cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci,
                                int co, float* dW, float* db, cudaStream_t s);

@@ -46,10 +46,11 @@ __global__ void k_features(const float* __restrict__ phi, const float* __restric
 
 // loss = sum over masked points of (z - t)^2 / count;  dz = 2 (z - t) / count
 // on masked points (channel 0 of a 16-channel BF16 gradient), 0 elsewhere.
-// mask: |phi^n| < gamma (the tube of Eq. 6).  target t = (phi_ref - phi~) / h.
+// mask: |phi^n| < gamma (the tube of Eq. 6), compared in FP64 like the band's
+// tube test.  target t = (phi_ref - phi~) / h.
 __global__ void k_loss_grad(const float* __restrict__ z, const float* __restrict__ phi,
                             const float* __restrict__ phit, const float* __restrict__ phiref,
-                            float inv_h, float gamma, const int* __restrict__ count, long long n,
+                            float inv_h, double gamma, const int* __restrict__ count, long long n,
                             __nv_bfloat16* __restrict__ dz, double* loss)
 {
     double local = 0.0;
@@ -57,7 +58,7 @@ __global__ void k_loss_grad(const float* __restrict__ z, const float* __restrict
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         float g = 0.f;
-        if (fabsf(phi[p]) < gamma) {
+        if (fabs((double)phi[p]) < gamma) {
             const float t = (phiref[p] - phit[p]) * inv_h;
             const float r = z[p] - t;
             local += (double)r * r * inv_cnt;
@@ -74,12 +75,12 @@ __global__ void k_loss_grad(const float* __restrict__ z, const float* __restrict
     if ((threadIdx.x & 31) == 0 && local != 0.0) atomicAdd(loss, local);
 }
 
-__global__ void k_count_mask(const float* __restrict__ phi, float gamma, long long n, int* count)
+__global__ void k_count_mask(const float* __restrict__ phi, double gamma, long long n, int* count)
 {
     int local = 0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x)
-        local += fabsf(phi[p]) < gamma;
+        local += fabs((double)phi[p]) < gamma;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
@@ -255,14 +256,14 @@ cudaError_t launch_features(const float* phi, const float* phit, const float* F,
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_mask(const float* phi, float gamma, long long n, int* count, cudaStream_t s)
+cudaError_t launch_count_mask(const float* phi, double gamma, long long n, int* count, cudaStream_t s)
 {
     k_count_mask<<<grid_for(n, 256), 256, 0, s>>>(phi, gamma, n, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_loss_grad(const float* z, const float* phi, const float* phit,
-                             const float* phiref, float inv_h, float gamma, const int* count,
+                             const float* phiref, float inv_h, double gamma, const int* count,
                              long long n, void* dz, double* loss, cudaStream_t s)
 {
     k_loss_grad<<<grid_for(n, 256), 256, 0, s>>>(z, phi, phit, phiref, inv_h, gamma, count, n,

@@ -8,6 +8,7 @@
 // accumulation and FP32 master parameters.  Parameter vector layout: for
 // layer l = 0..3: W_l [27][ci_l][co_l] then b_l [co_l].
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -308,7 +309,7 @@ int ls_learned_train_stored(ls_ctx* c, int iters, double lr, double dt, double h
     cudaStream_t s = c->stream;
     const Inst in = c->in0();
     const float inv_h = (float)in.inv_h;
-    const float gamma = (float)(halfwidth * in.h);
+    const double gamma = halfwidth * in.h;
     unsigned long long st = seed;
     double loss = 0.0;
     // the context's phi / speed are used as scratch for the plain coarse
@@ -672,6 +673,40 @@ int ls_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci
     if (!x || !dy || !dW || ci < 1 || ci > 16 || co < 1 || co > 16) return LS_EINVAL;
     if (nx % 64 || ny < 1 || nz < 1) return LS_EINVAL;
     LCK(lsk::launch_conv3_wgrad(x, dy, nx, ny, nz, ci, co, dW, db, (cudaStream_t)stream));
+    return LS_OK;
+}
+
+int ls_learned_features(const float* phi, const float* phit, const float* F, double Fc, double h,
+                        long long n, void* X, void* stream)
+{
+    if (!phi || !phit || !X || n < 1 || !std::isfinite(h) || !(h > 0.0) || !std::isfinite(Fc))
+        return LS_EINVAL;
+    if (((uintptr_t)X & 15u) != 0) return LS_EINVAL;
+    LCK(lsk::launch_features(phi, phit, F, (float)Fc, (float)(1.0 / h), n, X, (cudaStream_t)stream));
+    return LS_OK;
+}
+
+int ls_learned_loss_grad(const float* z, const float* phi, const float* phit, const float* phiref,
+                         long long n, double h, double gamma, void* dz, int* count, double* loss,
+                         void* stream)
+{
+    if (!z || !phi || !phit || !phiref || !dz || !count || !loss || n < 1) return LS_EINVAL;
+    if (!std::isfinite(h) || !(h > 0.0) || !std::isfinite(gamma) || !(gamma > 0.0)) return LS_EINVAL;
+    if (((uintptr_t)dz & 15u) != 0) return LS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    LCK(cudaMemsetAsync(count, 0, sizeof(int), s));
+    LCK(cudaMemsetAsync(loss, 0, sizeof(double), s));
+    LCK(lsk::launch_count_mask(phi, gamma, n, count, s));
+    LCK(lsk::launch_loss_grad(z, phi, phit, phiref, (float)(1.0 / h), gamma, count, n, dz, loss, s));
+    return LS_OK;
+}
+
+int ls_adam_step(float* w, const float* g, float* m, float* v, int n, double lr, int step,
+                 void* stream)
+{
+    if (!w || !g || !m || !v || n < 1 || step < 1 || !std::isfinite(lr) || !(lr > 0.0))
+        return LS_EINVAL;
+    LCK(lsk::launch_adam(w, g, m, v, n, (float)lr, step, (cudaStream_t)stream));
     return LS_OK;
 }
 

@@ -358,13 +358,9 @@ def torus_params(centre, axis, R, r):
 
 
 def sh_params(w: "PerturbedSphere", centre=(0.5, 0.5, 0.5)):
-    norms = []
-    for l in range(1, w.lmax + 1):
-        for m in range(-l, l + 1):
-            am = abs(m)
-            nv = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - am) / math.factorial(l + am))
-            norms.append(nv if m == 0 else math.sqrt(2.0) * nv)
-    return np.asarray(list(centre) + [w.base, w.amp * w.scale, float(w.lmax)] + list(w.coeffs) + norms,
+    """[cx, cy, cz, base, amp, lmax, a_lm...]: the device generator computes
+    the normalisations of the real spherical harmonics itself."""
+    return np.asarray(list(centre) + [w.base, w.amp * w.scale, float(w.lmax)] + list(w.coeffs),
                       dtype=np.float64)
 
 

@@ -56,6 +56,7 @@ SIGNATURES = {
     "ls_step": (_i, [_vp, _i, _d, _i, _i, _c.POINTER(_d)]),
     "ls_set_full_domain": (_i, [_vp, _i]),
     "ls_get_phi": (_i, [_vp, _vp, _i]),
+    "ls_get_speed": (_i, [_vp, _vp, _i]),
     "ls_stage_inputs": (_i, [_vp, _vp, _vp]),
     "ls_load_staged": (_i, [_vp]),
     "ls_get_phi_async": (_i, [_vp, _vp]),
@@ -102,6 +103,9 @@ SIGNATURES = {
     "ls_conv3_bf16": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
     "ls_conv3_wgrad": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
     "ls_restrict4": (_i, [_vp, _i, _i, _i, _vp, _vp]),
+    "ls_learned_features": (_i, [_vp, _vp, _vp, _d, _d, _ll, _vp, _vp]),
+    "ls_learned_loss_grad": (_i, [_vp, _vp, _vp, _vp, _ll, _d, _d, _vp, _vp, _vp, _vp]),
+    "ls_adam_step": (_i, [_vp, _vp, _vp, _vp, _i, _d, _i, _vp]),
     "ls_profile_enable": (_i, [_vp, _i]),
     "ls_get_profile": (_i, [_vp, _vp]),
     "ls_reset_profile": (_i, [_vp]),
@@ -282,6 +286,55 @@ def restrict4(fine, stream=None):
     return out
 
 
+def _f32_cuda(name, t, n=None):
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float32 CUDA tensor" % name)
+    if n is not None and t.numel() != n:
+        raise ValueError("%s must hold %d values" % (name, n))
+    return _dptr(t)
+
+
+def learned_features(phi, phit, h, F=None, Fc=0.0, stream=None):
+    """ls_learned_features: BF16 (..., 16) features of float32 CUDA tensors."""
+    lib = load()
+    n = phi.numel()
+    X = torch.empty(tuple(phi.shape) + (16,), dtype=torch.bfloat16, device=phi.device)
+    Fp = None if F is None else _f32_cuda("F", F, n)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib.ls_learned_features(_f32_cuda("phi", phi), _f32_cuda("phit", phit, n), Fp, float(Fc),
+                                  float(h), n, _dptr(X), ctypes.c_void_p(stream)), "ls_learned_features")
+    return X
+
+
+def learned_loss_grad(z, phi, phit, phiref, h, gamma, stream=None):
+    """ls_learned_loss_grad: returns (dz BF16 (..., 16), count int32 (1,),
+    loss float64 (1,)) as CUDA tensors."""
+    lib = load()
+    n = phi.numel()
+    dz = torch.empty(tuple(phi.shape) + (16,), dtype=torch.bfloat16, device=phi.device)
+    count = torch.empty(1, dtype=torch.int32, device=phi.device)
+    loss = torch.empty(1, dtype=torch.float64, device=phi.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib.ls_learned_loss_grad(_f32_cuda("z", z, n), _f32_cuda("phi", phi), _f32_cuda("phit", phit, n),
+                                   _f32_cuda("phiref", phiref, n), n, float(h), float(gamma), _dptr(dz),
+                                   _dptr(count), _dptr(loss), ctypes.c_void_p(stream)),
+          "ls_learned_loss_grad")
+    return dz, count, loss
+
+
+def adam_step(w, g, m, v, t, lr, stream=None):
+    """ls_adam_step on float32 CUDA tensors (w, m, v updated in place)."""
+    lib = load()
+    n = w.numel()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    check(lib.ls_adam_step(_f32_cuda("w", w), _f32_cuda("g", g, n), _f32_cuda("m", m, n),
+                           _f32_cuda("v", v, n), n, float(lr), int(t), ctypes.c_void_p(stream)),
+          "ls_adam_step")
+
+
 def probe_dfma(iters=1 << 16, stream=None):
     """Measured FP64 peak of the current device (TFLOP/s, FMA = 2)."""
     lib = load()
@@ -391,6 +444,14 @@ class LevelSet:
             out = np.empty(self.shape, dtype=self.dtype)
         p, dev = array_ptr(out, self.dtype, self.count)
         check(self.lib.ls_get_phi(self.ctx, p, dev), "ls_get_phi")
+        return out
+
+    def get_speed(self, out=None):
+        """The speed field F (row-major, context precision)."""
+        if out is None:
+            out = np.empty(self.shape, dtype=self.dtype)
+        p, dev = array_ptr(out, self.dtype, self.count)
+        check(self.lib.ls_get_speed(self.ctx, p, dev), "ls_get_speed")
         return out
 
     # stream-ordered host input/output (ls_stage_inputs ... ls_wait_host);

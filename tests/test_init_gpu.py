@@ -51,11 +51,43 @@ def test_sphere_union_and_torus(prec):
 
 
 def test_spherical_harmonic_sphere():
+    """The device computes the harmonics' normalisations itself (the
+    parameters carry only centre, base, amplitude, lmax and the a_lm); the
+    reference is the host basis, pinned orthonormal by quadrature on the CPU."""
     w = inputs.PerturbedSphere(n=64)
     shape, h = (64, 64, 64), 1.0 / 64
     ref = w.phi().numpy()
-    dev = device_field(shape, h, ls.LS_FP64, lambda g: g.init_phi(ls.LS_SHAPE_SH, inputs.sh_params(w)))
+    p = inputs.sh_params(w)
+    assert p.size == 6 + 80
+    dev = device_field(shape, h, ls.LS_FP64, lambda g: g.init_phi(ls.LS_SHAPE_SH, p))
     assert np.max(np.abs(dev - ref)) <= 1e-12
+    g = ls.LevelSet(16, 16, 16, 1.0 / 16, ls.LS_FP64)
+    with pytest.raises(ls.LSError) as e:                      # the old layout with N_lm appended
+        g.init_phi(ls.LS_SHAPE_SH, np.concatenate([p, np.ones(80)]))
+    assert e.value.status == ls.LS_EINVAL
+    g.close()
+
+
+@pytest.mark.parametrize("prec", [ls.LS_FP32, ls.LS_FP64])
+def test_speed_field_read_back(prec):
+    shape, h = (24, 32, 40), 1.0 / 40
+    modes = inputs.fourier_modes(np.random.default_rng(4))
+    ref = inputs.speed_fourier(shape, h, modes).numpy()
+    nz, ny, nx = shape
+    g = ls.LevelSet(nx, ny, nz, h, prec)
+    with pytest.raises(ls.LSError) as e:
+        g.get_speed()
+    assert e.value.status == ls.LS_ESTATE
+    g.init_speed(ls.LS_SPEED_FOURIER, inputs.fourier_params(modes))
+    compare(g.get_speed(), ref, prec)
+    dev = torch.empty(shape, dtype=torch.float32 if prec == ls.LS_FP32 else torch.float64, device="cuda")
+    g.get_speed(dev)
+    compare(dev.cpu().numpy(), ref, prec)
+    g.set_speed_const(0.5)
+    with pytest.raises(ls.LSError) as e:
+        g.get_speed()
+    assert e.value.status == ls.LS_ESTATE
+    g.close()
 
 
 @pytest.mark.parametrize("kind", ["sinusoid", "coscos", "fourier"])

@@ -5,7 +5,13 @@ training.
 
 Bars: convolution outputs are BF16, so they are compared with the oracle on
 the same BF16-rounded inputs and weights within 1e-2 relative (BF16 has an
-8-bit mantissa; the accumulation is FP32); FP32 outputs within 1e-4."""
+8-bit mantissa; the accumulation is FP32); FP32 outputs within 1e-4.
+
+Two shapes: SMALL gives each CTA of the persistent convolution one block;
+MULTI (64 x 64 x 128 points, 1024 blocks on at most 148 CTAs) gives every CTA
+six or more blocks, so the reuse of both shared-memory stages, both TMEM
+accumulator buffers and every mbarrier phase after the first are compared
+with the oracle too."""
 import numpy as np
 import pytest
 import torch
@@ -16,7 +22,9 @@ from paper_1612_04040_b300 import native as ls
 
 pytestmark = pytest.mark.gpu
 
-SHAPE = (6, 4, 128)  # (nz, ny, nx): nx a multiple of 128, ny and nz even
+SMALL = (6, 4, 128)   # (nz, ny, nx): nx a multiple of 128, ny and nz even
+MULTI = (64, 64, 128)
+SHAPES = pytest.mark.parametrize("shape", [SMALL, MULTI], ids=["small", "multi"])
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,10 +36,10 @@ def bf16_round(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy()
 
 
-def rand_act(seed, ci, scale=1.0):
+def rand_act(seed, ci, shape, scale=1.0):
     g = np.random.default_rng(seed)
-    x = np.zeros(SHAPE + (16,), dtype=np.float32)
-    x[..., :ci] = g.normal(size=SHAPE + (ci,)) * scale
+    x = np.zeros(shape + (16,), dtype=np.float32)
+    x[..., :ci] = g.normal(size=shape + (ci,)) * scale
     return bf16_round(x)
 
 
@@ -45,9 +53,10 @@ def close(gpu, ref, rtol):
     assert err <= rtol * scale, (err, scale)
 
 
+@SHAPES
 @pytest.mark.parametrize("ci,co", [(16, 16), (3, 16)])
-def test_conv_forward_relu(ci, co):
-    x = rand_act(1, ci)
+def test_conv_forward_relu(ci, co, shape):
+    x = rand_act(1, ci, shape)
     g = np.random.default_rng(2)
     W = bf16_round(g.normal(size=(27, ci, co)) * 0.2)
     b = g.normal(size=(co,)).astype(np.float32) * 0.1
@@ -58,8 +67,9 @@ def test_conv_forward_relu(ci, co):
     close(out.float().cpu().numpy()[..., :co], ref, 1e-2)
 
 
-def test_conv_last_layer_fp32():
-    x = rand_act(3, 16)
+@SHAPES
+def test_conv_last_layer_fp32(shape):
+    x = rand_act(3, 16, shape)
     g = np.random.default_rng(4)
     W = bf16_round(g.normal(size=(27, 16, 1)) * 0.2)
     b = np.array([0.3], dtype=np.float32)
@@ -70,15 +80,16 @@ def test_conv_last_layer_fp32():
     close(out.cpu().numpy(), ref, 1e-4)
 
 
+@SHAPES
 @pytest.mark.parametrize("ci,co", [(16, 16), (16, 1)])
-def test_conv_input_gradient_masked(ci, co):
+def test_conv_input_gradient_masked(ci, co, shape):
     """mode 2: conv^T of the output gradient, times the ReLU mask."""
-    gy = np.zeros(SHAPE + (16,), dtype=np.float32)
-    gy[..., :co] = np.random.default_rng(5).normal(size=SHAPE + (co,))
+    gy = np.zeros(shape + (16,), dtype=np.float32)
+    gy[..., :co] = np.random.default_rng(5).normal(size=shape + (co,))
     gy = bf16_round(gy)
     g = np.random.default_rng(6)
     W = bf16_round(g.normal(size=(27, ci, co)) * 0.2)
-    mask = bf16_round(np.maximum(g.normal(size=SHAPE + (16,)), 0))
+    mask = bf16_round(np.maximum(g.normal(size=shape + (16,)), 0))
     out, st = ls.conv3_bf16(to_dev_bf16(gy), torch.from_numpy(W).cuda(), None, 2, mask=to_dev_bf16(mask))
     torch.cuda.synchronize()
     assert int(st.item()) == 0
@@ -86,11 +97,12 @@ def test_conv_input_gradient_masked(ci, co):
     close(out.float().cpu().numpy()[..., :ci], ref, 1e-2)
 
 
+@SHAPES
 @pytest.mark.parametrize("ci,co", [(16, 16), (3, 16), (16, 1)])
-def test_weight_gradient(ci, co):
-    x = rand_act(7, ci)
-    gy = np.zeros(SHAPE + (16,), dtype=np.float32)
-    gy[..., :co] = np.random.default_rng(8).normal(size=SHAPE + (co,))
+def test_weight_gradient(ci, co, shape):
+    x = rand_act(7, ci, shape)
+    gy = np.zeros(shape + (16,), dtype=np.float32)
+    gy[..., :co] = np.random.default_rng(8).normal(size=shape + (co,))
     gy = bf16_round(gy)
     dW, db = ls.conv3_wgrad(to_dev_bf16(x), to_dev_bf16(gy), ci, co)
     rW, rb = oracle.conv3_bwd_weight(x[..., :ci].astype(np.float64), gy[..., :co].astype(np.float64))
@@ -104,9 +116,10 @@ def test_restriction():
     assert np.max(np.abs(c - oracle.restrict4(f.astype(np.float64)))) <= 1e-6
 
 
-def test_conv_matches_oracle_network_forward():
+@SHAPES
+def test_conv_matches_oracle_network_forward(shape):
     """The four layers chained on the GPU against the oracle's network."""
-    x = rand_act(10, 3)
+    x = rand_act(10, 3, shape)
     r = np.random.default_rng(11)
     chans = [3, 16, 16, 16, 1]
     params = [(bf16_round(r.normal(size=(27, chans[k], chans[k + 1])) * 0.15),
