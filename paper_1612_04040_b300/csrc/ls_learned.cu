@@ -155,16 +155,18 @@ __global__ void __launch_bounds__(448) k_conv3_wgrad(const __nv_bfloat16* __rest
     }
 }
 
-// Adam (decoupled moments, bias-corrected) on a flat parameter vector
+// Adam (bias-corrected moments) on a flat parameter vector.  The factors
+// come from the host, computed in FP64 and rounded once: 1 - beta2 taken in
+// FP32 from a rounded beta2 would be off by 1.3e-5 relative.
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
-                       float c1, float c2)
+                       float* __restrict__ v, int n, float lr, float b1, float b2, float omb1,
+                       float omb2, float eps, float c1, float c2)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float mi = b1 * m[i] + omb1 * gi;
+    const float vi = b2 * v[i] + omb2 * gi * gi;
     m[i] = mi;
     v[i] = vi;
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -285,9 +287,10 @@ cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, in
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, float lr, int step,
                         cudaStream_t s)
 {
-    const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-    k_adam<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, lr, b1, b2, 1e-8f, c1, c2);
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = (float)(1.0 - pow(b1, (double)step)), c2 = (float)(1.0 - pow(b2, (double)step));
+    k_adam<<<(n + 255) / 256, 256, 0, s>>>(w, g, m, v, n, lr, (float)b1, (float)b2, (float)(1.0 - b1),
+                                           (float)(1.0 - b2), 1e-8f, c1, c2);
     return cudaGetLastError();
 }
 

@@ -112,13 +112,17 @@ def test_adam_matches_oracle():
     w = g.normal(size=n).astype(np.float32)
     dw, dm, dv = cuda32(w), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
     rw, rm, rv = w.astype(np.float64), np.zeros(n), np.zeros(n)
+    gsum = np.zeros(n)
     for t in range(1, 6):
         grad = (g.normal(size=n) * 10.0 ** g.uniform(-4, 1, size=n)).astype(np.float32)
         ls.adam_step(dw, cuda32(grad), dm, dv, t, 1e-3)
         rw, rm, rv = oracle.adam_step(rw, grad, rm, rv, t, 1e-3)
+        gsum += np.abs(grad)
     torch.cuda.synchronize()
     assert np.max(np.abs(dw.cpu().numpy() - rw)) <= 1e-5 * 5e-3 + 1e-6 * np.max(np.abs(rw))
-    assert np.allclose(dm.cpu().numpy(), rm, rtol=1e-5, atol=1e-12)
+    # m sums gradients of either sign: FP32 rounding is bounded by the terms'
+    # magnitudes, not by the (possibly cancelled) result; v sums squares
+    assert np.all(np.abs(dm.cpu().numpy() - rm) <= 1e-5 * np.abs(rm) + 2e-6 * gsum)
     assert np.allclose(dv.cpu().numpy(), rv, rtol=1e-5, atol=1e-20)
 
 
