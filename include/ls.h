@@ -541,14 +541,16 @@ int ls_learned_fallbacks(ls_ctx *ctx, unsigned long long *n);
  * BF16 [p][16] conv^T(x) * [mask > 0], x = gradient of the layer output,
  * W = the forward weights, mask = BF16 [p][16].
  * ls_conv3_wgrad: dW [27][ci][co] += sum_p x[p + off(tap)] dy[p],
- * db[co] += sum_p dy[p] (nx a multiple of 64; caller zeroes dW, db).
+ * db[co] += sum_p dy[p] (db may be NULL), on the tensor cores with FP32
+ * accumulation; x and dy BF16 [p][16] (16-byte aligned), nx a multiple of
+ * 64; the caller zeroes dW and db; status as for ls_conv3_bf16.
  * ls_restrict4: coarse[I] = mean of the fine points 4I+1, 4I+2 per axis. */
 #define LS_CONV3_WORK_BYTES 13824
 int ls_conv3_bf16(const void *x, int nx, int ny, int nz, const float *W, int ci, int co,
                   const float *bias, int mode, const void *mask, void *out, void *work,
                   unsigned *status, void *cuda_stream);
 int ls_conv3_wgrad(const void *x, const void *dy, int nx, int ny, int nz, int ci, int co,
-                   float *dW, float *db, void *cuda_stream);
+                   float *dW, float *db, unsigned *status, void *cuda_stream);
 int ls_restrict4(const float *fine, int nfx, int nfy, int nfz, float *coarse, void *cuda_stream);
 
 /* The corrector's element-wise steps on caller-owned device buffers (no

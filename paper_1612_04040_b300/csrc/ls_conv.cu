@@ -329,6 +329,182 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
                      : "memory");
 }
 
+// ---- weight gradient on the tensor cores --------------------------------
+//
+// dW[t][c][o] = sum_p x[p + off(t)][c] dy[p][o] and db[o] = sum_p dy[p][o]
+// as one GEMM per CTA: M = (tap slot, input channel) in 4 M-tiles of 8 tap
+// slots x 16 channels, N = 16 output channels, K = the points of the CTA's
+// chunks.  Both operands are MN-major (the 8 channels of a point are one
+// contiguous 16-byte run): a chunk is 64 consecutive x-points of one
+// (y, z) row, and for every tap the TMA engine loads the chunk's points
+// shifted by the tap offset (out-of-grid points zero-filled: the
+// convolution's zero padding), one 1 KB box per tap and channel half, so
+// the 8-channel groups of all taps sit at one uniform stride (SBO = 1 KB)
+// and the 8-point groups at 128 B (LBO).  Tap slot 27 is a box of ones in
+// shared memory: its rows accumulate sum_p dy[p][o], the bias gradient;
+// slots 28..31 repeat it and are discarded.  The accumulator (64 TMEM
+// columns) lives across all chunks of the CTA; the epilogue adds it to dW
+// and db with FP32 atomics.
+constexpr int WG_PTS = 64;
+constexpr int WG_BOX = WG_PTS * 16;                  // 64 points x 8 channels, BF16
+constexpr int WG_SLOTS = 32;
+constexpr int WG_A_BYTES = WG_SLOTS * 2 * WG_BOX;    // 64 KB: 32 slots x 2 halves
+constexpr int WG_LOAD_BYTES = (27 * 2 + 2) * WG_BOX; // what the TMA writes per chunk
+constexpr int WG_STAGE = WG_A_BYTES + 2 * WG_BOX;    // + dy (2 halves)
+constexpr int WG_NSTAGE = 3;
+constexpr int WG_THREADS = 192;
+// kind::f16, D F32, A and B BF16, both MN-major (transpose bits 15, 16),
+// N = 16, M = 128
+constexpr unsigned IDESC_WG = IDESC | (1u << 15) | (1u << 16);
+
+struct WgradArgs {
+    float* dW;        // [27][ci][co], accumulated into
+    float* db;        // [co] or NULL
+    unsigned* status;
+    int nx, ny, nz, ci, co;
+};
+
+__global__ void __launch_bounds__(WG_THREADS, 1)
+    k_conv3_wgrad_tc(const __grid_constant__ CUtensorMap mx0, const __grid_constant__ CUtensorMap mx1,
+                     const __grid_constant__ CUtensorMap mg0, const __grid_constant__ CUtensorMap mg1,
+                     WgradArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) unsigned long long full[WG_NSTAGE], empty[WG_NSTAGE], acc_full;
+    __shared__ unsigned tmem_base_s;
+    __shared__ volatile int abort_s;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ncx = a.nx / WG_PTS;
+    const long long nchunks = (long long)ncx * a.ny * a.nz;
+
+    // the ones slots (27..31, both halves) of every stage; the TMA never
+    // writes there
+    for (int st = 0; st < WG_NSTAGE; ++st) {
+        uint4* o = reinterpret_cast<uint4*>(smem + st * WG_STAGE + 27 * 2 * WG_BOX);
+        const unsigned one2 = 0x3F803F80u;  // two BF16 ones
+        for (int i = tid; i < 5 * 2 * WG_BOX / 16; i += WG_THREADS) o[i] = make_uint4(one2, one2, one2, one2);
+    }
+    if (tid == 0) {
+        for (int s = 0; s < WG_NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&acc_full, 1);
+        abort_s = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_s)),
+                     "r"(64)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = tmem_base_s;
+    const unsigned base = smem_u32(smem);
+    int issued = 0;  // chunks whose loads thread 0 issued (for the exit drain)
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int i = 0;
+            for (long long q = blockIdx.x; q < nchunks && !abort_s; q += gridDim.x, ++i) {
+                const int s = i % WG_NSTAGE, u = i / WG_NSTAGE;
+                if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    abort_s = 1;
+                    break;
+                }
+                const int x0 = (int)(q % ncx) * WG_PTS;
+                const int y = (int)((q / ncx) % a.ny), z = (int)(q / ((long long)ncx * a.ny));
+                unsigned char* st = smem + s * WG_STAGE;
+                mbar_expect_tx(&full[s], WG_LOAD_BYTES);
+                for (int t = 0; t < 27; ++t) {
+                    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+                    tma_load_4d(st + (2 * t) * WG_BOX, &mx0, 0, x0 + dx, y + dy, z + dz, &full[s]);
+                    tma_load_4d(st + (2 * t + 1) * WG_BOX, &mx1, 0, x0 + dx, y + dy, z + dz, &full[s]);
+                }
+                tma_load_4d(st + WG_A_BYTES, &mg0, 0, x0, y, z, &full[s]);
+                tma_load_4d(st + WG_A_BYTES + WG_BOX, &mg1, 0, x0, y, z, &full[s]);
+                issued = i + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int i = 0;
+            for (long long q = blockIdx.x; q < nchunks && !abort_s; q += gridDim.x, ++i) {
+                const int s = i % WG_NSTAGE, u = i / WG_NSTAGE;
+                if (!mbar_wait(&full[s], u & 1)) {
+                    atomicOr(a.status, ST_TIMEOUT);
+                    abort_s = 1;
+                    break;
+                }
+                fence_after();
+                const unsigned st = base + s * WG_STAGE;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned long long da = smem_desc(st + j * 16 * WG_BOX, 128, WG_BOX);
+                    const unsigned long long db = smem_desc(st + WG_A_BYTES, 128, WG_BOX);
+#pragma unroll
+                    for (int k = 0; k < WG_PTS / 16; ++k) {
+                        // K step k = points 16k .. 16k+15 = two 8-point groups (256 B)
+                        const unsigned acc = (i > 0 || k > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+                            "  tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem + 16 * j),
+                            "l"(da + (unsigned long long)(k * 16)), "l"(db + (unsigned long long)(k * 16)),
+                            "r"(IDESC_WG), "r"(acc)
+                            : "memory");
+                    }
+                }
+                mma_commit(&empty[s]);
+            }
+            // all issued MMAs (also after an abort) complete before acc_full
+            mma_commit(&acc_full);
+        }
+    } else {
+        // epilogue: lane quadrant q = warp % 4 -> rows 32 q + lane of each M-tile
+        const int q = warp & 3;
+        const bool any = (long long)blockIdx.x < nchunks;
+        if (any) {
+            if (!mbar_wait(&acc_full, 0)) {
+                if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
+                abort_s = 1;
+            } else if (!abort_s) {
+                fence_after();
+                const int r = 32 * q + lane;
+                const int c = r & 15;
+                for (int j = 0; j < 4; ++j) {
+                    float v[16];
+                    tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + 16 * j, v);
+                    const int slot = 8 * j + (r >> 4);
+                    if (slot < 27 && c < a.ci) {
+                        float* w = a.dW + ((size_t)slot * a.ci + c) * a.co;
+                        for (int o = 0; o < a.co; ++o) atomicAdd(&w[o], v[o]);
+                    } else if (slot == 27 && c == 0 && a.db) {
+                        for (int o = 0; o < a.co; ++o) atomicAdd(&a.db[o], v[o]);
+                    }
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    // copies still in flight after an abort land before the CTA exits
+    if (abort_s && tid == 0) {
+        for (int i = (issued > WG_NSTAGE ? issued - WG_NSTAGE : 0); i < issued; ++i)
+            mbar_wait(&full[i % WG_NSTAGE], (i / WG_NSTAGE) & 1, 1 << 20);
+    }
+    if (abort_s && tid == 32) mbar_wait(&acc_full, 0, 1 << 20);
+    __syncthreads();
+    fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64)
+                     : "memory");
+}
+
 // self-test of the bounded wait: an mbarrier nobody arrives at; the wait
 // must give up after `polls` polls and record ST_TIMEOUT
 __global__ void k_selftest_wait(unsigned* status, long long polls)
@@ -388,15 +564,17 @@ bool conv3_shape_ok(int nx, int ny, int nz)
 }
 
 // tensor maps over act[nz][ny][nx][16] bf16 viewed as (8 channels, x, y, z):
-// map[h] covers channels 8h..8h+7 (base address + 16 h bytes)
-cudaError_t make_act_maps(CUtensorMap* maps, const void* act, int nx, int ny, int nz)
+// map[h] covers channels 8h..8h+7 (base address + 16 h bytes); box of
+// bx x by x bz points
+static cudaError_t make_maps_box(CUtensorMap* maps, const void* act, int nx, int ny, int nz, int bx,
+                                 int by, int bz)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     if (((uintptr_t)act & 15u) != 0) return cudaErrorInvalidValue;
     const cuuint64_t dims[4] = {8, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t strides[3] = {32, (cuuint64_t)32 * nx, (cuuint64_t)32 * nx * ny};
-    const cuuint32_t box[4] = {8, PX, PY, PZ};
+    const cuuint32_t box[4] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     for (int h = 0; h < 2; ++h) {
         CUresult r = fn(&maps[h], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
@@ -406,6 +584,51 @@ cudaError_t make_act_maps(CUtensorMap* maps, const void* act, int nx, int ny, in
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
     return cudaSuccess;
+}
+
+cudaError_t make_act_maps(CUtensorMap* maps, const void* act, int nx, int ny, int nz)
+{
+    return make_maps_box(maps, act, nx, ny, nz, PX, PY, PZ);
+}
+
+bool conv3_wgrad_shape_ok(int nx, int ny, int nz)
+{
+    return nx >= WG_PTS && nx % WG_PTS == 0 && ny >= 1 && nz >= 1;
+}
+
+cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci,
+                               int co, float* dW, float* db, unsigned* status, cudaStream_t s)
+{
+    if (!conv3_wgrad_shape_ok(nx, ny, nz) || ci < 1 || ci > 16 || co < 1 || co > 16)
+        return cudaErrorInvalidValue;
+    CUtensorMap mx[2], mg[2];
+    cudaError_t e = make_maps_box(mx, x, nx, ny, nz, WG_PTS, 1, 1);
+    if (e != cudaSuccess) return e;
+    e = make_maps_box(mg, dy, nx, ny, nz, WG_PTS, 1, 1);
+    if (e != cudaSuccess) return e;
+    static bool attr = false;
+    const int smem = WG_NSTAGE * WG_STAGE;
+    if (!attr) {
+        e = cudaFuncSetAttribute(k_conv3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    WgradArgs a;
+    a.dW = dW;
+    a.db = db;
+    a.status = status;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.ci = ci;
+    a.co = co;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long nchunks = (long long)(nx / WG_PTS) * ny * nz;
+    const int grid = (int)(nchunks < sms ? nchunks : sms);
+    k_conv3_wgrad_tc<<<grid, WG_THREADS, smem, s>>>(mx[0], mx[1], mg[0], mg[1], a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_selftest_wait(unsigned* status, long long polls, cudaStream_t s)

@@ -258,8 +258,11 @@ cudaError_t launch_count_mask(const float* phi, double gamma, long long n, int* 
 cudaError_t launch_loss_grad(const float* z, const float* phi, const float* phit,
                              const float* phiref, float inv_h, double gamma, const int* count,
                              long long n, void* dz, double* loss, cudaStream_t s);
+// dW [27][ci][co] += sum_p x[p + off(tap)] dy[p], db += sum_p dy[p] (db may
+// be NULL) on the tensor cores; nx a multiple of 64
+bool conv3_wgrad_shape_ok(int nx, int ny, int nz);
 cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci,
-                               int co, float* dW, float* db, cudaStream_t s);
+                               int co, float* dW, float* db, unsigned* status, cudaStream_t s);
 cudaError_t launch_adam(float* w, const float* g, float* m, float* v, int n, float lr, int step,
                         cudaStream_t s);
 cudaError_t launch_residual(float* phit, const float* z, const int* list, const int* count,

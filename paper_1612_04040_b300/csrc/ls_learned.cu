@@ -1,7 +1,7 @@
 // ls_learned.cu -- the learned coarse-grid corrector's non-convolution
-// kernels (not in the paper): feature assembly, loss and its gradient,
-// weight / bias gradients of a 3x3x3 convolution, Adam, the band-residual
-// check with plain-step fallback, and the fine -> coarse restriction.
+// kernels (not in the paper): feature assembly, loss and its gradient, Adam,
+// the band-residual check with plain-step fallback, and the fine -> coarse
+// restriction.  (The convolutions and their gradients are in ls_conv.cu.)
 //
 // Corrector: z = CNN(features), phi^{n+1} = phi~ + h * z on band points,
 // where phi~ = the plain upwind step (Eq. 3) of phi^n and the features are
@@ -84,75 +84,6 @@ __global__ void k_count_mask(const float* __restrict__ phi, double gamma, long l
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(count, local);
-}
-
-// Weight and bias gradients of a 3x3x3 convolution on CUDA cores (FP32):
-// dW[t][c][o] = sum_p x[p + off(t)][c] * dy[p][o],  db[o] = sum_p dy[p][o].
-// One block per chunk of 64 consecutive x points of one (y, z) row; the input
-// rows (x0-1 .. x0+64) of the 9 (y, z) neighbours and the dy row are staged in
-// shared memory as FP32; thread (t, cb, ob) accumulates a 4x4 block of
-// (c, o) for tap t over the chunk, then adds it to dW with atomics.
-constexpr int WG_X = 64;
-__global__ void __launch_bounds__(448) k_conv3_wgrad(const __nv_bfloat16* __restrict__ x,
-                                                     const __nv_bfloat16* __restrict__ dy,
-                                                     int nx, int ny, int nz, int ci, int co,
-                                                     float* dW, float* db)
-{
-    __shared__ float xs[9][WG_X + 2][16];
-    __shared__ float gs[WG_X][16];
-    const int nchunks = nx / WG_X;
-    const long long nblk = (long long)nchunks * ny * nz;
-    const int tid = threadIdx.x;
-    const int t = tid / 16, cb = (tid % 16) / 4, ob = tid % 4;  // tid < 432
-    float acc[4][4] = {};
-    float bacc = 0.f;
-    for (long long b = blockIdx.x; b < nblk; b += gridDim.x) {
-        const int cx = (int)(b % nchunks);
-        const int y = (int)((b / nchunks) % ny);
-        const int z = (int)(b / ((long long)nchunks * ny));
-        const int x0 = cx * WG_X;
-        __syncthreads();
-        for (int i = tid; i < 9 * (WG_X + 2) * 16; i += blockDim.x) {
-            const int c = i % 16, xi = (i / 16) % (WG_X + 2), r = i / (16 * (WG_X + 2));
-            const int yy = y + r % 3 - 1, zz = z + r / 3 - 1, xx = x0 + xi - 1;
-            float v = 0.f;
-            if (xx >= 0 && xx < nx && yy >= 0 && yy < ny && zz >= 0 && zz < nz)
-                v = __bfloat162float(x[rm_index(xx, yy, zz, nx, ny) * 16 + c]);
-            xs[r][xi][c] = v;
-        }
-        for (int i = tid; i < WG_X * 16; i += blockDim.x) {
-            const int c = i % 16, xi = i / 16;
-            gs[xi][c] = __bfloat162float(dy[rm_index(x0 + xi, y, z, nx, ny) * 16 + c]);
-        }
-        __syncthreads();
-        if (t < 27) {
-            const int dx = t % 3 - 1, r = (t / 3);  // r = (dz+1)*3 + (dy+1)
-            for (int xi = 0; xi < WG_X; ++xi) {
-                const float* xr = &xs[r][xi + 1 + dx][4 * cb];
-                const float* gr = &gs[xi][4 * ob];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(xr[i], gr[j], acc[i][j]);
-            }
-        } else if (tid < 432 + 16) {
-            const int o = tid - 432;
-            for (int xi = 0; xi < WG_X; ++xi) bacc += gs[xi][o];
-        }
-    }
-    if (t < 27) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = 4 * cb + i, o = 4 * ob + j;
-                if (c < ci && o < co && acc[i][j] != 0.f)
-                    atomicAdd(&dW[((size_t)t * ci + c) * co + o], acc[i][j]);
-            }
-    } else if (tid < 432 + 16 && db) {
-        const int o = tid - 432;
-        if (o < co && bacc != 0.f) atomicAdd(&db[o], bacc);
-    }
 }
 
 // Adam (bias-corrected moments) on a flat parameter vector.  The factors
@@ -270,17 +201,6 @@ cudaError_t launch_loss_grad(const float* z, const float* phi, const float* phit
 {
     k_loss_grad<<<grid_for(n, 256), 256, 0, s>>>(z, phi, phit, phiref, inv_h, gamma, count, n,
                                                  (__nv_bfloat16*)dz, loss);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci,
-                               int co, float* dW, float* db, cudaStream_t s)
-{
-    if (nx % WG_X) return cudaErrorInvalidValue;
-    const long long nblk = (long long)(nx / WG_X) * ny * nz;
-    long long g = nblk < 148 * 4 ? nblk : 148 * 4;
-    k_conv3_wgrad<<<(int)g, 448, 0, s>>>((const __nv_bfloat16*)x, (const __nv_bfloat16*)dy, nx, ny,
-                                         nz, ci, co, dW, db);
     return cudaGetLastError();
 }
 

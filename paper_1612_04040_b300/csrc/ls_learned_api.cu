@@ -347,7 +347,8 @@ int ls_learned_train_stored(ls_ctx* c, int iters, double lr, double dt, double h
         for (int l = lsk::NL - 1; l >= 0; --l) {
             const void* xin = (l == 0) ? L->X0 : L->A[l - 1];
             LCK(lsk::launch_conv3_wgrad(xin, L->G[l], L->nx, L->ny, L->nz, lsk::CI[l], lsk::CO[l],
-                                        L->grads + lsk::w_off(l), L->grads + lsk::b_off(l), s));
+                                        L->grads + lsk::w_off(l), L->grads + lsk::b_off(l),
+                                        c->d_status, s));
             if (l > 0)
                 LCK(lsk::launch_conv3(L->map_G[l], L->wpack_bwd[l], nullptr, L->A[l - 1],
                                       L->G[l - 1], nullptr, L->nx, L->ny, L->nz, 2, c->d_status, s));
@@ -668,11 +669,12 @@ int ls_conv3_bf16(const void* x, int nx, int ny, int nz, const float* W, int ci,
 }
 
 int ls_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci, int co,
-                   float* dW, float* db, void* stream)
+                   float* dW, float* db, unsigned* status, void* stream)
 {
-    if (!x || !dy || !dW || ci < 1 || ci > 16 || co < 1 || co > 16) return LS_EINVAL;
-    if (nx % 64 || ny < 1 || nz < 1) return LS_EINVAL;
-    LCK(lsk::launch_conv3_wgrad(x, dy, nx, ny, nz, ci, co, dW, db, (cudaStream_t)stream));
+    if (!x || !dy || !dW || !status || ci < 1 || ci > 16 || co < 1 || co > 16) return LS_EINVAL;
+    if (!lsk::conv3_wgrad_shape_ok(nx, ny, nz)) return LS_EINVAL;
+    if ((((uintptr_t)x | (uintptr_t)dy) & 15u) != 0) return LS_EINVAL;
+    LCK(lsk::launch_conv3_wgrad(x, dy, nx, ny, nz, ci, co, dW, db, status, (cudaStream_t)stream));
     return LS_OK;
 }
 

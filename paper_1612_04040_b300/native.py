@@ -101,7 +101,7 @@ SIGNATURES = {
     "ls_band_breaches": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
     "ls_learned_fallbacks": (_i, [_vp, _c.POINTER(_c.c_ulonglong)]),
     "ls_conv3_bf16": (_i, [_vp, _i, _i, _i, _vp, _i, _i, _vp, _i, _vp, _vp, _vp, _vp, _vp]),
-    "ls_conv3_wgrad": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "ls_conv3_wgrad": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _vp]),
     "ls_restrict4": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "ls_learned_features": (_i, [_vp, _vp, _vp, _d, _d, _ll, _vp, _vp]),
     "ls_learned_loss_grad": (_i, [_vp, _vp, _vp, _vp, _ll, _d, _d, _vp, _vp, _vp, _vp]),
@@ -262,17 +262,19 @@ def selftest_bounded_wait(polls, stream=None):
     return int(status.item())
 
 
-def conv3_wgrad(x, dy, ci, co, stream=None):
-    """ls_conv3_wgrad: returns (dW (27, ci, co), db (co,)) as float32 tensors."""
+def conv3_wgrad(x, dy, ci, co, stream=None, with_status=False):
+    """ls_conv3_wgrad: returns (dW (27, ci, co), db (co,)) as float32 tensors
+    (and the status word when with_status)."""
     lib = load()
     nz, ny, nx, _ = x.shape
     dW = torch.zeros((27, ci, co), dtype=torch.float32, device=x.device)
     db = torch.zeros((co,), dtype=torch.float32, device=x.device)
+    status = torch.zeros(1, dtype=torch.int32, device=x.device)
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    check(lib.ls_conv3_wgrad(_dptr(x), _dptr(dy), nx, ny, nz, ci, co, _dptr(dW), _dptr(db),
+    check(lib.ls_conv3_wgrad(_dptr(x), _dptr(dy), nx, ny, nz, ci, co, _dptr(dW), _dptr(db), _dptr(status),
                              ctypes.c_void_p(stream)), "ls_conv3_wgrad")
-    return dW, db
+    return (dW, db, status) if with_status else (dW, db)
 
 
 def restrict4(fine, stream=None):

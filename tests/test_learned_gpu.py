@@ -104,7 +104,9 @@ def test_weight_gradient(ci, co, shape):
     gy = np.zeros(shape + (16,), dtype=np.float32)
     gy[..., :co] = np.random.default_rng(8).normal(size=shape + (co,))
     gy = bf16_round(gy)
-    dW, db = ls.conv3_wgrad(to_dev_bf16(x), to_dev_bf16(gy), ci, co)
+    dW, db, st = ls.conv3_wgrad(to_dev_bf16(x), to_dev_bf16(gy), ci, co, with_status=True)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
     rW, rb = oracle.conv3_bwd_weight(x[..., :ci].astype(np.float64), gy[..., :co].astype(np.float64))
     close(dW.cpu().numpy(), rW, 1e-4)
     close(db.cpu().numpy(), rb, 1e-4)
