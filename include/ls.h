@@ -203,6 +203,51 @@ int ls_band_breaches(ls_ctx *ctx, unsigned long long *n);
  * its edge sooner).  Marks the band stale.  Errors: LS_EINVAL. */
 int ls_set_dilation(ls_ctx *ctx, int neighbours);
 
+/* ---------------------------------------------------------------------
+ * Slab split along z (section 2: the grid is decomposed by one axis, each
+ * part with a ghost layer from each neighbour; the tube's rows are shared
+ * out by the greedy rule of Eq. 14).  A context then holds one slab of
+ * whole tile rows plus, on each side that has a neighbour, one ghost tile
+ * row holding that neighbour's copy.  The host moves the data between
+ * slabs (its transport: a device copy, NCCL, ...); these calls only pack,
+ * unpack, rebuild and report.
+ * ------------------------------------------------------------------- */
+
+/* Mark the bottom (lo = 1) and / or top (hi = 1) tile row of a single-grid
+ * context as ghost rows: they are never active, their tube test is made on
+ * the values last imported into them, and only they accept
+ * ls_set_tile_rows.  Marks the band stale.  Errors: LS_EINVAL (batch
+ * context, flags not 0 / 1, fewer than lo + hi + 1 tile rows). */
+int ls_set_ghost_rows(ls_ctx *ctx, int lo, int hi);
+
+/* The band rebuild that ls_step would make before its next step (Step 1 of
+ * section 1.1): from the tube test fused into the last step when that step
+ * made one, else by a scan of every tile; ghost rows are tested on their
+ * current values.  Returns M = max |F| over the points of the new active
+ * tiles (0 if none) and the active-tile count (both nullable).  Resets the
+ * rebuild counter, so ls_step's own rebuild_every counts from here.
+ * Synchronises the stream.  Errors: LS_EINVAL, LS_ESTATE (phi, speed or
+ * halfwidth not set, full-domain mode). */
+int ls_band_refresh(ls_ctx *ctx, double *M, long long *n_active);
+
+/* Active tiles per tile row z (counts[tz], nrows = nz / 8) of the current
+ * band: the row weights of Eq. 14.  Synchronises.  Errors: LS_EINVAL,
+ * LS_ESTATE (no band). */
+int ls_band_row_counts(ls_ctx *ctx, long long *counts, int nrows);
+
+/* Copy tile rows [row0, row0 + nrows) of the current phi out to dst, or one
+ * ghost row (nrows = 1) in from src.  plane = -1: whole rows, 512 values
+ * per tile in the bricked order (tile by tile in row order, each x fastest,
+ * then y, then z); plane = 0..7: only that z-plane of every tile, 64 values
+ * per tile (x fastest, then y).  Values in the context precision.  Device
+ * buffers (16-byte aligned) are asynchronous on the context's stream; host
+ * buffers synchronise.  ls_set_tile_rows writes the buffer the next step
+ * reads and leaves the band as it is.  Errors: LS_EINVAL (range, plane, not
+ * a ghost row for ls_set_tile_rows), LS_ESTATE (phi not set). */
+int ls_get_tile_rows(ls_ctx *ctx, int row0, int nrows, int plane, void *dst, int dst_on_device);
+int ls_set_tile_rows(ls_ctx *ctx, int row0, int nrows, int plane, const void *src,
+                     int src_on_device);
+
 /* Full-domain mode, FP32 single grids, plain scheme: on, every step streams
  * tile columns along z (each tile's z halos are the neighbouring tiles of
  * its column, staged once); off (default): the active-list kernel over all

@@ -142,7 +142,7 @@ void free_all(ls_ctx* c)
                     c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params, c->nmask,
                     c->d_breaches, c->list_nact, c->nmask2, c->nflag, c->nl, c->nl_info,
                     c->d_ncount, c->d_rupdates, c->d_done, c->d_updates2, c->xface,
-                    c->d_updates_timed};
+                    c->d_updates_timed, c->d_rowcnt};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_nonfinite) cudaFreeHost(c->h_nonfinite);
@@ -263,9 +263,22 @@ int rebuild(ls_ctx* c, bool full_scan, cudaStream_t s)
     NvtxRange range("ls band rebuild");
     const bool incr = c->band_valid;
     void* cur = c->phi[c->cur];
-    if (full_scan || !c->core_fresh)
+    if (full_scan || !c->core_fresh) {
         KL(c, lsk::launch_classify_all(cur, c->core, c->dinst(), c->tinst(), c->in0(), c->ntiles,
                                        c->prec, s));
+    } else if (!c->batched && c->in0().ghost) {
+        // ghost rows are never active, so the fused tube test of the last
+        // step did not see them: test them on their imported values
+        const Inst& in = c->in0();
+        const long long tpl = (long long)in.tnx * in.tny;
+        const size_t row_bytes = (size_t)tpl * lsk::TILE_PTS * c->esize;
+        if (in.ghost & 1)
+            KL(c, lsk::launch_classify_all(cur, c->core, nullptr, nullptr, in, tpl, c->prec, s));
+        if (in.ghost & 2)
+            KL(c, lsk::launch_classify_all((char*)cur + (size_t)(in.tnz - 1) * row_bytes,
+                                           c->core + (in.tnz - 1) * tpl, nullptr, nullptr, in, tpl,
+                                           c->prec, s));
+    }
     KL(c, lsk::launch_dilate(c->core, c->act, c->block_counts, c->dinst(), c->tinst(), c->in0(),
                              c->ntiles, c->d_done, c->d_count, c->dilation, s));
     RET(finish_rebuild(c, incr, s));
@@ -942,6 +955,101 @@ int ls_band_rebuild(ls_ctx* c, double halfwidth, long long* n_active)
         *n_active = n;
     }
     return LS_OK;
+}
+
+// ---- slab split support -------------------------------------------------
+
+int ls_set_ghost_rows(ls_ctx* c, int lo, int hi)
+{
+    if (!c || c->batched || (lo != 0 && lo != 1) || (hi != 0 && hi != 1)) return LS_EINVAL;
+    Inst& in = c->in0();
+    if (in.tnz < 1 + lo + hi) return LS_EINVAL;
+    in.ghost = lo | (hi << 1);
+    state_changed(c);
+    return LS_OK;
+}
+
+int ls_band_refresh(ls_ctx* c, double* M, long long* n_active)
+{
+    if (!c || c->batched) return LS_EINVAL;
+    if (!all_phi_set(c) || speed_mode(c) == 0) return LS_ESTATE;
+    if (!c->have_halfwidth || c->full_domain) return LS_ESTATE;
+    clear_graphs(c);
+    // the rebuild ls_step would make now: from the tube test fused into the
+    // last step when that step made one, else from a scan of every tile
+    RET(rebuild(c, !c->band_valid, c->stream));
+    lsk::StepScalars sc;
+    int n = 0;
+    CK(cudaMemcpyAsync(&sc, c->d_sc, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&n, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (M) *M = sc.M;
+    if (n_active) *n_active = n;
+    return LS_OK;
+}
+
+int ls_band_row_counts(ls_ctx* c, long long* counts, int nrows)
+{
+    if (!c || c->batched || !counts) return LS_EINVAL;
+    const Inst& in = c->in0();
+    if (nrows != in.tnz) return LS_EINVAL;
+    if (!c->band_valid) return LS_ESTATE;
+    if (!c->d_rowcnt) CK(cudaMalloc(&c->d_rowcnt, sizeof(int) * (size_t)in.tnz));
+    CK(cudaMemsetAsync(c->d_rowcnt, 0, sizeof(int) * (size_t)in.tnz, c->stream));
+    KL(c, lsk::launch_row_counts(c->list, c->d_count, in.tnx * in.tny, c->d_rowcnt, in.tnz, c->stream));
+    std::vector<int> h((size_t)in.tnz);
+    CK(cudaMemcpyAsync(h.data(), c->d_rowcnt, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < in.tnz; ++i) counts[i] = h[(size_t)i];
+    return LS_OK;
+}
+
+// copies between the current phi buffer's tile rows [row0, row0 + nrows) and
+// a packed buffer: plane < 0: whole rows (tile after tile, 512 values each,
+// the bricked order); plane 0..7: that z-plane of every tile (64 values per
+// tile, tile after tile)
+static int tile_rows_copy(ls_ctx* c, int row0, int nrows, int plane, void* buf, int on_device,
+                          bool to_ctx)
+{
+    const Inst& in = c->in0();
+    const size_t tpl = (size_t)in.tnx * in.tny;
+    const size_t es = c->esize;
+    char* base = (char*)c->phi[c->cur] + (size_t)row0 * tpl * lsk::TILE_PTS * es;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                          : (to_ctx ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+    if (plane < 0) {
+        const size_t bytes = (size_t)nrows * tpl * lsk::TILE_PTS * es;
+        if (to_ctx) CK(cudaMemcpyAsync(base, buf, bytes, kind, c->stream));
+        else CK(cudaMemcpyAsync(buf, base, bytes, kind, c->stream));
+    } else {
+        const size_t w = 64 * es, pitch = lsk::TILE_PTS * es, rows = (size_t)nrows * tpl;
+        char* p = base + (size_t)plane * w;
+        if (to_ctx) CK(cudaMemcpy2DAsync(p, pitch, buf, w, w, rows, kind, c->stream));
+        else CK(cudaMemcpy2DAsync(buf, w, p, pitch, w, rows, kind, c->stream));
+    }
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return LS_OK;
+}
+
+int ls_get_tile_rows(ls_ctx* c, int row0, int nrows, int plane, void* dst, int on_device)
+{
+    if (!c || c->batched || !dst || plane < -1 || plane > 7) return LS_EINVAL;
+    const Inst& in = c->in0();
+    if (row0 < 0 || nrows < 1 || row0 + nrows > in.tnz) return LS_EINVAL;
+    if (!all_phi_set(c)) return LS_ESTATE;
+    return tile_rows_copy(c, row0, nrows, plane, dst, on_device, false);
+}
+
+int ls_set_tile_rows(ls_ctx* c, int row0, int nrows, int plane, const void* src, int on_device)
+{
+    if (!c || c->batched || !src || plane < -1 || plane > 7 || nrows != 1) return LS_EINVAL;
+    const Inst& in = c->in0();
+    const bool lo = (in.ghost & 1) && row0 == 0;
+    const bool hi = (in.ghost & 2) && row0 == in.tnz - 1;
+    if (!lo && !hi) return LS_EINVAL;  // only a ghost row takes a neighbour's values
+    if (!all_phi_set(c)) return LS_ESTATE;
+    clear_graphs(c);
+    return tile_rows_copy(c, row0, nrows, plane, const_cast<void*>(src), on_device, true);
 }
 
 int ls_step(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every, double* last_dt)

@@ -321,6 +321,8 @@ __global__ void __launch_bounds__(256) k_dilate(const uint8_t* __restrict__ core
             }
         }
         on = acc != 0;
+        // a ghost row (a neighbour slab's copy) is never active here
+        if (((in.ghost & 1) && tz == 0) || ((in.ghost & 2) && tz == in.tnz - 1)) on = 0;
         const int old = act[t] & 1;
         act[t] = (uint8_t)(on | (old << 1));
     }
@@ -802,6 +804,23 @@ cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_in
     else
         k_classify_all<double><<<warp_grid(ntiles), 256, 0, s>>>((const double*)phi, core, d_inst,
                                                                  tile_inst, single, ntiles);
+    return cudaGetLastError();
+}
+
+__global__ void k_row_counts(const int* __restrict__ list, const int* __restrict__ count,
+                             int tiles_per_row, int* rows, int capacity)
+{
+    const int n = *count;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int r = list[k] / tiles_per_row;
+        if (r < capacity) atomicAdd(&rows[r], 1);
+    }
+}
+
+cudaError_t launch_row_counts(const int* list, const int* count, int tiles_per_row, int* rows,
+                              int capacity, cudaStream_t s)
+{
+    k_row_counts<<<148, 256, 0, s>>>(list, count, tiles_per_row, rows, capacity);
     return cudaGetLastError();
 }
 

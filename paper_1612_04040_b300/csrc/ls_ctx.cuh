@@ -91,6 +91,7 @@ struct ls_ctx {
     unsigned* d_done = nullptr;   // last-block counters: dilate, scatter, N-flag count
     int* block_counts = nullptr;
     int nblocks = 0;
+    int* d_rowcnt = nullptr;      // per tile row active counts (slab split, lazy)
     lsk::StepScalars* d_sc = nullptr;
     unsigned long long* d_Mbits = nullptr;
     unsigned long long* d_updates = nullptr;

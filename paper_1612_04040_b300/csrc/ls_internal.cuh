@@ -33,7 +33,8 @@ struct Inst {
     int speed_mode;        // 0: unset, 1: constant, 2: field
     int pow2h;             // h is a power of two (1/h exact)
     int bc;                // 0 extrapolate, 1 neumann
-    int pad;
+    int ghost;             // slab split: bit 0 / bit 1 = the bottom / top tile row
+                           // holds a neighbour's copy (never active)
 };
 
 // Device status word bits (sticky).
@@ -90,6 +91,9 @@ cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_in
 // 0 = new flag, bit 1 = previous) + block counts, turned into exclusive
 // offsets and the active count *count by the last block to finish (done: a
 // zeroed device counter, reset by that block)
+// per tile row (tz) count of the active-list entries: rows[tz] += 1
+cudaError_t launch_row_counts(const int* list, const int* count, int tiles_per_row, int* rows,
+                              int capacity, cudaStream_t s);
 cudaError_t launch_dilate(const uint8_t* core, uint8_t* act, int* block_counts,
                           const Inst* d_inst, const uint16_t* tile_inst, const Inst& single,
                           long long ntiles, unsigned* done, int* count, int conn,

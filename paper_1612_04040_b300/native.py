@@ -57,6 +57,11 @@ SIGNATURES = {
     "ls_set_full_domain": (_i, [_vp, _i]),
     "ls_get_phi": (_i, [_vp, _vp, _i]),
     "ls_get_speed": (_i, [_vp, _vp, _i]),
+    "ls_set_ghost_rows": (_i, [_vp, _i, _i]),
+    "ls_band_refresh": (_i, [_vp, _vp, _vp]),
+    "ls_band_row_counts": (_i, [_vp, _vp, _i]),
+    "ls_get_tile_rows": (_i, [_vp, _i, _i, _i, _vp, _i]),
+    "ls_set_tile_rows": (_i, [_vp, _i, _i, _i, _vp, _i]),
     "ls_stage_inputs": (_i, [_vp, _vp, _vp]),
     "ls_load_staged": (_i, [_vp]),
     "ls_get_phi_async": (_i, [_vp, _vp]),
@@ -455,6 +460,39 @@ class LevelSet:
         p, dev = array_ptr(out, self.dtype, self.count)
         check(self.lib.ls_get_speed(self.ctx, p, dev), "ls_get_speed")
         return out
+
+    # -- slab split (section 2) ---------------------------------------------
+    def set_ghost_rows(self, lo, hi):
+        check(self.lib.ls_set_ghost_rows(self.ctx, int(lo), int(hi)), "ls_set_ghost_rows")
+
+    def band_refresh(self):
+        """The rebuild the next step would make; returns (M, active tiles)."""
+        M = ctypes.c_double(0.0)
+        n = ctypes.c_longlong(0)
+        check(self.lib.ls_band_refresh(self.ctx, ctypes.byref(M), ctypes.byref(n)), "ls_band_refresh")
+        return M.value, n.value
+
+    def band_row_counts(self):
+        nz = self.shape[0] // 8
+        out = np.zeros(nz, dtype=np.int64)
+        check(self.lib.ls_band_row_counts(self.ctx, out.ctypes.data_as(ctypes.c_void_p), nz),
+              "ls_band_row_counts")
+        return out
+
+    def _rows_ptr(self, a, nrows, plane):
+        n = nrows * (self.shape[1] // 8) * (self.shape[2] // 8) * (512 if plane < 0 else 64)
+        return array_ptr(a, self.dtype, n)
+
+    def get_tile_rows(self, row0, nrows, plane, out):
+        p, dev = self._rows_ptr(out, nrows, plane)
+        check(self.lib.ls_get_tile_rows(self.ctx, int(row0), int(nrows), int(plane), p, dev),
+              "ls_get_tile_rows")
+        return out
+
+    def set_tile_rows(self, row0, nrows, plane, src):
+        p, dev = self._rows_ptr(src, nrows, plane)
+        check(self.lib.ls_set_tile_rows(self.ctx, int(row0), int(nrows), int(plane), p, dev),
+              "ls_set_tile_rows")
 
     # stream-ordered host input/output (ls_stage_inputs ... ls_wait_host);
     # the arrays must be host (CPU) arrays, page-locked for the copies to

@@ -1,0 +1,390 @@
+"""Slab split of the narrow-band step along z (section 2 of the paper).
+
+The paper decomposes the grid by one axis, each core holding its rows plus
+a ghost row from each neighbour, and shares the tube out row by row with a
+greedy rule (Eq. 14): a core takes the next row while that brings its count
+S of active points closer to M/n, i.e. while S < M/n - c/2 for a next row of
+c points.  Here a "row" is a tile row (the 8 z-planes of one layer of 8^3
+tiles), its weight the active tiles in it, and a part is a slab of whole
+tile rows held by one engine (one GPU, one process, or one of several slabs
+on the same GPU).
+
+Per step the parts exchange one z-plane across every boundary (the plane
+next to the neighbour's first or last owned row) into the neighbour's ghost
+row; before every band rebuild they exchange whole rows, so that each part
+can make the tube test of its ghost rows and dilate the band across the
+boundary, and all-reduce M = max |F| over the active points for the common
+dt.  After a rebuild the rows are shared out again by Eq. 14 and rows that
+change owner move between parts.
+
+This module holds the host logic only: the partition, the exchange plan and
+the schedule.  The arithmetic runs in the engines (the library's kernels
+for ``GpuSlab``); the data moves through a ``comm`` object: ``LocalComm``
+(every part in this process) or ``DistComm`` (one part per rank of a
+torch.distributed group: NCCL between GPUs, gloo on CPU).
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import native as ls
+
+TILE = 8
+
+
+# --------------------------------------------------------------------------
+# Eq. 14
+# --------------------------------------------------------------------------
+
+def partition_rows(counts, nparts):
+    """Bounds [b_0 = 0, b_1, ..., b_n = len(counts)] of n consecutive row
+    ranges.  Rows are taken in order; the current part takes the next row of
+    c active tiles while S < M/n - c/2 (Eq. 14, evaluated exactly as
+    n (2 S + c) < 2 M), where S is what it holds and M the total.  Readings
+    for the cases the rule does not settle: every part takes at least one
+    row (a part has a slab to hold), a part stops when the rows left are
+    just enough for one each of the parts after it, and the last part takes
+    what remains.  For a row with c > 0 the rule is the paper's
+    |S - M/n| > |S + c - M/n|; for an empty row (c = 0) both sides are
+    equal and the paper's consequence S < M/n is what decides."""
+    counts = [int(c) for c in counts]
+    nrows = len(counts)
+    if nparts < 1 or nrows < nparts:
+        raise ValueError("need 1 <= parts <= rows (%d parts, %d rows)" % (nparts, nrows))
+    if any(c < 0 for c in counts):
+        raise ValueError("row counts must be non-negative")
+    M = sum(counts)
+    bounds = [0]
+    S = 0
+    for r, c in enumerate(counts):
+        part = len(bounds) - 1
+        held = r - bounds[-1]
+        if part < nparts - 1 and held > 0:
+            rows_left = nrows - r
+            must_close = rows_left == nparts - 1 - part
+            if must_close or not (nparts * (2 * S + c) < 2 * M):
+                bounds.append(r)
+                S = 0
+        S += c
+    bounds.append(nrows)
+    return bounds
+
+
+def even_rows(nrows, nparts):
+    """The global decomposition (equal numbers of rows), used before any
+    band exists."""
+    if nparts < 1 or nrows < nparts:
+        raise ValueError("need 1 <= parts <= rows")
+    return [(nrows * p) // nparts for p in range(nparts + 1)]
+
+
+# --------------------------------------------------------------------------
+# transports
+# --------------------------------------------------------------------------
+
+class LocalComm:
+    """Every part lives in this process; moving data is a copy."""
+
+    def __init__(self, nparts):
+        self.nparts = int(nparts)
+        self.parts = list(range(self.nparts))
+
+    def max(self, values):
+        return max(float(v) for v in values.values())
+
+    def sum_arrays(self, arrays):
+        return np.sum([np.asarray(a, dtype=np.int64) for a in arrays.values()], axis=0)
+
+    def transfer(self, moves):
+        """moves: (src_part, dst_part, src_buffer, dst_buffer); src_buffer
+        is read, dst_buffer written."""
+        for _, _, src, dst in moves:
+            dst.copy_(src)
+
+
+class DistComm:
+    """Part p lives on rank p of a torch.distributed group (NCCL with CUDA
+    buffers, gloo with CPU buffers)."""
+
+    def __init__(self, dist, device):
+        self.dist = dist
+        self.device = torch.device(device)
+        self.nparts = dist.get_world_size()
+        self.parts = [dist.get_rank()]
+
+    def max(self, values):
+        t = torch.tensor([max(float(v) for v in values.values())], dtype=torch.float64,
+                         device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_arrays(self, arrays):
+        a = np.sum([np.asarray(v, dtype=np.int64) for v in arrays.values()], axis=0)
+        t = torch.from_numpy(a).to(self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return t.cpu().numpy()
+
+    def transfer(self, moves):
+        me = self.parts[0]
+        ops = []
+        for src_part, dst_part, src, dst in moves:
+            if src_part == me and dst_part == me:
+                dst.copy_(src)
+            elif src_part == me:
+                ops.append(self.dist.P2POp(self.dist.isend, src, dst_part))
+            elif dst_part == me:
+                ops.append(self.dist.P2POp(self.dist.irecv, dst, src_part))
+        if ops:
+            for r in self.dist.batch_isend_irecv(ops):
+                r.wait()
+
+
+# --------------------------------------------------------------------------
+# the library engine of one slab
+# --------------------------------------------------------------------------
+
+class GpuSlab:
+    """One slab of tile rows (plus ghost rows) in a library context on the
+    current CUDA device, fed from row-major device tensors."""
+
+    def __init__(self, nx, ny, rows, h, lo, hi, precision=ls.LS_FP32, stream=None):
+        self.nx, self.ny, self.rows, self.lo, self.hi = nx, ny, rows, int(lo), int(hi)
+        self.h = float(h)
+        self.dtype = torch.float32 if precision == ls.LS_FP32 else torch.float64
+        self.ctx = ls.LevelSet(nx, ny, TILE * rows, h, precision, stream)
+        self.tiles_per_row = (nx // TILE) * (ny // TILE)
+
+    def close(self):
+        self.ctx.close()
+
+    def setup(self, phi, F, halfwidth):
+        """phi, F: row-major (8 rows, ny, nx) tensors of the whole slab,
+        ghost rows included (their F is not used)."""
+        self.ctx.set_phi(phi.contiguous())
+        self.ctx.set_speed(F.contiguous())
+        self.ctx.set_ghost_rows(self.lo, self.hi)
+        self.ctx.band_rebuild(halfwidth, want_count=False)
+
+    def refresh(self):
+        return self.ctx.band_refresh()
+
+    def row_counts(self):
+        return self.ctx.band_row_counts()
+
+    def step(self, dt, rebuild_every):
+        self.ctx.step(1, dt, ls.LS_DT_FIXED, rebuild_every)
+
+    def buffer(self, plane):
+        n = self.tiles_per_row * (512 if plane < 0 else 64)
+        return torch.empty(n, dtype=self.dtype, device="cuda")
+
+    def export_row(self, row, plane, out):
+        self.ctx.get_tile_rows(row, 1, plane, out)
+
+    def import_row(self, row, plane, src):
+        self.ctx.set_tile_rows(row, 1, plane, src)
+
+    def phi(self):
+        out = torch.empty((TILE * self.rows, self.ny, self.nx), dtype=self.dtype, device="cuda")
+        self.ctx.get_phi(out)
+        return out
+
+    def speed(self):
+        out = torch.empty((TILE * self.rows, self.ny, self.nx), dtype=self.dtype, device="cuda")
+        self.ctx.get_speed(out)
+        return out
+
+    def zeros(self, nplanes):
+        return torch.zeros((nplanes, self.ny, self.nx), dtype=self.dtype, device="cuda")
+
+
+# --------------------------------------------------------------------------
+# the schedule
+# --------------------------------------------------------------------------
+
+class SlabRun:
+    """A narrow-band run split into z-slabs.
+
+    make_engine(nx, ny, rows, h, lo, hi) builds the engine of one slab (rows =
+    tile rows including the ghost rows lo / hi); source(z0, z1) returns the
+    row-major (z1 - z0, ny, nx) planes [z0, z1) of phi and of F (both as
+    engine tensors) for the initial state.  The parts start from the even
+    row split, rebuild, and are then shared out by Eq. 14; with
+    ``rebalance`` they are shared out again after every rebuild."""
+
+    def __init__(self, comm, make_engine, shape, h, halfwidth, source, rebalance=True):
+        self.comm = comm
+        self.make_engine = make_engine
+        self.nz, self.ny, self.nx = (int(v) for v in shape)
+        if self.nz % TILE or self.ny % TILE or self.nx % TILE:
+            raise ValueError("grid edges must be multiples of 8")
+        self.nrows = self.nz // TILE
+        self.h = float(h)
+        self.halfwidth = float(halfwidth)
+        self.rebalance = bool(rebalance)
+        self.engines = {}
+        self.bounds = even_rows(self.nrows, comm.nparts)
+        self.since_rebuild = 0
+        self.updates = 0
+        self.migrations = 0
+        self.dt = None
+        self._build({p: self._initial_rows(source, p) for p in comm.parts})
+        self._rebuild(first=True)
+
+    # -- layout -------------------------------------------------------------
+    def _span(self, p, bounds=None):
+        """(owned rows r0..r1, ghost flags lo / hi, first tile row held)"""
+        b = self.bounds if bounds is None else bounds
+        r0, r1 = b[p], b[p + 1]
+        lo = 1 if p > 0 else 0
+        hi = 1 if p < self.comm.nparts - 1 else 0
+        return r0, r1, lo, hi, r0 - lo
+
+    def _initial_rows(self, source, p):
+        r0, r1, lo, hi, first = self._span(p)
+        return source(TILE * first, TILE * (r1 + hi))
+
+    def _build(self, fields):
+        for e in self.engines.values():
+            e.close()
+        self.engines = {}
+        for p, (phi, F) in fields.items():
+            r0, r1, lo, hi, _ = self._span(p)
+            e = self.make_engine(self.nx, self.ny, r1 - r0 + lo + hi, self.h, lo, hi)
+            e.setup(phi, F, self.halfwidth)
+            self.engines[p] = e
+
+    # -- exchanges ----------------------------------------------------------
+    def _exchange(self, plane_up, plane_down):
+        """Across every boundary p | p+1: p's last owned row -> p+1's bottom
+        ghost row (plane_up of it), p+1's first owned row -> p's top ghost
+        row (plane_down); -1 means whole rows."""
+        moves, keep = [], []
+        for p in range(self.comm.nparts - 1):
+            q = p + 1
+            for src, dst, plane in ((p, q, plane_up), (q, p, plane_down)):
+                s_in = src in self.engines
+                d_in = dst in self.engines
+                if not (s_in or d_in):
+                    continue
+                sbuf = dbuf = None
+                if s_in:
+                    e = self.engines[src]
+                    r0, r1, lo, hi, _ = self._span(src)
+                    row = lo + (r1 - r0 - 1) if dst > src else lo
+                    sbuf = e.buffer(plane)
+                    e.export_row(row, plane, sbuf)
+                if d_in:
+                    e = self.engines[dst]
+                    r0, r1, lo, hi, _ = self._span(dst)
+                    row = 0 if src < dst else lo + (r1 - r0)
+                    dbuf = e.buffer(plane)
+                    keep.append((e, row, plane, dbuf))
+                moves.append((src, dst, sbuf, dbuf))
+        self.comm.transfer(moves)
+        for e, row, plane, dbuf in keep:
+            e.import_row(row, plane, dbuf)
+
+    # -- rebuild, balance and dt ----------------------------------------------
+    def _rebuild(self, first=False):
+        self._exchange(-1, -1)
+        Ms = {p: e.refresh()[0] for p, e in self.engines.items()}
+        if self.rebalance:
+            counts = self.row_counts()
+            new = partition_rows(counts, self.comm.nparts)
+            if new != self.bounds:
+                self._migrate(new)
+                self._exchange(-1, -1)
+                Ms = {p: e.refresh()[0] for p, e in self.engines.items()}
+        M = self.comm.max(Ms)
+        self.M = M
+        self.since_rebuild = 0
+
+    def row_counts(self):
+        """Active tiles per tile row of the whole grid (gathered)."""
+        arrays = {}
+        for p, e in self.engines.items():
+            r0, r1, lo, hi, _ = self._span(p)
+            full = np.zeros(self.nrows, dtype=np.int64)
+            full[r0:r1] = e.row_counts()[lo:lo + (r1 - r0)]
+            arrays[p] = full
+        return self.comm.sum_arrays(arrays)
+
+    def _migrate(self, new):
+        """Move owned rows to their new parts (Eq. 14 after a rebuild):
+        every overlap of an old and a new range goes from its old to its new
+        owner; ghost rows are filled by the next exchange."""
+        old = self.bounds
+        held = {}
+        for p, e in self.engines.items():
+            r0, r1, lo, hi, _ = self._span(p)
+            held[p] = (e.phi()[TILE * lo:TILE * (lo + r1 - r0)], e.speed()[TILE * lo:TILE * (lo + r1 - r0)])
+        # receive buffers of the new slabs (owned planes; ghosts zero for now)
+        fresh = {}
+        for q in self.comm.parts:
+            r0, r1, lo, hi, _ = self._span(q, new)
+            proto = next(iter(self.engines.values()))
+            fresh[q] = (proto.zeros(TILE * (r1 - r0 + lo + hi)), proto.zeros(TILE * (r1 - r0 + lo + hi)))
+        moves = []
+        for p in range(self.comm.nparts):
+            for q in range(self.comm.nparts):
+                a = max(old[p], new[q])
+                b = min(old[p + 1], new[q + 1])
+                if a >= b:
+                    continue
+                if p not in held and q not in fresh:
+                    continue
+                for k in (0, 1):
+                    src = dst = None
+                    if p in held:
+                        src = held[p][k][TILE * (a - old[p]):TILE * (b - old[p])].contiguous()
+                    if q in fresh:
+                        lo_q = 1 if q > 0 else 0
+                        dst = fresh[q][k][TILE * (lo_q + a - new[q]):TILE * (lo_q + b - new[q])]
+                    moves.append((p, q, src, dst))
+        # views of the receive buffers may be non-contiguous for P2P: receive
+        # into contiguous staging and copy back
+        staged = []
+        for i, (p, q, src, dst) in enumerate(moves):
+            if dst is not None and not dst.is_contiguous():
+                tmp = torch.empty_like(dst, memory_format=torch.contiguous_format)
+                staged.append((tmp, dst))
+                moves[i] = (p, q, src, tmp)
+        self.comm.transfer(moves)
+        for tmp, dst in staged:
+            dst.copy_(tmp)
+        self.bounds = list(new)
+        self.migrations += 1
+        self._build(fresh)
+
+    # -- stepping -------------------------------------------------------------
+    def step(self, nsteps, cfl, rebuild_every):
+        """nsteps steps at dt = cfl h / M (cfl h when M = 0), M taken over
+        the whole band at each rebuild, a rebuild every rebuild_every steps
+        (the same schedule and dt as one unsplit context)."""
+        for _ in range(nsteps):
+            if self.since_rebuild >= rebuild_every:
+                self._rebuild()
+            ch = cfl * self.h
+            self.dt = ch / self.M if self.M > 0.0 else ch
+            self._exchange(TILE - 1, 0)
+            for e in self.engines.values():
+                e.step(self.dt, rebuild_every)
+            self.since_rebuild += 1
+
+    def gather_phi(self):
+        """Owned planes of the parts in this process: {part: (z0, planes)}."""
+        out = {}
+        for p, e in self.engines.items():
+            r0, r1, lo, hi, _ = self._span(p)
+            out[p] = (TILE * r0, e.phi()[TILE * lo:TILE * (lo + r1 - r0)])
+        return out
+
+    def active_rows(self):
+        return self.row_counts()
+
+    def close(self):
+        for e in self.engines.values():
+            e.close()
+        self.engines = {}

@@ -1,0 +1,106 @@
+"""The slab split on one GPU: several slab contexts of the library on the
+same device, exchanging their boundary planes and ghost rows through the
+same code path that moves them between GPUs (here device copies), the
+common dt from the all-reduced M, and Eq. 14 re-partitions that migrate
+rows between slabs.  Bars: bitwise equal to one unsplit context in FP32 and
+FP64 (same per-point arithmetic, same band, same dt), and FP64 bitwise equal
+to the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1612_04040_b300 import inputs
+from paper_1612_04040_b300 import native as ls
+from paper_1612_04040_b300 import slab
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (96, 48, 48)
+H = 1.0 / 48
+HW = 4.0
+NSTEPS = 30
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(cuda_ok):
+    ls.load()
+
+
+def fields(dtype):
+    Z = SHAPE[0] * H
+    phi = inputs.sphere_union_sdf(SHAPE, H, [(0.5, 0.5, 0.25 * Z), (0.35, 0.6, 0.8 * Z), (0.7, 0.3, 0.7 * Z)],
+                                  [0.18, 0.1, 0.08]).numpy().astype(dtype)
+    z = (np.arange(SHAPE[0]) + 0.5) * H
+    F = np.broadcast_to((1.0 - 1.6 * z / Z)[:, None, None], SHAPE).astype(dtype)
+    return phi, np.ascontiguousarray(F)
+
+
+def unsplit(phi, F, prec):
+    nz, ny, nx = SHAPE
+    g = ls.LevelSet(nx, ny, nz, H, prec)
+    g.set_phi(phi)
+    g.set_speed(F)
+    g.band_rebuild(HW)
+    dt = g.step(NSTEPS, 0.5, ls.LS_DT_CFL, 5, want_dt=True)
+    out = g.get_phi()
+    g.close()
+    return out, dt
+
+
+def split(phi, F, prec, nparts):
+    dphi, dF = torch.from_numpy(phi).cuda(), torch.from_numpy(F).cuda()
+
+    def make(nx, ny, rows, h, lo, hi):
+        return slab.GpuSlab(nx, ny, rows, h, lo, hi, prec)
+
+    run = slab.SlabRun(slab.LocalComm(nparts), make, SHAPE, H, HW, lambda z0, z1: (dphi[z0:z1], dF[z0:z1]))
+    first = run.migrations
+    run.step(NSTEPS, 0.5, 5)
+    got = np.full_like(phi, np.nan)
+    for p, (z0, planes) in run.gather_phi().items():
+        got[z0:z0 + planes.shape[0]] = planes.cpu().numpy()
+    out = (got, run.dt, run.migrations - first, list(run.bounds))
+    run.close()
+    return out
+
+
+@pytest.mark.parametrize("nparts", [2, 3, 4])
+@pytest.mark.parametrize("prec", [ls.LS_FP32, ls.LS_FP64])
+def test_split_equals_unsplit_bitwise(prec, nparts):
+    dt_np = np.float32 if prec == ls.LS_FP32 else np.float64
+    phi, F = fields(dt_np)
+    ref, ref_dt = unsplit(phi, F, prec)
+    got, dt, moved, bounds = split(phi, F, prec, nparts)
+    assert dt == ref_dt
+    assert np.array_equal(got.view(np.int32 if prec == ls.LS_FP32 else np.int64),
+                          ref.view(np.int32 if prec == ls.LS_FP32 else np.int64))
+    if nparts >= 3:
+        assert moved >= 1, bounds
+
+
+def test_split_fp64_equals_oracle_bitwise():
+    phi, F = fields(np.float64)
+    got, dt, _, _ = split(phi, F, ls.LS_FP64, 3)
+    o = oracle.Oracle(SHAPE, H)
+    o.set_phi(phi)
+    o.set_speed(F)
+    o.band_rebuild(HW)
+    o.step(NSTEPS, 0.5, oracle.DT_CFL, 5)
+    assert dt == o.last_dt
+    assert np.array_equal(got, o.phi)
+
+
+def test_ghost_row_calls_refuse_owned_rows():
+    g = ls.LevelSet(16, 16, 32, 1.0 / 16, ls.LS_FP32)
+    g.set_phi(np.zeros((32, 16, 16), dtype=np.float32) + 1.0)
+    buf = torch.zeros(4 * 64, device="cuda")
+    with pytest.raises(ls.LSError):
+        g.set_tile_rows(0, 1, 0, buf)                  # no ghost rows declared
+    g.set_ghost_rows(1, 0)
+    g.set_tile_rows(0, 1, 0, buf)                      # the bottom ghost row takes it
+    with pytest.raises(ls.LSError):
+        g.set_tile_rows(3, 1, 0, buf)                  # the top row is owned
+    with pytest.raises(ls.LSError):
+        g.set_ghost_rows(2, 0)
+    g.close()
