@@ -87,6 +87,15 @@ def parse():
                    help="local workload: reinitialisation iterations per step (-1: ceil(halfwidth/dtau))")
     p.add_argument("--pairs", type=int, default=2000)
     p.add_argument("--train-iters", type=int, default=2000)
+    p.add_argument("--parallelism", choices=["replicas", "slab"], default="replicas",
+                   help="sphere-union with --gpus N: independent replicas (default) or one grid split "
+                        "into z-slabs, one per GPU, balanced by Eq. 14 (NCCL exchanges)")
+    p.add_argument("--slabs", type=int, default=1,
+                   help="--parallelism slab on one GPU: number of slabs in this process (device "
+                        "copies instead of NCCL)")
+    p.add_argument("--rebalance-gain", type=float, default=0.05,
+                   help="--parallelism slab: move rows to the Eq. 14 partition after a rebuild only "
+                        "when that lowers the largest slab's active tiles by more than this fraction")
     p.add_argument("--step-config", default=None, metavar="STAGES,GRID_PCT,PPT",
                    help="fix the stencil launch configuration instead of autotuning it "
                         "(so that a profiler run times the same kernel as the plain run)")
@@ -668,8 +677,86 @@ def run_sphere64(args):
           flush=True)
 
 
+def run_slab(args):
+    """The standard 512^3 run split into z-slabs (section 2 of the paper):
+    one slab per rank (NCCL exchanges) or --slabs slabs on one GPU (device
+    copies), rows shared out by Eq. 14 after every band rebuild.  One bench
+    step = one whole 500-step run from phi^0 (slab contexts set up before the
+    timed region, the initial rebuilds and partition inside it); value = all
+    slabs' updates (active tiles x 512 per step, counted at each rebuild) /
+    max time over ranks.  The total work is fixed as N grows
+    (one grid): scaling "strong"."""
+    import torch
+    from paper_1612_04040_b300 import inputs
+    from paper_1612_04040_b300 import native as ls
+    from paper_1612_04040_b300 import slab
+    world, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    w = inputs.SphereUnion(n=args.grid)
+    # phi^0 and F by the library's Step 0 kernels on every rank (the same
+    # seeded parameters), kept as device tensors to slice the slabs from
+    g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32, stream=stream.cuda_stream)
+    g.init_speed(ls.LS_SPEED_SINUSOID)
+    g.init_phi(ls.LS_SHAPE_SPHERES, inputs.spheres_params(w.centres, w.radii))
+    phi0 = torch.empty((w.n,) * 3, dtype=torch.float32, device=dev)
+    F0 = torch.empty_like(phi0)
+    g.get_phi(phi0)
+    g.get_speed(F0)
+    g.close()
+    comm = slab.DistComm(pg, dev) if world > 1 else slab.LocalComm(max(args.slabs, 1))
+
+    def make(nx, ny, rows, h, lo, hi):
+        return slab.GpuSlab(nx, ny, rows, h, lo, hi, ls.LS_FP32, stream.cuda_stream)
+
+    def new_run():
+        return slab.SlabRun(comm, make, (w.n,) * 3, w.h, w.halfwidth,
+                            lambda z0, z1: (phi0[z0:z1], F0[z0:z1]), rebalance=True,
+                            rebalance_gain=args.rebalance_gain)
+
+    for _ in range(max(args.warmup, 0)):
+        r = new_run()
+        r.step(w.steps, w.cfl, w.rebuild_every)
+        r.close()
+    torch.cuda.synchronize()
+    total_ms, updates, migrations, bounds = 0.0, 0, 0, None
+    for _ in range(args.steps):
+        r = new_run()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.step(w.steps, w.cfl, w.rebuild_every)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        total_ms += e0.elapsed_time(e1)
+        updates += r.updates
+        migrations += r.migrations
+        bounds = list(r.bounds)
+        r.close()
+    t_s, all_updates = aggregate(pg, total_ms / 1e3, float(updates), device=dev)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": all_updates / t_s / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_s / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "grid": args.grid, "parallelism": "slab",
+                       "slabs": comm.nparts, "transport": "nccl" if world > 1 else "device copies",
+                       "final_bounds_tile_rows": bounds, "migrations_per_run": migrations / max(args.steps, 1),
+                       "l2": "inputs larger than L2 (phi + F 1.5 GB)"},
+            "updates_per_step": all_updates / max(args.steps, 1),
+        }), flush=True)
+
+
 def main():
     args = parse()
+    if args.parallelism == "slab" and args.impl == "mine":
+        run_slab(args)
+        return
     if args.workload == "perturbed":
         run_perturbed(args)
         return

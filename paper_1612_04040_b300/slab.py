@@ -172,8 +172,8 @@ class GpuSlab:
     def row_counts(self):
         return self.ctx.band_row_counts()
 
-    def step(self, dt, rebuild_every):
-        self.ctx.step(1, dt, ls.LS_DT_FIXED, rebuild_every)
+    def step(self, dt, rebuild_every, n=1):
+        self.ctx.step(n, dt, ls.LS_DT_FIXED, rebuild_every)
 
     def buffer(self, plane):
         n = self.tiles_per_row * (512 if plane < 0 else 64)
@@ -211,9 +211,14 @@ class SlabRun:
     row-major (z1 - z0, ny, nx) planes [z0, z1) of phi and of F (both as
     engine tensors) for the initial state.  The parts start from the even
     row split, rebuild, and are then shared out by Eq. 14; with
-    ``rebalance`` they are shared out again after every rebuild."""
+    ``rebalance`` they are shared out again after every rebuild, when the
+    Eq. 14 partition lowers the largest part's active tiles by more than
+    the fraction ``rebalance_gain`` (0: whenever it lowers it; moving rows
+    costs the moved parts new contexts, so a run on GPUs takes a few per
+    cent)."""
 
-    def __init__(self, comm, make_engine, shape, h, halfwidth, source, rebalance=True):
+    def __init__(self, comm, make_engine, shape, h, halfwidth, source, rebalance=True,
+                 rebalance_gain=0.0):
         self.comm = comm
         self.make_engine = make_engine
         self.nz, self.ny, self.nx = (int(v) for v in shape)
@@ -223,7 +228,9 @@ class SlabRun:
         self.h = float(h)
         self.halfwidth = float(halfwidth)
         self.rebalance = bool(rebalance)
+        self.rebalance_gain = float(rebalance_gain)
         self.engines = {}
+        self.n_active = 0
         self.bounds = even_rows(self.nrows, comm.nparts)
         self.since_rebuild = 0
         self.updates = 0
@@ -279,24 +286,36 @@ class SlabRun:
                     e = self.engines[dst]
                     r0, r1, lo, hi, _ = self._span(dst)
                     row = 0 if src < dst else lo + (r1 - r0)
-                    dbuf = e.buffer(plane)
+                    # both parts here: the neighbour reads the exported buffer itself
+                    dbuf = sbuf if s_in else e.buffer(plane)
                     keep.append((e, row, plane, dbuf))
-                moves.append((src, dst, sbuf, dbuf))
+                if not (s_in and d_in):
+                    moves.append((src, dst, sbuf, dbuf))
         self.comm.transfer(moves)
         for e, row, plane, dbuf in keep:
             e.import_row(row, plane, dbuf)
 
     # -- rebuild, balance and dt ----------------------------------------------
+    def _refresh_all(self):
+        res = {p: e.refresh() for p, e in self.engines.items()}
+        self.n_active = sum(n for _, n in res.values())   # active tiles of this process's parts
+        return {p: M for p, (M, _) in res.items()}
+
+    @staticmethod
+    def _largest(counts, bounds):
+        return max(int(np.sum(counts[bounds[i]:bounds[i + 1]])) for i in range(len(bounds) - 1))
+
     def _rebuild(self, first=False):
         self._exchange(-1, -1)
-        Ms = {p: e.refresh()[0] for p, e in self.engines.items()}
-        if self.rebalance:
+        Ms = self._refresh_all()
+        if self.rebalance and self.comm.nparts > 1:
             counts = self.row_counts()
             new = partition_rows(counts, self.comm.nparts)
-            if new != self.bounds:
+            now, then = self._largest(counts, self.bounds), self._largest(counts, new)
+            if new != self.bounds and (first or then < (1.0 - self.rebalance_gain) * now):
                 self._migrate(new)
                 self._exchange(-1, -1)
-                Ms = {p: e.refresh()[0] for p, e in self.engines.items()}
+                Ms = self._refresh_all()
         M = self.comm.max(Ms)
         self.M = M
         self.since_rebuild = 0
@@ -363,15 +382,25 @@ class SlabRun:
         """nsteps steps at dt = cfl h / M (cfl h when M = 0), M taken over
         the whole band at each rebuild, a rebuild every rebuild_every steps
         (the same schedule and dt as one unsplit context)."""
-        for _ in range(nsteps):
+        k = 0
+        while k < nsteps:
             if self.since_rebuild >= rebuild_every:
                 self._rebuild()
             ch = cfl * self.h
             self.dt = ch / self.M if self.M > 0.0 else ch
-            self._exchange(TILE - 1, 0)
-            for e in self.engines.values():
-                e.step(self.dt, rebuild_every)
-            self.since_rebuild += 1
+            if self.comm.nparts == 1:
+                # nothing to exchange: the rest of the rebuild period in one call
+                n = min(nsteps - k, rebuild_every - self.since_rebuild)
+                for e in self.engines.values():
+                    e.step(self.dt, rebuild_every, n)
+            else:
+                n = 1
+                self._exchange(TILE - 1, 0)
+                for e in self.engines.values():
+                    e.step(self.dt, rebuild_every)
+            self.updates += n * self.n_active * TILE ** 3
+            self.since_rebuild += n
+            k += n
 
     def gather_phi(self):
         """Owned planes of the parts in this process: {part: (z0, planes)}."""

@@ -36,8 +36,9 @@ class OracleSlab:
     def row_counts(self):
         return self.active.reshape(self.rows, -1).sum(axis=1).astype(np.int64)
 
-    def step(self, dt, rebuild_every):
-        self.p = oracle.step(self.p, self.h, dt, self.F, 0.0, self.active)
+    def step(self, dt, rebuild_every, n=1):
+        for _ in range(n):
+            self.p = oracle.step(self.p, self.h, dt, self.F, 0.0, self.active)
 
     def buffer(self, plane):
         return torch.empty((8 if plane < 0 else 1) * self.ny * self.nx, dtype=torch.float64)

@@ -109,7 +109,7 @@ def source_of(phi, F):
     return lambda z0, z1: (torch.from_numpy(phi[z0:z1].copy()), torch.from_numpy(F[z0:z1].copy()))
 
 
-@pytest.mark.parametrize("nparts", [3, 4])
+@pytest.mark.parametrize("nparts", [3, 6])
 def test_local_split_equals_unsplit_oracle_bitwise(nparts):
     phi, F = fields()
     run = slab.SlabRun(slab.LocalComm(nparts), OracleSlab, SHAPE, H, HW, source_of(phi, F))
@@ -122,7 +122,9 @@ def test_local_split_equals_unsplit_oracle_bitwise(nparts):
     assert np.array_equal(got, ref.phi)
     assert run.dt == ref.last_dt
     assert run.migrations > first                # Eq. 14 moved rows during the run
-    assert run.bounds == slab.partition_rows(run.active_rows(), nparts)
+    counts = run.active_rows()
+    best = slab.partition_rows(counts, nparts)
+    assert slab.SlabRun._largest(counts, run.bounds) <= slab.SlabRun._largest(counts, best)
 
 
 def _free_port():

@@ -65,7 +65,7 @@ def split(phi, F, prec, nparts):
     return out
 
 
-@pytest.mark.parametrize("nparts", [2, 3, 4])
+@pytest.mark.parametrize("nparts", [2, 3, 6])
 @pytest.mark.parametrize("prec", [ls.LS_FP32, ls.LS_FP64])
 def test_split_equals_unsplit_bitwise(prec, nparts):
     dt_np = np.float32 if prec == ls.LS_FP32 else np.float64
