@@ -7,22 +7,25 @@
 // X[m + off(t)][k] * W[t][k][n]  with K = N = 16 channels, accumulated in FP32
 // over the 27 taps.
 //
-// One CTA (128 threads) handles a block of BY x BZ output x-rows of 128
-// points (x0..x0+127).  The TMA engine loads the halo'd input block
-// (130 x (BY+2) x (BZ+2) points x 16 channels) as two 4-D boxes (8 channels,
-// x, y, z), one per half of the channels (the second tensor map starts 16
-// bytes into the activations), so shared memory holds
-// X_s[half][z][y][x][8]: every run of 8 consecutive
-// points x 8 channels is one contiguous 128-byte "core matrix" of the
-// canonical no-swizzle K-major operand layout.  The A operand of any tap is
-// then just a descriptor whose start address is shifted by the tap's offset
-// (SBO = 128 B between 8-point groups, LBO = one channel-half plane): no
-// im2col copy.  Points outside the grid are zero-filled by the TMA (zero
-// padding for free).  Weights are packed once per launch into the B layout.
-// Each M-tile (one x-row) accumulates its 27 MMAs (M=128, N=16, K=16) in its
-// own 16 TMEM columns; the epilogue reads TMEM with tcgen05.ld (warp w owns
-// lanes 32w..32w+31 = points x0+32w..) and applies bias + ReLU, bias only
-// (last layer), or the ReLU mask of the backward pass.
+// A block is 8 x 16 x 8 output points (x, y, z): one 8^3 tile wide in x and
+// z, two in y, so a block list can follow the band's tiles.  The TMA engine
+// loads the halo'd input block (10 x 18 x 10 points x 16 channels) as two
+// 4-D boxes (8 channels, x, y, z), one per half of the channels (the second
+// tensor map starts 16 bytes into the activations), so shared memory holds
+// X_s[half][z][y][x][8]: every run of 8 consecutive points x 8 channels is
+// one contiguous 128-byte "core matrix" of the canonical no-swizzle K-major
+// operand layout.  An M-tile is one z-plane of the block, 8 x-points x 16
+// y-rows = 128 points: its 16 groups of 8 points are the 16 rows, one
+// 10-point row apart (SBO = 160 B), and the A operand of any tap is then
+// just a descriptor whose start address is shifted by the tap's offset
+// (LBO = one channel-half plane): no im2col copy.  Points outside the grid
+// are zero-filled by the TMA (zero padding for free).  Weights are packed
+// once per launch into the B layout.  Each M-tile accumulates its 27 MMAs
+// (M=128, N=16, K=16) in its own 16 TMEM columns; the epilogue reads TMEM
+// with tcgen05.ld (warp w owns lanes 32w..32w+31, i.e. y-rows 4w..4w+3) and
+// applies bias + ReLU, bias only (last layer), or the ReLU mask of the
+// backward pass.  An optional list of blocks restricts the work (the
+// corrected step needs the network only near the band).
 //
 // Every wait on an mbarrier is bounded; on timeout the kernel records
 // ST_TIMEOUT in the status word, stops issuing work, frees its TMEM and
@@ -37,14 +40,14 @@ namespace lsk {
 
 namespace {
 
-constexpr int CX = 128;            // output points per x-row tile (= MMA M)
-constexpr int BY = 2, BZ = 2;      // x-rows per block in y and z
-constexpr int PX = CX + 2, PY = BY + 2, PZ = BZ + 2;
+constexpr int BXP = 8, BYP = 16, BZP = 8;  // output points of a block per axis
+constexpr int PX = BXP + 2, PY = BYP + 2, PZ = BZP + 2;
 constexpr int PB = PX * PY * PZ;   // points in the halo'd block
 constexpr int HALF_BYTES = PB * 16;
 constexpr int XS_BYTES = 2 * HALF_BYTES;
 constexpr int W_BYTES = 27 * 512;  // 27 taps x (16 x 16 bf16)
-constexpr int MT = BY * BZ;        // M-tiles per block
+constexpr int MT = BZP;            // M-tiles per block: one per z-plane
+constexpr int A_SBO = PX * 16;     // between the 8-point groups (y-rows) of an M-tile
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p)
@@ -152,6 +155,8 @@ struct ConvArgs {
     __nv_bfloat16* out_bf16;     // hidden / backward modes: [p][16]
     float* out_f32;              // last-layer mode: [p] (channel 0)
     unsigned* status;
+    const int* blist;            // blocks to compute (NULL: every block)
+    const int* bcount;           // their number (device)
     int nx, ny, nz;
     int mode;                    // 0 bias+ReLU, 1 bias (channel 0, FP32), 2 ReLU mask
 };
@@ -163,8 +168,8 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
 
 // Warp-specialised pipeline, one CTA per SM, 6 warps:
 //   warp 0      TMA producer: halo'd input block -> shared stage s (2 stages)
-//   warp 1      TMEM owner and MMA issuer: 4 M-tiles x 27 taps into TMEM
-//               accumulator buffer b (2 buffers x 64 columns)
+//   warp 1      TMEM owner and MMA issuer: 8 M-tiles x 27 taps into TMEM
+//               accumulator buffer b (2 buffers x 128 columns)
 //   warps 2..5  epilogue: TMEM -> registers -> global (warp w reads lane
 //               quadrant w % 4)
 // Barriers: full[s] (TMA bytes landed), empty[s] (MMAs reading stage s
@@ -172,7 +177,7 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
 // 4 arrivals).  Block i of this CTA uses stage and buffer i % 2.
 constexpr int NSTAGE = 2;
 constexpr int CONV_THREADS = 192;
-constexpr int ACC_COLS = 64;  // per accumulator buffer
+constexpr int ACC_COLS = 16 * MT;  // per accumulator buffer
 
 __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_constant__ CUtensorMap map0,
                                                               const __grid_constant__ CUtensorMap map1,
@@ -210,31 +215,32 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
     __syncthreads();
     fence_after();
     const unsigned tmem = tmem_base_s;
-    const int nbx = a.nx / CX, nby = a.ny / BY, nbz = a.nz / BZ;
-    const int nblocks = nbx * nby * nbz;
+    const int nbx = a.nx / BXP, nby = a.ny / BYP;
+    const int nblocks = a.bcount ? *a.bcount : nbx * nby * (a.nz / BZP);
     const unsigned xs_addr = smem_u32(smem), ws_addr = smem_u32(ws);
 
     if (warp == 0) {
         if (lane == 0) {
             int i = 0;
-            for (int blk = blockIdx.x; blk < nblocks && !abort_s; blk += gridDim.x, ++i) {
+            for (int k = blockIdx.x; k < nblocks && !abort_s; k += gridDim.x, ++i) {
                 const int s = i % NSTAGE, u = i / NSTAGE;
                 if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1)) {
                     atomicOr(a.status, ST_TIMEOUT);
                     abort_s = 1;
                     break;
                 }
+                const int blk = a.blist ? a.blist[k] : k;
                 const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
                 unsigned char* xs = smem + s * XS_BYTES;
                 mbar_expect_tx(&full[s], XS_BYTES);
-                tma_load_4d(xs, &map0, 0, bx * CX - 1, by * BY - 1, bz * BZ - 1, &full[s]);
-                tma_load_4d(xs + HALF_BYTES, &map1, 0, bx * CX - 1, by * BY - 1, bz * BZ - 1, &full[s]);
+                tma_load_4d(xs, &map0, 0, bx * BXP - 1, by * BYP - 1, bz * BZP - 1, &full[s]);
+                tma_load_4d(xs + HALF_BYTES, &map1, 0, bx * BXP - 1, by * BYP - 1, bz * BZP - 1, &full[s]);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             int i = 0;
-            for (int blk = blockIdx.x; blk < nblocks && !abort_s; blk += gridDim.x, ++i) {
+            for (int k = blockIdx.x; k < nblocks && !abort_s; k += gridDim.x, ++i) {
                 const int s = i % NSTAGE, u = i / NSTAGE;
                 const int b = i % 2, ub = i / 2;
                 if (!mbar_wait(&full[s], u & 1) || (ub > 0 && !mbar_wait(&acc_empty[b], (ub - 1) & 1))) {
@@ -244,17 +250,17 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
                 }
                 fence_after();
                 // descriptors are linear in the start address (field =
-                // address >> 4, all shared addresses < 256 KB): the 108 MMAs
+                // address >> 4, all shared addresses < 256 KB): the 216 MMAs
                 // of a block differ only by compile-time offsets
-                const unsigned long long da = smem_desc(xs_addr + s * XS_BYTES, HALF_BYTES, 128);
+                const unsigned long long da = smem_desc(xs_addr + s * XS_BYTES, HALF_BYTES, A_SBO);
                 const unsigned long long db = smem_desc(ws_addr, 256, 128);
                 const unsigned acc = tmem + b * ACC_COLS;
 #pragma unroll
                 for (int j = 0; j < MT; ++j) {
 #pragma unroll
                     for (int t = 0; t < 27; ++t) {
-                        const int pofs = ((j / BY + 1 + t / 9 - 1) * PY + (j % BY + 1 + (t / 3) % 3 - 1)) * PX +
-                                         (1 + t % 3 - 1);
+                        // z-plane j + dz, y-row 0 + dy, x 0 + dx of the halo'd block
+                        const int pofs = ((j + t / 9) * PY + (t / 3) % 3) * PX + t % 3;
                         mma_bf16(acc + 16 * j, da + (unsigned long long)pofs,
                                  db + (unsigned long long)(t * 32), t > 0 ? 1u : 0u);
                     }
@@ -264,10 +270,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
             }
         }
     } else {
-        // epilogue warps: lane quadrant q = warp % 4 -> points x0 + 32 q + lane
+        // epilogue warps: lane quadrant q = warp % 4 -> M rows 32 q + lane,
+        // i.e. point (x0 + lane % 8, y0 + 4 q + lane / 8) of every z-plane
         const int q = warp & 3;
         int i = 0;
-        for (int blk = blockIdx.x; blk < nblocks && !abort_s; blk += gridDim.x, ++i) {
+        for (int k = blockIdx.x; k < nblocks && !abort_s; k += gridDim.x, ++i) {
             const int b = i % 2, ub = i / 2;
             if (!mbar_wait(&acc_full[b], ub & 1)) {
                 if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
@@ -275,10 +282,12 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
                 break;
             }
             fence_after();
+            const int blk = a.blist ? a.blist[k] : k;
             const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
-            const int x = bx * CX + 32 * q + lane;
+            const int x = bx * BXP + (lane & 7);
+            const int y = by * BYP + 4 * q + (lane >> 3);
             for (int j = 0; j < MT; ++j) {
-                const int y = by * BY + j % BY, z = bz * BZ + j / BY;
+                const int z = bz * BZP + j;
                 float v[16];
                 tmem_ld16(tmem + b * ACC_COLS + ((unsigned)(32 * q) << 16) + 16 * j, v);
                 const size_t pidx = ((size_t)z * a.ny + y) * a.nx + x;
@@ -560,7 +569,7 @@ EncodeTiledFn encode_fn()
 
 bool conv3_shape_ok(int nx, int ny, int nz)
 {
-    return nx >= CX && nx % CX == 0 && ny % BY == 0 && nz % BZ == 0 && ny >= BY && nz >= BZ;
+    return nx >= BXP && nx % BXP == 0 && ny >= BYP && ny % BYP == 0 && nz >= BZP && nz % BZP == 0;
 }
 
 // tensor maps over act[nz][ny][nx][16] bf16 viewed as (8 channels, x, y, z):
@@ -590,6 +599,8 @@ cudaError_t make_act_maps(CUtensorMap* maps, const void* act, int nx, int ny, in
 {
     return make_maps_box(maps, act, nx, ny, nz, PX, PY, PZ);
 }
+
+int conv3_blocks(int nx, int ny, int nz) { return (nx / BXP) * (ny / BYP) * (nz / BZP); }
 
 bool conv3_wgrad_shape_ok(int nx, int ny, int nz)
 {
@@ -645,7 +656,8 @@ cudaError_t launch_pack_weights(const float* W, int ci, int co, int flip, void* 
 
 cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float* bias,
                          const void* mask, void* out_bf16, float* out_f32, int nx, int ny, int nz,
-                         int mode, unsigned* status, cudaStream_t s)
+                         int mode, unsigned* status, cudaStream_t s, const int* blist,
+                         const int* bcount)
 {
     static bool attr = false;
     const int smem = NSTAGE * XS_BYTES + W_BYTES;
@@ -661,6 +673,8 @@ cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float
     a.out_bf16 = (__nv_bfloat16*)out_bf16;
     a.out_f32 = out_f32;
     a.status = status;
+    a.blist = blist;
+    a.bcount = blist ? bcount : nullptr;
     a.nx = nx;
     a.ny = ny;
     a.nz = nz;
@@ -668,7 +682,8 @@ cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int nblocks = (nx / CX) * (ny / BY) * (nz / BZ);
+    // with a list the grid covers every block (the count is on the device)
+    const int nblocks = conv3_blocks(nx, ny, nz);
     int grid = sms;
     if (grid > nblocks) grid = nblocks;
     k_conv3_tc<<<grid, CONV_THREADS, smem, s>>>(maps[0], maps[1], a);

@@ -248,14 +248,21 @@ cudaError_t launch_set_dt_batch(StepScalars* sc, int n_inst, const Inst* d_inst,
 // ---------------------------------------------------------------------------
 // learned corrector (ls_conv.cu, ls_learned.cu)
 // ---------------------------------------------------------------------------
+// blocks of 8 x 16 x 8 points: nx, nz multiples of 8, ny of 16
 bool conv3_shape_ok(int nx, int ny, int nz);
+int conv3_blocks(int nx, int ny, int nz);
 cudaError_t make_act_maps(CUtensorMap* maps, const void* act, int nx, int ny, int nz);
+// the convolution blocks (ids bx + nbx (by + nby bz)) whose tiles lie within
+// one tile of an active tile (act bit 0) of a single grid; unordered
+cudaError_t launch_block_list(const uint8_t* act, const Inst& in, int* list, int* count,
+                              cudaStream_t s);
 cudaError_t launch_pack_weights(const float* W, int ci, int co, int flip, void* out, cudaStream_t s);
 // mode 0: out_bf16 = relu(conv + b); 1: out_f32 = (conv + b) channel 0;
 // 2: out_bf16 = conv(x) * [mask > 0] (x: gradient, weights packed flipped)
 cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float* bias,
                          const void* mask, void* out_bf16, float* out_f32, int nx, int ny, int nz,
-                         int mode, unsigned* status, cudaStream_t s);
+                         int mode, unsigned* status, cudaStream_t s, const int* blist = nullptr,
+                         const int* bcount = nullptr);
 cudaError_t launch_features(const float* phi, const float* phit, const float* F, float Fc,
                             float inv_h, long long n, void* X, cudaStream_t s);
 cudaError_t launch_count_mask(const float* phi, double gamma, long long n, int* count, cudaStream_t s);

@@ -173,6 +173,34 @@ __global__ void k_restrict4(const float* __restrict__ fine, int nfx, int nfy, in
     }
 }
 
+// the corrected step needs the network's output only on the active tiles;
+// four 3x3x3 layers reach 4 cells, so computing every layer on the blocks
+// within one tile (8 cells) of an active tile leaves those outputs exact.
+// A block (bx, by, bz) holds tile (bx, 2 by .. 2 by + 1, bz).
+__global__ void k_block_list(const uint8_t* __restrict__ act, Inst in, int* list, int* count)
+{
+    const int nbx = in.tnx, nby = in.tny / 2, nbz = in.tnz;
+    const int n = nbx * nby * nbz;
+    for (int blk = blockIdx.x * blockDim.x + threadIdx.x; blk < n; blk += gridDim.x * blockDim.x) {
+        const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
+        bool need = false;
+        for (int tz = bz - 1; tz <= bz + 1 && !need; ++tz) {
+            if (tz < 0 || tz >= in.tnz) continue;
+            for (int ty = 2 * by - 1; ty <= 2 * by + 2 && !need; ++ty) {
+                if (ty < 0 || ty >= in.tny) continue;
+                for (int tx = bx - 1; tx <= bx + 1; ++tx) {
+                    if (tx < 0 || tx >= in.tnx) continue;
+                    if (act[((size_t)tz * in.tny + ty) * in.tnx + tx] & 1) {
+                        need = true;
+                        break;
+                    }
+                }
+            }
+        }
+        if (need) list[atomicAdd(count, 1)] = blk;
+    }
+}
+
 int grid_for(long long n, int threads)
 {
     long long g = (n + threads - 1) / threads;
@@ -222,6 +250,16 @@ cudaError_t launch_residual(float* phit, const float* z, const int* list, const 
     k_residual_check<<<g, 128, 0, s>>>(z, list, count, in, sc, hc, flag);
     k_residual_apply<<<g, 128, 0, s>>>(phit, z, list, count, in, hc, flag);
     k_flag_account<<<1, 1, 0, s>>>(flag, fallbacks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_list(const uint8_t* act, const Inst& in, int* list, int* count,
+                              cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    const int n = in.tnx * (in.tny / 2) * in.tnz;
+    k_block_list<<<grid_for(n, 256), 256, 0, s>>>(act, in, list, count);
     return cudaGetLastError();
 }
 

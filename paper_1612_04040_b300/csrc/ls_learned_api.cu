@@ -61,6 +61,8 @@ struct Learned {
     double* d_loss = nullptr;
     unsigned* d_flag = nullptr;
     unsigned long long* d_fallbacks = nullptr;
+    int* d_blist = nullptr;       // convolution blocks near the band (corrected step)
+    int* d_bcount = nullptr;
     CUtensorMap map_X0[2], map_A[NL - 1][2], map_G[NL][2];
     std::vector<Pair> pairs;
     bool initialised = false;
@@ -70,7 +72,8 @@ void learned_free(Learned* L)
 {
     if (!L) return;
     void* ptrs[] = {L->params, L->grads, L->adam_m, L->adam_v, L->X0, L->z, L->rm_phi, L->rm_phit,
-                    L->rm_F, L->d_count, L->d_loss, L->d_flag, L->d_fallbacks};
+                    L->rm_F, L->d_count, L->d_loss, L->d_flag, L->d_fallbacks, L->d_blist,
+                    L->d_bcount};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int l = 0; l < NL; ++l) {
@@ -123,15 +126,24 @@ int ensure_learned(ls_ctx* c, Learned** out)
     LCK(cudaMalloc(&L->adam_v, np * 4));
     LCK(cudaMemset(L->adam_m, 0, np * 4));
     LCK(cudaMemset(L->adam_v, 0, np * 4));
+    // activations start at zero: a step that computes the network only near
+    // the band reads finite values everywhere
     for (int l = 0; l < lsk::NL; ++l) {
         LCK(cudaMalloc(&L->wpack_fwd[l], 27 * 512));
         LCK(cudaMalloc(&L->wpack_bwd[l], 27 * 512));
         LCK(cudaMalloc(&L->G[l], act));
-        if (l < lsk::NL - 1) LCK(cudaMalloc(&L->A[l], act));
+        LCK(cudaMemset(L->G[l], 0, act));
+        if (l < lsk::NL - 1) {
+            LCK(cudaMalloc(&L->A[l], act));
+            LCK(cudaMemset(L->A[l], 0, act));
+        }
     }
     LCK(cudaMalloc(&L->X0, act));
     LCK(cudaMemset(L->X0, 0, act));
     LCK(cudaMalloc(&L->z, L->npts * 4));
+    LCK(cudaMemset(L->z, 0, L->npts * 4));
+    LCK(cudaMalloc(&L->d_blist, sizeof(int) * (size_t)lsk::conv3_blocks(L->nx, L->ny, L->nz)));
+    LCK(cudaMalloc(&L->d_bcount, sizeof(int)));
     LCK(cudaMalloc(&L->rm_phi, L->npts * 4));
     LCK(cudaMalloc(&L->rm_phit, L->npts * 4));
     LCK(cudaMalloc(&L->rm_F, L->npts * 4));
@@ -163,15 +175,16 @@ int pack_all(ls_ctx* c, Learned* L, bool bwd, cudaStream_t s)
     return LS_OK;
 }
 
-// forward network on L->X0 -> L->z
-int forward(ls_ctx* c, Learned* L, cudaStream_t s)
+// forward network on L->X0 -> L->z, on every block or on the listed ones
+int forward(ls_ctx* c, Learned* L, cudaStream_t s, bool band_only = false)
 {
     const CUtensorMap* in = L->map_X0;
     for (int l = 0; l < lsk::NL; ++l) {
         const bool last = l == lsk::NL - 1;
         LCK(lsk::launch_conv3(in, L->wpack_fwd[l], L->params + lsk::b_off(l), nullptr,
                               last ? nullptr : L->A[l], last ? L->z : nullptr, L->nx, L->ny, L->nz,
-                              last ? 1 : 0, c->d_status, s));
+                              last ? 1 : 0, c->d_status, s, band_only ? L->d_blist : nullptr,
+                              band_only ? L->d_bcount : nullptr));
         ++c->launches;
         if (!last) in = L->map_A[l];
     }
@@ -201,7 +214,9 @@ int ls_engine_learned_after_step(ls_ctx* c, cudaStream_t s)
     c->launches += 3;
     int r = pack_all(c, L, false, s);
     if (r) return r;
-    r = forward(c, L, s);
+    LCK(lsk::launch_block_list(c->act, in, L->d_blist, L->d_bcount, s));
+    c->launches += 1;
+    r = forward(c, L, s, true);
     if (r) return r;
     LCK(lsk::launch_residual((float*)dst, L->z, c->list, c->d_count, in, c->d_sc, (float)in.h,
                              L->d_flag, L->d_fallbacks, s));

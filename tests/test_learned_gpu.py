@@ -8,8 +8,8 @@ the same BF16-rounded inputs and weights within 1e-2 relative (BF16 has an
 8-bit mantissa; the accumulation is FP32); FP32 outputs within 1e-4.
 
 Two shapes: SMALL gives each CTA of the persistent convolution one block;
-MULTI (64 x 64 x 128 points, 1024 blocks on at most 148 CTAs) gives every CTA
-six or more blocks, so the reuse of both shared-memory stages, both TMEM
+MULTI (64 x 128 x 128 points, 1024 blocks of 8 x 16 x 8 on at most 148 CTAs)
+gives every CTA six or more blocks, so the reuse of both shared-memory stages, both TMEM
 accumulator buffers and every mbarrier phase after the first are compared
 with the oracle too."""
 import numpy as np
@@ -22,8 +22,8 @@ from paper_1612_04040_b300 import native as ls
 
 pytestmark = pytest.mark.gpu
 
-SMALL = (6, 4, 128)   # (nz, ny, nx): nx a multiple of 128, ny and nz even
-MULTI = (64, 64, 128)
+SMALL = (8, 16, 64)   # (nz, ny, nx): nx a multiple of 64 (weight gradient), nz of 8, ny of 16
+MULTI = (64, 128, 128)
 SHAPES = pytest.mark.parametrize("shape", [SMALL, MULTI], ids=["small", "multi"])
 
 
