@@ -508,7 +508,7 @@ int ls_write_vtk(const char *path, const void *phi, int nx, int ny, int nz, doub
  * or |h * CNN| exceeds dt * max|F|.  Training pairs are (phi^n, phi_ref,
  * F) on the coarse grid, phi_ref = the restricted fine-grid plain solution
  * one coarse step later.  The corrected step computes the network only on
- * the blocks of 8 x 16 x 8 points within one tile of an active tile (its
+ * the blocks of 8 x 16 x 4 points within one tile of an active tile (its
  * four 3x3x3 layers reach 4 cells, so the outputs on the active tiles are
  * those of the whole grid).  Single FP32 contexts with nx and nz multiples
  * of 8 and ny of 16; LS_EINVAL otherwise.
@@ -581,8 +581,8 @@ int ls_set_step_mode(ls_ctx *ctx, int mode);
 int ls_learned_fallbacks(ls_ctx *ctx, unsigned long long *n);
 
 /* Layer primitives on caller-owned device buffers (no allocation):
- * ls_conv3_bf16: x = BF16 [p][16] channels-last (nx and nz multiples of 8,
- * ny of 16), W = FP32 [27][ci][co] (ci, co <= 16), work = device scratch
+ * ls_conv3_bf16: x = BF16 [p][16] channels-last (nx a multiple of 8, ny of
+ * 16, nz of 4), W = FP32 [27][ci][co] (ci, co <= 16), work = device scratch
  * of LS_CONV3_WORK_BYTES, status = device word that records LS_ETIMEOUT-type
  * failures (bit 1).  mode 0: out = BF16 [p][16] relu(conv(x) + b);
  * mode 1: out = FP32 [p] conv(x)[0] + b[0]; mode 2 (input gradient): out =

@@ -7,22 +7,31 @@
 // X[m + off(t)][k] * W[t][k][n]  with K = N = 16 channels, accumulated in FP32
 // over the 27 taps.
 //
-// A block is 8 x 16 x 8 output points (x, y, z): one 8^3 tile wide in x and
-// z, two in y, so a block list can follow the band's tiles.  The TMA engine
-// loads the halo'd input block (10 x 18 x 10 points x 16 channels) as two
-// 4-D boxes (8 channels, x, y, z), one per half of the channels (the second
-// tensor map starts 16 bytes into the activations), so shared memory holds
-// X_s[half][z][y][x][8]: every run of 8 consecutive points x 8 channels is
-// one contiguous 128-byte "core matrix" of the canonical no-swizzle K-major
-// operand layout.  An M-tile is one z-plane of the block, 8 x-points x 16
-// y-rows = 128 points: its 16 groups of 8 points are the 16 rows, one
-// 10-point row apart (SBO = 160 B), and the A operand of any tap is then
-// just a descriptor whose start address is shifted by the tap's offset
-// (LBO = one channel-half plane): no im2col copy.  Points outside the grid
-// are zero-filled by the TMA (zero padding for free).  Weights are packed
-// once per launch into the B layout.  Each M-tile accumulates its 27 MMAs
-// (M=128, N=16, K=16) in its own 16 TMEM columns; the epilogue reads TMEM
-// with tcgen05.ld (warp w owns lanes 32w..32w+31, i.e. y-rows 4w..4w+3) and
+// A block is 8 x 16 x 4 output points (x, y, z): one 8^3 tile wide in x,
+// two in y, half a tile in z, so a block list can follow the band's tiles.
+// The TMA engine loads the halo'd input block (10 x 18 x 6 points x 16
+// channels) as two 4-D boxes (8 channels, x, y, z), one per half of the
+// channels (the second tensor map starts 16 bytes into the activations), so
+// shared memory holds X_s[half][z][y][x][8]: every run of 8 consecutive
+// points x 8 channels is one contiguous 128-byte "core matrix" of the
+// canonical no-swizzle K-major operand layout.  An M-tile is 8 x-points x
+// 16 y-rows = 128 points of one z-plane of the halo'd block: its 16 groups
+// of 8 points are the 16 rows, one 10-point row apart (SBO = 160 B), and
+// the A operand of any (dx, dy) shift is just a descriptor whose start
+// address is shifted by it (LBO = one channel-half plane): no im2col copy.
+// Points outside the grid are zero-filled by the TMA (zero padding for
+// free).
+//
+// The three dz taps share their A operand: for input plane i of the halo'd
+// block and shift (dx, dy), one MMA with N = 48 (dz = -1, 0, 1 stacked x 16
+// output channels) gives D_i[p][dz, o] = sum_c X_i[p + (dx, dy)][c]
+// W[dx, dy, dz][c][o], accumulated over the 9 shifts; output plane j then
+// sums D_j[-1], D_{j+1}[0], D_{j+2}[+1] in the epilogue.  That is 9 x 6 = 54
+// MMAs per block (the first and last input planes feed one output plane
+// and take N = 16) instead of 27 per output plane: the tensor core's
+// operand reads (a 4 KB A tile per MMA) bound this layer.  Weights are
+// packed once per launch into the B layout.  The epilogue reads TMEM with
+// tcgen05.ld (warp w owns lanes 32w..32w+31, i.e. y-rows 4w..4w+3) and
 // applies bias + ReLU, bias only (last layer), or the ReLU mask of the
 // backward pass.  An optional list of blocks restricts the work (the
 // corrected step needs the network only near the band).
@@ -40,13 +49,14 @@ namespace lsk {
 
 namespace {
 
-constexpr int BXP = 8, BYP = 16, BZP = 8;  // output points of a block per axis
+constexpr int BXP = 8, BYP = 16, BZP = 4;  // output points of a block per axis
 constexpr int PX = BXP + 2, PY = BYP + 2, PZ = BZP + 2;
 constexpr int PB = PX * PY * PZ;   // points in the halo'd block
 constexpr int HALF_BYTES = PB * 16;
 constexpr int XS_BYTES = 2 * HALF_BYTES;
-constexpr int W_BYTES = 27 * 512;  // 27 taps x (16 x 16 bf16)
-constexpr int MT = BZP;            // M-tiles per block: one per z-plane
+constexpr int W_BYTES = 27 * 512;  // 9 shifts x (48 x 16 bf16)
+constexpr int W_PAIR = 48 * 16 * 2;  // bytes of one (dx, dy) shift: N = 48 (dz, o), K = 16
+constexpr int MT = BZP;            // output z-planes per block
 constexpr int A_SBO = PX * 16;     // between the 8-point groups (y-rows) of an M-tile
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
@@ -109,16 +119,17 @@ __device__ __forceinline__ unsigned long long smem_desc(unsigned addr, unsigned 
 }
 
 // instruction descriptor, kind::f16: D F32, A and B BF16, both K-major,
-// N = 16, M = 128
+// M = 128, N = 16 (IDESC) or 48 (IDESC48)
 constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr unsigned IDESC48 = (1u << 4) | (1u << 7) | (1u << 10) | ((48u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(unsigned d_tmem, unsigned long long a, unsigned long long b,
-                                         unsigned accumulate)
+                                         unsigned accumulate, unsigned idesc = IDESC)
 {
     asm volatile(
         "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
         "  tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -168,16 +179,22 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
 
 // Warp-specialised pipeline, one CTA per SM, 6 warps:
 //   warp 0      TMA producer: halo'd input block -> shared stage s (2 stages)
-//   warp 1      TMEM owner and MMA issuer: 8 M-tiles x 27 taps into TMEM
-//               accumulator buffer b (2 buffers x 128 columns)
+//   warp 1      TMEM owner and MMA issuer: 6 input planes x 9 shifts into
+//               TMEM accumulator buffer b (2 buffers x 256 columns)
 //   warps 2..5  epilogue: TMEM -> registers -> global (warp w reads lane
 //               quadrant w % 4)
 // Barriers: full[s] (TMA bytes landed), empty[s] (MMAs reading stage s
 // finished), acc_full[b] (accumulators ready), acc_empty[b] (epilogue done,
 // 4 arrivals).  Block i of this CTA uses stage and buffer i % 2.
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 3;
 constexpr int CONV_THREADS = 192;
-constexpr int ACC_COLS = 16 * MT;  // per accumulator buffer
+constexpr int ACC_COLS = 256;  // per accumulator buffer (224 used)
+// TMEM column of input plane i's dz group g: plane 0 holds only g = 0 (its
+// only output is plane 0), plane MT + 1 only g = 2, the others all three
+__host__ __device__ constexpr int acc_col(int i, int g)
+{
+    return i == 0 ? 0 : (i == MT + 1 ? 16 + 48 * MT : 16 + 48 * (i - 1) + 16 * g);
+}
 
 __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_constant__ CUtensorMap map0,
                                                               const __grid_constant__ CUtensorMap map1,
@@ -253,16 +270,21 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
                 // address >> 4, all shared addresses < 256 KB): the 216 MMAs
                 // of a block differ only by compile-time offsets
                 const unsigned long long da = smem_desc(xs_addr + s * XS_BYTES, HALF_BYTES, A_SBO);
-                const unsigned long long db = smem_desc(ws_addr, 256, 128);
+                const unsigned long long db = smem_desc(ws_addr, W_PAIR / 2, 128);
                 const unsigned acc = tmem + b * ACC_COLS;
 #pragma unroll
-                for (int j = 0; j < MT; ++j) {
+                for (int i = 0; i < MT + 2; ++i) {
 #pragma unroll
-                    for (int t = 0; t < 27; ++t) {
-                        // z-plane j + dz, y-row 0 + dy, x 0 + dx of the halo'd block
-                        const int pofs = ((j + t / 9) * PY + (t / 3) % 3) * PX + t % 3;
-                        mma_bf16(acc + 16 * j, da + (unsigned long long)pofs,
-                                 db + (unsigned long long)(t * 32), t > 0 ? 1u : 0u);
+                    for (int p = 0; p < 9; ++p) {
+                        // input plane i, y-row 0 + (dy + 1), x 0 + (dx + 1) of the halo'd block
+                        const unsigned long long a_ = da + (unsigned long long)((i * PY + p / 3) * PX + p % 3);
+                        const unsigned long long b_ = db + (unsigned long long)(p * (W_PAIR / 16));
+                        if (i == 0)
+                            mma_bf16(acc + acc_col(0, 0), a_, b_, p > 0 ? 1u : 0u);
+                        else if (i == MT + 1)  // the dz = +1 group: 2 x 8 rows of N in
+                            mma_bf16(acc + acc_col(i, 2), a_, b_ + 2 * 16, p > 0 ? 1u : 0u);
+                        else
+                            mma_bf16(acc + acc_col(i, 0), a_, b_, p > 0 ? 1u : 0u, IDESC48);
                     }
                 }
                 mma_commit(&empty[s]);
@@ -276,20 +298,38 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
         int i = 0;
         for (int k = blockIdx.x; k < nblocks && !abort_s; k += gridDim.x, ++i) {
             const int b = i % 2, ub = i / 2;
+            const int blk = a.blist ? a.blist[k] : k;
+            const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
+            const int x = bx * BXP + (lane & 7);
+            const int y = by * BYP + 4 * q + (lane >> 3);
+            // the backward pass's ReLU mask does not depend on the MMAs: its
+            // loads go out before the wait for the accumulators
+            uint4 mk[MT][2];
+            if (a.mode == 2) {
+#pragma unroll
+                for (int j = 0; j < MT; ++j) {
+                    const size_t pidx = ((size_t)(bz * BZP + j) * a.ny + y) * a.nx + x;
+                    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + pidx * 16);
+                    mk[j][0] = mp[0];
+                    mk[j][1] = mp[1];
+                }
+            }
             if (!mbar_wait(&acc_full[b], ub & 1)) {
                 if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
                 abort_s = 1;
                 break;
             }
             fence_after();
-            const int blk = a.blist ? a.blist[k] : k;
-            const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
-            const int x = bx * BXP + (lane & 7);
-            const int y = by * BYP + 4 * q + (lane >> 3);
+#pragma unroll
             for (int j = 0; j < MT; ++j) {
                 const int z = bz * BZP + j;
-                float v[16];
-                tmem_ld16(tmem + b * ACC_COLS + ((unsigned)(32 * q) << 16) + 16 * j, v);
+                float v[16], v1[16], v2[16];
+                const unsigned tb = tmem + b * ACC_COLS + ((unsigned)(32 * q) << 16);
+                tmem_ld16(tb + acc_col(j, 0), v);
+                tmem_ld16(tb + acc_col(j + 1, 1), v1);
+                tmem_ld16(tb + acc_col(j + 2, 2), v2);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) v[c] = (v[c] + v1[c]) + v2[c];
                 const size_t pidx = ((size_t)z * a.ny + y) * a.nx + x;
                 if (a.mode == 1) {
                     a.out_f32[pidx] = v[0] + a.bias[0];
@@ -299,10 +339,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
 #pragma unroll
                     for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + a.bias[c], 0.f);
                 } else {
-                    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + pidx * 16);
-                    const uint4 m0 = mp[0], m1 = mp[1];
-                    const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
-                    const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+                    const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&mk[j][0]);
+                    const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&mk[j][1]);
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         if (!(__bfloat162float(mb0[c]) > 0.f)) v[c] = 0.f;
@@ -525,23 +563,26 @@ __global__ void k_selftest_wait(unsigned* status, long long polls)
 }
 
 // pack W (FP32 [27][ci][co], ci, co <= 16) into the canonical K-major B
-// layout per tap: [kb][nb][8 n][8 k] bf16, B[n][k] = W[t][k][n].  flip: the
-// backward-data operator, B[n][k] = W[26 - t][n][k] (taps mirrored, channels
-// swapped).  Missing channels are zero.
+// layout per (dx, dy) shift p = (dy + 1) 3 + (dx + 1): [kb][nb][8 n][8 k]
+// bf16 with N = 48 rows n = 16 g + o (g = dz + 1) and K = 16:
+// B[n][k] = W[t][k][o], t = 9 g + p.  flip: the backward-data operator,
+// B[n][k] = W[26 - t][o][k] (taps mirrored, channels swapped).  Missing
+// channels are zero.
 __global__ void k_pack_weights(const float* __restrict__ W, int ci, int co, int flip,
                                __nv_bfloat16* out)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 27*256 entries
-    if (i >= 27 * 256) return;
-    const int t = i / 256, r = i % 256;
-    const int kb = r / 128, nb = (r / 64) % 2, n8 = (r / 8) % 8, k8 = r % 8;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // over 9 * 768 entries
+    if (i >= 9 * 768) return;
+    const int p = i / 768, r = i % 768;
+    const int kb = r / 384, nb = (r / 64) % 6, n8 = (r / 8) % 8, k8 = r % 8;
     const int n = nb * 8 + n8, k = kb * 8 + k8;
+    const int g = n / 16, o = n % 16, t = 9 * g + p;
     float v = 0.f;
     if (!flip) {
-        if (k < ci && n < co) v = W[((size_t)t * ci + k) * co + n];
+        if (k < ci && o < co) v = W[((size_t)t * ci + k) * co + o];
     } else {
-        // forward weights W[t][c][o] with c < ci, o < co; here k = o, n = c
-        if (n < ci && k < co) v = W[((size_t)(26 - t) * ci + n) * co + k];
+        // forward weights W[t][c][o'] with c < ci, o' < co; here k = o', o = c
+        if (o < ci && k < co) v = W[((size_t)(26 - t) * ci + o) * co + k];
     }
     out[i] = __float2bfloat16_rn(v);
 }
@@ -650,7 +691,7 @@ cudaError_t launch_selftest_wait(unsigned* status, long long polls, cudaStream_t
 
 cudaError_t launch_pack_weights(const float* W, int ci, int co, int flip, void* out, cudaStream_t s)
 {
-    k_pack_weights<<<(27 * 256 + 255) / 256, 256, 0, s>>>(W, ci, co, flip, (__nv_bfloat16*)out);
+    k_pack_weights<<<(9 * 768 + 255) / 256, 256, 0, s>>>(W, ci, co, flip, (__nv_bfloat16*)out);
     return cudaGetLastError();
 }
 

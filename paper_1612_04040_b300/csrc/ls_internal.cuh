@@ -248,7 +248,7 @@ cudaError_t launch_set_dt_batch(StepScalars* sc, int n_inst, const Inst* d_inst,
 // ---------------------------------------------------------------------------
 // learned corrector (ls_conv.cu, ls_learned.cu)
 // ---------------------------------------------------------------------------
-// blocks of 8 x 16 x 8 points: nx, nz multiples of 8, ny of 16
+// blocks of 8 x 16 x 4 points: nx a multiple of 8, ny of 16, nz of 4
 bool conv3_shape_ok(int nx, int ny, int nz);
 int conv3_blocks(int nx, int ny, int nz);
 cudaError_t make_act_maps(CUtensorMap* maps, const void* act, int nx, int ny, int nz);

@@ -176,15 +176,16 @@ __global__ void k_restrict4(const float* __restrict__ fine, int nfx, int nfy, in
 // the corrected step needs the network's output only on the active tiles;
 // four 3x3x3 layers reach 4 cells, so computing every layer on the blocks
 // within one tile (8 cells) of an active tile leaves those outputs exact.
-// A block (bx, by, bz) holds tile (bx, 2 by .. 2 by + 1, bz).
+// A block (bx, by, bz) of 8 x 16 x 4 points lies in tiles (bx, 2 by ..
+// 2 by + 1, bz / 2).
 __global__ void k_block_list(const uint8_t* __restrict__ act, Inst in, int* list, int* count)
 {
-    const int nbx = in.tnx, nby = in.tny / 2, nbz = in.tnz;
+    const int nbx = in.tnx, nby = in.tny / 2, nbz = 2 * in.tnz;
     const int n = nbx * nby * nbz;
     for (int blk = blockIdx.x * blockDim.x + threadIdx.x; blk < n; blk += gridDim.x * blockDim.x) {
         const int bx = blk % nbx, by = (blk / nbx) % nby, bz = blk / (nbx * nby);
         bool need = false;
-        for (int tz = bz - 1; tz <= bz + 1 && !need; ++tz) {
+        for (int tz = bz / 2 - 1; tz <= bz / 2 + 1 && !need; ++tz) {
             if (tz < 0 || tz >= in.tnz) continue;
             for (int ty = 2 * by - 1; ty <= 2 * by + 2 && !need; ++ty) {
                 if (ty < 0 || ty >= in.tny) continue;
@@ -258,7 +259,7 @@ cudaError_t launch_block_list(const uint8_t* act, const Inst& in, int* list, int
 {
     cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    const int n = in.tnx * (in.tny / 2) * in.tnz;
+    const int n = in.tnx * (in.tny / 2) * (2 * in.tnz);
     k_block_list<<<grid_for(n, 256), 256, 0, s>>>(act, in, list, count);
     return cudaGetLastError();
 }

@@ -8,7 +8,7 @@ the same BF16-rounded inputs and weights within 1e-2 relative (BF16 has an
 8-bit mantissa; the accumulation is FP32); FP32 outputs within 1e-4.
 
 Two shapes: SMALL gives each CTA of the persistent convolution one block;
-MULTI (64 x 128 x 128 points, 1024 blocks of 8 x 16 x 8 on at most 148 CTAs)
+MULTI (64 x 128 x 128 points, 2048 blocks of 8 x 16 x 4 on at most 148 CTAs)
 gives every CTA six or more blocks, so the reuse of both shared-memory stages, both TMEM
 accumulator buffers and every mbarrier phase after the first are compared
 with the oracle too."""
