@@ -77,11 +77,23 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
                  : "memory");
 }
 
-// bounded wait for the phase with the given parity; false on timeout
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the phase with the given parity; false on timeout: after
+// `limit` polls or WAIT_NS nanoseconds, whichever comes first (a poll of
+// try_wait may suspend the thread for a while, so the poll count alone can
+// take minutes)
+constexpr unsigned long long WAIT_NS = 2000000000ull;
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
                                           long long limit = WAIT_LIMIT)
 {
     const unsigned a = smem_u32(bar);
+    const unsigned long long t0 = global_ns();
     for (long long i = 0; i < limit; ++i) {
         unsigned ok;
         asm volatile(
@@ -91,6 +103,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((i & 255) == 255 && global_ns() - t0 > WAIT_NS) return false;
     }
     return false;
 }
@@ -314,7 +327,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
                     mk[j][1] = mp[1];
                 }
             }
-            if (!mbar_wait(&acc_full[b], ub & 1)) {
+            // the lanes agree before the warp-collective TMEM loads
+            if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[b], ub & 1) ? 1 : 0)) {
                 if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
                 abort_s = 1;
                 break;
@@ -378,31 +392,36 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
 
 // ---- weight gradient on the tensor cores --------------------------------
 //
-// dW[t][c][o] = sum_p x[p + off(t)][c] dy[p][o] and db[o] = sum_p dy[p][o]
-// as one GEMM per CTA: M = (tap slot, input channel) in 4 M-tiles of 8 tap
-// slots x 16 channels, N = 16 output channels, K = the points of the CTA's
-// chunks.  Both operands are MN-major (the 8 channels of a point are one
-// contiguous 16-byte run): a chunk is 64 consecutive x-points of one
-// (y, z) row, and for every tap the TMA engine loads the chunk's points
-// shifted by the tap offset (out-of-grid points zero-filled: the
-// convolution's zero padding), one 1 KB box per tap and channel half, so
-// the 8-channel groups of all taps sit at one uniform stride (SBO = 1 KB)
-// and the 8-point groups at 128 B (LBO).  Tap slot 27 is a box of ones in
-// shared memory: its rows accumulate sum_p dy[p][o], the bias gradient;
-// slots 28..31 repeat it and are discarded.  The accumulator (64 TMEM
-// columns) lives across all chunks of the CTA; the epilogue adds it to dW
-// and db with FP32 atomics.
+// dW[t][c][o] = sum_p x[p + off(t)][c] dy[p][o] and db[o] = sum_p dy[p][o].
+// A tap is split as (dx, dy, dz) = (0, dy, dz) + (dx, 0, 0): with
+// q = p + (dx, 0, 0),
+//   dW[t][c][o] = sum_q x[q + (0, dy, dz)][c] dy[q - (dx, 0, 0)][o],
+// one GEMM per CTA with M = ((dy, dz) pair, input channel), N = (dx, output
+// channel) = 48 and K = the points q of the CTA's chunks (64 consecutive
+// x-points of one (y, z) row each; out-of-grid points zero-filled by the
+// TMA, which is the convolution's zero padding on both operands).  Both
+// operands are MN-major (the 8 channels of a point are one contiguous
+// 16-byte run).  Per chunk the TMA loads, per channel half, 9 boxes of x
+// (one per (dy, dz) pair, 1 KB each) and 3 boxes of dy (one per dx), so
+// the 8-channel groups of the pairs (M) and of the dx shifts (N) sit at one
+// stride (SBO = 1 KB) and the 8-point groups at 128 B (LBO).  M-tile 0 holds
+// pairs 0..7, M-tile 1 pair 8 and in slot 9 a box of ones kept in shared
+// memory, whose rows accumulate sum_q dy[q][o] (the bias gradient, from the
+// dx = 0 columns); slots 10..15 repeat it and are discarded.  The 96-column
+// accumulator lives in TMEM across all of a CTA's chunks; the epilogue adds
+// it to dW and db with FP32 atomics.
 constexpr int WG_PTS = 64;
 constexpr int WG_BOX = WG_PTS * 16;                  // 64 points x 8 channels, BF16
-constexpr int WG_SLOTS = 32;
-constexpr int WG_A_BYTES = WG_SLOTS * 2 * WG_BOX;    // 64 KB: 32 slots x 2 halves
-constexpr int WG_LOAD_BYTES = (27 * 2 + 2) * WG_BOX; // what the TMA writes per chunk
-constexpr int WG_STAGE = WG_A_BYTES + 2 * WG_BOX;    // + dy (2 halves)
-constexpr int WG_NSTAGE = 3;
+constexpr int WG_A_BYTES = 2 * 16 * WG_BOX;          // 2 M-tiles x 16 channel groups: 32 KB
+constexpr int WG_B_BYTES = 3 * 2 * WG_BOX;           // 3 dx shifts x 2 halves: 6 KB
+constexpr int WG_LOAD_BYTES = (9 * 2 + 3 * 2) * WG_BOX;  // what the TMA writes per chunk
+constexpr int WG_STAGE = WG_A_BYTES + WG_B_BYTES;    // 38 KB
+constexpr int WG_NSTAGE = 4;
 constexpr int WG_THREADS = 192;
 // kind::f16, D F32, A and B BF16, both MN-major (transpose bits 15, 16),
-// N = 16, M = 128
-constexpr unsigned IDESC_WG = IDESC | (1u << 15) | (1u << 16);
+// N = 48, M = 128
+constexpr unsigned IDESC_WG = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                              ((48u >> 3) << 17) | ((128u >> 4) << 24);
 
 struct WgradArgs {
     float* dW;        // [27][ci][co], accumulated into
@@ -424,12 +443,12 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     const int ncx = a.nx / WG_PTS;
     const long long nchunks = (long long)ncx * a.ny * a.nz;
 
-    // the ones slots (27..31, both halves) of every stage; the TMA never
-    // writes there
+    // the ones slots (9..15 of M-tile 1, both halves) of every stage; the
+    // TMA never writes there
     for (int st = 0; st < WG_NSTAGE; ++st) {
-        uint4* o = reinterpret_cast<uint4*>(smem + st * WG_STAGE + 27 * 2 * WG_BOX);
+        uint4* o = reinterpret_cast<uint4*>(smem + st * WG_STAGE + (16 + 2 * 1) * WG_BOX);
         const unsigned one2 = 0x3F803F80u;  // two BF16 ones
-        for (int i = tid; i < 5 * 2 * WG_BOX / 16; i += WG_THREADS) o[i] = make_uint4(one2, one2, one2, one2);
+        for (int i = tid; i < 7 * 2 * WG_BOX / 16; i += WG_THREADS) o[i] = make_uint4(one2, one2, one2, one2);
     }
     if (tid == 0) {
         for (int s = 0; s < WG_NSTAGE; ++s) {
@@ -442,7 +461,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_s)),
-                     "r"(64)
+                     "r"(128)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -468,13 +487,15 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
                 const int y = (int)((q / ncx) % a.ny), z = (int)(q / ((long long)ncx * a.ny));
                 unsigned char* st = smem + s * WG_STAGE;
                 mbar_expect_tx(&full[s], WG_LOAD_BYTES);
-                for (int t = 0; t < 27; ++t) {
-                    const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-                    tma_load_4d(st + (2 * t) * WG_BOX, &mx0, 0, x0 + dx, y + dy, z + dz, &full[s]);
-                    tma_load_4d(st + (2 * t + 1) * WG_BOX, &mx1, 0, x0 + dx, y + dy, z + dz, &full[s]);
+                for (int pr = 0; pr < 9; ++pr) {  // pair (dy, dz) = (pr % 3 - 1, pr / 3 - 1)
+                    const int dy = pr % 3 - 1, dz = pr / 3 - 1;
+                    tma_load_4d(st + (2 * pr) * WG_BOX, &mx0, 0, x0, y + dy, z + dz, &full[s]);
+                    tma_load_4d(st + (2 * pr + 1) * WG_BOX, &mx1, 0, x0, y + dy, z + dz, &full[s]);
                 }
-                tma_load_4d(st + WG_A_BYTES, &mg0, 0, x0, y, z, &full[s]);
-                tma_load_4d(st + WG_A_BYTES + WG_BOX, &mg1, 0, x0, y, z, &full[s]);
+                for (int g = 0; g < 3; ++g) {  // dx = g - 1: dy at q - (dx, 0, 0)
+                    tma_load_4d(st + WG_A_BYTES + (2 * g) * WG_BOX, &mg0, 0, x0 - (g - 1), y, z, &full[s]);
+                    tma_load_4d(st + WG_A_BYTES + (2 * g + 1) * WG_BOX, &mg1, 0, x0 - (g - 1), y, z, &full[s]);
+                }
                 issued = i + 1;
             }
         }
@@ -490,17 +511,17 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
                 }
                 fence_after();
                 const unsigned st = base + s * WG_STAGE;
+                const unsigned long long db = smem_desc(st + WG_A_BYTES, 128, WG_BOX);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 2; ++j) {
                     const unsigned long long da = smem_desc(st + j * 16 * WG_BOX, 128, WG_BOX);
-                    const unsigned long long db = smem_desc(st + WG_A_BYTES, 128, WG_BOX);
 #pragma unroll
                     for (int k = 0; k < WG_PTS / 16; ++k) {
                         // K step k = points 16k .. 16k+15 = two 8-point groups (256 B)
                         const unsigned acc = (i > 0 || k > 0) ? 1u : 0u;
                         asm volatile(
                             "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
-                            "  tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem + 16 * j),
+                            "  tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem + 48 * j),
                             "l"(da + (unsigned long long)(k * 16)), "l"(db + (unsigned long long)(k * 16)),
                             "r"(IDESC_WG), "r"(acc)
                             : "memory");
@@ -516,22 +537,31 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
         const int q = warp & 3;
         const bool any = (long long)blockIdx.x < nchunks;
         if (any) {
-            if (!mbar_wait(&acc_full, 0)) {
+            // the lanes agree before the warp-collective TMEM loads
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full, 0) ? 1 : 0);
+            if (!ok) {
                 if (lane == 0) atomicOr(a.status, ST_TIMEOUT);
                 abort_s = 1;
-            } else if (!abort_s) {
+            } else if (__all_sync(0xffffffffu, abort_s ? 0 : 1)) {
                 fence_after();
                 const int r = 32 * q + lane;
                 const int c = r & 15;
-                for (int j = 0; j < 4; ++j) {
-                    float v[16];
-                    tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + 16 * j, v);
-                    const int slot = 8 * j + (r >> 4);
-                    if (slot < 27 && c < a.ci) {
-                        float* w = a.dW + ((size_t)slot * a.ci + c) * a.co;
-                        for (int o = 0; o < a.co; ++o) atomicAdd(&w[o], v[o]);
-                    } else if (slot == 27 && c == 0 && a.db) {
-                        for (int o = 0; o < a.co; ++o) atomicAdd(&a.db[o], v[o]);
+                for (int j = 0; j < 2; ++j) {
+                    const int slot = 8 * j + (r >> 4);  // 0..8 pairs, 9 ones
+                    const bool use = (slot < 9 && c < a.ci) || (slot == 9 && c == 0 && a.db);
+                    for (int g = 0; g < 3; ++g) {
+                        // tcgen05.ld is warp-collective: every lane loads, then
+                        // only the lanes with a gradient entry add it
+                        float v[16];
+                        tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + 48 * j + 16 * g, v);
+                        if (!use) continue;
+                        if (slot < 9) {
+                            const int t = 3 * slot + g;  // (dz+1) 9 + (dy+1) 3 + (dx+1)
+                            float* w = a.dW + ((size_t)t * a.ci + c) * a.co;
+                            for (int o = 0; o < a.co; ++o) atomicAdd(&w[o], v[o]);
+                        } else if (g == 1) {
+                            for (int o = 0; o < a.co; ++o) atomicAdd(&a.db[o], v[o]);
+                        }
                     }
                 }
             }
@@ -548,7 +578,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     __syncthreads();
     fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128)
                      : "memory");
 }
 
