@@ -265,6 +265,8 @@ cudaError_t launch_conv3(const CUtensorMap* maps, const void* wpack, const float
                          const int* bcount = nullptr);
 cudaError_t launch_features(const float* phi, const float* phit, const float* F, float Fc,
                             float inv_h, long long n, void* X, cudaStream_t s);
+cudaError_t launch_features_bricked(const float* phi, const float* phit, const float* F,
+                                   const Inst& in, void* X, cudaStream_t s);
 cudaError_t launch_count_mask(const float* phi, double gamma, long long n, int* count, cudaStream_t s);
 cudaError_t launch_loss_grad(const float* z, const float* phi, const float* phit,
                              const float* phiref, float inv_h, double gamma, const int* count,

@@ -44,6 +44,38 @@ __global__ void k_features(const float* __restrict__ phi, const float* __restric
     }
 }
 
+// the same features from the bricked (tile-major) phi^n, phi~ and F of a
+// single grid, written row-major: one thread per point in bricked order
+// (reads contiguous; writes 8 points = 256 B contiguous per x-run)
+__global__ void k_features_bricked(const float* __restrict__ phi, const float* __restrict__ phit,
+                                   const float* __restrict__ F, Inst in, __nv_bfloat16* __restrict__ X)
+{
+    const long long n = in.ntiles * TILE_PTS;
+    const float inv_h = (float)in.inv_h, Fc = (float)in.Fc;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long t = e / TILE_PTS;
+        const int r = (int)(e - t * TILE_PTS);
+        const int lx = r & 7, ly = (r >> 3) & 7, lz = r >> 6;
+        const int tpl = in.tnx * in.tny;
+        const int tz = (int)(t / tpl), rem = (int)(t - (long long)tz * tpl);
+        const int ty = rem / in.tnx, tx = rem - ty * in.tnx;
+        const size_t p = rm_index(tx * 8 + lx, ty * 8 + ly, tz * 8 + lz, in.nx, in.ny);
+        const float a = phi[e];
+        const float f = F ? F[e] : Fc;
+        const float c0 = fminf(fmaxf(a * inv_h, -8.f), 8.f);
+        const float c2 = (phit[e] - a) * inv_h;
+        uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(o);
+        ob[0] = __float2bfloat16_rn(c0);
+        ob[1] = __float2bfloat16_rn(f);
+        ob[2] = __float2bfloat16_rn(c2);
+        uint4* d = reinterpret_cast<uint4*>(X + p * 16);
+        d[0] = o[0];
+        d[1] = o[1];
+    }
+}
+
 // loss = sum over masked points of (z - t)^2 / count;  dz = 2 (z - t) / count
 // on masked points (channel 0 of a 16-channel BF16 gradient), 0 elsewhere.
 // mask: |phi^n| < gamma (the tube of Eq. 6), compared in FP64 like the band's
@@ -215,6 +247,14 @@ cudaError_t launch_features(const float* phi, const float* phit, const float* F,
                             float inv_h, long long n, void* X, cudaStream_t s)
 {
     k_features<<<grid_for(n, 256), 256, 0, s>>>(phi, phit, F, Fc, inv_h, n, (__nv_bfloat16*)X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features_bricked(const float* phi, const float* phit, const float* F,
+                                   const Inst& in, void* X, cudaStream_t s)
+{
+    k_features_bricked<<<grid_for(in.ntiles * TILE_PTS, 256), 256, 0, s>>>(phi, phit, F, in,
+                                                                          (__nv_bfloat16*)X);
     return cudaGetLastError();
 }
 

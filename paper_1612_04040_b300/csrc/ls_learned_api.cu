@@ -66,6 +66,7 @@ struct Learned {
     CUtensorMap map_X0[2], map_A[NL - 1][2], map_G[NL][2];
     std::vector<Pair> pairs;
     bool initialised = false;
+    bool fwd_packed = false;      // wpack_fwd holds the current parameters
 };
 
 void learned_free(Learned* L)
@@ -164,6 +165,9 @@ int ensure_learned(ls_ctx* c, Learned** out)
 
 int pack_all(ls_ctx* c, Learned* L, bool bwd, cudaStream_t s)
 {
+    // inference packs once per parameter change; training every iteration
+    if (!bwd && L->fwd_packed) return LS_OK;
+    L->fwd_packed = !bwd;
     for (int l = 0; l < lsk::NL; ++l) {
         LCK(lsk::launch_pack_weights(L->params + lsk::w_off(l), lsk::CI[l], lsk::CO[l], 0,
                                      L->wpack_fwd[l], s));
@@ -202,16 +206,10 @@ int ls_engine_learned_after_step(ls_ctx* c, cudaStream_t s)
     const Inst& in = c->in0();
     void* src = c->phi[c->cur];
     void* dst = c->phi[c->cur ^ 1];
-    LCK(lsk::launch_unpack(src, L->rm_phi, in, 0, s));
-    LCK(lsk::launch_unpack(dst, L->rm_phit, in, 0, s));
-    const float* F = nullptr;
-    if (in.speed_mode == 2) {
-        LCK(lsk::launch_unpack(c->F, L->rm_F, in, 0, s));
-        F = L->rm_F;
-        ++c->launches;
-    }
-    LCK(lsk::launch_features(L->rm_phi, L->rm_phit, F, (float)in.Fc, (float)in.inv_h, L->npts, L->X0, s));
-    c->launches += 3;
+    // features straight from the bricked phi^n, phi~ and F
+    LCK(lsk::launch_features_bricked((const float*)src, (const float*)dst,
+                                     in.speed_mode == 2 ? (const float*)c->F : nullptr, in, L->X0, s));
+    c->launches += 1;
     int r = pack_all(c, L, false, s);
     if (r) return r;
     LCK(lsk::launch_block_list(c->act, in, L->d_blist, L->d_bcount, s));
@@ -254,6 +252,7 @@ int ls_learned_init(ls_ctx* c, unsigned long long seed)
     LCK(cudaMemset(L->adam_v, 0, p.size() * 4));
     L->adam_step = 0;
     L->initialised = true;
+    L->fwd_packed = false;
     c->graphs.clear();
     return LS_OK;
 }
@@ -273,6 +272,7 @@ int ls_learned_set_params(ls_ctx* c, const float* src, long long n)
     if (r) return r;
     LCK(cudaMemcpy(L->params, src, (size_t)n * 4, cudaMemcpyHostToDevice));
     L->initialised = true;
+    L->fwd_packed = false;
     return LS_OK;
 }
 
@@ -377,6 +377,7 @@ int ls_learned_train_stored(ls_ctx* c, int iters, double lr, double dt, double h
         }
     }
     c->full_domain = fd;
+    L->fwd_packed = false;
     c->band_valid = false;
     c->core_fresh = false;
     c->inst_phi_set[0] = 0;  // phi holds a training sample now
@@ -401,6 +402,7 @@ int ls_learned_load(ls_ctx* c, const void* bf16_weights, size_t bytes)
     LCK(cudaMemset(L->adam_v, 0, p.size() * 4));
     L->adam_step = 0;
     L->initialised = true;
+    L->fwd_packed = false;
     c->graphs.clear();
     return LS_OK;
 }
