@@ -93,7 +93,7 @@ def parse():
     p.add_argument("--slabs", type=int, default=1,
                    help="--parallelism slab on one GPU: number of slabs in this process (device "
                         "copies instead of NCCL)")
-    p.add_argument("--rebalance-gain", type=float, default=0.05,
+    p.add_argument("--rebalance-gain", type=float, default=0.1,
                    help="--parallelism slab: move rows to the Eq. 14 partition after a rebuild only "
                         "when that lowers the largest slab's active tiles by more than this fraction")
     p.add_argument("--step-config", default=None, metavar="STAGES,GRID_PCT,PPT",
@@ -680,11 +680,13 @@ def run_sphere64(args):
 def run_slab(args):
     """The standard 512^3 run split into z-slabs (section 2 of the paper):
     one slab per rank (NCCL exchanges) or --slabs slabs on one GPU (device
-    copies), rows shared out by Eq. 14 after every band rebuild.  One bench
-    step = one whole 500-step run from phi^0 (slab contexts set up before the
-    timed region, the initial rebuilds and partition inside it); value = all
-    slabs' updates (active tiles x 512 per step, counted at each rebuild) /
-    max time over ranks.  The total work is fixed as N grows
+    copies), rows shared out by Eq. 14 (checked every 10 rebuild periods).
+    The common dt is made on the device from the max-reduced bounds, and
+    with every slab in this process two rebuild periods at a time run from
+    one CUDA graph.  One bench step = one whole 500-step run from phi^0
+    (slab contexts, the initial rebuild and partition set up before the
+    timed region); value = all slabs' updates (the library's device
+    counters) / max time over ranks.  The total work is fixed as N grows
     (one grid): scaling "strong"."""
     import torch
     from paper_1612_04040_b300 import inputs
@@ -703,16 +705,24 @@ def run_slab(args):
     F0 = torch.empty_like(phi0)
     g.get_phi(phi0)
     g.get_speed(F0)
+    # the stencil launch configuration the autotuner picks on the unsplit
+    # grid (a band from the middle of the run), used by every slab
+    g.band_rebuild(w.halfwidth, want_count=False)
+    g.step(w.steps // 2, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+    tuned = tune(g, args)
     g.close()
     comm = slab.DistComm(pg, dev) if world > 1 else slab.LocalComm(max(args.slabs, 1))
+    # a stream of its own: the rebuild periods are captured in CUDA graphs on it
+    run_stream = torch.cuda.Stream()
 
     def make(nx, ny, rows, h, lo, hi):
-        return slab.GpuSlab(nx, ny, rows, h, lo, hi, ls.LS_FP32, stream.cuda_stream)
+        return slab.GpuSlab(nx, ny, rows, h, lo, hi, ls.LS_FP32, run_stream.cuda_stream, tuned)
 
     def new_run():
-        return slab.SlabRun(comm, make, (w.n,) * 3, w.h, w.halfwidth,
-                            lambda z0, z1: (phi0[z0:z1], F0[z0:z1]), rebalance=True,
-                            rebalance_gain=args.rebalance_gain)
+        return slab.DeviceSlabRun(comm, make, (w.n,) * 3, w.h, w.halfwidth,
+                                  lambda z0, z1: (phi0[z0:z1], F0[z0:z1]), rebalance=True,
+                                  rebalance_gain=args.rebalance_gain, rebalance_every=10,
+                                  graphs=True, stream=run_stream)
 
     for _ in range(max(args.warmup, 0)):
         r = new_run()
@@ -722,18 +732,20 @@ def run_slab(args):
     total_ms, updates, migrations, bounds = 0.0, 0, 0, None
     for _ in range(args.steps):
         r = new_run()
+        r.prepare(w.cfl, w.rebuild_every)   # the graph of the first two periods, recorded untimed
+        u0 = r.updates_done
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e0.record(run_stream)
         r.step(w.steps, w.cfl, w.rebuild_every)
-        e1.record(stream)
+        e1.record(run_stream)
         torch.cuda.synchronize()
         if pg:
             pg.barrier()
         total_ms += e0.elapsed_time(e1)
-        updates += r.updates
+        updates += r.updates_done - u0
         migrations += r.migrations
         bounds = list(r.bounds)
         r.close()
@@ -745,6 +757,8 @@ def run_slab(args):
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded)",
             "config": {"workload": WORKLOAD, "grid": args.grid, "parallelism": "slab",
+                       "stencil_config": {"stages": tuned[0], "grid_pct": tuned[1],
+                                          "points_per_thread": tuned[2]},
                        "slabs": comm.nparts, "transport": "nccl" if world > 1 else "device copies",
                        "final_bounds_tile_rows": bounds, "migrations_per_run": migrations / max(args.steps, 1),
                        "l2": "inputs larger than L2 (phi + F 1.5 GB)"},

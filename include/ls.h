@@ -61,7 +61,7 @@ typedef enum {
 } ls_status;
 
 enum { LS_FP32 = 0, LS_FP64 = 1 };               /* storage + arithmetic precision */
-enum { LS_DT_FIXED = 0, LS_DT_CFL = 1 };         /* meaning of dt_or_cfl           */
+enum { LS_DT_FIXED = 0, LS_DT_CFL = 1, LS_DT_KEEP = 2 };  /* meaning of dt_or_cfl  */
 enum { LS_PLAIN = 0, LS_LEARNED = 1 };           /* step flavour                   */
 enum { LS_SCHEME_PLAIN = 0, LS_SCHEME_LOCAL = 1 }; /* advance scheme (ls_set_scheme) */
 enum { LS_BC_EXTRAPOLATE = 0, LS_BC_NEUMANN = 1 };
@@ -155,9 +155,17 @@ int ls_band_rebuild(ls_ctx *ctx, double halfwidth_in_h, long long *n_active_tile
  * ls_set_phi / ls_set_speed*) is rebuilt from the whole grid before the first
  * step.  If last_dt is not NULL the stream is synchronised and the dt of the
  * last step written there.
+ * LS_DT_KEEP (single grid, band, plain steps): the dt already on the
+ * device (from the last rebuild, or from ls_set_dt_from_bound) is used and
+ * dt_or_cfl is ignored; the caller makes every rebuild (ls_band_refresh),
+ * so a call in which one would fall due returns LS_ESTATE; the tube test is
+ * still fused into the step before it.  Calls in this mode do not
+ * synchronise (unless last_dt is given), so a sequence of them can be
+ * captured in a CUDA graph by the caller.
  * Errors: LS_EINVAL (nsteps < 0, rebuild_every < 0, dt_or_cfl <= 0 or not
  * finite, bad dt_mode), LS_ESTATE (phi or speed not set; no halfwidth given
- * yet and not in full-domain mode), LS_ECUDA. */
+ * yet and not in full-domain mode; LS_DT_KEEP outside its conditions),
+ * LS_ECUDA. */
 int ls_step(ls_ctx *ctx, int nsteps, double dt_or_cfl, int dt_mode,
             int rebuild_every, double *last_dt);
 
@@ -230,6 +238,17 @@ int ls_set_ghost_rows(ls_ctx *ctx, int lo, int hi);
  * halfwidth not set, full-domain mode). */
 int ls_band_refresh(ls_ctx *ctx, double *M, long long *n_active);
 
+/* With M and n_active both NULL, ls_band_refresh does not synchronise (it
+ * can then be captured in a CUDA graph).  The bound M of the current band:
+ * ls_band_speed_bound copies it to dst (device: asynchronous on the
+ * context's stream; host: synchronises); ls_set_dt_from_bound sets, on the
+ * device, M := *M_device and dt = cfl h / M (cfl h when M = 0) in FP64 with
+ * the rebuild's expression, for the steps that follow in LS_DT_KEEP mode
+ * (the slab split's common dt from an all-reduced M).  Errors: LS_EINVAL
+ * (NULL, batch context, cfl not finite and positive), LS_ESTATE (no band). */
+int ls_band_speed_bound(ls_ctx *ctx, double *dst, int dst_on_device);
+int ls_set_dt_from_bound(ls_ctx *ctx, const double *M_device, double cfl);
+
 /* Active tiles per tile row z (counts[tz], nrows = nz / 8) of the current
  * band: the row weights of Eq. 14.  Synchronises.  Errors: LS_EINVAL,
  * LS_ESTATE (no band). */
@@ -247,6 +266,14 @@ int ls_band_row_counts(ls_ctx *ctx, long long *counts, int nrows);
 int ls_get_tile_rows(ls_ctx *ctx, int row0, int nrows, int plane, void *dst, int dst_on_device);
 int ls_set_tile_rows(ls_ctx *ctx, int row0, int nrows, int plane, const void *src,
                      int src_on_device);
+
+/* Copy tile row src_row of the context src (its current phi) straight into
+ * ghost row `row` of ctx (plane as above): slabs of one grid held on the
+ * same device in one process.  Asynchronous on ctx's stream; the caller
+ * orders it after src's work (one stream for both, or an event).  Errors:
+ * LS_EINVAL (batch context, precision or tile rows differ, range, not a
+ * ghost row of ctx), LS_ESTATE (phi not set). */
+int ls_copy_ghost_row(const ls_ctx *src, int src_row, ls_ctx *ctx, int row, int plane);
 
 /* Full-domain mode, FP32 single grids, plain scheme: on, every step streams
  * tile columns along z (each tile's z halos are the neighbouring tiles of

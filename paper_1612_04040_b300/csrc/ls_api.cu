@@ -447,7 +447,7 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
             RET(rebuild(c, false, s));
             rebuilt = true;
         }
-        if (dt_pending && !rebuilt) {
+        if (dt_pending && !rebuilt && dt_mode != LS_DT_KEEP) {
             if (c->batched)
                 KL(c, lsk::launch_set_dt_batch(c->d_sc, c->n_inst, c->d_inst, dt_mode, value, 0,
                                                c->prec, c->d_Mbits, c->d_inst_count, s));
@@ -978,6 +978,7 @@ int ls_band_refresh(ls_ctx* c, double* M, long long* n_active)
     // the rebuild ls_step would make now: from the tube test fused into the
     // last step when that step made one, else from a scan of every tile
     RET(rebuild(c, !c->band_valid, c->stream));
+    if (!M && !n_active) return LS_OK;  // nothing to read back: no synchronisation
     lsk::StepScalars sc;
     int n = 0;
     CK(cudaMemcpyAsync(&sc, c->d_sc, sizeof(sc), cudaMemcpyDeviceToHost, c->stream));
@@ -985,6 +986,29 @@ int ls_band_refresh(ls_ctx* c, double* M, long long* n_active)
     CK(cudaStreamSynchronize(c->stream));
     if (M) *M = sc.M;
     if (n_active) *n_active = n;
+    return LS_OK;
+}
+
+int ls_band_speed_bound(ls_ctx* c, double* dst, int on_device)
+{
+    if (!c || c->batched || !dst) return LS_EINVAL;
+    if (!c->band_valid) return LS_ESTATE;
+    // StepScalars::M is the first member
+    const double* M = &c->d_sc[0].M;
+    if (on_device) {
+        CK(cudaMemcpyAsync(dst, M, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        CK(cudaMemcpyAsync(dst, M, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return LS_OK;
+}
+
+int ls_set_dt_from_bound(ls_ctx* c, const double* M_device, double cfl)
+{
+    if (!c || c->batched || !M_device || !(cfl > 0.0) || !std::isfinite(cfl)) return LS_EINVAL;
+    if (!c->band_valid) return LS_ESTATE;
+    KL(c, lsk::launch_set_dt_from(c->d_sc, M_device, c->in0(), cfl, c->prec, c->stream));
     return LS_OK;
 }
 
@@ -1021,6 +1045,13 @@ static int tile_rows_copy(ls_ctx* c, int row0, int nrows, int plane, void* buf, 
         const size_t bytes = (size_t)nrows * tpl * lsk::TILE_PTS * es;
         if (to_ctx) CK(cudaMemcpyAsync(base, buf, bytes, kind, c->stream));
         else CK(cudaMemcpyAsync(buf, base, bytes, kind, c->stream));
+    } else if (on_device) {
+        // one z-plane (64 values) per tile: a copy kernel (a strided
+        // device-to-device cudaMemcpy2D of 256-byte rows is several times slower)
+        const long long words = 64 * (long long)es / 4, pitch = lsk::TILE_PTS * (long long)es / 4;
+        char* p = base + (size_t)plane * 64 * es;
+        if (to_ctx) KL(c, lsk::launch_chunk_copy(buf, words, p, pitch, (int)words, (long long)nrows * tpl, c->stream));
+        else KL(c, lsk::launch_chunk_copy(p, pitch, buf, words, (int)words, (long long)nrows * tpl, c->stream));
     } else {
         const size_t w = 64 * es, pitch = lsk::TILE_PTS * es, rows = (size_t)nrows * tpl;
         char* p = base + (size_t)plane * w;
@@ -1040,6 +1071,31 @@ int ls_get_tile_rows(ls_ctx* c, int row0, int nrows, int plane, void* dst, int o
     return tile_rows_copy(c, row0, nrows, plane, dst, on_device, false);
 }
 
+int ls_copy_ghost_row(const ls_ctx* src, int src_row, ls_ctx* c, int row, int plane)
+{
+    if (!src || !c || src->batched || c->batched || plane < -1 || plane > 7) return LS_EINVAL;
+    const Inst& si = src->insts[0];
+    const Inst& in = c->in0();
+    if (src->prec != c->prec || si.tnx != in.tnx || si.tny != in.tny) return LS_EINVAL;
+    if (src_row < 0 || src_row >= si.tnz) return LS_EINVAL;
+    const bool lo = (in.ghost & 1) && row == 0;
+    const bool hi = (in.ghost & 2) && row == in.tnz - 1;
+    if (!lo && !hi) return LS_EINVAL;  // only a ghost row takes a neighbour's values
+    if (!src->inst_phi_set[0] || !all_phi_set(c)) return LS_ESTATE;
+    clear_graphs(c);
+    const size_t tpl = (size_t)in.tnx * in.tny, es = c->esize;
+    const char* sb = (const char*)src->phi[src->cur] + (size_t)src_row * tpl * lsk::TILE_PTS * es;
+    char* db = (char*)c->phi[c->cur] + (size_t)row * tpl * lsk::TILE_PTS * es;
+    if (plane < 0) {
+        CK(cudaMemcpyAsync(db, sb, tpl * lsk::TILE_PTS * es, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        const long long words = 64 * (long long)es / 4, pitch = lsk::TILE_PTS * (long long)es / 4;
+        KL(c, lsk::launch_chunk_copy(sb + (size_t)plane * 64 * es, pitch, db + (size_t)plane * 64 * es,
+                                     pitch, (int)words, (long long)tpl, c->stream));
+    }
+    return LS_OK;
+}
+
 int ls_set_tile_rows(ls_ctx* c, int row0, int nrows, int plane, const void* src, int on_device)
 {
     if (!c || c->batched || !src || plane < -1 || plane > 7 || nrows != 1) return LS_EINVAL;
@@ -1056,14 +1112,22 @@ int ls_step(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every,
 {
     if (!c) return LS_EINVAL;
     if (nsteps < 0 || rebuild_every < 0) return LS_EINVAL;
-    if (dt_mode != LS_DT_FIXED && dt_mode != LS_DT_CFL) return LS_EINVAL;
-    if (!(value > 0.0) || !std::isfinite(value)) return LS_EINVAL;
+    if (dt_mode != LS_DT_FIXED && dt_mode != LS_DT_CFL && dt_mode != LS_DT_KEEP) return LS_EINVAL;
+    if (dt_mode != LS_DT_KEEP && (!(value > 0.0) || !std::isfinite(value))) return LS_EINVAL;
     if (!all_phi_set(c) || speed_mode(c) == 0) return LS_ESTATE;
     if (!c->full_domain && !c->have_halfwidth) return LS_ESTATE;
     if (c->scheme == LS_SCHEME_LOCAL && (!c->have_halfwidth || !(c->beta_in_h < c->halfwidth)))
         return LS_ESTATE;
-    c->dt_mode = dt_mode;
-    c->dt_value = value;
+    if (dt_mode == LS_DT_KEEP) {
+        // the dt on the device stays; every rebuild is the caller's
+        // (ls_band_refresh), so none may fall due inside this call
+        if (c->batched || c->full_domain || !c->band_valid || c->step_mode != LS_PLAIN)
+            return LS_ESTATE;
+        if (rebuild_every > 0 && c->since_rebuild + nsteps > rebuild_every) return LS_ESTATE;
+    } else {
+        c->dt_mode = dt_mode;
+        c->dt_value = value;
+    }
     NvtxRange range("ls_step");
     if (nsteps > 0) {
         if (c->use_graphs && !c->profiling && !c->output)

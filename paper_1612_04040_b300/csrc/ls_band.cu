@@ -817,6 +817,49 @@ __global__ void k_row_counts(const int* __restrict__ list, const int* __restrict
     }
 }
 
+// dt from an external bound: M = *Mext (e.g. the maximum over the slabs of
+// a split grid), dt = cfl h / M (cfl h when M = 0), as at a rebuild
+__global__ void k_set_dt_from(StepScalars* sc, const double* Mext, Inst single, double cfl, int prec)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    sc[0].M = *Mext;
+    set_dt_one(sc, 0, single, 1, cfl, 0, prec, nullptr, 0);
+}
+
+cudaError_t launch_set_dt_from(StepScalars* sc, const double* Mext, const Inst& in, double cfl,
+                               int prec, cudaStream_t s)
+{
+    k_set_dt_from<<<1, 32, 0, s>>>(sc, Mext, in, cfl, prec);
+    return cudaGetLastError();
+}
+
+// chunk copy: chunk t of `words` 32-bit words from src + t * src_stride to
+// dst + t * dst_stride (a z-plane of each tile of a tile row, between the
+// bricked layout and a packed buffer or another context's ghost row)
+__global__ void k_chunk_copy(const uint32_t* __restrict__ src, long long src_stride,
+                             uint32_t* __restrict__ dst, long long dst_stride, int words,
+                             long long nchunks)
+{
+    const long long n = nchunks * words;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long t = i / words;
+        const int j = (int)(i - t * words);
+        dst[t * dst_stride + j] = src[t * src_stride + j];
+    }
+}
+
+cudaError_t launch_chunk_copy(const void* src, long long src_stride_words, void* dst,
+                              long long dst_stride_words, int words, long long nchunks, cudaStream_t s)
+{
+    const long long n = nchunks * words;
+    long long g = (n + 255) / 256;
+    if (g > 148 * 8) g = 148 * 8;
+    k_chunk_copy<<<(int)(g > 0 ? g : 1), 256, 0, s>>>((const uint32_t*)src, src_stride_words,
+                                                       (uint32_t*)dst, dst_stride_words, words, nchunks);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_row_counts(const int* list, const int* count, int tiles_per_row, int* rows,
                               int capacity, cudaStream_t s)
 {

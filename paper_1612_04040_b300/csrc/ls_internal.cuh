@@ -91,6 +91,13 @@ cudaError_t launch_classify_all(const void* phi, uint8_t* core, const Inst* d_in
 // 0 = new flag, bit 1 = previous) + block counts, turned into exclusive
 // offsets and the active count *count by the last block to finish (done: a
 // zeroed device counter, reset by that block)
+// dst + t * dst_stride <- src + t * src_stride, `words` 32-bit words per
+// chunk, t < nchunks (strides in words)
+cudaError_t launch_chunk_copy(const void* src, long long src_stride_words, void* dst,
+                              long long dst_stride_words, int words, long long nchunks, cudaStream_t s);
+// sc[0].M = *Mext, then dt = cfl h / M as at a rebuild (single grid)
+cudaError_t launch_set_dt_from(StepScalars* sc, const double* Mext, const Inst& in, double cfl,
+                               int prec, cudaStream_t s);
 // per tile row (tz) count of the active-list entries: rows[tz] += 1
 cudaError_t launch_row_counts(const int* list, const int* count, int tiles_per_row, int* rows,
                               int capacity, cudaStream_t s);

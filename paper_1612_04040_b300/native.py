@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(HERE, "libls.so")
 
 LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ETIMEOUT, LS_ENONFINITE, LS_ESTATE, LS_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 LS_FP32, LS_FP64 = 0, 1
-LS_DT_FIXED, LS_DT_CFL = 0, 1
+LS_DT_FIXED, LS_DT_CFL, LS_DT_KEEP = 0, 1, 2
 LS_PLAIN, LS_LEARNED = 0, 1
 LS_SCHEME_PLAIN, LS_SCHEME_LOCAL = 0, 1
 LS_OUTPUT_VTS, LS_OUTPUT_VTI = 0, 1
@@ -59,9 +59,12 @@ SIGNATURES = {
     "ls_get_speed": (_i, [_vp, _vp, _i]),
     "ls_set_ghost_rows": (_i, [_vp, _i, _i]),
     "ls_band_refresh": (_i, [_vp, _vp, _vp]),
+    "ls_band_speed_bound": (_i, [_vp, _vp, _i]),
+    "ls_set_dt_from_bound": (_i, [_vp, _vp, _d]),
     "ls_band_row_counts": (_i, [_vp, _vp, _i]),
     "ls_get_tile_rows": (_i, [_vp, _i, _i, _i, _vp, _i]),
     "ls_set_tile_rows": (_i, [_vp, _i, _i, _i, _vp, _i]),
+    "ls_copy_ghost_row": (_i, [_vp, _i, _vp, _i, _i]),
     "ls_stage_inputs": (_i, [_vp, _vp, _vp]),
     "ls_load_staged": (_i, [_vp]),
     "ls_get_phi_async": (_i, [_vp, _vp]),
@@ -472,6 +475,23 @@ class LevelSet:
         check(self.lib.ls_band_refresh(self.ctx, ctypes.byref(M), ctypes.byref(n)), "ls_band_refresh")
         return M.value, n.value
 
+    def band_refresh_async(self):
+        """The rebuild the next step would make, without synchronising."""
+        check(self.lib.ls_band_refresh(self.ctx, None, None), "ls_band_refresh")
+
+    def band_speed_bound(self, out):
+        """Copy M of the current band into `out` (float64 tensor / array, 1 value)."""
+        p, dev = array_ptr(out, np.float64, 1)
+        check(self.lib.ls_band_speed_bound(self.ctx, p, dev), "ls_band_speed_bound")
+        return out
+
+    def set_dt_from_bound(self, M_device, cfl):
+        """dt = cfl h / M with M read from a float64 CUDA tensor of 1 value."""
+        if not (M_device.is_cuda and M_device.dtype == torch.float64 and M_device.numel() >= 1):
+            raise ValueError("M_device must be a float64 CUDA tensor")
+        check(self.lib.ls_set_dt_from_bound(self.ctx, ctypes.c_void_p(M_device.data_ptr()), float(cfl)),
+              "ls_set_dt_from_bound")
+
     def band_row_counts(self):
         nz = self.shape[0] // 8
         out = np.zeros(nz, dtype=np.int64)
@@ -493,6 +513,11 @@ class LevelSet:
         p, dev = self._rows_ptr(src, nrows, plane)
         check(self.lib.ls_set_tile_rows(self.ctx, int(row0), int(nrows), int(plane), p, dev),
               "ls_set_tile_rows")
+
+    def copy_ghost_row(self, src, src_row, row, plane):
+        """Tile row src_row of the LevelSet `src` into this context's ghost row."""
+        check(self.lib.ls_copy_ghost_row(src.ctx, int(src_row), self.ctx, int(row), int(plane)),
+              "ls_copy_ghost_row")
 
     # stream-ordered host input/output (ls_stage_inputs ... ls_wait_host);
     # the arrays must be host (CPU) arrays, page-locked for the copies to

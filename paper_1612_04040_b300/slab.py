@@ -96,6 +96,12 @@ class LocalComm:
     def sum_arrays(self, arrays):
         return np.sum([np.asarray(a, dtype=np.int64) for a in arrays.values()], axis=0)
 
+    def max_device(self, tensors):
+        """Max of the parts' device scalars, as a device scalar (no host
+        synchronisation)."""
+        ts = list(tensors.values())
+        return ts[0] if len(ts) == 1 else torch.amax(torch.cat(ts), dim=0, keepdim=True)
+
     def transfer(self, moves):
         """moves: (src_part, dst_part, src_buffer, dst_buffer); src_buffer
         is read, dst_buffer written."""
@@ -118,6 +124,11 @@ class DistComm:
                          device=self.device)
         self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
         return float(t.item())
+
+    def max_device(self, tensors):
+        (t,) = tensors.values()
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return t
 
     def sum_arrays(self, arrays):
         a = np.sum([np.asarray(v, dtype=np.int64) for v in arrays.values()], axis=0)
@@ -148,11 +159,15 @@ class GpuSlab:
     """One slab of tile rows (plus ghost rows) in a library context on the
     current CUDA device, fed from row-major device tensors."""
 
-    def __init__(self, nx, ny, rows, h, lo, hi, precision=ls.LS_FP32, stream=None):
+    def __init__(self, nx, ny, rows, h, lo, hi, precision=ls.LS_FP32, stream=None, step_config=None):
+        """step_config: (stages, grid_pct, points_per_thread) of the stencil
+        launches, e.g. what ls_autotune picked on the unsplit grid."""
         self.nx, self.ny, self.rows, self.lo, self.hi = nx, ny, rows, int(lo), int(hi)
         self.h = float(h)
         self.dtype = torch.float32 if precision == ls.LS_FP32 else torch.float64
         self.ctx = ls.LevelSet(nx, ny, TILE * rows, h, precision, stream)
+        if step_config is not None:
+            self.ctx.set_step_config(*step_config)
         self.tiles_per_row = (nx // TILE) * (ny // TILE)
 
     def close(self):
@@ -253,9 +268,10 @@ class SlabRun:
         return source(TILE * first, TILE * (r1 + hi))
 
     def _build(self, fields):
-        for e in self.engines.values():
-            e.close()
-        self.engines = {}
+        """New engines for the parts in `fields` (the others keep theirs)."""
+        for p in fields:
+            if p in self.engines:
+                self.engines.pop(p).close()
         for p, (phi, F) in fields.items():
             r0, r1, lo, hi, _ = self._span(p)
             e = self.make_engine(self.nx, self.ny, r1 - r0 + lo + hi, self.h, lo, hi)
@@ -335,13 +351,19 @@ class SlabRun:
         every overlap of an old and a new range goes from its old to its new
         owner; ghost rows are filled by the next exchange."""
         old = self.bounds
+        # a part whose rows do not change keeps its engine (and its rows)
+        same = {q for q in range(self.comm.nparts) if old[q] == new[q] and old[q + 1] == new[q + 1]}
         held = {}
         for p, e in self.engines.items():
+            if p in same:
+                continue
             r0, r1, lo, hi, _ = self._span(p)
             held[p] = (e.phi()[TILE * lo:TILE * (lo + r1 - r0)], e.speed()[TILE * lo:TILE * (lo + r1 - r0)])
         # receive buffers of the new slabs (owned planes; ghosts zero for now)
         fresh = {}
         for q in self.comm.parts:
+            if q in same:
+                continue
             r0, r1, lo, hi, _ = self._span(q, new)
             proto = next(iter(self.engines.values()))
             fresh[q] = (proto.zeros(TILE * (r1 - r0 + lo + hi)), proto.zeros(TILE * (r1 - r0 + lo + hi)))
@@ -350,7 +372,7 @@ class SlabRun:
             for q in range(self.comm.nparts):
                 a = max(old[p], new[q])
                 b = min(old[p + 1], new[q + 1])
-                if a >= b:
+                if a >= b or p in same or q in same:
                     continue
                 if p not in held and q not in fresh:
                     continue
@@ -417,3 +439,152 @@ class SlabRun:
         for e in self.engines.values():
             e.close()
         self.engines = {}
+
+
+class DeviceSlabRun(SlabRun):
+    """The same schedule with the common dt made on the device: after each
+    rebuild the slabs' bounds M are max-reduced into a device scalar
+    (``comm.max_device``: a device max, or an NCCL all-reduce) and every
+    slab sets dt = CFL h / M from it (``ls_set_dt_from_bound``), and the
+    steps run with that dt (``LS_DT_KEEP``).  A rebuild period then waits
+    for nothing on the host, and with ``graphs`` (every part in this
+    process) two periods at a time (an even number of steps, so each
+    context's ping-pong and traversal state comes back to where it was) are
+    captured in one CUDA graph on ``stream`` and replayed.  The Eq. 14
+    re-partition needs the row counts on the host: it is checked every
+    ``rebalance_every`` periods.  Library slab engines (``GpuSlab``) only."""
+
+    def __init__(self, comm, make_engine, shape, h, halfwidth, source, rebalance=True,
+                 rebalance_gain=0.05, rebalance_every=4, graphs=False, stream=None):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.graphs = bool(graphs) and isinstance(comm, LocalComm)
+        self.rebalance_every = max(int(rebalance_every), 1)
+        self._bufs = {}
+        self._graph = None
+        self._graph_period = None
+        self._counted = 0
+        self.cfl = None
+        with torch.cuda.stream(self.stream):
+            super().__init__(comm, make_engine, shape, h, halfwidth, source, rebalance, rebalance_gain)
+            self.Mdev = {p: torch.zeros(1, dtype=torch.float64, device="cuda") for p in comm.parts}
+
+    # engines change on migration: keep their update counts, drop buffers
+    # and the captured graph
+    def _build(self, fields):
+        for p in fields:
+            if p in getattr(self, "engines", {}):
+                self._counted += self.engines[p].ctx.updates()
+        self._graph = None
+        super()._build(fields)
+
+    def _buffer(self, key, e, plane):
+        b = self._bufs.get(key)
+        if b is None:
+            b = e.buffer(plane)
+            self._bufs[key] = b
+        return b
+
+    def _exchange(self, plane_up, plane_down):
+        moves, keep = [], []
+        for p in range(self.comm.nparts - 1):
+            q = p + 1
+            for src, dst, plane in ((p, q, plane_up), (q, p, plane_down)):
+                s_in, d_in = src in self.engines, dst in self.engines
+                if not (s_in or d_in):
+                    continue
+                kind = "row" if plane < 0 else "plane"
+                sbuf = dbuf = None
+                if s_in and not d_in:
+                    e = self.engines[src]
+                    r0, r1, lo, hi, _ = self._span(src)
+                    row = lo + (r1 - r0 - 1) if dst > src else lo
+                    sbuf = self._buffer(("s", src, dst, kind), e, plane)
+                    e.export_row(row, plane, sbuf)
+                if d_in:
+                    e = self.engines[dst]
+                    r0, r1, lo, hi, _ = self._span(dst)
+                    row = 0 if src < dst else lo + (r1 - r0)
+                    if s_in:
+                        # both slabs here: straight from the neighbour's rows
+                        sr0, sr1, slo, _, _ = self._span(src)
+                        srow = slo + (sr1 - sr0 - 1) if dst > src else slo
+                        e.ctx.copy_ghost_row(self.engines[src].ctx, srow, row, plane)
+                        continue
+                    dbuf = self._buffer(("r", src, dst, kind), e, plane)
+                    keep.append((e, row, plane, dbuf))
+                moves.append((src, dst, sbuf, dbuf))
+        self.comm.transfer(moves)
+        for e, row, plane, dbuf in keep:
+            e.import_row(row, plane, dbuf)
+
+    def _rebuild_device(self):
+        self._exchange(-1, -1)
+        for p, e in self.engines.items():
+            e.ctx.band_refresh_async()
+            e.ctx.band_speed_bound(self.Mdev[p])
+        M = self.comm.max_device(self.Mdev)
+        for e in self.engines.values():
+            e.ctx.set_dt_from_bound(M, self.cfl)
+
+    def _period(self, rebuild_every):
+        self._rebuild_device()
+        for _ in range(rebuild_every):
+            self._exchange(TILE - 1, 0)
+            for e in self.engines.values():
+                e.ctx.step(1, 1.0, ls.LS_DT_KEEP, rebuild_every)
+
+    def _check_balance(self):
+        """Eq. 14 on the current band (host: row counts); rows move when
+        that lowers the largest part by more than rebalance_gain."""
+        if not self.rebalance or self.comm.nparts == 1:
+            return
+        counts = self.row_counts()
+        new = partition_rows(counts, self.comm.nparts)
+        now, then = self._largest(counts, self.bounds), self._largest(counts, new)
+        if new != self.bounds and then < (1.0 - self.rebalance_gain) * now:
+            self._migrate(new)
+
+    def _capture(self, rebuild_every):
+        # recording does not run the work, and the contexts' host state
+        # moves on by the two periods recorded: the next replay brings the
+        # device to the same point
+        self._graph = torch.cuda.CUDAGraph()
+        self._graph_period = rebuild_every
+        with torch.cuda.graph(self._graph, stream=self.stream):
+            self._period(rebuild_every)
+            self._period(rebuild_every)
+
+    def prepare(self, cfl, rebuild_every):
+        """Record the graph of the next two periods now (set-up), so that
+        step() starts by replaying it."""
+        self.cfl = float(cfl)
+        if self.graphs and self._graph is None:
+            with torch.cuda.stream(self.stream):
+                self._capture(rebuild_every)
+
+    def step(self, nsteps, cfl, rebuild_every):
+        """nsteps (a multiple of rebuild_every) steps in whole rebuild periods."""
+        if nsteps % rebuild_every:
+            raise ValueError("nsteps must be a multiple of rebuild_every here")
+        if self._graph is not None and (self._graph_period != rebuild_every or self.cfl != float(cfl)):
+            raise ValueError("a graph is recorded for another period or CFL number")
+        self.cfl = float(cfl)
+        periods = nsteps // rebuild_every
+        done = 0
+        with torch.cuda.stream(self.stream):
+            while done < periods:
+                if done and done % self.rebalance_every == 0:
+                    self._check_balance()
+                if self.graphs and periods - done >= 2:
+                    if self._graph is None:
+                        self._capture(rebuild_every)
+                    self._graph.replay()
+                    done += 2
+                else:
+                    self._period(rebuild_every)
+                    done += 1
+        self.since_rebuild = rebuild_every
+
+    @property
+    def updates_done(self):
+        return self._counted + sum(e.ctx.updates() for e in self.engines.values())

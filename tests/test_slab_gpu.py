@@ -79,6 +79,45 @@ def test_split_equals_unsplit_bitwise(prec, nparts):
         assert moved >= 1, bounds
 
 
+def split_device(phi, F, prec, nparts, graphs):
+    dphi, dF = torch.from_numpy(phi).cuda(), torch.from_numpy(F).cuda()
+    stream = torch.cuda.Stream()
+
+    def make(nx, ny, rows, h, lo, hi):
+        return slab.GpuSlab(nx, ny, rows, h, lo, hi, prec, stream.cuda_stream)
+
+    run = slab.DeviceSlabRun(slab.LocalComm(nparts), make, SHAPE, H, HW,
+                             lambda z0, z1: (dphi[z0:z1], dF[z0:z1]), rebalance=True,
+                             rebalance_gain=0.0, rebalance_every=2, graphs=graphs, stream=stream)
+    first = run.migrations
+    run.step(NSTEPS, 0.5, 5)
+    torch.cuda.synchronize()
+    got = np.full_like(phi, np.nan)
+    for p, (z0, planes) in run.gather_phi().items():
+        got[z0:z0 + planes.shape[0]] = planes.cpu().numpy()
+    moved = run.migrations - first
+    updates = run.updates_done
+    run.close()
+    return got, moved, updates
+
+
+@pytest.mark.parametrize("graphs", [False, True], ids=["eager", "graphs"])
+@pytest.mark.parametrize("nparts", [1, 3])
+@pytest.mark.parametrize("prec", [ls.LS_FP32, ls.LS_FP64])
+def test_device_dt_split_equals_unsplit_bitwise(prec, nparts, graphs):
+    """The dt made on the device from the max-reduced bounds, the steps in
+    LS_DT_KEEP mode, two periods at a time replayed from a CUDA graph:
+    still the unsplit run bit for bit (rows migrating between slabs every
+    second period at most)."""
+    dt_np = np.float32 if prec == ls.LS_FP32 else np.float64
+    phi, F = fields(dt_np)
+    ref, _ = unsplit(phi, F, prec)
+    got, moved, updates = split_device(phi, F, prec, nparts, graphs)
+    view = np.int32 if prec == ls.LS_FP32 else np.int64
+    assert np.array_equal(got.view(view), ref.view(view))
+    assert updates > 0
+
+
 def test_split_fp64_equals_oracle_bitwise():
     phi, F = fields(np.float64)
     got, dt, _, _ = split(phi, F, ls.LS_FP64, 3)
