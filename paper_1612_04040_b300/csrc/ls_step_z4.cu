@@ -29,6 +29,16 @@ struct StageZ4 {
                      // [160,192): z-halo runs [16*(lz==7) + 2*ly + xh]
     float xo[128];   // x-halo value of each quad
     int4 meta;       // tile id, info byte, instance
+    float2 mf;       // batched: the instance's dt / h and constant speed
+};
+
+// a list entry with what its staging and its update need (batched: the
+// instance's tile-row strides, dt / h and speed), fetched two tiles ahead
+// so that the dependent loads behind it are off the critical path
+struct EntZ4 {
+    unsigned t, info, inst;
+    int tnx, tny;
+    float coef, Fc;
 };
 
 // the four quads of one thread, one class of tile (SGN, FACES as upd4)
@@ -123,16 +133,19 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     const unsigned a_y0 = sm0 + (unsigned)offsetof(Stage, v) + 16u * y_slot0;
     const unsigned a_z = sm0 + (unsigned)offsetof(Stage, v) + 16u * z_slot;
 
-    auto issue = [&](unsigned t, unsigned info, unsigned inst, int s) {
+    auto issue = [&](const EntZ4& e, int s) {
+        const unsigned t = e.t, info = e.info, inst = e.inst;
         const unsigned base = t * TILE_PTS;
         const float* tp = src + base;
         const unsigned so = (unsigned)s * SB;
-        if (tid == 0) st[s].meta = make_int4((int)t, (int)info, (int)inst, 0);
+        if (tid == 0) {
+            st[s].meta = make_int4((int)t, (int)info, (int)inst, 0);
+            if (BATCHED) st[s].mf = make_float2(e.coef, e.Fc);
+        }
         int y_off = y_off1, z_off = z_off1;
         if (BATCHED) {
-            const int tnx = a.insts[inst].tnx, tny = a.insts[inst].tny;
-            y_off = y_sgn * (tnx * TILE_PTS) + y_in;
-            z_off = z_sgn * (tnx * tny * TILE_PTS) + z_in;
+            y_off = y_sgn * (e.tnx * TILE_PTS) + y_in;
+            z_off = z_sgn * (e.tnx * e.tny * TILE_PTS) + z_in;
         }
         const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0;
         // inst: the entry's active face-neighbour and fill bits when xf is set
@@ -147,11 +160,17 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         }
         cp_async16s(a_z + so, tp + z_off, (info & z_bit) != 0);
     };
-    auto fetch = [&](int k, unsigned& t, unsigned& info, unsigned& inst) {
+    auto fetch = [&](int k, EntZ4& e) {
         k = ent(k);
-        t = (unsigned)__ldg(list + k);
-        info = __ldg(linfo + k);
-        inst = BATCHED ? (unsigned)__ldg(linst + k) : (xf ? (unsigned)__ldg(a.nact + k) : 0u);
+        e.t = (unsigned)__ldg(list + k);
+        e.info = __ldg(linfo + k);
+        e.inst = BATCHED ? (unsigned)__ldg(linst + k) : (xf ? (unsigned)__ldg(a.nact + k) : 0u);
+        if (BATCHED) {
+            e.tnx = a.insts[e.inst].tnx;
+            e.tny = a.insts[e.inst].tny;
+            e.coef = a.sc[e.inst].coef;
+            e.Fc = a.sc[e.inst].Fc;
+        }
     };
 
     // tile ids of the staged entries in the order they are computed, so
@@ -162,17 +181,17 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     for (int s = 0; s < S - 1; ++s) {
         tq[s] = 0u;
         if (kn < n) {
-            unsigned t, info, inst;
-            fetch(kn, t, info, inst);
-            issue(t, info, inst, s);
-            tq[s] = t;
+            EntZ4 e;
+            fetch(kn, e);
+            issue(e, s);
+            tq[s] = e.t;
         }
         cp_async_commit();
         kn += stride;
     }
-    unsigned t1 = 0, i1 = 0, n1 = 0, t2 = 0, i2 = 0, n2 = 0;
-    if (kn < n) fetch(kn, t1, i1, n1);
-    if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
+    EntZ4 e1 = {}, e2 = {};
+    if (kn < n) fetch(kn, e1);
+    if (kn + stride < n) fetch(kn + stride, e2);
     int cur = 0;
     for (int k = blockIdx.x; k < n; k += stride) {
         // this tile's speeds (each thread its own 16: nobody's neighbours),
@@ -187,23 +206,21 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         __syncthreads();
         {
             const int sn = cur == 0 ? S - 1 : cur - 1;
-            if (kn < n) issue(t1, i1, n1, sn);
+            if (kn < n) issue(e1, sn);
             cp_async_commit();
 #pragma unroll
             for (int i = 0; i + 1 < S - 1; ++i) tq[i] = tq[i + 1];
-            tq[S - 2] = t1;
+            tq[S - 2] = e1.t;
             kn += stride;
-            t1 = t2;
-            i1 = i2;
-            n1 = n2;
-            if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
+            e1 = e2;
+            if (kn + stride < n) fetch(kn + stride, e2);
         }
         const Stage& Sg = st[cur];
         const int t = Sg.meta.x;
         const unsigned info = (unsigned)Sg.meta.y;
         const int inst = Sg.meta.z;
-        const float coef = BATCHED ? a.sc[inst].coef : coef1;
-        const float Fc = BATCHED ? a.sc[inst].Fc : Fc1;
+        const float coef = BATCHED ? Sg.mf.x : coef1;
+        const float Fc = BATCHED ? Sg.mf.y : Fc1;
         float4 c[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[j] = Sg.v[q0 + 16 * j];
