@@ -154,6 +154,17 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def measured_bf16():
+    """Dense bf16 tensor-core peak (TFLOP/s): the measured burst figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured (cuBLAS bf16 burst)"
+    return 1800.0, "fallback"
+
+
 PROFILE_EVERY = 5  # plain scheme: one run of stencil launches in 5 timed with CUDA events
 
 
@@ -558,6 +569,39 @@ def run_learned(args):
         plain_ms = res["plain_512_ms"] if match == 512 else res["plain_%d" % match]["ms"]
         cmp.append({"plain_resolution_at_equal_error": match,
                     "speedup_learned_vs_plain": plain_ms / res["learned_128"]["ms"]})
+    # the convolution's roofline: one 16 -> 16 layer on the whole 128^3 grid
+    # (forward, input gradient, weight gradient), CUDA events over 20 calls of
+    # the layer primitives (each forward / input-gradient call also packs its
+    # weights: a 3 us launch, counted)
+    g0 = torch.Generator(device="cuda").manual_seed(0)
+    xa = torch.randn(cs + (16,), device="cuda", generator=g0).to(torch.bfloat16)
+    ga = torch.randn(cs + (16,), device="cuda", generator=g0).to(torch.bfloat16)
+    Wl = torch.randn(27, 16, 16, device="cuda", generator=g0) * 0.1
+    bl = torch.zeros(16, device="cuda")
+    mk = torch.relu(torch.randn(cs + (16,), device="cuda", generator=g0)).to(torch.bfloat16)
+    ol = torch.empty(cs + (16,), dtype=torch.bfloat16, device="cuda")
+    flop = 2 * 27 * 16 * 16 * n_c ** 3
+    bf16_peak, bf16_kind = measured_bf16()
+
+    def conv_rate(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record()
+        for _ in range(20):
+            fn()
+        c1.record()
+        torch.cuda.synchronize()
+        us = c0.elapsed_time(c1) / 20 * 1e3
+        return {"us": us, "achieved": flop / us / 1e6, "frac": flop / us / 1e6 / bf16_peak}
+
+    conv = {"bound": "tensor", "unit": "TFLOP/s", "peak": bf16_peak, "peak_kind": bf16_kind,
+            "flop_per_layer": flop,
+            "forward (k_conv3_tc)": conv_rate(lambda: ls.conv3_bf16(xa, Wl, bl, 0, out=ol)),
+            "input_gradient (k_conv3_tc, mode 2)": conv_rate(lambda: ls.conv3_bf16(ga, Wl, None, 2, mask=mk,
+                                                                                    out=ol)),
+            "weight_gradient (k_conv3_wgrad_tc)": conv_rate(lambda: ls.conv3_wgrad(xa, ga, 16, 16))}
     print(json.dumps({
         "metric": "learned-coarse vs plain at equal error", "workload": "learned corrector 128^3 / 512^3",
         "unit": "wall-time ratio (plain at equal error / learned)", "value": float(np.mean(
@@ -566,7 +610,7 @@ def run_learned(args):
         "pair_generation_s": t_pairs, "training_s": t_train, "coarse_steps": nsteps,
         "error_unit": "coarse cells h_c (max, mean of |phi - ref| within 1.5 h_c of the reference front)",
         "problems": results, "comparison": cmp, "fallbacks": ctx.learned_fallbacks(),
-        "data": "synthetic (seeded)"}), flush=True)
+        "conv_roofline": conv, "data": "synthetic (seeded)"}), flush=True)
     ctx.close()
 
 

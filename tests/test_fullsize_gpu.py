@@ -260,3 +260,42 @@ def test_local_scheme_sphere_union_512():
     assert torch.equal(before[~mask], after[~mask])
     assert g.band_breaches() == 0
     g.close()
+
+
+def test_slab_split_512_equals_one_grid_bitwise():
+    """The 512^3 sphere-union run split into two z-slabs on this GPU (the
+    path bench.py --parallelism slab times: device-side dt, two rebuild
+    periods per CUDA-graph replay, rows moved by Eq. 14 when that pays, the
+    autotuner's stencil configuration) against one context, 100 steps: the
+    same bits everywhere."""
+    from paper_1612_04040_b300 import slab
+    w = inputs.SphereUnion(n=512)
+    g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32)
+    g.init_speed(ls.LS_SPEED_SINUSOID)
+    g.init_phi(ls.LS_SHAPE_SPHERES, inputs.spheres_params(w.centres, w.radii))
+    phi0 = torch.empty((w.n,) * 3, dtype=torch.float32, device="cuda")
+    F0 = torch.empty_like(phi0)
+    g.get_phi(phi0)
+    g.get_speed(F0)
+    g.set_step_config(2, 100, 16)
+    g.band_rebuild(w.halfwidth, want_count=False)
+    g.step(100, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+    ref = torch.empty_like(phi0)
+    g.get_phi(ref)
+    g.close()
+    stream = torch.cuda.Stream()
+
+    def make(nx, ny, rows, h, lo, hi):
+        return slab.GpuSlab(nx, ny, rows, h, lo, hi, ls.LS_FP32, stream.cuda_stream, (2, 100, 16))
+
+    run = slab.DeviceSlabRun(slab.LocalComm(2), make, (w.n,) * 3, w.h, w.halfwidth,
+                             lambda z0, z1: (phi0[z0:z1], F0[z0:z1]), rebalance=True,
+                             rebalance_gain=0.0, rebalance_every=4, graphs=True, stream=stream)
+    run.prepare(w.cfl, w.rebuild_every)
+    run.step(100, w.cfl, w.rebuild_every)
+    torch.cuda.synchronize()
+    got = torch.full_like(ref, float("nan"))
+    for p, (z0, planes) in run.gather_phi().items():
+        got[z0:z0 + planes.shape[0]] = planes
+    run.close()
+    assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
