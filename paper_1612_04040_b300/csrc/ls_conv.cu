@@ -401,20 +401,22 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
 // x-points of one (y, z) row each; out-of-grid points zero-filled by the
 // TMA, which is the convolution's zero padding on both operands).  Both
 // operands are MN-major (the 8 channels of a point are one contiguous
-// 16-byte run).  Per chunk the TMA loads, per channel half, 9 boxes of x
-// (one per (dy, dz) pair, 1 KB each) and 3 boxes of dy (one per dx), so
-// the 8-channel groups of the pairs (M) and of the dx shifts (N) sit at one
-// stride (SBO = 1 KB) and the 8-point groups at 128 B (LBO).  M-tile 0 holds
-// pairs 0..7, M-tile 1 pair 8 and in slot 9 a box of ones kept in shared
-// memory, whose rows accumulate sum_q dy[q][o] (the bias gradient, from the
-// dx = 0 columns); slots 10..15 repeat it and are discarded.  The 96-column
-// accumulator lives in TMEM across all of a CTA's chunks; the epilogue adds
-// it to dW and db with FP32 atomics.
+// 16-byte run).  Per chunk the TMA loads, per dz and channel half, one box
+// of x holding the three rows y - 1, y, y + 1 (3 KB), the boxes in the
+// order (dz, half), so the 18 8-channel groups of the (dy, dz) pairs sit at
+// one stride (SBO = 1 KB) in the order (dz, half, dy); and 3 boxes of dy per
+// half (one per dx, 1 KB) for the N operand.  The 8-point groups sit at
+// 128 B (LBO).  M-tile 0 holds groups 0..15, M-tile 1 groups 16, 17 and two
+// groups of ones kept in shared memory, whose rows accumulate
+// sum_q dy[q][o] (the bias gradient, from the dx = 0 columns); the rest of
+// M-tile 1 repeats them and is discarded.  The 96-column accumulator lives
+// in TMEM across all of a CTA's chunks; the epilogue adds it to dW and db
+// with FP32 atomics.
 constexpr int WG_PTS = 64;
 constexpr int WG_BOX = WG_PTS * 16;                  // 64 points x 8 channels, BF16
 constexpr int WG_A_BYTES = 2 * 16 * WG_BOX;          // 2 M-tiles x 16 channel groups: 32 KB
 constexpr int WG_B_BYTES = 3 * 2 * WG_BOX;           // 3 dx shifts x 2 halves: 6 KB
-constexpr int WG_LOAD_BYTES = (9 * 2 + 3 * 2) * WG_BOX;  // what the TMA writes per chunk
+constexpr int WG_LOAD_BYTES = (9 * 2 + 3 * 2) * WG_BOX;  // what the TMA writes per chunk (6 x 3 KB + 6 x 1 KB)
 constexpr int WG_STAGE = WG_A_BYTES + WG_B_BYTES;    // 38 KB
 constexpr int WG_NSTAGE = 4;
 constexpr int WG_THREADS = 192;
@@ -433,7 +435,7 @@ struct WgradArgs {
 __global__ void __launch_bounds__(WG_THREADS, 1)
     k_conv3_wgrad_tc(const __grid_constant__ CUtensorMap mx0, const __grid_constant__ CUtensorMap mx1,
                      const __grid_constant__ CUtensorMap mg0, const __grid_constant__ CUtensorMap mg1,
-                     WgradArgs a)
+                     WgradArgs a)  // mx*: boxes of 64 x 3 x 1 points, mg*: 64 x 1 x 1
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[WG_NSTAGE], empty[WG_NSTAGE], acc_full;
@@ -443,10 +445,10 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
     const int ncx = a.nx / WG_PTS;
     const long long nchunks = (long long)ncx * a.ny * a.nz;
 
-    // the ones slots (9..15 of M-tile 1, both halves) of every stage; the
-    // TMA never writes there
+    // the ones groups (18..31: M-tile 1 after its two pair groups) of every
+    // stage; the TMA never writes there
     for (int st = 0; st < WG_NSTAGE; ++st) {
-        uint4* o = reinterpret_cast<uint4*>(smem + st * WG_STAGE + (16 + 2 * 1) * WG_BOX);
+        uint4* o = reinterpret_cast<uint4*>(smem + st * WG_STAGE + 18 * WG_BOX);
         const unsigned one2 = 0x3F803F80u;  // two BF16 ones
         for (int i = tid; i < 7 * 2 * WG_BOX / 16; i += WG_THREADS) o[i] = make_uint4(one2, one2, one2, one2);
     }
@@ -487,10 +489,9 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
                 const int y = (int)((q / ncx) % a.ny), z = (int)(q / ((long long)ncx * a.ny));
                 unsigned char* st = smem + s * WG_STAGE;
                 mbar_expect_tx(&full[s], WG_LOAD_BYTES);
-                for (int pr = 0; pr < 9; ++pr) {  // pair (dy, dz) = (pr % 3 - 1, pr / 3 - 1)
-                    const int dy = pr % 3 - 1, dz = pr / 3 - 1;
-                    tma_load_4d(st + (2 * pr) * WG_BOX, &mx0, 0, x0, y + dy, z + dz, &full[s]);
-                    tma_load_4d(st + (2 * pr + 1) * WG_BOX, &mx1, 0, x0, y + dy, z + dz, &full[s]);
+                for (int dz = -1; dz <= 1; ++dz) {  // rows y - 1 .. y + 1 of plane z + dz
+                    tma_load_4d(st + (6 * (dz + 1)) * WG_BOX, &mx0, 0, x0, y - 1, z + dz, &full[s]);
+                    tma_load_4d(st + (6 * (dz + 1) + 3) * WG_BOX, &mx1, 0, x0, y - 1, z + dz, &full[s]);
                 }
                 for (int g = 0; g < 3; ++g) {  // dx = g - 1: dy at q - (dx, 0, 0)
                     tma_load_4d(st + WG_A_BYTES + (2 * g) * WG_BOX, &mg0, 0, x0 - (g - 1), y, z, &full[s]);
@@ -545,10 +546,13 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
             } else if (__all_sync(0xffffffffu, abort_s ? 0 : 1)) {
                 fence_after();
                 const int r = 32 * q + lane;
-                const int c = r & 15;
                 for (int j = 0; j < 2; ++j) {
-                    const int slot = 8 * j + (r >> 4);  // 0..8 pairs, 9 ones
-                    const bool use = (slot < 9 && c < a.ci) || (slot == 9 && c == 0 && a.db);
+                    // M row r of tile j: group gi = 16 j + r / 8 in the order
+                    // (dz, half, dy) for gi < 18, then the ones (18: half 0)
+                    const int gi = 16 * j + (r >> 3);
+                    const int c = 8 * ((gi % 6) / 3) + (r & 7);
+                    const int slot = gi < 18 ? 3 * (gi / 6) + gi % 3 : 9;  // pair (dz+1) 3 + (dy+1); 9 ones
+                    const bool use = (gi < 18 && c < a.ci) || (gi == 18 && (r & 7) == 0 && a.db);
                     for (int g = 0; g < 3; ++g) {
                         // tcgen05.ld is warp-collective: every lane loads, then
                         // only the lanes with a gradient entry add it
@@ -684,7 +688,7 @@ cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, in
     if (!conv3_wgrad_shape_ok(nx, ny, nz) || ci < 1 || ci > 16 || co < 1 || co > 16)
         return cudaErrorInvalidValue;
     CUtensorMap mx[2], mg[2];
-    cudaError_t e = make_maps_box(mx, x, nx, ny, nz, WG_PTS, 1, 1);
+    cudaError_t e = make_maps_box(mx, x, nx, ny, nz, WG_PTS, 3, 1);
     if (e != cudaSuccess) return e;
     e = make_maps_box(mg, dy, nx, ny, nz, WG_PTS, 1, 1);
     if (e != cudaSuccess) return e;
