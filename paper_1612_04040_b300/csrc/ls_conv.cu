@@ -412,13 +412,18 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) k_conv3_tc(const __grid_const
 // M-tile 1 repeats them and is discarded.  The 96-column accumulator lives
 // in TMEM across all of a CTA's chunks; the epilogue adds it to dW and db
 // with FP32 atomics.
-constexpr int WG_PTS = 64;
-constexpr int WG_BOX = WG_PTS * 16;                  // 64 points x 8 channels, BF16
-constexpr int WG_A_BYTES = 2 * 16 * WG_BOX;          // 2 M-tiles x 16 channel groups: 32 KB
-constexpr int WG_B_BYTES = 3 * 2 * WG_BOX;           // 3 dx shifts x 2 halves: 6 KB
-constexpr int WG_LOAD_BYTES = (9 * 2 + 3 * 2) * WG_BOX;  // what the TMA writes per chunk (6 x 3 KB + 6 x 1 KB)
-constexpr int WG_STAGE = WG_A_BYTES + WG_B_BYTES;    // 38 KB
-constexpr int WG_NSTAGE = 4;
+// per chunk width PTS (64 or 128 x-points): sizes of one box row (PTS
+// points x 8 channels), the stage (A: 2 M-tiles x 16 channel groups; B: 3 dx
+// shifts x 2 halves) and the ring depth
+template <int PTS>
+struct WgCfg {
+    static constexpr int BOX = PTS * 16;
+    static constexpr int A_BYTES = 2 * 16 * BOX;
+    static constexpr int B_BYTES = 3 * 2 * BOX;
+    static constexpr int LOAD_BYTES = (9 * 2 + 3 * 2) * BOX;  // what the TMA writes per chunk
+    static constexpr int STAGE = A_BYTES + B_BYTES;            // 38 / 76 KB
+    static constexpr int NSTAGE = PTS == 64 ? 4 : 2;
+};
 constexpr int WG_THREADS = 192;
 // kind::f16, D F32, A and B BF16, both MN-major (transpose bits 15, 16),
 // N = 48, M = 128
@@ -432,12 +437,16 @@ struct WgradArgs {
     int nx, ny, nz, ci, co;
 };
 
+template <int PTS>
 __global__ void __launch_bounds__(WG_THREADS, 1)
     k_conv3_wgrad_tc(const __grid_constant__ CUtensorMap mx0, const __grid_constant__ CUtensorMap mx1,
                      const __grid_constant__ CUtensorMap mg0, const __grid_constant__ CUtensorMap mg1,
-                     WgradArgs a)  // mx*: boxes of 64 x 3 x 1 points, mg*: 64 x 1 x 1
+                     WgradArgs a)  // mx*: boxes of PTS x 3 x 1 points, mg*: PTS x 1 x 1
 {
     extern __shared__ __align__(1024) unsigned char smem[];
+    using C = WgCfg<PTS>;
+    constexpr int WG_PTS = PTS, WG_BOX = C::BOX, WG_A_BYTES = C::A_BYTES, WG_LOAD_BYTES = C::LOAD_BYTES,
+                  WG_STAGE = C::STAGE, WG_NSTAGE = C::NSTAGE;
     __shared__ __align__(8) unsigned long long full[WG_NSTAGE], empty[WG_NSTAGE], acc_full;
     __shared__ unsigned tmem_base_s;
     __shared__ volatile int abort_s;
@@ -679,23 +688,23 @@ int conv3_blocks(int nx, int ny, int nz) { return (nx / BXP) * (ny / BYP) * (nz 
 
 bool conv3_wgrad_shape_ok(int nx, int ny, int nz)
 {
-    return nx >= WG_PTS && nx % WG_PTS == 0 && ny >= 1 && nz >= 1;
+    return nx >= 64 && nx % 64 == 0 && ny >= 1 && nz >= 1;
 }
 
-cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci,
-                               int co, float* dW, float* db, unsigned* status, cudaStream_t s)
+template <int PTS>
+static cudaError_t launch_wgrad_pts(const void* x, const void* dy, int nx, int ny, int nz, int ci,
+                                    int co, float* dW, float* db, unsigned* status, cudaStream_t s)
 {
-    if (!conv3_wgrad_shape_ok(nx, ny, nz) || ci < 1 || ci > 16 || co < 1 || co > 16)
-        return cudaErrorInvalidValue;
+    using C = WgCfg<PTS>;
     CUtensorMap mx[2], mg[2];
-    cudaError_t e = make_maps_box(mx, x, nx, ny, nz, WG_PTS, 3, 1);
+    cudaError_t e = make_maps_box(mx, x, nx, ny, nz, PTS, 3, 1);
     if (e != cudaSuccess) return e;
-    e = make_maps_box(mg, dy, nx, ny, nz, WG_PTS, 1, 1);
+    e = make_maps_box(mg, dy, nx, ny, nz, PTS, 1, 1);
     if (e != cudaSuccess) return e;
     static bool attr = false;
-    const int smem = WG_NSTAGE * WG_STAGE;
+    const int smem = C::NSTAGE * C::STAGE;
     if (!attr) {
-        e = cudaFuncSetAttribute(k_conv3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(k_conv3_wgrad_tc<PTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -711,10 +720,20 @@ cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, in
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long nchunks = (long long)(nx / WG_PTS) * ny * nz;
+    const long long nchunks = (long long)(nx / PTS) * ny * nz;
     const int grid = (int)(nchunks < sms ? nchunks : sms);
-    k_conv3_wgrad_tc<<<grid, WG_THREADS, smem, s>>>(mx[0], mx[1], mg[0], mg[1], a);
+    k_conv3_wgrad_tc<PTS><<<grid, WG_THREADS, smem, s>>>(mx[0], mx[1], mg[0], mg[1], a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_conv3_wgrad(const void* x, const void* dy, int nx, int ny, int nz, int ci,
+                               int co, float* dW, float* db, unsigned* status, cudaStream_t s)
+{
+    if (!conv3_wgrad_shape_ok(nx, ny, nz) || ci < 1 || ci > 16 || co < 1 || co > 16)
+        return cudaErrorInvalidValue;
+    // chunks of 128 points where the rows allow: half the TMA boxes per point
+    if (nx % 128 == 0) return launch_wgrad_pts<128>(x, dy, nx, ny, nz, ci, co, dW, db, status, s);
+    return launch_wgrad_pts<64>(x, dy, nx, ny, nz, ci, co, dW, db, status, s);
 }
 
 cudaError_t launch_selftest_wait(unsigned* status, long long polls, cudaStream_t s)
