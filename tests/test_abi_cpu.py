@@ -66,6 +66,53 @@ def test_host_side_argument_errors(lib):
     assert lib.ls_strerror(native.LS_ENONFINITE).decode() == "non-finite value in input"
 
 
+_NEWER_CALLS_CHILD = r"""
+import ctypes, sys
+sys.path.insert(0, %(root)r)
+from paper_1612_04040_b300 import native
+lib = native.load()
+P = ctypes.c_void_p(256)      # placeholder, never dereferenced when a check holds
+d = ctypes.c_double(0.0)
+n = ctypes.c_longlong(0)
+codes = [
+    lib.ls_set_ghost_rows(None, 1, 0),
+    lib.ls_band_refresh(None, ctypes.byref(d), ctypes.byref(n)),
+    lib.ls_band_row_counts(None, P, 1),
+    lib.ls_get_tile_rows(None, 0, 1, -1, P, 1),
+    lib.ls_set_tile_rows(None, 0, 1, -1, P, 1),
+    lib.ls_copy_ghost_row(None, 0, None, 0, -1),
+    lib.ls_band_speed_bound(None, P, 1),
+    lib.ls_set_dt_from_bound(None, P, 0.5),
+    lib.ls_get_speed(None, P, 1),
+    lib.ls_learned_features(None, P, None, 0.0, 1.0, 1, P, None),
+    lib.ls_learned_features(P, P, None, 0.0, float("nan"), 1, P, None),
+    lib.ls_learned_features(P, P, None, 0.0, 1.0, 0, P, None),
+    lib.ls_learned_loss_grad(P, P, P, P, 8, 1.0, -1.0, P, P, P, None),
+    lib.ls_adam_step(P, P, P, P, 8, 1e-3, 0, None),               # step t >= 1
+    lib.ls_adam_step(P, P, P, P, 8, float("inf"), 1, None),
+    lib.ls_conv3_wgrad(P, P, 48, 16, 16, 16, 16, P, P, P, None),  # nx not a multiple of 64
+    lib.ls_conv3_wgrad(P, P, 64, 16, 16, 16, 16, P, P, None, None),  # no status word
+    lib.ls_step(None, 1, 1.0, native.LS_DT_KEEP, 5, None),
+]
+print(",".join(str(c) for c in codes))
+"""
+
+
+def test_newer_calls_refuse_bad_arguments_on_the_host():
+    """The slab-split, learned-primitive and dt calls refuse NULL contexts
+    and bad arguments before any CUDA call.  Run in a child process that sees
+    no CUDA device, so even a broken check could only end in a CUDA error
+    status, never in a kernel reading the placeholder pointers."""
+    import subprocess
+    import sys
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", _NEWER_CALLS_CHILD % {"root": ROOT}], env=env,
+                         capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    codes = [int(v) for v in out.stdout.strip().splitlines()[-1].split(",")]
+    assert codes == [native.LS_EINVAL] * len(codes), codes
+
+
 def _struct_fields(header, name):
     """Field names of `typedef struct { ... } name;` in the header, in order."""
     body = re.search(r"typedef struct \{([^{}]*)\} %s;" % name, header).group(1)

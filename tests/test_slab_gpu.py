@@ -143,3 +143,42 @@ def test_ghost_row_calls_refuse_owned_rows():
     with pytest.raises(ls.LSError):
         g.set_ghost_rows(2, 0)
     g.close()
+
+
+def test_keep_mode_and_slab_calls_refuse_misuse():
+    """LS_DT_KEEP needs a band and leaves every rebuild to the caller; the
+    ghost-row copy needs matching contexts and a ghost row to write."""
+    phi, F = fields(np.float32)
+    nz, ny, nx = SHAPE
+    g = ls.LevelSet(nx, ny, nz, H, ls.LS_FP32)
+    g.set_phi(phi)
+    g.set_speed(F)
+    with pytest.raises(ls.LSError) as e:                 # no band yet
+        g.step(1, 1.0, ls.LS_DT_KEEP, 5)
+    assert e.value.status == ls.LS_ESTATE
+    g.band_rebuild(HW)
+    g.step(5, 1.0, ls.LS_DT_KEEP, 5)                     # one whole period: fine
+    with pytest.raises(ls.LSError) as e:                 # the next step would need a rebuild
+        g.step(1, 1.0, ls.LS_DT_KEEP, 5)
+    assert e.value.status == ls.LS_ESTATE
+    M = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.band_refresh_async()
+    g.band_speed_bound(M)
+    Mh = np.zeros(1)
+    g.band_speed_bound(Mh)
+    assert float(M.item()) == Mh[0] > 0.0
+    h2 = ls.LevelSet(nx, ny, 2 * 8, H, ls.LS_FP32)
+    h2.set_phi(np.ones((16, ny, nx), dtype=np.float32))
+    with pytest.raises(ls.LSError):                      # no ghost rows declared
+        h2.copy_ghost_row(g, 3, 0, 0)
+    h2.set_ghost_rows(1, 0)
+    h2.copy_ghost_row(g, 3, 0, 7)                        # the bottom ghost row takes it
+    with pytest.raises(ls.LSError):                      # the top row is owned
+        h2.copy_ghost_row(g, 3, 1, 7)
+    h3 = ls.LevelSet(nx, 2 * ny, 16, H, ls.LS_FP32)
+    h3.set_phi(np.ones((16, 2 * ny, nx), dtype=np.float32))
+    h3.set_ghost_rows(1, 0)
+    with pytest.raises(ls.LSError):                      # other tile rows
+        h3.copy_ghost_row(g, 3, 0, 7)
+    for c in (g, h2, h3):
+        c.close()
