@@ -228,9 +228,9 @@ class SlabRun:
     row split, rebuild, and are then shared out by Eq. 14; with
     ``rebalance`` they are shared out again after every rebuild, when the
     Eq. 14 partition lowers the largest part's active tiles by more than
-    the fraction ``rebalance_gain`` (0: whenever it lowers it; moving rows
-    costs the moved parts new contexts, so a run on GPUs takes a few per
-    cent)."""
+    the fraction ``rebalance_gain`` (0: whenever it lowers it).  Moving rows
+    gives the moved parts new contexts, so a run on GPUs asks for a gain of
+    some per cent before it pays (``bench.py`` uses 10 %)."""
 
     def __init__(self, comm, make_engine, shape, h, halfwidth, source, rebalance=True,
                  rebalance_gain=0.0):
