@@ -93,6 +93,9 @@ def parse():
     p.add_argument("--slabs", type=int, default=1,
                    help="--parallelism slab on one GPU: number of slabs in this process (device "
                         "copies instead of NCCL)")
+    p.add_argument("--slab-graphs", type=int, choices=[0, 1], default=0,
+                   help="--parallelism slab with every slab in this process: replay the rebuild "
+                        "periods from CUDA graphs (1) or issue them eagerly (0)")
     p.add_argument("--rebalance-gain", type=float, default=0.1,
                    help="--parallelism slab: move rows to the Eq. 14 partition after a rebuild only "
                         "when that lowers the largest slab's active tiles by more than this fraction")
@@ -725,9 +728,9 @@ def run_slab(args):
     """The standard 512^3 run split into z-slabs (section 2 of the paper):
     one slab per rank (NCCL exchanges) or --slabs slabs on one GPU (device
     copies), rows shared out by Eq. 14 (checked every 10 rebuild periods).
-    The common dt is made on the device from the max-reduced bounds, and
-    with every slab in this process two rebuild periods at a time run from
-    one CUDA graph.  One bench step = one whole 500-step run from phi^0
+    The common dt is made on the device from the max-reduced bounds, so no
+    rebuild period waits on the host (--slab-graphs 1 replays two periods
+    at a time from a CUDA graph instead: measured slower).  One bench step = one whole 500-step run from phi^0
     (slab contexts, the initial rebuild and partition set up before the
     timed region); value = all slabs' updates (the library's device
     counters) / max time over ranks.  The total work is fixed as N grows
@@ -756,7 +759,7 @@ def run_slab(args):
     tuned = tune(g, args)
     g.close()
     comm = slab.DistComm(pg, dev) if world > 1 else slab.LocalComm(max(args.slabs, 1))
-    # a stream of its own: the rebuild periods are captured in CUDA graphs on it
+    # a stream of its own (the rebuild periods can be captured in CUDA graphs on it)
     run_stream = torch.cuda.Stream()
 
     def make(nx, ny, rows, h, lo, hi):
@@ -766,7 +769,7 @@ def run_slab(args):
         return slab.DeviceSlabRun(comm, make, (w.n,) * 3, w.h, w.halfwidth,
                                   lambda z0, z1: (phi0[z0:z1], F0[z0:z1]), rebalance=True,
                                   rebalance_gain=args.rebalance_gain, rebalance_every=10,
-                                  graphs=True, stream=run_stream)
+                                  graphs=bool(args.slab_graphs), stream=run_stream)
 
     for _ in range(max(args.warmup, 0)):
         r = new_run()
