@@ -245,3 +245,22 @@ def test_training_iteration_update_matches_oracle():
         o += n
     assert np.allclose(w1[np.abs(g) > 0.05 * np.max(np.abs(g))],
                        after[np.abs(g) > 0.05 * np.max(np.abs(g))], rtol=0, atol=1e-5)
+
+
+def test_corrected_step_with_an_empty_band_leaves_phi_unchanged():
+    """No point within the band: no active tile, no convolution block, no
+    correction, no fallback, phi unchanged bit for bit."""
+    shape = (32, 32, 128)
+    nz, ny, nx = shape
+    phi = np.full(shape, 0.5, dtype=np.float32)          # |phi| = 64 cells everywhere
+    F = np.full(shape, 0.5, dtype=np.float32)
+    params = random_params(41, last_scale=1.0, last_bias=2.0)
+    c = ls.LevelSet(nx, ny, nz, H_STEP, ls.LS_FP32)
+    c.learned_load(weights_image(params))
+    c.set_phi(phi)
+    c.set_speed(F)
+    got = run_steps(c, ls.LS_LEARNED, 3, 0.5 * H_STEP, 6.0)
+    assert c.active_tiles().size == 0
+    assert c.learned_fallbacks() == 0
+    c.close()
+    assert np.array_equal(got.view(np.int32), phi.view(np.int32))

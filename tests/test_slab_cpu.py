@@ -171,3 +171,28 @@ def test_two_gloo_ranks_equal_unsplit_oracle_bitwise():
         assert dt == ref.last_dt and mig >= 1
         assert bounds == res[0][5]
     assert np.array_equal(got, ref.phi)
+
+
+def test_parts_with_an_empty_band_and_a_single_row():
+    """A front only in the top rows: the lower parts hold no active tile (M = 0
+    there, the all-reduced M comes from the top), one part is a single tile
+    row, and the split is still the unsplit run bit for bit."""
+    shape, h = (96, 32, 32), 1.0 / 32
+    Z = shape[0] * h
+    phi = inputs.sphere_union_sdf(shape, h, [(0.5, 0.5, 0.85 * Z)], [0.12]).numpy()
+    F = np.full(shape, 0.75)
+    src = lambda z0, z1: (torch.from_numpy(phi[z0:z1].copy()), torch.from_numpy(F[z0:z1].copy()))
+    run = slab.SlabRun(slab.LocalComm(5), OracleSlab, shape, h, 3.0, src)
+    counts = run.active_rows()
+    assert counts[:6].sum() == 0 and counts.sum() > 0
+    assert min(run.bounds[i + 1] - run.bounds[i] for i in range(5)) == 1
+    run.step(20, 0.5, 5)
+    o = oracle.Oracle(shape, h)
+    o.set_phi(phi)
+    o.set_speed(F)
+    o.band_rebuild(3.0)
+    o.step(20, 0.5, oracle.DT_CFL, 5)
+    got = np.empty_like(phi)
+    for p, (z0, planes) in run.gather_phi().items():
+        got[z0:z0 + planes.shape[0]] = planes.numpy()
+    assert np.array_equal(got, o.phi)
