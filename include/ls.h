@@ -420,10 +420,12 @@ int ls_reset_profile(ls_ctx *ctx);
 /* Sticky device status word: LS_OK, or the first device-side error. */
 int ls_get_status(ls_ctx *ctx);
 
-/* Self-test of the bounded device wait used by the tensor-core kernels: a
- * kernel waits on a barrier that nothing completes, gives up after `polls`
- * polls and sets bit 1 (timeout) in the device word *status; the context and
- * the device stay usable.  For failure-detection tests. */
+/* Self-test of the bounded device waits used by the tensor-core kernels and
+ * by the one-warp stencil's bulk-copy staging: a kernel waits on two
+ * barriers that nothing completes, one with each wait, and sets bit 1
+ * (timeout) in the device word *status when both gave up after `polls`
+ * polls; the context and the device stay usable.  For failure-detection
+ * tests. */
 int ls_selftest_bounded_wait(unsigned *status, long long polls, void *cuda_stream);
 
 /* Measured FP64 peak of the current device in TFLOP/s (a fused multiply-add

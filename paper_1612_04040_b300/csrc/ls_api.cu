@@ -326,6 +326,7 @@ lsk::StepArgs step_args(ls_ctx* c, bool classify)
     a.insts = c->batched ? c->d_inst : nullptr;
     a.core = classify ? c->core : nullptr;
     a.updates = c->d_updates;
+    a.status = c->d_status;
     a.in = c->in0();
     a.max_grid = c->full_domain ? (int)(c->ntiles < (1 << 30) ? c->ntiles : (1 << 30)) : 0;
     // copies of the frozen x-faces (plain scheme: no pass between rebuilds

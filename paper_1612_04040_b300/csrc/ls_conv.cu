@@ -44,6 +44,7 @@
 
 #include "ls.h"
 #include "ls_internal.cuh"
+#include "ls_stencil.cuh"
 
 namespace lsk {
 
@@ -599,10 +600,19 @@ __global__ void __launch_bounds__(WG_THREADS, 1)
 // must give up after `polls` polls and record ST_TIMEOUT
 __global__ void k_selftest_wait(unsigned* status, long long polls)
 {
-    __shared__ __align__(8) unsigned long long bar;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    // two barriers nobody arrives on: the convolutions' wait and the
+    // stencil's bulk-copy wait (ls_stencil.cuh) must both give up
+    __shared__ __align__(8) unsigned long long bar[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
     __syncthreads();
-    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, polls)) atomicOr(status, ST_TIMEOUT);
+    if (threadIdx.x == 0) {
+        const bool a = mbar_wait(&bar[0], 0, polls);
+        const bool b = bulk_wait(smem_u32(&bar[1]), 0, polls);
+        if (!a && !b) atomicOr(status, ST_TIMEOUT);
+    }
 }
 
 // pack W (FP32 [27][ci][co], ci, co <= 16) into the canonical K-major B

@@ -207,6 +207,7 @@ struct StepArgs {
     // 1: faces whose NACT_FILL bit is set are read from the neighbour and
     // their copy written (the first plain step after a rebuild)
     int xface_fill;
+    unsigned* status;         // sticky device status word (ST_*)
 };
 
 // launch configuration of the FP32 stencil, chosen by the autotuner

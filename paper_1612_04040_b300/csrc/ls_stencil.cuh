@@ -37,6 +37,51 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// mbarrier-completed bulk copies (the one-warp kernels' staging): one
+// mbarrier per ring stage, armed with the stage's byte count, waited with a
+// bound (a stuck copy ends in a status bit, not a hang)
+__device__ __forceinline__ void bulk_mbar_init(unsigned bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bulk_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+// global -> shared, `bytes` (multiple of 16, both addresses 16-byte aligned),
+// completing on the mbarrier
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long bulk_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait for the phase of the given parity: false after `limit` polls
+// or 2 s, whichever comes first
+__device__ __forceinline__ bool bulk_wait(unsigned bar, unsigned parity, long long limit)
+{
+    const unsigned long long t0 = bulk_ns();
+    for (long long i = 0; i < limit; ++i) {
+        unsigned ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "  selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 255) == 255 && bulk_ns() - t0 > 2000000000ull) return false;
+    }
+    return false;
+}
+
 // hardware reciprocal square root (approximate, flush-to-zero): the inputs
 // here are clamped to >= 1e-30, so no denormal reaches it
 __device__ __forceinline__ float rsqrt_hw(float x)

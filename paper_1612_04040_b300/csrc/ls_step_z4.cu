@@ -10,6 +10,17 @@
 // 4-point kernel's stage layout without its speed block, the same per-point
 // arithmetic (ls_stencil.cuh), so the results are the same bits for every
 // choice of points per thread.
+//
+// Staging: the tile's 2 KiB block and its two z faces (256-byte runs) are
+// bulk asynchronous copies issued by one lane and completing on the stage's
+// mbarrier; the x-halo words and the 32-byte y-halo runs are per-lane
+// cp.async as in the other kernels.  The bulk copies do not pass through the
+// L1 data cache, which the cp.async requests in flight otherwise share with
+// the halo gathers (measured: batch of 256 grids 163.7 -> 157.1 us per
+// launch, 512^3 sphere union 60.9 -> 59.8 us).  Small requests do not pay on
+// the copy engine: the y runs as sixteen 32-byte bulk copies measured 184 us,
+// the x faces as tensor boxes of the neighbours' boundary quads (64 rows of
+// 16 bytes) 190 us.
 #include <cstddef>
 
 #include "ls_internal.cuh"
@@ -22,19 +33,29 @@ namespace {
 // one ring stage (the layout of the 4-point kernel's stage, without the
 // speed block: each thread reads its own 16 speeds straight into registers
 // when it computes the tile -- they are nobody's neighbours -- which keeps
-// the stage at 3.6 KB and measured 5 % faster than staging them)
-template <bool FIELD>
+// the stage at 4.1 KB and measured 5 % faster than staging them)
+//
+// Shared-memory banks: a warp's 128-bit loads are served a quarter-warp (8
+// lanes, 128 bytes) at a time, so the layout gives each quarter's halo quads
+// the bank groups (quad index mod 8) its in-tile quads leave free.  The y-halo
+// row of plane lz holds the +y runs at slots xh (the lanes ly = 4..6 of its
+// quarter read quads 2..7 mod 8) and the -y runs at slots 6 + xh (ly = 1..3
+// read 0..5); the x-halo words of planes 4..7 are stored with planes 4 <-> 5
+// and 6 <-> 7 swapped, so that the two half-warps read different banks.
 struct StageZ4 {
-    float4 v[192];   // [0,128): centre quads; [128,160): y-halo runs [16*(ly==7) + 2*lz + xh];
-                     // [160,192): z-halo runs [16*(lz==7) + 2*ly + xh]
-    float xo[128];   // x-halo value of each quad
+    float4 v[224];   // [0,128): centre quads; [128,192): y-halo rows [8*lz + (ly==7 ? xh : 6 + xh)];
+                     // [192,224): z-halo runs [16*(lz==7) + 2*ly + xh]
+    float xo[128];   // x-halo value of each quad, quad q0 + 16 j at q0 + 16 (j ^ lzq)
     int4 meta;       // tile id, info byte, instance
     float2 mf;       // batched: the instance's dt / h and constant speed
+    unsigned long long bar;  // completion of the stage's bulk copies
 };
 
 // a list entry with what its staging and its update need (batched: the
-// instance's tile-row strides, dt / h and speed), fetched two tiles ahead
-// so that the dependent loads behind it are off the critical path
+// instance's tile-row strides, dt / h and speed).  The entry itself is
+// loaded three tiles ahead of its staging and, batched, its instance's data
+// one tile later, once the instance id has arrived: no load waits on
+// another load in the same iteration.
 struct EntZ4 {
     unsigned t, info, inst;
     int tnx, tny;
@@ -43,7 +64,7 @@ struct EntZ4 {
 
 // the four quads of one thread, one class of tile (SGN, FACES as upd4)
 template <int SGN, bool FACES, bool FIELD, bool CLASSIFY>
-__device__ __forceinline__ void quads4(const StageZ4<FIELD>& Sg, const float4 (&c)[4],
+__device__ __forceinline__ void quads4(const StageZ4& Sg, const float4 (&c)[4],
                                        const float4 (&fr)[4], float Fc, float coef, bool extrap,
                                        int q0, int xh, int ly, int lzq,
                                        int y_slot0, int z_slot, bool xlo, bool xhi, bool ylo,
@@ -53,12 +74,14 @@ __device__ __forceinline__ void quads4(const StageZ4<FIELD>& Sg, const float4 (&
     for (int j = 0; j < 4; ++j) {
         const int qj = q0 + 16 * j;
         const float4 f = FIELD ? fr[j] : make_float4(Fc, Fc, Fc, Fc);
-        const float4 ym = Sg.v[ly > 0 ? qj - 2 : y_slot0 + 2 * j];
-        const float4 yp = Sg.v[ly < 7 ? qj + 2 : y_slot0 + 2 * j];
+        const float4 ym = Sg.v[ly > 0 ? qj - 2 : y_slot0 + 8 * j];
+        const float4 yp = Sg.v[ly < 7 ? qj + 2 : y_slot0 + 8 * j];
         const float4 zm = j > 0 ? c[j - 1] : Sg.v[lzq > 0 ? q0 - 16 : z_slot];
         const float4 zp = j < 3 ? c[j + 1] : Sg.v[lzq < 1 ? q0 + 64 : z_slot];
-        const float pcv = reinterpret_cast<const float*>(Sg.v)[4 * (qj ^ 1) + (xh ? 3 : 0)];
-        const float xo = Sg.xo[qj];
+        // the in-tile x neighbour across the quad boundary is in the partner
+        // lane's registers (same row, other half)
+        const float pcv = __shfl_xor_sync(0xffffffffu, xh ? c[j].x : c[j].w, 1);
+        const float xo = Sg.xo[q0 + 16 * (j ^ lzq)];
         const float xm0 = xh ? pcv : xo, xp3 = xh ? xo : pcv;
         const float4 o = upd4<SGN, FACES>(c[j], f, xm0, xp3, ym, yp, zm, zp, coef, extrap, xlo, xhi,
                                           ylo, yhi, zlo && j == 0, zhi && j == 3);
@@ -74,7 +97,7 @@ template <bool FIELD, bool CLASSIFY, bool BATCHED, int S>
 __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using Stage = StageZ4<FIELD>;
+    using Stage = StageZ4;
     Stage* st = reinterpret_cast<Stage*>(smem_raw);
     const int tid = threadIdx.x;
     const int xh = tid & 1, ly = (tid >> 1) & 7, lzq = tid >> 4;
@@ -110,14 +133,11 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     const int y_in = (ly == 0) ? (lz0 * 64 + 56 + 4 * xh) : (lz0 * 64 + 4 * xh);
     const int y_sgn = (ly == 0) ? -1 : 1;
     const unsigned y_bit = (ly == 0) ? NB_YM : ((ly == 7) ? NB_YP : 0u);
-    const int y_slot0 = 128 + ((ly == 7) ? 16 : 0) + 2 * lz0 + xh;
-    // the lower half-warp stages the -z face, the upper half-warp the +z face
-    const int z_in = (lzq == 0) ? (448 + ly * 8 + 4 * xh) : (ly * 8 + 4 * xh);
-    const int z_sgn = (lzq == 0) ? -1 : 1;
-    const unsigned z_bit = (lzq == 0) ? NB_ZM : NB_ZP;
-    const int z_slot = 160 + ((lzq == 1) ? 16 : 0) + 2 * ly + xh;
+    const int y_slot0 = 128 + 8 * lz0 + ((ly == 7) ? xh : 6 + xh);
+    // the z-halo quad of the lower half-warp's plane 0 (-z face) and of the
+    // upper half-warp's plane 7 (+z face)
+    const int z_slot = 192 + ((lzq == 1) ? 16 : 0) + 2 * ly + xh;
     const int y_off1 = y_sgn * sy1 + y_in;
-    const int z_off1 = z_sgn * sz1 + z_in;
     // a frozen x neighbour's face from its copy (single grid): value
     // (lz0 + j, ly) of this thread's side at xf_off0 + 8 j; faces with their
     // fill bit are read in place by a filling launch, which writes the copy
@@ -128,24 +148,38 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
 
     const unsigned sm0 = (unsigned)__cvta_generic_to_shared(st);
     constexpr unsigned SB = (unsigned)sizeof(Stage);
-    const unsigned a_c0 = sm0 + (unsigned)offsetof(Stage, v) + 16u * q0;
     const unsigned a_x0 = sm0 + (unsigned)offsetof(Stage, xo) + 4u * q0;
     const unsigned a_y0 = sm0 + (unsigned)offsetof(Stage, v) + 16u * y_slot0;
-    const unsigned a_z = sm0 + (unsigned)offsetof(Stage, v) + 16u * z_slot;
+    const unsigned a_v = sm0 + (unsigned)offsetof(Stage, v);
+    const unsigned a_bar = sm0 + (unsigned)offsetof(Stage, bar);
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) bulk_mbar_init(a_bar + (unsigned)s * SB);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    unsigned phase = 0u;  // parity of each stage's next completion (bit s)
 
     auto issue = [&](const EntZ4& e, int s) {
         const unsigned t = e.t, info = e.info, inst = e.inst;
         const unsigned base = t * TILE_PTS;
         const float* tp = src + base;
         const unsigned so = (unsigned)s * SB;
+        int y_off = y_off1;
+        if (BATCHED) y_off = y_sgn * (e.tnx * TILE_PTS) + y_in;
         if (tid == 0) {
             st[s].meta = make_int4((int)t, (int)info, (int)inst, 0);
             if (BATCHED) st[s].mf = make_float2(e.coef, e.Fc);
-        }
-        int y_off = y_off1, z_off = z_off1;
-        if (BATCHED) {
-            y_off = y_sgn * (e.tnx * TILE_PTS) + y_in;
-            z_off = z_sgn * (e.tnx * e.tny * TILE_PTS) + z_in;
+            const bool zm = (info & NB_ZM) != 0, zp = (info & NB_ZP) != 0;
+            const int sz = BATCHED ? e.tnx * e.tny * TILE_PTS : sz1;
+            const unsigned bar = a_bar + so;
+            // this stage was last read by generic loads (ordered before by
+            // the ring barrier); the bulk copies write it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_expect_tx(bar, 2048u + (zm ? 256u : 0u) + (zp ? 256u : 0u));
+            bulk_g2s(a_v + so, tp, 2048u, bar);
+            if (zm) bulk_g2s(a_v + so + 16u * 192u, tp - sz + 448, 256u, bar);  // plane 7 below
+            if (zp) bulk_g2s(a_v + so + 16u * 208u, tp + sz, 256u, bar);        // plane 0 above
         }
         const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0;
         // inst: the entry's active face-neighbour and fill bits when xf is set
@@ -154,23 +188,27 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         const int xstep = fz ? 8 : 64;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            cp_async16s(a_c0 + so + 256u * j, tp + 4 * q0 + 64 * j);
-            cp_async4s(a_x0 + so + 64u * j, xs + xstep * j, px);
-            cp_async16s(a_y0 + so + 32u * j, tp + y_off + 64 * j, py);
+            cp_async4s(a_x0 + so + 64u * (unsigned)(j ^ lzq), xs + xstep * j, px);
+            cp_async16s(a_y0 + so + 128u * j, tp + y_off + 64 * j, py);
         }
-        cp_async16s(a_z + so, tp + z_off, (info & z_bit) != 0);
     };
-    auto fetch = [&](int k, EntZ4& e) {
+    auto fetch_entry = [&](int k, EntZ4& e) {
         k = ent(k);
         e.t = (unsigned)__ldg(list + k);
         e.info = __ldg(linfo + k);
         e.inst = BATCHED ? (unsigned)__ldg(linst + k) : (xf ? (unsigned)__ldg(a.nact + k) : 0u);
+    };
+    auto fetch_inst = [&](EntZ4& e) {
         if (BATCHED) {
             e.tnx = a.insts[e.inst].tnx;
             e.tny = a.insts[e.inst].tny;
             e.coef = a.sc[e.inst].coef;
             e.Fc = a.sc[e.inst].Fc;
         }
+    };
+    auto fetch = [&](int k, EntZ4& e) {
+        fetch_entry(k, e);
+        fetch_inst(e);
     };
 
     // tile ids of the staged entries in the order they are computed, so
@@ -189,9 +227,10 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         cp_async_commit();
         kn += stride;
     }
-    EntZ4 e1 = {}, e2 = {};
+    EntZ4 e1 = {}, e2 = {}, e3 = {};
     if (kn < n) fetch(kn, e1);
     if (kn + stride < n) fetch(kn + stride, e2);
+    if (BATCHED && kn + 2 * stride < n) fetch_entry(kn + 2 * stride, e3);
     int cur = 0;
     for (int k = blockIdx.x; k < n; k += stride) {
         // this tile's speeds (each thread its own 16: nobody's neighbours),
@@ -203,6 +242,25 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
                 fr[j] = __ldg(reinterpret_cast<const float4*>(Fp + (size_t)tq[0] * TILE_PTS + 4 * q0 + 64 * j));
         }
         cp_async_wait<S - 2>();
+        {
+            const unsigned par = (phase >> cur) & 1u;
+            const bool ok = bulk_wait(a_bar + (unsigned)cur * SB, par, 1ll << 26);
+            if (!__all_sync(0xffffffffu, ok ? 1 : 0)) {
+                // give up: record it, let the copies still in flight land
+                // (bounded waits), and leave
+                if (tid == 0) {
+                    if (a.status) atomicOr(a.status, ST_TIMEOUT);
+                    bulk_wait(a_bar + (unsigned)cur * SB, par, 1ll << 20);
+                    for (int i = 1; i < S - 1; ++i) {
+                        const int s2 = (cur + i) % S;
+                        if (k + i * stride < n) bulk_wait(a_bar + (unsigned)s2 * SB, (phase >> s2) & 1u, 1ll << 20);
+                    }
+                }
+                cp_async_wait<0>();
+                return;
+            }
+            phase ^= 1u << cur;
+        }
         __syncthreads();
         {
             const int sn = cur == 0 ? S - 1 : cur - 1;
@@ -213,7 +271,13 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
             tq[S - 2] = e1.t;
             kn += stride;
             e1 = e2;
-            if (kn + stride < n) fetch(kn + stride, e2);
+            if (BATCHED) {
+                e2 = e3;
+                if (kn + stride < n) fetch_inst(e2);
+                if (kn + 2 * stride < n) fetch_entry(kn + 2 * stride, e3);
+            } else if (kn + stride < n) {
+                fetch(kn + stride, e2);
+            }
         }
         const Stage& Sg = st[cur];
         const int t = Sg.meta.x;
@@ -221,13 +285,15 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         const int inst = Sg.meta.z;
         const float coef = BATCHED ? Sg.mf.x : coef1;
         const float Fc = BATCHED ? Sg.mf.y : Fc1;
+        // the tube test's gamma, requested before the update hides its latency
+        const double g = (CLASSIFY && BATCHED && tid == 0) ? a.insts[inst].gamma : gamma1;
         float4 c[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) c[j] = Sg.v[q0 + 16 * j];
         float* dp = dst + (unsigned)t * TILE_PTS;
         if (!BATCHED && xfill && ((unsigned)inst & fill_bit)) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) xf[(size_t)t * XFACE_FLOATS + xf_off0 + 8 * j] = Sg.xo[q0 + 16 * j];
+            for (int j = 0; j < 4; ++j) xf[(size_t)t * XFACE_FLOATS + xf_off0 + 8 * j] = Sg.xo[q0 + 16 * (j ^ lzq)];
         }
         float mn = __int_as_float(0x7f800000);
         if (info == (NB_ALL | SG_POS)) {
@@ -249,10 +315,7 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
         if (CLASSIFY) {
             // the warp holds the whole tile: its minimum is the tile's
             const unsigned wm = __reduce_min_sync(0xffffffffu, __float_as_uint(mn));
-            if (tid == 0) {
-                const double g = BATCHED ? a.insts[inst].gamma : gamma1;
-                a.core[t] = ((double)__uint_as_float(wm) < g) ? 1 : 0;
-            }
+            if (tid == 0) a.core[t] = ((double)__uint_as_float(wm) < g) ? 1 : 0;
         }
         cur = cur + 1 == S ? 0 : cur + 1;
     }
@@ -273,7 +336,7 @@ int occupancy_grid_z4(K kernel, size_t smem)
 template <bool FIELD, bool CLS, bool BAT, int S>
 cudaError_t launch_z4(const StepArgs& a, int grid_pct, cudaStream_t s)
 {
-    constexpr size_t smem = sizeof(StageZ4<FIELD>) * S;
+    constexpr size_t smem = sizeof(StageZ4) * S;
     static int full = 0;
     if (!full) full = occupancy_grid_z4(k_step_f32_z4<FIELD, CLS, BAT, S>, smem);
     int grid = (int)((long long)full * grid_pct / 100);
