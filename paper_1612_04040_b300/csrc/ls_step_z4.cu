@@ -33,18 +33,15 @@ namespace {
 // one ring stage (the layout of the 4-point kernel's stage, without the
 // speed block: each thread reads its own 16 speeds straight into registers
 // when it computes the tile -- they are nobody's neighbours -- which keeps
-// the stage at 4.1 KB and measured 5 % faster than staging them)
-//
-// Shared-memory banks: a warp's 128-bit loads are served a quarter-warp (8
-// lanes, 128 bytes) at a time, so the layout gives each quarter's halo quads
-// the bank groups (quad index mod 8) its in-tile quads leave free.  The y-halo
-// row of plane lz holds the +y runs at slots xh (the lanes ly = 4..6 of its
-// quarter read quads 2..7 mod 8) and the -y runs at slots 6 + xh (ly = 1..3
-// read 0..5); the x-halo words of planes 4..7 are stored with planes 4 <-> 5
-// and 6 <-> 7 swapped, so that the two half-warps read different banks.
+// the stage at 3.6 KB and measured 5 % faster than staging them).  The x-halo
+// words of planes 4..7 are stored with planes 4 <-> 5 and 6 <-> 7 swapped, so
+// that the two half-warps read different banks.  (A y-halo layout free of
+// bank conflicts, eight-quad rows with each quarter-warp's halo quads in the
+// bank groups its in-tile quads leave free, measured no faster: the 512 bytes
+// it adds per stage come out of the L1 capacity the halo gathers use.)
 struct StageZ4 {
-    float4 v[224];   // [0,128): centre quads; [128,192): y-halo rows [8*lz + (ly==7 ? xh : 6 + xh)];
-                     // [192,224): z-halo runs [16*(lz==7) + 2*ly + xh]
+    float4 v[192];   // [0,128): centre quads; [128,160): y-halo runs [16*(ly==7) + 2*lz + xh];
+                     // [160,192): z-halo runs [16*(lz==7) + 2*ly + xh]
     float xo[128];   // x-halo value of each quad, quad q0 + 16 j at q0 + 16 (j ^ lzq)
     int4 meta;       // tile id, info byte, instance
     float2 mf;       // batched: the instance's dt / h and constant speed
@@ -74,8 +71,8 @@ __device__ __forceinline__ void quads4(const StageZ4& Sg, const float4 (&c)[4],
     for (int j = 0; j < 4; ++j) {
         const int qj = q0 + 16 * j;
         const float4 f = FIELD ? fr[j] : make_float4(Fc, Fc, Fc, Fc);
-        const float4 ym = Sg.v[ly > 0 ? qj - 2 : y_slot0 + 8 * j];
-        const float4 yp = Sg.v[ly < 7 ? qj + 2 : y_slot0 + 8 * j];
+        const float4 ym = Sg.v[ly > 0 ? qj - 2 : y_slot0 + 2 * j];
+        const float4 yp = Sg.v[ly < 7 ? qj + 2 : y_slot0 + 2 * j];
         const float4 zm = j > 0 ? c[j - 1] : Sg.v[lzq > 0 ? q0 - 16 : z_slot];
         const float4 zp = j < 3 ? c[j + 1] : Sg.v[lzq < 1 ? q0 + 64 : z_slot];
         // the in-tile x neighbour across the quad boundary is in the partner
@@ -133,10 +130,10 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     const int y_in = (ly == 0) ? (lz0 * 64 + 56 + 4 * xh) : (lz0 * 64 + 4 * xh);
     const int y_sgn = (ly == 0) ? -1 : 1;
     const unsigned y_bit = (ly == 0) ? NB_YM : ((ly == 7) ? NB_YP : 0u);
-    const int y_slot0 = 128 + 8 * lz0 + ((ly == 7) ? xh : 6 + xh);
+    const int y_slot0 = 128 + ((ly == 7) ? 16 : 0) + 2 * lz0 + xh;
     // the z-halo quad of the lower half-warp's plane 0 (-z face) and of the
     // upper half-warp's plane 7 (+z face)
-    const int z_slot = 192 + ((lzq == 1) ? 16 : 0) + 2 * ly + xh;
+    const int z_slot = 160 + ((lzq == 1) ? 16 : 0) + 2 * ly + xh;
     const int y_off1 = y_sgn * sy1 + y_in;
     // a frozen x neighbour's face from its copy (single grid): value
     // (lz0 + j, ly) of this thread's side at xf_off0 + 8 j; faces with their
@@ -178,8 +175,8 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             bulk_expect_tx(bar, 2048u + (zm ? 256u : 0u) + (zp ? 256u : 0u));
             bulk_g2s(a_v + so, tp, 2048u, bar);
-            if (zm) bulk_g2s(a_v + so + 16u * 192u, tp - sz + 448, 256u, bar);  // plane 7 below
-            if (zp) bulk_g2s(a_v + so + 16u * 208u, tp + sz, 256u, bar);        // plane 0 above
+            if (zm) bulk_g2s(a_v + so + 16u * 160u, tp - sz + 448, 256u, bar);  // plane 7 below
+            if (zp) bulk_g2s(a_v + so + 16u * 176u, tp + sz, 256u, bar);        // plane 0 above
         }
         const bool px = (info & x_bit) != 0, py = (info & y_bit) != 0;
         // inst: the entry's active face-neighbour and fill bits when xf is set
@@ -189,7 +186,7 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             cp_async4s(a_x0 + so + 64u * (unsigned)(j ^ lzq), xs + xstep * j, px);
-            cp_async16s(a_y0 + so + 128u * j, tp + y_off + 64 * j, py);
+            cp_async16s(a_y0 + so + 32u * j, tp + y_off + 64 * j, py);
         }
     };
     auto fetch_entry = [&](int k, EntZ4& e) {
