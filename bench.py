@@ -85,6 +85,8 @@ def parse():
                    help="perturbed workload: grid edge (1024 = the standard workload)")
     p.add_argument("--reinit-iters", type=int, default=-1,
                    help="local workload: reinitialisation iterations per step (-1: ceil(halfwidth/dtau))")
+    p.add_argument("--batch-count", type=int, default=256,
+                   help="batch workload: the first N of its 256 instances (smaller cases for profiling)")
     p.add_argument("--pairs", type=int, default=2000)
     p.add_argument("--train-iters", type=int, default=2000)
     p.add_argument("--parallelism", choices=["replicas", "slab"], default="replicas",
@@ -380,20 +382,53 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def cpu_baseline_batch(insts, budget_s=12.0, steps=10):
+    """The FP64 CPU oracle, as it stands, on the batch's instances in order
+    (each: band 4h, `steps` steps at CFL 0.5, rebuild every 5) until about
+    `budget_s` seconds of CPU work have been spent."""
+    import numpy as np
+    import oracle
+    t_all = 0.0
+    updates = 0
+    done = 0
+    for it in insts:
+        phi = it.phi().numpy().astype(np.float64)
+        o = oracle.Oracle(phi.shape, it.h)
+        o.set_phi(phi)
+        o.set_speed_const(it.speed)
+        t0 = time.perf_counter()
+        o.band_rebuild(4.0)
+        for _ in range(steps):
+            o.step(1, 0.5, oracle.DT_CFL, 5)
+            updates += int(o.active.sum()) * 512
+        t_all += time.perf_counter() - t0
+        done += 1
+        if t_all >= budget_s:
+            break
+    cores = len(os.sched_getaffinity(0))
+    return {"value": updates / t_all / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d of the batch's instances, %d level-set steps each (band 4h, CFL 0.5, "
+                      "rebuild every 5), FP64 C oracle with OpenMP on %d host threads, %.1f s"
+                      % (done, steps, cores, t_all)}
+
+
 def run_batch(args):
     """256 independent grids (edges 32..192, sphere or torus, constant F in
     [-1, 1]), band 4h, rebuild every 5, 200 steps at CFL 0.5, FP32, one
-    batched context: one stencil launch per step for all instances, the
-    200-step call replayed as a CUDA graph, launch configuration from the
-    autotuner.  One bench step = restore phi^0 (device snapshot) ->
-    ls_band_rebuild(4) -> ls_step(200)."""
+    batched context: one stencil launch per step for all instances, launch
+    configuration from the autotuner.  One bench step = restore phi^0
+    (device snapshot) -> ls_band_rebuild(4) -> ls_step(200).  The stencil's
+    roofline comes from CUDA events around one run of back-to-back stencil
+    launches in PROFILE_EVERY inside the timed region (eager launches: the
+    200-step call replayed as a CUDA graph measured no faster, 38.6 against
+    38.5 ms, and a graph cannot carry the event records)."""
     import torch
     from paper_1612_04040_b300 import inputs
     from paper_1612_04040_b300 import native as ls
     world, rank, local, pg = dist_setup(args)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    insts = inputs.batch_instances()
+    insts = inputs.batch_instances()[:max(1, min(args.batch_count, 256))]
     b = ls.Batch([i.edge for i in insts], [i.h for i in insts], stream=stream.cuda_stream)
     for k, it in enumerate(insts):
         b.set_phi_i(k, it.phi(device=dev).to(torch.float32).contiguous())
@@ -409,19 +444,20 @@ def run_batch(args):
         b.band_rebuild(4.0, want_count=False)
         b.step(200, 0.5, ls.LS_DT_CFL, 5)
 
-    # profiled eager pass for the roofline of the stencil
-    b.reset_profile()
-    b.profile_enable(True)
-    u0 = b.updates()
-    run_once()
-    prof = b.profile()
-    b.profile_enable(False)
-    upd_prof = b.updates() - u0
-    b.set_graphs(True)
     for _ in range(max(args.warmup, 0)):
         run_once()
     torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
     b.reset_profile()
+    b.profile_enable(PROFILE_EVERY)
     u0 = b.updates()
     if pg:
         pg.barrier()
@@ -436,34 +472,48 @@ def run_batch(args):
     if pg:
         pg.barrier()
     ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    b.profile_enable(False)
+    prof = b.profile()
     updates = b.updates() - u0
-    launches = b.profile()["kernel_launches"]
-    value = updates / (ms / 1e3) / 1e9 * world
+    t_s, total_updates = aggregate(pg, ms / 1e3, float(updates), dev)
+    value = total_updates / t_s / 1e9
     peak, peak_kind = measured_peaks()
     st_s = prof["stencil_ms"] / 1e3
-    achieved = upd_prof * 8 / 1e9 / st_s if st_s > 0 else None
+    n_launch = max(prof["stencil_timed"], 1)
+    achieved = prof["stencil_updates"] * 8 / 1e9 / st_s if st_s > 0 else None
     tpu_b = recorded_traffic(ppt, "batch")
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_batch(insts)
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
-            "config": {"workload": "batch of 256 grids (edges 32..192, sphere/torus, constant F in "
-                                   "[-1,1]), band 4h, rebuild/5, 200 steps CFL 0.5",
-                       "total_points": total_pts, "graphs": True,
+            "config": {"workload": "batch of %d grids (edges 32..192, sphere/torus, constant F in "
+                                   "[-1,1]), band 4h, rebuild/5, 200 steps CFL 0.5" % len(insts),
+                       "total_points": total_pts, "graphs": False,
                        "autotuned": {"stages": stages, "grid_pct": pct, "points_per_thread": ppt},
                        "l2": "inputs larger than L2 (phi 2 x 2.3 GB)"},
             "updates_per_step": updates / max(args.steps, 1),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None,
-                         "traffic": (tpu_b * upd_prof / max(prof["stencil_timed"], 1))
+                         "traffic": (tpu_b * prof["stencil_updates"] / n_launch)
                                     if tpu_b is not None else None,
                          "peak_kind": peak_kind, "bytes_per_update": 8,
-                         "kernel": STENCIL_KERNELS.get(ppt, "k_step_f32") + ", batched (eager profiled pass)",
-                         "avg_launch_us": 1e6 * st_s / max(prof["stencil_timed"], 1)},
-            "gpu_launches": launches,
+                         "kernel": STENCIL_KERNELS.get(ppt, "k_step_f32") + ", batched",
+                         "avg_launch_us": 1e6 * st_s / n_launch,
+                         "launches": prof["stencil_launches"], "launches_timed": prof["stencil_timed"],
+                         "timed_runs": "one run of back-to-back stencil launches in %d" % PROFILE_EVERY,
+                         "share_of_step_time": (st_s / n_launch * prof["stencil_launches"] / t_s)
+                                               if t_s > 0 else None},
+            "e2e": None, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": prof["kernel_launches"],
         }), flush=True)
     b.close()
+    if pg:
+        pg.destroy_process_group()
 
 
 def restrict_to(a, factor):

@@ -89,7 +89,13 @@ __device__ __forceinline__ void quads4(const StageZ4& Sg, const float4 (&c)[4],
 }
 
 // FIELD: speed field (else constant per instance); CLASSIFY: fused tube test
-// (Eq. 6); BATCHED: per-entry instance; S: ring stages
+// (Eq. 6); BATCHED: per-entry instance; S: ring stages.  16 warps of up to
+// 128 registers per SM.  (Without a speed field the kernel also fits in 96
+// registers, 21 warps per SM: faster in a short burst, batch of 256 grids
+// 163.3 against 166.6 us per launch, but slower sustained under the power
+// cap, 177.1 against 172.5 us, and 2 % fewer updates per second over the
+// whole run; with a speed field slower either way, 512^3 sphere union 63.4
+// against 59.7 us.)
 template <bool FIELD, bool CLASSIFY, bool BATCHED, int S>
 __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
 {
