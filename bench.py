@@ -190,12 +190,13 @@ STENCIL_KERNELS = {4: "k_step_f32 (128 threads per 8^3 tile, 4 points per thread
                    16: "k_step_f32_z4 (one warp per 8^3 tile, 16 points per thread)"}
 
 
-def recorded_traffic(ppt, workload="sphere-union"):
-    """DRAM bytes per grid-point update of the step kernel with `ppt` points
-    per thread on `workload` from the last ncu capture of that
-    decomposition, if it was taken on the current kernel source (else
-    None).  The records in profiles/stencil_traffic.txt are separated by
-    blank lines; a record without a workload line is the sphere union's."""
+def recorded_traffic(ppt, workload="sphere-union", field="dram_bytes_per_update"):
+    """DRAM bytes per grid-point update (or another recorded `field`) of the
+    step kernel with `ppt` points per thread on `workload` from the last ncu
+    capture of that decomposition, if it was taken on the current kernel
+    source (else None).  The records in profiles/stencil_traffic.txt are
+    separated by blank lines; a record without a workload line is the
+    sphere union's."""
     path = os.path.join(ROOT, "profiles", "stencil_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -214,8 +215,8 @@ def recorded_traffic(ppt, workload="sphere-union"):
     for d in recs:
         if (d.get("stencil_source_sha256_16") == kernel_source_hash()
                 and int(d.get("points_per_thread", "0")) == int(ppt)
-                and d.get("workload", "sphere-union") == workload):
-            return float(d["dram_bytes_per_update"])
+                and d.get("workload", "sphere-union") == workload and field in d):
+            return float(d[field])
     return None
 
 
@@ -1026,6 +1027,10 @@ def main():
                     "peak_kind": peak_kind,
                     "kernel": "k_step_f32<..., OP_REINIT> (Eq. 12 iteration on N over the active tiles)",
                     "bytes_per_update": b_rein, "avg_launch_us": 1e6 * rein_s / n_rein,
+                    # thread instructions per point-iteration of the pass (ncu
+                    # record of the current source; the pass is issue-bound)
+                    "instructions_per_point_iteration":
+                        recorded_traffic(4, "local", "instructions_per_point_iteration"),
                     "launches": prof["reinit_timed"], "point_iterations": rupd,
                     "share_of_step_time": rein_s / t_s if t_s > 0 else None}
         roofline_advance = {"bound": "hbm", "achieved": a_adv, "peak": peak, "unit": "GB/s",
