@@ -91,6 +91,18 @@ __device__ __forceinline__ float rsqrt_hw(float x)
     return r;
 }
 
+// hardware square root (approximate, flush-to-zero; sqrt(0) = 0, so no
+// clamp).  |grad| = sqrt(q) by it instead of q * rsqrt(max(q, 1e-30)) saves a
+// min/max on the ALU pipe and a multiply per point: batch of 256 grids
+// 594 -> 602 GLUPS, local scheme 45.1 -> 46.8, 512^3 sphere union 469.5 ->
+// 470.8 (A/B on one box)
+__device__ __forceinline__ float sqrt_hw(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Programmatic dependent launch: a stencil launch may start while the
 // previous one drains.  Every CTA lets the next grid launch at once (it can
 // only take the slots this grid frees), then waits for the previous grid's
@@ -104,7 +116,7 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // Eq. 3-5 at one point, FP32.  Differences are unscaled (1/h is folded into
 // coef = dt/h).  SGN = +1: every F >= 0 here, G+ of Eq. 4; SGN = -1: every
 // F < 0, G- of Eq. 5; SGN = 0: per point, through G-(phi) = G+(-phi).
-// |grad| = q * rsqrt(q) (q clamped away from 0, where the product is 0).
+// |grad| = sqrt(q) with the hardware square root.
 template <int SGN>
 __device__ __forceinline__ float upd32(float c, float f, float dmx, float dpx, float dmy,
                                        float dpy, float dmz, float dpz, float coef)
@@ -130,7 +142,7 @@ __device__ __forceinline__ float upd32(float c, float f, float dmx, float dpx, f
     q = fmaf(by, by, q);
     q = fmaf(az, az, q);
     q = fmaf(bz, bz, q);
-    const float g = q * rsqrt_hw(fmaxf(q, 1e-30f));
+    const float g = sqrt_hw(q);
     return fmaf(-(coef * f), g, c);
 }
 
@@ -268,7 +280,7 @@ __device__ __forceinline__ float4 rei4(const float4& c, float xm0, float xp3, co
         q = fmaf(by, by, q);
         q = fmaf(az, az, q);
         q = fmaf(bz, bz, q);
-        const float gu = q * rsqrt_hw(fmaxf(q, 1e-30f));
+        const float gu = sqrt_hw(q);
         const float S = d * rsqrt_hw(fmaxf(fmaf(d, d, q), 1e-30f));
         float v = fmaf(-S, fmaf(lp.lam, gu, -lp.dtau_f), d);
         if (CLAMP) v = fminf(fmaxf(v, -lp.gamma_up), lp.gamma_up);
