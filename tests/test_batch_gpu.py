@@ -86,6 +86,47 @@ def test_batch_step_configs_agree(ppt):
         assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("stages,pct", [(2, 100), (4, 50), (6, 100)])
+def test_batch_one_warp_rings_agree(stages, pct):
+    """The one-warp batched stencil (bulk-staged tile blocks and z faces, the
+    entries' instance data loaded a tile after them) computes the 8-point
+    kernel's bits for every ring depth and a partial grid, across rebuilds."""
+    insts = small_batch(count=7, seed=13)
+    outs = []
+    for cfg in ((3, 100, 8), (stages, pct, 16)):
+        b, _ = make_batch(insts)
+        b.set_step_config(*cfg)
+        b.band_rebuild(4.0)
+        b.step(11, 0.5, ls.LS_DT_CFL, 5)
+        outs.append([b.get_phi_i(k) for k in range(len(insts))])
+        b.close()
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("F", [0.7, -0.9])
+def test_single_grid_constant_speed_one_warp_agrees(F):
+    """Single grid, constant speed (the one-warp kernel's variant without
+    speed loads): every ring depth gives the 8-point kernel's bits, the
+    frozen x-face copies included."""
+    w = inputs.SphereUnion(n=48, count=4)
+    p = w.phi().numpy().astype(np.float32)
+    ref = None
+    for cfg in ((3, 100, 8), (2, 100, 16), (4, 75, 16), (6, 50, 16)):
+        g = ls.LevelSet(48, 48, 48, w.h, ls.LS_FP32)
+        g.set_phi(p)
+        g.set_speed_const(F)
+        g.set_step_config(*cfg)
+        g.band_rebuild(4.0)
+        g.step(12, 0.5, ls.LS_DT_CFL, 5)
+        out = g.get_phi()
+        g.close()
+        if ref is None:
+            ref = out
+        else:
+            assert np.array_equal(out, ref), cfg
+
+
 def test_batch_graph_replay_equals_eager():
     insts = small_batch(count=5, seed=9)
     outs = []
