@@ -645,6 +645,7 @@ __global__ void k_set_dt_batch(StepScalars* sc, int n_inst, const Inst* __restri
                                int mode, double value, int finalize, unsigned long long* Mbits,
                                int* inst_count)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_inst) return;
     const Inst& in = d_inst[i];
@@ -927,10 +928,9 @@ cudaError_t launch_scatter_batch(const uint8_t* act, const int* block_offsets, i
 {
     if (prec != 0) return cudaErrorInvalidValue;
     const int nb = (int)((ntiles + 255) / 256);
-    k_scatter_batch<<<nb, 256, 0, s>>>(act, block_offsets, list, list_info, list_inst, tile_sgn,
-                                       d_inst, tile_inst, ntiles, (const float*)tile_maxF, Mbits,
-                                       inst_count, (const uint4*)cur, (uint4*)other);
-    return cudaGetLastError();
+    return launch_after(k_scatter_batch, nb, 256, s, act, block_offsets, list, list_info, list_inst,
+                        tile_sgn, d_inst, tile_inst, ntiles, (const float*)tile_maxF, Mbits, inst_count,
+                        (const uint4*)cur, (uint4*)other);
 }
 
 cudaError_t launch_set_dt_batch(StepScalars* sc, int n_inst, const Inst* d_inst, int mode,
@@ -938,9 +938,8 @@ cudaError_t launch_set_dt_batch(StepScalars* sc, int n_inst, const Inst* d_inst,
                                 int* inst_count, cudaStream_t s)
 {
     (void)prec;
-    k_set_dt_batch<<<(n_inst + 127) / 128, 128, 0, s>>>(sc, n_inst, d_inst, mode, value, finalize,
-                                                       Mbits, inst_count);
-    return cudaGetLastError();
+    return launch_after(k_set_dt_batch, (n_inst + 127) / 128, 128, s, sc, n_inst, d_inst, mode, value,
+                        finalize, Mbits, inst_count);
 }
 
 cudaError_t launch_full_list(int* list, uint8_t* list_info, const uint8_t* tile_sgn,
