@@ -1025,12 +1025,12 @@ def main():
         roofline = {"bound": "hbm", "achieved": a_rein, "peak": peak, "unit": "GB/s",
                     "frac": (a_rein / peak) if a_rein else None, "traffic": None,
                     "peak_kind": peak_kind,
-                    "kernel": "k_step_f32<..., OP_REINIT> (Eq. 12 iteration on N over the active tiles)",
+                    "kernel": "k_step_f32_z2<..., OP_REINIT> (Eq. 12 iteration on N over the tiles holding N points, 8 points per thread)",
                     "bytes_per_update": b_rein, "avg_launch_us": 1e6 * rein_s / n_rein,
                     # thread instructions per point-iteration of the pass (ncu
                     # record of the current source; the pass is issue-bound)
                     "instructions_per_point_iteration":
-                        recorded_traffic(4, "local", "instructions_per_point_iteration"),
+                        recorded_traffic(8, "local", "instructions_per_point_iteration"),
                     "launches": prof["reinit_timed"], "point_iterations": rupd,
                     "share_of_step_time": rein_s / t_s if t_s > 0 else None}
         roofline_advance = {"bound": "hbm", "achieved": a_adv, "peak": peak, "unit": "GB/s",

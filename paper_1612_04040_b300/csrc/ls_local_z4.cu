@@ -6,8 +6,9 @@
 // (ls_stencil.cuh: cut32, upd4, n_nibble, count_breaches) and the N bits keep
 // their layout (bit e of the tile's 512-bit mask = element e), so the
 // results are the same bits; only the per-tile work is spread over 16
-// points.  (The reinitialisation passes stay with 4 points per thread: with
-// one warp per tile they measured 5 % slower.)
+// points.  (The reinitialisation passes take 8 points per thread, the
+// 64-thread kernel of ls_step.cu: with one warp per tile they measured
+// slower.)
 #include <cstddef>
 
 #include "ls_internal.cuh"
