@@ -318,8 +318,11 @@ __global__ void __launch_bounds__(128, 8) k_step_f32(StepArgs a)
 // the plain step, or a reinitialisation pass of the local scheme (Eq. 12 on
 // the points of N, whose 512-bit mask per entry is staged with the tile;
 // the sign classes are voted per warp and quad set, as in the 4-point pass).
+// (the reinitialisation passes: 10 CTAs of up to 102 registers per SM,
+// 37.4 us per pass at 512^3 against 40.2 / 41.5 / 44.5 with 12 / 16 / 20
+// and 38.5 / 37.9 / 38.3 with 8 / 9 / 11)
 template <bool FIELD, bool CLASSIFY, bool BATCHED, int S, int OP = OP_PLAIN>
-__global__ void __launch_bounds__(64, 16) k_step_f32_z2(StepArgs a)
+__global__ void __launch_bounds__(64, OP >= OP_REINIT ? 10 : 16) k_step_f32_z2(StepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using Stage32 = Stage32T<FIELD>;
@@ -605,9 +608,10 @@ cudaError_t launch32_op(const StepArgs& a, int grid_pct, cudaStream_t s)
 }
 
 // the reinitialisation passes (Eq. 12 on the tiles holding N points): 8
-// points per thread, a 2-stage ring (measured: 41.4 us per pass at 512^3
-// against 42.8 with 3 stages, 44.4 with 4, 49.0 for the 4-point kernel with
-// 6, and 53.5 with one warp per tile)
+// points per thread, a 2-stage ring (measured with 16 CTAs per SM: 41.4 us
+// per pass at 512^3 against 42.8 with 3 stages, 44.4 with 4, 49.0 for the
+// 4-point kernel with 6, and 53.5 with one warp per tile; with 10 CTAs per
+// SM 37.4 against 37.6 with 3 stages)
 template <bool CLS, int OP>
 cudaError_t launch_rei_z2(const StepArgs& a, int grid_pct, cudaStream_t s)
 {
