@@ -137,7 +137,7 @@ void free_all(ls_ctx* c)
     }
     for (auto e : c->ev_free) cudaEventDestroy(e);
     void* ptrs[] = {c->phi[0], c->phi[1], c->F, c->tile_maxF, c->tile_sgn, c->staging, c->snapshot, c->core,
-                    c->act, c->list, c->list_info, c->d_count, c->block_counts, c->d_sc,
+                    c->act, c->mark, c->d_leave, c->d_nleave, c->list, c->list_info, c->d_count, c->block_counts, c->d_sc,
                     c->d_Mbits, c->d_updates, c->d_status, c->d_inst,
                     c->d_tile_inst, c->d_list_inst, c->d_inst_count, c->init_params, c->nmask,
                     c->d_breaches, c->list_nact, c->nmask2, c->nflag, c->nl, c->nl_info,
@@ -258,11 +258,39 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
 };
 
+// the incremental rebuild of a batch: the new active set marked from the
+// core entries of the previous list (core is fresh on every entry and 0 on
+// the other tiles), then compacted 16 tiles per thread
+int rebuild_batch_incr(ls_ctx* c, cudaStream_t s)
+{
+    void* cur = c->phi[c->cur];
+    void* other = c->phi[c->cur ^ 1];
+    const void* tmf = speed_mode(c) == 2 ? c->tile_maxF : nullptr;
+    KL(c, lsk::launch_mark_batch(c->list, c->d_count, c->core, c->mark, c->d_inst, c->d_tile_inst,
+                                 c->ntiles, c->dilation, s));
+    KL(c, lsk::launch_mark_count(c->mark, c->ntiles, c->block_counts, c->d_done, c->d_count,
+                                 c->d_nleave, s));
+    KL(c, lsk::launch_mark_scatter(c->mark, c->act, c->ntiles, c->block_counts, c->list, c->d_leave,
+                                   c->d_nleave, s));
+    KL(c, lsk::launch_entry_batch(c->list, c->d_count, c->list_info, c->d_list_inst, sign_table(c),
+                                  c->d_inst, c->d_tile_inst, c->ntiles, tmf, c->prec, c->d_Mbits,
+                                  c->d_inst_count, c->d_leave, c->d_nleave, cur, other, s));
+    KL(c, lsk::launch_set_dt_batch(c->d_sc, c->n_inst, c->d_inst, c->dt_mode, c->dt_value, 1,
+                                   c->prec, c->d_Mbits, c->d_inst_count, s));
+    return LS_OK;
+}
+
 int rebuild(ls_ctx* c, bool full_scan, cudaStream_t s)
 {
     NvtxRange range("ls band rebuild");
     const bool incr = c->band_valid;
     void* cur = c->phi[c->cur];
+    if (c->batched && c->mark && !full_scan && c->core_fresh && c->band_valid && !c->full_domain) {
+        RET(rebuild_batch_incr(c, s));
+        c->core_fresh = false;
+        c->since_rebuild = 0;
+        return LS_OK;
+    }
     if (full_scan || !c->core_fresh) {
         KL(c, lsk::launch_classify_all(cur, c->core, c->dinst(), c->tinst(), c->in0(), c->ntiles,
                                        c->prec, s));
@@ -685,7 +713,10 @@ int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h
     A(dalloc(&c->phi[0], grid_bytes(c)));
     A(dalloc(&c->phi[1], grid_bytes(c)));
     A(dalloc(&c->core, c->ntiles));
-    A(dalloc(&c->act, c->ntiles));
+    // the flag arrays in whole 16-byte chunks (the incremental batch rebuild
+    // reads and writes them 16 tiles at a time)
+    const long long flag_bytes = (c->ntiles + 15) / 16 * 16;
+    A(dalloc(&c->act, flag_bytes));
     A(dalloc(&c->list, c->ntiles * sizeof(int)));
     A(dalloc(&c->list_info, c->ntiles));
     A(dalloc(&c->d_count, sizeof(int)));
@@ -710,10 +741,14 @@ int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h
         A(dalloc(&c->d_tile_inst, sizeof(uint16_t) * c->ntiles));
         A(dalloc(&c->d_list_inst, sizeof(uint16_t) * c->ntiles));
         A(dalloc(&c->d_inst_count, sizeof(int) * n));
+        A(dalloc(&c->mark, flag_bytes));
+        A(dalloc(&c->d_leave, c->ntiles * sizeof(int)));
+        A(dalloc(&c->d_nleave, sizeof(int)));
     }
     if (e == cudaSuccess) {
         A(cudaMemset(c->core, 0, c->ntiles));
-        A(cudaMemset(c->act, 0, c->ntiles));
+        A(cudaMemset(c->act, 0, flag_bytes));
+        if (batched) A(cudaMemset(c->mark, 0, flag_bytes));
         A(cudaMemset(c->d_count, 0, sizeof(int)));
         A(cudaMemset(c->d_sc, 0, sizeof(lsk::StepScalars) * n));
         A(cudaMemset(c->d_Mbits, 0, sizeof(unsigned long long) * n));

@@ -640,6 +640,217 @@ __global__ void __launch_bounds__(256) k_scatter_batch(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Incremental rebuild of a batch.  When the steps since the previous rebuild
+// ran the fused tube test, core is fresh on every entry of the list and 0 on
+// every other tile (a tile whose core flag is set is active), so the new
+// active set -- the one-tile dilation of core (Eq. 11 cover) -- is marked
+// from the core entries of the previous list alone, and only the
+// compaction walks every tile, 16 flag bytes per thread:
+//   k_mark_batch     marks[t] = 1 for the neighbourhood of each core entry
+//   k_mark_count     per-block counts of the marks, scanned by the last block
+//   k_mark_scatter   the ascending list ids, act = new | old << 1, marks
+//                    cleared, the ids of the tiles leaving the set
+//   k_entry_batch    per entry: info byte, instance, per-instance count and
+//                    max |F|; the leaving tiles' copies (then k_set_dt_batch
+//                    as after the full scatter)
+// The list, act and the counts equal those of k_dilate + k_scatter_batch.
+
+// 1 for each byte (0..15) of v whose bit 0 is set, packed into bits 0..15
+__device__ __forceinline__ unsigned byte_bits16(const uint4& v)
+{
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+    unsigned r = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        unsigned x = w[k] & 0x01010101u;   // bits 0, 8, 16, 24
+        x |= x >> 7;                       // bytes 0, 1 -> bits 0, 1; bytes 2, 3 -> bits 16, 17
+        x = (x | (x >> 14)) & 0xFu;        // bits 16, 17 -> bits 2, 3
+        r |= x << (4 * k);
+    }
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_mark_batch(const int* __restrict__ list,
+                                                    const int* __restrict__ count,
+                                                    const uint8_t* __restrict__ core,
+                                                    uint8_t* mark, const Inst* __restrict__ d_inst,
+                                                    const uint16_t* __restrict__ tile_inst, int conn)
+{
+    pdl_wait();
+    const int n = *count;
+    const bool all26 = conn != 6;
+    for (int k = blockIdx.x * 256 + threadIdx.x; k < n; k += gridDim.x * 256) {
+        const int t = __ldg(list + k);
+        if (!__ldg(core + t)) continue;
+        const Inst& in = d_inst[__ldg(tile_inst + t)];
+        const int loc = (int)(t - in.tile_base);
+        const int tpl = in.tnx * in.tny;
+        const int tz = loc / tpl;
+        const int rem = loc - tz * tpl;
+        const int ty = rem / in.tnx, tx = rem - ty * in.tnx;
+        const bool ex[3] = {tx > 0, true, tx < in.tnx - 1};
+        const bool ey[3] = {ty > 0, true, ty < in.tny - 1};
+        const bool ez[3] = {tz > 0, true, tz < in.tnz - 1};
+        uint8_t* mt = mark + t;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                uint8_t* row = mt + (long long)dz * tpl + (long long)dy * in.tnx;
+                const bool vzy = ez[dz + 1] && ey[dy + 1];
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const bool face = abs(dx) + abs(dy) + abs(dz) <= 1;
+                    if (vzy && ex[dx + 1] && (face || all26)) row[dx] = 1;
+                }
+            }
+        }
+    }
+}
+
+// one thread per 16 tiles (nchunks = ceil(ntiles / 16); the flag arrays are
+// padded with zero bytes to whole chunks)
+__global__ void __launch_bounds__(256) k_mark_count(const uint4* __restrict__ mark, long long nchunks,
+                                                    int* block_counts, unsigned* done, int* total,
+                                                    int* nleave)
+{
+    __shared__ int warp_cnt[8];
+    pdl_wait();
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (i == 0) *nleave = 0;
+    int cnt = 0;
+    if (i < nchunks) cnt = __popc(byte_bits16(mark[i]));
+    const int ws = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane_id() == 0) warp_cnt[threadIdx.x >> 5] = ws;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int k = 0; k < 8; ++k) s += warp_cnt[k];
+        block_counts[blockIdx.x] = s;
+    }
+    if (last_block(done)) block_scan256(block_counts, (int)gridDim.x, total);
+}
+
+// exclusive prefix over the block of v (each thread's value <= 16), and the
+// block's total
+__device__ __forceinline__ int block_excl256(int v, int* warp_tot, int& total)
+{
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane_id() >= o) inc += u;
+    }
+    if (lane_id() == 31) warp_tot[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    int before = 0;
+    total = 0;
+    for (int k = 0; k < 8; ++k) {
+        if (k < (int)(threadIdx.x >> 5)) before += warp_tot[k];
+        total += warp_tot[k];
+    }
+    return before + inc - v;
+}
+
+__global__ void __launch_bounds__(256) k_mark_scatter(uint4* mark, uint4* act, long long nchunks,
+                                                      const int* __restrict__ offsets, int* list,
+                                                      int* leave, int* nleave)
+{
+    __shared__ int warp_a[8];
+    __shared__ int warp_b[8];
+    __shared__ int leave_base;
+    pdl_wait();
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    uint4 m = make_uint4(0u, 0u, 0u, 0u), a = m;
+    if (i < nchunks) {
+        m = mark[i];
+        a = act[i];
+    }
+    const unsigned nw = byte_bits16(m);            // active after this rebuild
+    const unsigned ol = byte_bits16(a);            // active before it
+    const unsigned lv = ol & ~nw;                  // leaving the set
+    int ltotal = 0, dummy = 0;
+    int pos = block_excl256(__popc(nw), warp_a, dummy) + offsets[blockIdx.x];
+    int lpos = block_excl256(__popc(lv), warp_b, ltotal);
+    const int t0 = (int)(i * 16);
+    for (unsigned b = nw; b; b &= b - 1u) list[pos++] = t0 + __ffs(b) - 1;
+    if (i < nchunks) {
+        const uint4 o = make_uint4(m.x | ((a.x & 0x01010101u) << 1), m.y | ((a.y & 0x01010101u) << 1),
+                                   m.z | ((a.z & 0x01010101u) << 1), m.w | ((a.w & 0x01010101u) << 1));
+        act[i] = o;
+        mark[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // the leaving tiles (in any order): copied by the whole next grid, a
+    // block holds too many of them to copy them itself
+    if (ltotal == 0) return;
+    if (threadIdx.x == 0) leave_base = atomicAdd(nleave, ltotal);
+    __syncthreads();
+    lpos += leave_base;
+    for (unsigned b = lv; b; b &= b - 1u) leave[lpos++] = t0 + __ffs(b) - 1;
+}
+
+// per list entry (ascending): the info byte and instance of the entry, the
+// per-instance active counts and max |F| (as k_scatter_batch)
+__global__ void __launch_bounds__(256) k_entry_batch(const int* __restrict__ list,
+                                                     const int* __restrict__ count,
+                                                     uint8_t* list_info, uint16_t* list_inst,
+                                                     const uint8_t* __restrict__ tile_sgn,
+                                                     const Inst* __restrict__ d_inst,
+                                                     const uint16_t* __restrict__ tile_inst,
+                                                     const float* __restrict__ tile_maxF,
+                                                     unsigned long long* Mbits, int* inst_count,
+                                                     const int* __restrict__ leave,
+                                                     const int* __restrict__ nleave,
+                                                     const uint4* __restrict__ cur,
+                                                     uint4* __restrict__ other)
+{
+    pdl_wait();
+    const int n = *count;
+    // the tiles leaving the active set keep their values in both buffers:
+    // 128 16-byte words per tile, four independent copies in flight per thread
+    {
+        constexpr int VEC = TILE_PTS * 4 / 16;
+        const long long total = (long long)*nleave * VEC;
+        const long long nthr = (long long)gridDim.x * 256;
+        for (long long j = (long long)blockIdx.x * 256 + threadIdx.x; j < total; j += 4 * nthr) {
+            uint4 v[4];
+            size_t off[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long jj = j + u * nthr;
+                off[u] = jj < total ? (size_t)__ldg(leave + jj / VEC) * VEC + (size_t)(jj % VEC) : 0;
+                if (jj < total) v[u] = cur[off[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j + u * nthr < total) other[off[u]] = v[u];
+        }
+    }
+    // every thread of a block runs the same number of rounds (warp-wide
+    // match / reduce below)
+    for (int base = blockIdx.x * 256; base < n; base += gridDim.x * 256) {
+        const int k = base + threadIdx.x;
+        const bool on = k < n;
+        const int t = on ? list[k] : 0;
+        const unsigned inst = on ? (unsigned)__ldg(tile_inst + t) : 0xffffu;
+        const unsigned key = on ? inst : 0x10000u + lane_id();
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const unsigned mbits = (on && tile_maxF) ? __float_as_uint(__ldg(tile_maxF + t)) : 0u;
+        const unsigned gmax = __reduce_max_sync(grp, mbits);
+        if (on && (__ffs(grp) - 1) == (int)lane_id()) {
+            atomicAdd(&inst_count[inst], __popc(grp));
+            if (tile_maxF && gmax) atomicMax(&Mbits[inst], (unsigned long long)gmax);
+        }
+        if (on) {
+            const Inst& in = d_inst[inst];
+            const unsigned sg = tile_sgn ? tile_sgn[t] : (in.Fc >= 0.0 ? SG_POS : SG_NEG);
+            list_info[k] = (uint8_t)(nb_bits(t, in) | sg);
+            list_inst[k] = (uint16_t)inst;
+        }
+    }
+}
+
 // per-instance dt (one thread per instance)
 __global__ void k_set_dt_batch(StepScalars* sc, int n_inst, const Inst* __restrict__ d_inst,
                                int mode, double value, int finalize, unsigned long long* Mbits,
@@ -930,6 +1141,61 @@ cudaError_t launch_scatter_batch(const uint8_t* act, const int* block_offsets, i
     const int nb = (int)((ntiles + 255) / 256);
     return launch_after(k_scatter_batch, nb, 256, s, act, block_offsets, list, list_info, list_inst,
                         tile_sgn, d_inst, tile_inst, ntiles, (const float*)tile_maxF, Mbits, inst_count,
+                        (const uint4*)cur, (uint4*)other);
+}
+
+static int band_sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    return sms;
+}
+
+cudaError_t launch_mark_batch(const int* list, const int* count, const uint8_t* core, uint8_t* mark,
+                              const Inst* d_inst, const uint16_t* tile_inst, long long ntiles,
+                              int conn, cudaStream_t s)
+{
+    long long nb = (ntiles + 255) / 256;
+    if (nb > 8LL * band_sm_count()) nb = 8LL * band_sm_count();
+    return launch_after(k_mark_batch, (int)nb, 256, s, list, count, core, mark, d_inst, tile_inst, conn);
+}
+
+int mark_chunk_blocks(long long ntiles) { return (int)((ntiles + 4095) / 4096); }
+
+cudaError_t launch_mark_count(const uint8_t* mark, long long ntiles, int* block_counts,
+                              unsigned* done, int* count, int* nleave, cudaStream_t s)
+{
+    const long long nchunks = (ntiles + 15) / 16;
+    return launch_after(k_mark_count, mark_chunk_blocks(ntiles), 256, s, (const uint4*)mark, nchunks,
+                        block_counts, done, count, nleave);
+}
+
+cudaError_t launch_mark_scatter(uint8_t* mark, uint8_t* act, long long ntiles,
+                                const int* block_offsets, int* list, int* leave, int* nleave,
+                                cudaStream_t s)
+{
+    const long long nchunks = (ntiles + 15) / 16;
+    return launch_after(k_mark_scatter, mark_chunk_blocks(ntiles), 256, s, (uint4*)mark, (uint4*)act,
+                        nchunks, block_offsets, list, leave, nleave);
+}
+
+cudaError_t launch_entry_batch(const int* list, const int* count, uint8_t* list_info,
+                               uint16_t* list_inst, const uint8_t* tile_sgn, const Inst* d_inst,
+                               const uint16_t* tile_inst, long long ntiles, const void* tile_maxF,
+                               int prec, unsigned long long* Mbits, int* inst_count,
+                               const int* leave, const int* nleave, const void* cur, void* other,
+                               cudaStream_t s)
+{
+    if (prec != 0) return cudaErrorInvalidValue;
+    long long nb = (ntiles + 255) / 256;
+    if (nb > 8LL * band_sm_count()) nb = 8LL * band_sm_count();
+    return launch_after(k_entry_batch, (int)nb, 256, s, list, count, list_info, list_inst, tile_sgn,
+                        d_inst, tile_inst, (const float*)tile_maxF, Mbits, inst_count, leave, nleave,
                         (const uint4*)cur, (uint4*)other);
 }
 

@@ -84,7 +84,10 @@ struct ls_ctx {
     double* init_params = nullptr;  // device copy of Step 0 shape / speed parameters
     int init_params_cap = 0;
     uint8_t* core = nullptr;
-    uint8_t* act = nullptr;
+    uint8_t* act = nullptr;       // bit 0: active, bit 1: active before the last rebuild
+    uint8_t* mark = nullptr;      // batched: new-active marks of the incremental rebuild (0 between)
+    int* d_leave = nullptr;       // batched: ids of the tiles leaving the set at a rebuild
+    int* d_nleave = nullptr;
     int* list = nullptr;
     uint8_t* list_info = nullptr;
     int* d_count = nullptr;

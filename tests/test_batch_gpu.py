@@ -104,6 +104,39 @@ def test_batch_one_warp_rings_agree(stages, pct):
         assert np.array_equal(a, c)
 
 
+def test_batch_incremental_rebuild_equals_full_scan():
+    """The periodic rebuild of a batch marks the new band from the core
+    entries of the previous list; on the full-size batch (256 grids of
+    32^3..192^3, 1.12 M tiles) it gives the list, the dt and, one step
+    later, the bits that a rebuild scanning every tile gives on the same
+    state (the leaving tiles' copies into the other buffer included)."""
+    dev = torch.device("cuda")
+    insts = inputs.batch_instances()
+    runs = []
+    for full in (False, True):
+        b = ls.Batch([i.edge for i in insts], [i.h for i in insts])
+        for k, it in enumerate(insts):
+            b.set_phi_i(k, it.phi(device=dev).to(torch.float32).contiguous())
+            b.set_speed_const_i(k, it.speed)
+        b.band_rebuild(4.0)
+        # 35 steps: the last periodic rebuild before step 30, the tube
+        # test at step 35
+        b.step(35, 0.5, ls.LS_DT_CFL, 5)
+        if full:
+            b.band_rebuild(4.0)            # every tile classified and scanned
+        b.step(1, 0.5, ls.LS_DT_CFL, 5)    # incremental rebuild first when not
+        runs.append(([b.active_tiles_i(k) for k in range(len(insts))],
+                     [b.last_dt_i(k) for k in range(len(insts))],
+                     [torch.from_numpy(b.get_phi_i(k)) for k in range(len(insts))]))
+        b.close()
+    (la, da, pa), (lb, db, pb) = runs
+    assert sum(len(x) for x in la) > 100000
+    for k in range(len(insts)):
+        assert np.array_equal(la[k], lb[k]), k
+        assert da[k] == db[k], k
+        assert torch.equal(pa[k], pb[k]), k
+
+
 @pytest.mark.parametrize("F", [0.7, -0.9])
 def test_single_grid_constant_speed_one_warp_agrees(F):
     """Single grid, constant speed (the one-warp kernel's variant without
