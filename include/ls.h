@@ -211,6 +211,28 @@ int ls_band_breaches(ls_ctx *ctx, unsigned long long *n);
  * its edge sooner).  Marks the band stale.  Errors: LS_EINVAL. */
 int ls_set_dilation(ls_ctx *ctx, int neighbours);
 
+/* How ls_step's periodic band rebuild (section 1.1: the tube T of Eq. 6
+ * dilated by one tile, which covers N of Eq. 11) is computed when the step
+ * before it ran the fused tube test on every active tile:
+ *   LS_REBUILD_FULL         the dilation and the compaction each walk every
+ *                           tile of the context (two launches);
+ *   LS_REBUILD_INCREMENTAL  the dilation is marked from the core entries of
+ *                           the previous active list (a core tile is always
+ *                           active, so no other tile can be core), and only
+ *                           the compaction reads every tile's flags, 16 per
+ *                           thread (four launches);
+ *   LS_REBUILD_AUTO         (default) incremental for contexts of at least
+ *                           LS_REBUILD_AUTO_TILES tiles, else full (measured:
+ *                           at 2^18 tiles the full walk is the faster, at
+ *                           1.1 M and 2^21 tiles the incremental).
+ * Both give the same list, flags, M, dt and values.  ls_band_rebuild, the
+ * first rebuild after any change of state, full-domain mode and slab
+ * contexts with ghost rows always walk every tile.  Clears the cached step
+ * graphs.  Errors: LS_EINVAL (NULL context, unknown mode). */
+enum { LS_REBUILD_AUTO = 0, LS_REBUILD_FULL = 1, LS_REBUILD_INCREMENTAL = 2 };
+#define LS_REBUILD_AUTO_TILES (1 << 19)
+int ls_set_rebuild_mode(ls_ctx *ctx, int mode);
+
 /* ---------------------------------------------------------------------
  * Slab split along z (section 2: the grid is decomposed by one axis, each
  * part with a ghost layer from each neighbour; the tube's rows are shared

@@ -258,25 +258,35 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
 };
 
-// the incremental rebuild of a batch: the new active set marked from the
-// core entries of the previous list (core is fresh on every entry and 0 on
-// the other tiles), then compacted 16 tiles per thread
-int rebuild_batch_incr(ls_ctx* c, cudaStream_t s)
+// the incremental rebuild: the new active set marked from the core entries
+// of the previous list (core is fresh on every entry and 0 on the other
+// tiles), then compacted 16 tiles per thread; the list, the flags, the
+// frozen x-face bits, M and dt are those of the full scan
+int rebuild_incr(ls_ctx* c, bool incr, cudaStream_t s)
 {
     void* cur = c->phi[c->cur];
     void* other = c->phi[c->cur ^ 1];
     const void* tmf = speed_mode(c) == 2 ? c->tile_maxF : nullptr;
-    KL(c, lsk::launch_mark_batch(c->list, c->d_count, c->core, c->mark, c->d_inst, c->d_tile_inst,
-                                 c->ntiles, c->dilation, s));
+    KL(c, lsk::launch_mark(c->list, c->d_count, c->core, c->mark, c->dinst(), c->tinst(), c->in0(),
+                           c->ntiles, c->dilation, s));
     KL(c, lsk::launch_mark_count(c->mark, c->ntiles, c->block_counts, c->d_done, c->d_count,
                                  c->d_nleave, s));
     KL(c, lsk::launch_mark_scatter(c->mark, c->act, c->ntiles, c->block_counts, c->list, c->d_leave,
                                    c->d_nleave, s));
-    KL(c, lsk::launch_entry_batch(c->list, c->d_count, c->list_info, c->d_list_inst, sign_table(c),
-                                  c->d_inst, c->d_tile_inst, c->ntiles, tmf, c->prec, c->d_Mbits,
-                                  c->d_inst_count, c->d_leave, c->d_nleave, cur, other, s));
-    KL(c, lsk::launch_set_dt_batch(c->d_sc, c->n_inst, c->d_inst, c->dt_mode, c->dt_value, 1,
-                                   c->prec, c->d_Mbits, c->d_inst_count, s));
+    if (c->batched) {
+        KL(c, lsk::launch_entry_batch(c->list, c->d_count, c->list_info, c->d_list_inst, sign_table(c),
+                                      c->d_inst, c->d_tile_inst, c->ntiles, tmf, c->prec, c->d_Mbits,
+                                      c->d_inst_count, c->d_leave, c->d_nleave, cur, other, s));
+        KL(c, lsk::launch_set_dt_batch(c->d_sc, c->n_inst, c->d_inst, c->dt_mode, c->dt_value, 1,
+                                       c->prec, c->d_Mbits, c->d_inst_count, s));
+    } else {
+        const int xmode = c->xface ? (incr && !c->xface_pending ? 2 : 1) : 0;
+        KL(c, lsk::launch_entry_single(c->list, c->d_count, c->list_info, c->act, sign_table(c),
+                                       const_sign_bits(c), c->in0(), c->ntiles, tmf, c->prec,
+                                       c->d_Mbits, c->list_nact, xmode, c->d_leave, c->d_nleave, cur,
+                                       other, c->d_sc, c->dt_mode, c->dt_value, c->d_done + 1, s));
+        c->xface_pending = xmode != 0;
+    }
     return LS_OK;
 }
 
@@ -285,8 +295,11 @@ int rebuild(ls_ctx* c, bool full_scan, cudaStream_t s)
     NvtxRange range("ls band rebuild");
     const bool incr = c->band_valid;
     void* cur = c->phi[c->cur];
-    if (c->batched && c->mark && !full_scan && c->core_fresh && c->band_valid && !c->full_domain) {
-        RET(rebuild_batch_incr(c, s));
+    const bool incr_mode = c->rebuild_mode == LS_REBUILD_INCREMENTAL ||
+                           (c->rebuild_mode == LS_REBUILD_AUTO && c->ntiles >= LS_REBUILD_AUTO_TILES);
+    if (incr_mode && !full_scan && c->core_fresh && c->band_valid && !c->full_domain &&
+        (c->batched || c->in0().ghost == 0)) {
+        RET(rebuild_incr(c, incr, s));
         c->core_fresh = false;
         c->since_rebuild = 0;
         return LS_OK;
@@ -725,6 +738,9 @@ int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h
     if (e == cudaSuccess) e = cudaMemset(c->d_updates2, 0, sizeof(unsigned long long));
     A(dalloc(&c->d_updates_timed, sizeof(unsigned long long)));
     if (e == cudaSuccess) e = cudaMemset(c->d_updates_timed, 0, sizeof(unsigned long long));
+    A(dalloc(&c->mark, flag_bytes));
+    A(dalloc(&c->d_leave, c->ntiles * sizeof(int)));
+    A(dalloc(&c->d_nleave, sizeof(int)));
     if (!batched && precision == LS_FP32) A(dalloc(&c->list_nact, c->ntiles));
     if (!batched && precision == LS_FP32)
         A(dalloc(&c->xface, (size_t)c->ntiles * lsk::XFACE_FLOATS * sizeof(float)));
@@ -741,14 +757,11 @@ int make_ctx(int n, const int* nx, const int* ny, const int* nz, const double* h
         A(dalloc(&c->d_tile_inst, sizeof(uint16_t) * c->ntiles));
         A(dalloc(&c->d_list_inst, sizeof(uint16_t) * c->ntiles));
         A(dalloc(&c->d_inst_count, sizeof(int) * n));
-        A(dalloc(&c->mark, flag_bytes));
-        A(dalloc(&c->d_leave, c->ntiles * sizeof(int)));
-        A(dalloc(&c->d_nleave, sizeof(int)));
     }
     if (e == cudaSuccess) {
         A(cudaMemset(c->core, 0, c->ntiles));
         A(cudaMemset(c->act, 0, flag_bytes));
-        if (batched) A(cudaMemset(c->mark, 0, flag_bytes));
+        A(cudaMemset(c->mark, 0, flag_bytes));
         A(cudaMemset(c->d_count, 0, sizeof(int)));
         A(cudaMemset(c->d_sc, 0, sizeof(lsk::StepScalars) * n));
         A(cudaMemset(c->d_Mbits, 0, sizeof(unsigned long long) * n));
@@ -1632,6 +1645,15 @@ int ls_set_scheme(ls_ctx* c, int scheme, double beta_in_h, int reinit_iters, dou
     c->beta_in_h = beta_in_h;
     c->reinit_iters = reinit_iters;
     c->dtau_in_h = dtau_in_h;
+    clear_graphs(c);
+    return LS_OK;
+}
+
+int ls_set_rebuild_mode(ls_ctx* c, int mode)
+{
+    if (!c || (mode != LS_REBUILD_AUTO && mode != LS_REBUILD_FULL && mode != LS_REBUILD_INCREMENTAL))
+        return LS_EINVAL;
+    c->rebuild_mode = mode;
     clear_graphs(c);
     return LS_OK;
 }

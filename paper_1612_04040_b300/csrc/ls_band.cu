@@ -641,20 +641,24 @@ __global__ void __launch_bounds__(256) k_scatter_batch(
 }
 
 // ---------------------------------------------------------------------------
-// Incremental rebuild of a batch.  When the steps since the previous rebuild
+// Incremental rebuild.  When the steps since the previous rebuild
 // ran the fused tube test, core is fresh on every entry of the list and 0 on
 // every other tile (a tile whose core flag is set is active), so the new
 // active set -- the one-tile dilation of core (Eq. 11 cover) -- is marked
 // from the core entries of the previous list alone, and only the
 // compaction walks every tile, 16 flag bytes per thread:
-//   k_mark_batch     marks[t] = 1 for the neighbourhood of each core entry
+//   k_mark           marks[t] = 1 for the neighbourhood of each core entry
 //   k_mark_count     per-block counts of the marks, scanned by the last block
 //   k_mark_scatter   the ascending list ids, act = new | old << 1, marks
 //                    cleared, the ids of the tiles leaving the set
 //   k_entry_batch    per entry: info byte, instance, per-instance count and
 //                    max |F|; the leaving tiles' copies (then k_set_dt_batch
 //                    as after the full scatter)
-// The list, act and the counts equal those of k_dilate + k_scatter_batch.
+//   k_entry_single   single grid: per entry the info byte, the active /
+//                    frozen-face byte, max |F|; the leaving tiles' copies;
+//                    dt in the last block (as k_scatter)
+// The list, act, the counts and dt equal those of k_dilate + k_scatter /
+// k_scatter_batch.
 
 // 1 for each byte (0..15) of v whose bit 0 is set, packed into bits 0..15
 __device__ __forceinline__ unsigned byte_bits16(const uint4& v)
@@ -671,11 +675,12 @@ __device__ __forceinline__ unsigned byte_bits16(const uint4& v)
     return r;
 }
 
-__global__ void __launch_bounds__(256) k_mark_batch(const int* __restrict__ list,
-                                                    const int* __restrict__ count,
-                                                    const uint8_t* __restrict__ core,
-                                                    uint8_t* mark, const Inst* __restrict__ d_inst,
-                                                    const uint16_t* __restrict__ tile_inst, int conn)
+__global__ void __launch_bounds__(256) k_mark(const int* __restrict__ list,
+                                              const int* __restrict__ count,
+                                              const uint8_t* __restrict__ core, uint8_t* mark,
+                                              const Inst* __restrict__ d_inst,
+                                              const uint16_t* __restrict__ tile_inst, Inst single,
+                                              int conn)
 {
     pdl_wait();
     const int n = *count;
@@ -683,7 +688,7 @@ __global__ void __launch_bounds__(256) k_mark_batch(const int* __restrict__ list
     for (int k = blockIdx.x * 256 + threadIdx.x; k < n; k += gridDim.x * 256) {
         const int t = __ldg(list + k);
         if (!__ldg(core + t)) continue;
-        const Inst& in = d_inst[__ldg(tile_inst + t)];
+        const Inst& in = tile_inst ? d_inst[__ldg(tile_inst + t)] : single;
         const int loc = (int)(t - in.tile_base);
         const int tpl = in.tnx * in.tny;
         const int tz = loc / tpl;
@@ -849,6 +854,93 @@ __global__ void __launch_bounds__(256) k_entry_batch(const int* __restrict__ lis
             list_inst[k] = (uint16_t)inst;
         }
     }
+}
+
+// copies of the leaving tiles (ids in leave[0 .. *nleave)) from cur into
+// other, spread over the whole grid: four independent 16-byte copies in
+// flight per thread
+template <int VEC>
+__device__ __forceinline__ void copy_leaving(const int* __restrict__ leave, const int* __restrict__ nleave,
+                                             const uint4* __restrict__ cur, uint4* __restrict__ other)
+{
+    const long long total = (long long)*nleave * VEC;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < total; j += 4 * nthr) {
+        uint4 v[4];
+        size_t off[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long jj = j + u * nthr;
+            off[u] = jj < total ? (size_t)__ldg(leave + jj / VEC) * VEC + (size_t)(jj % VEC) : 0;
+            if (jj < total) v[u] = cur[off[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (j + u * nthr < total) other[off[u]] = v[u];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_entry_single(
+    const int* __restrict__ list, const int* __restrict__ count, uint8_t* list_info,
+    const uint8_t* __restrict__ act, const uint8_t* __restrict__ tile_sgn, unsigned const_sgn,
+    Inst single, const T* __restrict__ tile_maxF, unsigned long long* Mbits, uint8_t* list_nact,
+    int xface_mode, const int* __restrict__ leave, const int* __restrict__ nleave,
+    const uint4* __restrict__ cur, uint4* __restrict__ other, StepScalars* sc, int dt_mode,
+    double dt_value, unsigned* done)
+{
+    __shared__ unsigned long long warp_max[8];
+    pdl_wait();
+    const int n = *count;
+    copy_leaving<TILE_PTS * (int)sizeof(T) / 16>(leave, nleave, cur, other);
+    const long long tpl = (long long)single.tnx * single.tny;
+    unsigned long long mb = 0;
+    for (int k = blockIdx.x * 256 + threadIdx.x; k < n; k += gridDim.x * 256) {
+        const int t = list[k];
+        const unsigned nb = nb_bits(t, single);
+        const unsigned sgn = tile_sgn ? (unsigned)tile_sgn[t] : const_sgn;
+        if (tile_maxF) {
+            const unsigned long long u = ordered_bits(tile_maxF[t]);
+            mb = u > mb ? u : mb;
+        }
+        list_info[k] = (uint8_t)(nb | sgn);
+        if (list_nact) {
+            // act: bit 0 active now, bit 1 active before this rebuild
+            unsigned nf[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+            if (nb & NB_XM) nf[0] = act[t - 1];
+            if (nb & NB_XP) nf[1] = act[t + 1];
+            if (nb & NB_YM) nf[2] = act[t - single.tnx];
+            if (nb & NB_YP) nf[3] = act[t + single.tnx];
+            if (nb & NB_ZM) nf[4] = act[t - tpl];
+            if (nb & NB_ZP) nf[5] = act[t + tpl];
+            const unsigned fl = act[t];
+            unsigned an = 0u;
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                if (nf[q] & 1u) an |= 1u << q;  // NB_XM, NB_XP, NB_YM, NB_YP, NB_ZM, NB_ZP
+            const unsigned fz = nb & ~an;
+            const bool was = xface_mode == 2 && (fl & 2u);
+            if (xface_mode && (fz & NB_XM) && !(was && !(nf[0] & 2u))) an |= NACT_FILL_XM;
+            if (xface_mode && (fz & NB_XP) && !(was && !(nf[1] & 2u))) an |= NACT_FILL_XP;
+            list_nact[k] = (uint8_t)an;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = u > mb ? u : mb;
+    }
+    if (lane_id() == 0) warp_max[threadIdx.x >> 5] = mb;
+    __syncthreads();
+    if (threadIdx.x == 0 && tile_maxF) {
+        unsigned long long m = 0;
+        for (int q = 0; q < 8; ++q) m = warp_max[q] > m ? warp_max[q] : m;
+        if (m) atomicMax(Mbits, m);
+    }
+    // the last block has every block's max |F| bits: the step's dt
+    if (last_block(done) && threadIdx.x == 0)
+        set_dt_one(sc, 0, single, dt_mode, dt_value, 1, sizeof(T) == 4 ? 0 : 1, Mbits,
+                   (long long)__ldcg(count));
 }
 
 // per-instance dt (one thread per instance)
@@ -1156,13 +1248,32 @@ static int band_sm_count()
     return sms;
 }
 
-cudaError_t launch_mark_batch(const int* list, const int* count, const uint8_t* core, uint8_t* mark,
-                              const Inst* d_inst, const uint16_t* tile_inst, long long ntiles,
-                              int conn, cudaStream_t s)
+cudaError_t launch_mark(const int* list, const int* count, const uint8_t* core, uint8_t* mark,
+                        const Inst* d_inst, const uint16_t* tile_inst, const Inst& single,
+                        long long ntiles, int conn, cudaStream_t s)
 {
     long long nb = (ntiles + 255) / 256;
     if (nb > 8LL * band_sm_count()) nb = 8LL * band_sm_count();
-    return launch_after(k_mark_batch, (int)nb, 256, s, list, count, core, mark, d_inst, tile_inst, conn);
+    return launch_after(k_mark, (int)nb, 256, s, list, count, core, mark, d_inst, tile_inst, single, conn);
+}
+
+cudaError_t launch_entry_single(const int* list, const int* count, uint8_t* list_info,
+                                const uint8_t* act, const uint8_t* tile_sgn, unsigned const_sgn,
+                                const Inst& single, long long ntiles, const void* tile_maxF, int prec,
+                                unsigned long long* Mbits, uint8_t* list_nact, int xface_mode,
+                                const int* leave, const int* nleave, const void* cur, void* other,
+                                StepScalars* sc, int dt_mode, double dt_value, unsigned* done,
+                                cudaStream_t s)
+{
+    long long nb = (ntiles + 255) / 256;
+    if (nb > 8LL * band_sm_count()) nb = 8LL * band_sm_count();
+    if (prec == 0)
+        return launch_after(k_entry_single<float>, (int)nb, 256, s, list, count, list_info, act, tile_sgn,
+                            const_sgn, single, (const float*)tile_maxF, Mbits, list_nact, xface_mode,
+                            leave, nleave, (const uint4*)cur, (uint4*)other, sc, dt_mode, dt_value, done);
+    return launch_after(k_entry_single<double>, (int)nb, 256, s, list, count, list_info, act, tile_sgn,
+                        const_sgn, single, (const double*)tile_maxF, Mbits, list_nact, xface_mode,
+                        leave, nleave, (const uint4*)cur, (uint4*)other, sc, dt_mode, dt_value, done);
 }
 
 int mark_chunk_blocks(long long ntiles) { return (int)((ntiles + 4095) / 4096); }

@@ -85,8 +85,8 @@ struct ls_ctx {
     int init_params_cap = 0;
     uint8_t* core = nullptr;
     uint8_t* act = nullptr;       // bit 0: active, bit 1: active before the last rebuild
-    uint8_t* mark = nullptr;      // batched: new-active marks of the incremental rebuild (0 between)
-    int* d_leave = nullptr;       // batched: ids of the tiles leaving the set at a rebuild
+    uint8_t* mark = nullptr;      // new-active marks of the incremental rebuild (0 between)
+    int* d_leave = nullptr;       // ids of the tiles leaving the set at an incremental rebuild
     int* d_nleave = nullptr;
     int* list = nullptr;
     uint8_t* list_info = nullptr;
@@ -111,6 +111,7 @@ struct ls_ctx {
     int since_rebuild = 0;
     int dir = 0;                  // traversal direction of the next stencil launch
     int dilation = 26;            // band dilation: 26 or 6 face neighbours
+    int rebuild_mode = 0;         // LS_REBUILD_AUTO / _FULL / _INCREMENTAL
     int dt_mode = LS_DT_FIXED;
     double dt_value = 0.0;
     lsk::StepConfig cfg;

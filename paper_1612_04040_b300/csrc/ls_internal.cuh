@@ -249,16 +249,16 @@ cudaError_t launch_scatter_batch(const uint8_t* act, const int* block_offsets, i
                                  int* inst_count, const void* cur, void* other, cudaStream_t s);
 // per-instance dt from per-instance M (finalize: from Mbits / |Fc| and the
 // per-instance active counts, then clear both)
-// incremental rebuild of a batch (the steps since the previous rebuild ran
+// incremental rebuild (the steps since the previous rebuild ran
 // the fused tube test): marks from the core entries of the previous list,
 // their count and scan, the ascending ids + act + the leaving tiles' ids,
 // and the entries' info bytes, instances, per-instance counts and max |F|
 // with the leaving tiles' copies (leave: ntiles ints, nleave: one int).  The
 // flag arrays act and mark hold whole 16-byte chunks (zero padding); mark
 // is zero between rebuilds.
-cudaError_t launch_mark_batch(const int* list, const int* count, const uint8_t* core, uint8_t* mark,
-                              const Inst* d_inst, const uint16_t* tile_inst, long long ntiles,
-                              int conn, cudaStream_t s);
+cudaError_t launch_mark(const int* list, const int* count, const uint8_t* core, uint8_t* mark,
+                        const Inst* d_inst, const uint16_t* tile_inst, const Inst& single,
+                        long long ntiles, int conn, cudaStream_t s);
 cudaError_t launch_mark_count(const uint8_t* mark, long long ntiles, int* block_counts,
                               unsigned* done, int* count, int* nleave, cudaStream_t s);
 cudaError_t launch_mark_scatter(uint8_t* mark, uint8_t* act, long long ntiles,
@@ -270,6 +270,15 @@ cudaError_t launch_entry_batch(const int* list, const int* count, uint8_t* list_
                                int prec, unsigned long long* Mbits, int* inst_count,
                                const int* leave, const int* nleave, const void* cur, void* other,
                                cudaStream_t s);
+// single grid: info bytes, active / frozen-face bytes (xface_mode as
+// launch_scatter), max |F|, the leaving tiles' copies, dt in the last block
+cudaError_t launch_entry_single(const int* list, const int* count, uint8_t* list_info,
+                                const uint8_t* act, const uint8_t* tile_sgn, unsigned const_sgn,
+                                const Inst& single, long long ntiles, const void* tile_maxF, int prec,
+                                unsigned long long* Mbits, uint8_t* list_nact, int xface_mode,
+                                const int* leave, const int* nleave, const void* cur, void* other,
+                                StepScalars* sc, int dt_mode, double dt_value, unsigned* done,
+                                cudaStream_t s);
 cudaError_t launch_set_dt_batch(StepScalars* sc, int n_inst, const Inst* d_inst, int mode,
                                 double value, int finalize, int prec, unsigned long long* Mbits,
                                 int* inst_count, cudaStream_t s);

@@ -30,6 +30,8 @@ LS_PLAIN, LS_LEARNED = 0, 1
 LS_SCHEME_PLAIN, LS_SCHEME_LOCAL = 0, 1
 LS_OUTPUT_VTS, LS_OUTPUT_VTI = 0, 1
 LS_BC_EXTRAPOLATE, LS_BC_NEUMANN = 0, 1
+LS_REBUILD_AUTO, LS_REBUILD_FULL, LS_REBUILD_INCREMENTAL = 0, 1, 2
+LS_REBUILD_AUTO_TILES = 1 << 19
 LS_SHAPE_SPHERES, LS_SHAPE_TORUS, LS_SHAPE_SH = 0, 1, 2
 LS_SPEED_SINUSOID, LS_SPEED_COSCOS, LS_SPEED_FOURIER = 0, 1, 2
 
@@ -98,6 +100,7 @@ SIGNATURES = {
     "ls_set_step_mode": (_i, [_vp, _i]),
     "ls_set_scheme": (_i, [_vp, _i, _c.c_double, _i, _c.c_double]),
     "ls_set_dilation": (_i, [_vp, _i]),
+    "ls_set_rebuild_mode": (_i, [_vp, _i]),
     "ls_set_dense_kernel": (_i, [_vp, _i]),
     "ls_set_steps_per_pass": (_i, [_vp, _i]),
     "ls_get_steps_per_pass": (_i, [_vp, _c.POINTER(_i)]),
@@ -675,6 +678,9 @@ class LevelSet:
 
     def set_dilation(self, neighbours):
         check(self.lib.ls_set_dilation(self.ctx, int(neighbours)), "ls_set_dilation")
+
+    def set_rebuild_mode(self, mode):
+        check(self.lib.ls_set_rebuild_mode(self.ctx, int(mode)), "ls_set_rebuild_mode")
 
     def band_breaches(self):
         n = ctypes.c_ulonglong(0)

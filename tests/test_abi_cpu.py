@@ -93,6 +93,7 @@ codes = [
     lib.ls_conv3_wgrad(P, P, 48, 16, 16, 16, 16, P, P, P, None),  # nx not a multiple of 64
     lib.ls_conv3_wgrad(P, P, 64, 16, 16, 16, 16, P, P, None, None),  # no status word
     lib.ls_step(None, 1, 1.0, native.LS_DT_KEEP, 5, None),
+    lib.ls_set_rebuild_mode(None, native.LS_REBUILD_FULL),
 ]
 print(",".join(str(c) for c in codes))
 """

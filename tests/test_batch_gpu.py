@@ -39,9 +39,11 @@ def make_batch(insts, graphs=False):
     return b, phis
 
 
-def test_batch_matches_per_instance_oracle():
+@pytest.mark.parametrize("mode", [ls.LS_REBUILD_FULL, ls.LS_REBUILD_INCREMENTAL])
+def test_batch_matches_per_instance_oracle(mode):
     insts = small_batch()
     b, phis = make_batch(insts)
+    b.set_rebuild_mode(mode)
     b.band_rebuild(4.0)
     oracles = []
     for it, p in zip(insts, phis):
@@ -105,26 +107,23 @@ def test_batch_one_warp_rings_agree(stages, pct):
 
 
 def test_batch_incremental_rebuild_equals_full_scan():
-    """The periodic rebuild of a batch marks the new band from the core
-    entries of the previous list; on the full-size batch (256 grids of
-    32^3..192^3, 1.12 M tiles) it gives the list, the dt and, one step
-    later, the bits that a rebuild scanning every tile gives on the same
-    state (the leaving tiles' copies into the other buffer included)."""
+    """The periodic rebuilds of the full-size batch (256 grids of
+    32^3..192^3, 1.12 M tiles) marked from the previous list's core entries
+    give, over 40 steps (seven such rebuilds), the lists, dt and bits of
+    rebuilds that walk every tile (the leaving tiles' copies into the other
+    buffer included)."""
     dev = torch.device("cuda")
     insts = inputs.batch_instances()
     runs = []
-    for full in (False, True):
+    for mode in (ls.LS_REBUILD_FULL, ls.LS_REBUILD_INCREMENTAL):
         b = ls.Batch([i.edge for i in insts], [i.h for i in insts])
+        b.set_rebuild_mode(mode)
         for k, it in enumerate(insts):
             b.set_phi_i(k, it.phi(device=dev).to(torch.float32).contiguous())
             b.set_speed_const_i(k, it.speed)
         b.band_rebuild(4.0)
-        # 35 steps: the last periodic rebuild before step 30, the tube
-        # test at step 35
-        b.step(35, 0.5, ls.LS_DT_CFL, 5)
-        if full:
-            b.band_rebuild(4.0)            # every tile classified and scanned
-        b.step(1, 0.5, ls.LS_DT_CFL, 5)    # incremental rebuild first when not
+        b.step(40, 0.5, ls.LS_DT_CFL, 5)
+        b.step(1, 0.5, ls.LS_DT_CFL, 5)    # one more rebuild, then a step
         runs.append(([b.active_tiles_i(k) for k in range(len(insts))],
                      [b.last_dt_i(k) for k in range(len(insts))],
                      [torch.from_numpy(b.get_phi_i(k)) for k in range(len(insts))]))

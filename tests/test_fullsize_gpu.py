@@ -104,6 +104,38 @@ def test_sphere_union_512(config):
     assert np.array_equal(g.active_tiles(), band_from(state, w.halfwidth * w.h))
 
 
+@pytest.mark.parametrize("scheme", ["plain", "local"])
+def test_sphere_union_512_incremental_rebuild_equals_full_scan(scheme):
+    """The periodic rebuilds marked from the core entries of the previous
+    list (the tube test fused into the last step, or, in the local scheme,
+    into its last reinitialisation pass) give, on the 512^3 workload in the
+    benchmark's launch configuration over 40 steps, the list, the dt and the
+    bits (the frozen x-face copies and the leaving tiles' values included)
+    of rebuilds that walk every tile."""
+    w = inputs.SphereUnion()
+    runs = []
+    for mode in (ls.LS_REBUILD_FULL, ls.LS_REBUILD_INCREMENTAL):
+        g = ls.LevelSet(w.n, w.n, w.n, w.h, ls.LS_FP32)
+        g.set_step_config(2, 100, 16)
+        g.set_rebuild_mode(mode)
+        g.init_speed(ls.LS_SPEED_SINUSOID)
+        g.init_phi(ls.LS_SHAPE_SPHERES, inputs.spheres_params(w.centres, w.radii))
+        if scheme == "local":
+            g.set_scheme(ls.LS_SCHEME_LOCAL, 3.0, 12, 0.5)
+        g.band_rebuild(w.halfwidth)
+        g.step(40, w.cfl, ls.LS_DT_CFL, w.rebuild_every)
+        dt = g.step(1, w.cfl, ls.LS_DT_CFL, w.rebuild_every, want_dt=True)
+        out = torch.empty((w.n,) * 3, dtype=torch.float32, device="cuda")
+        g.get_phi(out)
+        runs.append((g.active_tiles(), dt, out))
+        g.close()
+    (la, da, pa), (lb, db, pb) = runs
+    assert len(la) > 10000
+    assert np.array_equal(la, lb)
+    assert da == db
+    assert torch.equal(pa, pb)
+
+
 def test_maximum_grid_fp32():
     """The largest grid the ABI accepts: 2^31 points (nx = ny = 1024,
     nz = 2048; 2^22 tiles, element offsets up to 2^31 - 1), FP32, three

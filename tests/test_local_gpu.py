@@ -76,10 +76,12 @@ def make(prec, phi, F, Fc=None, full=False, iters=K):
     return g, o
 
 
-@pytest.mark.parametrize("iters", [K, 0, -1])
-def test_fp64_trajectory_bitwise(iters):
+@pytest.mark.parametrize("iters,mode", [(K, ls.LS_REBUILD_FULL), (0, ls.LS_REBUILD_FULL),
+                                        (-1, ls.LS_REBUILD_FULL), (K, ls.LS_REBUILD_INCREMENTAL)])
+def test_fp64_trajectory_bitwise(iters, mode):
     phi, F = case()
     g, o = make(ls.LS_FP64, phi, F, iters=iters)
+    g.set_rebuild_mode(mode)
     for n in (1, 2, 4, 5):
         dg = g.step(n, 0.45, ls.LS_DT_CFL, 3, want_dt=True)
         do = o.step(n, 0.45, oracle.DT_CFL, 3)

@@ -81,16 +81,19 @@ def test_fp64_single_sphere_full_domain_bitwise():
 
 
 @pytest.mark.parametrize("device_inputs", [False, True])
-def test_fp64_narrow_band_field_bitwise(device_inputs):
+@pytest.mark.parametrize("mode", [ls.LS_REBUILD_FULL, ls.LS_REBUILD_INCREMENTAL])
+def test_fp64_narrow_band_field_bitwise(device_inputs, mode):
     """Union of spheres, sinusoidal F field, band 6h, rebuild every 5 steps,
     CFL 0.5, on a non-cubic grid: phi bit for bit and the active-tile set
-    identical at every rebuild."""
+    identical at every rebuild, with the periodic rebuilds walking every
+    tile or marked from the previous list's core entries."""
     shape = (64, 48, 80)
     h = 1.0 / 64
     w = inputs.SphereUnion(n=64, count=6)
     phi0 = inputs.sphere_union_sdf(shape, h, w.centres, w.radii).numpy()
     F = inputs.speed_sinusoid(shape, h).numpy()
     g, o = make_pair(shape, h, ls.LS_FP64, phi0, F=F, device_inputs=device_inputs)
+    g.set_rebuild_mode(mode)
     ng = g.band_rebuild(6.0)
     no = o.band_rebuild(6.0)
     assert ng == no
@@ -112,6 +115,7 @@ def test_fp64_six_neighbour_dilation_bitwise():
     o.set_phi(phi0)
     o.set_speed(F)
     g.set_dilation(6)
+    g.set_rebuild_mode(ls.LS_REBUILD_INCREMENTAL)   # the 6-neighbour marks
     n6 = g.band_rebuild(6.0)
     assert n6 == o.band_rebuild(6.0)
     g26, _ = make_pair(shape, h, ls.LS_FP64, phi0, F=F)
@@ -206,8 +210,9 @@ def test_fp32_sphere_union_reduced_size(config):
     assert err <= 1e-5 * w.h * nsteps, err
 
 
-@pytest.mark.parametrize("ppt", [4, 8, 16])
-def test_fp32_frozen_face_copies_follow_the_band(ppt):
+@pytest.mark.parametrize("ppt,mode", [(4, ls.LS_REBUILD_FULL), (8, ls.LS_REBUILD_FULL),
+                                      (16, ls.LS_REBUILD_FULL), (16, ls.LS_REBUILD_INCREMENTAL)])
+def test_fp32_frozen_face_copies_follow_the_band(ppt, mode):
     """The steps read the x-faces of frozen neighbours from copies made after
     each rebuild; the copies stay right through rebuilds with no step
     between them, graph replay in uneven chunks, the autotuner's probe
@@ -218,6 +223,7 @@ def test_fp32_frozen_face_copies_follow_the_band(ppt):
     F = w.speed().numpy()
     g, o = make_pair(shape, w.h, ls.LS_FP32, w.phi().numpy(), F=F)
     g.set_step_config(2, 100, ppt)
+    g.set_rebuild_mode(mode)
     for _ in range(2):  # two rebuilds, no step between them
         assert g.band_rebuild(w.halfwidth) == o.band_rebuild(w.halfwidth)
     g.set_graphs(True)
