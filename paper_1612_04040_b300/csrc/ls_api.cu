@@ -472,6 +472,9 @@ bool two_step_ok(const ls_ctx* c)
 int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_every, cudaStream_t s)
 {
     bool dt_pending = true;
+    // the previous launch of this call was a plain step over the current
+    // list and dt (the next step may read the list before waiting for it)
+    bool prev_step = false;
     for (int k = 0; k < nsteps;) {
         bool rebuilt = false;
         if (c->profiling && (!c->band_valid || (rebuild_every > 0 && c->since_rebuild >= rebuild_every) ||
@@ -489,7 +492,9 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
             RET(rebuild(c, false, s));
             rebuilt = true;
         }
+        if (rebuilt) prev_step = false;
         if (dt_pending && !rebuilt && dt_mode != LS_DT_KEEP) {
+            prev_step = false;
             if (c->batched)
                 KL(c, lsk::launch_set_dt_batch(c->d_sc, c->n_inst, c->d_inst, dt_mode, value, 0,
                                                c->prec, c->d_Mbits, c->d_inst_count, s));
@@ -517,6 +522,7 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
             RET(prof_before_stencil(c, 0, s, a));
             a.reverse = c->dir;
             KL(c, lsk::launch_step2(a, c->cfg, s));
+            prev_step = false;
             c->stencil_launches += 1;
             c->dir ^= 1;
             c->cur ^= 1;
@@ -563,9 +569,12 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
             if (!local && c->full_domain && c->cfg.dense && two_step_ok(c)) {
                 a.tile_sgn = sign_table(c);
                 KL(c, lsk::launch_dense_step(a, c->cfg, s));
+                prev_step = false;
             } else {
+                a.early = (prev_step && !local) ? 1 : 0;
                 KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
                 if (a.xface_fill) c->xface_pending = false;  // this step wrote the copies
+                prev_step = !local && c->step_mode != LS_LEARNED;
             }
             ++c->stencil_launches;
             c->dir ^= 1;
@@ -591,6 +600,7 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
         if (c->output && c->step_count % c->output_every == 0) {
             if (c->profiling) RET(prof_close(c, s));
             RET(ls_engine_output_after_step(c, s));
+            prev_step = false;
         }
     }
     if (c->profiling) RET(prof_close(c, s));

@@ -187,6 +187,9 @@ struct StepArgs {
     Inst in;                  // single instance parameters (bc is read from here always)
     int max_grid;             // cap on the persistent grid (0 = none)
     int reverse;              // FP32: walk the list from its end (L2 reuse across launches)
+    int early;                // the previous launch was a step over the same list and
+                              // dt: the list, its count and the scalars may be read
+                              // before the wait for that launch (one-warp kernel)
     const uint8_t* tile_sgn;  // full-domain column kernel: per-tile sign class of F, or NULL
     // local scheme (single instance, 4 points per thread)
     int op;                   // OP_*

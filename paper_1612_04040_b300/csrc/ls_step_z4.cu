@@ -106,9 +106,12 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     const int xh = tid & 1, ly = (tid >> 1) & 7, lzq = tid >> 4;
     const int lz0 = 4 * lzq;
     const int q0 = (tid & 15) + 64 * lzq;  // quad of plane lz0; plane lz0 + j: q0 + 16 j
-    // everything this grid reads may come from the previous grid
+    // what this grid reads may come from the previous grid; when that grid
+    // was a step over the same list (early), only the tiles' values do, so
+    // the list entries of the first tiles are loaded before the wait
     pdl_launch_dependents();
-    pdl_wait();
+    const bool early = a.early != 0;
+    if (!early) pdl_wait();
     const int n = *a.count;
     // every other launch walks the list backwards (L2 reuse across launches)
     const bool rev = a.reverse != 0;
@@ -217,21 +220,29 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     // tile ids of the staged entries in the order they are computed, so
     // that a tile's speeds can be requested before the ring wait
     unsigned tq[S - 1];
+    EntZ4 e0[S - 1];
+    EntZ4 e1_init = {};
     int kn = blockIdx.x;
 #pragma unroll
     for (int s = 0; s < S - 1; ++s) {
         tq[s] = 0u;
-        if (kn < n) {
-            EntZ4 e;
-            fetch(kn, e);
-            issue(e, s);
-            tq[s] = e.t;
+        if (kn + s * stride < n) {
+            fetch(kn + s * stride, e0[s]);
+            tq[s] = e0[s].t;
         }
+    }
+    {
+        const int k1 = kn + (S - 1) * stride;
+        if (k1 < n) fetch(k1, e1_init);
+    }
+    if (early) pdl_wait();
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s) {
+        if (kn < n) issue(e0[s], s);
         cp_async_commit();
         kn += stride;
     }
-    EntZ4 e1 = {}, e2 = {}, e3 = {};
-    if (kn < n) fetch(kn, e1);
+    EntZ4 e1 = e1_init, e2 = {}, e3 = {};
     if (kn + stride < n) fetch(kn + stride, e2);
     if (BATCHED && kn + 2 * stride < n) fetch_entry(kn + 2 * stride, e3);
     int cur = 0;
