@@ -1035,7 +1035,9 @@ def main():
                     "share_of_step_time": rein_s / t_s if t_s > 0 else None}
         roofline_advance = {"bound": "hbm", "achieved": a_adv, "peak": peak, "unit": "GB/s",
                             "frac": (a_adv / peak) if a_adv else None,
-                            "kernel": "k_step_f32<..., OP_CUT> (Eq. 8 advance + N mask)",
+                            "kernel": ("k_local_z4<..., OP_CUT> (Eq. 8 advance + N mask, one warp per tile)"
+                                       if tuned[2] == 16 else
+                                       "k_step_f32<..., OP_CUT> (Eq. 8 advance + N mask, 4 points per thread)"),
                             "bytes_per_update": b_adv, "avg_launch_us": 1e6 * adv_s / n_adv,
                             "launches": n_adv, "share_of_step_time": adv_s / t_s if t_s > 0 else None}
 
