@@ -132,7 +132,12 @@ __global__ void __launch_bounds__(32, 16) k_step_f32_z4(StepArgs a)
     const double gamma1 = a.in.gamma;
     const int sy1 = a.in.tnx * TILE_PTS;
     const int sz1 = a.in.tnx * a.in.tny * TILE_PTS;
-    const int stride = gridDim.x;
+    // as many rounds over the list as the whole grid needs, spread evenly
+    // over the CTAs (no last round with a fraction of them busy: 512^3
+    // sphere union 475.1 -> 476.0 GLUPS)
+    const int rounds = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int stride = rounds > 0 ? (n + rounds - 1) / rounds : (int)gridDim.x;
+    if ((int)blockIdx.x >= stride) return;
     // halo sources of plane lz0 (plane lz0 + j: + 64 j elements)
     const int x_off0 = xh ? (TILE_PTS + lz0 * 64 + ly * 8) : (-TILE_PTS + lz0 * 64 + ly * 8 + 7);
     const unsigned x_bit = xh ? NB_XP : NB_XM;
