@@ -571,7 +571,9 @@ int run_steps(ls_ctx* c, int nsteps, double value, int dt_mode, int rebuild_ever
                 KL(c, lsk::launch_dense_step(a, c->cfg, s));
                 prev_step = false;
             } else {
-                a.early = (prev_step && !local) ? 1 : 0;
+                // reinitialisation passes after the first: the previous launch
+                // was the pass before, over the same list of N tiles
+                a.early = local ? (p >= 2 ? 1 : 0) : (prev_step ? 1 : 0);
                 KL(c, lsk::launch_step(a, c->prec, c->cfg, s));
                 if (a.xface_fill) c->xface_pending = false;  // this step wrote the copies
                 prev_step = !local && c->step_mode != LS_LEARNED;

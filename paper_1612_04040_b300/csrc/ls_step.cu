@@ -334,9 +334,12 @@ __global__ void __launch_bounds__(64, OP >= OP_REINIT ? 10 : 16) k_step_f32_z2(S
     const int xh = tid & 1, ly = (tid >> 1) & 7, lzp = tid >> 4;
     const int q0 = tid + 16 * lzp, q1 = q0 + 16;
     const int lz0 = 2 * lzp;
-    // everything this grid reads may come from the previous grid
+    // what this grid reads may come from the previous grid; when that grid
+    // was a pass over the same list (early), only the tiles' values and N
+    // bits do, so the first entries are loaded before the wait
     pdl_launch_dependents();
-    pdl_wait();
+    const bool early = a.early != 0;
+    if (!early) pdl_wait();
     const int n = *a.count;
     // list position of the k-th entry processed: every other launch walks the
     // list backwards, so it starts on the tiles the previous launch wrote
@@ -359,6 +362,8 @@ __global__ void __launch_bounds__(64, OP >= OP_REINIT ? 10 : 16) k_step_f32_z2(S
     const double gamma1 = a.in.gamma;
     const int sy1 = a.in.tnx * TILE_PTS;
     const int sz1 = a.in.tnx * a.in.tny * TILE_PTS;
+    // (rounds spread evenly over the CTAs, as in the one-warp kernel,
+    // measured slower here: reinitialisation pass 38.7 against 37.4 us)
     const int stride = gridDim.x;
     const int x_off0 = xh ? (TILE_PTS + lz0 * 64 + ly * 8) : (-TILE_PTS + lz0 * 64 + ly * 8 + 7);
     const unsigned x_bit = xh ? NB_XP : NB_XM;
@@ -430,19 +435,20 @@ __global__ void __launch_bounds__(64, OP >= OP_REINIT ? 10 : 16) k_step_f32_z2(S
     auto gamma_of = [&](int inst) -> double { return BATCHED ? a.insts[inst].gamma : gamma1; };
 
     int kn = blockIdx.x;
+    unsigned pt[S - 1], pi[S - 1], pn[S - 1];
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s)
+        if (kn + s * stride < n) fetch(kn + s * stride, pt[s], pi[s], pn[s]);
+    unsigned t1 = 0, i1 = 0, n1 = 0, t2 = 0, i2 = 0, n2 = 0;
+    if (kn + (S - 1) * stride < n) fetch(kn + (S - 1) * stride, t1, i1, n1);
+    if (kn + S * stride < n) fetch(kn + S * stride, t2, i2, n2);
+    if (early) pdl_wait();
 #pragma unroll
     for (int s = 0; s < S - 1; ++s) {
-        if (kn < n) {
-            unsigned t, info, inst;
-            fetch(kn, t, info, inst);
-            issue(t, info, inst, s, kn);
-        }
+        if (kn < n) issue(pt[s], pi[s], pn[s], s, kn);
         cp_async_commit();
         kn += stride;
     }
-    unsigned t1 = 0, i1 = 0, n1 = 0, t2 = 0, i2 = 0, n2 = 0;
-    if (kn < n) fetch(kn, t1, i1, n1);
-    if (kn + stride < n) fetch(kn + stride, t2, i2, n2);
     int cur = 0, prev = -1, prev_t = -1, prev_inst = 0;
     for (int k = blockIdx.x; k < n; k += stride) {
         cp_async_wait<S - 2>();
