@@ -414,4 +414,9 @@ def test_state_errors():
     with pytest.raises(ls.LSError) as e:
         g.band_rebuild(-1.0)
     assert e.value.status == ls.LS_EINVAL
+    for mode in (ls.LS_REBUILD_AUTO, ls.LS_REBUILD_FULL, ls.LS_REBUILD_INCREMENTAL):
+        g.set_rebuild_mode(mode)
+    with pytest.raises(ls.LSError) as e:
+        g.set_rebuild_mode(3)
+    assert e.value.status == ls.LS_EINVAL
     assert g.status() == ls.LS_OK
