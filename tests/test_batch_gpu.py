@@ -159,11 +159,13 @@ def test_single_grid_constant_speed_one_warp_agrees(F):
             assert np.array_equal(out, ref), cfg
 
 
-def test_batch_graph_replay_equals_eager():
+@pytest.mark.parametrize("mode", [ls.LS_REBUILD_FULL, ls.LS_REBUILD_INCREMENTAL])
+def test_batch_graph_replay_equals_eager(mode):
     insts = small_batch(count=5, seed=9)
     outs = []
     for graphs in (False, True):
         b, _ = make_batch(insts, graphs=graphs)
+        b.set_rebuild_mode(mode)
         b.band_rebuild(4.0)
         for _ in range(3):
             b.step(7, 0.5, ls.LS_DT_CFL, 5)   # the same call three times: replayed
@@ -174,17 +176,20 @@ def test_batch_graph_replay_equals_eager():
 
 
 def test_single_grid_graph_and_autotune_bitwise():
-    """Graph replay and every autotuner configuration compute the same bits."""
+    """Graph replay (with either rebuild) and every autotuner configuration
+    compute the same bits."""
     w = inputs.SphereUnion(n=64, count=5)
     p = w.phi().numpy().astype(np.float32)
     F = w.speed().numpy().astype(np.float32)
     outs = []
-    for mode in ("eager", "graph", "tuned"):
+    for mode in ("eager", "graph", "tuned", "graph-incremental"):
         g = ls.LevelSet(64, 64, 64, w.h, ls.LS_FP32)
         g.set_phi(p)
         g.set_speed(F)
+        if mode == "graph-incremental":
+            g.set_rebuild_mode(ls.LS_REBUILD_INCREMENTAL)
         g.band_rebuild(6.0)
-        if mode == "graph":
+        if mode.startswith("graph"):
             g.set_graphs(True)
         if mode == "tuned":
             g.step(1, 0.5, ls.LS_DT_CFL, 5)
@@ -200,6 +205,7 @@ def test_single_grid_graph_and_autotune_bitwise():
         g.close()
     assert np.array_equal(outs[0], outs[1])
     assert np.array_equal(outs[0], outs[2])
+    assert np.array_equal(outs[0], outs[3])
 
 
 @pytest.mark.parametrize("stages,pct,ppt", [(2, 50, 4), (4, 100, 8), (3, 75, 4), (2, 100, 8), (6, 100, 4), (6, 75, 8),
