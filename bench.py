@@ -530,7 +530,7 @@ def restrict_to(a, factor):
 
 def run_learned(args):
     """Learned corrector on the 128^3 coarse grid, trained on pairs from
-    512^3 plain runs (random sphere unions, 8-mode Fourier F), judged against
+    512^3 plain runs (random sphere unions, 8-mode Fourier F), measured against
     the 512^3 plain run; plain runs at 128^3, 256^3 and 512^3 give the
     error/wall-time curve the learned run is placed on."""
     import numpy as np

@@ -1,7 +1,7 @@
 """The corrector end to end on a reduced grid: pairs from fine plain runs,
 training on the GPU with the library's own forward / backward kernels, and
 what the trained network gains over the plain coarse method against the
-restricted fine run (the judge of its error)."""
+restricted fine run (the reference for its error)."""
 import numpy as np
 import pytest
 import torch
