@@ -83,7 +83,7 @@ __device__ __forceinline__ bool bulk_wait(unsigned bar, unsigned parity, long lo
 }
 
 // hardware reciprocal square root (approximate, flush-to-zero): the inputs
-// here are clamped to >= 1e-30, so no denormal reaches it
+// here are at least 1e-30, so no denormal reaches it
 __device__ __forceinline__ float rsqrt_hw(float x)
 {
     float r;
@@ -281,7 +281,10 @@ __device__ __forceinline__ float4 rei4(const float4& c, float xm0, float xp3, co
         q = fmaf(az, az, q);
         q = fmaf(bz, bz, q);
         const float gu = sqrt_hw(q);
-        const float S = d * rsqrt_hw(fmaxf(fmaf(d, d, q), 1e-30f));
+        // d^2 + q + 1e-30 >= 1e-30 (the guard as an add on the FMA pipe
+        // rather than a max on the ALU pipe, which this pass keeps busy:
+        // 37.14 -> 36.79 us per pass; the two agree once d^2 + q > 2e-23)
+        const float S = d * rsqrt_hw(fmaf(d, d, q + 1e-30f));
         float v = fmaf(-S, fmaf(lp.lam, gu, -lp.dtau_f), d);
         if (CLAMP) v = fminf(fmaxf(v, -lp.gamma_up), lp.gamma_up);
         r[j] = ((nb >> j) & 1u) ? v : d;
