@@ -235,8 +235,9 @@ __device__ __forceinline__ unsigned n_nibble(const float4& c, float xm0, float x
 // (Eq. 13) with unscaled differences (|Dd| h = sqrt(q)), then
 // d - dtau S (|grad d| - 1); CLAMP: Eq. 10 afterwards, to +-(smallest float
 // >= gamma), so that a clamped value stays outside T as in FP64.
-// SGN = +1 / -1: every N point of the warp has d >= 0 / d <= 0 (d = 0 gives
-// S = 0 on either path); SGN = 0: per point, through G-(d) = G+(-d).
+// SGN = +1 / -1: every N point of the warp has its sign bit clear / set
+// (d >= +0 / d <= -0; a zero gets S = 0 and keeps its value on any path);
+// SGN = 0: per point, through G-(d) = G+(-d).
 template <int SGN, bool FACES, bool CLAMP>
 __device__ __forceinline__ float4 rei4(const float4& c, float xm0, float xp3, const float4& ym,
                                        const float4& yp, const float4& zm, const float4& zp,
@@ -302,14 +303,18 @@ __device__ __forceinline__ float4 rei_tile(const float4& c, float xm0, float xp3
                                            bool zhi)
 {
     if (!__any_sync(0xffffffffu, nb != 0u)) return c;
-    const unsigned neg = (c.x < 0.f ? 1u : 0u) | (c.y < 0.f ? 2u : 0u) | (c.z < 0.f ? 4u : 0u) |
-                         (c.w < 0.f ? 8u : 0u);
-    const unsigned pos = (c.x > 0.f ? 1u : 0u) | (c.y > 0.f ? 2u : 0u) | (c.z > 0.f ? 4u : 0u) |
-                         (c.w > 0.f ? 8u : 0u);
-    if (__all_sync(0xffffffffu, (nb & neg) == 0u))
+    // the sign bytes of the four values gathered into one word, and the N
+    // bits spread to the sign bit of each byte (the multiplies run on the
+    // FMA pipe; the float compares they replace kept the ALU pipe, which
+    // bounds this pass, busier: 36.8 -> 35.5 us per pass).  A zero takes the
+    // path of its sign bit; either path gives it S = 0.
+    const unsigned sb = __byte_perm(__byte_perm(__float_as_uint(c.x), __float_as_uint(c.y), 0x0073),
+                                    __byte_perm(__float_as_uint(c.z), __float_as_uint(c.w), 0x0073), 0x5410);
+    const unsigned nbm = ((nb * 0x00204081u) & 0x01010101u) * 0x80u;
+    if (__all_sync(0xffffffffu, (sb & nbm) == 0u))
         return rei4<1, FACES, CLAMP>(c, xm0, xp3, ym, yp, zm, zp, nb, lp, extrap, xlo, xhi, ylo,
                                      yhi, zlo, zhi);
-    if (__all_sync(0xffffffffu, (nb & pos) == 0u))
+    if (__all_sync(0xffffffffu, (~sb & nbm) == 0u))
         return rei4<-1, FACES, CLAMP>(c, xm0, xp3, ym, yp, zm, zp, nb, lp, extrap, xlo, xhi, ylo,
                                       yhi, zlo, zhi);
     return rei4<0, FACES, CLAMP>(c, xm0, xp3, ym, yp, zm, zp, nb, lp, extrap, xlo, xhi, ylo, yhi,
