@@ -159,7 +159,9 @@ enum : int { OP_PLAIN = 0, OP_CUT = 1, OP_CUT_CLAMP = 2, OP_REINIT = 3, OP_REINI
 struct LocalParams {
     double beta, gamma;   // Eq. 7 thresholds (FP64)
     double dtau;          // pseudo-time step of Eq. 12
-    float beta_dn;        // largest float <= beta: FP32 |phi| <= beta decided as in FP64
+    float beta_dn;        // largest float <= beta (the FP32 kernels no longer test it;
+                          // without it the parameter block measured slower for the
+                          // reinitialisation pass, 35.3 against 34.9 us)
     float gamma_up;       // smallest float >= gamma: FP32 |phi| < gamma decided as in FP64,
                           // and the clamp bound (a clamped value is not in T)
     float beta_n, gamma_n;  // nearest floats (the cubic of Eq. 7)

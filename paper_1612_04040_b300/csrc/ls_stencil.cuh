@@ -183,15 +183,17 @@ __device__ __forceinline__ float4 upd4(const float4& c, const float4& f, float x
 // ------------------------------------------------- local scheme, FP32 ----
 // Eq. 7 at a = |phi|, branch-free: with s = (a - beta)/(gamma - beta) the
 // cubic is 1 - 3 s^2 + 2 s^3 (the paper's (a-gamma)^2 (2a + gamma - 3 beta)
-// / (gamma - beta)^3 expanded), s clamped to [0, 1].  The two end tests use
-// thresholds rounded outward on the host (largest float <= beta, smallest
-// float >= gamma), so they decide exactly as the FP64 comparisons do.
+// / (gamma - beta)^3 expanded), s clamped to [0, 1].  The end at gamma is
+// tested against the smallest float >= gamma (rounded outward on the host),
+// so it decides exactly as the FP64 comparison does.  The end at beta needs
+// no test: every a <= beta (at most the largest float <= beta, which is at
+// most the nearest float beta_n) gives a - beta_n <= 0, s = 0 and c = 1
+// exactly.
 __device__ __forceinline__ float cut32(float a, const LocalParams& lp)
 {
     const float s = __saturatef((a - lp.beta_n) * lp.inv_w);
-    float c = fmaf(s * s, fmaf(2.f, s, -3.f), 1.f);
-    c = a < lp.gamma_up ? c : 0.f;
-    return a <= lp.beta_dn ? 1.f : c;
+    const float c = fmaf(s * s, fmaf(2.f, s, -3.f), 1.f);
+    return a < lp.gamma_up ? c : 0.f;
 }
 
 // Eq. 11 for the thread's four points: bit j set when point j or one of its
