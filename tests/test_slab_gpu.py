@@ -36,9 +36,10 @@ def fields(dtype):
     return phi, np.ascontiguousarray(F)
 
 
-def unsplit(phi, F, prec):
+def unsplit(phi, F, prec, mode=ls.LS_REBUILD_AUTO):
     nz, ny, nx = SHAPE
     g = ls.LevelSet(nx, ny, nz, H, prec)
+    g.set_rebuild_mode(mode)
     g.set_phi(phi)
     g.set_speed(F)
     g.band_rebuild(HW)
@@ -48,11 +49,13 @@ def unsplit(phi, F, prec):
     return out, dt
 
 
-def split(phi, F, prec, nparts):
+def split(phi, F, prec, nparts, mode=ls.LS_REBUILD_AUTO):
     dphi, dF = torch.from_numpy(phi).cuda(), torch.from_numpy(F).cuda()
 
     def make(nx, ny, rows, h, lo, hi):
-        return slab.GpuSlab(nx, ny, rows, h, lo, hi, prec)
+        part = slab.GpuSlab(nx, ny, rows, h, lo, hi, prec)
+        part.ctx.set_rebuild_mode(mode)
+        return part
 
     run = slab.SlabRun(slab.LocalComm(nparts), make, SHAPE, H, HW, lambda z0, z1: (dphi[z0:z1], dF[z0:z1]))
     first = run.migrations
@@ -77,6 +80,17 @@ def test_split_equals_unsplit_bitwise(prec, nparts):
                           ref.view(np.int32 if prec == ls.LS_FP32 else np.int64))
     if nparts >= 3:
         assert moved >= 1, bounds
+
+
+def test_split_with_incremental_rebuild_mode_equals_unsplit_bitwise():
+    """Slab contexts hold ghost rows, so their rebuilds walk every tile even
+    with the incremental rebuild asked for; the split run still equals one
+    grid whose periodic rebuilds are incremental."""
+    phi, F = fields(np.float32)
+    ref, ref_dt = unsplit(phi, F, ls.LS_FP32, ls.LS_REBUILD_INCREMENTAL)
+    got, dt, _, _ = split(phi, F, ls.LS_FP32, 2, ls.LS_REBUILD_INCREMENTAL)
+    assert dt == ref_dt
+    assert np.array_equal(got.view(np.int32), ref.view(np.int32))
 
 
 def split_device(phi, F, prec, nparts, graphs):
