@@ -292,6 +292,32 @@ def cpu_baseline(phi0_f32, F_f32, w, steps=40):
     return out, o
 
 
+def oracle_one_thread(o, w, steps=2):
+    """The same oracle continued for `steps` further level-set steps on one
+    host thread (OpenMP's thread count of the calling thread set through
+    libgomp, then restored), beside the all-threads figure; None where
+    libgomp cannot be loaded."""
+    import ctypes
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+    except OSError:
+        return None
+    import oracle
+    nmax = gomp.omp_get_max_threads()
+    gomp.omp_set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        updates = 0
+        for _ in range(steps):
+            o.step(1, w.cfl, oracle.DT_CFL, w.rebuild_every)
+            updates += int(o.active.sum()) * 512
+        t = time.perf_counter() - t0
+    finally:
+        gomp.omp_set_num_threads(nmax)
+    return {"value": updates / t / 1e9, "unit": UNIT, "cores": 1,
+            "sample": "%d further level-set steps of the same run on one host thread, %.1f s" % (steps, t)}
+
+
 def parity_vs_oracle(g, o, w, steps):
     """The GPU's state after the same first `steps` steps, against the
     oracle's: max |phi_gpu - phi_oracle| over the points of the oracle's
@@ -1082,6 +1108,7 @@ def main():
         else:
             cpu, orc = cpu_baseline(phi0.cpu().numpy(), F_np, w)
             cpu["parity"] = parity_vs_oracle(g, orc, w, 40)
+            cpu["single_thread"] = oracle_one_thread(orc, w)
             del orc
 
     # band points (|phi| < gamma) of the final state of the last run
